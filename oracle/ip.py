@@ -1,0 +1,125 @@
+"""Incremental potential for one implicit-Euler timestep (oracle).
+
+Eq. IP with implicit Euler (Sec. 3.1): alpha = 1, predictor
+x_tilde = x^t + h v^t, velocity update v^{t+1} = (x^{t+1} - x^t) / h.
+Readings used where the paper is silent:
+
+* mass: lumped, m_v = sum over tets e containing v of rho_e vol_e / 4;
+* gravity g enters through the predictor, x_tilde = x^t + h v^t + h^2 g
+  (equivalent to the potential -M g . x in the h^2-scaled bracket);
+* friction D = 0 (no workload uses friction);
+* Dirichlet vertices are held at x^t: they are not unknowns, their inertia
+  term is dropped, their gradient entries are zero and their Hessian rows
+  and columns are the identity.
+
+    E(x) = 1/2 sum_{v free} m_v |x_v - x_tilde_v|^2
+           + h^2 ( sum_e vol_e psi(F_e(x)) + kappa sum_v b(n . x_v - o) ).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import barrier, elastic
+
+
+class Problem:
+    """One timestep's incremental potential built from a synthetic scene."""
+
+    def __init__(self, scene, x_t=None, v_t=None, dt=None, project=True):
+        self.X = np.asarray(scene.X, dtype=np.float64)
+        self.tets = np.asarray(scene.tets, dtype=np.int64)
+        self.n = self.X.shape[0]
+        self.vol, self.Dm_inv = elastic.rest_shape(self.X, self.tets)
+        self.mu, self.lam = elastic.lame(scene.E, scene.nu)
+        rho = np.asarray(scene.rho, dtype=np.float64)
+        self.mass = np.zeros(self.n)
+        np.add.at(self.mass, self.tets.ravel(), np.repeat(rho * self.vol / 4.0, 4))
+        self.pinned = np.asarray(scene.dirichlet).astype(bool)
+        self.free = ~self.pinned
+        self.h = float(scene.dt if dt is None else dt)
+        self.gravity = np.asarray(scene.gravity, dtype=np.float64)
+        self.contact = bool(scene.contact)
+        self.plane_n = np.asarray(scene.plane_n, dtype=np.float64)
+        self.plane_o = float(scene.plane_o)
+        self.dhat = float(scene.dhat)
+        self.kappa = float(scene.kappa)
+        self.project = project
+        self.x_t = np.array(scene.x0 if x_t is None else x_t, dtype=np.float64)
+        self.v_t = np.array(scene.v0 if v_t is None else v_t, dtype=np.float64)
+        self.x_tilde = self.x_t + self.h * self.v_t + self.h ** 2 * self.gravity[None, :]
+        self.x_tilde[self.pinned] = self.x_t[self.pinned]
+
+    # -- pieces -----------------------------------------------------------
+    def distances(self, x):
+        return x @ self.plane_n - self.plane_o
+
+    def energy(self, x):
+        """E(x); +inf if a tet is inverted or a vertex is on/below the plane."""
+        x = np.asarray(x, dtype=np.float64)
+        dx = x[self.free] - self.x_tilde[self.free]
+        K = 0.5 * np.sum(self.mass[self.free] * np.sum(dx * dx, axis=1))
+        Psi = np.sum(elastic.element_energy(x, self.tets, self.vol, self.Dm_inv,
+                                            self.mu, self.lam))
+        B = 0.0
+        if self.contact:
+            B = self.kappa * np.sum(barrier.b(self.distances(x), self.dhat))
+        return K + self.h ** 2 * (Psi + B)
+
+    def gradient(self, x):
+        """dE/dx as [n,3]; zero on Dirichlet vertices."""
+        x = np.asarray(x, dtype=np.float64)
+        g = self.mass[:, None] * (x - self.x_tilde)
+        ge = elastic.element_gradient(x, self.tets, self.vol, self.Dm_inv, self.mu, self.lam)
+        gel = np.zeros((self.n, 3))
+        np.add.at(gel, self.tets.ravel(), ge.reshape(-1, 3))
+        if self.contact:
+            gel += self.kappa * barrier.db(self.distances(x), self.dhat)[:, None] \
+                * self.plane_n[None, :]
+        g += self.h ** 2 * gel
+        g[self.pinned] = 0.0
+        return g
+
+    def hessian(self, x):
+        """Projected Hessian as a (3n x 3n) CSR matrix:
+        M + h^2 (sum_e vol_e B^T [dP/dF]_+ B + kappa sum_v b''(d_v) n n^T),
+        with Dirichlet rows and columns replaced by the identity."""
+        x = np.asarray(x, dtype=np.float64)
+        He = elastic.element_hessian(x, self.tets, self.vol, self.Dm_inv, self.mu,
+                                     self.lam, project=self.project)
+        dof = (3 * self.tets[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
+        rows = np.repeat(dof, 12, axis=1).ravel()
+        cols = np.tile(dof, (1, 12)).ravel()
+        vals = (self.h ** 2 * He).ravel()
+        diag_idx = np.arange(3 * self.n)
+        diag_val = np.repeat(self.mass, 3)
+        rows = np.concatenate([rows, diag_idx])
+        cols = np.concatenate([cols, diag_idx])
+        vals = np.concatenate([vals, diag_val])
+        if self.contact:
+            k2 = self.kappa * barrier.d2b(self.distances(x), self.dhat)
+            nn = np.outer(self.plane_n, self.plane_n)
+            act = np.nonzero(k2)[0]
+            r = (3 * act[:, None, None] + np.arange(3)[None, :, None]).repeat(3, 2)
+            c = (3 * act[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1)
+            rows = np.concatenate([rows, r.ravel()])
+            cols = np.concatenate([cols, c.ravel()])
+            vals = np.concatenate([vals, (self.h ** 2 * k2[act, None, None] * nn[None]).ravel()])
+        H = sp.coo_matrix((vals, (rows, cols)), shape=(3 * self.n, 3 * self.n)).tocsr()
+        fixed = np.repeat(self.pinned, 3)
+        if fixed.any():
+            keep = sp.diags((~fixed).astype(np.float64))
+            H = (keep @ H @ keep + sp.diags(fixed.astype(np.float64))).tocsr()
+        H.sum_duplicates()
+        H.eliminate_zeros()
+        return H
+
+    def feasible(self, x):
+        """True when every tet has J > 0 and, with contact, every vertex is
+        strictly above the plane."""
+        F = elastic.deformation_gradient(x, self.tets, self.Dm_inv)
+        if np.any(np.linalg.det(F) <= 0):
+            return False
+        if self.contact and np.any(self.distances(x) <= 0):
+            return False
+        return True

@@ -1,0 +1,196 @@
+"""Pins for the oracle's barrier, incremental potential, Newton timestep and
+PCG (no GPU)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import barrier, ip, newton, pcg
+
+rng = np.random.default_rng(99)
+
+
+# -- barrier -----------------------------------------------------------------
+def test_barrier_closed_form_points():
+    dhat = 1e-3
+    # at d = dhat / e: ln(d/dhat) = -1, so b = (d - dhat)^2
+    d = dhat / np.e
+    assert barrier.b(np.array([d]), dhat)[0] == pytest.approx((d - dhat) ** 2, rel=1e-14)
+    assert barrier.db(np.array([d]), dhat)[0] == pytest.approx(2 * (d - dhat) - (d - dhat) ** 2 / d, rel=1e-13)
+
+
+def test_barrier_vanishes_smoothly_at_dhat():
+    dhat = 1e-3
+    d = np.array([dhat, 2 * dhat, dhat * (1 - 1e-9)])
+    assert np.allclose(barrier.b(d, dhat), 0.0, atol=1e-20)
+    assert np.allclose(barrier.db(d, dhat), 0.0, atol=1e-14)
+    assert np.allclose(barrier.d2b(d, dhat), 0.0, atol=1e-5)
+
+
+def test_barrier_derivatives_finite_differences():
+    dhat = 1e-3
+    d = np.linspace(0.05, 0.95, 19) * dhat
+    eps = 1e-10
+    fd1 = (barrier.b(d + eps, dhat) - barrier.b(d - eps, dhat)) / (2 * eps)
+    fd2 = (barrier.db(d + eps, dhat) - barrier.db(d - eps, dhat)) / (2 * eps)
+    assert np.allclose(barrier.db(d, dhat), fd1, rtol=1e-5)
+    assert np.allclose(barrier.d2b(d, dhat), fd2, rtol=1e-5)
+
+
+def test_barrier_convex_and_infinite_below_plane():
+    dhat = 1e-3
+    d = np.linspace(1e-6, 0.999, 50) * dhat
+    assert np.all(barrier.d2b(d, dhat) > 0)
+    assert np.isinf(barrier.b(np.array([0.0, -1e-4]), dhat)).all()
+
+
+# -- incremental potential ----------------------------------------------------
+def _problem(contact=False):
+    s = synth.tiny_scene(2, 2, 1, seed=7, contact=contact, pinned=not contact)
+    return s, ip.Problem(s)
+
+
+def test_lumped_mass_totals():
+    s, p = _problem()
+    assert p.mass.sum() == pytest.approx(np.sum(s.rho * p.vol), rel=1e-13)
+    # the unit cube's six-tet voxels add up to its volume
+    c = ip.Problem(synth.cube_scene())
+    assert c.vol.sum() == pytest.approx(1.0, rel=1e-13)
+    assert c.mass.sum() == pytest.approx(1000.0, rel=1e-13)
+
+
+@pytest.mark.parametrize("contact", [False, True])
+def test_gradient_matches_finite_differences(contact):
+    s, p = _problem(contact)
+    x = p.x_tilde + 1e-4 * rng.normal(size=p.x_tilde.shape)
+    if contact:
+        x[:, 2] = np.maximum(x[:, 2], 2e-4)
+    x[p.pinned] = p.x_t[p.pinned]
+    g = p.gradient(x)
+    eps = 1e-8
+    for v in range(0, p.n, 3):
+        if p.pinned[v]:
+            continue
+        for c in range(3):
+            xp = x.copy(); xp[v, c] += eps
+            xm = x.copy(); xm[v, c] -= eps
+            fd = (p.energy(xp) - p.energy(xm)) / (2 * eps)
+            assert fd == pytest.approx(g[v, c], rel=1e-4, abs=1e-7 * np.abs(g).max())
+
+
+@pytest.mark.parametrize("contact", [False, True])
+def test_unprojected_hessian_matches_finite_differences(contact):
+    s, p = _problem(contact)
+    p.project = False
+    x = p.x_tilde + 1e-4 * rng.normal(size=p.x_tilde.shape)
+    if contact:
+        x[:, 2] = np.maximum(x[:, 2], 2e-4)
+    x[p.pinned] = p.x_t[p.pinned]
+    H = p.hessian(x).toarray()
+    eps = 1e-8
+    for v in range(p.n):
+        if p.pinned[v]:
+            continue
+        for c in range(3):
+            xp = x.copy(); xp[v, c] += eps
+            xm = x.copy(); xm[v, c] -= eps
+            fd = ((p.gradient(xp) - p.gradient(xm)) / (2 * eps)).ravel()
+            col = H[:, 3 * v + c].copy()
+            col[np.repeat(p.pinned, 3)] = 0.0
+            assert np.allclose(col, fd, rtol=1e-4, atol=1e-6 * np.abs(H).max())
+
+
+def test_hessian_symmetric_positive_definite():
+    s, p = _problem(True)
+    x = p.x_tilde.copy()
+    H = p.hessian(x).toarray()
+    assert np.allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+    assert np.linalg.eigvalsh(H).min() > 0
+
+
+# -- Newton timestep -----------------------------------------------------------
+def test_uniform_translation_is_exact():
+    """No gravity, no contact, no pins: a rigid translation with velocity v
+    costs no elastic energy, so x^{t+1} = x^t + h v exactly."""
+    s = synth.tiny_scene(2, 2, 2, seed=1, pinned=False)
+    s.gravity = (0.0, 0.0, 0.0)
+    v = np.array([0.3, -1.2, 0.7])
+    s.v0 = np.broadcast_to(v, s.X.shape).copy()
+    p = ip.Problem(s)
+    x, info = newton.timestep(p)
+    assert np.allclose(x, s.x0 + s.dt * v[None, :], atol=1e-14)
+
+
+def test_rest_without_forces_stays():
+    s = synth.tiny_scene(2, 1, 1, seed=2, pinned=True)
+    s.gravity = (0.0, 0.0, 0.0)
+    s.v0 = np.zeros_like(s.X)
+    x, info = newton.timestep(ip.Problem(s))
+    assert np.abs(x - s.x0).max() <= 1e-15
+
+
+@pytest.mark.parametrize("contact", [False, True])
+def test_timestep_is_a_minimiser(contact):
+    """KKT by finite differences of E (independent of the analytic gradient),
+    and every feasible perturbation raises E."""
+    s = synth.tiny_scene(2, 2, 1, seed=11, contact=contact, pinned=not contact)
+    p = ip.Problem(s)
+    x, info = newton.timestep(p)
+    assert info["converged"]
+    E0 = p.energy(x)
+    scale = np.abs(x - p.x_t).max()
+    for trial in range(10):
+        dv = rng.normal(size=x.shape)
+        dv[p.pinned] = 0
+        dv *= 1e-3 * scale / np.abs(dv).max()
+        assert p.energy(x + dv) > E0
+        assert p.energy(x - dv) > E0
+    g = p.gradient(x)
+    assert np.linalg.norm(g) <= 1e-9 * np.linalg.norm(p.mass[:, None] * (x - p.x_tilde)) + 1e-14
+
+
+def test_minimiser_unique_from_two_starts():
+    s = synth.tiny_scene(3, 2, 1, seed=4, contact=True, pinned=False)
+    p = ip.Problem(s)
+    xa, _ = newton.timestep(p)
+    xb, _ = newton.timestep(p, x_init=p.x_t)
+    assert np.abs(xa - xb).max() <= 1e-12 * np.abs(xa - p.x_t).max()
+
+
+def test_cube_newton_reaches_grad_norm():
+    s = synth.cube_scene()
+    p = ip.Problem(s)
+    x, info = newton.timestep(p)
+    assert info["converged"] and info["gnorm_final"] <= 1e-8
+    # the dense direct solve and the sparse LU give the same minimiser
+    x2, _ = newton.timestep(p, method="splu")
+    assert np.abs(x - x2).max() <= 1e-12 * np.abs(x - p.x_t).max()
+
+
+def test_contact_keeps_vertices_above_plane():
+    s = synth.tiny_scene(3, 2, 2, seed=8, contact=True, pinned=False)
+    s.v0[:] = np.array([0.0, 0.0, -2.0])
+    p = ip.Problem(s)
+    x, info = newton.timestep(p)
+    assert p.distances(x).min() > 0
+    # with the barrier switched off the same step would cross the plane
+    assert (p.x_tilde[:, 2]).min() < 0
+
+
+# -- PCG -------------------------------------------------------------------------
+def test_pcg_solves_random_spd():
+    n = 40
+    A = rng.normal(size=(n, n))
+    A = A @ A.T + n * np.eye(n)
+    b = rng.normal(size=n)
+    x, info = pcg.pcg(lambda v: A @ v, b, lambda r: r / np.diag(A), rtol=1e-12)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9)
+
+
+def test_pcg_exact_preconditioner_one_iteration():
+    n = 30
+    A = rng.normal(size=(n, n))
+    A = A @ A.T + np.eye(n)
+    b = rng.normal(size=n)
+    Ainv = np.linalg.inv(A)
+    x, info = pcg.pcg(lambda v: A @ v, b, lambda r: Ainv @ r, rtol=1e-10)
+    assert info["iters"] == 1

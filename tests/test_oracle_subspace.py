@@ -1,0 +1,117 @@
+"""Pins for the oracle's subspace algebra (no GPU): LBS basis layout (Eq. LBS),
+linear precision under a partition of unity (Sec. 3.5), Galerkin operator
+by brute force, Galerkin orthogonality, and the two-level preconditioner's
+symmetry, definiteness and exactness in the full-rank case."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ip, pcg, subspace
+
+rng = np.random.default_rng(7)
+
+
+def _scene_and_basis(m=5, k=3):
+    s = synth.tiny_scene(3, 2, 2, seed=21, pinned=False)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=m, k=k, seed=4)
+    U = subspace.lbs_basis_matrix(s.X, origins, vrow, handle, phi)
+    return s, origins, vrow, handle, phi, U
+
+
+def test_lbs_block_layout_single_vertex():
+    X = np.array([[1.0, 2.0, 3.0]])
+    origins = np.array([[0.5, 0.0, -1.0]])
+    U = subspace.lbs_basis_matrix(X, origins, np.array([0, 1]), np.array([0]), np.array([0.25]))
+    a = np.array([1.0, 0.5, 2.0, 4.0])
+    expect = 0.25 * np.kron(np.eye(3), a[None, :])   # I_3 (x) [1, x, y, z]
+    assert np.allclose(U.toarray(), expect)
+
+
+def test_linear_precision_with_partition_of_unity():
+    """With sum_j phi_j = 1, every affine map x -> A x + t is reproduced by
+    q_j = (A o_j + t | A), the same map written about each handle origin."""
+    s, origins, vrow, handle, phi, U = _scene_and_basis()
+    A = rng.normal(size=(3, 3))
+    t = rng.normal(size=3)
+    m = origins.shape[0]
+    q = np.zeros((m, 12))
+    for j in range(m):
+        M34 = np.concatenate([(A @ origins[j] + t)[:, None], A], axis=1)
+        q[j] = M34.ravel()
+    w = subspace.prolong(U, q)
+    assert np.allclose(w, s.X @ A.T + t[None, :], atol=1e-12)
+
+
+def test_restriction_is_transpose_of_prolongation():
+    s, origins, vrow, handle, phi, U = _scene_and_basis()
+    q = rng.normal(size=(origins.shape[0], 12))
+    r = rng.normal(size=s.X.shape)
+    lhs = np.sum(subspace.prolong(U, q) * r)
+    rhs = np.sum(q * subspace.restrict(U, r))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_galerkin_brute_force():
+    s, origins, vrow, handle, phi, U = _scene_and_basis(m=3, k=2)
+    H = ip.Problem(s).hessian(s.X)
+    Ac = subspace.galerkin(H, U)
+    r = U.shape[1]
+    cols = [subspace.prolong(U, np.eye(r)[a]).ravel() for a in range(r)]
+    brute = np.array([[cols[a] @ (H @ cols[b]) for b in range(r)] for a in range(r)])
+    assert np.allclose(Ac, brute, rtol=1e-12, atol=1e-12 * np.abs(brute).max())
+    assert np.allclose(Ac, Ac.T, rtol=1e-12, atol=1e-12 * np.abs(Ac).max())
+    assert np.linalg.eigvalsh(Ac).min() > 0
+
+
+def test_galerkin_orthogonality():
+    s, origins, vrow, handle, phi, U = _scene_and_basis()
+    H = ip.Problem(s).hessian(s.X)
+    Ac = subspace.galerkin(H, U)
+    r = rng.normal(size=3 * s.n_verts)
+    z = subspace.two_level_apply(H, U, Ac, r, mode="coarse")
+    assert np.abs(U.T @ (r - H @ z)).max() <= 1e-9 * np.abs(U.T @ r).max()
+
+
+@pytest.mark.parametrize("mode", ["additive", "multiplicative"])
+def test_two_level_preconditioner_spd(mode):
+    s, origins, vrow, handle, phi, U = _scene_and_basis()
+    H = ip.Problem(s).hessian(s.X)
+    Ac = subspace.galerkin(H, U)
+    n3 = H.shape[0]
+    M = np.stack([subspace.two_level_apply(H, U, Ac, e, mode=mode, omega=0.5)
+                  for e in np.eye(n3)], axis=1)
+    assert np.allclose(M, M.T, atol=1e-10 * np.abs(M).max())
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_full_rank_coarse_space_solves_in_one_iteration():
+    """When U spans the whole space the coarse correction is H^{-1}."""
+    s = synth.tiny_scene(1, 1, 1, seed=3, pinned=False)
+    H = ip.Problem(s).hessian(s.X)
+    n3 = H.shape[0]
+    import scipy.sparse as sp
+    U = sp.csr_matrix(rng.normal(size=(n3, n3)))
+    Ac = subspace.galerkin(H, U)
+    b = rng.normal(size=n3)
+    x, info = pcg.pcg(lambda v: H @ v, b,
+                      lambda r: subspace.two_level_apply(H, U, Ac, r, mode="coarse"), rtol=1e-9)
+    assert info["iters"] == 1
+
+
+def test_multilevel_pcg_beats_jacobi_on_stiff_beam_slice():
+    s = synth.tiny_scene(6, 2, 2, seed=12, pinned=True, E_range=(1e5, 1e9))
+    p = ip.Problem(s)
+    H = p.hessian(p.x_tilde)
+    b = -p.gradient(p.x_tilde).ravel()
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=6, k=2, seed=1)
+    phi = phi.copy()
+    phi[np.repeat(p.pinned, 2)] = 0.0
+    U = subspace.lbs_basis_matrix(s.X, origins, vrow, handle, phi)
+    Ac = subspace.galerkin(H, U)
+    Ac += 1e-12 * np.trace(Ac) / Ac.shape[0] * np.eye(Ac.shape[0])
+    Dinv = subspace.block_diagonal_inverse(H)
+    _, jac = pcg.pcg(lambda v: H @ v, b, lambda r: Dinv @ r, rtol=1e-8)
+    _, ml = pcg.pcg(lambda v: H @ v, b,
+                    lambda r: subspace.two_level_apply(H, U, Ac, r, omega=0.5, Dinv=Dinv), rtol=1e-8)
+    assert ml["converged"] and jac["converged"]
+    assert ml["iters"] < jac["iters"]
