@@ -1,0 +1,241 @@
+/*
+ * mls.h -- C ABI of the GB300 (sm_103a) multilevel elastodynamics timestep
+ * library: the per-Newton-iteration linear solve of arXiv 2508.13386,
+ * "Sparse, Geometry- and Material-Aware Bases for Multilevel Elastodynamic
+ * Simulation", and the Newton loop around it.
+ *
+ * What one timestep computes (Sec. 3.1, Eq. IP with implicit Euler):
+ *   x^{t+1} = argmin_x E(x),
+ *   E(x) = 1/2 sum_{v free} m_v |x_v - x_tilde_v|^2
+ *          + h^2 ( sum_e vol_e psi(F_e(x)) + kappa sum_v b(n . x_v - o) ),
+ *   x_tilde = x^t + h v^t + h^2 g,      v^{t+1} = (x^{t+1} - x^t) / h,
+ * with the non-inverting Neo-Hookean psi of Sec. 4 (psi = mu/2 (tr F^T F - 3)
+ * - mu ln J + lam/2 ln^2 J), the point-plane IPC log barrier
+ * b(d) = -(d - dhat)^2 ln(d / dhat) on (0, dhat), lumped masses, and
+ * Dirichlet vertices held at x^t.  Each Newton iteration solves H d = -g
+ * (Eq. 5) with H the element-wise PSD-projected Hessian, by conjugate
+ * gradient preconditioned either with 3x3 block Jacobi or with the two-level
+ * cycle built from the paper's sparse LBS basis (Eq. LBS, Sec. 3.5): smoothing
+ * by block Jacobi plus the Galerkin coarse correction U (U^T H U)^{-1} U^T
+ * (Alg. 2 / Sec. 3.7.1, here with the coarse operator formed explicitly and
+ * factored by dense Cholesky).  A filtered backtracking line search (Sec. 3.9)
+ * follows: the point-plane CCD bound, J > 0 on every tet, Armijo on E.
+ *
+ * Conventions for every entry point:
+ *  - Units are SI; positions, velocities and energies are float64.
+ *  - Arrays are C-contiguous.  "[n][3]" means n rows of (x, y, z).
+ *  - Pointers documented as DEVICE must be device memory of the current
+ *    CUDA device (for example torch.Tensor.data_ptr() of a CUDA tensor); those
+ *    documented as HOST are ordinary host memory.  The caller owns every
+ *    pointer it passes; uploads copy into library-owned device buffers, and
+ *    the library keeps no caller pointer after a call returns.
+ *  - Every call runs on the context's stream (mls_options.stream, 0 = the
+ *    legacy default stream) and returns only after its work on that stream
+ *    has completed, so results are ready when the call returns.
+ *  - Errors are returned as a negative mls_status with a message available
+ *    from mls_last_error(); no call aborts, traps or throws across the ABI.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef MLS_H_
+#define MLS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mls_status {
+  MLS_OK = 0,
+  MLS_EINVAL = -1,      /* bad argument, size or call order */
+  MLS_ENOMEM = -2,      /* device or host allocation failed */
+  MLS_ECUDA = -3,       /* a CUDA runtime call failed */
+  MLS_ENOTCONV = -4,    /* Newton or PCG hit its iteration cap */
+  MLS_ELINESEARCH = -5, /* no acceptable step after the halving cap */
+  MLS_ECHOL = -6,       /* coarse operator not positive definite */
+  MLS_ENONFINITE = -7,  /* NaN or Inf in an input or an iterate */
+  MLS_ETIMEOUT = -8,    /* a bounded device-side wait gave up */
+  MLS_EINVERTED = -9    /* an input state has a tet with J <= 0 or a vertex on/below the plane */
+} mls_status;
+
+/* Arithmetic of the linear solve.  Gradients, energies, norms, dot products,
+ * the line search and the coarse Cholesky factorisation are float64 in every
+ * mode. */
+enum {
+  MLS_FP64 = 0,        /* element Hessians, H, PCG vectors: float64 */
+  MLS_MIXED_FP32 = 1,  /* element Hessians, H, PCG vectors, smoothing and
+                          basis projection: float32 with float32 accumulation */
+  MLS_MIXED_BF16 = 2   /* as MIXED_FP32, but H's values stored as bfloat16 */
+};
+
+enum {
+  MLS_PRECOND_BLOCK_JACOBI = 0, /* 3x3 block-diagonal inverse */
+  MLS_PRECOND_TWO_LEVEL = 1     /* block-Jacobi smoothing + Galerkin coarse correction */
+};
+
+enum {
+  MLS_CYCLE_ADDITIVE = 0,       /* z = omega D^-1 r + U A_c^-1 U^T r */
+  MLS_CYCLE_MULTIPLICATIVE = 1  /* smooth, coarse-correct the residual, smooth (symmetric) */
+};
+
+typedef struct mls_options {
+  int precision;       /* MLS_FP64 | MLS_MIXED_FP32 | MLS_MIXED_BF16 */
+  int preconditioner;  /* MLS_PRECOND_BLOCK_JACOBI | MLS_PRECOND_TWO_LEVEL */
+  int cycle;           /* MLS_CYCLE_* (two-level only) */
+  double omega;        /* block-Jacobi damping in the two-level cycle */
+  double newton_tol;   /* stop when |d|_inf <= newton_tol * max(|x - x^t|_inf, h^2 |g|) */
+  double pcg_rtol;     /* PCG stops at |r|_2 <= eta |b|_2, eta = min(pcg_rtol, forcing term) */
+  int max_newton;      /* Newton iteration cap per timestep */
+  int max_pcg;         /* PCG iteration cap per Newton iteration */
+  int coarse_refresh;  /* 0: rebuild U^T H U and its factor every Newton iteration;
+                          k > 0: at the first iteration of a step and then every k */
+  int pcg_check_every; /* PCG iterations launched between host convergence checks */
+  void* stream;        /* cudaStream_t the context runs on (0 = legacy default) */
+} mls_options;
+
+typedef struct mls_stats {
+  int newton_iters;        /* Newton iterations taken */
+  int pcg_iters;           /* PCG iterations summed over the Newton iterations */
+  int line_search_trials;  /* energy evaluations in the line search */
+  int coarse_builds;       /* Galerkin builds + factorisations */
+  double step_rel;         /* final |d|_inf / max(|x - x^t|_inf, h^2 |g|) */
+  double grad_norm;        /* |g|_2 at the last evaluated iterate */
+  double energy;           /* E at the returned iterate */
+} mls_stats;
+
+typedef struct mls_ctx mls_ctx;
+
+/* Fill *opt with defaults: FP64, block Jacobi, newton_tol 1e-10, pcg_rtol
+ * 1e-4 (the paper's subspace PCG tolerance, Sec. 3.7.1), 50 Newton and 20000
+ * PCG iterations, additive cycle, omega 1, coarse_refresh 0, check every 16,
+ * default stream.  Returns MLS_EINVAL if opt is NULL. */
+mls_status mls_default_options(mls_options* opt);
+
+/* Create a context on the current CUDA device.  opt may be NULL (defaults).
+ * *out receives the context; free it with mls_destroy. */
+mls_status mls_create(mls_ctx** out, const mls_options* opt);
+
+/* Free a context and all its device memory.  NULL is a no-op. */
+mls_status mls_destroy(mls_ctx* ctx);
+
+/* Message for the last failed call on ctx ("" if none).  Owned by ctx. */
+const char* mls_last_error(const mls_ctx* ctx);
+
+/* Change options after creation (same meaning as in mls_create). */
+mls_status mls_set_options(mls_ctx* ctx, const mls_options* opt);
+
+/* Upload the tet mesh and its materials (Sec. 3.1 discretisation; Sec. 4
+ * material model).  All HOST pointers:
+ *   rest_xyz  [n_verts][3]  rest positions X
+ *   tets      [n_tets][4]   vertex indices, each tet positively oriented at rest
+ *   youngs, poisson, density   [n_tets]  E (Pa), nu, rho (kg/m^3)
+ *   dirichlet [n_verts]     1 = vertex held at its current position, 0 = free;
+ *                           NULL = none
+ * Builds rest shapes, lumped masses and the BSR sparsity of H.  Replaces a
+ * previous mesh and drops an uploaded basis.  MLS_EINVAL for n_verts < 1,
+ * n_tets < 1, an index out of range, a non-positive rest volume, E <= 0,
+ * nu outside (-1, 0.5) or rho <= 0. */
+mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n_verts, const double* rest_xyz,
+                           int32_t n_tets, const int32_t* tets, const double* youngs,
+                           const double* poisson, const double* density,
+                           const uint8_t* dirichlet);
+
+/* Upload a sparse LBS basis (Eq. LBS): handle origins and, per vertex, the
+ * handles whose weight phi_j(v) is nonzero (Sec. 3.5), as HOST arrays:
+ *   origins [n_handles][3]    handle origins o_j
+ *   vrow    [n_verts + 1]     CSR row pointer over vertices
+ *   handle  [vrow[n]]         handle index of each entry, 0 <= j < n_handles
+ *   phi     [vrow[n]]         weight phi_j(v)
+ * Column 12 j + 4 c + l of U at row 3 v + c is phi_j(v) a_l with
+ * a = [1, X_v - o_j].  Needed by MLS_PRECOND_TWO_LEVEL.  MLS_EINVAL for
+ * sizes or indices out of range or a call before mls_upload_mesh. */
+mls_status mls_upload_basis(mls_ctx* ctx, int32_t n_handles, const double* origins,
+                            const int32_t* vrow, const int32_t* handle, const double* phi);
+
+/* External loads (HOST arrays of 3): gravity g (m/s^2); when contact != 0 the
+ * ground plane {x : n . x = o} with unit normal plane_n, barrier distance
+ * dhat > 0 and stiffness kappa > 0.  Defaults: g = (0, 0, -9.81), no contact. */
+mls_status mls_set_forces(mls_ctx* ctx, const double* gravity, int contact,
+                          const double* plane_n, double plane_o, double dhat, double kappa);
+
+/* One implicit-Euler timestep.  DEVICE pointers:
+ *   x [n][3] positions x^t, v [n][3] velocities v^t (read only),
+ *   dx_out [n][3] receives x^{t+1} - x^t.
+ * stats_out (HOST, may be NULL) receives iteration counts.  The start iterate
+ * is x_tilde with Dirichlet vertices at x^t, or x^t when x_tilde is
+ * infeasible.  MLS_EINVERTED if x^t itself is infeasible, MLS_ENOTCONV if the
+ * Newton cap is hit (dx_out then holds the last iterate's displacement). */
+mls_status mls_newton_step(mls_ctx* ctx, const double* x, const double* v, double dt,
+                           double* dx_out, mls_stats* stats_out);
+
+/* Same as mls_newton_step with HOST x, v and dx_out: copies x and v to the
+ * device and dx back inside the call. */
+mls_status mls_newton_step_host(mls_ctx* ctx, const double* x, const double* v, double dt,
+                                double* dx_out, mls_stats* stats_out);
+
+/* ---- Stage entry points: one step of the path on the context's state ----
+ * These run single rows of the hot path so each can be checked on its own.
+ * All array arguments are DEVICE pointers unless stated otherwise. */
+
+/* Per-tet element evaluation (Sec. 4 Neo-Hookean, element-wise PSD
+ * projection of dP/dF): for positions x [n][3] write, per tet e,
+ *   energy [t]        vol_e psi(F_e)   (+inf where J <= 0)   (nullable)
+ *   grad   [t][12]    d(vol psi)/dx_e, element DOF 3 a + c   (nullable)
+ *   hess   [t][12][12] vol B^T [dP/dF]_+ B in the context's precision,
+ *                      widened to float64                      (nullable) */
+mls_status mls_eval_elements(mls_ctx* ctx, const double* x, double* energy, double* grad,
+                             double* hess);
+
+/* Assemble the gradient g [n][3] (float64, written to grad_out, nullable) and
+ * the projected Hessian H (kept in the context) at x for the timestep whose
+ * predictor uses x_t and v_t (all [n][3]) and step dt. */
+mls_status mls_assemble(mls_ctx* ctx, const double* x, const double* x_t, const double* v_t,
+                        double dt, double* grad_out);
+
+/* Copy the assembled H out as HOST block-CSR: row_ptr [n+1], col [nnzb],
+ * val [nnzb][3][3] (float64).  *nnzb receives the block count; pass NULL
+ * arrays to query it first. */
+mls_status mls_get_hessian(mls_ctx* ctx, int32_t* row_ptr, int32_t* col, double* val,
+                           int64_t* nnzb);
+
+/* y = H x with the assembled H in its storage precision (float64 in and out). */
+mls_status mls_spmv(mls_ctx* ctx, const double* x, double* y);
+
+/* z = M^{-1} r with the current preconditioner (float64 in and out). */
+mls_status mls_precond_apply(mls_ctx* ctx, const double* r, double* z);
+
+/* Solve H d = b by PCG from d = 0 to |r| <= rtol |b|: b, d [n][3] float64;
+ * *iters and *rel_res (HOST, nullable) receive the iteration count and final
+ * |r|/|b| of the recursively updated residual. */
+mls_status mls_pcg_solve(mls_ctx* ctx, const double* b, double* d, double rtol, int max_iter,
+                         int* iters, double* rel_res);
+
+/* w = U q (prolongation, Eq. LBS): q [m][12] -> w [n][3]. */
+mls_status mls_prolong(mls_ctx* ctx, const double* q, double* w);
+
+/* z = U^T r (restriction): r [n][3] -> z [m][12]. */
+mls_status mls_restrict(mls_ctx* ctx, const double* r, double* z);
+
+/* Build the Galerkin operator A_c = U^T H U from the assembled H and factor
+ * it (dense Cholesky, float64).  MLS_ECHOL if a pivot is not positive. */
+mls_status mls_build_coarse(mls_ctx* ctx);
+
+/* Copy A_c (HOST, [12m][12m] float64, before factorisation) out. */
+mls_status mls_get_coarse(mls_ctx* ctx, double* A);
+
+/* Energy E(x + alpha d) for the current timestep (after mls_assemble) and
+ * whether the point is feasible (every J > 0 and every vertex above the
+ * plane).  x, d DEVICE [n][3]; *E and *feasible HOST. */
+mls_status mls_energy(mls_ctx* ctx, const double* x, const double* d, double alpha, double* E,
+                      int* feasible);
+
+/* Point-plane CCD step bound min(1, 0.9 min_v dist_v / (-n . d_v)) over
+ * vertices approaching the plane; 1 without contact.  *alpha HOST. */
+mls_status mls_ccd_bound(mls_ctx* ctx, const double* x, const double* d, double* alpha);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLS_H_ */

@@ -1,0 +1,254 @@
+"""GB300 (sm_103a) multilevel elastodynamics timestep library.
+
+Python face of the C ABI in ``include/mls.h`` (libmls.so): argument
+marshalling only.  Device arrays are torch CUDA tensors (float64, [n, 3]);
+host arrays are numpy arrays.  Every step of the timestep runs in the
+library's CUDA kernels; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+
+__all__ = ["Solver", "MLSError", "lib"]
+
+lib = None
+
+
+def _get_lib():
+    global lib
+    if lib is None:
+        lib = _lib.load()
+    return lib
+
+
+class MLSError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_lib.STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def _dev(t, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One library context (``mls_ctx``) bound to a CUDA stream."""
+
+    def __init__(self, precision="fp64", preconditioner="jacobi", cycle="additive", omega=1.0,
+                 newton_tol=1e-10, pcg_rtol=1e-4, max_newton=50, max_pcg=20000,
+                 coarse_refresh=0, pcg_check_every=16, stream=None):
+        self._l = _get_lib()
+        self._ctx = C.c_void_p()
+        self.opt = _lib.Options()
+        self._l.mls_default_options(C.byref(self.opt))
+        self._fill(precision, preconditioner, cycle, omega, newton_tol, pcg_rtol, max_newton, max_pcg,
+                   coarse_refresh, pcg_check_every, stream)
+        st = self._l.mls_create(C.byref(self._ctx), C.byref(self.opt))
+        if st != _lib.MLS_OK:
+            raise MLSError(st, "mls_create failed")
+        self.n = 0
+        self.t = 0
+        self.m = 0
+
+    def _fill(self, precision, preconditioner, cycle, omega, newton_tol, pcg_rtol, max_newton, max_pcg,
+              coarse_refresh, pcg_check_every, stream):
+        o = self.opt
+        o.precision = _lib.PRECISION[precision]
+        o.preconditioner = _lib.PRECOND[preconditioner]
+        o.cycle = _lib.CYCLE[cycle]
+        o.omega = float(omega)
+        o.newton_tol = float(newton_tol)
+        o.pcg_rtol = float(pcg_rtol)
+        o.max_newton = int(max_newton)
+        o.max_pcg = int(max_pcg)
+        o.coarse_refresh = int(coarse_refresh)
+        o.pcg_check_every = int(pcg_check_every)
+        if stream is None:
+            o.stream = None
+        else:
+            o.stream = C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+
+    def set_options(self, **kw):
+        cur = dict(precision={v: k for k, v in _lib.PRECISION.items()}[self.opt.precision],
+                   preconditioner=["jacobi", "two_level"][self.opt.preconditioner],
+                   cycle=["additive", "multiplicative"][self.opt.cycle], omega=self.opt.omega,
+                   newton_tol=self.opt.newton_tol, pcg_rtol=self.opt.pcg_rtol,
+                   max_newton=self.opt.max_newton, max_pcg=self.opt.max_pcg,
+                   coarse_refresh=self.opt.coarse_refresh, pcg_check_every=self.opt.pcg_check_every,
+                   stream=self.opt.stream)
+        cur.update(kw)
+        self._fill(**cur)
+        self._check(self._l.mls_set_options(self._ctx, C.byref(self.opt)))
+
+    def close(self):
+        if self._ctx:
+            self._l.mls_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=()):
+        if st != _lib.MLS_OK and st not in allow:
+            msg = self._l.mls_last_error(self._ctx)
+            raise MLSError(st, msg.decode() if msg else "")
+        return st
+
+    # ---- uploads ---------------------------------------------------------------
+    def upload_mesh(self, X, tets, E, nu, rho, dirichlet=None):
+        X, pX = _host(X, np.float64)
+        tets, pT = _host(tets, np.int32)
+        E, pE = _host(E, np.float64)
+        nu, pN = _host(nu, np.float64)
+        rho, pR = _host(rho, np.float64)
+        if dirichlet is None:
+            pD = None
+        else:
+            dirichlet, pD = _host(dirichlet, np.uint8)
+        self._check(self._l.mls_upload_mesh(self._ctx, X.shape[0], pX, tets.shape[0], pT, pE, pN, pR, pD))
+        self.n, self.t = X.shape[0], tets.shape[0]
+
+    def upload_basis(self, origins, vrow, handle, phi):
+        origins, pO = _host(origins, np.float64)
+        vrow, pV = _host(vrow, np.int32)
+        handle, pH = _host(handle, np.int32)
+        phi, pP = _host(phi, np.float64)
+        self._check(self._l.mls_upload_basis(self._ctx, origins.shape[0], pO, pV, pH, pP))
+        self.m = origins.shape[0]
+
+    def set_forces(self, gravity=(0.0, 0.0, -9.81), contact=False, plane_n=(0.0, 0.0, 1.0), plane_o=0.0,
+                   dhat=1e-3, kappa=1e5):
+        g, pg = _host(gravity, np.float64)
+        pn, ppn = _host(plane_n, np.float64)
+        self._check(self._l.mls_set_forces(self._ctx, pg, 1 if contact else 0, ppn, float(plane_o),
+                                           float(dhat), float(kappa)))
+
+    def setup_scene(self, scene):
+        """Upload a ``synth.Scene``-like object's mesh, materials and loads."""
+        self.upload_mesh(scene.X, scene.tets, scene.E, scene.nu, scene.rho, scene.dirichlet)
+        self.set_forces(scene.gravity, scene.contact, scene.plane_n, scene.plane_o, scene.dhat, scene.kappa)
+
+    # ---- timestep ----------------------------------------------------------------
+    def newton_step(self, x, v, dt, dx=None, allow_notconv=False):
+        import torch
+        if dx is None:
+            dx = torch.empty_like(x)
+        st = _lib.Stats()
+        allow = (-4,) if allow_notconv else ()
+        status = self._check(self._l.mls_newton_step(self._ctx, _dev(x, (self.n, 3)), _dev(v, (self.n, 3)),
+                                                     float(dt), _dev(dx, (self.n, 3)), C.byref(st)), allow)
+        out = st.as_dict()
+        out["status"] = status
+        return dx, out
+
+    def newton_step_host(self, x, v, dt, dx=None):
+        x, px = _host(x, np.float64)
+        v, pv = _host(v, np.float64)
+        if dx is None:
+            dx = np.empty_like(x)
+        st = _lib.Stats()
+        self._check(self._l.mls_newton_step_host(self._ctx, px, pv, float(dt),
+                                                 dx.ctypes.data_as(C.c_void_p), C.byref(st)))
+        return dx, st.as_dict()
+
+    # ---- stage entry points --------------------------------------------------------
+    def eval_elements(self, x):
+        import torch
+        dev = x.device
+        energy = torch.empty(self.t, dtype=torch.float64, device=dev)
+        grad = torch.empty(self.t, 12, dtype=torch.float64, device=dev)
+        hess = torch.empty(self.t, 12, 12, dtype=torch.float64, device=dev)
+        self._check(self._l.mls_eval_elements(self._ctx, _dev(x, (self.n, 3)), _dev(energy), _dev(grad),
+                                              _dev(hess)))
+        return energy, grad, hess
+
+    def assemble(self, x, x_t, v_t, dt):
+        import torch
+        g = torch.empty_like(x)
+        self._check(self._l.mls_assemble(self._ctx, _dev(x, (self.n, 3)), _dev(x_t, (self.n, 3)),
+                                         _dev(v_t, (self.n, 3)), float(dt), _dev(g)))
+        return g
+
+    def get_hessian(self):
+        nnzb = C.c_int64()
+        self._check(self._l.mls_get_hessian(self._ctx, None, None, None, C.byref(nnzb)))
+        rp = np.zeros(self.n + 1, dtype=np.int32)
+        col = np.zeros(nnzb.value, dtype=np.int32)
+        val = np.zeros((nnzb.value, 3, 3), dtype=np.float64)
+        self._check(self._l.mls_get_hessian(self._ctx, rp.ctypes.data_as(C.c_void_p),
+                                            col.ctypes.data_as(C.c_void_p), val.ctypes.data_as(C.c_void_p),
+                                            C.byref(nnzb)))
+        return rp, col, val
+
+    def spmv(self, x):
+        import torch
+        y = torch.empty_like(x)
+        self._check(self._l.mls_spmv(self._ctx, _dev(x, (self.n, 3)), _dev(y)))
+        return y
+
+    def precond_apply(self, r):
+        import torch
+        z = torch.empty_like(r)
+        self._check(self._l.mls_precond_apply(self._ctx, _dev(r, (self.n, 3)), _dev(z)))
+        return z
+
+    def pcg_solve(self, b, rtol, max_iter=20000):
+        import torch
+        d = torch.empty_like(b)
+        it = C.c_int()
+        rel = C.c_double()
+        st = self._check(self._l.mls_pcg_solve(self._ctx, _dev(b, (self.n, 3)), _dev(d), float(rtol),
+                                               int(max_iter), C.byref(it), C.byref(rel)), allow=(-4,))
+        return d, it.value, rel.value, st
+
+    def prolong(self, q):
+        import torch
+        w = torch.empty(self.n, 3, dtype=torch.float64, device=q.device)
+        self._check(self._l.mls_prolong(self._ctx, _dev(q, (self.m, 12)), _dev(w)))
+        return w
+
+    def restrict(self, r):
+        import torch
+        z = torch.empty(self.m, 12, dtype=torch.float64, device=r.device)
+        self._check(self._l.mls_restrict(self._ctx, _dev(r, (self.n, 3)), _dev(z)))
+        return z
+
+    def build_coarse(self):
+        self._check(self._l.mls_build_coarse(self._ctx))
+
+    def get_coarse(self):
+        r = 12 * self.m
+        A = np.zeros((r, r), dtype=np.float64)
+        self._check(self._l.mls_get_coarse(self._ctx, A.ctypes.data_as(C.c_void_p)))
+        return A
+
+    def energy(self, x, d, alpha):
+        E = C.c_double()
+        feas = C.c_int()
+        self._check(self._l.mls_energy(self._ctx, _dev(x, (self.n, 3)), _dev(d, (self.n, 3)), float(alpha),
+                                       C.byref(E), C.byref(feas)))
+        return E.value, bool(feas.value)
+
+    def ccd_bound(self, x, d):
+        a = C.c_double()
+        self._check(self._l.mls_ccd_bound(self._ctx, _dev(x, (self.n, 3)), _dev(d, (self.n, 3)), C.byref(a)))
+        return a.value

@@ -1,0 +1,98 @@
+"""ctypes declarations of the C ABI in ``include/mls.h``.
+
+Loads ``libmls.so`` from this package directory.  There is no fallback: if
+the library is missing, importing this module raises ImportError telling the
+user to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmls.so")
+
+MLS_OK = 0
+STATUS = {
+    0: "MLS_OK", -1: "MLS_EINVAL", -2: "MLS_ENOMEM", -3: "MLS_ECUDA", -4: "MLS_ENOTCONV",
+    -5: "MLS_ELINESEARCH", -6: "MLS_ECHOL", -7: "MLS_ENONFINITE", -8: "MLS_ETIMEOUT",
+    -9: "MLS_EINVERTED",
+}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed_fp32": 1, "bf16": 2, "mixed_bf16": 2}
+PRECOND = {"jacobi": 0, "block_jacobi": 0, "two_level": 1, "multilevel": 1}
+CYCLE = {"additive": 0, "multiplicative": 1}
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("preconditioner", C.c_int),
+        ("cycle", C.c_int),
+        ("omega", C.c_double),
+        ("newton_tol", C.c_double),
+        ("pcg_rtol", C.c_double),
+        ("max_newton", C.c_int),
+        ("max_pcg", C.c_int),
+        ("coarse_refresh", C.c_int),
+        ("pcg_check_every", C.c_int),
+        ("stream", C.c_void_p),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("newton_iters", C.c_int),
+        ("pcg_iters", C.c_int),
+        ("line_search_trials", C.c_int),
+        ("coarse_builds", C.c_int),
+        ("step_rel", C.c_double),
+        ("grad_norm", C.c_double),
+        ("energy", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# (name, argtypes) for every entry point declared in include/mls.h
+_P = C.c_void_p
+_D = C.c_double
+_I = C.c_int
+_I32 = C.c_int32
+SIGNATURES = {
+    "mls_default_options": [C.POINTER(Options)],
+    "mls_create": [C.POINTER(_P), C.POINTER(Options)],
+    "mls_destroy": [_P],
+    "mls_last_error": [_P],
+    "mls_set_options": [_P, C.POINTER(Options)],
+    "mls_upload_mesh": [_P, _I32, _P, _I32, _P, _P, _P, _P, _P],
+    "mls_upload_basis": [_P, _I32, _P, _P, _P, _P],
+    "mls_set_forces": [_P, _P, _I, _P, _D, _D, _D],
+    "mls_newton_step": [_P, _P, _P, _D, _P, C.POINTER(Stats)],
+    "mls_newton_step_host": [_P, _P, _P, _D, _P, C.POINTER(Stats)],
+    "mls_eval_elements": [_P, _P, _P, _P, _P],
+    "mls_assemble": [_P, _P, _P, _P, _D, _P],
+    "mls_get_hessian": [_P, _P, _P, _P, C.POINTER(C.c_int64)],
+    "mls_spmv": [_P, _P, _P],
+    "mls_precond_apply": [_P, _P, _P],
+    "mls_pcg_solve": [_P, _P, _P, _D, _I, C.POINTER(_I), C.POINTER(_D)],
+    "mls_prolong": [_P, _P, _P],
+    "mls_restrict": [_P, _P, _P],
+    "mls_build_coarse": [_P],
+    "mls_get_coarse": [_P, _P],
+    "mls_energy": [_P, _P, _P, _D, C.POINTER(_D), C.POINTER(_I)],
+    "mls_ccd_bound": [_P, _P, _P, C.POINTER(_D)],
+}
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -m paper_2508_13386_gb300.build, or __graft_entry__.build())")
+    lib = C.CDLL(path)
+    for name, args in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_char_p if name == "mls_last_error" else C.c_int
+    return lib

@@ -1,0 +1,365 @@
+// Gradient and Hessian assembly of the incremental potential (Eq. IP with
+// implicit Euler, Sec. 3.1), and the state-vector helpers of the timestep.
+//
+//   g = M (x - x_tilde) + h^2 (sum_e grad_e + kappa b'(d_v) n),  g_v = 0 on
+//       Dirichlet vertices;
+//   H = M + h^2 (sum_e H_e + kappa b''(d_v) n n^T), Dirichlet rows and
+//       columns replaced by the identity.
+//
+// Both are deterministic gathers (no floating-point atomics): every vertex
+// sums its incident element gradients through a precomputed incidence list
+// and every block slot of H sums the element blocks mapped onto it.
+#include "mls_internal.cuh"
+
+namespace mls {
+
+struct AsmIn {
+  int n, t;
+  const double* __restrict__ mass;
+  const uint8_t* __restrict__ pinned;
+  const Vec4d* __restrict__ xtil;
+  const int* __restrict__ vt_ptr;
+  const int* __restrict__ vt_code;
+  const double* __restrict__ egrad;
+  double h2, kappa, dhat, po, pn0, pn1, pn2;
+  int contact;
+};
+
+__device__ __forceinline__ double bar_db(double d, double dhat) {
+  if (d >= dhat || d <= 0.0) return 0.0;
+  const double r = d - dhat;
+  return -2.0 * r * log(d / dhat) - r * r / d;
+}
+__device__ __forceinline__ double bar_d2b(double d, double dhat) {
+  if (d >= dhat || d <= 0.0) return 0.0;
+  const double r = d - dhat;
+  return -2.0 * log(d / dhat) - 4.0 * r / d + r * r / (d * d);
+}
+
+// g (float64) and the PCG right-hand side b = -g in solve precision
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_gather_grad(AsmIn in, const Vec4d* __restrict__ x,
+                                                        Vec4d* __restrict__ g, Vec4<VT>* __restrict__ b,
+                                                        GridReduce gr, double* __restrict__ gnorm2) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (v < in.n) {
+    Vec4d gv{0.0, 0.0, 0.0, 0.0};
+    if (!in.pinned[v]) {
+      double sx = 0.0, sy = 0.0, sz = 0.0;
+      const int t = in.t;
+      for (int k = in.vt_ptr[v]; k < in.vt_ptr[v + 1]; ++k) {
+        const int code = in.vt_code[k];
+        const int e = code >> 2, a = code & 3;
+        sx += in.egrad[(3 * a + 0) * t + e];
+        sy += in.egrad[(3 * a + 1) * t + e];
+        sz += in.egrad[(3 * a + 2) * t + e];
+      }
+      const Vec4d xv = x[v];
+      if (in.contact) {
+        const double dist = in.pn0 * xv.x + in.pn1 * xv.y + in.pn2 * xv.z - in.po;
+        const double k1 = in.kappa * bar_db(dist, in.dhat);
+        sx += k1 * in.pn0; sy += k1 * in.pn1; sz += k1 * in.pn2;
+      }
+      const Vec4d xt = in.xtil[v];
+      const double m = in.mass[v];
+      gv.x = m * (xv.x - xt.x) + in.h2 * sx;
+      gv.y = m * (xv.y - xt.y) + in.h2 * sy;
+      gv.z = m * (xv.z - xt.z) + in.h2 * sz;
+    }
+    g[v] = gv;
+    b[v] = Vec4<VT>{(VT)(-gv.x), (VT)(-gv.y), (VT)(-gv.z), (VT)0};
+    acc[0] = gv.x * gv.x + gv.y * gv.y + gv.z * gv.z;
+  }
+  if (grid_sum<1>(acc, gr, RS_GRAD) && threadIdx.x == 0) *gnorm2 = acc[0];
+}
+
+struct SellAsmIn {
+  int n, t;
+  const int* __restrict__ group_slice;
+  const int* __restrict__ col;
+  const int* __restrict__ row_len;
+  const int* __restrict__ slice_ptr;
+  const int* __restrict__ asm_ptr;
+  const int* __restrict__ asm_code;
+  const double* __restrict__ mass;
+  const uint8_t* __restrict__ pinned;
+  double h2, kappa, dhat, po, pn0, pn1, pn2;
+  int contact;
+};
+
+template <typename AT, typename ET>
+__device__ __forceinline__ void add_elem_block(AT (&acc)[9], const ET* __restrict__ hs, int t, int e,
+                                               int a, int b) {
+  if (a == b) {
+    const int off = hess_offset(a, a);
+    const AT h00 = load_as<AT>(hs[(off + 0) * t + e]), h01 = load_as<AT>(hs[(off + 1) * t + e]),
+             h02 = load_as<AT>(hs[(off + 2) * t + e]), h11 = load_as<AT>(hs[(off + 3) * t + e]),
+             h12 = load_as<AT>(hs[(off + 4) * t + e]), h22 = load_as<AT>(hs[(off + 5) * t + e]);
+    acc[0] += h00; acc[1] += h01; acc[2] += h02;
+    acc[3] += h01; acc[4] += h11; acc[5] += h12;
+    acc[6] += h02; acc[7] += h12; acc[8] += h22;
+  } else if (a < b) {
+    const int off = hess_offset(a, b);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] += load_as<AT>(hs[(off + k) * t + e]);
+  } else {
+    const int off = hess_offset(b, a);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) acc[3 * c + d] += load_as<AT>(hs[(off + 3 * d + c) * t + e]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void inv3(const T (&A)[9], T (&R)[9]) {
+  const T c00 = A[4] * A[8] - A[5] * A[7];
+  const T c01 = A[5] * A[6] - A[3] * A[8];
+  const T c02 = A[3] * A[7] - A[4] * A[6];
+  const T det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+  const T id = T(1) / det;
+  R[0] = c00 * id;
+  R[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+  R[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+  R[3] = c01 * id;
+  R[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+  R[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+  R[6] = c02 * id;
+  R[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+  R[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+}
+
+// One thread per block slot of H.  AT: accumulation type, ET: element
+// Hessian type, MT: storage type of H, VT: solve type (for D^{-1}).
+template <typename AT, typename ET, typename MT, typename VT>
+__global__ void __launch_bounds__(kBlock) k_assemble(SellAsmIn in, int64_t n_slots,
+                                                     const Vec4d* __restrict__ x,
+                                                     const ET* __restrict__ hs, MT* __restrict__ val,
+                                                     VT* __restrict__ dinv) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots) return;
+  const int64_t g = s >> 5;
+  const int lane = (int)(s & 31);
+  const int slice = in.group_slice[g];
+  const int row = slice * kSlice + lane;
+  if (row >= in.n) return;
+  const int k = (int)(g - in.slice_ptr[slice]);
+  MT* out = val + g * 288 + lane;
+  if (k >= in.row_len[row]) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) out[q * 32] = from_d<MT>(0.0);
+    return;
+  }
+  const int c = in.col[s];
+  AT acc[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) acc[q] = AT(0);
+  const bool pin = in.pinned[row] || in.pinned[c];
+  if (pin) {
+    if (c == row) { acc[0] = AT(1); acc[4] = AT(1); acc[8] = AT(1); }
+  } else {
+    for (int q = in.asm_ptr[s]; q < in.asm_ptr[s + 1]; ++q) {
+      const int code = in.asm_code[q];
+      add_elem_block<AT, ET>(acc, hs, in.t, code >> 4, (code >> 2) & 3, code & 3);
+    }
+    const AT h2 = (AT)in.h2;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] *= h2;
+    if (c == row) {
+      const AT m = (AT)in.mass[row];
+      acc[0] += m; acc[4] += m; acc[8] += m;
+      if (in.contact) {
+        const Vec4d xv = x[row];
+        const double dist = in.pn0 * xv.x + in.pn1 * xv.y + in.pn2 * xv.z - in.po;
+        const double k2 = in.h2 * in.kappa * bar_d2b(dist, in.dhat);
+        if (k2 != 0.0) {
+          const double nn[3] = {in.pn0, in.pn1, in.pn2};
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) acc[3 * a + b] += (AT)(k2 * nn[a] * nn[b]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 9; ++q) out[q * 32] = from_d<MT>((double)acc[q]);
+  if (c == row) {
+    // block-Jacobi inverse of the diagonal block as stored
+    VT A[9], R[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] = load_as<VT>(from_d<MT>((double)acc[q]));
+    inv3<VT>(A, R);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) dinv[(int64_t)row * 9 + q] = R[q];
+  }
+}
+
+// ---- state helpers ------------------------------------------------------------------
+__global__ void k_predictor(int n, const double* __restrict__ x, const double* __restrict__ v,
+                            const uint8_t* __restrict__ pinned, double h, double gx, double gy,
+                            double gz, Vec4d* __restrict__ xt, Vec4d* __restrict__ xtil,
+                            Vec4d* __restrict__ xk) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Vec4d p{x[3 * i], x[3 * i + 1], x[3 * i + 2], 0.0};
+  xt[i] = p;
+  Vec4d q = p;
+  if (!pinned[i]) {
+    const double h2 = h * h;
+    q.x = p.x + h * v[3 * i] + h2 * gx;
+    q.y = p.y + h * v[3 * i + 1] + h2 * gy;
+    q.z = p.z + h * v[3 * i + 2] + h2 * gz;
+  }
+  xtil[i] = q;
+  xk[i] = q;
+}
+
+__global__ void k_pack(int n, const double* __restrict__ src, Vec4d* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = Vec4d{src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.0};
+}
+
+__global__ void k_unpack(int n, const Vec4d* __restrict__ src, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const Vec4d s = src[i];
+    dst[3 * i] = s.x; dst[3 * i + 1] = s.y; dst[3 * i + 2] = s.z;
+  }
+}
+
+__global__ void k_disp(int n, const Vec4d* __restrict__ xk, const Vec4d* __restrict__ xt,
+                       double* __restrict__ dx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const Vec4d a = xk[i], b = xt[i];
+    dx[3 * i] = a.x - b.x; dx[3 * i + 1] = a.y - b.y; dx[3 * i + 2] = a.z - b.z;
+  }
+}
+
+__global__ void k_axpy_state(int n, Vec4d* __restrict__ x, const Vec4d* __restrict__ d, double alpha) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    Vec4d a = x[i];
+    const Vec4d b = d[i];
+    a.x += alpha * b.x; a.y += alpha * b.y; a.z += alpha * b.z;
+    x[i] = a;
+  }
+}
+
+template <typename VT>
+__global__ void k_to_solve(int n, const Vec4d* __restrict__ src, Vec4<VT>* __restrict__ dst, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const Vec4d s = src[i];
+    dst[i] = Vec4<VT>{(VT)(scale * s.x), (VT)(scale * s.y), (VT)(scale * s.z), (VT)0};
+  }
+}
+
+template <typename VT>
+__global__ void k_from_solve(int n, const Vec4<VT>* __restrict__ src, const uint8_t* __restrict__ pinned,
+                             Vec4d* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const Vec4<VT> s = src[i];
+    dst[i] = (pinned && pinned[i]) ? Vec4d{0.0, 0.0, 0.0, 0.0} : Vec4d{(double)s.x, (double)s.y, (double)s.z, 0.0};
+  }
+}
+
+// ---- launchers -----------------------------------------------------------------------
+static AsmIn asm_in(mls_ctx* ctx) {
+  return AsmIn{ctx->n, ctx->t, ctx->mass, ctx->pinned, ctx->xtil, ctx->vt_ptr, ctx->vt_code, ctx->egrad,
+               ctx->h * ctx->h, ctx->kappa, ctx->dhat, ctx->po, ctx->pn[0], ctx->pn[1], ctx->pn[2],
+               ctx->contact};
+}
+
+static inline int nblk(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
+
+mls_status launch_gather_grad(mls_ctx* ctx, const Vec4d* x, double* gnorm2_out) {
+  const int nb = nblk(ctx->n);
+  if (nb > kMaxPartials) return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
+  if (ctx->opt.precision == MLS_FP64)
+    k_gather_grad<double><<<nb, kBlock, 0, ctx->stream>>>(asm_in(ctx), x, ctx->grad, (Vec4d*)ctx->vb,
+                                                          ctx->red, gnorm2_out);
+  else
+    k_gather_grad<float><<<nb, kBlock, 0, ctx->stream>>>(asm_in(ctx), x, ctx->grad, (Vec4f*)ctx->vb,
+                                                         ctx->red, gnorm2_out);
+  return cuda_check(ctx, cudaGetLastError(), "k_gather_grad");
+}
+
+mls_status launch_assemble(mls_ctx* ctx, const Vec4d* x) {
+  SellAsmIn in{ctx->n, ctx->t, ctx->group_slice, ctx->col, ctx->row_len, ctx->slice_ptr, ctx->asm_ptr,
+               ctx->asm_code, ctx->mass, ctx->pinned, ctx->h * ctx->h, ctx->kappa, ctx->dhat, ctx->po,
+               ctx->pn[0], ctx->pn[1], ctx->pn[2], ctx->contact};
+  const int64_t n_slots = ctx->n_groups * kSlice;
+  const int nb = nblk(n_slots);
+  switch (ctx->opt.precision) {
+    case MLS_FP64:
+      k_assemble<double, double, double, double><<<nb, kBlock, 0, ctx->stream>>>(
+          in, n_slots, x, (const double*)ctx->ehess, (double*)ctx->hval, (double*)ctx->dinv);
+      break;
+    case MLS_MIXED_FP32:
+      k_assemble<float, float, float, float><<<nb, kBlock, 0, ctx->stream>>>(
+          in, n_slots, x, (const float*)ctx->ehess, (float*)ctx->hval, (float*)ctx->dinv);
+      break;
+    default:
+      k_assemble<float, float, __nv_bfloat16, float><<<nb, kBlock, 0, ctx->stream>>>(
+          in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)ctx->hval, (float*)ctx->dinv);
+      break;
+  }
+  return cuda_check(ctx, cudaGetLastError(), "k_assemble");
+}
+
+mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, double dt) {
+  k_predictor<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, v, ctx->pinned, dt, ctx->grav[0],
+                                                       ctx->grav[1], ctx->grav[2], ctx->xt, ctx->xtil,
+                                                       ctx->xk);
+  return cuda_check(ctx, cudaGetLastError(), "k_predictor");
+}
+
+mls_status launch_pack(mls_ctx* ctx, const double* src, Vec4d* dst) {
+  k_pack<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, dst);
+  return cuda_check(ctx, cudaGetLastError(), "k_pack");
+}
+
+mls_status launch_unpack(mls_ctx* ctx, const Vec4d* src, double* dst) {
+  k_unpack<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, dst);
+  return cuda_check(ctx, cudaGetLastError(), "k_unpack");
+}
+
+mls_status launch_disp_out(mls_ctx* ctx, double* dx_out) {
+  k_disp<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, ctx->xk, ctx->xt, dx_out);
+  return cuda_check(ctx, cudaGetLastError(), "k_disp");
+}
+
+mls_status launch_axpy_state(mls_ctx* ctx, Vec4d* x, const Vec4d* d, double alpha) {
+  k_axpy_state<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, d, alpha);
+  return cuda_check(ctx, cudaGetLastError(), "k_axpy_state");
+}
+
+mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double scale) {
+  if (ctx->opt.precision == MLS_FP64)
+    k_to_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, (Vec4d*)dst, scale);
+  else
+    k_to_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, (Vec4f*)dst, scale);
+  return cuda_check(ctx, cudaGetLastError(), "k_to_solve");
+}
+
+mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst) {
+  if (ctx->opt.precision == MLS_FP64)
+    k_from_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4d*)src, ctx->pinned, dst);
+  else
+    k_from_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4f*)src, ctx->pinned, dst);
+  return cuda_check(ctx, cudaGetLastError(), "k_from_solve");
+}
+
+mls_status launch_from_solve_raw(mls_ctx* ctx, const void* src, Vec4d* dst) {
+  if (ctx->opt.precision == MLS_FP64)
+    k_from_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4d*)src, nullptr, dst);
+  else
+    k_from_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4f*)src, nullptr, dst);
+  return cuda_check(ctx, cudaGetLastError(), "k_from_solve");
+}
+
+}  // namespace mls

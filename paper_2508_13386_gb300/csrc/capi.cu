@@ -1,0 +1,761 @@
+// C ABI: context management, mesh/basis upload and the Newton timestep driver
+// (Sec. 3.1 implicit Euler on Eq. IP; Eq. 5 linear solves; Sec. 3.9 filtered
+// backtracking line search).  The driver keeps every vector on the device and
+// reads back only the few scalars that steer the loop (PCG convergence flags,
+// step norms, line-search energies).
+#include "mls_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+using namespace mls;
+
+namespace mls {
+
+mls_status fail(mls_ctx* ctx, mls_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+mls_status cuda_check(mls_ctx* ctx, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MLS_OK;
+  return fail(ctx, MLS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+mls_status dalloc(mls_ctx* ctx, void** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, MLS_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  ctx->allocs.push_back(q);
+  *p = q;
+  return MLS_OK;
+}
+
+void dfree(mls_ctx* ctx, void* p) {
+  if (!p) return;
+  auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+  if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+  cudaFree(p);
+}
+
+int solve_bytes(const mls_ctx* ctx) { return ctx->opt.precision == MLS_FP64 ? 8 : 4; }
+int storage_bytes(const mls_ctx* ctx) {
+  return ctx->opt.precision == MLS_FP64 ? 8 : (ctx->opt.precision == MLS_MIXED_FP32 ? 4 : 2);
+}
+int element_bytes(const mls_ctx* ctx) { return ctx->opt.precision == MLS_FP64 ? 8 : 4; }
+
+// g . d over float64 vertex vectors
+__global__ void __launch_bounds__(kBlock) k_dot4(int n, const Vec4d* __restrict__ a, const Vec4d* __restrict__ b,
+                                                 GridReduce gr, double* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (v < n) {
+    const Vec4d x = a[v], y = b[v];
+    acc[0] = x.x * y.x + x.y * y.y + x.z * y.z;
+  }
+  if (grid_sum<1>(acc, gr, RS_MISC) && threadIdx.x == 0) *out = acc[0];
+}
+
+static mls_status dot4(mls_ctx* ctx, const Vec4d* a, const Vec4d* b, double* out) {
+  const int nb = (ctx->n + kBlock - 1) / kBlock;
+  k_dot4<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, a, b, ctx->red, ctx->dscal + 8);
+  mls_status st = cuda_check(ctx, cudaGetLastError(), "k_dot4");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemcpyAsync(ctx->dscal_host + 8, ctx->dscal + 8, sizeof(double),
+                                       cudaMemcpyDeviceToHost, ctx->stream), "dot readback");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "dot sync");
+  *out = ctx->dscal_host[8];
+  return st;
+}
+
+static mls_status read_scalar(mls_ctx* ctx, const double* dev, double* host_out) {
+  mls_status st = cuda_check(ctx, cudaMemcpyAsync(ctx->dscal_host + 10, dev, sizeof(double),
+                                                  cudaMemcpyDeviceToHost, ctx->stream), "scalar readback");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "scalar sync");
+  *host_out = ctx->dscal_host[10];
+  return st;
+}
+
+static void free_all(mls_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+  ctx->basis = Basis{};
+  ctx->has_basis = false;
+  ctx->coarse_ready = false;
+  ctx->assembled = false;
+}
+
+static mls_status alloc_state(mls_ctx* ctx);
+
+}  // namespace mls
+
+extern "C" {
+
+mls_status mls_default_options(mls_options* opt) {
+  if (!opt) return MLS_EINVAL;
+  opt->precision = MLS_FP64;
+  opt->preconditioner = MLS_PRECOND_BLOCK_JACOBI;
+  opt->cycle = MLS_CYCLE_ADDITIVE;
+  opt->omega = 1.0;
+  opt->newton_tol = 1e-10;
+  opt->pcg_rtol = 1e-4;
+  opt->max_newton = 50;
+  opt->max_pcg = 20000;
+  opt->coarse_refresh = 0;
+  opt->pcg_check_every = 16;
+  opt->stream = nullptr;
+  return MLS_OK;
+}
+
+static mls_status check_options(const mls_options* o) {
+  if (o->precision < MLS_FP64 || o->precision > MLS_MIXED_BF16) return MLS_EINVAL;
+  if (o->preconditioner < 0 || o->preconditioner > 1) return MLS_EINVAL;
+  if (o->cycle < 0 || o->cycle > 1) return MLS_EINVAL;
+  if (!(o->newton_tol > 0) || !(o->pcg_rtol > 0) || o->max_newton < 1 || o->max_pcg < 1) return MLS_EINVAL;
+  if (!(o->omega > 0) || o->coarse_refresh < 0 || o->pcg_check_every < 1) return MLS_EINVAL;
+  return MLS_OK;
+}
+
+mls_status mls_create(mls_ctx** out, const mls_options* opt) {
+  if (!out) return MLS_EINVAL;
+  *out = nullptr;
+  mls_ctx* ctx = new (std::nothrow) mls_ctx();
+  if (!ctx) return MLS_ENOMEM;
+  if (opt) {
+    if (check_options(opt) != MLS_OK) { delete ctx; return MLS_EINVAL; }
+    ctx->opt = *opt;
+  } else {
+    mls_default_options(&ctx->opt);
+  }
+  ctx->stream = (cudaStream_t)ctx->opt.stream;
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) { cudaGetLastError(); delete ctx; return MLS_ECUDA; }
+  void* h = nullptr;
+  if (cudaMallocHost(&h, sizeof(double) * 16 + sizeof(PcgScalars)) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return MLS_ECUDA;
+  }
+  ctx->host_allocs.push_back(h);
+  ctx->dscal_host = (double*)h;
+  ctx->pcg_host = (PcgScalars*)((char*)h + sizeof(double) * 16);
+  *out = ctx;
+  return MLS_OK;
+}
+
+mls_status mls_destroy(mls_ctx* ctx) {
+  if (!ctx) return MLS_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  free_all(ctx);
+  for (void* p : ctx->host_allocs) cudaFreeHost(p);
+  delete ctx;
+  return MLS_OK;
+}
+
+const char* mls_last_error(const mls_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mls_status mls_set_options(mls_ctx* ctx, const mls_options* opt) {
+  if (!ctx || !opt) return MLS_EINVAL;
+  if (check_options(opt) != MLS_OK) return fail(ctx, MLS_EINVAL, "invalid options");
+  const bool realloc = opt->precision != ctx->opt.precision || opt->stream != ctx->opt.stream;
+  if (realloc && ctx->n > 0)
+    return fail(ctx, MLS_EINVAL, "precision and stream are fixed once a mesh is uploaded");
+  ctx->opt = *opt;
+  ctx->stream = (cudaStream_t)opt->stream;
+  ctx->coarse_ready = false;
+  return MLS_OK;
+}
+
+mls_status mls_set_forces(mls_ctx* ctx, const double* gravity, int contact, const double* plane_n,
+                          double plane_o, double dhat, double kappa) {
+  if (!ctx) return MLS_EINVAL;
+  if (gravity) for (int k = 0; k < 3; ++k) ctx->grav[k] = gravity[k];
+  ctx->contact = contact ? 1 : 0;
+  if (contact) {
+    if (!plane_n || !(dhat > 0) || !(kappa > 0)) return fail(ctx, MLS_EINVAL, "contact needs a plane, dhat > 0, kappa > 0");
+    const double nn = std::sqrt(plane_n[0] * plane_n[0] + plane_n[1] * plane_n[1] + plane_n[2] * plane_n[2]);
+    if (!(nn > 0)) return fail(ctx, MLS_EINVAL, "plane normal must be non-zero");
+    for (int k = 0; k < 3; ++k) ctx->pn[k] = plane_n[k] / nn;
+    ctx->po = plane_o / nn;
+    ctx->dhat = dhat;
+    ctx->kappa = kappa;
+  }
+  return MLS_OK;
+}
+
+mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n, const double* X, int32_t t, const int32_t* tets,
+                           const double* youngs, const double* poisson, const double* density,
+                           const uint8_t* dirichlet) {
+  if (!ctx) return MLS_EINVAL;
+  if (n < 1 || t < 1 || !X || !tets || !youngs || !poisson || !density)
+    return fail(ctx, MLS_EINVAL, "upload_mesh: empty mesh or null array");
+  if ((int64_t)t * 16 > INT32_MAX / 2) return fail(ctx, MLS_EINVAL, "upload_mesh: too many tets");
+  for (int64_t k = 0; k < 4 * (int64_t)t; ++k)
+    if (tets[k] < 0 || tets[k] >= n) return fail(ctx, MLS_EINVAL, "upload_mesh: tet index out of range");
+  for (int e = 0; e < t; ++e) {
+    if (!(youngs[e] > 0) || !(poisson[e] > -1.0 && poisson[e] < 0.5) || !(density[e] > 0))
+      return fail(ctx, MLS_EINVAL, "upload_mesh: invalid material at tet " + std::to_string(e));
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        if (tets[4 * e + a] == tets[4 * e + b]) return fail(ctx, MLS_EINVAL, "upload_mesh: repeated vertex in a tet");
+  }
+  free_all(ctx);
+  ctx->n = n;
+  ctx->t = t;
+  // rest shapes, materials, lumped masses
+  std::vector<double> h_Dminv(9 * (size_t)t), h_vol(t), h_mu(t), h_lam(t), h_mass(n, 0.0);
+  for (int e = 0; e < t; ++e) {
+    const double* p0 = X + 3 * (size_t)tets[4 * e];
+    double D[3][3];
+    for (int k = 0; k < 3; ++k) {
+      const double* pk = X + 3 * (size_t)tets[4 * e + k + 1];
+      for (int a = 0; a < 3; ++a) D[a][k] = pk[a] - p0[a];
+    }
+    const double det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                       D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                       D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+    if (!(det > 0)) return fail(ctx, MLS_EINVAL, "upload_mesh: tet " + std::to_string(e) + " has non-positive rest volume");
+    const double inv[3][3] = {
+        {(D[1][1] * D[2][2] - D[1][2] * D[2][1]) / det, (D[0][2] * D[2][1] - D[0][1] * D[2][2]) / det,
+         (D[0][1] * D[1][2] - D[0][2] * D[1][1]) / det},
+        {(D[1][2] * D[2][0] - D[1][0] * D[2][2]) / det, (D[0][0] * D[2][2] - D[0][2] * D[2][0]) / det,
+         (D[0][2] * D[1][0] - D[0][0] * D[1][2]) / det},
+        {(D[1][0] * D[2][1] - D[1][1] * D[2][0]) / det, (D[0][1] * D[2][0] - D[0][0] * D[2][1]) / det,
+         (D[0][0] * D[1][1] - D[0][1] * D[1][0]) / det}};
+    for (int k = 0; k < 3; ++k)
+      for (int b = 0; b < 3; ++b) h_Dminv[(3 * k + b) * (size_t)t + e] = inv[k][b];
+    h_vol[e] = det / 6.0;
+    const double E = youngs[e], nu = poisson[e];
+    h_mu[e] = E / (2.0 * (1.0 + nu));
+    h_lam[e] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    for (int a = 0; a < 4; ++a) h_mass[tets[4 * e + a]] += density[e] * h_vol[e] / 4.0;
+  }
+  // vertex adjacency through tets (diagonal first, then ascending)
+  std::vector<std::vector<int>> nbr(n);
+  for (int e = 0; e < t; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) nbr[tets[4 * e + a]].push_back(tets[4 * e + b]);
+  std::vector<int> row_len(n);
+  for (int v = 0; v < n; ++v) {
+    auto& L = nbr[v];
+    std::sort(L.begin(), L.end());
+    L.erase(std::unique(L.begin(), L.end()), L.end());
+    auto it = std::find(L.begin(), L.end(), v);
+    if (it == L.end()) L.insert(L.begin(), v);
+    else std::rotate(L.begin(), it, it + 1);
+    row_len[v] = (int)L.size();
+  }
+  const int n_slices = (n + kSlice - 1) / kSlice;
+  std::vector<int> slice_ptr(n_slices + 1, 0);
+  for (int s = 0; s < n_slices; ++s) {
+    int w = 0;
+    for (int v = s * kSlice; v < std::min(n, (s + 1) * kSlice); ++v) w = std::max(w, row_len[v]);
+    slice_ptr[s + 1] = slice_ptr[s] + w;
+  }
+  const int64_t n_groups = slice_ptr[n_slices];
+  const int64_t n_slots = n_groups * kSlice;
+  std::vector<int> group_slice(n_groups), col(n_slots);
+  for (int s = 0; s < n_slices; ++s)
+    for (int g = slice_ptr[s]; g < slice_ptr[s + 1]; ++g) group_slice[g] = s;
+  int64_t nnzb = 0;
+  for (int v = 0; v < n; ++v) {
+    const int s = v / kSlice, lane = v % kSlice;
+    const int w = slice_ptr[s + 1] - slice_ptr[s];
+    for (int k = 0; k < w; ++k)
+      col[((int64_t)slice_ptr[s] + k) * kSlice + lane] = k < row_len[v] ? nbr[v][k] : v;
+    nnzb += row_len[v];
+  }
+  // element-block contributions per slot (CSR over slots)
+  std::vector<int> asm_cnt(n_slots + 1, 0);
+  std::vector<int64_t> code_slot(16 * (size_t)t);
+  for (int e = 0; e < t; ++e)
+    for (int a = 0; a < 4; ++a) {
+      const int v = tets[4 * e + a];
+      const auto& L = nbr[v];
+      const int s = v / kSlice, lane = v % kSlice;
+      for (int b = 0; b < 4; ++b) {
+        const int w = tets[4 * e + b];
+        const int k = (int)(std::find(L.begin(), L.end(), w) - L.begin());
+        const int64_t slot = ((int64_t)slice_ptr[s] + k) * kSlice + lane;
+        code_slot[16 * (size_t)e + 4 * a + b] = slot;
+        asm_cnt[slot + 1]++;
+      }
+    }
+  for (int64_t s = 0; s < n_slots; ++s) asm_cnt[s + 1] += asm_cnt[s];
+  std::vector<int> asm_code(16 * (size_t)t);
+  {
+    std::vector<int> fill(asm_cnt.begin(), asm_cnt.end() - 1);
+    for (int e = 0; e < t; ++e)
+      for (int ab = 0; ab < 16; ++ab) asm_code[fill[code_slot[16 * (size_t)e + ab]]++] = 16 * e + ab;
+  }
+  std::vector<int> vt_ptr(n + 1, 0), vt_code(4 * (size_t)t);
+  for (int e = 0; e < t; ++e)
+    for (int a = 0; a < 4; ++a) vt_ptr[tets[4 * e + a] + 1]++;
+  for (int v = 0; v < n; ++v) vt_ptr[v + 1] += vt_ptr[v];
+  {
+    std::vector<int> fill(vt_ptr.begin(), vt_ptr.end() - 1);
+    for (int e = 0; e < t; ++e)
+      for (int a = 0; a < 4; ++a) vt_code[fill[tets[4 * e + a]]++] = 4 * e + a;
+  }
+  std::vector<int> tets_soa(4 * (size_t)t);
+  for (int e = 0; e < t; ++e)
+    for (int a = 0; a < 4; ++a) tets_soa[a * (size_t)t + e] = tets[4 * e + a];
+  std::vector<Vec4d> Xp(n);
+  for (int v = 0; v < n; ++v) Xp[v] = Vec4d{X[3 * v], X[3 * v + 1], X[3 * v + 2], 0.0};
+  std::vector<uint8_t> pin(n, 0);
+  if (dirichlet)
+    for (int v = 0; v < n; ++v) pin[v] = dirichlet[v] ? 1 : 0;
+
+  auto up = [&](void** dst, const void* src, size_t bytes) -> mls_status {
+    mls_status st = dalloc(ctx, dst, bytes);
+    if (st != MLS_OK) return st;
+    return cuda_check(ctx, cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "mesh upload");
+  };
+  mls_status st;
+  if ((st = up((void**)&ctx->tets, tets_soa.data(), sizeof(int) * 4 * (size_t)t)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->Dminv, h_Dminv.data(), sizeof(double) * 9 * (size_t)t)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->vol, h_vol.data(), sizeof(double) * t)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->mu, h_mu.data(), sizeof(double) * t)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->lam, h_lam.data(), sizeof(double) * t)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->mass, h_mass.data(), sizeof(double) * n)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->pinned, pin.data(), n)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->X, Xp.data(), sizeof(Vec4d) * n)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->slice_ptr, slice_ptr.data(), sizeof(int) * (n_slices + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->group_slice, group_slice.data(), sizeof(int) * n_groups)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->col, col.data(), sizeof(int) * n_slots)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->row_len, row_len.data(), sizeof(int) * n)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->asm_ptr, asm_cnt.data(), sizeof(int) * (n_slots + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->asm_code, asm_code.data(), sizeof(int) * 16 * (size_t)t)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->vt_ptr, vt_ptr.data(), sizeof(int) * (n + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->vt_code, vt_code.data(), sizeof(int) * 4 * (size_t)t)) != MLS_OK) return st;
+  ctx->n_slices = n_slices;
+  ctx->n_groups = n_groups;
+  ctx->nnzb = nnzb;
+  ctx->h_slice_ptr = slice_ptr;
+  ctx->h_row_len = row_len;
+  ctx->h_col = col;
+  return alloc_state(ctx);
+}
+
+}  // extern "C"
+
+namespace mls {
+static mls_status alloc_state(mls_ctx* ctx) {
+  const int n = ctx->n, t = ctx->t;
+  mls_status st;
+  const size_t v4 = sizeof(Vec4d) * (size_t)n;
+  Vec4d** v4bufs[] = {&ctx->xk, &ctx->xt, &ctx->xtil, &ctx->dir, &ctx->grad, &ctx->tmp4};
+  for (Vec4d** b : v4bufs)
+    if ((st = dalloc(ctx, (void**)b, v4)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->egrad, sizeof(double) * 12 * (size_t)t)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->stage, sizeof(double) * 9 * (size_t)n)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->ehess, (size_t)element_bytes(ctx) * 78 * t)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->hval, (size_t)storage_bytes(ctx) * 288 * ctx->n_groups)) != MLS_OK) return st;
+  const int vb = solve_bytes(ctx);
+  if ((st = dalloc(ctx, &ctx->dinv, (size_t)vb * 9 * n)) != MLS_OK) return st;
+  void** sv[] = {&ctx->vb, &ctx->vx, &ctx->vr, &ctx->vz, &ctx->vp, &ctx->vq, &ctx->vw};
+  for (void** b : sv)
+    if ((st = dalloc(ctx, b, (size_t)vb * 4 * n)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->pcg, sizeof(PcgScalars))) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->dscal, sizeof(double) * 16)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->red.partials, sizeof(double) * 4 * kMaxPartials)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->red.counter, sizeof(unsigned) * RS_COUNT)) != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemset(ctx->red.counter, 0, sizeof(unsigned) * RS_COUNT), "counter init");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemset(ctx->tmp4, 0, v4), "zero init");
+  if (st != MLS_OK) return st;
+  return cuda_check(ctx, cudaMemset(ctx->hval, 0, (size_t)storage_bytes(ctx) * 288 * ctx->n_groups), "H init");
+}
+
+// ---- the timestep -------------------------------------------------------------------------
+static const double kArmijo = 1e-4;
+static const double kRoundingRegime = 1e-13;
+static const int kMaxHalvings = 60;
+
+static mls_status assemble_at(mls_ctx* ctx, const Vec4d* x, double* gnorm) {
+  mls_status st;
+  if ((st = launch_eval_elements(ctx, x, nullptr)) != MLS_OK) return st;
+  if ((st = launch_gather_grad(ctx, x, ctx->dscal + 2)) != MLS_OK) return st;
+  if ((st = launch_assemble(ctx, x)) != MLS_OK) return st;
+  ctx->assembled = true;
+  if (gnorm) {
+    double g2 = 0;
+    if ((st = read_scalar(ctx, ctx->dscal + 2, &g2)) != MLS_OK) return st;
+    *gnorm = std::sqrt(g2);
+  }
+  return MLS_OK;
+}
+
+static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
+  mls_stats S{};
+  mls_status st;
+  const double h = ctx->h;
+  const double gmag = std::sqrt(ctx->grav[0] * ctx->grav[0] + ctx->grav[1] * ctx->grav[1] + ctx->grav[2] * ctx->grav[2]);
+  const double scale0 = h * h * std::max(gmag, 1e-30);
+  double E = 0;
+  int infeasible = 0;
+  // x^t must be feasible; start from x_tilde when it is, else from x^t
+  if ((st = launch_energy(ctx, ctx->xt, ctx->tmp4, 0.0, &E, &infeasible)) != MLS_OK) return st;
+  if (infeasible) return fail(ctx, MLS_EINVERTED, "x^t has an inverted tet or a vertex on/below the plane");
+  if (!std::isfinite(E)) return fail(ctx, MLS_ENONFINITE, "non-finite energy at x^t");
+  if ((st = launch_energy(ctx, ctx->xk, ctx->tmp4, 0.0, &E, &infeasible)) != MLS_OK) return st;
+  if (infeasible || !std::isfinite(E)) {
+    st = cuda_check(ctx, cudaMemcpyAsync(ctx->xk, ctx->xt, sizeof(Vec4d) * ctx->n, cudaMemcpyDeviceToDevice,
+                                         ctx->stream), "restart from x^t");
+    if (st != MLS_OK) return st;
+  }
+  const bool two_level = ctx->opt.preconditioner == MLS_PRECOND_TWO_LEVEL;
+  if (two_level && !ctx->has_basis) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_upload_basis");
+  const double eta_floor = ctx->opt.precision == MLS_FP64 ? 1e-13 : 1e-6;
+  double g0 = -1.0;
+  mls_status result = MLS_ENOTCONV;
+  for (int it = 0; it < ctx->opt.max_newton; ++it) {
+    double gnorm = 0;
+    if ((st = assemble_at(ctx, ctx->xk, &gnorm)) != MLS_OK) return st;
+    if (!std::isfinite(gnorm)) return fail(ctx, MLS_ENONFINITE, "non-finite gradient");
+    if (g0 < 0) g0 = gnorm;
+    S.grad_norm = gnorm;
+    S.newton_iters = it + 1;
+    if (gnorm == 0.0) { S.step_rel = 0.0; result = MLS_OK; break; }
+    if (two_level) {
+      const int k = ctx->opt.coarse_refresh;
+      if (k == 0 || it % k == 0 || !ctx->coarse_ready) {
+        if ((st = build_coarse(ctx)) != MLS_OK) return st;
+        S.coarse_builds++;
+      }
+    }
+    double eta = std::min(ctx->opt.pcg_rtol, std::sqrt(gnorm / g0));
+    eta = std::max(eta, eta_floor);
+    int iters = 0;
+    double rel = 0;
+    st = pcg_solve(ctx, eta, ctx->opt.max_pcg, &iters, &rel);
+    S.pcg_iters += iters;
+    if (st != MLS_OK && st != MLS_ENOTCONV) return st;
+    if ((st = launch_from_solve(ctx, ctx->vx, ctx->dir)) != MLS_OK) return st;
+    double dinf = 0, xdisp = 0;
+    if ((st = launch_norms(ctx, ctx->dir, &dinf, &xdisp)) != MLS_OK) return st;
+    if (!std::isfinite(dinf)) return fail(ctx, MLS_ENONFINITE, "non-finite Newton direction");
+    const double step_rel = dinf / std::max(xdisp, scale0);
+    S.step_rel = step_rel;
+    double gd = 0;
+    if ((st = dot4(ctx, ctx->grad, ctx->dir, &gd)) != MLS_OK) return st;
+    if (step_rel <= ctx->opt.newton_tol) {
+      // converged: apply the final (tiny) direction in full when feasible
+      if ((st = launch_energy(ctx, ctx->xk, ctx->dir, 1.0, &E, &infeasible)) != MLS_OK) return st;
+      S.line_search_trials++;
+      if (!infeasible) {
+        if ((st = launch_axpy_state(ctx, ctx->xk, ctx->dir, 1.0)) != MLS_OK) return st;
+      }
+      result = MLS_OK;
+      break;
+    }
+    if (!(gd < 0)) return fail(ctx, MLS_ELINESEARCH, "Newton direction is not a descent direction");
+    double alpha = 1.0;
+    if ((st = launch_ccd(ctx, ctx->xk, ctx->dir, &alpha)) != MLS_OK) return st;
+    double E0 = 0;
+    if ((st = launch_energy(ctx, ctx->xk, ctx->dir, 0.0, &E0, &infeasible)) != MLS_OK) return st;
+    bool accepted = false;
+    for (int hv = 0; hv <= kMaxHalvings; ++hv) {
+      if ((st = launch_energy(ctx, ctx->xk, ctx->dir, alpha, &E, &infeasible)) != MLS_OK) return st;
+      S.line_search_trials++;
+      if (!infeasible) {
+        if (std::fabs(kArmijo * alpha * gd) <= kRoundingRegime * std::fabs(E0) ||
+            E <= E0 + kArmijo * alpha * gd) {
+          accepted = true;
+          break;
+        }
+      }
+      alpha *= 0.5;
+    }
+    if (!accepted) return fail(ctx, MLS_ELINESEARCH, "line search found no acceptable step");
+    if ((st = launch_axpy_state(ctx, ctx->xk, ctx->dir, alpha)) != MLS_OK) return st;
+  }
+  if ((st = launch_energy(ctx, ctx->xk, ctx->tmp4, 0.0, &E, &infeasible)) != MLS_OK) return st;
+  S.energy = E;
+  if (stats) *stats = S;
+  if (result != MLS_OK) return fail(ctx, result, "Newton reached its iteration cap");
+  return MLS_OK;
+}
+
+static mls_status check_mesh(mls_ctx* ctx) {
+  if (!ctx) return MLS_EINVAL;
+  if (ctx->n < 1) return fail(ctx, MLS_EINVAL, "no mesh uploaded");
+  return MLS_OK;
+}
+
+// Stage calls set up the timestep state from (x_t, v_t, dt) without running Newton
+static mls_status set_timestep(mls_ctx* ctx, const double* x_t, const double* v_t, double dt) {
+  if (!(dt > 0)) return fail(ctx, MLS_EINVAL, "dt must be positive");
+  ctx->h = dt;
+  return launch_predictor(ctx, x_t, v_t, dt);
+}
+
+}  // namespace mls
+
+extern "C" {
+
+mls_status mls_newton_step(mls_ctx* ctx, const double* x, const double* v, double dt, double* dx_out,
+                           mls_stats* stats_out) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!x || !v || !dx_out) return fail(ctx, MLS_EINVAL, "null state pointer");
+  if ((st = set_timestep(ctx, x, v, dt)) != MLS_OK) return st;
+  mls_status res = newton(ctx, stats_out);
+  if (res != MLS_OK && res != MLS_ENOTCONV) return res;
+  if ((st = launch_disp_out(ctx, dx_out)) != MLS_OK) return st;
+  st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "newton_step sync");
+  return st != MLS_OK ? st : res;
+}
+
+mls_status mls_newton_step_host(mls_ctx* ctx, const double* x, const double* v, double dt, double* dx_out,
+                                mls_stats* stats_out) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!x || !v || !dx_out) return fail(ctx, MLS_EINVAL, "null state pointer");
+  const size_t bytes = sizeof(double) * 3 * (size_t)ctx->n;
+  double* dev = ctx->stage;
+  st = cuda_check(ctx, cudaMemcpyAsync(dev, x, bytes, cudaMemcpyHostToDevice, ctx->stream), "x upload");
+  if (st == MLS_OK) st = cuda_check(ctx, cudaMemcpyAsync(dev + 3 * (size_t)ctx->n, v, bytes, cudaMemcpyHostToDevice, ctx->stream), "v upload");
+  mls_status res = st;
+  if (st == MLS_OK) res = mls_newton_step(ctx, dev, dev + 3 * (size_t)ctx->n, dt, dev + 6 * (size_t)ctx->n, stats_out);
+  if (res == MLS_OK || res == MLS_ENOTCONV) {
+    st = cuda_check(ctx, cudaMemcpyAsync(dx_out, dev + 6 * (size_t)ctx->n, bytes, cudaMemcpyDeviceToHost, ctx->stream), "dx download");
+    if (st == MLS_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "host step sync");
+    if (st != MLS_OK) res = st;
+  }
+  cudaStreamSynchronize(ctx->stream);
+  return res;
+}
+
+mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, const int32_t* vrow,
+                            const int32_t* handle, const double* phi) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!origins || !vrow || (!handle && vrow[ctx->n] > 0) || (!phi && vrow[ctx->n] > 0))
+    return fail(ctx, MLS_EINVAL, "upload_basis: null array");
+  if (ctx->has_basis) {
+    Basis& B = ctx->basis;
+    void* old[] = {B.vrow, B.vh, B.vphi, B.hrow, B.hv, B.hphi, B.origins, B.yrow, B.yh, B.yslot, B.hn_row, B.hn,
+                   B.ent_ptr, B.ent_y, B.ent_v, B.ent_phi, B.ypair_row, ctx->yval, ctx->Ac, ctx->Acopy,
+                   ctx->Linv, ctx->LinvT, ctx->cvec, ctx->cvec2, ctx->chol_info};
+    for (void* p : old) dfree(ctx, p);
+    ctx->basis = Basis{};
+    ctx->has_basis = false;
+    ctx->coarse_ready = false;
+  }
+  return basis_upload(ctx, m, origins, vrow, handle, phi);
+}
+
+mls_status mls_eval_elements(mls_ctx* ctx, const double* x, double* energy, double* grad, double* hess) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!x) return fail(ctx, MLS_EINVAL, "null x");
+  if ((st = launch_pack(ctx, x, ctx->tmp4)) != MLS_OK) return st;
+  if ((st = launch_eval_elements(ctx, ctx->tmp4, energy)) != MLS_OK) return st;
+  if (grad) {
+    // [12][t] SoA -> [t][12]
+    std::vector<double> h(12 * (size_t)ctx->t), o(12 * (size_t)ctx->t);
+    st = cuda_check(ctx, cudaMemcpyAsync(h.data(), ctx->egrad, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream), "grad readback");
+    if (st != MLS_OK) return st;
+    if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "grad sync")) != MLS_OK) return st;
+    for (int e = 0; e < ctx->t; ++e)
+      for (int k = 0; k < 12; ++k) o[12 * (size_t)e + k] = h[(size_t)k * ctx->t + e];
+    st = cuda_check(ctx, cudaMemcpyAsync(grad, o.data(), sizeof(double) * o.size(), cudaMemcpyHostToDevice, ctx->stream), "grad out");
+    if (st != MLS_OK) return st;
+  }
+  if (hess) {
+    if ((st = launch_expand_hessian(ctx, hess)) != MLS_OK) return st;
+  }
+  // restore zero scratch
+  st = cuda_check(ctx, cudaMemsetAsync(ctx->tmp4, 0, sizeof(Vec4d) * ctx->n, ctx->stream), "scratch reset");
+  if (st != MLS_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "eval sync");
+}
+
+mls_status mls_assemble(mls_ctx* ctx, const double* x, const double* x_t, const double* v_t, double dt,
+                        double* grad_out) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!x || !x_t || !v_t) return fail(ctx, MLS_EINVAL, "null pointer");
+  if ((st = set_timestep(ctx, x_t, v_t, dt)) != MLS_OK) return st;
+  if ((st = launch_pack(ctx, x, ctx->xk)) != MLS_OK) return st;
+  if ((st = assemble_at(ctx, ctx->xk, nullptr)) != MLS_OK) return st;
+  if (grad_out && (st = launch_unpack(ctx, ctx->grad, grad_out)) != MLS_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "assemble sync");
+}
+
+mls_status mls_get_hessian(mls_ctx* ctx, int32_t* row_ptr, int32_t* colout, double* val, int64_t* nnzb) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (nnzb) *nnzb = ctx->nnzb;
+  if (!row_ptr && !colout && !val) return MLS_OK;
+  if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "H not assembled");
+  const int sb = storage_bytes(ctx);
+  std::vector<unsigned char> raw((size_t)sb * 288 * ctx->n_groups);
+  st = cuda_check(ctx, cudaMemcpy(raw.data(), ctx->hval, raw.size(), cudaMemcpyDeviceToHost), "H readback");
+  if (st != MLS_OK) return st;
+  int64_t pos = 0;
+  for (int v = 0; v < ctx->n; ++v) {
+    if (row_ptr) row_ptr[v] = (int32_t)pos;
+    const int s = v / kSlice, lane = v % kSlice;
+    // ascending column order for the exported CSR
+    std::vector<std::pair<int, int>> order;
+    for (int k = 0; k < ctx->h_row_len[v]; ++k)
+      order.emplace_back(ctx->h_col[((size_t)ctx->h_slice_ptr[s] + k) * kSlice + lane], k);
+    std::sort(order.begin(), order.end());
+    for (auto& ck : order) {
+      const int64_t g = (int64_t)ctx->h_slice_ptr[s] + ck.second;
+      if (colout) colout[pos] = ck.first;
+      if (val)
+        for (int q = 0; q < 9; ++q) {
+          const size_t idx = (size_t)g * 288 + q * 32 + lane;
+          double x;
+          if (sb == 8) x = ((const double*)raw.data())[idx];
+          else if (sb == 4) x = ((const float*)raw.data())[idx];
+          else {
+            uint16_t b = ((const uint16_t*)raw.data())[idx];
+            uint32_t u = (uint32_t)b << 16;
+            float f;
+            memcpy(&f, &u, 4);
+            x = f;
+          }
+          val[pos * 9 + q] = x;
+        }
+      ++pos;
+    }
+  }
+  if (row_ptr) row_ptr[ctx->n] = (int32_t)pos;
+  return MLS_OK;
+}
+
+mls_status mls_spmv(mls_ctx* ctx, const double* x, double* y) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "H not assembled");
+  if ((st = launch_pack(ctx, x, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_to_solve(ctx, ctx->dir, ctx->vp, 1.0)) != MLS_OK) return st;
+  if ((st = launch_spmv(ctx, ctx->vp, ctx->vq)) != MLS_OK) return st;
+  if ((st = launch_from_solve(ctx, ctx->vq, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_unpack(ctx, ctx->dir, y)) != MLS_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "spmv sync");
+}
+
+mls_status mls_precond_apply(mls_ctx* ctx, const double* r, double* z) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "H not assembled");
+  if ((st = launch_pack(ctx, r, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_to_solve(ctx, ctx->dir, ctx->vr, 1.0)) != MLS_OK) return st;
+  if ((st = precond_apply(ctx, ctx->vr, ctx->vz)) != MLS_OK) return st;
+  if ((st = launch_from_solve(ctx, ctx->vz, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_unpack(ctx, ctx->dir, z)) != MLS_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "precond sync");
+}
+
+mls_status mls_pcg_solve(mls_ctx* ctx, const double* b, double* d, double rtol, int max_iter, int* iters,
+                         double* rel_res) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "H not assembled");
+  if (!(rtol > 0) || max_iter < 1) return fail(ctx, MLS_EINVAL, "rtol must be > 0 and max_iter >= 1");
+  if ((st = launch_pack(ctx, b, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_to_solve(ctx, ctx->dir, ctx->vb, 1.0)) != MLS_OK) return st;
+  mls_status res = pcg_solve(ctx, rtol, max_iter, iters, rel_res);
+  if (res != MLS_OK && res != MLS_ENOTCONV) return res;
+  if ((st = launch_from_solve(ctx, ctx->vx, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_unpack(ctx, ctx->dir, d)) != MLS_OK) return st;
+  st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "pcg sync");
+  return st != MLS_OK ? st : res;
+}
+
+// q [m][12] float64 <-> solve precision on the device
+__global__ void k_cast_in(int n, const double* __restrict__ a, float* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_cast_out(int n, const float* __restrict__ a, double* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+mls_status mls_prolong(mls_ctx* ctx, const double* q, double* w) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
+  const int r = 12 * ctx->basis.m;
+  if (ctx->opt.precision == MLS_FP64) {
+    st = cuda_check(ctx, cudaMemcpyAsync(ctx->cvec, q, sizeof(double) * r, cudaMemcpyDeviceToDevice, ctx->stream), "q copy");
+  } else {
+    k_cast_in<<<(r + 255) / 256, 256, 0, ctx->stream>>>(r, q, (float*)ctx->cvec);
+    st = cuda_check(ctx, cudaGetLastError(), "cast");
+  }
+  if (st != MLS_OK) return st;
+  if ((st = launch_prolong(ctx, ctx->cvec, ctx->vw, false)) != MLS_OK) return st;
+  if ((st = launch_from_solve_raw(ctx, ctx->vw, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_unpack(ctx, ctx->dir, w)) != MLS_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "prolong sync");
+}
+
+mls_status mls_restrict(mls_ctx* ctx, const double* r, double* z) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
+  const int rr = 12 * ctx->basis.m;
+  if ((st = launch_pack(ctx, r, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_to_solve(ctx, ctx->dir, ctx->vr, 1.0)) != MLS_OK) return st;
+  if ((st = launch_restrict(ctx, ctx->vr, ctx->cvec)) != MLS_OK) return st;
+  if (ctx->opt.precision == MLS_FP64) {
+    st = cuda_check(ctx, cudaMemcpyAsync(z, ctx->cvec, sizeof(double) * rr, cudaMemcpyDeviceToDevice, ctx->stream), "z copy");
+  } else {
+    k_cast_out<<<(rr + 255) / 256, 256, 0, ctx->stream>>>(rr, (const float*)ctx->cvec, z);
+    st = cuda_check(ctx, cudaGetLastError(), "cast");
+  }
+  if (st != MLS_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "restrict sync");
+}
+
+mls_status mls_build_coarse(mls_ctx* ctx) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  st = build_coarse(ctx);
+  if (st != MLS_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "coarse sync");
+}
+
+mls_status mls_get_coarse(mls_ctx* ctx, double* A) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!ctx->has_basis || !ctx->Acopy) return fail(ctx, MLS_EINVAL, "no coarse operator");
+  const int r = 12 * ctx->basis.m;
+  return cuda_check(ctx, cudaMemcpy(A, ctx->Acopy, sizeof(double) * r * r, cudaMemcpyDeviceToHost), "Ac readback");
+}
+
+mls_status mls_energy(mls_ctx* ctx, const double* x, const double* d, double alpha, double* E, int* feasible) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!x || !d || !E) return fail(ctx, MLS_EINVAL, "null pointer");
+  if ((st = launch_pack(ctx, x, ctx->xk)) != MLS_OK) return st;
+  if ((st = launch_pack(ctx, d, ctx->dir)) != MLS_OK) return st;
+  int inf = 0;
+  if ((st = launch_energy(ctx, ctx->xk, ctx->dir, alpha, E, &inf)) != MLS_OK) return st;
+  if (feasible) *feasible = inf ? 0 : 1;
+  return MLS_OK;
+}
+
+mls_status mls_ccd_bound(mls_ctx* ctx, const double* x, const double* d, double* alpha) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!x || !d || !alpha) return fail(ctx, MLS_EINVAL, "null pointer");
+  if ((st = launch_pack(ctx, x, ctx->xk)) != MLS_OK) return st;
+  if ((st = launch_pack(ctx, d, ctx->dir)) != MLS_OK) return st;
+  return launch_ccd(ctx, ctx->xk, ctx->dir, alpha);
+}
+
+}  // extern "C"

@@ -1,0 +1,298 @@
+// Internal declarations of the sm_103a multilevel timestep library.
+//
+// Data layout in device memory (n vertices, t tets):
+//   vertex vectors      Vec4<T>[n]   (x, y, z, pad) -- one 16 B (float) or
+//                                    32 B (double) aligned load per vertex
+//   tets                int32 [4][t] SoA, Dm^{-1} double [9][t] SoA,
+//                       vol/mu/lam double [t]
+//   element gradients   double [12][t] SoA
+//   element Hessians    ET [78][t] SoA: the 10 upper 3x3 blocks of the 12x12
+//                       (diagonal blocks keep their 6 upper entries)
+//   H (3x3 BSR)         sliced ELL with 32 rows per slice ("SELL-32"):
+//                       group g holds one block slot of 32 consecutive rows;
+//                       col[g*32 + lane], val[g*288 + k*32 + lane] (k = 0..8,
+//                       row-major 3x3).  Slot 0 of every row is its diagonal
+//                       block; slots past a row's length are padding.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "mls.h"
+
+namespace mls {
+
+template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T x, y, z, w; };
+using Vec4d = Vec4<double>;
+using Vec4f = Vec4<float>;
+
+constexpr int kBlock = 256;
+constexpr int kSlice = 32;
+constexpr int kMaxPartials = 8192;
+
+// offsets of the 10 upper 3x3 blocks inside the 78-value element Hessian
+// (order (0,0),(0,1),(0,2),(0,3),(1,1),(1,2),(1,3),(2,2),(2,3),(3,3))
+__host__ __device__ constexpr int hess_offset(int a, int b) {
+  return a == 0 ? (b == 0 ? 0 : b == 1 ? 6 : b == 2 ? 15 : 24)
+       : a == 1 ? (b == 1 ? 33 : b == 2 ? 39 : 48)
+       : a == 2 ? (b == 2 ? 57 : 63)
+       : 72;
+}
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T> __device__ __forceinline__ T from_d(double v);
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __float2bfloat16((float)v); }
+
+template <typename A, typename T> __device__ __forceinline__ A load_as(T v) { return (A)v; }
+template <> __device__ __forceinline__ float load_as<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ double load_as<double, __nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+// ---- deterministic grid-wide sums: block partials, reduced by the last block
+struct GridReduce {
+  double* partials;        // [K][kMaxPartials]
+  unsigned int* counter;   // one counter per reduction slot, left at zero
+};
+
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double (&sh)[K][32]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    v[k] = s;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[k][warp] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = lane < nw ? sh[k][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Sums v over the whole grid.  Returns true in exactly one block (the last
+// to arrive), where thread 0 holds the totals in v.  Partials are summed in
+// block order, so the result does not depend on scheduling.
+template <int K>
+__device__ bool grid_sum(double (&v)[K], const GridReduce& gr, int slot) {
+  __shared__ double sh[K][32];
+  __shared__ bool last;
+  block_sum<K>(v, sh);
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) gr.partials[k * kMaxPartials + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned prev = atomicAdd(gr.counter + slot, 1u);
+    last = (prev == (unsigned)nb - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+      s += ((volatile double*)gr.partials)[k * kMaxPartials + b];
+    acc[k] = s;
+  }
+  block_sum<K>(acc, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = acc[k];
+    gr.counter[slot] = 0;
+  }
+  return true;
+}
+
+// atomic max / min for non-negative doubles through their bit patterns
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+  atomicMax((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_min_nonneg(double* addr, double v) {
+  atomicMin((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// PCG scalars kept on the device so iterations run without host round trips
+struct PcgScalars {
+  double rz, pq, rr, bb, alpha, beta, tol2;
+  int iter, max_iter, done;
+};
+
+// Reduction slots (one counter each)
+enum { RS_PCG_PQ = 0, RS_PCG_RR, RS_PCG_RZ, RS_ENERGY, RS_MISC, RS_GRAD, RS_COUNT };
+
+struct Basis {
+  int m = 0;                  // handles
+  int nnz = 0;                // vertex-handle pairs
+  int* vrow = nullptr;        // [n+1]  per-vertex CSR
+  int* vh = nullptr;          // [nnz]  handle
+  double* vphi = nullptr;     // [nnz]
+  int* hrow = nullptr;        // [m+1]  per-handle CSR (transpose)
+  int* hv = nullptr;          // [nnz]  vertex
+  double* hphi = nullptr;     // [nnz]
+  double* origins = nullptr;  // [m][3]
+  // Galerkin structure
+  int* yrow = nullptr;        // [n+1] CSR of handles reachable from row v through H
+  int* yh = nullptr;          // [ny] handle of each (v, j) pair
+  int64_t ny = 0;
+  int16_t* yslot = nullptr;   // [n_slots * maxk] local index into row v's Y list per (slot, basis entry)
+  int maxk = 0;               // max handles per vertex
+  int* hn_row = nullptr;      // [m+1] coarse block-row neighbours (CSR)
+  int* hn = nullptr;          // [nb] neighbour handle
+  int nb = 0;
+  int* ent_ptr = nullptr;     // [nb+1] entries of each coarse block (i, hn[s])
+  int* ent_y = nullptr;       // [nent] index of Y_vj
+  int* ent_v = nullptr;       // [nent] vertex v in supp(i)
+  double* ent_phi = nullptr;  // [nent] phi_i(v)
+  int64_t nent = 0;
+  int* ypair_row = nullptr;   // [ny] row v of each (v, j) pair
+  std::vector<int> h_vrow, h_hrow;
+};
+
+}  // namespace mls
+
+struct mls_ctx {
+  mls_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int device = 0;
+
+  // mesh
+  int n = 0, t = 0;
+  int* tets = nullptr;       // [4][t]
+  double* Dminv = nullptr;   // [9][t]
+  double* vol = nullptr;     // [t]
+  double* mu = nullptr;      // [t]
+  double* lam = nullptr;     // [t]
+  double* mass = nullptr;    // [n]
+  uint8_t* pinned = nullptr; // [n]
+  mls::Vec4d* X = nullptr;   // [n] rest positions
+
+  // sparsity of H (SELL-32)
+  int n_slices = 0;
+  int64_t n_groups = 0;            // slot groups of 32
+  int* slice_ptr = nullptr;        // [n_slices + 1] first group of each slice
+  int* group_slice = nullptr;      // [n_groups]
+  int* col = nullptr;              // [n_groups * 32]
+  int* row_len = nullptr;          // [n]
+  int* asm_ptr = nullptr;          // [n_groups * 32 + 1]
+  int* asm_code = nullptr;         // [16 t] (e * 16 + a * 4 + b)
+  int* vt_ptr = nullptr;           // [n + 1]
+  int* vt_code = nullptr;          // [4 t] (e * 4 + a)
+  int64_t nnzb = 0;                // real (non-padding) blocks
+  std::vector<int> h_slice_ptr, h_row_len, h_col;
+
+  // per-timestep / per-iteration state
+  double h = 1.0 / 60.0;
+  mls::Vec4d* xk = nullptr;        // current iterate
+  mls::Vec4d* xt = nullptr;        // x^t
+  mls::Vec4d* xtil = nullptr;      // predictor
+  mls::Vec4d* dir = nullptr;       // Newton direction (float64)
+  mls::Vec4d* grad = nullptr;      // gradient (float64)
+  mls::Vec4d* tmp4 = nullptr;      // zero vector (float64), restored after scratch use
+  double* stage = nullptr;         // [3][n][3] staging for host-pointer timesteps
+  double* egrad = nullptr;         // [12][t]
+  void* ehess = nullptr;           // [78][t] element precision
+  void* hval = nullptr;            // [n_groups * 288] storage precision
+  void* dinv = nullptr;            // [n][9] solve precision
+  void* vb = nullptr;              // PCG vectors in solve precision: b, x, r, z, p, q, w
+  void* vx = nullptr;
+  void* vr = nullptr;
+  void* vz = nullptr;
+  void* vp = nullptr;
+  void* vq = nullptr;
+  void* vw = nullptr;
+  mls::PcgScalars* pcg = nullptr;  // device
+  mls::PcgScalars* pcg_host = nullptr;  // pinned
+  double* dscal = nullptr;         // device scalars [16]
+  double* dscal_host = nullptr;    // pinned [16]
+  mls::GridReduce red{};
+  bool assembled = false;
+
+  // forces
+  double grav[3] = {0.0, 0.0, -9.81};
+  int contact = 0;
+  double pn[3] = {0.0, 0.0, 1.0};
+  double po = 0.0, dhat = 1e-3, kappa = 1e5;
+
+  // basis / coarse level
+  mls::Basis basis;
+  bool has_basis = false;
+  double* Ac = nullptr;            // [r][r] float64 Galerkin operator, then its Cholesky factor
+  void* Linv = nullptr;            // [r][r] W = L^{-1} in solve precision (lower)
+  void* LinvT = nullptr;           // [r][r] W^T (upper)
+  double* Acopy = nullptr;         // [r][r] copy of the operator before factorisation
+  void* yval = nullptr;            // [ny][36] H U blocks (solve precision)
+  void* cvec = nullptr;            // [r] coarse vectors (solve precision)
+  void* cvec2 = nullptr;
+  bool coarse_ready = false;
+  int* chol_info = nullptr;        // device: first non-positive pivot + 1, or 0
+
+  std::vector<void*> allocs;       // every device allocation, freed by mls_destroy
+  std::vector<void*> host_allocs;  // pinned host allocations
+};
+
+namespace mls {
+
+// allocation helpers (host side; record for cleanup)
+mls_status dalloc(mls_ctx* ctx, void** p, size_t bytes);
+void dfree(mls_ctx* ctx, void* p);
+mls_status fail(mls_ctx* ctx, mls_status st, const std::string& msg);
+mls_status cuda_check(mls_ctx* ctx, cudaError_t e, const char* what);
+
+int solve_bytes(const mls_ctx* ctx);     // bytes per scalar of PCG vectors
+int storage_bytes(const mls_ctx* ctx);   // bytes per scalar of H values
+int element_bytes(const mls_ctx* ctx);   // bytes per scalar of element Hessians
+
+// kernels launched from the host code (each file exposes launchers)
+mls_status launch_eval_elements(mls_ctx* ctx, const Vec4d* x, double* energy_out);
+mls_status launch_expand_hessian(mls_ctx* ctx, double* hess_out);
+mls_status launch_gather_grad(mls_ctx* ctx, const Vec4d* x, double* gnorm2_out);
+mls_status launch_assemble(mls_ctx* ctx, const Vec4d* x);
+mls_status launch_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double alpha, double* E,
+                         int* infeasible);
+mls_status launch_ccd(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double* alpha);
+mls_status launch_norms(mls_ctx* ctx, const Vec4d* d, double* dinf, double* xdisp_inf);
+mls_status launch_axpy_state(mls_ctx* ctx, Vec4d* x, const Vec4d* d, double alpha);
+mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, double dt);
+mls_status launch_pack(mls_ctx* ctx, const double* src, Vec4d* dst);
+mls_status launch_unpack(mls_ctx* ctx, const Vec4d* src, double* dst);
+mls_status launch_disp_out(mls_ctx* ctx, double* dx_out);
+
+mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y);  // solve-precision vectors
+mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double scale);
+mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst);      // zero on Dirichlet vertices
+mls_status launch_from_solve_raw(mls_ctx* ctx, const void* src, Vec4d* dst);  // no masking
+mls_status pcg_solve(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res);
+mls_status precond_apply(mls_ctx* ctx, const void* r, void* z);
+
+mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* vrow,
+                        const int* handle, const double* phi);
+mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate);
+mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q);
+mls_status build_coarse(mls_ctx* ctx);
+mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out);
+
+}  // namespace mls

@@ -1,0 +1,673 @@
+// The two-level preconditioner built from the sparse LBS basis.
+//
+// Basis (Eq. LBS, Sec. 3.4-3.5): U[3v + c, 12j + 4c + l] = phi_j(v) a_l with
+// a = [1, X_v - o_j].  Prolongation w = U q and restriction z = U^T r apply it
+// without assembling U (the paper's CSR-like basis products, Sec. 3.7.1).
+//
+// Coarse operator: A_c = U^T H U (the subspace "sandwich" matrix of Alg. 2),
+// formed explicitly in two sparse passes:
+//   Y = H U       one thread per (row v, handle j reachable from v): the 3x12
+//                 block Y_vj = sum_w H_vw phi_j(w) (I_3 (x) a_wj^T)
+//   A_c = U^T Y   one CTA per coarse block row i: for each neighbour handle j,
+//                 A_ij = sum_{v in supp i} phi_i(v) a_vi (x) Y_vj, summed in a
+//                 fixed order (no atomics)
+// then factored A_c = L L^T by a blocked right-looking Cholesky in float64,
+// and inverted, W = L^{-1}, so that each coarse solve A_c^{-1} c = W^T (W c)
+// is two dense triangular matrix-vector products spread over all SMs.
+//
+// Preconditioner (S = omega D^{-1}, D the 3x3 block diagonal of H,
+// Q = U A_c^{-1} U^T):
+//   additive        z = S r + Q r
+//   multiplicative  z1 = S r; z2 = z1 + Q (r - H z1); z = z2 + S (r - H z2)
+#include "mls_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace mls {
+
+mls_status launch_residual(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S);
+mls_status launch_jacobi(mls_ctx* ctx, const void* r, void* z, double omega, const PcgScalars* S);
+
+static inline int nblk(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
+
+// ---- host: basis upload and symbolic structure ---------------------------------------
+mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* vrow, const int* handle,
+                        const double* phi) {
+  const int n = ctx->n;
+  Basis& B = ctx->basis;
+  if (m < 1) return fail(ctx, MLS_EINVAL, "n_handles must be >= 1");
+  if (vrow[0] != 0) return fail(ctx, MLS_EINVAL, "vrow[0] must be 0");
+  for (int v = 0; v < n; ++v)
+    if (vrow[v + 1] < vrow[v]) return fail(ctx, MLS_EINVAL, "vrow must be non-decreasing");
+  const int nnz = vrow[n];
+  for (int k = 0; k < nnz; ++k)
+    if (handle[k] < 0 || handle[k] >= m) return fail(ctx, MLS_EINVAL, "basis handle index out of range");
+  // per-vertex lists sorted by handle, duplicates merged
+  std::vector<int> h_vrow(n + 1, 0), h_vh;
+  std::vector<double> h_vphi;
+  h_vh.reserve(nnz);
+  h_vphi.reserve(nnz);
+  int maxk = 0;
+  for (int v = 0; v < n; ++v) {
+    std::vector<std::pair<int, double>> e;
+    for (int k = vrow[v]; k < vrow[v + 1]; ++k) e.emplace_back(handle[k], phi[k]);
+    std::sort(e.begin(), e.end());
+    int cnt = 0;
+    for (size_t q = 0; q < e.size(); ++q) {
+      if (q > 0 && e[q].first == e[q - 1].first) { h_vphi.back() += e[q].second; continue; }
+      h_vh.push_back(e[q].first);
+      h_vphi.push_back(e[q].second);
+      ++cnt;
+    }
+    h_vrow[v + 1] = h_vrow[v] + cnt;
+    maxk = std::max(maxk, cnt);
+  }
+  const int nz = h_vrow[n];
+  // transpose: per-handle vertex lists
+  std::vector<int> h_hrow(m + 1, 0), h_hv(nz);
+  std::vector<double> h_hphi(nz);
+  for (int k = 0; k < nz; ++k) h_hrow[h_vh[k] + 1]++;
+  for (int j = 0; j < m; ++j) h_hrow[j + 1] += h_hrow[j];
+  {
+    std::vector<int> fill(h_hrow.begin(), h_hrow.end() - 1);
+    for (int v = 0; v < n; ++v)
+      for (int k = h_vrow[v]; k < h_vrow[v + 1]; ++k) {
+        const int p = fill[h_vh[k]]++;
+        h_hv[p] = v;
+        h_hphi[p] = h_vphi[k];
+      }
+  }
+  // K_v: handles reachable from row v through the sparsity of H
+  const std::vector<int>& sp = ctx->h_slice_ptr;
+  const std::vector<int>& rl = ctx->h_row_len;
+  const std::vector<int>& hc = ctx->h_col;
+  auto col_of = [&](int v, int k) { return hc[((size_t)sp[v >> 5] + k) * 32 + (v & 31)]; };
+  std::vector<int> h_yrow(n + 1, 0), h_yh;
+  std::vector<int16_t> h_yslot((size_t)ctx->n_groups * 32 * std::max(maxk, 1), (int16_t)-1);
+  std::vector<int> mark(m, -1), local(m, 0);
+  for (int v = 0; v < n; ++v) {
+    std::vector<int> Kv;
+    for (int k = 0; k < rl[v]; ++k) {
+      const int w = col_of(v, k);
+      for (int q = h_vrow[w]; q < h_vrow[w + 1]; ++q) {
+        const int j = h_vh[q];
+        if (mark[j] != v) { mark[j] = v; Kv.push_back(j); }
+      }
+    }
+    std::sort(Kv.begin(), Kv.end());
+    for (size_t q = 0; q < Kv.size(); ++q) local[Kv[q]] = (int)q;
+    for (int k = 0; k < rl[v]; ++k) {
+      const int w = col_of(v, k);
+      const size_t slot = ((size_t)sp[v >> 5] + k) * 32 + (v & 31);
+      for (int q = h_vrow[w]; q < h_vrow[w + 1]; ++q)
+        h_yslot[slot * maxk + (q - h_vrow[w])] = (int16_t)local[h_vh[q]];
+    }
+    h_yrow[v + 1] = h_yrow[v] + (int)Kv.size();
+    h_yh.insert(h_yh.end(), Kv.begin(), Kv.end());
+  }
+  const int64_t ny = h_yrow[n];
+  // coarse block-row neighbours N_i = union of K_v over v in supp(i), and the
+  // per-(i, j) entry lists (v, y index) sorted by neighbour slot
+  std::vector<int> h_hn_row(m + 1, 0), h_hn;
+  std::vector<int> h_ent_ptr(1, 0), h_ent_y, h_ent_v;
+  std::vector<double> h_ent_phi;
+  std::vector<int> mark2(m, -1);
+  std::vector<std::vector<std::pair<int, int>>> per_slot;  // reused
+  for (int i = 0; i < m; ++i) {
+    std::vector<int> Ni;
+    for (int p = h_hrow[i]; p < h_hrow[i + 1]; ++p) {
+      const int v = h_hv[p];
+      for (int q = h_yrow[v]; q < h_yrow[v + 1]; ++q) {
+        const int j = h_yh[q];
+        if (mark2[j] != i) { mark2[j] = i; Ni.push_back(j); }
+      }
+    }
+    std::sort(Ni.begin(), Ni.end());
+    for (size_t q = 0; q < Ni.size(); ++q) local[Ni[q]] = (int)q;
+    per_slot.assign(Ni.size(), {});
+    for (int p = h_hrow[i]; p < h_hrow[i + 1]; ++p) {
+      const int v = h_hv[p];
+      for (int q = h_yrow[v]; q < h_yrow[v + 1]; ++q) per_slot[local[h_yh[q]]].emplace_back(p, q);
+    }
+    for (size_t s = 0; s < Ni.size(); ++s) {
+      for (auto& pq : per_slot[s]) {
+        h_ent_y.push_back(pq.second);
+        h_ent_v.push_back(h_hv[pq.first]);
+        h_ent_phi.push_back(h_hphi[pq.first]);
+      }
+      h_ent_ptr.push_back((int)h_ent_y.size());
+    }
+    h_hn_row[i + 1] = h_hn_row[i] + (int)Ni.size();
+    h_hn.insert(h_hn.end(), Ni.begin(), Ni.end());
+  }
+  const int nbk = h_hn_row[m];
+  const size_t nent = h_ent_y.size();
+
+  // device copies
+  auto up = [&](void** dst, const void* src, size_t bytes) -> mls_status {
+    mls_status st = dalloc(ctx, dst, std::max<size_t>(bytes, 16));
+    if (st != MLS_OK) return st;
+    if (bytes) return cuda_check(ctx, cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "basis upload");
+    return MLS_OK;
+  };
+  mls_status st;
+  if ((st = up((void**)&B.vrow, h_vrow.data(), sizeof(int) * (n + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&B.vh, h_vh.data(), sizeof(int) * nz)) != MLS_OK) return st;
+  if ((st = up((void**)&B.vphi, h_vphi.data(), sizeof(double) * nz)) != MLS_OK) return st;
+  if ((st = up((void**)&B.hrow, h_hrow.data(), sizeof(int) * (m + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&B.hv, h_hv.data(), sizeof(int) * nz)) != MLS_OK) return st;
+  if ((st = up((void**)&B.hphi, h_hphi.data(), sizeof(double) * nz)) != MLS_OK) return st;
+  if ((st = up((void**)&B.origins, origins, sizeof(double) * 3 * m)) != MLS_OK) return st;
+  if ((st = up((void**)&B.yrow, h_yrow.data(), sizeof(int) * (n + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&B.yh, h_yh.data(), sizeof(int) * ny)) != MLS_OK) return st;
+  if ((st = up((void**)&B.yslot, h_yslot.data(), sizeof(int16_t) * h_yslot.size())) != MLS_OK) return st;
+  if ((st = up((void**)&B.hn_row, h_hn_row.data(), sizeof(int) * (m + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&B.hn, h_hn.data(), sizeof(int) * nbk)) != MLS_OK) return st;
+  if ((st = up((void**)&B.ent_ptr, h_ent_ptr.data(), sizeof(int) * (nbk + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&B.ent_y, h_ent_y.data(), sizeof(int) * nent)) != MLS_OK) return st;
+  if ((st = up((void**)&B.ent_v, h_ent_v.data(), sizeof(int) * nent)) != MLS_OK) return st;
+  if ((st = up((void**)&B.ent_phi, h_ent_phi.data(), sizeof(double) * nent)) != MLS_OK) return st;
+  B.m = m;
+  B.nnz = nz;
+  B.ny = ny;
+  B.maxk = std::max(maxk, 1);
+  B.nb = nbk;
+  B.nent = (int64_t)nent;
+  B.h_hrow = h_hrow;
+  B.h_vrow = h_vrow;
+  const int r = 12 * m;
+  const int vb = solve_bytes(ctx);
+  if ((st = dalloc(ctx, &ctx->yval, (size_t)ny * 36 * vb)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->Ac, (size_t)r * r * sizeof(double))) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->Acopy, (size_t)r * r * sizeof(double))) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->Linv, (size_t)r * r * vb)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->LinvT, (size_t)r * r * vb)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->cvec, (size_t)r * vb)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->cvec2, (size_t)r * vb)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->chol_info, sizeof(int) * 4)) != MLS_OK) return st;
+  ctx->has_basis = true;
+  ctx->coarse_ready = false;
+  return MLS_OK;
+}
+
+// ---- prolongation / restriction ---------------------------------------------------------
+struct BasisView {
+  int n, m;
+  const int* __restrict__ vrow;
+  const int* __restrict__ vh;
+  const double* __restrict__ vphi;
+  const int* __restrict__ hrow;
+  const int* __restrict__ hv;
+  const double* __restrict__ hphi;
+  const double* __restrict__ origins;
+  const Vec4d* __restrict__ X;
+};
+
+// w_v = [acc ? w_v : 0] + sum_j phi_j(v) (I_3 (x) a_vj^T) q_j  (+ omega D^-1 s_v)
+// (q may be null: then only the base and smoothing terms are applied; base
+// and w may alias, each thread reads its own entry before writing it)
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_prolong(BasisView B, const VT* __restrict__ q,
+                                                    const Vec4<VT>* base,
+                                                    const VT* __restrict__ dinv, const Vec4<VT>* __restrict__ s,
+                                                    VT omega, Vec4<VT>* w,
+                                                    const PcgScalars* __restrict__ S) {
+  if (S && S->done) return;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= B.n) return;
+  const Vec4d X = B.X[v];
+  VT o0 = VT(0), o1 = VT(0), o2 = VT(0);
+  if (q) for (int k = B.vrow[v]; k < B.vrow[v + 1]; ++k) {
+    const int j = B.vh[k];
+    const VT ph = (VT)B.vphi[k];
+    const VT a1 = (VT)(X.x - B.origins[3 * j]), a2 = (VT)(X.y - B.origins[3 * j + 1]),
+             a3 = (VT)(X.z - B.origins[3 * j + 2]);
+    const VT* qj = q + 12 * (int64_t)j;
+    o0 += ph * (qj[0] + a1 * qj[1] + a2 * qj[2] + a3 * qj[3]);
+    o1 += ph * (qj[4] + a1 * qj[5] + a2 * qj[6] + a3 * qj[7]);
+    o2 += ph * (qj[8] + a1 * qj[9] + a2 * qj[10] + a3 * qj[11]);
+  }
+  if (base) {
+    const Vec4<VT> b = base[v];
+    o0 += b.x; o1 += b.y; o2 += b.z;
+  }
+  if (s) {
+    const Vec4<VT> sv = s[v];
+    const VT* D = dinv + (int64_t)v * 9;
+    o0 += omega * (D[0] * sv.x + D[1] * sv.y + D[2] * sv.z);
+    o1 += omega * (D[3] * sv.x + D[4] * sv.y + D[5] * sv.z);
+    o2 += omega * (D[6] * sv.x + D[7] * sv.y + D[8] * sv.z);
+  }
+  w[v] = Vec4<VT>{o0, o1, o2, VT(0)};
+}
+
+// z_j = sum_{v in supp j} phi_j(v) r_v (x) a_vj : one CTA per handle
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_restrict(BasisView B, const Vec4<VT>* __restrict__ r,
+                                                     VT* __restrict__ z, const PcgScalars* __restrict__ S) {
+  if (S && S->done) return;
+  const int j = blockIdx.x;
+  const double ox = B.origins[3 * j], oy = B.origins[3 * j + 1], oz = B.origins[3 * j + 2];
+  VT acc[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) acc[q] = VT(0);
+  for (int p = B.hrow[j] + threadIdx.x; p < B.hrow[j + 1]; p += blockDim.x) {
+    const int v = B.hv[p];
+    const VT ph = (VT)B.hphi[p];
+    const Vec4d X = B.X[v];
+    const VT a[4] = {VT(1), (VT)(X.x - ox), (VT)(X.y - oy), (VT)(X.z - oz)};
+    const Vec4<VT> rv = r[v];
+    const VT rc[3] = {ph * rv.x, ph * rv.y, ph * rv.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) acc[4 * c + l] += rc[c] * a[l];
+  }
+  __shared__ VT sh[12][kBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {
+    VT s = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[q][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 12) {
+    VT s = VT(0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[threadIdx.x][w];
+    z[12 * (int64_t)j + threadIdx.x] = s;
+  }
+}
+
+// ---- Galerkin: Y = H U ----------------------------------------------------------------
+struct GalerkinView {
+  int n;
+  const int* __restrict__ slice_ptr;
+  const int* __restrict__ col;
+  const int* __restrict__ row_len;
+  const int* __restrict__ yrow;
+  const int* __restrict__ yh;
+  const int16_t* __restrict__ yslot;
+  int maxk;
+};
+
+// one thread per (v, local handle q of K_v); Y stored [ny][36]
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kBlock) k_galerkin_y(BasisView B, GalerkinView G, const MT* __restrict__ val,
+                                                       const int* __restrict__ ypair_row, int64_t ny,
+                                                       VT* __restrict__ Y) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ny) return;
+  const int v = ypair_row[idx];
+  const int q = (int)(idx - G.yrow[v]);
+  const int j = G.yh[idx];
+  const double ox = B.origins[3 * j], oy = B.origins[3 * j + 1], oz = B.origins[3 * j + 2];
+  VT acc[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) acc[k] = VT(0);
+  const int slice = v >> 5, lane = v & 31;
+  const int g0 = G.slice_ptr[slice];
+  const int len = G.row_len[v];
+  for (int k = 0; k < len; ++k) {
+    const int64_t slot = ((int64_t)g0 + k) * 32 + lane;
+    const int w = G.col[slot];
+    const int kb = B.vrow[w], ke = B.vrow[w + 1];
+    for (int e = kb; e < ke; ++e) {
+      if (G.yslot[slot * G.maxk + (e - kb)] != q) continue;
+      const Vec4d Xw = B.X[w];
+      const VT ph = (VT)B.vphi[e];
+      const VT a[4] = {ph, ph * (VT)(Xw.x - ox), ph * (VT)(Xw.y - oy), ph * (VT)(Xw.z - oz)};
+      const MT* hv = val + ((int64_t)g0 + k) * 288 + lane;
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const VT h = load_as<VT>(hv[(3 * c + d) * 32]);
+#pragma unroll
+          for (int l = 0; l < 4; ++l) acc[(3 * c + d) * 4 + l] += h * a[l];
+        }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 36; ++k) Y[idx * 36 + k] = acc[k];
+}
+
+// A_ij (12x12) = sum over entries (v, y) of phi_i(v) a_vi (x) Y_y ; one CTA per
+// coarse block row i, 144 threads per neighbour block, several blocks at once.
+template <typename VT>
+__global__ void __launch_bounds__(288) k_galerkin_a(BasisView B, const int* __restrict__ hn_row,
+                                                    const int* __restrict__ hn, const int* __restrict__ ent_ptr,
+                                                    const int* __restrict__ ent_y, const int* __restrict__ ent_v,
+                                                    const double* __restrict__ ent_phi, int64_t ny,
+                                                    const VT* __restrict__ Y, int r, double* __restrict__ A) {
+  const int i = blockIdx.x;
+  const int team = threadIdx.x / 144, tt = threadIdx.x % 144;
+  const int row = tt / 12, colq = tt % 12;  // output (row, col) inside the 12x12 block
+  const int c = row >> 2, lp = row & 3;      // row = 4 c + l'
+  const int d = colq >> 2, l = colq & 3;     // col = 4 d + l
+  const double ox = B.origins[3 * i], oy = B.origins[3 * i + 1], oz = B.origins[3 * i + 2];
+  const int yk = (3 * c + d) * 4 + l;        // component of Y_vj
+  for (int s = hn_row[i] + team; s < hn_row[i + 1]; s += 2) {
+    const int j = hn[s];
+    VT acc = VT(0);
+    for (int p = ent_ptr[s]; p < ent_ptr[s + 1]; ++p) {
+      const int v = ent_v[p];
+      VT coef = (VT)ent_phi[p];
+      if (lp > 0) {
+        const Vec4d X = B.X[v];
+        coef *= (VT)(lp == 1 ? X.x - ox : lp == 2 ? X.y - oy : X.z - oz);
+      }
+      acc += coef * Y[(int64_t)ent_y[p] * 36 + yk];
+    }
+    A[(int64_t)(12 * i + row) * r + 12 * j + colq] = (double)acc;
+  }
+}
+
+// ---- dense Cholesky (float64), blocked right-looking ---------------------------------------
+constexpr int NB = 32;
+
+// factor the diagonal tile (k, k) in place; one CTA of 32x32 threads
+__global__ void k_potrf_tile(double* __restrict__ A, int r, int k, int* __restrict__ info) {
+  __shared__ double T[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int base = k * NB;
+  const int nr = min(NB, r - base);
+  if (ty < nr && tx < nr) T[ty][tx] = A[(int64_t)(base + ty) * r + base + tx];
+  __syncthreads();
+  for (int p = 0; p < nr; ++p) {
+    if (tx == 0 && ty == 0) {
+      const double d = T[p][p];
+      if (!(d > 0.0)) {
+        if (*info == 0) *info = base + p + 1;
+        T[p][p] = 1.0;
+      } else {
+        T[p][p] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (tx == 0 && ty > p && ty < nr) T[ty][p] /= T[p][p];
+    __syncthreads();
+    if (ty > p && tx > p && tx <= ty && ty < nr) T[ty][tx] -= T[ty][p] * T[tx][p];
+    __syncthreads();
+  }
+  if (ty < nr && tx < nr) A[(int64_t)(base + ty) * r + base + tx] = (tx <= ty) ? T[ty][tx] : 0.0;
+}
+
+// L_ik = A_ik L_kk^{-T} for tiles i > k; one CTA (32x32 threads) per tile row i
+__global__ void k_trsm_tiles(double* __restrict__ A, int r, int k) {
+  __shared__ double Lk[NB][NB + 1];
+  __shared__ double X[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = k + 1 + blockIdx.x;
+  const int bk = k * NB, bi = i * NB;
+  const int nk = min(NB, r - bk), ni = min(NB, r - bi);
+  if (ty < nk && tx < nk) Lk[ty][tx] = A[(int64_t)(bk + ty) * r + bk + tx];
+  if (ty < ni && tx < nk) X[ty][tx] = A[(int64_t)(bi + ty) * r + bk + tx];
+  __syncthreads();
+  // solve X L^T = B row by row: X[row][c] = (B[row][c] - sum_{q<c} X[row][q] L[c][q]) / L[c][c]
+  if (tx == 0 && ty < ni) {
+    for (int c = 0; c < nk; ++c) {
+      double s = X[ty][c];
+      for (int q = 0; q < c; ++q) s -= X[ty][q] * Lk[c][q];
+      X[ty][c] = s / Lk[c][c];
+    }
+  }
+  __syncthreads();
+  if (ty < ni && tx < nk) A[(int64_t)(bi + ty) * r + bk + tx] = X[ty][tx];
+}
+
+// A_ij -= L_ik L_jk^T for k < j <= i (lower triangle of the trailing matrix);
+// one CTA (32x8 threads, 4 outputs each) per tile pair
+__global__ void k_syrk_tiles(double* __restrict__ A, int r, int k, int ntiles) {
+  // map blockIdx.x to (i, j) with k < j <= i < ntiles
+  const int m = ntiles - k - 1;
+  int idx = blockIdx.x;
+  int jj = 0;
+  while (idx >= m - jj) { idx -= m - jj; ++jj; }
+  const int j = k + 1 + jj;
+  const int i = j + idx;
+  __shared__ double Li[NB][NB + 1];
+  __shared__ double Lj[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int bk = k * NB, bi = i * NB, bj = j * NB;
+  const int nk = min(NB, r - bk), ni = min(NB, r - bi), nj = min(NB, r - bj);
+  for (int rr = ty; rr < NB; rr += 8) {
+    Li[rr][tx] = (rr < ni && tx < nk) ? A[(int64_t)(bi + rr) * r + bk + tx] : 0.0;
+    Lj[rr][tx] = (rr < nj && tx < nk) ? A[(int64_t)(bj + rr) * r + bk + tx] : 0.0;
+  }
+  __syncthreads();
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = 0; q < NB; ++q) {
+    const double b = Lj[tx][q];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += Li[ty + 8 * u][q] * b;
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = ty + 8 * u;
+    if (rr < ni && tx < nj) A[(int64_t)(bi + rr) * r + bj + tx] -= acc[u];
+  }
+}
+
+// W = L^{-1} column block by column block: for tile column k,
+// W_kk = L_kk^{-1}; W_ik = -L_ii^{-1} sum_{k<=q<i} L_iq W_qk, tile rows in order.
+// One CTA (32x32 threads) per tile column, walking down its tile rows.
+template <typename VT>
+__global__ void k_trinv_column(const double* __restrict__ L, int r, int ntiles, VT* __restrict__ W,
+                               VT* __restrict__ WT) {
+  const int k = blockIdx.x;
+  __shared__ double Lii[NB][NB + 1];
+  __shared__ double Acc[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int bk = k * NB;
+  const int nk = min(NB, r - bk);
+  for (int i = k; i < ntiles; ++i) {
+    const int bi = i * NB;
+    const int ni = min(NB, r - bi);
+    // Acc = (i == k) ? I : -sum_{q=k}^{i-1} L_iq W_qk
+    VT s = VT(0);
+    if (i == k) {
+      s = (ty == tx) ? VT(1) : VT(0);
+    } else if (ty < ni && tx < nk) {
+      const double* Lr = L + (int64_t)(bi + ty) * r;
+      for (int q = bk; q < bi; ++q) s -= (VT)Lr[q] * W[(int64_t)q * r + bk + tx];
+    }
+    Acc[ty][tx] = (double)s;
+    Lii[ty][tx] = (ty < ni && tx < ni) ? L[(int64_t)(bi + ty) * r + bi + tx] : (ty == tx ? 1.0 : 0.0);
+    __syncthreads();
+    // solve L_ii X = Acc by forward substitution, one thread per column
+    if (ty == 0 && tx < nk) {
+      for (int rr = 0; rr < ni; ++rr) {
+        double v = Acc[rr][tx];
+        for (int q = 0; q < rr; ++q) v -= Lii[rr][q] * Acc[q][tx];
+        Acc[rr][tx] = v / Lii[rr][rr];
+      }
+    }
+    __syncthreads();
+    if (ty < ni && tx < nk) {
+      const VT w = (VT)Acc[ty][tx];
+      W[(int64_t)(bi + ty) * r + bk + tx] = w;
+      WT[(int64_t)(bk + tx) * r + bi + ty] = w;
+    }
+    __syncthreads();
+  }
+}
+
+// y = W x restricted to the lower (lower = 1: columns <= row) or upper
+// (lower = 0: columns >= row) triangle; one warp per row
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_trigemv(const VT* __restrict__ W, int r, int lower,
+                                                    const VT* __restrict__ x, VT* __restrict__ y,
+                                                    const PcgScalars* __restrict__ S) {
+  if (S && S->done) return;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= r) return;
+  const int c0 = lower ? 0 : row, c1 = lower ? row + 1 : r;
+  const VT* Wr = W + (int64_t)row * r;
+  VT acc = VT(0);
+  for (int c = c0 + lane; c < c1; c += 32) acc += Wr[c] * x[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) y[row] = acc;
+}
+
+__global__ void k_ypair_rows(int n, const int* __restrict__ yrow, int* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  for (int k = yrow[v]; k < yrow[v + 1]; ++k) out[k] = v;
+}
+
+// ---- host drivers --------------------------------------------------------------------------
+static BasisView basis_view(mls_ctx* ctx) {
+  const Basis& B = ctx->basis;
+  return BasisView{ctx->n, B.m, B.vrow, B.vh, B.vphi, B.hrow, B.hv, B.hphi, B.origins, ctx->X};
+}
+
+mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate) {
+  if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
+  if (ctx->opt.precision == MLS_FP64)
+    k_prolong<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const double*)q,
+        accumulate ? (const Vec4d*)w : nullptr, nullptr, nullptr, 0.0, (Vec4d*)w, nullptr);
+  else
+    k_prolong<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const float*)q,
+        accumulate ? (const Vec4f*)w : nullptr, nullptr, nullptr, 0.0f, (Vec4f*)w, nullptr);
+  return cuda_check(ctx, cudaGetLastError(), "k_prolong");
+}
+
+mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q) {
+  if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
+  if (ctx->opt.precision == MLS_FP64)
+    k_restrict<double><<<ctx->basis.m, kBlock, 0, ctx->stream>>>(basis_view(ctx), (const Vec4d*)r, (double*)q, nullptr);
+  else
+    k_restrict<float><<<ctx->basis.m, kBlock, 0, ctx->stream>>>(basis_view(ctx), (const Vec4f*)r, (float*)q, nullptr);
+  return cuda_check(ctx, cudaGetLastError(), "k_restrict");
+}
+
+template <typename VT, typename MT>
+static mls_status galerkin_t(mls_ctx* ctx) {
+  Basis& B = ctx->basis;
+  const int r = 12 * B.m;
+  GalerkinView G{ctx->n, ctx->slice_ptr, ctx->col, ctx->row_len, B.yrow, B.yh, B.yslot, B.maxk};
+  if (!B.ypair_row) {
+    mls_status st = dalloc(ctx, (void**)&B.ypair_row, sizeof(int) * std::max<int64_t>(B.ny, 1));
+    if (st != MLS_OK) return st;
+    k_ypair_rows<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, B.yrow, B.ypair_row);
+  }
+  k_galerkin_y<VT, MT><<<nblk(B.ny), kBlock, 0, ctx->stream>>>(basis_view(ctx), G, (const MT*)ctx->hval,
+                                                               B.ypair_row, B.ny, (VT*)ctx->yval);
+  mls_status st = cuda_check(ctx, cudaMemsetAsync(ctx->Ac, 0, sizeof(double) * r * r, ctx->stream), "Ac clear");
+  if (st != MLS_OK) return st;
+  k_galerkin_a<VT><<<B.m, 288, 0, ctx->stream>>>(basis_view(ctx), B.hn_row, B.hn, B.ent_ptr, B.ent_y, B.ent_v,
+                                                 B.ent_phi, B.ny, (const VT*)ctx->yval, r, ctx->Ac);
+  return cuda_check(ctx, cudaGetLastError(), "galerkin");
+}
+
+template <typename VT>
+static mls_status factor_t(mls_ctx* ctx) {
+  const int r = 12 * ctx->basis.m;
+  const int nt = (r + NB - 1) / NB;
+  mls_status st = cuda_check(ctx, cudaMemcpyAsync(ctx->Acopy, ctx->Ac, sizeof(double) * r * r,
+                                                  cudaMemcpyDeviceToDevice, ctx->stream), "Ac copy");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemsetAsync(ctx->chol_info, 0, sizeof(int), ctx->stream), "info clear");
+  if (st != MLS_OK) return st;
+  // symmetrise from the lower triangle is implicit: only the lower triangle is read
+  for (int k = 0; k < nt; ++k) {
+    k_potrf_tile<<<1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, k, ctx->chol_info);
+    if (k + 1 < nt) {
+      k_trsm_tiles<<<nt - k - 1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, k);
+      const int m = nt - k - 1;
+      k_syrk_tiles<<<m * (m + 1) / 2, dim3(32, 8), 0, ctx->stream>>>(ctx->Ac, r, k, nt);
+    }
+  }
+  st = cuda_check(ctx, cudaGetLastError(), "cholesky");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemsetAsync(ctx->Linv, 0, (size_t)r * r * sizeof(VT), ctx->stream), "W clear");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemsetAsync(ctx->LinvT, 0, (size_t)r * r * sizeof(VT), ctx->stream), "WT clear");
+  if (st != MLS_OK) return st;
+  k_trinv_column<VT><<<nt, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, nt, (VT*)ctx->Linv, (VT*)ctx->LinvT);
+  st = cuda_check(ctx, cudaGetLastError(), "triangular inverse");
+  if (st != MLS_OK) return st;
+  int info = 0;
+  st = cuda_check(ctx, cudaMemcpyAsync(&ctx->dscal_host[12], ctx->chol_info, sizeof(int),
+                                       cudaMemcpyDeviceToHost, ctx->stream), "info readback");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cholesky sync");
+  if (st != MLS_OK) return st;
+  memcpy(&info, &ctx->dscal_host[12], sizeof(int));
+  if (info != 0) {
+    ctx->coarse_ready = false;
+    return fail(ctx, MLS_ECHOL, "coarse operator is not positive definite (pivot " + std::to_string(info - 1) + ")");
+  }
+  ctx->coarse_ready = true;
+  return MLS_OK;
+}
+
+mls_status build_coarse(mls_ctx* ctx) {
+  if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
+  if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "assemble H before building the coarse operator");
+  mls_status st;
+  switch (ctx->opt.precision) {
+    case MLS_FP64: st = galerkin_t<double, double>(ctx); break;
+    case MLS_MIXED_FP32: st = galerkin_t<float, float>(ctx); break;
+    default: st = galerkin_t<float, __nv_bfloat16>(ctx); break;
+  }
+  if (st != MLS_OK) return st;
+  return ctx->opt.precision == MLS_FP64 ? factor_t<double>(ctx) : factor_t<float>(ctx);
+}
+
+template <typename VT>
+static mls_status coarse_apply_t(mls_ctx* ctx, const VT* c_in, VT* c_out, const PcgScalars* S) {
+  const int r = 12 * ctx->basis.m;
+  const int rows_per_block = kBlock / 32;
+  const int nb = (r + rows_per_block - 1) / rows_per_block;
+  k_trigemv<VT><<<nb, kBlock, 0, ctx->stream>>>((const VT*)ctx->Linv, r, 1, c_in, (VT*)ctx->cvec2, S);
+  k_trigemv<VT><<<nb, kBlock, 0, ctx->stream>>>((const VT*)ctx->LinvT, r, 0, (const VT*)ctx->cvec2, c_out, S);
+  return cuda_check(ctx, cudaGetLastError(), "coarse apply");
+}
+
+mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out) {
+  if (!ctx->coarse_ready) return fail(ctx, MLS_EINVAL, "coarse operator not built");
+  if (ctx->opt.precision == MLS_FP64) return coarse_apply_t<double>(ctx, (const double*)c_in, (double*)c_out, nullptr);
+  return coarse_apply_t<float>(ctx, (const float*)c_in, (float*)c_out, nullptr);
+}
+
+template <typename VT>
+static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, const PcgScalars* S) {
+  const BasisView BV = basis_view(ctx);
+  const VT omega = (VT)ctx->opt.omega;
+  const int m = ctx->basis.m;
+  VT* c = (VT*)ctx->cvec;
+  const VT* dinv = (const VT*)ctx->dinv;
+  if (ctx->opt.cycle == MLS_CYCLE_ADDITIVE) {
+    k_restrict<VT><<<m, kBlock, 0, ctx->stream>>>(BV, r, c, S);
+    mls_status st = coarse_apply_t<VT>(ctx, c, c, S);
+    if (st != MLS_OK) return st;
+    k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, nullptr, dinv, r, omega, z, S);
+    return cuda_check(ctx, cudaGetLastError(), "two-level additive");
+  }
+  // multiplicative: z1 = S r; t = r - H z1; z2 = z1 + Q t; t = r - H z2; z = z2 + S t
+  Vec4<VT>* tmp = (Vec4<VT>*)ctx->vw;
+  mls_status st = launch_jacobi(ctx, r, z, ctx->opt.omega, S);
+  if (st != MLS_OK) return st;
+  if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
+  k_restrict<VT><<<m, kBlock, 0, ctx->stream>>>(BV, tmp, c, S);
+  if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
+  k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, z, nullptr, nullptr, omega, z, S);
+  if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
+  k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, nullptr, z, dinv, tmp, omega, z, S);
+  return cuda_check(ctx, cudaGetLastError(), "two-level multiplicative");
+}
+
+mls_status precond_apply_dev(mls_ctx* ctx, const void* r, void* z, const PcgScalars* S) {
+  if (ctx->opt.preconditioner == MLS_PRECOND_BLOCK_JACOBI) return launch_jacobi(ctx, r, z, 1.0, S);
+  if (!ctx->coarse_ready) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs the coarse operator");
+  if (ctx->opt.precision == MLS_FP64) return two_level_t<double>(ctx, (const Vec4d*)r, (Vec4d*)z, S);
+  return two_level_t<float>(ctx, (const Vec4f*)r, (Vec4f*)z, S);
+}
+
+}  // namespace mls

@@ -1,0 +1,325 @@
+// Sparse matrix-vector product with the SELL-32 block matrix H and the
+// preconditioned conjugate gradient loop on it (the Newton linear solve
+// H d = -g of Eq. 5, preconditioned as in Sec. 3.7).
+//
+// PCG runs entirely on the device: the scalars alpha, beta, r.z, |r|^2 live in
+// device memory and are produced by the last block of each reduction, so one
+// iteration is two (block Jacobi) or more (two-level) kernel launches with no
+// host round trip.  The direction update p = z + beta p is folded into the
+// product kernel through q = H p = H z + beta q_old, so the kernel that reads
+// neighbours (the product) needs only z, which is complete when it starts.
+// Dot products and norms accumulate in float64 in every precision mode.
+#include "mls_internal.cuh"
+
+namespace mls {
+
+struct SellView {
+  int n;
+  const int* __restrict__ slice_ptr;
+  const int* __restrict__ col;
+  const int* __restrict__ row_len;
+};
+
+template <typename VT, typename MT>
+__device__ __forceinline__ void spmv_row(const SellView& A, const MT* __restrict__ val, int row,
+                                         const Vec4<VT>* __restrict__ x, VT (&y)[3]) {
+  const int slice = row >> 5, lane = row & 31;
+  const int g0 = A.slice_ptr[slice];
+  const int len = A.row_len[row];
+  VT y0 = VT(0), y1 = VT(0), y2 = VT(0);
+  for (int k = 0; k < len; ++k) {
+    const int64_t g = g0 + k;
+    const int c = A.col[g * 32 + lane];
+    const Vec4<VT> xv = x[c];
+    const MT* v = val + g * 288 + lane;
+    y0 += load_as<VT>(v[0]) * xv.x + load_as<VT>(v[32]) * xv.y + load_as<VT>(v[64]) * xv.z;
+    y1 += load_as<VT>(v[96]) * xv.x + load_as<VT>(v[128]) * xv.y + load_as<VT>(v[160]) * xv.z;
+    y2 += load_as<VT>(v[192]) * xv.x + load_as<VT>(v[224]) * xv.y + load_as<VT>(v[256]) * xv.z;
+  }
+  y[0] = y0; y[1] = y1; y[2] = y2;
+}
+
+template <typename VT>
+__device__ __forceinline__ Vec4<VT> dinv_apply(const VT* __restrict__ dinv, int row, const Vec4<VT>& r, VT omega) {
+  const VT* D = dinv + (int64_t)row * 9;
+  return Vec4<VT>{omega * (D[0] * r.x + D[1] * r.y + D[2] * r.z),
+                  omega * (D[3] * r.x + D[4] * r.y + D[5] * r.z),
+                  omega * (D[6] * r.x + D[7] * r.y + D[8] * r.z), VT(0)};
+}
+
+// ---- plain product / residual ---------------------------------------------------------
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kBlock) k_spmv(SellView A, const MT* __restrict__ val,
+                                                 const Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ y) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= A.n) return;
+  VT r[3];
+  spmv_row<VT, MT>(A, val, row, x, r);
+  y[row] = Vec4<VT>{r[0], r[1], r[2], VT(0)};
+}
+
+// out = b - H x
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kBlock) k_residual(SellView A, const MT* __restrict__ val,
+                                                     const Vec4<VT>* __restrict__ b,
+                                                     const Vec4<VT>* __restrict__ x,
+                                                     Vec4<VT>* __restrict__ out,
+                                                     const PcgScalars* __restrict__ S) {
+  if (S && S->done) return;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= A.n) return;
+  VT r[3];
+  spmv_row<VT, MT>(A, val, row, x, r);
+  const Vec4<VT> bb = b[row];
+  out[row] = Vec4<VT>{bb.x - r[0], bb.y - r[1], bb.z - r[2], VT(0)};
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_jacobi(int n, const VT* __restrict__ dinv,
+                                                   const Vec4<VT>* __restrict__ r, Vec4<VT>* __restrict__ z,
+                                                   VT omega, const PcgScalars* __restrict__ S) {
+  if (S && S->done) return;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  z[row] = dinv_apply<VT>(dinv, row, r[row], omega);
+}
+
+// ---- PCG --------------------------------------------------------------------------------
+// init: x = 0, r = b, p = q = 0; with block Jacobi also z = D^{-1} b and r.z
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_pcg_init(int n, const Vec4<VT>* __restrict__ b, Vec4<VT>* __restrict__ x,
+                                                     Vec4<VT>* __restrict__ r, Vec4<VT>* __restrict__ z,
+                                                     Vec4<VT>* __restrict__ p, Vec4<VT>* __restrict__ q,
+                                                     const VT* __restrict__ dinv, int jacobi, double rtol,
+                                                     int max_iter, GridReduce gr, PcgScalars* __restrict__ S) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[2] = {0.0, 0.0};  // b.b, r.z
+  if (row < n) {
+    const Vec4<VT> bv = b[row];
+    const Vec4<VT> zero{VT(0), VT(0), VT(0), VT(0)};
+    x[row] = zero; p[row] = zero; q[row] = zero;
+    r[row] = bv;
+    acc[0] = (double)bv.x * bv.x + (double)bv.y * bv.y + (double)bv.z * bv.z;
+    if (jacobi) {
+      const Vec4<VT> zv = dinv_apply<VT>(dinv, row, bv, VT(1));
+      z[row] = zv;
+      acc[1] = (double)bv.x * zv.x + (double)bv.y * zv.y + (double)bv.z * zv.z;
+    }
+  }
+  if (grid_sum<2>(acc, gr, RS_PCG_RZ) && threadIdx.x == 0) {
+    S->bb = acc[0];
+    S->rr = acc[0];
+    S->rz = acc[1];
+    S->beta = 0.0;
+    S->alpha = 0.0;
+    S->pq = 0.0;
+    S->iter = 0;
+    S->max_iter = max_iter;
+    S->tol2 = rtol * rtol * acc[0];
+    S->done = (acc[0] == 0.0) ? 1 : 0;
+  }
+}
+
+// r.z after a non-local preconditioner; sets beta (0 on the first call)
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_pcg_rz(int n, const Vec4<VT>* __restrict__ r,
+                                                   const Vec4<VT>* __restrict__ z, int first, GridReduce gr,
+                                                   PcgScalars* __restrict__ S) {
+  if (S->done) return;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (row < n) {
+    const Vec4<VT> rv = r[row], zv = z[row];
+    acc[0] = (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z;
+  }
+  if (grid_sum<1>(acc, gr, RS_PCG_RZ) && threadIdx.x == 0) {
+    if (first) {
+      S->beta = 0.0;
+    } else {
+      S->beta = acc[0] / S->rz;
+    }
+    S->rz = acc[0];
+    if (!(acc[0] > 0.0) || !isfinite(acc[0])) S->done = (S->rr <= S->tol2) ? 1 : 3;
+  }
+}
+
+// w = H z; p = z + beta p; q = w + beta q; alpha = r.z / p.q
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(kBlock) k_pcg_spmv(SellView A, const MT* __restrict__ val,
+                                                     const Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p,
+                                                     Vec4<VT>* __restrict__ q, GridReduce gr,
+                                                     PcgScalars* __restrict__ S) {
+  if (S->done) return;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (row < A.n) {
+    VT w[3];
+    spmv_row<VT, MT>(A, val, row, z, w);
+    const VT beta = (VT)S->beta;
+    const Vec4<VT> zv = z[row], pv = p[row], qv = q[row];
+    const Vec4<VT> pn{zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, VT(0)};
+    const Vec4<VT> qn{w[0] + beta * qv.x, w[1] + beta * qv.y, w[2] + beta * qv.z, VT(0)};
+    p[row] = pn;
+    q[row] = qn;
+    acc[0] = (double)pn.x * qn.x + (double)pn.y * qn.y + (double)pn.z * qn.z;
+  }
+  if (grid_sum<1>(acc, gr, RS_PCG_PQ) && threadIdx.x == 0) {
+    S->pq = acc[0];
+    if (acc[0] > 0.0 && isfinite(acc[0])) {
+      S->alpha = S->rz / acc[0];
+    } else {
+      S->alpha = 0.0;
+      S->done = 3;  // breakdown: H or the preconditioner is not positive definite
+    }
+  }
+}
+
+// x += alpha p; r -= alpha q; with block Jacobi also z = D^{-1} r, r.z, beta
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_pcg_update(int n, Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r,
+                                                       Vec4<VT>* __restrict__ z, const Vec4<VT>* __restrict__ p,
+                                                       const Vec4<VT>* __restrict__ q, const VT* __restrict__ dinv,
+                                                       int jacobi, GridReduce gr, PcgScalars* __restrict__ S) {
+  if (S->done) return;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[2] = {0.0, 0.0};  // r.r, r.z
+  if (row < n) {
+    const VT alpha = (VT)S->alpha;
+    const Vec4<VT> pv = p[row], qv = q[row];
+    Vec4<VT> xv = x[row], rv = r[row];
+    xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z;
+    rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z;
+    x[row] = xv;
+    r[row] = rv;
+    acc[0] = (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z;
+    if (jacobi) {
+      const Vec4<VT> zv = dinv_apply<VT>(dinv, row, rv, VT(1));
+      z[row] = zv;
+      acc[1] = (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z;
+    }
+  }
+  if (grid_sum<2>(acc, gr, RS_PCG_RR) && threadIdx.x == 0) {
+    S->rr = acc[0];
+    S->iter += 1;
+    if (jacobi) {
+      S->beta = acc[1] / S->rz;
+      S->rz = acc[1];
+    }
+    if (!isfinite(acc[0])) S->done = 3;
+    else if (acc[0] <= S->tol2) S->done = 1;
+    else if (S->iter >= S->max_iter) S->done = 2;
+  }
+}
+
+// ---- launchers ---------------------------------------------------------------------------
+static SellView sell_view(mls_ctx* ctx) { return SellView{ctx->n, ctx->slice_ptr, ctx->col, ctx->row_len}; }
+static inline int nblk(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
+
+template <typename VT, typename MT>
+static void spmv_t(mls_ctx* ctx, const void* x, void* y) {
+  k_spmv<VT, MT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
+                                                           (const Vec4<VT>*)x, (Vec4<VT>*)y);
+}
+
+mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y) {
+  switch (ctx->opt.precision) {
+    case MLS_FP64: spmv_t<double, double>(ctx, x, y); break;
+    case MLS_MIXED_FP32: spmv_t<float, float>(ctx, x, y); break;
+    default: spmv_t<float, __nv_bfloat16>(ctx, x, y); break;
+  }
+  return cuda_check(ctx, cudaGetLastError(), "k_spmv");
+}
+
+template <typename VT, typename MT>
+mls_status launch_residual_t(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S) {
+  k_residual<VT, MT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
+                                                               (const Vec4<VT>*)b, (const Vec4<VT>*)x,
+                                                               (Vec4<VT>*)out, S);
+  return cuda_check(ctx, cudaGetLastError(), "k_residual");
+}
+
+mls_status launch_residual(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S) {
+  switch (ctx->opt.precision) {
+    case MLS_FP64: return launch_residual_t<double, double>(ctx, b, x, out, S);
+    case MLS_MIXED_FP32: return launch_residual_t<float, float>(ctx, b, x, out, S);
+    default: return launch_residual_t<float, __nv_bfloat16>(ctx, b, x, out, S);
+  }
+}
+
+mls_status launch_jacobi(mls_ctx* ctx, const void* r, void* z, double omega, const PcgScalars* S) {
+  if (ctx->opt.precision == MLS_FP64)
+    k_jacobi<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const double*)ctx->dinv,
+                                                               (const Vec4d*)r, (Vec4d*)z, omega, S);
+  else
+    k_jacobi<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const float*)ctx->dinv,
+                                                              (const Vec4f*)r, (Vec4f*)z, (float)omega, S);
+  return cuda_check(ctx, cudaGetLastError(), "k_jacobi");
+}
+
+mls_status precond_apply_dev(mls_ctx* ctx, const void* r, void* z, const PcgScalars* S);
+
+template <typename VT, typename MT>
+static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res) {
+  const int n = ctx->n;
+  const int nb = nblk(n);
+  if (nb > kMaxPartials) return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
+  const bool jacobi = ctx->opt.preconditioner == MLS_PRECOND_BLOCK_JACOBI;
+  if (!jacobi && !ctx->coarse_ready) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_build_coarse");
+  auto* b = (const Vec4<VT>*)ctx->vb;
+  auto* x = (Vec4<VT>*)ctx->vx;
+  auto* r = (Vec4<VT>*)ctx->vr;
+  auto* z = (Vec4<VT>*)ctx->vz;
+  auto* p = (Vec4<VT>*)ctx->vp;
+  auto* q = (Vec4<VT>*)ctx->vq;
+  const VT* dinv = (const VT*)ctx->dinv;
+  PcgScalars* S = ctx->pcg;
+  SellView A = sell_view(ctx);
+  const MT* val = (const MT*)ctx->hval;
+  k_pcg_init<VT><<<nb, kBlock, 0, ctx->stream>>>(n, b, x, r, z, p, q, dinv, jacobi ? 1 : 0, rtol, max_iter,
+                                                 ctx->red, S);
+  mls_status st = cuda_check(ctx, cudaGetLastError(), "k_pcg_init");
+  if (st != MLS_OK) return st;
+  if (!jacobi) {
+    st = precond_apply_dev(ctx, r, z, S);
+    if (st != MLS_OK) return st;
+    k_pcg_rz<VT><<<nb, kBlock, 0, ctx->stream>>>(n, r, z, 1, ctx->red, S);
+  }
+  const int chunk = ctx->opt.pcg_check_every > 0 ? ctx->opt.pcg_check_every : 16;
+  for (;;) {
+    for (int c = 0; c < chunk; ++c) {
+      k_pcg_spmv<VT, MT><<<nb, kBlock, 0, ctx->stream>>>(A, val, z, p, q, ctx->red, S);
+      k_pcg_update<VT><<<nb, kBlock, 0, ctx->stream>>>(n, x, r, z, p, q, dinv, jacobi ? 1 : 0, ctx->red, S);
+      if (!jacobi) {
+        st = precond_apply_dev(ctx, r, z, S);
+        if (st != MLS_OK) return st;
+        k_pcg_rz<VT><<<nb, kBlock, 0, ctx->stream>>>(n, r, z, 0, ctx->red, S);
+      }
+    }
+    st = cuda_check(ctx, cudaGetLastError(), "pcg iteration");
+    if (st != MLS_OK) return st;
+    st = cuda_check(ctx, cudaMemcpyAsync(ctx->pcg_host, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
+                                         ctx->stream), "pcg readback");
+    if (st != MLS_OK) return st;
+    st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "pcg sync");
+    if (st != MLS_OK) return st;
+    if (ctx->pcg_host->done) break;
+  }
+  const PcgScalars& h = *ctx->pcg_host;
+  if (iters) *iters = h.iter;
+  if (rel_res) *rel_res = h.bb > 0 ? sqrt(h.rr / h.bb) : 0.0;
+  if (h.done == 3) return fail(ctx, MLS_ENONFINITE, "PCG breakdown (non-positive curvature or non-finite value)");
+  if (h.done == 2) return fail(ctx, MLS_ENOTCONV, "PCG reached its iteration cap");
+  return MLS_OK;
+}
+
+mls_status pcg_solve(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res) {
+  switch (ctx->opt.precision) {
+    case MLS_FP64: return pcg_t<double, double>(ctx, rtol, max_iter, iters, rel_res);
+    case MLS_MIXED_FP32: return pcg_t<float, float>(ctx, rtol, max_iter, iters, rel_res);
+    default: return pcg_t<float, __nv_bfloat16>(ctx, rtol, max_iter, iters, rel_res);
+  }
+}
+
+mls_status precond_apply(mls_ctx* ctx, const void* r, void* z) { return precond_apply_dev(ctx, r, z, nullptr); }
+
+}  // namespace mls
