@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Timesteps per second of the multilevel elastodynamics timestep on GB300.
+
+One "step" is one implicit-Euler timestep of the whole scene: the complete
+Newton loop (element evaluation, assembly, Galerkin coarse operator and its
+Cholesky, preconditioned CG, filtered line search) until the Newton step
+tolerance is met.  The workload is the seeded random voxel lattice (41^3
+grid, p = 0.55, largest component: 224,226 tets, 72,931 vertices) dropped
+at 1 m/s from 0.05 m onto a ground plane with the point-plane barrier; it
+reaches the plane during the third step, and warm-up steps advance the same
+trajectory, so the timed steps are in contact.
+
+Arms:
+  ours (default)     mixed precision (FP32 H and PCG, FP64 gradient, norms,
+                     energies and coarse Cholesky) with the two-level
+                     preconditioner built from the SMS basis.  Also reported:
+                     the plain FP64 block-Jacobi PCG path on the same state,
+                     the per-step displacement error between the two, the
+                     end-to-end rate through the host-pointer entry point, the
+                     dominant kernel's roofline and the oracle's CPU rate.
+  --impl reference   the FP64 CPU oracle timed on the host cores on a bounded
+                     sample of the same workload (see cpu_sample()).
+
+Multi-GPU: the timestep does not shard across GPUs here, so N > 1 runs N
+independent replicas (one per rank) and reports their summed rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# iteration counts of the FP64 block-Jacobi GPU path on this workload, used to
+# scale the oracle sample in the reference arm (the main arm measures them live)
+REF_NEWTON = 4
+REF_PCG = 1000
+METRIC = "timesteps/s at 220K tets: plain FP64 vs mixed+learned PCG at 1e-4 disp error"
+UNIT = "timesteps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=41, help="lattice grid size (41: ~224K tets, 48: ~360K)")
+    ap.add_argument("--handles", type=int, default=160)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--cycle", default="additive", choices=["additive", "multiplicative"])
+    ap.add_argument("--coarse-refresh", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=2, help="plain FP64 steps timed for comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def workload(grid):
+    import synth
+    return synth.lattice_scene(n=grid, seed=3, v_down=1.0)
+
+
+def cpu_sample(scene, newton_iters, pcg_iters_per_newton, cg_sample=60):
+    """Time the oracle on the host cores on a bounded sample of one timestep:
+    at the start state, one full evaluation of E, its gradient and its
+    PSD-projected Hessian, plus ``cg_sample`` iterations of the oracle's
+    Jacobi-PCG (its full-size linear solver).  The timestep estimate is
+    newton_iters x (evaluation + pcg_iters_per_newton x one CG iteration), with
+    both counts taken from the FP64 block-Jacobi GPU path on the same step
+    (the same algorithm, so the same iteration counts).  A direct sparse
+    factorisation of the full-size Hessian does not finish in minutes, so it
+    is not the sample.  Returns (timesteps/s, description, seconds spent)."""
+    from oracle import ip, newton, pcg
+    t0 = time.perf_counter()
+    p = ip.Problem(scene)
+    x = newton.initial_guess(p)
+    ta = time.perf_counter()
+    p.energy(x)
+    g = p.gradient(x)
+    H = p.hessian(x)
+    tb = time.perf_counter()
+    diag = H.diagonal()
+    _, info = pcg.pcg(lambda v: H @ v, -g.ravel(), lambda r: r / diag, rtol=1e-30, max_iter=cg_sample)
+    tc = time.perf_counter()
+    t_eval = tb - ta
+    t_cg = (tc - tb) / max(info["iters"], 1)
+    step_s = newton_iters * (t_eval + pcg_iters_per_newton * t_cg)
+    desc = (f"oracle on the full {scene.n_tets}-tet lattice at the start state: E, gradient and "
+            f"projected Hessian {t_eval:.2f}s, {info['iters']} Jacobi-PCG iterations at {t_cg * 1e3:.1f} ms each; "
+            f"timestep = {newton_iters} Newton x (evaluation + {pcg_iters_per_newton:.0f} CG iterations), "
+            f"counts from the FP64 block-Jacobi GPU path on the same step")
+    return 1.0 / step_s, desc, time.perf_counter() - t0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.samples = []
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 2 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 2 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def spmv_bytes(solver_meta, precision):
+    """Algorithmic bytes of one launch of the PCG product kernel: H's blocks
+    (9 values + a 4-byte column index each), the row lengths, z read once and
+    p, q each read and written (3 components per vertex)."""
+    nnzb, n = solver_meta["nnzb"], solver_meta["n"]
+    sv = 8 if precision == "fp64" else 4
+    sm = {"fp64": 8, "fp32": 4, "bf16": 2}[precision]
+    return nnzb * (9 * sm + 4) + 4 * n + 5 * 3 * n * sv
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene = workload(args.grid)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        rate, desc, spent = cpu_sample(scene, newton_iters=REF_NEWTON, pcg_iters_per_newton=REF_PCG)
+        if k >= args.warmup:
+            vals.append(rate)
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"lattice{args.grid}^3 p=0.55 seed 3, "
+                                                       f"{scene.n_tets} tets, ground barrier, IE h=1/60"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "vs_baseline": None}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2508_13386_gb300 as mls
+    from paper_2508_13386_gb300 import basis as sms
+
+    scene = workload(args.grid)
+    t0 = time.perf_counter()
+    B = sms.build_sms_basis(scene.X, scene.tets, scene.E, args.handles, dirichlet=scene.dirichlet, seed=1)
+    basis_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream(dev)
+
+    def make(precision, precond):
+        s = mls.Solver(precision=precision, preconditioner=precond, cycle=args.cycle,
+                       newton_tol=1e-5 if precision != "fp64" else 1e-10,
+                       coarse_refresh=args.coarse_refresh, stream=stream)
+        s.setup_scene(scene)
+        if precond == "two_level":
+            s.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+        return s
+
+    ours = make(args.precision, "two_level")
+    h = scene.dt
+    x = torch.as_tensor(scene.x0, device=dev).contiguous()
+    v = torch.as_tensor(scene.v0, device=dev).contiguous()
+    dx = torch.empty_like(x)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def advance(solver, x, v):
+        _, st = solver.newton_step(x, v, h, dx=dx)
+        v.copy_(dx / h)
+        x.add_(dx)
+        return st
+
+    for _ in range(args.warmup):
+        advance(ours, x, v)
+    torch.cuda.synchronize()
+    # parity of the mixed step against the FP64 GPU path from the same state
+    fp64 = make("fp64", "jacobi")
+    x_chk, v_chk = x.clone(), v.clone()
+    dx64, st64 = fp64.newton_step(x_chk, v_chk, h)
+    dxm, stm = ours.newton_step(x_chk, v_chk, h)
+    disp_err = float(torch.linalg.norm(dxm - dx64) / torch.linalg.norm(dx64))
+    torch.cuda.synchronize()
+    # timed region
+    ours.profile_enable(["spmv"])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            _, st = ours.newton_step(x, v, h, dx=dx)
+            ev[k][1].record(stream)
+            v.copy_(dx / h)
+            x.add_(dx)
+            stats.append(st)
+        torch.cuda.synchronize()
+    prof = ours.profile_read()
+    ours.profile_enable([])
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+    # per kernel-class breakdown on one extra (untimed) step from the same state
+    ours.profile_enable(["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky"])
+    xb, vb = x.clone(), v.clone()
+    _, st_b = ours.newton_step(xb, vb, h)
+    breakdown = {k: {"ms": round(ms, 3), "launches": n} for k, (ms, n) in ours.profile_read().items() if n}
+    ours.profile_enable([])
+    # plain FP64 block-Jacobi PCG from the current state (same trajectory)
+    fp64_ms = []
+    fp64_stats = []
+    for k in range(args.fp64_steps):
+        xa, va = x.clone(), v.clone()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = fp64.newton_step(xa, va, h, dx=dx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms.append(e0.elapsed_time(e1))
+        fp64_stats.append(st)
+        v.copy_(dx / h)
+        x.add_(dx)
+    # end to end through the host-pointer entry point
+    xh = x.cpu().numpy().copy()
+    vh = v.cpu().numpy().copy()
+    dxh = np.empty_like(xh)
+    e2e_steps = max(2, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        ours.newton_step_host(xh, vh, h, dx=dxh)
+        vh = dxh / h
+        xh = xh + dxh
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * e2e_steps / e2e_s
+    # roofline of the dominant kernel (the PCG product)
+    spmv_ms, spmv_n = prof["spmv"]
+    meta = {"nnzb": int(ours_meta_nnzb(ours)), "n": scene.n_verts}
+    bytes_per = spmv_bytes(meta, args.precision)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_per / (spmv_ms / max(spmv_n, 1) / 1e3) / 1e9 if spmv_n else None
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        nit = float(np.mean([s["newton_iters"] for s in fp64_stats])) if fp64_stats else REF_NEWTON
+        npcg = float(np.mean([s["pcg_iters"] for s in fp64_stats])) / max(nit, 1) if fp64_stats else REF_PCG
+        rate, desc, spent = cpu_sample(scene, nit, npcg)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    pcg_total = sum(s["pcg_iters"] for s in stats)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32+f64", "bf16": "bf16+f32+f64", "fp64": "f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": f"lattice{args.grid}^3 p=0.55 seed 3: {scene.n_tets} tets, {scene.n_verts} verts, "
+                               f"E log-uniform 1e5-1e8 (32 Voronoi cells), ground barrier dhat=1e-3 kappa=1e5, "
+                               f"implicit Euler h=1/60, dropped at 1 m/s from 0.05 m (timed steps {args.warmup}..)",
+                   "solver": f"{args.precision} two-level PCG ({args.cycle}), SMS basis m={len(B['origins'])} "
+                             f"(r={12 * len(B['origins'])}), coarse refresh every {args.coarse_refresh}",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "pcg_iters_per_s": pcg_total / total_s,
+        "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in stats])),
+        "pcg_iters_per_step": pcg_total / args.steps,
+        "disp_err_vs_fp64": disp_err,
+        "fp64_plain": {"value": 1e3 / float(np.mean(fp64_ms)) if fp64_ms else None, "unit": UNIT,
+                       "steps": len(fp64_ms),
+                       "pcg_iters_per_step": float(np.mean([s["pcg_iters"] for s in fp64_stats])) if fp64_stats else None,
+                       "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in fp64_stats])) if fp64_stats else None},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 8 * scene.n_verts,
+                "d2h_bytes_per_step": 3 * 8 * scene.n_verts},
+        "roofline": {"kernel": "k_pcg_spmv", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "bytes_per_launch": bytes_per, "launches": spmv_n,
+                     "avg_launch_us": 1e3 * spmv_ms / max(spmv_n, 1), "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "clocks": clocks.summary(),
+        "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+        "cpu_baseline": cpu,
+        "setup": {"basis_build_s": basis_s},
+        "breakdown_one_step": breakdown,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+
+
+def ours_meta_nnzb(solver):
+    return solver.get_hessian_nnzb()
+
+
+if __name__ == "__main__":
+    main()

@@ -102,6 +102,7 @@ typedef struct mls_stats {
   double step_rel;         /* final |d|_inf / max(|x - x^t|_inf, h^2 |g|) */
   double grad_norm;        /* |g|_2 at the last evaluated iterate */
   double energy;           /* E at the returned iterate */
+  int64_t kernel_launches; /* CUDA kernels this call launched */
 } mls_stats;
 
 typedef struct mls_ctx mls_ctx;
@@ -233,6 +234,31 @@ mls_status mls_energy(mls_ctx* ctx, const double* x, const double* d, double alp
 /* Point-plane CCD step bound min(1, 0.9 min_v dist_v / (-n . d_v)) over
  * vertices approaching the plane; 1 without contact.  *alpha HOST. */
 mls_status mls_ccd_bound(mls_ctx* ctx, const double* x, const double* d, double* alpha);
+
+/* ---- Kernel timing (tracing) ---------------------------------------------
+ * Opt-in CUDA-event timing of the library's kernel classes, recorded on the
+ * context's stream around each launch of the enabled classes, for measuring
+ * kernel durations inside a running timestep.  Events cost about a
+ * microsecond per launch, so enable only the classes being measured. */
+enum {
+  MLS_PROF_ELEMENTS = 0,  /* per-tet energy/gradient/Hessian */
+  MLS_PROF_ASSEMBLE = 1,  /* gradient gather + H assembly */
+  MLS_PROF_SPMV = 2,      /* the PCG product kernel (H z, direction update, p.q) */
+  MLS_PROF_PCG_UPDATE = 3,/* PCG vector update + block-Jacobi + dots */
+  MLS_PROF_PRECOND = 4,   /* two-level preconditioner kernels */
+  MLS_PROF_GALERKIN = 5,  /* U^T H U */
+  MLS_PROF_CHOLESKY = 6,  /* coarse factorisation and inverse */
+  MLS_PROF_LINESEARCH = 7,/* energy / CCD / norm reductions */
+  MLS_PROF_COUNT = 8
+};
+
+/* Enable timing for the classes whose bits are set in mask (bit k = class k;
+ * 0 disables) and reset the accumulated totals. */
+mls_status mls_profile_enable(mls_ctx* ctx, uint32_t mask);
+
+/* Read accumulated totals: ms[MLS_PROF_COUNT] milliseconds and
+ * launches[MLS_PROF_COUNT] launch counts (HOST arrays, either nullable). */
+mls_status mls_profile_read(mls_ctx* ctx, double* ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

@@ -188,6 +188,11 @@ class Solver:
                                          _dev(v_t, (self.n, 3)), float(dt), _dev(g)))
         return g
 
+    def get_hessian_nnzb(self):
+        nnzb = C.c_int64()
+        self._check(self._l.mls_get_hessian(self._ctx, None, None, None, C.byref(nnzb)))
+        return nnzb.value
+
     def get_hessian(self):
         nnzb = C.c_int64()
         self._check(self._l.mls_get_hessian(self._ctx, None, None, None, C.byref(nnzb)))
@@ -247,6 +252,18 @@ class Solver:
         self._check(self._l.mls_energy(self._ctx, _dev(x, (self.n, 3)), _dev(d, (self.n, 3)), float(alpha),
                                        C.byref(E), C.byref(feas)))
         return E.value, bool(feas.value)
+
+    def profile_enable(self, classes=()):
+        mask = 0
+        for c in classes:
+            mask |= 1 << _lib.PROF_CLASSES.index(c)
+        self._check(self._l.mls_profile_enable(self._ctx, mask))
+
+    def profile_read(self):
+        ms = np.zeros(len(_lib.PROF_CLASSES), dtype=np.float64)
+        n = np.zeros(len(_lib.PROF_CLASSES), dtype=np.int64)
+        self._check(self._l.mls_profile_read(self._ctx, ms.ctypes.data_as(C.c_void_p), n.ctypes.data_as(C.c_void_p)))
+        return {c: (float(ms[i]), int(n[i])) for i, c in enumerate(_lib.PROF_CLASSES)}
 
     def ccd_bound(self, x, d):
         a = C.c_double()

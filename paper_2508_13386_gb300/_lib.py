@@ -48,6 +48,7 @@ class Stats(C.Structure):
         ("step_rel", C.c_double),
         ("grad_norm", C.c_double),
         ("energy", C.c_double),
+        ("kernel_launches", C.c_int64),
     ]
 
     def as_dict(self):
@@ -82,7 +83,11 @@ SIGNATURES = {
     "mls_get_coarse": [_P, _P],
     "mls_energy": [_P, _P, _P, _D, C.POINTER(_D), C.POINTER(_I)],
     "mls_ccd_bound": [_P, _P, _P, C.POINTER(_D)],
+    "mls_profile_enable": [_P, C.c_uint32],
+    "mls_profile_read": [_P, _P, _P],
 }
+PROF_CLASSES = ["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky",
+                "linesearch"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:

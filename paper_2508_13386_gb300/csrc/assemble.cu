@@ -280,11 +280,11 @@ mls_status launch_gather_grad(mls_ctx* ctx, const Vec4d* x, double* gnorm2_out) 
   const int nb = nblk(ctx->n);
   if (nb > kMaxPartials) return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
   if (ctx->opt.precision == MLS_FP64)
-    k_gather_grad<double><<<nb, kBlock, 0, ctx->stream>>>(asm_in(ctx), x, ctx->grad, (Vec4d*)ctx->vb,
-                                                          ctx->red, gnorm2_out);
+    { ++ctx->launches; k_gather_grad<double><<<nb, kBlock, 0, ctx->stream>>>(asm_in(ctx), x, ctx->grad, (Vec4d*)ctx->vb,
+                                                          ctx->red, gnorm2_out); }
   else
-    k_gather_grad<float><<<nb, kBlock, 0, ctx->stream>>>(asm_in(ctx), x, ctx->grad, (Vec4f*)ctx->vb,
-                                                         ctx->red, gnorm2_out);
+    { ++ctx->launches; k_gather_grad<float><<<nb, kBlock, 0, ctx->stream>>>(asm_in(ctx), x, ctx->grad, (Vec4f*)ctx->vb,
+                                                         ctx->red, gnorm2_out); }
   return cuda_check(ctx, cudaGetLastError(), "k_gather_grad");
 }
 
@@ -296,69 +296,69 @@ mls_status launch_assemble(mls_ctx* ctx, const Vec4d* x) {
   const int nb = nblk(n_slots);
   switch (ctx->opt.precision) {
     case MLS_FP64:
-      k_assemble<double, double, double, double><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const double*)ctx->ehess, (double*)ctx->hval, (double*)ctx->dinv);
+      { ++ctx->launches; k_assemble<double, double, double, double><<<nb, kBlock, 0, ctx->stream>>>(
+          in, n_slots, x, (const double*)ctx->ehess, (double*)ctx->hval, (double*)ctx->dinv); }
       break;
     case MLS_MIXED_FP32:
-      k_assemble<float, float, float, float><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const float*)ctx->ehess, (float*)ctx->hval, (float*)ctx->dinv);
+      { ++ctx->launches; k_assemble<float, float, float, float><<<nb, kBlock, 0, ctx->stream>>>(
+          in, n_slots, x, (const float*)ctx->ehess, (float*)ctx->hval, (float*)ctx->dinv); }
       break;
     default:
-      k_assemble<float, float, __nv_bfloat16, float><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)ctx->hval, (float*)ctx->dinv);
+      { ++ctx->launches; k_assemble<float, float, __nv_bfloat16, float><<<nb, kBlock, 0, ctx->stream>>>(
+          in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)ctx->hval, (float*)ctx->dinv); }
       break;
   }
   return cuda_check(ctx, cudaGetLastError(), "k_assemble");
 }
 
 mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, double dt) {
-  k_predictor<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, v, ctx->pinned, dt, ctx->grav[0],
+  { ++ctx->launches; k_predictor<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, v, ctx->pinned, dt, ctx->grav[0],
                                                        ctx->grav[1], ctx->grav[2], ctx->xt, ctx->xtil,
-                                                       ctx->xk);
+                                                       ctx->xk); }
   return cuda_check(ctx, cudaGetLastError(), "k_predictor");
 }
 
 mls_status launch_pack(mls_ctx* ctx, const double* src, Vec4d* dst) {
-  k_pack<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, dst);
+  { ++ctx->launches; k_pack<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, dst); }
   return cuda_check(ctx, cudaGetLastError(), "k_pack");
 }
 
 mls_status launch_unpack(mls_ctx* ctx, const Vec4d* src, double* dst) {
-  k_unpack<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, dst);
+  { ++ctx->launches; k_unpack<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, dst); }
   return cuda_check(ctx, cudaGetLastError(), "k_unpack");
 }
 
 mls_status launch_disp_out(mls_ctx* ctx, double* dx_out) {
-  k_disp<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, ctx->xk, ctx->xt, dx_out);
+  { ++ctx->launches; k_disp<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, ctx->xk, ctx->xt, dx_out); }
   return cuda_check(ctx, cudaGetLastError(), "k_disp");
 }
 
 mls_status launch_axpy_state(mls_ctx* ctx, Vec4d* x, const Vec4d* d, double alpha) {
-  k_axpy_state<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, d, alpha);
+  { ++ctx->launches; k_axpy_state<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, d, alpha); }
   return cuda_check(ctx, cudaGetLastError(), "k_axpy_state");
 }
 
 mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double scale) {
   if (ctx->opt.precision == MLS_FP64)
-    k_to_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, (Vec4d*)dst, scale);
+    { ++ctx->launches; k_to_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, (Vec4d*)dst, scale); }
   else
-    k_to_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, (Vec4f*)dst, scale);
+    { ++ctx->launches; k_to_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, (Vec4f*)dst, scale); }
   return cuda_check(ctx, cudaGetLastError(), "k_to_solve");
 }
 
 mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst) {
   if (ctx->opt.precision == MLS_FP64)
-    k_from_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4d*)src, ctx->pinned, dst);
+    { ++ctx->launches; k_from_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4d*)src, ctx->pinned, dst); }
   else
-    k_from_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4f*)src, ctx->pinned, dst);
+    { ++ctx->launches; k_from_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4f*)src, ctx->pinned, dst); }
   return cuda_check(ctx, cudaGetLastError(), "k_from_solve");
 }
 
 mls_status launch_from_solve_raw(mls_ctx* ctx, const void* src, Vec4d* dst) {
   if (ctx->opt.precision == MLS_FP64)
-    k_from_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4d*)src, nullptr, dst);
+    { ++ctx->launches; k_from_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4d*)src, nullptr, dst); }
   else
-    k_from_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4f*)src, nullptr, dst);
+    { ++ctx->launches; k_from_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4f*)src, nullptr, dst); }
   return cuda_check(ctx, cudaGetLastError(), "k_from_solve");
 }
 

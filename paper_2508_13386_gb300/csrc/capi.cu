@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kBlock) k_dot4(int n, const Vec4d* __restrict_
 
 static mls_status dot4(mls_ctx* ctx, const Vec4d* a, const Vec4d* b, double* out) {
   const int nb = (ctx->n + kBlock - 1) / kBlock;
-  k_dot4<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, a, b, ctx->red, ctx->dscal + 8);
+  { ++ctx->launches; k_dot4<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, a, b, ctx->red, ctx->dscal + 8); }
   mls_status st = cuda_check(ctx, cudaGetLastError(), "k_dot4");
   if (st != MLS_OK) return st;
   st = cuda_check(ctx, cudaMemcpyAsync(ctx->dscal_host + 8, ctx->dscal + 8, sizeof(double),
@@ -81,6 +81,37 @@ static mls_status read_scalar(mls_ctx* ctx, const double* dev, double* host_out)
   st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "scalar sync");
   *host_out = ctx->dscal_host[10];
   return st;
+}
+
+int prof_begin(mls_ctx* ctx, int cls) {
+  if (!(ctx->prof_mask & (1u << cls))) return -1;
+  const int base = (int)ctx->prof_pending.size() * 2;
+  while ((int)ctx->prof_pool.size() < base + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return -1; }
+    ctx->prof_pool.push_back(e);
+  }
+  cudaEventRecord(ctx->prof_pool[base], ctx->stream);
+  ctx->prof_pending.emplace_back(cls, base);
+  return base;
+}
+
+void prof_end(mls_ctx* ctx, int token) {
+  if (token < 0) return;
+  cudaEventRecord(ctx->prof_pool[token + 1], ctx->stream);
+}
+
+void prof_flush(mls_ctx* ctx) {
+  for (auto& pe : ctx->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->prof_pool[pe.second], ctx->prof_pool[pe.second + 1]) == cudaSuccess) {
+      ctx->prof_ms[pe.first] += ms;
+      ctx->prof_n[pe.first] += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  ctx->prof_pending.clear();
 }
 
 static void free_all(mls_ctx* ctx) {
@@ -155,6 +186,7 @@ mls_status mls_destroy(mls_ctx* ctx) {
   else cudaDeviceSynchronize();
   free_all(ctx);
   for (void* p : ctx->host_allocs) cudaFreeHost(p);
+  for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
   delete ctx;
   return MLS_OK;
 }
@@ -335,6 +367,7 @@ mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n, const double* X, int32_t t, 
   if ((st = up((void**)&ctx->asm_code, asm_code.data(), sizeof(int) * 16 * (size_t)t)) != MLS_OK) return st;
   if ((st = up((void**)&ctx->vt_ptr, vt_ptr.data(), sizeof(int) * (n + 1))) != MLS_OK) return st;
   if ((st = up((void**)&ctx->vt_code, vt_code.data(), sizeof(int) * 4 * (size_t)t)) != MLS_OK) return st;
+  ctx->mass_min = *std::min_element(h_mass.begin(), h_mass.end());
   ctx->n_slices = n_slices;
   ctx->n_groups = n_groups;
   ctx->nnzb = nnzb;
@@ -381,9 +414,13 @@ static const int kMaxHalvings = 60;
 
 static mls_status assemble_at(mls_ctx* ctx, const Vec4d* x, double* gnorm) {
   mls_status st;
+  int tk = prof_begin(ctx, MLS_PROF_ELEMENTS);
   if ((st = launch_eval_elements(ctx, x, nullptr)) != MLS_OK) return st;
+  prof_end(ctx, tk);
+  tk = prof_begin(ctx, MLS_PROF_ASSEMBLE);
   if ((st = launch_gather_grad(ctx, x, ctx->dscal + 2)) != MLS_OK) return st;
   if ((st = launch_assemble(ctx, x)) != MLS_OK) return st;
+  prof_end(ctx, tk);
   ctx->assembled = true;
   if (gnorm) {
     double g2 = 0;
@@ -433,6 +470,12 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
     }
     double eta = std::min(ctx->opt.pcg_rtol, std::sqrt(gnorm / g0));
     eta = std::max(eta, eta_floor);
+    // absolute floor: H >= M, so |d - d*|_2 <= |r|_2 / m_min; a residual below
+    // 0.01 newton_tol x scale x m_min cannot move the step test
+    double xdisp0 = 0, dn0 = 0;
+    if ((st = launch_norms(ctx, ctx->tmp4, &dn0, &xdisp0)) != MLS_OK) return st;
+    const double abs_floor = 0.01 * ctx->opt.newton_tol * std::max(xdisp0, scale0) * ctx->mass_min;
+    eta = std::max(eta, abs_floor / gnorm);
     int iters = 0;
     double rel = 0;
     st = pcg_solve(ctx, eta, ctx->opt.max_pcg, &iters, &rel);
@@ -478,6 +521,7 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
     if ((st = launch_axpy_state(ctx, ctx->xk, ctx->dir, alpha)) != MLS_OK) return st;
   }
   if ((st = launch_energy(ctx, ctx->xk, ctx->tmp4, 0.0, &E, &infeasible)) != MLS_OK) return st;
+  prof_flush(ctx);
   S.energy = E;
   if (stats) *stats = S;
   if (result != MLS_OK) return fail(ctx, result, "Newton reached its iteration cap");
@@ -506,10 +550,12 @@ mls_status mls_newton_step(mls_ctx* ctx, const double* x, const double* v, doubl
   mls_status st = check_mesh(ctx);
   if (st != MLS_OK) return st;
   if (!x || !v || !dx_out) return fail(ctx, MLS_EINVAL, "null state pointer");
+  const int64_t l0 = ctx->launches;
   if ((st = set_timestep(ctx, x, v, dt)) != MLS_OK) return st;
   mls_status res = newton(ctx, stats_out);
   if (res != MLS_OK && res != MLS_ENOTCONV) return res;
   if ((st = launch_disp_out(ctx, dx_out)) != MLS_OK) return st;
+  if (stats_out) stats_out->kernel_launches = ctx->launches - l0;
   st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "newton_step sync");
   return st != MLS_OK ? st : res;
 }
@@ -642,7 +688,7 @@ mls_status mls_spmv(mls_ctx* ctx, const double* x, double* y) {
   if ((st = launch_pack(ctx, x, ctx->dir)) != MLS_OK) return st;
   if ((st = launch_to_solve(ctx, ctx->dir, ctx->vp, 1.0)) != MLS_OK) return st;
   if ((st = launch_spmv(ctx, ctx->vp, ctx->vq)) != MLS_OK) return st;
-  if ((st = launch_from_solve(ctx, ctx->vq, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_from_solve_raw(ctx, ctx->vq, ctx->dir)) != MLS_OK) return st;
   if ((st = launch_unpack(ctx, ctx->dir, y)) != MLS_OK) return st;
   return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "spmv sync");
 }
@@ -654,7 +700,7 @@ mls_status mls_precond_apply(mls_ctx* ctx, const double* r, double* z) {
   if ((st = launch_pack(ctx, r, ctx->dir)) != MLS_OK) return st;
   if ((st = launch_to_solve(ctx, ctx->dir, ctx->vr, 1.0)) != MLS_OK) return st;
   if ((st = precond_apply(ctx, ctx->vr, ctx->vz)) != MLS_OK) return st;
-  if ((st = launch_from_solve(ctx, ctx->vz, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_from_solve_raw(ctx, ctx->vz, ctx->dir)) != MLS_OK) return st;
   if ((st = launch_unpack(ctx, ctx->dir, z)) != MLS_OK) return st;
   return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "precond sync");
 }
@@ -669,7 +715,7 @@ mls_status mls_pcg_solve(mls_ctx* ctx, const double* b, double* d, double rtol, 
   if ((st = launch_to_solve(ctx, ctx->dir, ctx->vb, 1.0)) != MLS_OK) return st;
   mls_status res = pcg_solve(ctx, rtol, max_iter, iters, rel_res);
   if (res != MLS_OK && res != MLS_ENOTCONV) return res;
-  if ((st = launch_from_solve(ctx, ctx->vx, ctx->dir)) != MLS_OK) return st;
+  if ((st = launch_from_solve_raw(ctx, ctx->vx, ctx->dir)) != MLS_OK) return st;
   if ((st = launch_unpack(ctx, ctx->dir, d)) != MLS_OK) return st;
   st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "pcg sync");
   return st != MLS_OK ? st : res;
@@ -693,7 +739,7 @@ mls_status mls_prolong(mls_ctx* ctx, const double* q, double* w) {
   if (ctx->opt.precision == MLS_FP64) {
     st = cuda_check(ctx, cudaMemcpyAsync(ctx->cvec, q, sizeof(double) * r, cudaMemcpyDeviceToDevice, ctx->stream), "q copy");
   } else {
-    k_cast_in<<<(r + 255) / 256, 256, 0, ctx->stream>>>(r, q, (float*)ctx->cvec);
+    { ++ctx->launches; k_cast_in<<<(r + 255) / 256, 256, 0, ctx->stream>>>(r, q, (float*)ctx->cvec); }
     st = cuda_check(ctx, cudaGetLastError(), "cast");
   }
   if (st != MLS_OK) return st;
@@ -714,7 +760,7 @@ mls_status mls_restrict(mls_ctx* ctx, const double* r, double* z) {
   if (ctx->opt.precision == MLS_FP64) {
     st = cuda_check(ctx, cudaMemcpyAsync(z, ctx->cvec, sizeof(double) * rr, cudaMemcpyDeviceToDevice, ctx->stream), "z copy");
   } else {
-    k_cast_out<<<(rr + 255) / 256, 256, 0, ctx->stream>>>(rr, (const float*)ctx->cvec, z);
+    { ++ctx->launches; k_cast_out<<<(rr + 255) / 256, 256, 0, ctx->stream>>>(rr, (const float*)ctx->cvec, z); }
     st = cuda_check(ctx, cudaGetLastError(), "cast");
   }
   if (st != MLS_OK) return st;
@@ -746,6 +792,28 @@ mls_status mls_energy(mls_ctx* ctx, const double* x, const double* d, double alp
   int inf = 0;
   if ((st = launch_energy(ctx, ctx->xk, ctx->dir, alpha, E, &inf)) != MLS_OK) return st;
   if (feasible) *feasible = inf ? 0 : 1;
+  return MLS_OK;
+}
+
+mls_status mls_profile_enable(mls_ctx* ctx, uint32_t mask) {
+  if (!ctx) return MLS_EINVAL;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  ctx->prof_pending.clear();
+  ctx->prof_mask = mask;
+  for (int k = 0; k < MLS_PROF_COUNT; ++k) { ctx->prof_ms[k] = 0.0; ctx->prof_n[k] = 0; }
+  return MLS_OK;
+}
+
+mls_status mls_profile_read(mls_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx) return MLS_EINVAL;
+  mls_status st = cuda_check(ctx, ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize(), "profile sync");
+  if (st != MLS_OK) return st;
+  prof_flush(ctx);
+  for (int k = 0; k < MLS_PROF_COUNT; ++k) {
+    if (ms) ms[k] = ctx->prof_ms[k];
+    if (launches) launches[k] = ctx->prof_n[k];
+  }
   return MLS_OK;
 }
 

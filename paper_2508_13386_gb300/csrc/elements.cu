@@ -504,12 +504,12 @@ mls_status launch_eval_elements(mls_ctx* ctx, const Vec4d* x, double* energy_out
   const int nb = (ctx->t + 127) / 128;
   switch (ctx->opt.precision) {
     case MLS_FP64:
-      k_eval_elements<double, double><<<nb, 128, 0, ctx->stream>>>(
-          elem_in(ctx), x, energy_out, ctx->egrad, (double*)ctx->ehess);
+      { ++ctx->launches; k_eval_elements<double, double><<<nb, 128, 0, ctx->stream>>>(
+          elem_in(ctx), x, energy_out, ctx->egrad, (double*)ctx->ehess); }
       break;
     default:
-      k_eval_elements<float, float><<<nb, 128, 0, ctx->stream>>>(
-          elem_in(ctx), x, energy_out, ctx->egrad, (float*)ctx->ehess);
+      { ++ctx->launches; k_eval_elements<float, float><<<nb, 128, 0, ctx->stream>>>(
+          elem_in(ctx), x, energy_out, ctx->egrad, (float*)ctx->ehess); }
       break;
   }
   return cuda_check(ctx, cudaGetLastError(), "k_eval_elements");
@@ -518,9 +518,9 @@ mls_status launch_eval_elements(mls_ctx* ctx, const Vec4d* x, double* energy_out
 mls_status launch_expand_hessian(mls_ctx* ctx, double* hess_out) {
   const int nb = (ctx->t + kBlock - 1) / kBlock;
   if (ctx->opt.precision == MLS_FP64)
-    k_expand_hessian<double><<<nb, kBlock, 0, ctx->stream>>>(ctx->t, (const double*)ctx->ehess, hess_out);
+    { ++ctx->launches; k_expand_hessian<double><<<nb, kBlock, 0, ctx->stream>>>(ctx->t, (const double*)ctx->ehess, hess_out); }
   else
-    k_expand_hessian<float><<<nb, kBlock, 0, ctx->stream>>>(ctx->t, (const float*)ctx->ehess, hess_out);
+    { ++ctx->launches; k_expand_hessian<float><<<nb, kBlock, 0, ctx->stream>>>(ctx->t, (const float*)ctx->ehess, hess_out); }
   return cuda_check(ctx, cudaGetLastError(), "k_expand_hessian");
 }
 
@@ -531,7 +531,7 @@ mls_status launch_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double al
   const int total = ctx->t + ctx->n;
   const int nb = (total + kBlock - 1) / kBlock;
   if (nb > kMaxPartials) return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
-  k_energy<<<nb, kBlock, 0, ctx->stream>>>(in, x, d, alpha, ctx->red, ctx->dscal);
+  { ++ctx->launches; k_energy<<<nb, kBlock, 0, ctx->stream>>>(in, x, d, alpha, ctx->red, ctx->dscal); }
   mls_status st = cuda_check(ctx, cudaGetLastError(), "k_energy");
   if (st != MLS_OK) return st;
   st = cuda_check(ctx, cudaMemcpyAsync(ctx->dscal_host, ctx->dscal, 2 * sizeof(double),
@@ -551,8 +551,8 @@ mls_status launch_ccd(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double* alph
                                                   cudaMemcpyHostToDevice, ctx->stream), "ccd init");
   if (st != MLS_OK) return st;
   const int nb = (ctx->n + kBlock - 1) / kBlock;
-  k_ccd<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, ctx->pinned, x, d, ctx->pn[0], ctx->pn[1], ctx->pn[2],
-                                        ctx->po, ctx->dscal + 4);
+  { ++ctx->launches; k_ccd<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, ctx->pinned, x, d, ctx->pn[0], ctx->pn[1], ctx->pn[2],
+                                        ctx->po, ctx->dscal + 4); }
   st = cuda_check(ctx, cudaGetLastError(), "k_ccd");
   if (st != MLS_OK) return st;
   st = cuda_check(ctx, cudaMemcpyAsync(ctx->dscal_host + 4, ctx->dscal + 4, sizeof(double),
@@ -570,7 +570,7 @@ mls_status launch_norms(mls_ctx* ctx, const Vec4d* d, double* dinf, double* xdis
                              "norms init");
   if (st != MLS_OK) return st;
   const int nb = (ctx->n + kBlock - 1) / kBlock;
-  k_norms<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, d, ctx->xk, ctx->xt, ctx->dscal + 6);
+  { ++ctx->launches; k_norms<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, d, ctx->xk, ctx->xt, ctx->dscal + 6); }
   st = cuda_check(ctx, cudaGetLastError(), "k_norms");
   if (st != MLS_OK) return st;
   st = cuda_check(ctx, cudaMemcpyAsync(ctx->dscal_host + 6, ctx->dscal + 6, 2 * sizeof(double),

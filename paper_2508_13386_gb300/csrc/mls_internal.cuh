@@ -202,6 +202,7 @@ struct mls_ctx {
   int* vt_ptr = nullptr;           // [n + 1]
   int* vt_code = nullptr;          // [4 t] (e * 4 + a)
   int64_t nnzb = 0;                // real (non-padding) blocks
+  double mass_min = 0.0;           // smallest lumped vertex mass
   std::vector<int> h_slice_ptr, h_row_len, h_col;
 
   // per-timestep / per-iteration state
@@ -250,11 +251,24 @@ struct mls_ctx {
   bool coarse_ready = false;
   int* chol_info = nullptr;        // device: first non-positive pivot + 1, or 0
 
+  // kernel-class timing
+  uint32_t prof_mask = 0;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<std::pair<int, int>> prof_pending;  // (class, first event of the pair)
+  double prof_ms[MLS_PROF_COUNT] = {};
+  int64_t prof_n[MLS_PROF_COUNT] = {};
+
+  int64_t launches = 0;            // kernels launched by this context
   std::vector<void*> allocs;       // every device allocation, freed by mls_destroy
   std::vector<void*> host_allocs;  // pinned host allocations
 };
 
 namespace mls {
+
+// kernel-class timing: prof_begin returns a token (or -1 when the class is off)
+int prof_begin(mls_ctx* ctx, int cls);
+void prof_end(mls_ctx* ctx, int token);
+void prof_flush(mls_ctx* ctx);  // call after the stream is synchronised
 
 // allocation helpers (host side; record for cleanup)
 mls_status dalloc(mls_ctx* ctx, void** p, size_t bytes);

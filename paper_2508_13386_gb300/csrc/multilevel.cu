@@ -529,20 +529,20 @@ static BasisView basis_view(mls_ctx* ctx) {
 mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   if (ctx->opt.precision == MLS_FP64)
-    k_prolong<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const double*)q,
-        accumulate ? (const Vec4d*)w : nullptr, nullptr, nullptr, 0.0, (Vec4d*)w, nullptr);
+    { ++ctx->launches; k_prolong<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const double*)q,
+        accumulate ? (const Vec4d*)w : nullptr, nullptr, nullptr, 0.0, (Vec4d*)w, nullptr); }
   else
-    k_prolong<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const float*)q,
-        accumulate ? (const Vec4f*)w : nullptr, nullptr, nullptr, 0.0f, (Vec4f*)w, nullptr);
+    { ++ctx->launches; k_prolong<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const float*)q,
+        accumulate ? (const Vec4f*)w : nullptr, nullptr, nullptr, 0.0f, (Vec4f*)w, nullptr); }
   return cuda_check(ctx, cudaGetLastError(), "k_prolong");
 }
 
 mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   if (ctx->opt.precision == MLS_FP64)
-    k_restrict<double><<<ctx->basis.m, kBlock, 0, ctx->stream>>>(basis_view(ctx), (const Vec4d*)r, (double*)q, nullptr);
+    { ++ctx->launches; k_restrict<double><<<ctx->basis.m, kBlock, 0, ctx->stream>>>(basis_view(ctx), (const Vec4d*)r, (double*)q, nullptr); }
   else
-    k_restrict<float><<<ctx->basis.m, kBlock, 0, ctx->stream>>>(basis_view(ctx), (const Vec4f*)r, (float*)q, nullptr);
+    { ++ctx->launches; k_restrict<float><<<ctx->basis.m, kBlock, 0, ctx->stream>>>(basis_view(ctx), (const Vec4f*)r, (float*)q, nullptr); }
   return cuda_check(ctx, cudaGetLastError(), "k_restrict");
 }
 
@@ -554,14 +554,14 @@ static mls_status galerkin_t(mls_ctx* ctx) {
   if (!B.ypair_row) {
     mls_status st = dalloc(ctx, (void**)&B.ypair_row, sizeof(int) * std::max<int64_t>(B.ny, 1));
     if (st != MLS_OK) return st;
-    k_ypair_rows<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, B.yrow, B.ypair_row);
+    { ++ctx->launches; k_ypair_rows<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, B.yrow, B.ypair_row); }
   }
-  k_galerkin_y<VT, MT><<<nblk(B.ny), kBlock, 0, ctx->stream>>>(basis_view(ctx), G, (const MT*)ctx->hval,
-                                                               B.ypair_row, B.ny, (VT*)ctx->yval);
+  { ++ctx->launches; k_galerkin_y<VT, MT><<<nblk(B.ny), kBlock, 0, ctx->stream>>>(basis_view(ctx), G, (const MT*)ctx->hval,
+                                                               B.ypair_row, B.ny, (VT*)ctx->yval); }
   mls_status st = cuda_check(ctx, cudaMemsetAsync(ctx->Ac, 0, sizeof(double) * r * r, ctx->stream), "Ac clear");
   if (st != MLS_OK) return st;
-  k_galerkin_a<VT><<<B.m, 288, 0, ctx->stream>>>(basis_view(ctx), B.hn_row, B.hn, B.ent_ptr, B.ent_y, B.ent_v,
-                                                 B.ent_phi, B.ny, (const VT*)ctx->yval, r, ctx->Ac);
+  { ++ctx->launches; k_galerkin_a<VT><<<B.m, 288, 0, ctx->stream>>>(basis_view(ctx), B.hn_row, B.hn, B.ent_ptr, B.ent_y, B.ent_v,
+                                                 B.ent_phi, B.ny, (const VT*)ctx->yval, r, ctx->Ac); }
   return cuda_check(ctx, cudaGetLastError(), "galerkin");
 }
 
@@ -576,11 +576,11 @@ static mls_status factor_t(mls_ctx* ctx) {
   if (st != MLS_OK) return st;
   // symmetrise from the lower triangle is implicit: only the lower triangle is read
   for (int k = 0; k < nt; ++k) {
-    k_potrf_tile<<<1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, k, ctx->chol_info);
+    { ++ctx->launches; k_potrf_tile<<<1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, k, ctx->chol_info); }
     if (k + 1 < nt) {
-      k_trsm_tiles<<<nt - k - 1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, k);
+      { ++ctx->launches; k_trsm_tiles<<<nt - k - 1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, k); }
       const int m = nt - k - 1;
-      k_syrk_tiles<<<m * (m + 1) / 2, dim3(32, 8), 0, ctx->stream>>>(ctx->Ac, r, k, nt);
+      { ++ctx->launches; k_syrk_tiles<<<m * (m + 1) / 2, dim3(32, 8), 0, ctx->stream>>>(ctx->Ac, r, k, nt); }
     }
   }
   st = cuda_check(ctx, cudaGetLastError(), "cholesky");
@@ -589,7 +589,7 @@ static mls_status factor_t(mls_ctx* ctx) {
   if (st != MLS_OK) return st;
   st = cuda_check(ctx, cudaMemsetAsync(ctx->LinvT, 0, (size_t)r * r * sizeof(VT), ctx->stream), "WT clear");
   if (st != MLS_OK) return st;
-  k_trinv_column<VT><<<nt, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, nt, (VT*)ctx->Linv, (VT*)ctx->LinvT);
+  { ++ctx->launches; k_trinv_column<VT><<<nt, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, nt, (VT*)ctx->Linv, (VT*)ctx->LinvT); }
   st = cuda_check(ctx, cudaGetLastError(), "triangular inverse");
   if (st != MLS_OK) return st;
   int info = 0;
@@ -611,13 +611,18 @@ mls_status build_coarse(mls_ctx* ctx) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "assemble H before building the coarse operator");
   mls_status st;
+  int tk = prof_begin(ctx, MLS_PROF_GALERKIN);
   switch (ctx->opt.precision) {
     case MLS_FP64: st = galerkin_t<double, double>(ctx); break;
     case MLS_MIXED_FP32: st = galerkin_t<float, float>(ctx); break;
     default: st = galerkin_t<float, __nv_bfloat16>(ctx); break;
   }
   if (st != MLS_OK) return st;
-  return ctx->opt.precision == MLS_FP64 ? factor_t<double>(ctx) : factor_t<float>(ctx);
+  prof_end(ctx, tk);
+  tk = prof_begin(ctx, MLS_PROF_CHOLESKY);
+  st = ctx->opt.precision == MLS_FP64 ? factor_t<double>(ctx) : factor_t<float>(ctx);
+  prof_end(ctx, tk);
+  return st;
 }
 
 template <typename VT>
@@ -625,8 +630,8 @@ static mls_status coarse_apply_t(mls_ctx* ctx, const VT* c_in, VT* c_out, const 
   const int r = 12 * ctx->basis.m;
   const int rows_per_block = kBlock / 32;
   const int nb = (r + rows_per_block - 1) / rows_per_block;
-  k_trigemv<VT><<<nb, kBlock, 0, ctx->stream>>>((const VT*)ctx->Linv, r, 1, c_in, (VT*)ctx->cvec2, S);
-  k_trigemv<VT><<<nb, kBlock, 0, ctx->stream>>>((const VT*)ctx->LinvT, r, 0, (const VT*)ctx->cvec2, c_out, S);
+  { ++ctx->launches; k_trigemv<VT><<<nb, kBlock, 0, ctx->stream>>>((const VT*)ctx->Linv, r, 1, c_in, (VT*)ctx->cvec2, S); }
+  { ++ctx->launches; k_trigemv<VT><<<nb, kBlock, 0, ctx->stream>>>((const VT*)ctx->LinvT, r, 0, (const VT*)ctx->cvec2, c_out, S); }
   return cuda_check(ctx, cudaGetLastError(), "coarse apply");
 }
 
@@ -644,10 +649,10 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   VT* c = (VT*)ctx->cvec;
   const VT* dinv = (const VT*)ctx->dinv;
   if (ctx->opt.cycle == MLS_CYCLE_ADDITIVE) {
-    k_restrict<VT><<<m, kBlock, 0, ctx->stream>>>(BV, r, c, S);
+    { ++ctx->launches; k_restrict<VT><<<m, kBlock, 0, ctx->stream>>>(BV, r, c, S); }
     mls_status st = coarse_apply_t<VT>(ctx, c, c, S);
     if (st != MLS_OK) return st;
-    k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, nullptr, dinv, r, omega, z, S);
+    { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, nullptr, dinv, r, omega, z, S); }
     return cuda_check(ctx, cudaGetLastError(), "two-level additive");
   }
   // multiplicative: z1 = S r; t = r - H z1; z2 = z1 + Q t; t = r - H z2; z = z2 + S t
@@ -655,11 +660,11 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   mls_status st = launch_jacobi(ctx, r, z, ctx->opt.omega, S);
   if (st != MLS_OK) return st;
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
-  k_restrict<VT><<<m, kBlock, 0, ctx->stream>>>(BV, tmp, c, S);
+  { ++ctx->launches; k_restrict<VT><<<m, kBlock, 0, ctx->stream>>>(BV, tmp, c, S); }
   if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
-  k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, z, nullptr, nullptr, omega, z, S);
+  { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, z, nullptr, nullptr, omega, z, S); }
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
-  k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, nullptr, z, dinv, tmp, omega, z, S);
+  { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, nullptr, z, dinv, tmp, omega, z, S); }
   return cuda_check(ctx, cudaGetLastError(), "two-level multiplicative");
 }
 

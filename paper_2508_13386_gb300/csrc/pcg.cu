@@ -217,8 +217,8 @@ static inline int nblk(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
 template <typename VT, typename MT>
 static void spmv_t(mls_ctx* ctx, const void* x, void* y) {
-  k_spmv<VT, MT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
-                                                           (const Vec4<VT>*)x, (Vec4<VT>*)y);
+  { ++ctx->launches; k_spmv<VT, MT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
+                                                           (const Vec4<VT>*)x, (Vec4<VT>*)y); }
 }
 
 mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y) {
@@ -232,9 +232,9 @@ mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y) {
 
 template <typename VT, typename MT>
 mls_status launch_residual_t(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S) {
-  k_residual<VT, MT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
+  { ++ctx->launches; k_residual<VT, MT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
                                                                (const Vec4<VT>*)b, (const Vec4<VT>*)x,
-                                                               (Vec4<VT>*)out, S);
+                                                               (Vec4<VT>*)out, S); }
   return cuda_check(ctx, cudaGetLastError(), "k_residual");
 }
 
@@ -248,11 +248,11 @@ mls_status launch_residual(mls_ctx* ctx, const void* b, const void* x, void* out
 
 mls_status launch_jacobi(mls_ctx* ctx, const void* r, void* z, double omega, const PcgScalars* S) {
   if (ctx->opt.precision == MLS_FP64)
-    k_jacobi<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const double*)ctx->dinv,
-                                                               (const Vec4d*)r, (Vec4d*)z, omega, S);
+    { ++ctx->launches; k_jacobi<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const double*)ctx->dinv,
+                                                               (const Vec4d*)r, (Vec4d*)z, omega, S); }
   else
-    k_jacobi<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const float*)ctx->dinv,
-                                                              (const Vec4f*)r, (Vec4f*)z, (float)omega, S);
+    { ++ctx->launches; k_jacobi<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const float*)ctx->dinv,
+                                                              (const Vec4f*)r, (Vec4f*)z, (float)omega, S); }
   return cuda_check(ctx, cudaGetLastError(), "k_jacobi");
 }
 
@@ -275,24 +275,30 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
   PcgScalars* S = ctx->pcg;
   SellView A = sell_view(ctx);
   const MT* val = (const MT*)ctx->hval;
-  k_pcg_init<VT><<<nb, kBlock, 0, ctx->stream>>>(n, b, x, r, z, p, q, dinv, jacobi ? 1 : 0, rtol, max_iter,
-                                                 ctx->red, S);
+  { ++ctx->launches; k_pcg_init<VT><<<nb, kBlock, 0, ctx->stream>>>(n, b, x, r, z, p, q, dinv, jacobi ? 1 : 0, rtol, max_iter,
+                                                 ctx->red, S); }
   mls_status st = cuda_check(ctx, cudaGetLastError(), "k_pcg_init");
   if (st != MLS_OK) return st;
   if (!jacobi) {
     st = precond_apply_dev(ctx, r, z, S);
     if (st != MLS_OK) return st;
-    k_pcg_rz<VT><<<nb, kBlock, 0, ctx->stream>>>(n, r, z, 1, ctx->red, S);
+    { ++ctx->launches; k_pcg_rz<VT><<<nb, kBlock, 0, ctx->stream>>>(n, r, z, 1, ctx->red, S); }
   }
   const int chunk = ctx->opt.pcg_check_every > 0 ? ctx->opt.pcg_check_every : 16;
   for (;;) {
     for (int c = 0; c < chunk; ++c) {
-      k_pcg_spmv<VT, MT><<<nb, kBlock, 0, ctx->stream>>>(A, val, z, p, q, ctx->red, S);
-      k_pcg_update<VT><<<nb, kBlock, 0, ctx->stream>>>(n, x, r, z, p, q, dinv, jacobi ? 1 : 0, ctx->red, S);
+      int tk = prof_begin(ctx, MLS_PROF_SPMV);
+      { ++ctx->launches; k_pcg_spmv<VT, MT><<<nb, kBlock, 0, ctx->stream>>>(A, val, z, p, q, ctx->red, S); }
+      prof_end(ctx, tk);
+      tk = prof_begin(ctx, MLS_PROF_PCG_UPDATE);
+      { ++ctx->launches; k_pcg_update<VT><<<nb, kBlock, 0, ctx->stream>>>(n, x, r, z, p, q, dinv, jacobi ? 1 : 0, ctx->red, S); }
+      prof_end(ctx, tk);
       if (!jacobi) {
+        tk = prof_begin(ctx, MLS_PROF_PRECOND);
         st = precond_apply_dev(ctx, r, z, S);
         if (st != MLS_OK) return st;
-        k_pcg_rz<VT><<<nb, kBlock, 0, ctx->stream>>>(n, r, z, 0, ctx->red, S);
+        { ++ctx->launches; k_pcg_rz<VT><<<nb, kBlock, 0, ctx->stream>>>(n, r, z, 0, ctx->red, S); }
+        prof_end(ctx, tk);
       }
     }
     st = cuda_check(ctx, cudaGetLastError(), "pcg iteration");
@@ -302,6 +308,7 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
     if (st != MLS_OK) return st;
     st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "pcg sync");
     if (st != MLS_OK) return st;
+    prof_flush(ctx);
     if (ctx->pcg_host->done) break;
   }
   const PcgScalars& h = *ctx->pcg_host;

@@ -14,8 +14,8 @@ barrier parameters, and the timestep.  The recipes:
                       6-connected component, lifted 0.05 m above the plane
                       z=0; E log-uniform in [1e5, 1e8] per Voronoi cell
                       (32 cells); nu=0.4; ground barrier dhat=1e-3,
-                      kappa=1e5; gravity; h=1/60.  n=41 gives about 225K tets,
-                      n=48 about 361K.
+                      kappa=1e5; gravity; h=1/60; optional initial downward
+                      speed.  n=41 gives 224,226 tets, n=48 360,126.
 * ``batched_lattice_scenes``  64 lattices with tet counts log-uniform in
                       [2K, 60K], materials as the beam, ground barrier.
 * ``tiny_scene``      jittered small blocks for unit tests.
@@ -99,9 +99,11 @@ def beam_scene(material_seed: int = 2, n_cells: int = 32) -> Scene:
 
 
 def lattice_scene(n: int = 41, seed: int = 3, p: float = 0.55, n_cells: int = 32,
-                  lift: float = 0.05, materials: str = "loguniform") -> Scene:
-    """Random voxel lattice in the unit cube resting ``lift`` above the ground
-    plane z=0 with the point-plane log barrier enabled."""
+                  lift: float = 0.05, materials: str = "loguniform",
+                  v_down: float = 0.0) -> Scene:
+    """Random voxel lattice in the unit cube ``lift`` above the ground plane
+    z=0 with the point-plane log barrier enabled, falling with initial speed
+    ``v_down`` (m/s)."""
     keep = lattice_mask(n, p, seed)
     mesh = kuhn_voxel_mesh(keep, voxel=1.0 / n, origin=(0.0, 0.0, lift))
     cell, _ = voronoi_cells(_tet_centroids(mesh), n_cells, seed=seed,
@@ -117,8 +119,8 @@ def lattice_scene(n: int = 41, seed: int = 3, p: float = 0.55, n_cells: int = 32
     return Scene(name=f"lattice{n}_p{p}_s{seed}", mesh=mesh, E=cell_E[cell],
                  nu=np.full(t, 0.4), rho=np.full(t, 1000.0),
                  dirichlet=np.zeros(mesh.n_verts, dtype=np.uint8), x0=mesh.X.copy(),
-                 v0=np.zeros_like(mesh.X), dt=1.0 / 60.0, contact=True,
-                 meta={"grid": n, "p": p, "seed": seed})
+                 v0=np.tile([0.0, 0.0, -v_down], (mesh.n_verts, 1)), dt=1.0 / 60.0, contact=True,
+                 meta={"grid": n, "p": p, "seed": seed, "v_down": v_down})
 
 
 def batched_lattice_scenes(count: int = 64, seed: int = 5, t_min: float = 2e3,

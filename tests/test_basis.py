@@ -1,0 +1,105 @@
+"""Invariants of the SMS basis construction (Sec. 3.5-3.6), checked on the
+host without a GPU: non-negativity, partition of unity with the Dirichlet
+basis, interpolation at handles, compact support inside each subdomain,
+vanishing at Dirichlet vertices, linear precision, and material awareness
+of the partition."""
+import numpy as np
+import pytest
+
+import synth
+from paper_2508_13386_gb300 import basis
+from oracle import subspace
+
+
+def _expand(B, n):
+    rows = np.repeat(np.arange(n), np.diff(B["vrow"]))
+    return rows, B["handle"], B["phi"]
+
+
+@pytest.fixture(scope="module")
+def beam():
+    s = synth.beam_scene()
+    return s, basis.build_sms_basis(s.X, s.tets, s.E, 32, dirichlet=s.dirichlet, seed=1)
+
+
+@pytest.fixture(scope="module")
+def lattice():
+    s = synth.lattice_scene(n=10, seed=7)
+    return s, basis.build_sms_basis(s.X, s.tets, s.E, 12, seed=2)
+
+
+@pytest.mark.parametrize("which", ["beam", "lattice"])
+def test_partition_of_unity_and_nonnegative(which, request):
+    s, B = request.getfixturevalue(which)
+    n = s.n_verts
+    rows, cols, phi = _expand(B, n)
+    assert np.all(phi >= 0)
+    tot = np.zeros(n)
+    np.add.at(tot, rows, phi)
+    assert np.allclose(tot + B["phi_dbc"], 1.0, atol=1e-12)
+    free = B["u_dbc"] == 0
+    assert np.allclose(tot[free], 1.0, atol=1e-12)
+
+
+def test_vanishes_at_dirichlet_vertices(beam):
+    s, B = beam
+    rows, cols, phi = _expand(B, s.n_verts)
+    assert np.all(phi[s.dirichlet[rows] == 1] == 0)
+    assert np.allclose(B["phi_dbc"][s.dirichlet == 1], 1.0)
+
+
+@pytest.mark.parametrize("which", ["beam", "lattice"])
+def test_interpolates_at_handles_and_compact_support(which, request):
+    s, B = request.getfixturevalue(which)
+    n = s.n_verts
+    rows, cols, phi = _expand(B, n)
+    hv = B["handle_vertex"]
+    m = len(hv)
+    W = np.zeros((n, m))
+    W[rows, cols] = phi
+    for i in range(m):
+        if B["u_dbc"][hv[i]] == 0:
+            assert W[hv[i], i] == pytest.approx(1.0, abs=1e-12)
+        for j in B["neighbours"][i]:
+            assert W[hv[j], i] == 0.0
+        # support within the subdomain (own partition + face neighbours)
+        sub = np.isin(B["partition"], [i] + B["neighbours"][i])
+        sub_verts = np.unique(s.tets[sub])
+        assert np.all(np.isin(np.nonzero(W[:, i])[0], sub_verts))
+
+
+@pytest.mark.parametrize("which", ["beam", "lattice"])
+def test_linear_precision(which, request):
+    """POU weights with affine handle DOFs reproduce any affine map (Sec. 3.5)
+    wherever the Dirichlet basis does not take part."""
+    s, B = request.getfixturevalue(which)
+    rng = np.random.default_rng(5)
+    A = rng.normal(size=(3, 3))
+    t = rng.normal(size=3)
+    U = subspace.lbs_basis_matrix(s.X, B["origins"], B["vrow"], B["handle"], B["phi"])
+    q = np.stack([np.concatenate([(A @ o + t)[:, None], A], axis=1).ravel() for o in B["origins"]])
+    w = subspace.prolong(U, q)
+    free = B["u_dbc"] == 0
+    assert np.allclose(w[free], (s.X @ A.T + t)[free], atol=1e-11)
+
+
+def test_partition_is_material_aware(beam):
+    """Stiff regions receive larger partitions than soft ones (Sec. 3.6.1)."""
+    s, B = beam
+    vol = np.abs(np.linalg.det(np.stack([s.X[s.tets[:, k]] - s.X[s.tets[:, 0]] for k in (1, 2, 3)], -1))) / 6
+    part = B["partition"]
+    m = part.max() + 1
+    pvol = np.bincount(part, weights=vol, minlength=m)
+    stiff_frac = np.bincount(part, weights=vol * (s.E > 1e8), minlength=m) / pvol
+    stiff = stiff_frac > 0.3
+    soft = stiff_frac < 0.05
+    assert stiff.any() and soft.any()
+    assert pvol[stiff].mean() > 1.5 * pvol[soft].mean()
+
+
+def test_handle_count_and_determinism():
+    s = synth.cube_scene()
+    B1 = basis.build_sms_basis(s.X, s.tets, s.E, 8, dirichlet=s.dirichlet, seed=3)
+    B2 = basis.build_sms_basis(s.X, s.tets, s.E, 8, dirichlet=s.dirichlet, seed=3)
+    assert len(B1["origins"]) == 8
+    assert np.array_equal(B1["handle"], B2["handle"]) and np.array_equal(B1["phi"], B2["phi"])

@@ -1,0 +1,117 @@
+"""Parity on the named workloads, in the configuration the benchmark runs.
+
+* Beam (40x10x10 voxels, 24,000 tets, E in {1e5, 1e9}, clamped end): one
+  timestep against the oracle's converged minimiser -- FP64 paths within
+  1e-9 and the mixed-precision two-level path within 1e-4 per-step relative
+  displacement, using the paper's SMS basis (32 handles).
+* Full-size lattice (41^3, 224,226 tets, ground contact): the oracle cannot
+  converge a full-size timestep in seconds, so the check is (a) per-tet
+  parity of element energies, gradients and projected Hessians on a sample
+  of tets at a deformed contact state, and (b) the oracle's Newton correction
+  at the GPU's result, e = H^{-1} g with the oracle's Hessian and gradient
+  (solved by the oracle's Jacobi-PCG to 1e-3 relative residual), as the
+  displacement error estimate |e| / |x^{t+1} - x^t| against the same
+  1e-9 / 1e-4 bars.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import elastic, ip, newton, pcg
+
+from gpu_helpers import dev, host, rel_disp_error, solver_for, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def beam():
+    s = synth.beam_scene()
+    p = ip.Problem(s)
+    x_o, info = newton.timestep(p, method="splu")
+    from paper_2508_13386_gb300 import basis
+    B = basis.build_sms_basis(s.X, s.tets, s.E, 32, dirichlet=s.dirichlet, seed=1)
+    return s, p, x_o, B
+
+
+@pytest.mark.parametrize("precision,precond,tol", [
+    ("fp64", "jacobi", 1e-9),
+    ("fp64", "two_level", 1e-9),
+    ("fp32", "two_level", 1e-4),
+    ("bf16", "two_level", 1e-4),
+])
+def test_beam_timestep(beam, precision, precond, tol):
+    s, p, x_o, B = beam
+    solver = solver_for(s, precision=precision, preconditioner=precond,
+                        newton_tol=1e-10 if precision == "fp64" else 1e-6)
+    if precond == "two_level":
+        solver.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    dx, stats = solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    err = rel_disp_error(s.x0 + host(dx), x_o, s.x0)
+    assert err <= tol, (err, stats)
+
+
+def test_beam_two_level_cuts_pcg_iterations(beam):
+    s, p, x_o, B = beam
+    jac = solver_for(s, precision="fp64", preconditioner="jacobi")
+    _, st_j = jac.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    ml = solver_for(s, precision="fp64", preconditioner="two_level")
+    ml.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    _, st_m = ml.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    assert st_m["pcg_iters"] < 0.5 * st_j["pcg_iters"]
+
+
+@pytest.fixture(scope="module")
+def lattice_state():
+    """The full-size lattice after three steps of the benchmark trajectory."""
+    from paper_2508_13386_gb300 import basis
+    s = synth.lattice_scene(n=41, seed=3, v_down=1.0)
+    B = basis.build_sms_basis(s.X, s.tets, s.E, 160, seed=1)
+    solver = solver_for(s, precision="fp32", preconditioner="two_level", newton_tol=1e-5, coarse_refresh=1)
+    solver.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    x = dev(s.x0)
+    v = dev(s.v0)
+    for _ in range(3):
+        dx, st = solver.newton_step(x, v, s.dt)
+        v.copy_(dx / s.dt)
+        x.add_(dx)
+    return s, B, host(x), host(v)
+
+
+@pytest.mark.parametrize("precision,rtol", [("fp64", 1e-10), ("fp32", 2e-4)])
+def test_fullsize_element_parity_sampled(lattice_state, precision, rtol):
+    s, B, x, v = lattice_state
+    solver = solver_for(s, precision=precision)
+    E, g, H = solver.eval_elements(dev(x))
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(s.n_tets, size=3000, replace=False))
+    tets = s.tets[idx]
+    vol, Dm_inv = elastic.rest_shape(s.X, tets)
+    mu, lam = elastic.lame(s.E[idx], s.nu[idx])
+    E_o = elastic.element_energy(x, tets, vol, Dm_inv, mu, lam)
+    g_o = elastic.element_gradient(x, tets, vol, Dm_inv, mu, lam)
+    H_o = elastic.element_hessian(x, tets, vol, Dm_inv, mu, lam, project=True)
+    assert np.allclose(host(E)[idx], E_o, rtol=1e-10, atol=1e-12 * np.abs(E_o).max())
+    gs = np.abs(g_o).max(axis=1, keepdims=True)
+    assert np.max(np.abs(host(g)[idx] - g_o) / gs) <= 1e-10
+    Hs = np.abs(H_o).max(axis=(1, 2), keepdims=True)
+    assert np.max(np.abs(host(H)[idx] - H_o) / Hs) <= rtol
+
+
+@pytest.mark.parametrize("precision,precond,tol", [("fp64", "jacobi", 1e-9), ("fp32", "two_level", 1e-4)])
+def test_fullsize_timestep_gradient_bound(lattice_state, precision, precond, tol):
+    s, B, x, v = lattice_state
+    p = ip.Problem(s, x_t=x, v_t=v)
+    solver = solver_for(s, precision=precision, preconditioner=precond,
+                        newton_tol=1e-10 if precision == "fp64" else 1e-6, coarse_refresh=1)
+    if precond == "two_level":
+        solver.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    dx, stats = solver.newton_step(dev(x), dev(v), s.dt)
+    x1 = x + host(dx)
+    assert p.feasible(x1)
+    g = p.gradient(x1).ravel()
+    H = p.hessian(x1)
+    diag = H.diagonal()
+    e, info = pcg.pcg(lambda u: H @ u, g, lambda r: r / diag, rtol=1e-3, max_iter=5000)
+    est = np.linalg.norm(e) / np.linalg.norm(x1 - x)
+    assert est <= tol, (est, stats)
