@@ -589,7 +589,8 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
   if (ctx->has_basis) {
     Basis& B = ctx->basis;
     void* old[] = {B.vrow, B.vh, B.vphi, B.hrow, B.hv, B.hphi, B.origins, B.yrow, B.yh, B.yslot, B.hn_row, B.hn,
-                   B.ent_ptr, B.ent_y, B.ent_v, B.ent_phi, B.ypair_row, ctx->yval, ctx->Ac, ctx->Acopy,
+                   B.ent_ptr, B.ent_y, B.ent_v, B.ent_phi, B.ypair_row, B.chunk_ptr, B.chunk_beg, B.slot_row,
+                   ctx->gpart, ctx->yval, ctx->Ac, ctx->Acopy,
                    ctx->Linv, ctx->LinvT, ctx->cvec, ctx->cvec2, ctx->chol_info};
     for (void* p : old) dfree(ctx, p);
     ctx->basis = Basis{};

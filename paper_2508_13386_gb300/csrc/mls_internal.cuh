@@ -33,6 +33,7 @@ using Vec4f = Vec4<float>;
 constexpr int kBlock = 256;
 constexpr int kSlice = 32;
 constexpr int kMaxPartials = 8192;
+constexpr int kGalerkinChunk = 128;
 
 // offsets of the 10 upper 3x3 blocks inside the 78-value element Hessian
 // (order (0,0),(0,1),(0,2),(0,3),(1,1),(1,2),(1,3),(2,2),(2,3),(3,3))
@@ -109,12 +110,23 @@ __device__ bool grid_sum(double (&v)[K], const GridReduce& gr, int slot) {
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // the partials of other blocks are read through L2 (__ldcg), eight loads in
+  // flight per thread before they are summed (in block order per thread)
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
-      s += ((volatile double*)gr.partials)[k * kMaxPartials + b];
+    const double* base = gr.partials + k * kMaxPartials;
+    for (int b0 = threadIdx.x; b0 < nb; b0 += 8 * blockDim.x) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + u * blockDim.x;
+        t[u] = b < nb ? __ldcg(base + b) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += t[u];
+    }
     acc[k] = s;
   }
   block_sum<K>(acc, sh);
@@ -168,6 +180,10 @@ struct Basis {
   double* ent_phi = nullptr;  // [nent] phi_i(v)
   int64_t nent = 0;
   int* ypair_row = nullptr;   // [ny] row v of each (v, j) pair
+  int* chunk_ptr = nullptr;   // [nb+1] first chunk of each coarse block
+  int* chunk_beg = nullptr;   // [nchunk] first entry of each chunk
+  int* slot_row = nullptr;    // [nb] coarse block row i of each block
+  int nchunk = 0;
   std::vector<int> h_vrow, h_hrow;
 };
 
@@ -246,6 +262,7 @@ struct mls_ctx {
   void* LinvT = nullptr;           // [r][r] W^T (upper)
   double* Acopy = nullptr;         // [r][r] copy of the operator before factorisation
   void* yval = nullptr;            // [ny][36] H U blocks (solve precision)
+  void* gpart = nullptr;           // [nchunk][144] Galerkin chunk partial sums
   void* cvec = nullptr;            // [r] coarse vectors (solve precision)
   void* cvec2 = nullptr;
   bool coarse_ready = false;

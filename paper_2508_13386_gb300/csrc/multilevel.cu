@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 namespace mls {
 
@@ -143,6 +144,15 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   }
   const int nbk = h_hn_row[m];
   const size_t nent = h_ent_y.size();
+  // chunks of at most kGalerkinChunk entries that never cross a coarse block
+  std::vector<int> h_chunk_ptr(1, 0), h_chunk_beg, h_slot_row(nbk);
+  for (int i = 0; i < m; ++i)
+    for (int sl = h_hn_row[i]; sl < h_hn_row[i + 1]; ++sl) h_slot_row[sl] = i;
+  for (int sl = 0; sl < nbk; ++sl) {
+    for (int b = h_ent_ptr[sl]; b < h_ent_ptr[sl + 1]; b += kGalerkinChunk) h_chunk_beg.push_back(b);
+    h_chunk_ptr.push_back((int)h_chunk_beg.size());
+  }
+  const int nchunk = (int)h_chunk_beg.size();
 
   // device copies
   auto up = [&](void** dst, const void* src, size_t bytes) -> mls_status {
@@ -168,17 +178,22 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   if ((st = up((void**)&B.ent_y, h_ent_y.data(), sizeof(int) * nent)) != MLS_OK) return st;
   if ((st = up((void**)&B.ent_v, h_ent_v.data(), sizeof(int) * nent)) != MLS_OK) return st;
   if ((st = up((void**)&B.ent_phi, h_ent_phi.data(), sizeof(double) * nent)) != MLS_OK) return st;
+  if ((st = up((void**)&B.chunk_ptr, h_chunk_ptr.data(), sizeof(int) * (nbk + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&B.chunk_beg, h_chunk_beg.data(), sizeof(int) * std::max(nchunk, 1))) != MLS_OK) return st;
+  if ((st = up((void**)&B.slot_row, h_slot_row.data(), sizeof(int) * std::max(nbk, 1))) != MLS_OK) return st;
   B.m = m;
   B.nnz = nz;
   B.ny = ny;
   B.maxk = std::max(maxk, 1);
   B.nb = nbk;
   B.nent = (int64_t)nent;
+  B.nchunk = nchunk;
   B.h_hrow = h_hrow;
   B.h_vrow = h_vrow;
   const int r = 12 * m;
   const int vb = solve_bytes(ctx);
   if ((st = dalloc(ctx, &ctx->yval, (size_t)ny * 36 * vb)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->gpart, (size_t)std::max(nchunk, 1) * 144 * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->Ac, (size_t)r * r * sizeof(double))) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->Acopy, (size_t)r * r * sizeof(double))) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->Linv, (size_t)r * r * vb)) != MLS_OK) return st;
@@ -334,35 +349,74 @@ __global__ void __launch_bounds__(kBlock) k_galerkin_y(BasisView B, GalerkinView
   for (int k = 0; k < 36; ++k) Y[idx * 36 + k] = acc[k];
 }
 
-// A_ij (12x12) = sum over entries (v, y) of phi_i(v) a_vi (x) Y_y ; one CTA per
-// coarse block row i, 144 threads per neighbour block, several blocks at once.
+// A_ij (12x12) = sum over entries (v, y) of phi_i(v) a_vi (x) Y_y.  Pass 1:
+// one 144-thread team per chunk of at most kGalerkinChunk entries of one
+// coarse block (two teams per CTA), each thread owning one of the 144
+// outputs; the chunk's entry metadata is staged in shared memory.
 template <typename VT>
-__global__ void __launch_bounds__(288) k_galerkin_a(BasisView B, const int* __restrict__ hn_row,
-                                                    const int* __restrict__ hn, const int* __restrict__ ent_ptr,
-                                                    const int* __restrict__ ent_y, const int* __restrict__ ent_v,
-                                                    const double* __restrict__ ent_phi, int64_t ny,
-                                                    const VT* __restrict__ Y, int r, double* __restrict__ A) {
-  const int i = blockIdx.x;
+__global__ void __launch_bounds__(288) k_galerkin_chunk(BasisView B, const int* __restrict__ chunk_beg,
+                                                        const int* __restrict__ chunk_ptr,
+                                                        const int* __restrict__ slot_row, int nbk,
+                                                        const int* __restrict__ ent_ptr,
+                                                        const int* __restrict__ ent_y,
+                                                        const int* __restrict__ ent_v,
+                                                        const double* __restrict__ ent_phi, int nchunk,
+                                                        const VT* __restrict__ Y, VT* __restrict__ part) {
+  __shared__ int s_y[2][kGalerkinChunk];
+  __shared__ VT s_coef[2][kGalerkinChunk][4];
   const int team = threadIdx.x / 144, tt = threadIdx.x % 144;
-  const int row = tt / 12, colq = tt % 12;  // output (row, col) inside the 12x12 block
-  const int c = row >> 2, lp = row & 3;      // row = 4 c + l'
-  const int d = colq >> 2, l = colq & 3;     // col = 4 d + l
-  const double ox = B.origins[3 * i], oy = B.origins[3 * i + 1], oz = B.origins[3 * i + 2];
-  const int yk = (3 * c + d) * 4 + l;        // component of Y_vj
-  for (int s = hn_row[i] + team; s < hn_row[i + 1]; s += 2) {
-    const int j = hn[s];
-    VT acc = VT(0);
-    for (int p = ent_ptr[s]; p < ent_ptr[s + 1]; ++p) {
-      const int v = ent_v[p];
-      VT coef = (VT)ent_phi[p];
-      if (lp > 0) {
-        const Vec4d X = B.X[v];
-        coef *= (VT)(lp == 1 ? X.x - ox : lp == 2 ? X.y - oy : X.z - oz);
-      }
-      acc += coef * Y[(int64_t)ent_y[p] * 36 + yk];
+  const int chunk = blockIdx.x * 2 + team;
+  const bool active = chunk < nchunk;
+  int beg = 0, end = 0, i = 0;
+  if (active) {
+    // slot of this chunk: last slot whose first chunk is <= chunk (binary search)
+    int lo = 0, hi = nbk - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (chunk_ptr[mid] <= chunk) lo = mid; else hi = mid - 1;
     }
-    A[(int64_t)(12 * i + row) * r + 12 * j + colq] = (double)acc;
+    beg = chunk_beg[chunk];
+    end = min(beg + kGalerkinChunk, ent_ptr[lo + 1]);
+    i = slot_row[lo];
   }
+  if (active) {
+    const double ox = B.origins[3 * i], oy = B.origins[3 * i + 1], oz = B.origins[3 * i + 2];
+    for (int p = beg + tt; p < end; p += 144) {
+      const int q = p - beg;
+      const int v = ent_v[p];
+      const Vec4d X = B.X[v];
+      const double ph = ent_phi[p];
+      s_y[team][q] = ent_y[p];
+      s_coef[team][q][0] = (VT)ph;
+      s_coef[team][q][1] = (VT)(ph * (X.x - ox));
+      s_coef[team][q][2] = (VT)(ph * (X.y - oy));
+      s_coef[team][q][3] = (VT)(ph * (X.z - oz));
+    }
+  }
+  __syncthreads();
+  if (!active) return;
+  const int row = tt / 12, colq = tt % 12;  // row = 4 c + l', col = 4 d + l
+  const int c = row >> 2, lp = row & 3, d = colq >> 2, l = colq & 3;
+  const int yk = (3 * c + d) * 4 + l;
+  VT acc = VT(0);
+  const int cnt = end - beg;
+#pragma unroll 4
+  for (int q = 0; q < cnt; ++q) acc += s_coef[team][q][lp] * Y[(int64_t)s_y[team][q] * 36 + yk];
+  part[(int64_t)chunk * 144 + tt] = acc;
+}
+
+// Pass 2: each coarse block sums its chunks in order and writes A (float64)
+template <typename VT>
+__global__ void __launch_bounds__(144) k_galerkin_reduce(const int* __restrict__ chunk_ptr,
+                                                         const int* __restrict__ slot_row,
+                                                         const int* __restrict__ hn, const VT* __restrict__ part,
+                                                         int r, double* __restrict__ A) {
+  const int sl = blockIdx.x;
+  const int tt = threadIdx.x;
+  double acc = 0.0;
+  for (int ch = chunk_ptr[sl]; ch < chunk_ptr[sl + 1]; ++ch) acc += (double)part[(int64_t)ch * 144 + tt];
+  const int i = slot_row[sl], j = hn[sl];
+  A[(int64_t)(12 * i + tt / 12) * r + 12 * j + tt % 12] = acc;
 }
 
 // ---- dense Cholesky (float64), blocked right-looking ---------------------------------------
@@ -451,64 +505,112 @@ __global__ void k_syrk_tiles(double* __restrict__ A, int r, int k, int ntiles) {
   }
 }
 
-// W = L^{-1} column block by column block: for tile column k,
-// W_kk = L_kk^{-1}; W_ik = -L_ii^{-1} sum_{k<=q<i} L_iq W_qk, tile rows in order.
-// One CTA (32x32 threads) per tile column, walking down its tile rows.
+// W = L^{-1} by a right-looking blocked solve of L W = I over tile rows:
+// step i solves the tile row in place, W_ic = L_ii^{-1} B_ic for c <= i
+// (k_trinv_solve), then updates the rows below, B_qc -= L_qi W_ic for q > i,
+// c <= i (k_trinv_update).  W starts as the identity; its upper part stays 0.
 template <typename VT>
-__global__ void k_trinv_column(const double* __restrict__ L, int r, int ntiles, VT* __restrict__ W,
-                               VT* __restrict__ WT) {
-  const int k = blockIdx.x;
-  __shared__ double Lii[NB][NB + 1];
-  __shared__ double Acc[NB][NB + 1];
+__global__ void k_eye(VT* __restrict__ W, int r) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < r) W[k * r + k] = VT(1);
+}
+
+template <typename VT>
+__global__ void k_trinv_solve(const double* __restrict__ L, int r, int i, VT* __restrict__ W) {
+  __shared__ VT Lii[NB][NB + 1];
+  __shared__ VT X[NB][NB + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int bk = k * NB;
-  const int nk = min(NB, r - bk);
-  for (int i = k; i < ntiles; ++i) {
-    const int bi = i * NB;
-    const int ni = min(NB, r - bi);
-    // Acc = (i == k) ? I : -sum_{q=k}^{i-1} L_iq W_qk
-    VT s = VT(0);
-    if (i == k) {
-      s = (ty == tx) ? VT(1) : VT(0);
-    } else if (ty < ni && tx < nk) {
-      const double* Lr = L + (int64_t)(bi + ty) * r;
-      for (int q = bk; q < bi; ++q) s -= (VT)Lr[q] * W[(int64_t)q * r + bk + tx];
+  const int c = blockIdx.x;  // column tile, c <= i
+  const int bi = i * NB, bc = c * NB;
+  const int ni = min(NB, r - bi), nc = min(NB, r - bc);
+  Lii[ty][tx] = (ty < ni && tx < ni) ? (VT)L[(int64_t)(bi + ty) * r + bi + tx] : (ty == tx ? VT(1) : VT(0));
+  X[ty][tx] = (ty < ni && tx < nc) ? W[(int64_t)(bi + ty) * r + bc + tx] : VT(0);
+  __syncthreads();
+  if (ty == 0 && tx < nc) {
+    for (int rr = 0; rr < ni; ++rr) {
+      VT v = X[rr][tx];
+      for (int q = 0; q < rr; ++q) v -= Lii[rr][q] * X[q][tx];
+      X[rr][tx] = v / Lii[rr][rr];
     }
-    Acc[ty][tx] = (double)s;
-    Lii[ty][tx] = (ty < ni && tx < ni) ? L[(int64_t)(bi + ty) * r + bi + tx] : (ty == tx ? 1.0 : 0.0);
-    __syncthreads();
-    // solve L_ii X = Acc by forward substitution, one thread per column
-    if (ty == 0 && tx < nk) {
-      for (int rr = 0; rr < ni; ++rr) {
-        double v = Acc[rr][tx];
-        for (int q = 0; q < rr; ++q) v -= Lii[rr][q] * Acc[q][tx];
-        Acc[rr][tx] = v / Lii[rr][rr];
-      }
-    }
-    __syncthreads();
-    if (ty < ni && tx < nk) {
-      const VT w = (VT)Acc[ty][tx];
-      W[(int64_t)(bi + ty) * r + bk + tx] = w;
-      WT[(int64_t)(bk + tx) * r + bi + ty] = w;
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  if (ty < ni && tx < nc) W[(int64_t)(bi + ty) * r + bc + tx] = X[ty][tx];
+}
+
+// B_qc -= L_qi W_ic for q in (i, nt), c in [0, i]; one CTA (32x8 threads,
+// 4 outputs each) per (q, c) tile
+template <typename VT>
+__global__ void k_trinv_update(const double* __restrict__ L, int r, int i, int nt, VT* __restrict__ W) {
+  const int q = i + 1 + blockIdx.x / (i + 1);
+  const int c = blockIdx.x % (i + 1);
+  __shared__ VT Lq[NB][NB + 1];
+  __shared__ VT Wi[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int bq = q * NB, bi = i * NB, bc = c * NB;
+  const int nq = min(NB, r - bq), ni = min(NB, r - bi), nc = min(NB, r - bc);
+  for (int rr = ty; rr < NB; rr += 8) {
+    Lq[rr][tx] = (rr < nq && tx < ni) ? (VT)L[(int64_t)(bq + rr) * r + bi + tx] : VT(0);
+    Wi[rr][tx] = (rr < ni && tx < nc) ? W[(int64_t)(bi + rr) * r + bc + tx] : VT(0);
+  }
+  __syncthreads();
+  VT acc[4] = {VT(0), VT(0), VT(0), VT(0)};
+#pragma unroll 8
+  for (int k = 0; k < NB; ++k) {
+    const VT b = Wi[k][tx];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] += Lq[ty + 8 * u][k] * b;
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = ty + 8 * u;
+    if (rr < nq && tx < nc) W[(int64_t)(bq + rr) * r + bc + tx] -= acc[u];
+  }
+}
+
+// WT = W^T, 32x32 tiles through shared memory
+template <typename VT>
+__global__ void k_transpose(const VT* __restrict__ W, int r, VT* __restrict__ WT) {
+  __shared__ VT T[NB][NB + 1];
+  const int bx = blockIdx.x * NB, by = blockIdx.y * NB;
+  for (int k = threadIdx.y; k < NB; k += blockDim.y) {
+    const int rr = by + k, cc = bx + threadIdx.x;
+    T[k][threadIdx.x] = (rr < r && cc < r) ? W[(int64_t)rr * r + cc] : VT(0);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < NB; k += blockDim.y) {
+    const int rr = bx + k, cc = by + threadIdx.x;
+    if (rr < r && cc < r) WT[(int64_t)rr * r + cc] = T[threadIdx.x][k];
   }
 }
 
 // y = W x restricted to the lower (lower = 1: columns <= row) or upper
-// (lower = 0: columns >= row) triangle; one warp per row
+// (lower = 0: columns >= row) triangle, widened to 16-byte boundaries (W is
+// zero outside its triangle); one warp per row, 16-byte loads, unrolled
 template <typename VT>
 __global__ void __launch_bounds__(kBlock) k_trigemv(const VT* __restrict__ W, int r, int lower,
                                                     const VT* __restrict__ x, VT* __restrict__ y,
                                                     const PcgScalars* __restrict__ S) {
   if (S && S->done) return;
+  constexpr int EV = 16 / sizeof(VT);
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= r) return;
-  const int c0 = lower ? 0 : row, c1 = lower ? row + 1 : r;
-  const VT* Wr = W + (int64_t)row * r;
+  const int v0 = lower ? 0 : row / EV;
+  const int v1 = lower ? (row + EV) / EV : r / EV;
+  using V16 = typename std::conditional<sizeof(VT) == 4, float4, double2>::type;
+  const V16* Wr = reinterpret_cast<const V16*>(W + (int64_t)row * r);
+  const V16* xv = reinterpret_cast<const V16*>(x);
   VT acc = VT(0);
-  for (int c = c0 + lane; c < c1; c += 32) acc += Wr[c] * x[c];
+#pragma unroll 4
+  for (int c = v0 + lane; c < v1; c += 32) {
+    const V16 w = Wr[c];
+    const V16 b = xv[c];
+    if constexpr (sizeof(VT) == 4) {
+      acc += w.x * b.x + w.y * b.y + w.z * b.z + w.w * b.w;
+    } else {
+      acc += w.x * b.x + w.y * b.y;
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) y[row] = acc;
@@ -560,8 +662,13 @@ static mls_status galerkin_t(mls_ctx* ctx) {
                                                                B.ypair_row, B.ny, (VT*)ctx->yval); }
   mls_status st = cuda_check(ctx, cudaMemsetAsync(ctx->Ac, 0, sizeof(double) * r * r, ctx->stream), "Ac clear");
   if (st != MLS_OK) return st;
-  { ++ctx->launches; k_galerkin_a<VT><<<B.m, 288, 0, ctx->stream>>>(basis_view(ctx), B.hn_row, B.hn, B.ent_ptr, B.ent_y, B.ent_v,
-                                                 B.ent_phi, B.ny, (const VT*)ctx->yval, r, ctx->Ac); }
+  if (B.nchunk > 0) {
+    { ++ctx->launches; k_galerkin_chunk<VT><<<(B.nchunk + 1) / 2, 288, 0, ctx->stream>>>(
+        basis_view(ctx), B.chunk_beg, B.chunk_ptr, B.slot_row, B.nb, B.ent_ptr, B.ent_y, B.ent_v, B.ent_phi,
+        B.nchunk, (const VT*)ctx->yval, (VT*)ctx->gpart); }
+    { ++ctx->launches; k_galerkin_reduce<VT><<<B.nb, 144, 0, ctx->stream>>>(B.chunk_ptr, B.slot_row, B.hn,
+                                                                            (const VT*)ctx->gpart, r, ctx->Ac); }
+  }
   return cuda_check(ctx, cudaGetLastError(), "galerkin");
 }
 
@@ -589,7 +696,14 @@ static mls_status factor_t(mls_ctx* ctx) {
   if (st != MLS_OK) return st;
   st = cuda_check(ctx, cudaMemsetAsync(ctx->LinvT, 0, (size_t)r * r * sizeof(VT), ctx->stream), "WT clear");
   if (st != MLS_OK) return st;
-  { ++ctx->launches; k_trinv_column<VT><<<nt, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, nt, (VT*)ctx->Linv, (VT*)ctx->LinvT); }
+  { ++ctx->launches; k_eye<VT><<<(r + 255) / 256, 256, 0, ctx->stream>>>((VT*)ctx->Linv, r); }
+  for (int i = 0; i < nt; ++i) {
+    { ++ctx->launches; k_trinv_solve<VT><<<i + 1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, i, (VT*)ctx->Linv); }
+    if (i + 1 < nt) {
+      { ++ctx->launches; k_trinv_update<VT><<<(nt - i - 1) * (i + 1), dim3(32, 8), 0, ctx->stream>>>(ctx->Ac, r, i, nt, (VT*)ctx->Linv); }
+    }
+  }
+  { ++ctx->launches; k_transpose<VT><<<dim3(nt, nt), dim3(32, 8), 0, ctx->stream>>>((const VT*)ctx->Linv, r, (VT*)ctx->LinvT); }
   st = cuda_check(ctx, cudaGetLastError(), "triangular inverse");
   if (st != MLS_OK) return st;
   int info = 0;

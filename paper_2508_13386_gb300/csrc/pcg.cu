@@ -39,6 +39,47 @@ __device__ __forceinline__ void spmv_row(const SellView& A, const MT* __restrict
   y[0] = y0; y[1] = y1; y[2] = y2;
 }
 
+// One CTA of kSpmvWarps warps per 32-row slice: warp w takes the slots
+// k = w, w + kSpmvWarps, ... of every row, so each value load stays a
+// coalesced 32-lane access and no load is duplicated; partial products are
+// summed through shared memory.  Returns true in warp 0, whose lane holds
+// the finished row (row = slice * 32 + lane) in y.
+constexpr int kSpmvWarps = 4;
+
+template <typename VT, typename MT>
+__device__ __forceinline__ bool spmv_slice(const SellView& A, const MT* __restrict__ val, int slice,
+                                           const Vec4<VT>* __restrict__ x, VT (&y)[3]) {
+  __shared__ VT red[kSpmvWarps][3][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = slice * 32 + lane;
+  const int len = row < A.n ? A.row_len[row] : 0;
+  const int g0 = A.slice_ptr[slice];
+  VT y0 = VT(0), y1 = VT(0), y2 = VT(0);
+#pragma unroll 2
+  for (int k = w; k < len; k += kSpmvWarps) {
+    const int64_t g = g0 + k;
+    const int c = __ldg(A.col + g * 32 + lane);
+    const Vec4<VT> xv = x[c];
+    const MT* v = val + g * 288 + lane;
+    y0 += load_as<VT>(v[0]) * xv.x + load_as<VT>(v[32]) * xv.y + load_as<VT>(v[64]) * xv.z;
+    y1 += load_as<VT>(v[96]) * xv.x + load_as<VT>(v[128]) * xv.y + load_as<VT>(v[160]) * xv.z;
+    y2 += load_as<VT>(v[192]) * xv.x + load_as<VT>(v[224]) * xv.y + load_as<VT>(v[256]) * xv.z;
+  }
+  red[w][0][lane] = y0;
+  red[w][1][lane] = y1;
+  red[w][2][lane] = y2;
+  __syncthreads();
+  if (w != 0) return false;
+#pragma unroll
+  for (int q = 1; q < kSpmvWarps; ++q) {
+    y0 += red[q][0][lane];
+    y1 += red[q][1][lane];
+    y2 += red[q][2][lane];
+  }
+  y[0] = y0; y[1] = y1; y[2] = y2;
+  return true;
+}
+
 template <typename VT>
 __device__ __forceinline__ Vec4<VT> dinv_apply(const VT* __restrict__ dinv, int row, const Vec4<VT>& r, VT omega) {
   const VT* D = dinv + (int64_t)row * 9;
@@ -49,27 +90,26 @@ __device__ __forceinline__ Vec4<VT> dinv_apply(const VT* __restrict__ dinv, int 
 
 // ---- plain product / residual ---------------------------------------------------------
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(kBlock) k_spmv(SellView A, const MT* __restrict__ val,
-                                                 const Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ y) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= A.n) return;
+__global__ void __launch_bounds__(32 * kSpmvWarps) k_spmv(SellView A, const MT* __restrict__ val,
+                                                          const Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ y) {
   VT r[3];
-  spmv_row<VT, MT>(A, val, row, x, r);
-  y[row] = Vec4<VT>{r[0], r[1], r[2], VT(0)};
+  if (!spmv_slice<VT, MT>(A, val, blockIdx.x, x, r)) return;
+  const int row = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (row < A.n) y[row] = Vec4<VT>{r[0], r[1], r[2], VT(0)};
 }
 
 // out = b - H x
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(kBlock) k_residual(SellView A, const MT* __restrict__ val,
-                                                     const Vec4<VT>* __restrict__ b,
-                                                     const Vec4<VT>* __restrict__ x,
-                                                     Vec4<VT>* __restrict__ out,
-                                                     const PcgScalars* __restrict__ S) {
+__global__ void __launch_bounds__(32 * kSpmvWarps) k_residual(SellView A, const MT* __restrict__ val,
+                                                              const Vec4<VT>* __restrict__ b,
+                                                              const Vec4<VT>* __restrict__ x,
+                                                              Vec4<VT>* __restrict__ out,
+                                                              const PcgScalars* __restrict__ S) {
   if (S && S->done) return;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= A.n) return;
   VT r[3];
-  spmv_row<VT, MT>(A, val, row, x, r);
+  if (!spmv_slice<VT, MT>(A, val, blockIdx.x, x, r)) return;
+  const int row = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (row >= A.n) return;
   const Vec4<VT> bb = b[row];
   out[row] = Vec4<VT>{bb.x - r[0], bb.y - r[1], bb.z - r[2], VT(0)};
 }
@@ -145,16 +185,16 @@ __global__ void __launch_bounds__(kBlock) k_pcg_rz(int n, const Vec4<VT>* __rest
 
 // w = H z; p = z + beta p; q = w + beta q; alpha = r.z / p.q
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(kBlock) k_pcg_spmv(SellView A, const MT* __restrict__ val,
-                                                     const Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p,
-                                                     Vec4<VT>* __restrict__ q, GridReduce gr,
-                                                     PcgScalars* __restrict__ S) {
+__global__ void __launch_bounds__(32 * kSpmvWarps) k_pcg_spmv(SellView A, const MT* __restrict__ val,
+                                                              const Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p,
+                                                              Vec4<VT>* __restrict__ q, GridReduce gr,
+                                                              PcgScalars* __restrict__ S) {
   if (S->done) return;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.x * 32 + (threadIdx.x & 31);
   double acc[1] = {0.0};
-  if (row < A.n) {
-    VT w[3];
-    spmv_row<VT, MT>(A, val, row, z, w);
+  VT w[3];
+  const bool mine = spmv_slice<VT, MT>(A, val, blockIdx.x, z, w);
+  if (mine && row < A.n) {
     const VT beta = (VT)S->beta;
     const Vec4<VT> zv = z[row], pv = p[row], qv = q[row];
     const Vec4<VT> pn{zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, VT(0)};
@@ -217,7 +257,7 @@ static inline int nblk(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
 template <typename VT, typename MT>
 static void spmv_t(mls_ctx* ctx, const void* x, void* y) {
-  { ++ctx->launches; k_spmv<VT, MT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
+  { ++ctx->launches; k_spmv<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
                                                            (const Vec4<VT>*)x, (Vec4<VT>*)y); }
 }
 
@@ -232,7 +272,7 @@ mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y) {
 
 template <typename VT, typename MT>
 mls_status launch_residual_t(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S) {
-  { ++ctx->launches; k_residual<VT, MT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
+  { ++ctx->launches; k_residual<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
                                                                (const Vec4<VT>*)b, (const Vec4<VT>*)x,
                                                                (Vec4<VT>*)out, S); }
   return cuda_check(ctx, cudaGetLastError(), "k_residual");
@@ -262,7 +302,8 @@ template <typename VT, typename MT>
 static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res) {
   const int n = ctx->n;
   const int nb = nblk(n);
-  if (nb > kMaxPartials) return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
+  if (nb > kMaxPartials || ctx->n_slices > kMaxPartials)
+    return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
   const bool jacobi = ctx->opt.preconditioner == MLS_PRECOND_BLOCK_JACOBI;
   if (!jacobi && !ctx->coarse_ready) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_build_coarse");
   auto* b = (const Vec4<VT>*)ctx->vb;
@@ -288,7 +329,7 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
   for (;;) {
     for (int c = 0; c < chunk; ++c) {
       int tk = prof_begin(ctx, MLS_PROF_SPMV);
-      { ++ctx->launches; k_pcg_spmv<VT, MT><<<nb, kBlock, 0, ctx->stream>>>(A, val, z, p, q, ctx->red, S); }
+      { ++ctx->launches; k_pcg_spmv<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(A, val, z, p, q, ctx->red, S); }
       prof_end(ctx, tk);
       tk = prof_begin(ctx, MLS_PROF_PCG_UPDATE);
       { ++ctx->launches; k_pcg_update<VT><<<nb, kBlock, 0, ctx->stream>>>(n, x, r, z, p, q, dinv, jacobi ? 1 : 0, ctx->red, S); }
