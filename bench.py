@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2, help="plain FP64 steps timed for comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end pass")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only warm-up and timed steps (for ncu: the timed steps sit in NVTX range 'mls_timed')")
     return ap.parse_args()
 
 
@@ -235,11 +237,14 @@ def main():
         advance(ours, x, v)
     torch.cuda.synchronize()
     # parity of the mixed step against the FP64 GPU path from the same state
-    fp64 = make("fp64", "jacobi")
-    x_chk, v_chk = x.clone(), v.clone()
-    dx64, st64 = fp64.newton_step(x_chk, v_chk, h)
-    dxm, stm = ours.newton_step(x_chk, v_chk, h)
-    disp_err = float(torch.linalg.norm(dxm - dx64) / torch.linalg.norm(dx64))
+    disp_err = None
+    fp64 = None
+    if not args.profile_run:
+        fp64 = make("fp64", "jacobi")
+        x_chk, v_chk = x.clone(), v.clone()
+        dx64, st64 = fp64.newton_step(x_chk, v_chk, h)
+        dxm, stm = ours.newton_step(x_chk, v_chk, h)
+        disp_err = float(torch.linalg.norm(dxm - dx64) / torch.linalg.norm(dx64))
     torch.cuda.synchronize()
     # timed region
     ours.profile_enable(["spmv"])
@@ -251,9 +256,11 @@ def main():
     with ClockSampler(local) as clocks:
         for k in range(args.steps):
             flush.zero_()
+            torch.cuda.nvtx.range_push("mls_timed")
             ev[k][0].record(stream)
             _, st = ours.newton_step(x, v, h, dx=dx)
             ev[k][1].record(stream)
+            torch.cuda.nvtx.range_pop()
             v.copy_(dx / h)
             x.add_(dx)
             stats.append(st)
@@ -268,15 +275,17 @@ def main():
         total_s = float(t.item())
     value = world * args.steps / total_s
     # per kernel-class breakdown on one extra (untimed) step from the same state
-    ours.profile_enable(["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky"])
-    xb, vb = x.clone(), v.clone()
-    _, st_b = ours.newton_step(xb, vb, h)
-    breakdown = {k: {"ms": round(ms, 3), "launches": n} for k, (ms, n) in ours.profile_read().items() if n}
-    ours.profile_enable([])
+    breakdown = None
+    if not args.profile_run:
+        ours.profile_enable(["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky"])
+        xb, vb = x.clone(), v.clone()
+        _, st_b = ours.newton_step(xb, vb, h)
+        breakdown = {k: {"ms": round(ms, 3), "launches": n} for k, (ms, n) in ours.profile_read().items() if n}
+        ours.profile_enable([])
     # plain FP64 block-Jacobi PCG from the current state (same trajectory)
     fp64_ms = []
     fp64_stats = []
-    for k in range(args.fp64_steps):
+    for k in range(0 if args.profile_run else args.fp64_steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -291,7 +300,7 @@ def main():
     xh = x.cpu().numpy().copy()
     vh = v.cpu().numpy().copy()
     dxh = np.empty_like(xh)
-    e2e_steps = 0 if args.no_e2e else max(2, args.steps // 2)
+    e2e_steps = 0 if (args.no_e2e or args.profile_run) else max(2, args.steps // 2)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(e2e_steps):
@@ -313,7 +322,7 @@ def main():
             dist.barrier()
         return
     cpu = None
-    if world == 1 and not args.no_cpu:
+    if world == 1 and not args.no_cpu and not args.profile_run:
         nit = float(np.mean([s["newton_iters"] for s in fp64_stats])) if fp64_stats else REF_NEWTON
         npcg = float(np.mean([s["pcg_iters"] for s in fp64_stats])) / max(nit, 1) if fp64_stats else REF_PCG
         rate, desc, spent = cpu_sample(scene, nit, npcg)

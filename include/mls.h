@@ -103,6 +103,7 @@ typedef struct mls_stats {
   double grad_norm;        /* |g|_2 at the last evaluated iterate */
   double energy;           /* E at the returned iterate */
   int64_t kernel_launches; /* CUDA kernels this call launched */
+  int warm_start_used;     /* 1 if the step started from the network's prediction */
 } mls_stats;
 
 typedef struct mls_ctx mls_ctx;
@@ -259,6 +260,79 @@ mls_status mls_profile_enable(mls_ctx* ctx, uint32_t mask);
 /* Read accumulated totals: ms[MLS_PROF_COUNT] milliseconds and
  * launches[MLS_PROF_COUNT] launch counts (HOST arrays, either nullable). */
 mls_status mls_profile_read(mls_ctx* ctx, double* ms, int64_t* launches);
+
+/* ---- Learned warm start: MLP trained and run by the library's kernels ----
+ * Not in the paper (an extension): a 3-layer MLP, h1 = relu(x W1^T + b1),
+ * h2 = relu(h1 W2^T + b2), y = h2 W3^T + b3, maps coarse-state features to
+ * the coarse increment of a timestep.  Products run on tensor cores with
+ * BF16 weights and operands and FP32 accumulation; parameters are kept as
+ * FP32 master copies updated by Adam (beta1 0.9, beta2 0.999, eps 1e-8) on
+ * the loss 1/(2B) sum_b |y_b - t_b|^2.  Parameter layout (one flat FP32
+ * array): W1 [h][in], b1 [h], W2 [h][h], b2 [h], W3 [out][h], b3 [out]. */
+typedef struct mls_mlp mls_mlp;
+
+/* Create a network with the given widths, batches of up to max_batch rows,
+ * initial parameters init_params (HOST, flat layout above), kernels queued
+ * on stream (cudaStream_t, NULL = legacy default). */
+mls_status mls_mlp_create(mls_mlp** out, int32_t n_in, int32_t n_hidden, int32_t n_out,
+                          int32_t max_batch, const float* init_params, void* stream);
+mls_status mls_mlp_destroy(mls_mlp* mlp);
+/* Number of parameters (length of the flat array). */
+int64_t mls_mlp_param_count(const mls_mlp* mlp);
+/* Y [batch][out] = net(X [batch][in]); DEVICE float32 arrays; any batch size. */
+mls_status mls_mlp_forward(mls_mlp* mlp, const float* X, int32_t batch, float* Y);
+/* Loss gradient for one batch (batch <= max_batch) into grad_out (DEVICE,
+ * flat layout, nullable); *loss_out (HOST, nullable) receives the loss. */
+mls_status mls_mlp_gradients(mls_mlp* mlp, const float* X, const float* T, int32_t batch,
+                             float* grad_out, double* loss_out);
+/* One Adam update with the given gradient (DEVICE, flat layout). */
+mls_status mls_mlp_adam_step(mls_mlp* mlp, const float* grad, float lr);
+/* Train on minibatches: rows order[0..batch), order[batch..2 batch), ... of
+ * X [n_samples][in] with targets T [n_samples][out] (DEVICE), order a DEVICE
+ * int32 array of n_order sample indices (a shuffled epoch, drawn by the
+ * caller); one Adam step per full minibatch.  *loss_out (HOST, nullable):
+ * mean minibatch loss. */
+mls_status mls_mlp_train(mls_mlp* mlp, const float* X, const float* T, int32_t n_samples,
+                         const int32_t* order, int32_t n_order, int32_t batch, float lr,
+                         double* loss_out);
+/* Copy the FP32 master parameters to HOST. */
+mls_status mls_mlp_get_params(mls_mlp* mlp, float* host_params);
+/* Standardise inputs and targets inside the network: inputs enter as
+ * (x - mean_in) / std_in, training targets as (t - mean_out) / std_out, and
+ * mls_mlp_forward returns y std_out + mean_out.  DEVICE float arrays (copied);
+ * non-positive standard deviations are treated as 1.  All NULL: no
+ * standardisation. */
+mls_status mls_mlp_set_normalization(mls_mlp* mlp, const float* mean_in, const float* std_in,
+                                     const float* mean_out, const float* std_out);
+/* Column means and standard deviations (population) of DEVICE X [n][d]
+ * into DEVICE mean [d], sd [d]. */
+mls_status mls_mlp_column_stats(const float* X, int32_t n, int32_t d, float* mean, float* sd,
+                                void* stream);
+
+/* ---- Warm start from the coarse state ------------------------------------
+ * Coarse coordinates q(x) = (U^T M U)^{-1} U^T M (x - X) of the uploaded SMS
+ * basis.  While enabled, every mls_newton_step records q(x^t) in a history and
+ * forms the features f = [q^t - q^{t-1}, q^{t-1} - q^{t-2}, q(X + h^2 g) - q(X)];
+ * when recording it also computes, after the step, the target
+ * dq = (U^T H U)^{-1} U^T H (x^{t+1} - x_tilde) (the Galerkin coarse
+ * projection of the step, H and its coarse factor taken at the first Newton
+ * iterate; requires coarse_refresh >= the Newton count).  With a network
+ * attached (3r inputs, r outputs, r = 12 handles) the step starts from
+ * x_tilde + U dq_hat, dq_hat = net(f), when that point is feasible and has
+ * lower energy than x_tilde; otherwise from x_tilde.  The converged step
+ * does not depend on the start.  Not in the paper. */
+/* enable: 0 off, 1 history/features (and prediction when a network is
+ * attached), 2 as 1 plus recording targets (two-level preconditioner only).
+ * The first enable factors U^T M U (float64 Cholesky). */
+mls_status mls_warm_start_enable(mls_ctx* ctx, int enable);
+/* Forget the history (start of a new trajectory). */
+mls_status mls_warm_start_reset(mls_ctx* ctx);
+/* Attach a trained network (not owned; NULL detaches). */
+mls_status mls_warm_start_attach(mls_ctx* ctx, mls_mlp* mlp);
+/* Copy the last step's features (DEVICE float [3r]) and target (DEVICE float [r]). */
+mls_status mls_warm_start_sample(mls_ctx* ctx, float* features, float* target);
+/* q(x) for DEVICE x [n][3] into DEVICE q [m][12] (float64). */
+mls_status mls_coarse_project(mls_ctx* ctx, const double* x, double* q);
 
 #ifdef __cplusplus
 }

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 
-__all__ = ["Solver", "MLSError", "lib"]
+__all__ = ["Solver", "MLP", "MLSError", "lib"]
 
 lib = None
 
@@ -253,6 +253,27 @@ class Solver:
                                        C.byref(E), C.byref(feas)))
         return E.value, bool(feas.value)
 
+    # ---- warm start -------------------------------------------------------------
+    def warm_start_enable(self, enable=True, record=False):
+        self._check(self._l.mls_warm_start_enable(self._ctx, (2 if record else 1) if enable else 0))
+
+    def warm_start_reset(self):
+        self._check(self._l.mls_warm_start_reset(self._ctx))
+
+    def warm_start_attach(self, mlp):
+        self._check(self._l.mls_warm_start_attach(self._ctx, mlp._h if mlp is not None else None))
+        self._attached = mlp  # keep the network alive while attached
+
+    def warm_start_sample(self, features, target):
+        self._check(self._l.mls_warm_start_sample(self._ctx, C.c_void_p(features.data_ptr()),
+                                                  C.c_void_p(target.data_ptr())))
+
+    def coarse_project(self, x):
+        import torch
+        q = torch.empty(self.m, 12, dtype=torch.float64, device=x.device)
+        self._check(self._l.mls_coarse_project(self._ctx, _dev(x, (self.n, 3)), _dev(q)))
+        return q
+
     def profile_enable(self, classes=()):
         mask = 0
         for c in classes:
@@ -269,3 +290,71 @@ class Solver:
         a = C.c_double()
         self._check(self._l.mls_ccd_bound(self._ctx, _dev(x, (self.n, 3)), _dev(d, (self.n, 3)), C.byref(a)))
         return a.value
+
+
+class MLP:
+    """A network trained and run by the library's kernels (``mls_mlp_*``)."""
+
+    def __init__(self, sizes, init_params, max_batch=256, stream=None):
+        self._l = _get_lib()
+        self.sizes = list(sizes)
+        flat = np.concatenate([np.asarray(p, dtype=np.float32).ravel() for p in init_params])
+        self._h = C.c_void_p()
+        st = self._l.mls_mlp_create(C.byref(self._h), sizes[0], sizes[1], sizes[-1], int(max_batch),
+                                    flat.ctypes.data_as(C.c_void_p),
+                                    None if stream is None else C.c_void_p(stream.cuda_stream))
+        if st != _lib.MLS_OK:
+            raise MLSError(st, "mls_mlp_create failed")
+        self.n_params = int(self._l.mls_mlp_param_count(self._h))
+
+    def close(self):
+        if self._h:
+            self._l.mls_mlp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _p(t):
+        return C.c_void_p(t.data_ptr())
+
+    def _ok(self, st, what):
+        if st != _lib.MLS_OK:
+            raise MLSError(st, what)
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty(X.shape[0], self.sizes[-1], dtype=torch.float32, device=X.device)
+        self._ok(self._l.mls_mlp_forward(self._h, self._p(X), X.shape[0], self._p(Y)), "forward")
+        return Y
+
+    def set_normalization(self, mean_in, std_in, mean_out, std_out):
+        self._ok(self._l.mls_mlp_set_normalization(self._h, self._p(mean_in), self._p(std_in),
+                                                   self._p(mean_out), self._p(std_out)), "normalization")
+
+    def train_epoch(self, X, T, order, batch, lr):
+        loss = C.c_double()
+        self._ok(self._l.mls_mlp_train(self._h, self._p(X), self._p(T), X.shape[0], self._p(order),
+                                       order.shape[0], int(batch), C.c_float(lr), C.byref(loss)), "train")
+        return loss.value
+
+    def params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        self._ok(self._l.mls_mlp_get_params(self._h, out.ctypes.data_as(C.c_void_p)), "get_params")
+        return out
+
+
+def column_stats(X):
+    """Column mean and standard deviation of a float32 CUDA tensor (library kernel)."""
+    import torch
+    mean = torch.empty(X.shape[1], dtype=torch.float32, device=X.device)
+    sd = torch.empty_like(mean)
+    st = _get_lib().mls_mlp_column_stats(C.c_void_p(X.data_ptr()), X.shape[0], X.shape[1],
+                                         C.c_void_p(mean.data_ptr()), C.c_void_p(sd.data_ptr()), None)
+    if st != _lib.MLS_OK:
+        raise MLSError(st, "column_stats")
+    return mean, sd

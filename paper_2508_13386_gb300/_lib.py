@@ -49,6 +49,7 @@ class Stats(C.Structure):
         ("grad_norm", C.c_double),
         ("energy", C.c_double),
         ("kernel_launches", C.c_int64),
+        ("warm_start_used", C.c_int),
     ]
 
     def as_dict(self):
@@ -85,6 +86,21 @@ SIGNATURES = {
     "mls_ccd_bound": [_P, _P, _P, C.POINTER(_D)],
     "mls_profile_enable": [_P, C.c_uint32],
     "mls_profile_read": [_P, _P, _P],
+    "mls_mlp_create": [C.POINTER(_P), _I32, _I32, _I32, _I32, _P, _P],
+    "mls_mlp_destroy": [_P],
+    "mls_mlp_param_count": [_P],
+    "mls_mlp_forward": [_P, _P, _I32, _P],
+    "mls_mlp_gradients": [_P, _P, _P, _I32, _P, C.POINTER(_D)],
+    "mls_mlp_adam_step": [_P, _P, C.c_float],
+    "mls_mlp_train": [_P, _P, _P, _I32, _P, _I32, _I32, C.c_float, C.POINTER(_D)],
+    "mls_mlp_get_params": [_P, _P],
+    "mls_mlp_set_normalization": [_P, _P, _P, _P, _P],
+    "mls_mlp_column_stats": [_P, _I32, _I32, _P, _P, _P],
+    "mls_warm_start_enable": [_P, _I],
+    "mls_warm_start_reset": [_P],
+    "mls_warm_start_attach": [_P, _P],
+    "mls_warm_start_sample": [_P, _P, _P],
+    "mls_coarse_project": [_P, _P, _P],
 }
 PROF_CLASSES = ["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky",
                 "linesearch"]
@@ -99,5 +115,5 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name, args in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = C.c_char_p if name == "mls_last_error" else C.c_int
+        fn.restype = {"mls_last_error": C.c_char_p, "mls_mlp_param_count": C.c_int64}.get(name, C.c_int)
     return lib

@@ -117,6 +117,12 @@ void prof_flush(mls_ctx* ctx) {
 static void free_all(mls_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
+  ctx->Am = nullptr; ctx->Wm = ctx->WmT = ctx->ws_c = ctx->ws_c2 = ctx->ws_tmp = nullptr;
+  ctx->ws_hist = ctx->ws_qg = ctx->ws_qtilde = ctx->ws_qnext = nullptr;
+  ctx->ws_feat = ctx->ws_target = ctx->ws_pred = nullptr;
+  ctx->ws_hsave = nullptr;
+  ctx->ws_ready = ctx->ws_enabled = ctx->ws_hist_valid = ctx->ws_record = false;
+  ctx->ws_mlp = nullptr;
   ctx->basis = Basis{};
   ctx->has_basis = false;
   ctx->coarse_ready = false;
@@ -368,6 +374,8 @@ mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n, const double* X, int32_t t, 
   if ((st = up((void**)&ctx->vt_ptr, vt_ptr.data(), sizeof(int) * (n + 1))) != MLS_OK) return st;
   if ((st = up((void**)&ctx->vt_code, vt_code.data(), sizeof(int) * 4 * (size_t)t)) != MLS_OK) return st;
   ctx->mass_min = *std::min_element(h_mass.begin(), h_mass.end());
+  ctx->h_mass = h_mass;
+  ctx->h_X.assign(X, X + 3 * (size_t)n);
   ctx->n_slices = n_slices;
   ctx->n_groups = n_groups;
   ctx->nnzb = nnzb;
@@ -393,7 +401,7 @@ static mls_status alloc_state(mls_ctx* ctx) {
   if ((st = dalloc(ctx, &ctx->hval, (size_t)storage_bytes(ctx) * 288 * ctx->n_groups)) != MLS_OK) return st;
   const int vb = solve_bytes(ctx);
   if ((st = dalloc(ctx, &ctx->dinv, (size_t)vb * 9 * n)) != MLS_OK) return st;
-  void** sv[] = {&ctx->vb, &ctx->vx, &ctx->vr, &ctx->vz, &ctx->vp, &ctx->vq, &ctx->vw};
+  void** sv[] = {&ctx->vb, &ctx->vx, &ctx->vr, &ctx->vz, &ctx->vp, &ctx->vq, &ctx->vw, &ctx->vz2};
   for (void** b : sv)
     if ((st = dalloc(ctx, b, (size_t)vb * 4 * n)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->pcg, sizeof(PcgScalars))) != MLS_OK) return st;
@@ -450,6 +458,11 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
   }
   const bool two_level = ctx->opt.preconditioner == MLS_PRECOND_TWO_LEVEL;
   if (two_level && !ctx->has_basis) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_upload_basis");
+  {
+    int used = 0;
+    if ((st = warm_start_begin(ctx, &used)) != MLS_OK) return st;
+    S.warm_start_used = used;
+  }
   const double eta_floor = ctx->opt.precision == MLS_FP64 ? 1e-13 : 1e-6;
   double g0 = -1.0;
   mls_status result = MLS_ENOTCONV;
@@ -468,6 +481,7 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
         S.coarse_builds++;
       }
     }
+    if (it == 0 && (st = warm_start_first_iteration(ctx)) != MLS_OK) return st;
     double eta = std::min(ctx->opt.pcg_rtol, std::sqrt(gnorm / g0));
     eta = std::max(eta, eta_floor);
     // absolute floor: H >= M, so |d - d*|_2 <= |r|_2 / m_min; a residual below
@@ -521,6 +535,7 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
     if ((st = launch_axpy_state(ctx, ctx->xk, ctx->dir, alpha)) != MLS_OK) return st;
   }
   if ((st = launch_energy(ctx, ctx->xk, ctx->tmp4, 0.0, &E, &infeasible)) != MLS_OK) return st;
+  if (result == MLS_OK && (st = warm_start_end(ctx)) != MLS_OK) return st;
   prof_flush(ctx);
   S.energy = E;
   if (stats) *stats = S;
@@ -590,9 +605,18 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
     Basis& B = ctx->basis;
     void* old[] = {B.vrow, B.vh, B.vphi, B.hrow, B.hv, B.hphi, B.origins, B.yrow, B.yh, B.yslot, B.hn_row, B.hn,
                    B.ent_ptr, B.ent_y, B.ent_v, B.ent_phi, B.ypair_row, B.chunk_ptr, B.chunk_beg, B.slot_row,
+                   B.vcoef, B.hcoef, B.rchunk_handle, B.rchunk_beg, B.rchunk_ptr, B.rpart, B.rcount,
                    ctx->gpart, ctx->yval, ctx->Ac, ctx->Acopy,
-                   ctx->Linv, ctx->LinvT, ctx->cvec, ctx->cvec2, ctx->chol_info};
+                   ctx->Linv, ctx->LinvT, ctx->cvec, ctx->cvec2, ctx->chol_info, ctx->chol_tinv,
+                   ctx->Am, ctx->Wm, ctx->WmT, ctx->ws_c, ctx->ws_c2, ctx->ws_tmp, ctx->ws_hist, ctx->ws_qg,
+                   ctx->ws_qtilde, ctx->ws_qnext, ctx->ws_feat, ctx->ws_target, ctx->ws_pred, ctx->ws_hsave};
     for (void* p : old) dfree(ctx, p);
+    ctx->Am = nullptr; ctx->Wm = ctx->WmT = ctx->ws_c = ctx->ws_c2 = ctx->ws_tmp = nullptr;
+    ctx->ws_hist = ctx->ws_qg = ctx->ws_qtilde = ctx->ws_qnext = nullptr;
+    ctx->ws_feat = ctx->ws_target = ctx->ws_pred = nullptr;
+    ctx->ws_hsave = nullptr;
+    ctx->ws_ready = ctx->ws_enabled = ctx->ws_hist_valid = ctx->ws_record = false;
+    ctx->ws_mlp = nullptr;
     ctx->basis = Basis{};
     ctx->has_basis = false;
     ctx->coarse_ready = false;

@@ -34,6 +34,7 @@ constexpr int kBlock = 256;
 constexpr int kSlice = 32;
 constexpr int kMaxPartials = 8192;
 constexpr int kGalerkinChunk = 128;
+constexpr int kRestrictChunk = 256;
 
 // offsets of the 10 upper 3x3 blocks inside the 78-value element Hessian
 // (order (0,0),(0,1),(0,2),(0,3),(1,1),(1,2),(1,3),(2,2),(2,3),(3,3))
@@ -184,10 +185,21 @@ struct Basis {
   int* chunk_beg = nullptr;   // [nchunk] first entry of each chunk
   int* slot_row = nullptr;    // [nb] coarse block row i of each block
   int nchunk = 0;
-  std::vector<int> h_vrow, h_hrow;
+  void* vcoef = nullptr;      // [nnz] Vec4 (phi, phi a) per (vertex, handle), solve precision
+  void* hcoef = nullptr;      // [nnz] same, handle-major
+  int* rchunk_handle = nullptr;  // restriction chunks
+  int* rchunk_beg = nullptr;
+  int* rchunk_ptr = nullptr;  // [m+1]
+  double* rpart = nullptr;    // [nrchunk][12]
+  unsigned* rcount = nullptr; // [m] arrivals per handle, left at zero
+  int nrchunk = 0;
+  std::vector<int> h_vrow, h_hrow, h_vh;
+  std::vector<double> h_vphi, h_origins;
 };
 
 }  // namespace mls
+
+struct mls_mlp;
 
 struct mls_ctx {
   mls_options opt{};
@@ -241,6 +253,7 @@ struct mls_ctx {
   void* vp = nullptr;
   void* vq = nullptr;
   void* vw = nullptr;
+  void* vz2 = nullptr;             // preconditioned residual of the multiplicative cycle
   mls::PcgScalars* pcg = nullptr;  // device
   mls::PcgScalars* pcg_host = nullptr;  // pinned
   double* dscal = nullptr;         // device scalars [16]
@@ -267,6 +280,27 @@ struct mls_ctx {
   void* cvec2 = nullptr;
   bool coarse_ready = false;
   int* chol_info = nullptr;        // device: first non-positive pivot + 1, or 0
+  double* chol_tinv = nullptr;     // [32][32] inverse of the current diagonal factor tile
+
+  // learned warm start (coarse projection with U^T M U, history, features)
+  double* Am = nullptr;            // [r][r] U^T M U, factored in place
+  void* Wm = nullptr;              // inverse factor of U^T M U (solve precision)
+  void* WmT = nullptr;
+  void* ws_c = nullptr;            // [r] solve-precision scratch
+  void* ws_c2 = nullptr;
+  void* ws_tmp = nullptr;
+  double* ws_hist = nullptr;       // [3][r] q^t, q^{t-1}, q^{t-2}
+  double* ws_qg = nullptr;         // [r] coarse coordinates of h^2 g
+  double* ws_qtilde = nullptr;     // [r] q(x_tilde)
+  double* ws_qnext = nullptr;      // [r] scratch projection
+  float* ws_feat = nullptr;        // [3r] features of the current step
+  float* ws_target = nullptr;      // [r] realised coarse increment of the last step
+  float* ws_pred = nullptr;        // [r] predicted increment
+  mls_mlp* ws_mlp = nullptr;       // attached network (not owned)
+  bool ws_ready = false, ws_enabled = false, ws_hist_valid = false;
+  bool ws_record = false;          // record training targets (keeps H(x_tilde))
+  void* ws_hsave = nullptr;        // copy of H's values at the first Newton iterate
+  std::vector<double> h_mass, h_X; // host copies for assembling U^T M U
 
   // kernel-class timing
   uint32_t prof_mask = 0;
@@ -313,6 +347,7 @@ mls_status launch_unpack(mls_ctx* ctx, const Vec4d* src, double* dst);
 mls_status launch_disp_out(mls_ctx* ctx, double* dx_out);
 
 mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y);  // solve-precision vectors
+mls_status launch_spmv_values(mls_ctx* ctx, const void* values, const void* x, void* y);
 mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double scale);
 mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst);      // zero on Dirichlet vertices
 mls_status launch_from_solve_raw(mls_ctx* ctx, const void* src, Vec4d* dst);  // no masking
@@ -325,5 +360,8 @@ mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate)
 mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q);
 mls_status build_coarse(mls_ctx* ctx);
 mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out);
+mls_status warm_start_begin(mls_ctx* ctx, int* used);
+mls_status warm_start_first_iteration(mls_ctx* ctx);
+mls_status warm_start_end(mls_ctx* ctx);
 
 }  // namespace mls

@@ -144,6 +144,38 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   }
   const int nbk = h_hn_row[m];
   const size_t nent = h_ent_y.size();
+  // per-entry coefficients (phi, phi a) in solve precision, vertex- and
+  // handle-major; restriction chunks of at most kRestrictChunk entries
+  const bool fp64 = ctx->opt.precision == MLS_FP64;
+  std::vector<double> h_vcoef(4 * (size_t)nz), h_hcoef(4 * (size_t)nz);
+  for (int v = 0; v < n; ++v)
+    for (int k = h_vrow[v]; k < h_vrow[v + 1]; ++k) {
+      const int j = h_vh[k];
+      const double ph = h_vphi[k];
+      h_vcoef[4 * (size_t)k + 0] = ph;
+      for (int c = 0; c < 3; ++c) h_vcoef[4 * (size_t)k + 1 + c] = ph * (ctx->h_X[3 * (size_t)v + c] - origins[3 * j + c]);
+    }
+  for (int j = 0; j < m; ++j)
+    for (int p = h_hrow[j]; p < h_hrow[j + 1]; ++p) {
+      const int v = h_hv[p];
+      const double ph = h_hphi[p];
+      h_hcoef[4 * (size_t)p + 0] = ph;
+      for (int c = 0; c < 3; ++c) h_hcoef[4 * (size_t)p + 1 + c] = ph * (ctx->h_X[3 * (size_t)v + c] - origins[3 * j + c]);
+    }
+  std::vector<int> h_rchunk_handle, h_rchunk_beg;
+  std::vector<int> h_rchunk_ptr(m + 1, 0);
+  for (int j = 0; j < m; ++j) {
+    for (int b = h_hrow[j]; b < h_hrow[j + 1]; b += kRestrictChunk) {
+      h_rchunk_handle.push_back(j);
+      h_rchunk_beg.push_back(b);
+    }
+    if (h_hrow[j + 1] == h_hrow[j]) {  // empty handle: one empty chunk writes its zeros
+      h_rchunk_handle.push_back(j);
+      h_rchunk_beg.push_back(h_hrow[j]);
+    }
+    h_rchunk_ptr[j + 1] = (int)h_rchunk_handle.size();
+  }
+  const int nrchunk = (int)h_rchunk_handle.size();
   // chunks of at most kGalerkinChunk entries that never cross a coarse block
   std::vector<int> h_chunk_ptr(1, 0), h_chunk_beg, h_slot_row(nbk);
   for (int i = 0; i < m; ++i)
@@ -179,6 +211,20 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   if ((st = up((void**)&B.ent_v, h_ent_v.data(), sizeof(int) * nent)) != MLS_OK) return st;
   if ((st = up((void**)&B.ent_phi, h_ent_phi.data(), sizeof(double) * nent)) != MLS_OK) return st;
   if ((st = up((void**)&B.chunk_ptr, h_chunk_ptr.data(), sizeof(int) * (nbk + 1))) != MLS_OK) return st;
+  if (fp64) {
+    if ((st = up(&B.vcoef, h_vcoef.data(), sizeof(double) * h_vcoef.size())) != MLS_OK) return st;
+    if ((st = up(&B.hcoef, h_hcoef.data(), sizeof(double) * h_hcoef.size())) != MLS_OK) return st;
+  } else {
+    std::vector<float> fv(h_vcoef.begin(), h_vcoef.end()), fh(h_hcoef.begin(), h_hcoef.end());
+    if ((st = up(&B.vcoef, fv.data(), sizeof(float) * fv.size())) != MLS_OK) return st;
+    if ((st = up(&B.hcoef, fh.data(), sizeof(float) * fh.size())) != MLS_OK) return st;
+  }
+  if ((st = up((void**)&B.rchunk_handle, h_rchunk_handle.data(), sizeof(int) * nrchunk)) != MLS_OK) return st;
+  if ((st = up((void**)&B.rchunk_beg, h_rchunk_beg.data(), sizeof(int) * nrchunk)) != MLS_OK) return st;
+  if ((st = up((void**)&B.rchunk_ptr, h_rchunk_ptr.data(), sizeof(int) * (m + 1))) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&B.rpart, sizeof(double) * 12 * nrchunk)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&B.rcount, sizeof(unsigned) * m)) != MLS_OK) return st;
+  if ((st = cuda_check(ctx, cudaMemset(B.rcount, 0, sizeof(unsigned) * m), "counters")) != MLS_OK) return st;
   if ((st = up((void**)&B.chunk_beg, h_chunk_beg.data(), sizeof(int) * std::max(nchunk, 1))) != MLS_OK) return st;
   if ((st = up((void**)&B.slot_row, h_slot_row.data(), sizeof(int) * std::max(nbk, 1))) != MLS_OK) return st;
   B.m = m;
@@ -188,8 +234,12 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   B.nb = nbk;
   B.nent = (int64_t)nent;
   B.nchunk = nchunk;
+  B.nrchunk = nrchunk;
   B.h_hrow = h_hrow;
   B.h_vrow = h_vrow;
+  B.h_vh = h_vh;
+  B.h_vphi = h_vphi;
+  B.h_origins.assign(origins, origins + 3 * (size_t)m);
   const int r = 12 * m;
   const int vb = solve_bytes(ctx);
   if ((st = dalloc(ctx, &ctx->yval, (size_t)ny * 36 * vb)) != MLS_OK) return st;
@@ -201,6 +251,7 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   if ((st = dalloc(ctx, &ctx->cvec, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->cvec2, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->chol_info, sizeof(int) * 4)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->chol_tinv, sizeof(double) * 32 * 32)) != MLS_OK) return st;
   ctx->has_basis = true;
   ctx->coarse_ready = false;
   return MLS_OK;
@@ -209,6 +260,13 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
 // ---- prolongation / restriction ---------------------------------------------------------
 struct BasisView {
   int n, m;
+  const void* __restrict__ vcoef;   // [nnz] (phi, phi a) vertex-major, solve precision
+  const void* __restrict__ hcoef;   // [nnz] (phi, phi a) handle-major
+  const int* __restrict__ rchunk_handle;
+  const int* __restrict__ rchunk_beg;
+  const int* __restrict__ rchunk_ptr;
+  double* rpart;
+  unsigned* rcount;
   const int* __restrict__ vrow;
   const int* __restrict__ vh;
   const double* __restrict__ vphi;
@@ -231,17 +289,15 @@ __global__ void __launch_bounds__(kBlock) k_prolong(BasisView B, const VT* __res
   if (S && S->done) return;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= B.n) return;
-  const Vec4d X = B.X[v];
   VT o0 = VT(0), o1 = VT(0), o2 = VT(0);
+  const Vec4<VT>* coef = (const Vec4<VT>*)B.vcoef;
   if (q) for (int k = B.vrow[v]; k < B.vrow[v + 1]; ++k) {
-    const int j = B.vh[k];
-    const VT ph = (VT)B.vphi[k];
-    const VT a1 = (VT)(X.x - B.origins[3 * j]), a2 = (VT)(X.y - B.origins[3 * j + 1]),
-             a3 = (VT)(X.z - B.origins[3 * j + 2]);
-    const VT* qj = q + 12 * (int64_t)j;
-    o0 += ph * (qj[0] + a1 * qj[1] + a2 * qj[2] + a3 * qj[3]);
-    o1 += ph * (qj[4] + a1 * qj[5] + a2 * qj[6] + a3 * qj[7]);
-    o2 += ph * (qj[8] + a1 * qj[9] + a2 * qj[10] + a3 * qj[11]);
+    const Vec4<VT> a = coef[k];
+    const Vec4<VT>* qj = (const Vec4<VT>*)(q + 12 * (int64_t)B.vh[k]);
+    const Vec4<VT> q0 = qj[0], q1 = qj[1], q2 = qj[2];
+    o0 += a.x * q0.x + a.y * q0.y + a.z * q0.z + a.w * q0.w;
+    o1 += a.x * q1.x + a.y * q1.y + a.z * q1.z + a.w * q1.w;
+    o2 += a.x * q2.x + a.y * q2.y + a.z * q2.z + a.w * q2.w;
   }
   if (base) {
     const Vec4<VT> b = base[v];
@@ -257,29 +313,63 @@ __global__ void __launch_bounds__(kBlock) k_prolong(BasisView B, const VT* __res
   w[v] = Vec4<VT>{o0, o1, o2, VT(0)};
 }
 
-// z_j = sum_{v in supp j} phi_j(v) r_v (x) a_vj : one CTA per handle
+// z1 += U y in place, then r.z1 and beta (the end of the additive cycle)
 template <typename VT>
-__global__ void __launch_bounds__(kBlock) k_restrict(BasisView B, const Vec4<VT>* __restrict__ r,
-                                                     VT* __restrict__ z, const PcgScalars* __restrict__ S) {
+__global__ void __launch_bounds__(kBlock) k_prolong_rz(BasisView B, const VT* __restrict__ q,
+                                                       const Vec4<VT>* __restrict__ r, Vec4<VT>* z, int first,
+                                                       GridReduce gr, PcgScalars* __restrict__ S) {
+  if (S->done) return;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (v < B.n) {
+    VT o0 = VT(0), o1 = VT(0), o2 = VT(0);
+    const Vec4<VT>* coef = (const Vec4<VT>*)B.vcoef;
+    for (int k = B.vrow[v]; k < B.vrow[v + 1]; ++k) {
+      const Vec4<VT> a = coef[k];
+      const Vec4<VT>* qj = (const Vec4<VT>*)(q + 12 * (int64_t)B.vh[k]);
+      const Vec4<VT> q0 = qj[0], q1 = qj[1], q2 = qj[2];
+      o0 += a.x * q0.x + a.y * q0.y + a.z * q0.z + a.w * q0.w;
+      o1 += a.x * q1.x + a.y * q1.y + a.z * q1.z + a.w * q1.w;
+      o2 += a.x * q2.x + a.y * q2.y + a.z * q2.z + a.w * q2.w;
+    }
+    const Vec4<VT> zb = z[v], rv = r[v];
+    const Vec4<VT> zo{zb.x + o0, zb.y + o1, zb.z + o2, VT(0)};
+    z[v] = zo;
+    acc[0] = (double)rv.x * zo.x + (double)rv.y * zo.y + (double)rv.z * zo.z;
+  }
+  if (grid_sum<1>(acc, gr, RS_PCG_RZ) && threadIdx.x == 0) {
+    S->beta = first ? 0.0 : acc[0] / S->rz;
+    S->rz = acc[0];
+    if (!(acc[0] > 0.0) || !isfinite(acc[0])) S->done = (S->rr <= S->tol2) ? 1 : 3;
+  }
+}
+
+// z_j = sum_{v in supp j} phi_j(v) r_v (x) a_vj.  One CTA per chunk of at most
+// kRestrictChunk entries of one handle (one entry per thread, coalesced
+// coefficients); chunk sums go to a per-chunk slot and the last chunk of a
+// handle to finish adds them in chunk order (deterministic).
+template <typename VT>
+__global__ void __launch_bounds__(kRestrictChunk) k_restrict(BasisView B, const Vec4<VT>* __restrict__ r,
+                                                             VT* __restrict__ z, const PcgScalars* __restrict__ S) {
   if (S && S->done) return;
-  const int j = blockIdx.x;
-  const double ox = B.origins[3 * j], oy = B.origins[3 * j + 1], oz = B.origins[3 * j + 2];
+  const int ch = blockIdx.x;
+  const int j = B.rchunk_handle[ch];
+  const int p = B.rchunk_beg[ch] + threadIdx.x;
   VT acc[12];
 #pragma unroll
   for (int q = 0; q < 12; ++q) acc[q] = VT(0);
-  for (int p = B.hrow[j] + threadIdx.x; p < B.hrow[j + 1]; p += blockDim.x) {
-    const int v = B.hv[p];
-    const VT ph = (VT)B.hphi[p];
-    const Vec4d X = B.X[v];
-    const VT a[4] = {VT(1), (VT)(X.x - ox), (VT)(X.y - oy), (VT)(X.z - oz)};
-    const Vec4<VT> rv = r[v];
-    const VT rc[3] = {ph * rv.x, ph * rv.y, ph * rv.z};
+  if (p < B.hrow[j + 1]) {
+    const Vec4<VT> a = ((const Vec4<VT>*)B.hcoef)[p];
+    const Vec4<VT> rv = r[B.hv[p]];
+    const VT rc[3] = {rv.x, rv.y, rv.z};
+    const VT av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int l = 0; l < 4; ++l) acc[4 * c + l] += rc[c] * a[l];
+      for (int l = 0; l < 4; ++l) acc[4 * c + l] = rc[c] * av[l];
   }
-  __shared__ VT sh[12][kBlock / 32];
+  __shared__ VT sh[12][kRestrictChunk / 32];
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < 12; ++q) {
@@ -292,8 +382,23 @@ __global__ void __launch_bounds__(kBlock) k_restrict(BasisView B, const Vec4<VT>
   if (threadIdx.x < 12) {
     VT s = VT(0);
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[threadIdx.x][w];
-    z[12 * (int64_t)j + threadIdx.x] = s;
+    B.rpart[12 * (int64_t)ch + threadIdx.x] = (double)s;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned nch = (unsigned)(B.rchunk_ptr[j + 1] - B.rchunk_ptr[j]);
+    last = (atomicAdd(B.rcount + j, 1u) == nch - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 12) {
+    double s = 0.0;
+    for (int c = B.rchunk_ptr[j]; c < B.rchunk_ptr[j + 1]; ++c) s += __ldcg(B.rpart + 12 * (int64_t)c + threadIdx.x);
+    z[12 * (int64_t)j + threadIdx.x] = (VT)s;
+  }
+  if (threadIdx.x == 0) B.rcount[j] = 0;
 }
 
 // ---- Galerkin: Y = H U ----------------------------------------------------------------
@@ -422,13 +527,17 @@ __global__ void __launch_bounds__(144) k_galerkin_reduce(const int* __restrict__
 // ---- dense Cholesky (float64), blocked right-looking ---------------------------------------
 constexpr int NB = 32;
 
-// factor the diagonal tile (k, k) in place; one CTA of 32x32 threads
-__global__ void k_potrf_tile(double* __restrict__ A, int r, int k, int* __restrict__ info) {
+// factor the diagonal tile (k, k) in place and write the inverse of its
+// lower-triangular factor to tinv (32 x 32, row-major); one CTA of 32x32 threads
+__global__ void k_potrf_tile(double* __restrict__ A, int r, int k, int* __restrict__ info,
+                             double* __restrict__ tinv) {
   __shared__ double T[NB][NB + 1];
+  __shared__ double Ti[NB][NB + 1];
+  __shared__ double rd[NB];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int base = k * NB;
   const int nr = min(NB, r - base);
-  if (ty < nr && tx < nr) T[ty][tx] = A[(int64_t)(base + ty) * r + base + tx];
+  T[ty][tx] = (ty < nr && tx < nr) ? A[(int64_t)(base + ty) * r + base + tx] : (ty == tx ? 1.0 : 0.0);
   __syncthreads();
   for (int p = 0; p < nr; ++p) {
     if (tx == 0 && ty == 0) {
@@ -439,37 +548,44 @@ __global__ void k_potrf_tile(double* __restrict__ A, int r, int k, int* __restri
       } else {
         T[p][p] = sqrt(d);
       }
+      rd[p] = 1.0 / T[p][p];
     }
     __syncthreads();
-    if (tx == 0 && ty > p && ty < nr) T[ty][p] /= T[p][p];
+    if (tx == 0 && ty > p && ty < nr) T[ty][p] *= rd[p];
     __syncthreads();
     if (ty > p && tx > p && tx <= ty && ty < nr) T[ty][tx] -= T[ty][p] * T[tx][p];
     __syncthreads();
   }
   if (ty < nr && tx < nr) A[(int64_t)(base + ty) * r + base + tx] = (tx <= ty) ? T[ty][tx] : 0.0;
+  // inverse of the factor: column j solved by forward substitution (lane j of warp 0)
+  if (ty == 0) {
+    const int j = tx;
+    for (int i = 0; i < NB; ++i) {
+      double v = (i == j) ? 1.0 : 0.0;
+      if (i >= nr) { Ti[i][j] = v; continue; }
+      for (int q = j; q < i; ++q) v -= T[i][q] * Ti[q][j];
+      Ti[i][j] = (i < j) ? 0.0 : v * rd[i];
+    }
+  }
+  __syncthreads();
+  tinv[ty * NB + tx] = Ti[ty][tx];
 }
 
-// L_ik = A_ik L_kk^{-T} for tiles i > k; one CTA (32x32 threads) per tile row i
-__global__ void k_trsm_tiles(double* __restrict__ A, int r, int k) {
-  __shared__ double Lk[NB][NB + 1];
+// L_ik = A_ik L_kk^{-T} = A_ik (tinv)^T for tiles i > k; one CTA (32x32) per tile
+__global__ void k_trsm_tiles(double* __restrict__ A, int r, int k, const double* __restrict__ tinv) {
+  __shared__ double Li[NB][NB + 1];
   __shared__ double X[NB][NB + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = k + 1 + blockIdx.x;
   const int bk = k * NB, bi = i * NB;
   const int nk = min(NB, r - bk), ni = min(NB, r - bi);
-  if (ty < nk && tx < nk) Lk[ty][tx] = A[(int64_t)(bk + ty) * r + bk + tx];
-  if (ty < ni && tx < nk) X[ty][tx] = A[(int64_t)(bi + ty) * r + bk + tx];
+  Li[ty][tx] = tinv[ty * NB + tx];
+  X[ty][tx] = (ty < ni && tx < nk) ? A[(int64_t)(bi + ty) * r + bk + tx] : 0.0;
   __syncthreads();
-  // solve X L^T = B row by row: X[row][c] = (B[row][c] - sum_{q<c} X[row][q] L[c][q]) / L[c][c]
-  if (tx == 0 && ty < ni) {
-    for (int c = 0; c < nk; ++c) {
-      double s = X[ty][c];
-      for (int q = 0; q < c; ++q) s -= X[ty][q] * Lk[c][q];
-      X[ty][c] = s / Lk[c][c];
-    }
-  }
-  __syncthreads();
-  if (ty < ni && tx < nk) A[(int64_t)(bi + ty) * r + bk + tx] = X[ty][tx];
+  double s = 0.0;
+#pragma unroll 8
+  for (int q = 0; q <= tx; ++q) s += X[ty][q] * Li[tx][q];
+  if (ty < ni && tx < nk) A[(int64_t)(bi + ty) * r + bk + tx] = s;
 }
 
 // A_ij -= L_ik L_jk^T for k < j <= i (lower triangle of the trailing matrix);
@@ -625,7 +741,8 @@ __global__ void k_ypair_rows(int n, const int* __restrict__ yrow, int* __restric
 // ---- host drivers --------------------------------------------------------------------------
 static BasisView basis_view(mls_ctx* ctx) {
   const Basis& B = ctx->basis;
-  return BasisView{ctx->n, B.m, B.vrow, B.vh, B.vphi, B.hrow, B.hv, B.hphi, B.origins, ctx->X};
+  return BasisView{ctx->n, B.m, B.vcoef, B.hcoef, B.rchunk_handle, B.rchunk_beg, B.rchunk_ptr, B.rpart, B.rcount,
+                   B.vrow, B.vh, B.vphi, B.hrow, B.hv, B.hphi, B.origins, ctx->X};
 }
 
 mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate) {
@@ -642,9 +759,9 @@ mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate)
 mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   if (ctx->opt.precision == MLS_FP64)
-    { ++ctx->launches; k_restrict<double><<<ctx->basis.m, kBlock, 0, ctx->stream>>>(basis_view(ctx), (const Vec4d*)r, (double*)q, nullptr); }
+    { ++ctx->launches; k_restrict<double><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(basis_view(ctx), (const Vec4d*)r, (double*)q, nullptr); }
   else
-    { ++ctx->launches; k_restrict<float><<<ctx->basis.m, kBlock, 0, ctx->stream>>>(basis_view(ctx), (const Vec4f*)r, (float*)q, nullptr); }
+    { ++ctx->launches; k_restrict<float><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(basis_view(ctx), (const Vec4f*)r, (float*)q, nullptr); }
   return cuda_check(ctx, cudaGetLastError(), "k_restrict");
 }
 
@@ -672,38 +789,40 @@ static mls_status galerkin_t(mls_ctx* ctx) {
   return cuda_check(ctx, cudaGetLastError(), "galerkin");
 }
 
+// Factor the dense SPD float64 matrix A (r x r, row-major, overwritten by
+// its Cholesky factor in the lower triangle) and form W = L^{-1} and W^T in
+// solve precision.  Acopy (nullable) receives A before factorisation.
 template <typename VT>
-static mls_status factor_t(mls_ctx* ctx) {
-  const int r = 12 * ctx->basis.m;
+static mls_status factor_dense_t(mls_ctx* ctx, double* A, int r, double* Acopy, void* W, void* WT) {
   const int nt = (r + NB - 1) / NB;
-  mls_status st = cuda_check(ctx, cudaMemcpyAsync(ctx->Acopy, ctx->Ac, sizeof(double) * r * r,
-                                                  cudaMemcpyDeviceToDevice, ctx->stream), "Ac copy");
-  if (st != MLS_OK) return st;
+  mls_status st;
+  if (Acopy) {
+    st = cuda_check(ctx, cudaMemcpyAsync(Acopy, A, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, ctx->stream),
+                    "A copy");
+    if (st != MLS_OK) return st;
+  }
   st = cuda_check(ctx, cudaMemsetAsync(ctx->chol_info, 0, sizeof(int), ctx->stream), "info clear");
   if (st != MLS_OK) return st;
-  // symmetrise from the lower triangle is implicit: only the lower triangle is read
   for (int k = 0; k < nt; ++k) {
-    { ++ctx->launches; k_potrf_tile<<<1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, k, ctx->chol_info); }
+    { ++ctx->launches; k_potrf_tile<<<1, dim3(NB, NB), 0, ctx->stream>>>(A, r, k, ctx->chol_info, ctx->chol_tinv); }
     if (k + 1 < nt) {
-      { ++ctx->launches; k_trsm_tiles<<<nt - k - 1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, k); }
+      { ++ctx->launches; k_trsm_tiles<<<nt - k - 1, dim3(NB, NB), 0, ctx->stream>>>(A, r, k, ctx->chol_tinv); }
       const int m = nt - k - 1;
-      { ++ctx->launches; k_syrk_tiles<<<m * (m + 1) / 2, dim3(32, 8), 0, ctx->stream>>>(ctx->Ac, r, k, nt); }
+      { ++ctx->launches; k_syrk_tiles<<<m * (m + 1) / 2, dim3(32, 8), 0, ctx->stream>>>(A, r, k, nt); }
     }
   }
   st = cuda_check(ctx, cudaGetLastError(), "cholesky");
   if (st != MLS_OK) return st;
-  st = cuda_check(ctx, cudaMemsetAsync(ctx->Linv, 0, (size_t)r * r * sizeof(VT), ctx->stream), "W clear");
+  st = cuda_check(ctx, cudaMemsetAsync(W, 0, (size_t)r * r * sizeof(VT), ctx->stream), "W clear");
   if (st != MLS_OK) return st;
-  st = cuda_check(ctx, cudaMemsetAsync(ctx->LinvT, 0, (size_t)r * r * sizeof(VT), ctx->stream), "WT clear");
-  if (st != MLS_OK) return st;
-  { ++ctx->launches; k_eye<VT><<<(r + 255) / 256, 256, 0, ctx->stream>>>((VT*)ctx->Linv, r); }
+  { ++ctx->launches; k_eye<VT><<<(r + 255) / 256, 256, 0, ctx->stream>>>((VT*)W, r); }
   for (int i = 0; i < nt; ++i) {
-    { ++ctx->launches; k_trinv_solve<VT><<<i + 1, dim3(NB, NB), 0, ctx->stream>>>(ctx->Ac, r, i, (VT*)ctx->Linv); }
+    { ++ctx->launches; k_trinv_solve<VT><<<i + 1, dim3(NB, NB), 0, ctx->stream>>>(A, r, i, (VT*)W); }
     if (i + 1 < nt) {
-      { ++ctx->launches; k_trinv_update<VT><<<(nt - i - 1) * (i + 1), dim3(32, 8), 0, ctx->stream>>>(ctx->Ac, r, i, nt, (VT*)ctx->Linv); }
+      { ++ctx->launches; k_trinv_update<VT><<<(nt - i - 1) * (i + 1), dim3(32, 8), 0, ctx->stream>>>(A, r, i, nt, (VT*)W); }
     }
   }
-  { ++ctx->launches; k_transpose<VT><<<dim3(nt, nt), dim3(32, 8), 0, ctx->stream>>>((const VT*)ctx->Linv, r, (VT*)ctx->LinvT); }
+  { ++ctx->launches; k_transpose<VT><<<dim3(nt, nt), dim3(32, 8), 0, ctx->stream>>>((const VT*)W, r, (VT*)WT); }
   st = cuda_check(ctx, cudaGetLastError(), "triangular inverse");
   if (st != MLS_OK) return st;
   int info = 0;
@@ -713,12 +832,36 @@ static mls_status factor_t(mls_ctx* ctx) {
   st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cholesky sync");
   if (st != MLS_OK) return st;
   memcpy(&info, &ctx->dscal_host[12], sizeof(int));
-  if (info != 0) {
-    ctx->coarse_ready = false;
-    return fail(ctx, MLS_ECHOL, "coarse operator is not positive definite (pivot " + std::to_string(info - 1) + ")");
-  }
-  ctx->coarse_ready = true;
+  if (info != 0) return fail(ctx, MLS_ECHOL, "matrix is not positive definite (pivot " + std::to_string(info - 1) + ")");
   return MLS_OK;
+}
+
+mls_status factor_dense(mls_ctx* ctx, double* A, int r, double* Acopy, void* W, void* WT) {
+  return ctx->opt.precision == MLS_FP64 ? factor_dense_t<double>(ctx, A, r, Acopy, W, WT)
+                                        : factor_dense_t<float>(ctx, A, r, Acopy, W, WT);
+}
+
+template <typename VT>
+static mls_status factor_t(mls_ctx* ctx) {
+  const int r = 12 * ctx->basis.m;
+  mls_status st = factor_dense_t<VT>(ctx, ctx->Ac, r, ctx->Acopy, ctx->Linv, ctx->LinvT);
+  ctx->coarse_ready = (st == MLS_OK);
+  if (st == MLS_ECHOL) return fail(ctx, MLS_ECHOL, "coarse operator U^T H U: " + ctx->err);
+  return st;
+}
+
+// y = W^T (W x) with a dense inverse factor pair, solve precision
+mls_status dense_apply(mls_ctx* ctx, const void* W, const void* WT, int r, const void* x, void* tmp, void* y) {
+  const int rows_per_block = kBlock / 32;
+  const int nb = (r + rows_per_block - 1) / rows_per_block;
+  if (ctx->opt.precision == MLS_FP64) {
+    { ++ctx->launches; k_trigemv<double><<<nb, kBlock, 0, ctx->stream>>>((const double*)W, r, 1, (const double*)x, (double*)tmp, nullptr); }
+    { ++ctx->launches; k_trigemv<double><<<nb, kBlock, 0, ctx->stream>>>((const double*)WT, r, 0, (const double*)tmp, (double*)y, nullptr); }
+  } else {
+    { ++ctx->launches; k_trigemv<float><<<nb, kBlock, 0, ctx->stream>>>((const float*)W, r, 1, (const float*)x, (float*)tmp, nullptr); }
+    { ++ctx->launches; k_trigemv<float><<<nb, kBlock, 0, ctx->stream>>>((const float*)WT, r, 0, (const float*)tmp, (float*)y, nullptr); }
+  }
+  return cuda_check(ctx, cudaGetLastError(), "dense apply");
 }
 
 mls_status build_coarse(mls_ctx* ctx) {
@@ -763,7 +906,7 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   VT* c = (VT*)ctx->cvec;
   const VT* dinv = (const VT*)ctx->dinv;
   if (ctx->opt.cycle == MLS_CYCLE_ADDITIVE) {
-    { ++ctx->launches; k_restrict<VT><<<m, kBlock, 0, ctx->stream>>>(BV, r, c, S); }
+    { ++ctx->launches; k_restrict<VT><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(BV, r, c, S); }
     mls_status st = coarse_apply_t<VT>(ctx, c, c, S);
     if (st != MLS_OK) return st;
     { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, nullptr, dinv, r, omega, z, S); }
@@ -774,12 +917,45 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   mls_status st = launch_jacobi(ctx, r, z, ctx->opt.omega, S);
   if (st != MLS_OK) return st;
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
-  { ++ctx->launches; k_restrict<VT><<<m, kBlock, 0, ctx->stream>>>(BV, tmp, c, S); }
+  { ++ctx->launches; k_restrict<VT><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(BV, tmp, c, S); }
   if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
   { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, z, nullptr, nullptr, omega, z, S); }
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
   { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, nullptr, z, dinv, tmp, omega, z, S); }
   return cuda_check(ctx, cudaGetLastError(), "two-level multiplicative");
+}
+
+mls_status launch_post_smooth_rz(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, PcgScalars* S);
+
+// One application of the two-level cycle inside PCG, with z1 = omega D^{-1} r
+// already in place: additive z = z1 + U A^{-1} U^T r; multiplicative
+// z2 = z1 + U A^{-1} U^T (r - H z1), zf = z2 + omega D^{-1} (r - H z2).  Ends
+// with r.zf and beta.
+template <typename VT>
+static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1, Vec4<VT>* zf, int first,
+                                   PcgScalars* S) {
+  const BasisView BV = basis_view(ctx);
+  const int m = ctx->basis.m;
+  VT* c = (VT*)ctx->cvec;
+  mls_status st;
+  if (ctx->opt.cycle == MLS_CYCLE_ADDITIVE) {
+    { ++ctx->launches; k_restrict<VT><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(BV, r, c, S); }
+    if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
+    { ++ctx->launches; k_prolong_rz<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, r, z1, first, ctx->red, S); }
+    return cuda_check(ctx, cudaGetLastError(), "two-level additive");
+  }
+  Vec4<VT>* tmp = (Vec4<VT>*)ctx->vw;
+  if ((st = launch_residual(ctx, r, z1, tmp, S)) != MLS_OK) return st;
+  { ++ctx->launches; k_restrict<VT><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(BV, tmp, c, S); }
+  if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
+  { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, z1, nullptr, nullptr, VT(0), z1, S); }
+  return launch_post_smooth_rz(ctx, r, z1, zf, first, S);
+}
+
+mls_status two_level_pcg_step(mls_ctx* ctx, const void* r, void* z1, void* zf, int first, PcgScalars* S) {
+  if (ctx->opt.precision == MLS_FP64)
+    return two_level_step_t<double>(ctx, (const Vec4d*)r, (Vec4d*)z1, (Vec4d*)zf, first, S);
+  return two_level_step_t<float>(ctx, (const Vec4f*)r, (Vec4f*)z1, (Vec4f*)zf, first, S);
 }
 
 mls_status precond_apply_dev(mls_ctx* ctx, const void* r, void* z, const PcgScalars* S) {

@@ -39,45 +39,59 @@ __device__ __forceinline__ void spmv_row(const SellView& A, const MT* __restrict
   y[0] = y0; y[1] = y1; y[2] = y2;
 }
 
-// One CTA of kSpmvWarps warps per 32-row slice: warp w takes the slots
-// k = w, w + kSpmvWarps, ... of every row, so each value load stays a
-// coalesced 32-lane access and no load is duplicated; partial products are
-// summed through shared memory.  Returns true in warp 0, whose lane holds
-// the finished row (row = slice * 32 + lane) in y.
+// One CTA of 128 threads per 32-row slice, four lanes per row (lane = 4 row + part):
+// part p takes the slots k = p, p + 4, p + 8, ... of its row, so every load
+// instruction of a warp covers 8 consecutive rows of 4 slot groups (four full
+// 32-byte sectors); a lane first issues all its column indices and x gathers
+// of a batch of up to four slots, then the values, to keep many loads in
+// flight; the four partial rows are combined with two shuffles (no shared
+// memory, no barrier).  Every lane returns the finished row in y.
 constexpr int kSpmvWarps = 4;
 
 template <typename VT, typename MT>
-__device__ __forceinline__ bool spmv_slice(const SellView& A, const MT* __restrict__ val, int slice,
-                                           const Vec4<VT>* __restrict__ x, VT (&y)[3]) {
-  __shared__ VT red[kSpmvWarps][3][32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = slice * 32 + lane;
+__device__ __forceinline__ void spmv_quad(const SellView& A, const MT* __restrict__ val, int slice,
+                                          const Vec4<VT>* __restrict__ x, VT (&y)[3]) {
+  const int part = threadIdx.x & 3;
+  const int rl = threadIdx.x >> 2;        // row within the slice
+  const int row = slice * 32 + rl;
   const int len = row < A.n ? A.row_len[row] : 0;
-  const int g0 = A.slice_ptr[slice];
+  const int64_t g0 = A.slice_ptr[slice];
   VT y0 = VT(0), y1 = VT(0), y2 = VT(0);
-#pragma unroll 2
-  for (int k = w; k < len; k += kSpmvWarps) {
-    const int64_t g = g0 + k;
-    const int c = __ldg(A.col + g * 32 + lane);
-    const Vec4<VT> xv = x[c];
-    const MT* v = val + g * 288 + lane;
-    y0 += load_as<VT>(v[0]) * xv.x + load_as<VT>(v[32]) * xv.y + load_as<VT>(v[64]) * xv.z;
-    y1 += load_as<VT>(v[96]) * xv.x + load_as<VT>(v[128]) * xv.y + load_as<VT>(v[160]) * xv.z;
-    y2 += load_as<VT>(v[192]) * xv.x + load_as<VT>(v[224]) * xv.y + load_as<VT>(v[256]) * xv.z;
-  }
-  red[w][0][lane] = y0;
-  red[w][1][lane] = y1;
-  red[w][2][lane] = y2;
-  __syncthreads();
-  if (w != 0) return false;
+  for (int k0 = part; k0 < len; k0 += 16) {
+    int c[4];
+    bool ok[4];
 #pragma unroll
-  for (int q = 1; q < kSpmvWarps; ++q) {
-    y0 += red[q][0][lane];
-    y1 += red[q][1][lane];
-    y2 += red[q][2][lane];
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 4 * u;
+      ok[u] = k < len;
+      c[u] = ok[u] ? __ldg(A.col + (g0 + k) * 32 + rl) : 0;
+    }
+    Vec4<VT> xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = ok[u] ? x[c[u]] : Vec4<VT>{VT(0), VT(0), VT(0), VT(0)};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!ok[u]) continue;
+      const MT* v = val + (g0 + k0 + 4 * u) * 288 + rl;
+      y0 += load_as<VT>(v[0]) * xv[u].x + load_as<VT>(v[32]) * xv[u].y + load_as<VT>(v[64]) * xv[u].z;
+      y1 += load_as<VT>(v[96]) * xv[u].x + load_as<VT>(v[128]) * xv[u].y + load_as<VT>(v[160]) * xv[u].z;
+      y2 += load_as<VT>(v[192]) * xv[u].x + load_as<VT>(v[224]) * xv[u].y + load_as<VT>(v[256]) * xv[u].z;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    y2 += __shfl_xor_sync(0xffffffffu, y2, o);
   }
   y[0] = y0; y[1] = y1; y[2] = y2;
-  return true;
+}
+
+// the row this thread finishes (part 0 of each quad), or -1
+__device__ __forceinline__ int quad_row(int slice, int n) {
+  if (threadIdx.x & 3) return -1;
+  const int row = slice * 32 + (threadIdx.x >> 2);
+  return row < n ? row : -1;
 }
 
 template <typename VT>
@@ -90,26 +104,26 @@ __device__ __forceinline__ Vec4<VT> dinv_apply(const VT* __restrict__ dinv, int 
 
 // ---- plain product / residual ---------------------------------------------------------
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps) k_spmv(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_spmv(SellView A, const MT* __restrict__ val,
                                                           const Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ y) {
   VT r[3];
-  if (!spmv_slice<VT, MT>(A, val, blockIdx.x, x, r)) return;
-  const int row = blockIdx.x * 32 + (threadIdx.x & 31);
-  if (row < A.n) y[row] = Vec4<VT>{r[0], r[1], r[2], VT(0)};
+  spmv_quad<VT, MT>(A, val, blockIdx.x, x, r);
+  const int row = quad_row(blockIdx.x, A.n);
+  if (row >= 0) y[row] = Vec4<VT>{r[0], r[1], r[2], VT(0)};
 }
 
 // out = b - H x
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps) k_residual(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_residual(SellView A, const MT* __restrict__ val,
                                                               const Vec4<VT>* __restrict__ b,
                                                               const Vec4<VT>* __restrict__ x,
                                                               Vec4<VT>* __restrict__ out,
                                                               const PcgScalars* __restrict__ S) {
   if (S && S->done) return;
   VT r[3];
-  if (!spmv_slice<VT, MT>(A, val, blockIdx.x, x, r)) return;
-  const int row = blockIdx.x * 32 + (threadIdx.x & 31);
-  if (row >= A.n) return;
+  spmv_quad<VT, MT>(A, val, blockIdx.x, x, r);
+  const int row = quad_row(blockIdx.x, A.n);
+  if (row < 0) return;
   const Vec4<VT> bb = b[row];
   out[row] = Vec4<VT>{bb.x - r[0], bb.y - r[1], bb.z - r[2], VT(0)};
 }
@@ -160,6 +174,35 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(int n, const Vec4<VT>* __re
   }
 }
 
+// zout = z2 + omega D^{-1} (r - H z2) (the post-smoothing of the symmetric
+// two-level cycle), fused with r.zout and beta (0 on the first call)
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_post_smooth_rz(SellView A, const MT* __restrict__ val,
+                                                                    const Vec4<VT>* __restrict__ r,
+                                                                    const Vec4<VT>* __restrict__ z2,
+                                                                    const VT* __restrict__ dinv, VT omega,
+                                                                    Vec4<VT>* __restrict__ zout, int first,
+                                                                    GridReduce gr, PcgScalars* __restrict__ S) {
+  if (S->done) return;
+  double acc[1] = {0.0};
+  VT hz[3];
+  spmv_quad<VT, MT>(A, val, blockIdx.x, z2, hz);
+  const int row = quad_row(blockIdx.x, A.n);
+  if (row >= 0) {
+    const Vec4<VT> rv = r[row], zv = z2[row];
+    const Vec4<VT> t{rv.x - hz[0], rv.y - hz[1], rv.z - hz[2], VT(0)};
+    const Vec4<VT> s = dinv_apply<VT>(dinv, row, t, omega);
+    const Vec4<VT> zo{zv.x + s.x, zv.y + s.y, zv.z + s.z, VT(0)};
+    zout[row] = zo;
+    acc[0] = (double)rv.x * zo.x + (double)rv.y * zo.y + (double)rv.z * zo.z;
+  }
+  if (grid_sum<1>(acc, gr, RS_PCG_RZ) && threadIdx.x == 0) {
+    S->beta = first ? 0.0 : acc[0] / S->rz;
+    S->rz = acc[0];
+    if (!(acc[0] > 0.0) || !isfinite(acc[0])) S->done = (S->rr <= S->tol2) ? 1 : 3;
+  }
+}
+
 // r.z after a non-local preconditioner; sets beta (0 on the first call)
 template <typename VT>
 __global__ void __launch_bounds__(kBlock) k_pcg_rz(int n, const Vec4<VT>* __restrict__ r,
@@ -185,16 +228,16 @@ __global__ void __launch_bounds__(kBlock) k_pcg_rz(int n, const Vec4<VT>* __rest
 
 // w = H z; p = z + beta p; q = w + beta q; alpha = r.z / p.q
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps) k_pcg_spmv(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_pcg_spmv(SellView A, const MT* __restrict__ val,
                                                               const Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p,
                                                               Vec4<VT>* __restrict__ q, GridReduce gr,
                                                               PcgScalars* __restrict__ S) {
   if (S->done) return;
-  const int row = blockIdx.x * 32 + (threadIdx.x & 31);
   double acc[1] = {0.0};
   VT w[3];
-  const bool mine = spmv_slice<VT, MT>(A, val, blockIdx.x, z, w);
-  if (mine && row < A.n) {
+  spmv_quad<VT, MT>(A, val, blockIdx.x, z, w);
+  const int row = quad_row(blockIdx.x, A.n);
+  if (row >= 0) {
     const VT beta = (VT)S->beta;
     const Vec4<VT> zv = z[row], pv = p[row], qv = q[row];
     const Vec4<VT> pn{zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, VT(0)};
@@ -214,12 +257,14 @@ __global__ void __launch_bounds__(32 * kSpmvWarps) k_pcg_spmv(SellView A, const 
   }
 }
 
-// x += alpha p; r -= alpha q; with block Jacobi also z = D^{-1} r, r.z, beta
+// x += alpha p; r -= alpha q; then by mode: 1 = block Jacobi z = D^{-1} r with
+// r.z and beta; 2 = the smoothing term z = omega D^{-1} r of a two-level cycle
 template <typename VT>
 __global__ void __launch_bounds__(kBlock) k_pcg_update(int n, Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r,
                                                        Vec4<VT>* __restrict__ z, const Vec4<VT>* __restrict__ p,
                                                        const Vec4<VT>* __restrict__ q, const VT* __restrict__ dinv,
-                                                       int jacobi, GridReduce gr, PcgScalars* __restrict__ S) {
+                                                       int jacobi, VT omega, GridReduce gr,
+                                                       PcgScalars* __restrict__ S) {
   if (S->done) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[2] = {0.0, 0.0};  // r.r, r.z
@@ -232,16 +277,18 @@ __global__ void __launch_bounds__(kBlock) k_pcg_update(int n, Vec4<VT>* __restri
     x[row] = xv;
     r[row] = rv;
     acc[0] = (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z;
-    if (jacobi) {
+    if (jacobi == 1) {
       const Vec4<VT> zv = dinv_apply<VT>(dinv, row, rv, VT(1));
       z[row] = zv;
       acc[1] = (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z;
+    } else if (jacobi == 2) {
+      z[row] = dinv_apply<VT>(dinv, row, rv, omega);
     }
   }
   if (grid_sum<2>(acc, gr, RS_PCG_RR) && threadIdx.x == 0) {
     S->rr = acc[0];
     S->iter += 1;
-    if (jacobi) {
+    if (jacobi == 1) {
       S->beta = acc[1] / S->rz;
       S->rz = acc[1];
     }
@@ -256,19 +303,21 @@ static SellView sell_view(mls_ctx* ctx) { return SellView{ctx->n, ctx->slice_ptr
 static inline int nblk(int64_t n) { return (int)((n + kBlock - 1) / kBlock); }
 
 template <typename VT, typename MT>
-static void spmv_t(mls_ctx* ctx, const void* x, void* y) {
-  { ++ctx->launches; k_spmv<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
+static void spmv_t(mls_ctx* ctx, const void* values, const void* x, void* y) {
+  { ++ctx->launches; k_spmv<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(sell_view(ctx), (const MT*)values,
                                                            (const Vec4<VT>*)x, (Vec4<VT>*)y); }
 }
 
-mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y) {
+mls_status launch_spmv_values(mls_ctx* ctx, const void* values, const void* x, void* y) {
   switch (ctx->opt.precision) {
-    case MLS_FP64: spmv_t<double, double>(ctx, x, y); break;
-    case MLS_MIXED_FP32: spmv_t<float, float>(ctx, x, y); break;
-    default: spmv_t<float, __nv_bfloat16>(ctx, x, y); break;
+    case MLS_FP64: spmv_t<double, double>(ctx, values, x, y); break;
+    case MLS_MIXED_FP32: spmv_t<float, float>(ctx, values, x, y); break;
+    default: spmv_t<float, __nv_bfloat16>(ctx, values, x, y); break;
   }
   return cuda_check(ctx, cudaGetLastError(), "k_spmv");
 }
+
+mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y) { return launch_spmv_values(ctx, ctx->hval, x, y); }
 
 template <typename VT, typename MT>
 mls_status launch_residual_t(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S) {
@@ -286,6 +335,22 @@ mls_status launch_residual(mls_ctx* ctx, const void* b, const void* x, void* out
   }
 }
 
+template <typename VT, typename MT>
+static mls_status post_smooth_t(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, PcgScalars* S) {
+  { ++ctx->launches; k_post_smooth_rz<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(
+      sell_view(ctx), (const MT*)ctx->hval, (const Vec4<VT>*)r, (const Vec4<VT>*)z2, (const VT*)ctx->dinv,
+      (VT)ctx->opt.omega, (Vec4<VT>*)zout, first, ctx->red, S); }
+  return cuda_check(ctx, cudaGetLastError(), "k_post_smooth_rz");
+}
+
+mls_status launch_post_smooth_rz(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, PcgScalars* S) {
+  switch (ctx->opt.precision) {
+    case MLS_FP64: return post_smooth_t<double, double>(ctx, r, z2, zout, first, S);
+    case MLS_MIXED_FP32: return post_smooth_t<float, float>(ctx, r, z2, zout, first, S);
+    default: return post_smooth_t<float, __nv_bfloat16>(ctx, r, z2, zout, first, S);
+  }
+}
+
 mls_status launch_jacobi(mls_ctx* ctx, const void* r, void* z, double omega, const PcgScalars* S) {
   if (ctx->opt.precision == MLS_FP64)
     { ++ctx->launches; k_jacobi<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const double*)ctx->dinv,
@@ -297,6 +362,7 @@ mls_status launch_jacobi(mls_ctx* ctx, const void* r, void* z, double omega, con
 }
 
 mls_status precond_apply_dev(mls_ctx* ctx, const void* r, void* z, const PcgScalars* S);
+mls_status two_level_pcg_step(mls_ctx* ctx, const void* r, void* z1, void* zfinal, int first, PcgScalars* S);
 
 template <typename VT, typename MT>
 static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res) {
@@ -320,25 +386,28 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
                                                  ctx->red, S); }
   mls_status st = cuda_check(ctx, cudaGetLastError(), "k_pcg_init");
   if (st != MLS_OK) return st;
+  // two-level: z1 (in vz) holds the smoothing term and then U-corrected
+  // iterate; zf is the preconditioned residual the product kernel reads
+  const bool mult = ctx->opt.cycle == MLS_CYCLE_MULTIPLICATIVE;
+  Vec4<VT>* z1 = z;
+  Vec4<VT>* zf = (!jacobi && mult) ? (Vec4<VT>*)ctx->vz2 : z;
   if (!jacobi) {
-    st = precond_apply_dev(ctx, r, z, S);
-    if (st != MLS_OK) return st;
-    { ++ctx->launches; k_pcg_rz<VT><<<nb, kBlock, 0, ctx->stream>>>(n, r, z, 1, ctx->red, S); }
+    if ((st = launch_jacobi(ctx, r, z1, ctx->opt.omega, S)) != MLS_OK) return st;
+    if ((st = two_level_pcg_step(ctx, r, z1, zf, 1, S)) != MLS_OK) return st;
   }
   const int chunk = ctx->opt.pcg_check_every > 0 ? ctx->opt.pcg_check_every : 16;
+  const VT omega = (VT)ctx->opt.omega;
   for (;;) {
     for (int c = 0; c < chunk; ++c) {
       int tk = prof_begin(ctx, MLS_PROF_SPMV);
-      { ++ctx->launches; k_pcg_spmv<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(A, val, z, p, q, ctx->red, S); }
+      { ++ctx->launches; k_pcg_spmv<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(A, val, zf, p, q, ctx->red, S); }
       prof_end(ctx, tk);
       tk = prof_begin(ctx, MLS_PROF_PCG_UPDATE);
-      { ++ctx->launches; k_pcg_update<VT><<<nb, kBlock, 0, ctx->stream>>>(n, x, r, z, p, q, dinv, jacobi ? 1 : 0, ctx->red, S); }
+      { ++ctx->launches; k_pcg_update<VT><<<nb, kBlock, 0, ctx->stream>>>(n, x, r, z1, p, q, dinv, jacobi ? 1 : 2, omega, ctx->red, S); }
       prof_end(ctx, tk);
       if (!jacobi) {
         tk = prof_begin(ctx, MLS_PROF_PRECOND);
-        st = precond_apply_dev(ctx, r, z, S);
-        if (st != MLS_OK) return st;
-        { ++ctx->launches; k_pcg_rz<VT><<<nb, kBlock, 0, ctx->stream>>>(n, r, z, 0, ctx->red, S); }
+        if ((st = two_level_pcg_step(ctx, r, z1, zf, 0, S)) != MLS_OK) return st;
         prof_end(ctx, tk);
       }
     }

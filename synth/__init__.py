@@ -21,4 +21,5 @@ from .workloads import (  # noqa: F401
     batched_lattice_scenes,
     tiny_scene,
     random_sparse_basis,
+    mlp_init,
 )

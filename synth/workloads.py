@@ -177,3 +177,15 @@ def random_sparse_basis(X: np.ndarray, m: int, k: int, seed: int):
     phi = np.take_along_axis(w, order, axis=1)
     vrow = (np.arange(n + 1) * k).astype(np.int32)
     return origins, vrow, handle.ravel(), phi.ravel()
+
+
+def mlp_init(sizes, seed: int):
+    """Initial weights of an MLP with layer widths ``sizes`` (e.g. [in, 256,
+    256, out]): W_k [out, in] ~ N(0, 2 / in) (He), biases zero.  Returned as a
+    flat list [W1, b1, W2, b2, ...] of float64 arrays."""
+    rng = np.random.default_rng(seed)
+    params = []
+    for fan_in, fan_out in zip(sizes[:-1], sizes[1:]):
+        params.append(rng.normal(scale=np.sqrt(2.0 / fan_in), size=(fan_out, fan_in)))
+        params.append(np.zeros(fan_out))
+    return params

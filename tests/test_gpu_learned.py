@@ -1,0 +1,72 @@
+"""The learned warm start on the beam workload: coarse projection parity
+against the oracle, and what a trained network gains over the plain start on
+held-out steps (with the plain Newton/PCG solve as the judge of its result).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ip, subspace
+
+from gpu_helpers import dev, host, solver_for, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def beam_basis():
+    from paper_2508_13386_gb300 import basis
+    s = synth.beam_scene(material_seed=4)
+    B = basis.build_sms_basis(s.X, s.tets, s.E, 32, dirichlet=s.dirichlet, seed=1)
+    return s, B
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-3)])
+def test_coarse_projection_matches_oracle(beam_basis, precision, tol):
+    s, B = beam_basis
+    solver = solver_for(s, precision=precision, preconditioner="two_level")
+    solver.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    rng = np.random.default_rng(0)
+    x = s.X + 0.01 * rng.normal(size=s.X.shape)
+    q = host(solver.coarse_project(dev(x)))
+    U = subspace.lbs_basis_matrix(s.X, B["origins"], B["vrow"], B["handle"], B["phi"])
+    M = np.repeat(ip.Problem(s).mass, 3)
+    UtMU = (U.T @ (U.multiply(M[:, None]))).toarray()
+    rhs = U.T @ (M * (x - s.X).ravel())
+    q_o = np.linalg.solve(UtMU, rhs).reshape(-1, 12)
+    assert np.max(np.abs(q - q_o)) <= tol * np.abs(q_o).max()
+
+
+def test_warm_start_gain_on_held_out_steps(beam_basis):
+    import paper_2508_13386_gb300 as mls
+    from paper_2508_13386_gb300 import learned
+    s, B = beam_basis
+    device = torch.device("cuda:0")
+    opts = dict(precision="fp32", preconditioner="two_level", cycle="multiplicative", omega=0.5,
+                newton_tol=1e-6, coarse_refresh=1000)
+    gen = solver_for(s, **opts)
+    gen.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    gen.warm_start_enable(True, record=True)
+    X, T, _ = learned.collect(gen, s, n_traj=12, n_steps=40, seed=7, device=device)
+    r = 12 * gen.m
+    net = mls.MLP([3 * r, 256, 256, r], synth.mlp_init([3 * r, 256, 256, r], 0), max_batch=256)
+    losses = learned.train(net, X, T, epochs=80, batch=128, lr=1e-3, seed=1)
+    assert losses[-1] < 0.5 * losses[0]
+    plain = solver_for(s, **opts)
+    plain.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    warm = solver_for(s, **opts)
+    warm.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    warm.warm_start_enable(True)
+    warm.warm_start_attach(net)
+    res = learned.evaluate(plain, warm, s, n_steps=30, seed=40, device=device)
+    # the judge: both starts converge to the same step
+    assert res["max_rel_diff"] <= 1e-4
+    used = sum(st["warm_start_used"] for st in res["warm"])
+    newton_p = sum(st["newton_iters"] for st in res["plain"])
+    newton_w = sum(st["newton_iters"] for st in res["warm"])
+    pcg_p = sum(st["pcg_iters"] for st in res["plain"])
+    pcg_w = sum(st["pcg_iters"] for st in res["warm"])
+    print(f"warm start used {used}/30, Newton {newton_p} -> {newton_w}, PCG {pcg_p} -> {pcg_w}, "
+          f"time {res['plain_s']:.3f}s -> {res['warm_s']:.3f}s")
+    assert used >= 15
+    assert pcg_w < pcg_p

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     text = open(os.path.join(ROOT, "include", "mls.h")).read()
-    return set(re.findall(r"^(?:mls_status|const char\*)\s+(mls_\w+)\(", text, re.M))
+    return set(re.findall(r"^(?:mls_status|const char\*|int64_t)\s+(mls_\w+)\(", text, re.M))
 
 
 def test_library_exports_every_declared_symbol():
