@@ -334,6 +334,36 @@ mls_status mls_warm_start_sample(mls_ctx* ctx, float* features, float* target);
 /* q(x) for DEVICE x [n][3] into DEVICE q [m][12] (float64). */
 mls_status mls_coarse_project(mls_ctx* ctx, const double* x, double* q);
 
+/* ---- Allocation-free elastic energy ------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory while they run (a fixed memory budget, a
+ * host framework that owns all device allocations, or code where an
+ * allocation's implicit synchronisation is not allowed).  It needs no
+ * context and calls no allocator: its reduction scratch is a file-scope
+ * device array (about 48 KB per device that uses it, held until the library
+ * is unloaded).
+ *
+ * Computes, with DEVICE pointers,
+ *   *energy_out  = sum_e vol_e psi(F_e(x))  (the Neo-Hookean energy of
+ *                  mls_eval_elements, summed in block order; rest shapes are
+ *                  formed from rest_xyz on the fly)
+ *   *invalid_out = number of tets skipped because an index lies outside
+ *                  [0, n_verts), the rest volume is <= 0 or J <= 0
+ * from rest_xyz [n_verts][3], x [n_verts][3], tets [n_tets][4] (int32),
+ * mu, lam [n_tets] (Lame parameters).  Work is queued on stream (a
+ * cudaStream_t, NULL = legacy default) and the call returns without waiting;
+ * results are valid once the stream reaches that point.
+ * Limits: n_tets <= MLS_NOALLOC_MAX_TETS, else MLS_EINVAL.  All calls share
+ * the scratch: calls whose kernels can overlap on the GPU (other streams or
+ * host threads on the same device) race and must be serialised.  The first
+ * call on each device looks up the scratch address with that device current;
+ * make it before any stream capture. */
+#define MLS_NOALLOC_MAX_TETS (4096 * 256)
+mls_status mls_elastic_energy_noalloc(int32_t n_verts, int32_t n_tets, const double* rest_xyz,
+                                      const int32_t* tets, const double* mu, const double* lam,
+                                      const double* x, double* energy_out, int32_t* invalid_out,
+                                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,7 @@ SIGNATURES = {
     "mls_ccd_bound": [_P, _P, _P, C.POINTER(_D)],
     "mls_profile_enable": [_P, C.c_uint32],
     "mls_profile_read": [_P, _P, _P],
+    "mls_elastic_energy_noalloc": [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P],
     "mls_mlp_create": [C.POINTER(_P), _I32, _I32, _I32, _I32, _P, _P],
     "mls_mlp_destroy": [_P],
     "mls_mlp_param_count": [_P],
