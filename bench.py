@@ -57,13 +57,16 @@ def parse():
     ap.add_argument("--grid", type=int, default=41, help="lattice grid size (41: ~224K tets, 48: ~360K)")
     ap.add_argument("--handles", type=int, default=160)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
-    ap.add_argument("--cycle", default="additive", choices=["additive", "multiplicative"])
-    ap.add_argument("--omega", type=float, default=1.0, help="block-Jacobi damping in the cycle")
+    ap.add_argument("--cycle", default="multiplicative", choices=["additive", "multiplicative"])
+    ap.add_argument("--omega", type=float, default=0.5, help="block-Jacobi damping in the cycle")
     ap.add_argument("--coarse-refresh", type=int, default=1000,
                     help="rebuild U^T H U every k Newton iterations (>= the Newton count: once per step)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="plain FP64 steps timed for comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end pass")
+    ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
+                    help="1: PCG iterations in one persistent cooperative kernel per solve")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="persistent kernel blocks per SM (0: library default)")
     ap.add_argument("--profile-run", action="store_true",
                     help="only warm-up and timed steps (for ncu: the timed steps sit in NVTX range 'mls_timed')")
     return ap.parse_args()
@@ -165,6 +168,28 @@ def spmv_bytes(solver_meta, precision):
     return nnzb * (9 * sm + 4) + 4 * n + 5 * 3 * n * sv
 
 
+def pcg_iteration_bytes(meta, precision, cycle):
+    """Algorithmic bytes of one PCG iteration of the persistent kernel: every
+    array each phase must touch, once (products: H's blocks, column indices
+    and row lengths, the gathered vector counted once; restriction and
+    prolongation: one 4-coefficient row and an index per vertex-handle pair;
+    the coarse solve: both triangular factors)."""
+    n, nnzb, nb, rc = meta["n"], meta["nnzb"], meta["basis_nnz"], meta["rc"]
+    sv = 8 if precision == "fp64" else 4
+    sm = {"fp64": 8, "fp32": 4, "bf16": 2}[precision]
+    H = nnzb * (9 * sm + 4) + 4 * n
+    vec = 3 * sv * n
+    dinv = 9 * sv * n
+    restrict = nb * (7 * sv + 4) + (n + 1) * 4
+    prolong = nb * (4 * sv + 4) + (n + 1) * 4
+    coarse = rc * (rc + 1) * sv
+    if cycle == "jacobi":
+        return H + 5 * vec + 7 * vec + dinv
+    if cycle == "additive":
+        return H + 5 * vec + 7 * vec + dinv + restrict + coarse + prolong + 3 * vec
+    return 3 * H + 5 * vec + (7 * vec + dinv) + 3 * vec + restrict + coarse + prolong + 2 * vec + (3 * vec + dinv)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -214,7 +239,8 @@ def main():
     def make(precision, precond):
         s = mls.Solver(precision=precision, preconditioner=precond, cycle=args.cycle, omega=args.omega,
                        newton_tol=1e-5 if precision != "fp64" else 1e-10,
-                       coarse_refresh=args.coarse_refresh, stream=stream)
+                       coarse_refresh=args.coarse_refresh, persistent=bool(args.persistent),
+                       persist_blocks_per_sm=args.blocks_per_sm, stream=stream)
         s.setup_scene(scene)
         if precond == "two_level":
             s.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
@@ -247,7 +273,7 @@ def main():
         disp_err = float(torch.linalg.norm(dxm - dx64) / torch.linalg.norm(dx64))
     torch.cuda.synchronize()
     # timed region
-    ours.profile_enable(["spmv"])
+    ours.profile_enable(["spmv", "pcg_fused"])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
     if world > 1:
@@ -277,7 +303,8 @@ def main():
     # per kernel-class breakdown on one extra (untimed) step from the same state
     breakdown = None
     if not args.profile_run:
-        ours.profile_enable(["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky"])
+        ours.profile_enable(["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky",
+                             "linesearch", "pcg_fused"])
         xb, vb = x.clone(), v.clone()
         _, st_b = ours.newton_step(xb, vb, h)
         breakdown = {k: {"ms": round(ms, 3), "launches": n} for k, (ms, n) in ours.profile_read().items() if n}
@@ -309,14 +336,28 @@ def main():
         xh = xh + dxh
     e2e_s = time.perf_counter() - t0
     e2e_value = world * e2e_steps / e2e_s if e2e_steps else None
-    # roofline of the dominant kernel (the PCG product)
-    spmv_ms, spmv_n = prof["spmv"]
-    meta = {"nnzb": int(ours_meta_nnzb(ours)), "n": scene.n_verts}
-    bytes_per = spmv_bytes(meta, args.precision)
+    # roofline of the dominant kernel: the persistent PCG kernel (or, with
+    # one launch per phase, the PCG product)
+    meta = {"nnzb": int(ours_meta_nnzb(ours)), "n": scene.n_verts, "basis_nnz": int(len(B["handle"])),
+            "rc": 12 * len(B["origins"])}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = bytes_per / (spmv_ms / max(spmv_n, 1) / 1e3) / 1e9 if spmv_n else None
+    pcg_total = sum(s["pcg_iters"] for s in stats)
+    if args.persistent:
+        k_ms, k_n = prof["pcg_fused"]
+        per_iter = pcg_iteration_bytes(meta, args.precision, args.cycle)
+        total_bytes = per_iter * pcg_total
+        roof = {"kernel": "k_pcg_persistent", "bytes_per_iteration": per_iter, "iterations": pcg_total,
+                "bytes_per_launch": total_bytes / max(k_n, 1)}
+    else:
+        k_ms, k_n = prof["spmv"]
+        total_bytes = spmv_bytes(meta, args.precision) * k_n
+        roof = {"kernel": "k_pcg_spmv", "bytes_per_launch": spmv_bytes(meta, args.precision)}
+    achieved = total_bytes / (k_ms / 1e3) / 1e9 if k_n else None
+    roof.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                 "frac": (achieved / peak) if achieved else None, "traffic": None, "launches": k_n,
+                 "avg_launch_us": 1e3 * k_ms / max(k_n, 1), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"})
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -327,7 +368,6 @@ def main():
         npcg = float(np.mean([s["pcg_iters"] for s in fp64_stats])) / max(nit, 1) if fp64_stats else REF_PCG
         rate, desc, spent = cpu_sample(scene, nit, npcg)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
-    pcg_total = sum(s["pcg_iters"] for s in stats)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
@@ -338,7 +378,8 @@ def main():
                                f"E log-uniform 1e5-1e8 (32 Voronoi cells), ground barrier dhat=1e-3 kappa=1e5, "
                                f"implicit Euler h=1/60, dropped at 1 m/s from 0.05 m (timed steps {args.warmup}..)",
                    "solver": f"{args.precision} two-level PCG ({args.cycle}), SMS basis m={len(B['origins'])} "
-                             f"(r={12 * len(B['origins'])}), coarse refresh every {args.coarse_refresh}",
+                             f"(r={12 * len(B['origins'])}), coarse refresh every {args.coarse_refresh}, "
+                             + ("persistent PCG kernel" if args.persistent else "one launch per PCG phase"),
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "pcg_iters_per_s": pcg_total / total_s,
@@ -352,10 +393,7 @@ def main():
                        "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in fp64_stats])) if fp64_stats else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * 3 * 8 * scene.n_verts,
                 "d2h_bytes_per_step": 3 * 8 * scene.n_verts},
-        "roofline": {"kernel": "k_pcg_spmv", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "bytes_per_launch": bytes_per, "launches": spmv_n,
-                     "avg_launch_us": 1e3 * spmv_ms / max(spmv_n, 1), "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "roofline": roof,
         "clocks": clocks.summary(),
         "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
         "cpu_baseline": cpu,

@@ -90,7 +90,12 @@ typedef struct mls_options {
   int max_pcg;         /* PCG iteration cap per Newton iteration */
   int coarse_refresh;  /* 0: rebuild U^T H U and its factor every Newton iteration;
                           k > 0: at the first iteration of a step and then every k */
-  int pcg_check_every; /* PCG iterations launched between host convergence checks */
+  int pcg_check_every; /* PCG iterations launched between host convergence checks
+                          (separate-kernel mode) */
+  int persistent;      /* 1: run the PCG iterations in one cooperative persistent
+                          kernel per solve; 0 (default): one launch per phase */
+  int persist_blocks_per_sm; /* resident blocks per SM of the persistent kernel
+                          (0: the library's choice; capped by occupancy) */
   void* stream;        /* cudaStream_t the context runs on (0 = legacy default) */
 } mls_options;
 
@@ -111,7 +116,7 @@ typedef struct mls_ctx mls_ctx;
 /* Fill *opt with defaults: FP64, block Jacobi, newton_tol 1e-10, pcg_rtol
  * 1e-4 (the paper's subspace PCG tolerance, Sec. 3.7.1), 50 Newton and 20000
  * PCG iterations, additive cycle, omega 1, coarse_refresh 0, check every 16,
- * default stream.  Returns MLS_EINVAL if opt is NULL. */
+ * one launch per PCG phase, default stream.  Returns MLS_EINVAL if opt is NULL. */
 mls_status mls_default_options(mls_options* opt);
 
 /* Create a context on the current CUDA device.  opt may be NULL (defaults).
@@ -250,7 +255,8 @@ enum {
   MLS_PROF_GALERKIN = 5,  /* U^T H U */
   MLS_PROF_CHOLESKY = 6,  /* coarse factorisation and inverse */
   MLS_PROF_LINESEARCH = 7,/* energy / CCD / norm reductions */
-  MLS_PROF_COUNT = 8
+  MLS_PROF_PCG_FUSED = 8, /* the persistent PCG kernel (one launch per solve) */
+  MLS_PROF_COUNT = 9
 };
 
 /* Enable timing for the classes whose bits are set in mask (bit k = class k;
@@ -312,7 +318,8 @@ mls_status mls_mlp_column_stats(const float* X, int32_t n, int32_t d, float* mea
 /* ---- Warm start from the coarse state ------------------------------------
  * Coarse coordinates q(x) = (U^T M U)^{-1} U^T M (x - X) of the uploaded SMS
  * basis.  While enabled, every mls_newton_step records q(x^t) in a history and
- * forms the features f = [q^t - q^{t-1}, q^{t-1} - q^{t-2}, q(X + h^2 g) - q(X)];
+ * forms the features f = [q^t, q^{t-1}, q(X + h^2 g)] (the coarse coordinates of
+ * the last two steps and of the gravity displacement);
  * when recording it also computes, after the step, the target
  * dq = (U^T H U)^{-1} U^T H (x^{t+1} - x_tilde) (the Galerkin coarse
  * projection of the step, H and its coarse factor taken at the first Newton

@@ -35,6 +35,8 @@ class Options(C.Structure):
         ("max_pcg", C.c_int),
         ("coarse_refresh", C.c_int),
         ("pcg_check_every", C.c_int),
+        ("persistent", C.c_int),
+        ("persist_blocks_per_sm", C.c_int),
         ("stream", C.c_void_p),
     ]
 
@@ -104,7 +106,7 @@ SIGNATURES = {
     "mls_coarse_project": [_P, _P, _P],
 }
 PROF_CLASSES = ["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky",
-                "linesearch"]
+                "linesearch", "pcg_fused"]
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:

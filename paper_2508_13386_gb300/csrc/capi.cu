@@ -147,6 +147,8 @@ mls_status mls_default_options(mls_options* opt) {
   opt->max_pcg = 20000;
   opt->coarse_refresh = 0;
   opt->pcg_check_every = 16;
+  opt->persistent = 0;
+  opt->persist_blocks_per_sm = 0;
   opt->stream = nullptr;
   return MLS_OK;
 }
@@ -157,6 +159,8 @@ static mls_status check_options(const mls_options* o) {
   if (o->cycle < 0 || o->cycle > 1) return MLS_EINVAL;
   if (!(o->newton_tol > 0) || !(o->pcg_rtol > 0) || o->max_newton < 1 || o->max_pcg < 1) return MLS_EINVAL;
   if (!(o->omega > 0) || o->coarse_refresh < 0 || o->pcg_check_every < 1) return MLS_EINVAL;
+  if (o->persistent < 0 || o->persistent > 1 || o->persist_blocks_per_sm < 0 || o->persist_blocks_per_sm > 32)
+    return MLS_EINVAL;
   return MLS_OK;
 }
 
@@ -405,6 +409,9 @@ static mls_status alloc_state(mls_ctx* ctx) {
   for (void** b : sv)
     if ((st = dalloc(ctx, b, (size_t)vb * 4 * n)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->pcg, sizeof(PcgScalars))) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->persist_part, sizeof(double) * 4 * kMaxPersistBlocks)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->persist_bar, 64)) != MLS_OK) return st;
+  if ((st = cuda_check(ctx, cudaMemset(ctx->persist_bar, 0, 64), "barrier init")) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->dscal, sizeof(double) * 16)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->red.partials, sizeof(double) * 4 * kMaxPartials)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->red.counter, sizeof(unsigned) * RS_COUNT)) != MLS_OK) return st;

@@ -35,6 +35,7 @@ constexpr int kSlice = 32;
 constexpr int kMaxPartials = 8192;
 constexpr int kGalerkinChunk = 128;
 constexpr int kRestrictChunk = 256;
+constexpr int kMaxPersistBlocks = 4096;
 
 // offsets of the 10 upper 3x3 blocks inside the 78-value element Hessian
 // (order (0,0),(0,1),(0,2),(0,3),(1,1),(1,2),(1,3),(2,2),(2,3),(3,3))
@@ -255,6 +256,10 @@ struct mls_ctx {
   void* vw = nullptr;
   void* vz2 = nullptr;             // preconditioned residual of the multiplicative cycle
   mls::PcgScalars* pcg = nullptr;  // device
+  double* persist_part = nullptr;  // [kMaxPersistBlocks][4] persistent-PCG block partials
+  void* persist_bar = nullptr;     // persistent-PCG grid barrier state
+  int persist_blocks = 0;          // cooperative grid size (0 = not yet sized)
+  int persist_bps = -1;            // (blocks per SM, precision, cycle) it was sized for
   mls::PcgScalars* pcg_host = nullptr;  // pinned
   double* dscal = nullptr;         // device scalars [16]
   double* dscal_host = nullptr;    // pinned [16]
@@ -352,6 +357,7 @@ mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double sca
 mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst);      // zero on Dirichlet vertices
 mls_status launch_from_solve_raw(mls_ctx* ctx, const void* src, Vec4d* dst);  // no masking
 mls_status pcg_solve(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res);
+mls_status launch_persistent_pcg(mls_ctx* ctx, int cycle, int iters);
 mls_status precond_apply(mls_ctx* ctx, const void* r, void* z);
 
 mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* vrow,

@@ -395,9 +395,24 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
     if ((st = launch_jacobi(ctx, r, z1, ctx->opt.omega, S)) != MLS_OK) return st;
     if ((st = two_level_pcg_step(ctx, r, z1, zf, 1, S)) != MLS_OK) return st;
   }
+  if (ctx->opt.persistent) {
+    const int cycle = jacobi ? 0 : (mult ? 2 : 1);
+    int tk = prof_begin(ctx, MLS_PROF_PCG_FUSED);
+    if ((st = launch_persistent_pcg(ctx, cycle, max_iter)) != MLS_OK) return st;
+    prof_end(ctx, tk);
+    st = cuda_check(ctx, cudaMemcpyAsync(ctx->pcg_host, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, ctx->stream),
+                    "pcg readback");
+    if (st != MLS_OK) return st;
+    if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "pcg sync")) != MLS_OK) return st;
+    prof_flush(ctx);
+    if (ctx->pcg_host->done == 4) {
+      cudaMemsetAsync(ctx->persist_bar, 0, 64, ctx->stream);
+      return fail(ctx, MLS_ETIMEOUT, "persistent PCG: a grid barrier wait gave up");
+    }
+  }
   const int chunk = ctx->opt.pcg_check_every > 0 ? ctx->opt.pcg_check_every : 16;
   const VT omega = (VT)ctx->opt.omega;
-  for (;;) {
+  for (; !ctx->opt.persistent;) {
     for (int c = 0; c < chunk; ++c) {
       int tk = prof_begin(ctx, MLS_PROF_SPMV);
       { ++ctx->launches; k_pcg_spmv<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(A, val, zf, p, q, ctx->red, S); }

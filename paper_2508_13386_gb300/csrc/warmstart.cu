@@ -2,8 +2,10 @@
 //
 // Coarse coordinates of a configuration x are the mass-weighted projection
 // onto the basis, q(x) = (U^T M U)^{-1} U^T M (x - X).  For each timestep the
-// features are [q^t - q^{t-1}, q^{t-1} - q^{t-2}, q_g] with q_g the coarse
-// coordinates of the gravity displacement h^2 g.  The target is the coarse
+// features are the coarse coordinates of the last two steps and of the
+// external load, [q^t, q^{t-1}, q_g], with q_g the coarse coordinates of the
+// gravity displacement h^2 g: q^t carries the deformation that sets the
+// elastic force, q^t - q^{t-1} the velocity that sets x_tilde.  The target is the coarse
 // Newton increment of the step: the Galerkin (H-orthogonal) projection
 // dq = (U^T H U)^{-1} U^T H (x^{t+1} - x_tilde) with H and U^T H U taken at the
 // step's first iterate, so that U dq is the best coarse approximation of the
@@ -59,14 +61,13 @@ __global__ void k_from_float(int n, const float* __restrict__ a, VT* __restrict_
   if (i < n) b[i] = (VT)a[i];
 }
 
-// features [q0 - q1, q1 - q2, qg] (float)
+// features [q^t, q^{t-1}, qg] (float)
 __global__ void k_features(int r, const double* __restrict__ hist, const double* __restrict__ qg,
                            float* __restrict__ f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= r) return;
-  const double q0 = hist[i], q1 = hist[r + i], q2 = hist[2 * r + i];
-  f[i] = (float)(q0 - q1);
-  f[r + i] = (float)(q1 - q2);
+  f[i] = (float)hist[i];
+  f[r + i] = (float)hist[r + i];
   f[2 * r + i] = (float)qg[i];
 }
 

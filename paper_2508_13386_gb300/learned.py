@@ -12,7 +12,8 @@ Protocol (the learned-warm-start workload): the beam geometry with a new
 material seed; training trajectories each start at rest under a random
 gravity (direction within 60 degrees of -z, magnitude 9.81 x U[0.5, 1.5])
 with a random initial tip velocity; the network (3r -> 256 -> 256 -> r)
-learns the coarse increment q(x^{t+1}) - q(x_tilde); a held-out trajectory
+maps [q^t, q^{t-1}, q(h^2 g)] to the Galerkin coarse projection of the
+step's increment x^{t+1} - x_tilde; a held-out trajectory
 with another seed measures what the warm start saves against the plain
 start on the same states.
 """
@@ -83,16 +84,28 @@ def train(mlp, X, T, epochs=60, batch=256, lr=1e-3, seed=0):
     return losses
 
 
-def evaluate(solver_plain, solver_ws, scene, n_steps, seed, device):
+def evaluate(solver_plain, solver_ws, scene, n_steps, seed, device, recorder=None):
     """Held-out trajectory: the plain solver advances it; the warm-started
     solver takes each step from the same state.  Returns per-step statistics
-    of both and the largest relative difference between their results."""
+    of both and the largest relative difference between their results.  With
+    a recorder (a third solver with target recording enabled and no network)
+    it also takes each step from the same state and returns the held-out
+    features and targets, on which the network's prediction error is
+    measured."""
     import torch
     rng = np.random.default_rng(seed)
     g, v0 = random_loads(scene, rng)
-    for s in (solver_plain, solver_ws):
+    solvers = (solver_plain, solver_ws) + ((recorder,) if recorder is not None else ())
+    for s in solvers:
         s.set_forces(tuple(g), scene.contact, scene.plane_n, scene.plane_o, scene.dhat, scene.kappa)
     solver_ws.warm_start_reset()
+    feats = targs = None
+    if recorder is not None:
+        recorder.warm_start_reset()
+        r = 12 * recorder.m
+        feats = torch.empty(n_steps, 3 * r, dtype=torch.float32, device=device)
+        targs = torch.empty(n_steps, r, dtype=torch.float32, device=device)
+        dxr = torch.empty_like(torch.as_tensor(scene.x0, device=device))
     x = torch.as_tensor(scene.x0, device=device).contiguous()
     v = torch.as_tensor(v0, device=device).contiguous()
     dxp = torch.empty_like(x)
@@ -100,7 +113,10 @@ def evaluate(solver_plain, solver_ws, scene, n_steps, seed, device):
     plain, warm = [], []
     worst = 0.0
     tp = tw = 0.0
-    for _ in range(n_steps):
+    for k in range(n_steps):
+        if recorder is not None:
+            recorder.newton_step(x, v, scene.dt, dx=dxr)
+            recorder.warm_start_sample(feats[k], targs[k])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, sp = solver_plain.newton_step(x, v, scene.dt, dx=dxp)
@@ -118,4 +134,5 @@ def evaluate(solver_plain, solver_ws, scene, n_steps, seed, device):
             worst = max(worst, float(torch.linalg.norm(dxw - dxp)) / den)
         v.copy_(dxp / scene.dt)
         x.add_(dxp)
-    return {"plain": plain, "warm": warm, "max_rel_diff": worst, "plain_s": tp, "warm_s": tw}
+    return {"plain": plain, "warm": warm, "max_rel_diff": worst, "plain_s": tp, "warm_s": tw,
+            "features": feats, "targets": targs}

@@ -93,11 +93,12 @@ def test_spmv_matches_oracle(precision, tol):
     assert np.max(np.abs(y - y_o)) <= tol * np.abs(H).max() * np.abs(v).max() * 16
 
 
+@pytest.mark.parametrize("persistent", [True, False])
 @pytest.mark.parametrize("precision,rtol", [("fp64", 1e-10), ("fp32", 1e-5)])
-def test_pcg_solves_newton_system(precision, rtol):
+def test_pcg_solves_newton_system(precision, rtol, persistent):
     s = synth.tiny_scene(6, 3, 3, seed=5, E_range=(1e5, 1e8))
     p = ip.Problem(s)
-    solver = solver_for(s, precision=precision)
+    solver = solver_for(s, precision=precision, persistent=persistent)
     solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
     H = p.hessian(p.x_tilde)
     b = -p.gradient(p.x_tilde)
@@ -109,6 +110,37 @@ def test_pcg_solves_newton_system(precision, rtol):
     # error bound through the condition number of H
     cond = np.linalg.cond(H.toarray())
     assert np.linalg.norm(host(d) - d_o) <= 10 * rtol * cond * np.linalg.norm(d_o)
+
+
+@pytest.mark.parametrize("cycle", ["additive", "multiplicative"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_persistent_two_level_pcg_matches_phase_kernels(precision, cycle):
+    """The persistent PCG kernel and the one-launch-per-phase loop run the
+    same iteration (only the order of the float64 reductions differs): same
+    iteration count within one, same solution to the solve tolerance, and
+    the true residual of both within the tolerance."""
+    s = synth.tiny_scene(9, 4, 3, seed=21, E_range=(1e5, 1e9))   # 200 vertices: 7 slices, ragged tail
+    p = ip.Problem(s)
+    H = p.hessian(p.x_tilde)
+    b = -p.gradient(p.x_tilde)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=7, k=3, seed=2)
+    rtol = 1e-9 if precision == "fp64" else 1e-5
+    out = []
+    for persistent in (True, False):
+        solver = solver_for(s, precision=precision, preconditioner="two_level", cycle=cycle, omega=0.5,
+                            persistent=persistent)
+        solver.upload_basis(origins, vrow, handle, phi)
+        solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
+        solver.build_coarse()
+        d, iters, rel, st = solver.pcg_solve(dev(b), rtol=rtol, max_iter=2000)
+        assert st == 0 and iters > 0
+        dh = host(d)
+        assert np.linalg.norm(b.ravel() - H @ dh.ravel()) <= 10 * rtol * np.linalg.norm(b)
+        out.append((dh, iters))
+    (d1, i1), (d2, i2) = out
+    assert abs(i1 - i2) <= 1
+    if i1 == i2:   # same iteration: only reduction rounding separates the iterates
+        assert np.linalg.norm(d1 - d2) <= (1e-10 if precision == "fp64" else 1e-4) * np.linalg.norm(d2)
 
 
 def test_pcg_zero_rhs():
