@@ -341,6 +341,71 @@ mls_status mls_warm_start_sample(mls_ctx* ctx, float* features, float* target);
 /* q(x) for DEVICE x [n][3] into DEVICE q [m][12] (float64). */
 mls_status mls_coarse_project(mls_ctx* ctx, const double* x, double* q);
 
+/* ---- Batched timestep of many independent meshes -----------------------
+ * Advances B independent meshes by one implicit-Euler step each (the
+ * timestep of mls_newton_step: projected Newton on the incremental potential,
+ * Eq. 5, with the filtered line search of Sec. 3.9), solving every Newton
+ * system with block-Jacobi PCG.  Each mesh keeps its own Newton and PCG
+ * scalars, tolerances and stopping decisions; a finished mesh idles while the
+ * others continue.  One timestep is one CUDA graph launch: the Newton, PCG
+ * and line-search loops are WHILE conditional nodes whose conditions are set
+ * on the device from the per-mesh states.  The first step times candidate
+ * launch shapes of the PCG kernels on the assembled system and keeps the
+ * fastest (mls_batch_retune forgets the choice).
+ *
+ * Options as for mls_create; the preconditioner must be block Jacobi
+ * (otherwise MLS_EINVAL); cycle, omega, coarse_refresh and the persistent
+ * settings are ignored.  Forces (gravity, ground plane, barrier) are shared by
+ * all meshes.  The batch owns a context and an internal stream, ordered after
+ * opt->stream on every step.  Not in the paper. */
+typedef struct mls_batch mls_batch;
+
+typedef struct mls_batch_mesh_stats {
+  int32_t status;             /* MLS_OK, MLS_ENOTCONV, MLS_ELINESEARCH, MLS_ENONFINITE, MLS_EINVERTED */
+  int32_t newton_iters;
+  int32_t pcg_iters;          /* summed over the mesh's Newton iterations */
+  int32_t line_search_trials;
+  double step_rel;            /* last |d|_inf / max(|x - x^t|_inf, h^2 |g|) */
+  double grad_norm;           /* |g|_2 at the last Newton iteration */
+  double energy;              /* E at the returned state */
+} mls_batch_mesh_stats;
+
+typedef struct mls_batch_info {
+  int64_t kernel_launches;    /* kernels run by the step (graph nodes executed + 2) */
+  int32_t graph_launches;     /* graph launches of the step (1) */
+  int32_t newton_rounds;      /* Newton loop bodies run (max Newton count over meshes) */
+  int32_t pcg_rounds;         /* PCG loop bodies run (2 iterations each) */
+  int32_t line_search_rounds; /* line-search loop bodies run */
+  int32_t spmv_lanes;         /* tuned lanes per row of the product (4 or 8) */
+  int32_t row_threads;        /* tuned threads per block of the row kernels */
+  int32_t rows_per_thread;    /* tuned rows per thread of the row kernels */
+  double tune_ms;             /* time spent timing candidates (first step) */
+} mls_batch_info;
+
+mls_status mls_batch_create(mls_batch** out, const mls_options* opt);
+mls_status mls_batch_destroy(mls_batch* b);
+const char* mls_batch_last_error(const mls_batch* b);
+/* B meshes concatenated: mesh m owns vertices [vert_offsets[m],
+ * vert_offsets[m+1]) and tets [tet_offsets[m], tet_offsets[m+1]); tets hold
+ * GLOBAL vertex indices of the concatenation, each tet within its own mesh.
+ * rest_xyz [V][3], tets [T][4], youngs/poisson/density [T], dirichlet [V]
+ * (nullable), all HOST arrays, copied.  MLS_EINVAL for an empty mesh, a tet
+ * crossing meshes, or anything mls_upload_mesh rejects. */
+mls_status mls_batch_upload(mls_batch* b, int32_t n_meshes, const int32_t* vert_offsets,
+                            const int32_t* tet_offsets, const double* rest_xyz, const int32_t* tets,
+                            const double* youngs, const double* poisson, const double* density,
+                            const uint8_t* dirichlet);
+mls_status mls_batch_set_forces(mls_batch* b, const double* gravity, int contact, const double* plane_n,
+                                double plane_o, double dhat, double kappa);
+mls_status mls_batch_retune(mls_batch* b);
+/* One timestep of every mesh from DEVICE x, v [V][3] (float64, concatenated)
+ * into DEVICE dx [V][3].  stats (HOST [B], nullable) receives per-mesh
+ * results, info (HOST, nullable) the launch counts.  Returns MLS_OK when every
+ * mesh succeeded, else the status of the first failing mesh (dx is written
+ * for all meshes; a mesh with MLS_ENOTCONV returns its last iterate). */
+mls_status mls_batch_step(mls_batch* b, const double* x, const double* v, double dt, double* dx_out,
+                          mls_batch_mesh_stats* stats, mls_batch_info* info);
+
 /* ---- Allocation-free elastic energy ------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory while they run (a fixed memory budget, a

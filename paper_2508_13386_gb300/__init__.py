@@ -296,6 +296,107 @@ class Solver:
         return a.value
 
 
+class Batch:
+    """Many independent meshes advanced together (``mls_batch``): one graph
+    launch per timestep, block-Jacobi PCG, per-mesh Newton decisions."""
+
+    def __init__(self, precision="fp32", newton_tol=1e-5, pcg_rtol=1e-4, max_newton=50, max_pcg=20000,
+                 stream=None):
+        self._l = _get_lib()
+        self._b = C.c_void_p()
+        opt = _lib.Options()
+        self._l.mls_default_options(C.byref(opt))
+        opt.precision = _lib.PRECISION[precision]
+        opt.preconditioner = _lib.PRECOND["jacobi"]
+        opt.newton_tol = float(newton_tol)
+        opt.pcg_rtol = float(pcg_rtol)
+        opt.max_newton = int(max_newton)
+        opt.max_pcg = int(max_pcg)
+        opt.stream = None if stream is None else C.c_void_p(stream.cuda_stream)
+        st = self._l.mls_batch_create(C.byref(self._b), C.byref(opt))
+        if st != _lib.MLS_OK:
+            raise MLSError(st, "mls_batch_create failed")
+        self.n_meshes = 0
+        self.vert_offsets = None
+
+    def close(self):
+        if self._b:
+            self._l.mls_batch_destroy(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=()):
+        if st != _lib.MLS_OK and st not in allow:
+            msg = self._l.mls_batch_last_error(self._b)
+            raise MLSError(st, msg.decode() if msg else "")
+        return st
+
+    def upload_scenes(self, scenes):
+        """Concatenate ``synth.Scene``-like meshes (forces from the first)."""
+        voff, toff, X, T, E, nu, rho, D = [0], [0], [], [], [], [], [], []
+        for sc in scenes:
+            nt = len(sc.tets)
+            X.append(np.asarray(sc.X, dtype=np.float64))
+            T.append(np.asarray(sc.tets, dtype=np.int64) + voff[-1])
+            E.append(np.broadcast_to(np.asarray(sc.E, dtype=np.float64), (nt,)))
+            nu.append(np.broadcast_to(np.asarray(sc.nu, dtype=np.float64), (nt,)))
+            rho.append(np.broadcast_to(np.asarray(sc.rho, dtype=np.float64), (nt,)))
+            D.append(np.asarray(sc.dirichlet, dtype=np.uint8) if sc.dirichlet is not None
+                     else np.zeros(len(sc.X), dtype=np.uint8))
+            voff.append(voff[-1] + len(sc.X))
+            toff.append(toff[-1] + nt)
+        self.upload(voff, toff, np.concatenate(X), np.concatenate(T), np.concatenate(E), np.concatenate(nu),
+                    np.concatenate(rho), np.concatenate(D))
+        s0 = scenes[0]
+        self.set_forces(s0.gravity, s0.contact, s0.plane_n, s0.plane_o, s0.dhat, s0.kappa)
+
+    def upload(self, vert_offsets, tet_offsets, X, tets, E, nu, rho, dirichlet=None):
+        vo, pvo = _host(vert_offsets, np.int32)
+        to, pto = _host(tet_offsets, np.int32)
+        X, pX = _host(X, np.float64)
+        tets, pT = _host(tets, np.int32)
+        E, pE = _host(E, np.float64)
+        nu, pN = _host(nu, np.float64)
+        rho, pR = _host(rho, np.float64)
+        pD = None
+        if dirichlet is not None:
+            dirichlet, pD = _host(dirichlet, np.uint8)
+        self._check(self._l.mls_batch_upload(self._b, len(vo) - 1, pvo, pto, pX, pT, pE, pN, pR, pD))
+        self.n_meshes = len(vo) - 1
+        self.vert_offsets = vo.copy()
+        self.n = int(vo[-1])
+
+    def set_forces(self, gravity=(0.0, 0.0, -9.81), contact=False, plane_n=(0.0, 0.0, 1.0), plane_o=0.0,
+                   dhat=1e-3, kappa=1e5):
+        g, pg = _host(gravity, np.float64)
+        pn, ppn = _host(plane_n, np.float64)
+        self._check(self._l.mls_batch_set_forces(self._b, pg, 1 if contact else 0, ppn, float(plane_o),
+                                                 float(dhat), float(kappa)))
+
+    def retune(self):
+        self._check(self._l.mls_batch_retune(self._b))
+
+    def step(self, x, v, dt, dx=None, allow=(-4,)):
+        """One timestep of every mesh; returns (dx, per-mesh stats, info).
+        Meshes that hit their Newton cap (-4) are reported, not raised."""
+        import torch
+        if dx is None:
+            dx = torch.empty_like(x)
+        stats = (_lib.BatchMeshStats * self.n_meshes)()
+        info = _lib.BatchInfo()
+        status = self._check(self._l.mls_batch_step(self._b, _dev(x, (self.n, 3)), _dev(v, (self.n, 3)), float(dt),
+                                                    _dev(dx, (self.n, 3)), stats, C.byref(info)), allow)
+        per = [{k: getattr(s, k) for k, _ in _lib.BatchMeshStats._fields_} for s in stats]
+        inf = {k: getattr(info, k) for k, _ in _lib.BatchInfo._fields_}
+        inf["status"] = status
+        return dx, per, inf
+
+
 class MLP:
     """A network trained and run by the library's kernels (``mls_mlp_*``)."""
 

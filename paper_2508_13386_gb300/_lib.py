@@ -104,7 +104,40 @@ SIGNATURES = {
     "mls_warm_start_attach": [_P, _P],
     "mls_warm_start_sample": [_P, _P, _P],
     "mls_coarse_project": [_P, _P, _P],
+    "mls_batch_create": [C.POINTER(_P), _P],
+    "mls_batch_last_error": [_P],
+    "mls_batch_destroy": [_P],
+    "mls_batch_upload": [_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P],
+    "mls_batch_set_forces": [_P, _P, C.c_int, _P, C.c_double, C.c_double, C.c_double],
+    "mls_batch_retune": [_P],
+    "mls_batch_step": [_P, _P, _P, C.c_double, _P, _P, _P],
 }
+class BatchMeshStats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32),
+        ("newton_iters", C.c_int32),
+        ("pcg_iters", C.c_int32),
+        ("line_search_trials", C.c_int32),
+        ("step_rel", C.c_double),
+        ("grad_norm", C.c_double),
+        ("energy", C.c_double),
+    ]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [
+        ("kernel_launches", C.c_int64),
+        ("graph_launches", C.c_int32),
+        ("newton_rounds", C.c_int32),
+        ("pcg_rounds", C.c_int32),
+        ("line_search_rounds", C.c_int32),
+        ("spmv_lanes", C.c_int32),
+        ("row_threads", C.c_int32),
+        ("rows_per_thread", C.c_int32),
+        ("tune_ms", C.c_double),
+    ]
+
+
 PROF_CLASSES = ["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky",
                 "linesearch", "pcg_fused"]
 
@@ -118,5 +151,6 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name, args in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = {"mls_last_error": C.c_char_p, "mls_mlp_param_count": C.c_int64}.get(name, C.c_int)
+        fn.restype = {"mls_last_error": C.c_char_p, "mls_batch_last_error": C.c_char_p,
+                      "mls_mlp_param_count": C.c_int64}.get(name, C.c_int)
     return lib

@@ -1,0 +1,1250 @@
+// Batched timestep: many independent meshes advanced together.
+//
+// Every mesh of the batch runs its own projected Newton loop on the
+// incremental potential (Sec. 3.1, Eq. 5) with a block-Jacobi PCG solve and
+// the filtered backtracking line search (Sec. 3.9) -- the same iteration as
+// the single-mesh timestep, with its own scalars, tolerances and stopping
+// decisions per mesh.  The meshes are stored as one concatenated mesh (their
+// Hessian is block diagonal), each mesh's vertex range padded with pinned
+// dummy vertices to whole 32-row slices, so that every SELL slice, every
+// row block and every tet block belongs to exactly one mesh.
+//
+// Control lives on the device.  Per-mesh reductions use block partials
+// summed in block order by the last block of that mesh to arrive (a
+// per-mesh counter), which then takes the mesh's decision (CG step sizes and
+// convergence, Newton tolerance and direction test, line-search acceptance)
+// in device memory.  A whole timestep is one CUDA graph: three nested WHILE
+// conditional nodes (Newton iterations, PCG iterations, line-search trials)
+// whose conditions are set by one-block kernels from the per-mesh states, so
+// the host launches one graph and reads the per-mesh statistics once.
+//
+// Launch shapes (lanes per row of the product, threads and rows per thread
+// of the row kernels) are chosen by timing the candidates on the first
+// timestep's assembled system (an autotuner); the graph is built for the
+// winner.
+#include "mls_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace mls {
+
+enum { BPH_ASSEMBLE = 0, BPH_LS = 1, BPH_FINAL = 2, BPH_DONE = 3 };
+enum { BC_PREP = 0, BC_SPMV, BC_UPD, BC_DIR, BC_ENERGY, BC_COUNT };
+
+// per-mesh state (device)
+struct BMesh {
+  double g0, gnorm, E0, gd, alpha, step_rel;
+  double bb, rr, rz, pq, alpha_p, beta, tol2;
+  int phase, newton, pcg, trials, halvings, status, apply, start_bad;
+  int iter, done, pad0, pad1;
+};
+
+struct BParams {        // per-timestep constants
+  double h2, scale0, newton_tol, pcg_rtol, eta_floor;
+  int max_newton, max_pcg;
+  double kappa, dhat, po, pn0, pn1, pn2;
+  int contact;
+};
+
+struct BView {
+  int nmesh;
+  // row blocks
+  int nrb;
+  const int* rb_mesh; const int* rb_row0; const int* rb_row1;
+  const int* rb_first; const int* rb_count;
+  // slices (32 rows)
+  const int* sl_mesh; const int* sl_first; const int* sl_count;
+  // tet blocks
+  int ntb;
+  const int* tb_mesh; const int* tb_t0; const int* tb_t1;
+  const int* tb_first; const int* tb_count;
+  const double* mass_min;        // [nmesh] smallest free-vertex mass
+  unsigned* cnt;                 // [BC_COUNT][nmesh], left at zero
+  double* part_rb;               // [nrb][4]
+  double* part_sl;               // [n_slices]
+  double* part_tb;               // [ntb][2]
+  BMesh* M;
+};
+
+constexpr int kTetBlock = 256;
+
+// ---- block reductions (any block size that is a multiple of 32, <= 1024) ----------------
+template <int K>
+__device__ __forceinline__ void bsum(double (&v)[K]) {
+  __shared__ double sh[K][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double s = lane < nw ? sh[k][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      v[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double bmax(double v) {
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < nw ? sh[lane] : -1e300;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  __syncthreads();
+  return v;
+}
+
+__device__ __forceinline__ double bmin(double v) { return -bmax(-v); }
+
+// Arrival of this block for mesh m; true in the last block of the mesh to
+// arrive (all its blocks' partials are then visible).  The counter is reset
+// by that block.
+__device__ __forceinline__ bool last_of_mesh(unsigned* counter, unsigned total) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(counter, 1u) == total - 1;
+    if (last) *counter = 0;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// ---- state kernels -----------------------------------------------------------------------
+__global__ void k_breset(int nmesh, BMesh* __restrict__ M) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= nmesh) return;
+  BMesh s{};
+  s.phase = BPH_ASSEMBLE;
+  s.status = MLS_OK;
+  s.done = 1;
+  s.alpha = 1.0;
+  M[m] = s;
+}
+
+// user [n_user][3] -> internal padded [n][3]; dummy rows parked far from the plane
+__global__ void k_bpack(int n, const int* __restrict__ vmap, const double* __restrict__ x,
+                        const double* __restrict__ v, double* __restrict__ bx, double* __restrict__ bv,
+                        double px, double py, double pz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int u = vmap[i];
+  if (u >= 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { bx[3 * i + k] = x[3 * (int64_t)u + k]; bv[3 * i + k] = v[3 * (int64_t)u + k]; }
+  } else {
+    bx[3 * i] = px; bx[3 * i + 1] = py; bx[3 * i + 2] = pz;
+    bv[3 * i] = 0.0; bv[3 * i + 1] = 0.0; bv[3 * i + 2] = 0.0;
+  }
+}
+
+__global__ void k_bunpack(int n, const int* __restrict__ vmap, const Vec4d* __restrict__ xk,
+                          const Vec4d* __restrict__ xt, double* __restrict__ dx) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int u = vmap[i];
+  if (u < 0) return;
+  const Vec4d a = xk[i], b = xt[i];
+  dx[3 * (int64_t)u] = a.x - b.x;
+  dx[3 * (int64_t)u + 1] = a.y - b.y;
+  dx[3 * (int64_t)u + 2] = a.z - b.z;
+}
+
+// ---- energy per mesh (tets, then vertices), three uses --------------------------------------
+// MODE 0: at x^t (must be feasible); MODE 1: at the predictor (start there
+// when feasible); MODE 2: a line-search trial x + alpha_m d.
+struct BEnergyIn {
+  int t;
+  const int* tets; const double* Dminv; const double* vol; const double* mu; const double* lam;
+  const double* mass; const uint8_t* pinned; const Vec4d* xtil;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kTetBlock) k_benergy(BView V, BEnergyIn in, BParams P, const Vec4d* __restrict__ x,
+                                                       const Vec4d* __restrict__ d) {
+  const bool tetblk = (int)blockIdx.x < V.ntb;
+  const int b = tetblk ? blockIdx.x : blockIdx.x - V.ntb;
+  const int m = tetblk ? V.tb_mesh[b] : V.rb_mesh[b];
+  BMesh* M = V.M + m;
+  const int phase = M->phase;
+  if (MODE == 2 ? (phase != BPH_LS && phase != BPH_FINAL) : phase == BPH_DONE) return;
+  const double alpha = MODE == 2 ? M->alpha : 0.0;
+  double acc[2] = {0.0, 0.0};
+  if (tetblk) {
+    const int t = in.t;
+    for (int e = V.tb_t0[b] + threadIdx.x; e < V.tb_t1[b]; e += blockDim.x) {
+      Vec4d p[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int v = in.tets[a * t + e];
+        Vec4d xv = x[v];
+        if (MODE == 2) {
+          const Vec4d dv = d[v];
+          xv.x += alpha * dv.x; xv.y += alpha * dv.y; xv.z += alpha * dv.z;
+        }
+        p[a] = xv;
+      }
+      double F[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double e1 = a == 0 ? p[1].x - p[0].x : a == 1 ? p[1].y - p[0].y : p[1].z - p[0].z;
+        const double e2 = a == 0 ? p[2].x - p[0].x : a == 1 ? p[2].y - p[0].y : p[2].z - p[0].z;
+        const double e3 = a == 0 ? p[3].x - p[0].x : a == 1 ? p[3].y - p[0].y : p[3].z - p[0].z;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          F[a][c] = e1 * in.Dminv[(0 + c) * t + e] + e2 * in.Dminv[(3 + c) * t + e] + e3 * in.Dminv[(6 + c) * t + e];
+      }
+      const double J = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                       F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                       F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+      if (J > 0.0) {
+        double I2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) I2 += F[a][c] * F[a][c];
+        const double lnJ = log(J), mu = in.mu[e], lam = in.lam[e];
+        acc[0] += P.h2 * in.vol[e] * (0.5 * mu * (I2 - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ);
+      } else {
+        acc[1] += 1.0;
+      }
+    }
+  } else {
+    for (int v = V.rb_row0[b] + threadIdx.x; v < V.rb_row1[b]; v += blockDim.x) {
+      Vec4d xv = x[v];
+      if (MODE == 2) {
+        const Vec4d dv = d[v];
+        xv.x += alpha * dv.x; xv.y += alpha * dv.y; xv.z += alpha * dv.z;
+      }
+      if (!in.pinned[v]) {
+        const Vec4d xt = in.xtil[v];
+        const double ex = xv.x - xt.x, ey = xv.y - xt.y, ez = xv.z - xt.z;
+        acc[0] += 0.5 * in.mass[v] * (ex * ex + ey * ey + ez * ez);
+      }
+      if (P.contact) {
+        const double dist = P.pn0 * xv.x + P.pn1 * xv.y + P.pn2 * xv.z - P.po;
+        if (dist <= 0.0) {
+          acc[1] += 1.0;
+        } else if (dist < P.dhat) {
+          const double r = dist - P.dhat;
+          acc[0] += P.h2 * P.kappa * (-r * r * log(dist / P.dhat));
+        }
+      }
+    }
+  }
+  bsum<2>(acc);
+  double* part = V.part_tb;  // tet blocks first, then row blocks, [ntb + nrb][2]
+  if (threadIdx.x == 0) { part[2 * (int64_t)blockIdx.x] = acc[0]; part[2 * (int64_t)blockIdx.x + 1] = acc[1]; }
+  const unsigned total = (unsigned)(V.tb_count[m] + V.rb_count[m]);
+  if (!last_of_mesh(V.cnt + BC_ENERGY * V.nmesh + m, total)) return;
+  double tot[2] = {0.0, 0.0};
+  const int tb0 = V.tb_first[m], ntbm = V.tb_count[m], rb0 = V.rb_first[m], nrbm = V.rb_count[m];
+  for (int i = threadIdx.x; i < ntbm + nrbm; i += blockDim.x) {
+    const int64_t blk = i < ntbm ? (int64_t)(tb0 + i) : (int64_t)(V.ntb + rb0 + i - ntbm);
+    tot[0] += __ldcg(part + 2 * blk);
+    tot[1] += __ldcg(part + 2 * blk + 1);
+  }
+  bsum<2>(tot);
+  if (threadIdx.x != 0) return;
+  const double E = tot[0];
+  const bool bad = tot[1] > 0.5 || !isfinite(E);
+  if (MODE == 0) {
+    if (bad) { M->status = MLS_EINVERTED; M->phase = BPH_DONE; }
+    else M->E0 = E;
+  } else if (MODE == 1) {
+    M->start_bad = bad ? 1 : 0;
+    if (!bad) M->E0 = E;
+  } else {
+    M->trials += 1;
+    M->apply = 0;
+    if (phase == BPH_FINAL) {
+      // converged: the final (tiny) direction is applied in full when feasible
+      M->apply = bad ? 0 : 1;
+      if (!bad) M->E0 = E;
+      M->phase = BPH_DONE;
+      M->status = MLS_OK;
+    } else {
+      const double a = M->alpha, cgd = 1e-4 * a * M->gd;
+      if (!bad && (fabs(cgd) <= 1e-13 * fabs(M->E0) || E <= M->E0 + cgd)) {
+        M->apply = 1;
+        M->E0 = E;
+        M->phase = BPH_ASSEMBLE;
+      } else {
+        M->alpha = 0.5 * a;
+        M->halvings += 1;
+        if (M->halvings > 60) { M->status = MLS_ELINESEARCH; M->phase = BPH_DONE; }
+      }
+    }
+  }
+}
+
+// meshes whose predictor is infeasible start from x^t
+__global__ void k_bselect(BView V, const Vec4d* __restrict__ xt, Vec4d* __restrict__ xk) {
+  const int m = V.rb_mesh[blockIdx.x];
+  if (!V.M[m].start_bad) return;
+  for (int v = V.rb_row0[blockIdx.x] + threadIdx.x; v < V.rb_row1[blockIdx.x]; v += blockDim.x) xk[v] = xt[v];
+}
+
+// x += alpha d for meshes whose trial was accepted
+__global__ void k_bapply(BView V, Vec4d* __restrict__ xk, const Vec4d* __restrict__ d) {
+  const int m = V.rb_mesh[blockIdx.x];
+  const BMesh* M = V.M + m;
+  if (!M->apply) return;
+  const double a = M->alpha;
+  for (int v = V.rb_row0[blockIdx.x] + threadIdx.x; v < V.rb_row1[blockIdx.x]; v += blockDim.x) {
+    Vec4d xv = xk[v];
+    const Vec4d dv = d[v];
+    xv.x += a * dv.x; xv.y += a * dv.y; xv.z += a * dv.z;
+    xk[v] = xv;
+  }
+}
+
+// ---- Newton iteration start: PCG initialisation and tolerance per mesh ---------------------
+template <typename VT>
+__global__ void k_bprep(BView V, BParams P, const Vec4d* __restrict__ grad, const Vec4<VT>* __restrict__ b,
+                        const VT* __restrict__ dinv, const Vec4d* __restrict__ xk, const Vec4d* __restrict__ xt,
+                        Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r, Vec4<VT>* __restrict__ z,
+                        Vec4<VT>* __restrict__ p, Vec4<VT>* __restrict__ q) {
+  const int m = V.rb_mesh[blockIdx.x];
+  BMesh* M = V.M + m;
+  if (M->phase != BPH_ASSEMBLE) return;
+  double acc[2] = {0.0, 0.0};  // g.g, r.z
+  double xd = 0.0;
+  const Vec4<VT> zero{VT(0), VT(0), VT(0), VT(0)};
+  for (int v = V.rb_row0[blockIdx.x] + threadIdx.x; v < V.rb_row1[blockIdx.x]; v += blockDim.x) {
+    const Vec4d g = grad[v];
+    acc[0] += g.x * g.x + g.y * g.y + g.z * g.z;
+    const Vec4<VT> bv = b[v];
+    const VT* D = dinv + (int64_t)v * 9;
+    const Vec4<VT> zv{D[0] * bv.x + D[1] * bv.y + D[2] * bv.z, D[3] * bv.x + D[4] * bv.y + D[5] * bv.z,
+                      D[6] * bv.x + D[7] * bv.y + D[8] * bv.z, VT(0)};
+    x[v] = zero; p[v] = zero; q[v] = zero;
+    r[v] = bv;
+    z[v] = zv;
+    acc[1] += (double)bv.x * zv.x + (double)bv.y * zv.y + (double)bv.z * zv.z;
+    const Vec4d a = xk[v], c = xt[v];
+    xd = fmax(xd, fmax(fabs(a.x - c.x), fmax(fabs(a.y - c.y), fabs(a.z - c.z))));
+  }
+  bsum<2>(acc);
+  xd = bmax(xd);
+  double* part = V.part_rb + 4 * (int64_t)blockIdx.x;
+  if (threadIdx.x == 0) { part[0] = acc[0]; part[1] = acc[1]; part[2] = xd; }
+  if (!last_of_mesh(V.cnt + BC_PREP * V.nmesh + m, (unsigned)V.rb_count[m])) return;
+  double tot[2] = {0.0, 0.0};
+  double xdm = 0.0;
+  const int rb0 = V.rb_first[m], nrbm = V.rb_count[m];
+  for (int i = threadIdx.x; i < nrbm; i += blockDim.x) {
+    const double* pp = V.part_rb + 4 * (int64_t)(rb0 + i);
+    tot[0] += __ldcg(pp);
+    tot[1] += __ldcg(pp + 1);
+    xdm = fmax(xdm, __ldcg(pp + 2));
+  }
+  bsum<2>(tot);
+  xdm = bmax(xdm);
+  if (threadIdx.x != 0) return;
+  M->newton += 1;
+  const double gnorm = sqrt(tot[0]);
+  M->gnorm = gnorm;
+  if (M->newton == 1) M->g0 = gnorm;
+  M->iter = 0;
+  M->beta = 0.0;
+  if (!isfinite(gnorm)) { M->status = MLS_ENONFINITE; M->phase = BPH_DONE; M->done = 1; return; }
+  if (gnorm == 0.0) { M->step_rel = 0.0; M->status = MLS_OK; M->phase = BPH_DONE; M->done = 1; return; }
+  // forcing term: min(rtol, sqrt(|g| / |g0|)), floored; absolute floor from
+  // H >= M: a residual below 0.01 tol scale m_min cannot move the step test
+  double eta = fmin(P.pcg_rtol, sqrt(gnorm / M->g0));
+  eta = fmax(eta, P.eta_floor);
+  const double abs_floor = 0.01 * P.newton_tol * fmax(xdm, P.scale0) * V.mass_min[m];
+  eta = fmax(eta, abs_floor / gnorm);
+  M->bb = tot[0];
+  M->rr = tot[0];
+  M->rz = tot[1];
+  M->tol2 = eta * eta * tot[0];
+  M->done = 0;
+}
+
+// ---- PCG iteration (block Jacobi), per-mesh scalars ---------------------------------------
+// Product: one slice (32 rows) per block, LANES lanes per row (4 or 8).
+template <typename VT, typename MT, int LANES>
+__global__ void __launch_bounds__(32 * LANES) k_bspmv(BView V, int n, const int* __restrict__ slice_ptr,
+                                                      const int* __restrict__ col, const int* __restrict__ row_len,
+                                                      const MT* __restrict__ val, const Vec4<VT>* __restrict__ z,
+                                                      Vec4<VT>* __restrict__ p, Vec4<VT>* __restrict__ q) {
+  const int s = blockIdx.x;
+  const int m = V.sl_mesh[s];
+  BMesh* M = V.M + m;
+  if (M->phase != BPH_ASSEMBLE || M->done) return;
+  const int part = threadIdx.x % LANES, rl = threadIdx.x / LANES;
+  const int row = s * 32 + rl;
+  const int len = row < n ? row_len[row] : 0;
+  const int64_t g0 = slice_ptr[s];
+  VT y0 = VT(0), y1 = VT(0), y2 = VT(0);
+  constexpr int U = 16 / LANES;
+  for (int k0 = part; k0 < len; k0 += 16) {
+    int c[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + LANES * u;
+      ok[u] = k < len;
+      c[u] = ok[u] ? __ldg(col + (g0 + k) * 32 + rl) : 0;
+    }
+    Vec4<VT> xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = ok[u] ? z[c[u]] : Vec4<VT>{VT(0), VT(0), VT(0), VT(0)};
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      const MT* v = val + (g0 + k0 + LANES * u) * 288 + rl;
+      y0 += load_as<VT>(v[0]) * xv[u].x + load_as<VT>(v[32]) * xv[u].y + load_as<VT>(v[64]) * xv[u].z;
+      y1 += load_as<VT>(v[96]) * xv[u].x + load_as<VT>(v[128]) * xv[u].y + load_as<VT>(v[160]) * xv[u].z;
+      y2 += load_as<VT>(v[192]) * xv[u].x + load_as<VT>(v[224]) * xv[u].y + load_as<VT>(v[256]) * xv[u].z;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < LANES; o <<= 1) {
+    y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+  }
+  double acc[1] = {0.0};
+  if (part == 0 && row < n) {
+    const VT beta = (VT)M->beta;
+    const Vec4<VT> zv = z[row], pv = p[row], qv = q[row];
+    const Vec4<VT> pn{zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, VT(0)};
+    const Vec4<VT> qn{y0 + beta * qv.x, y1 + beta * qv.y, y2 + beta * qv.z, VT(0)};
+    p[row] = pn;
+    q[row] = qn;
+    acc[0] = (double)pn.x * qn.x + (double)pn.y * qn.y + (double)pn.z * qn.z;
+  }
+  bsum<1>(acc);
+  if (threadIdx.x == 0) V.part_sl[s] = acc[0];
+  if (!last_of_mesh(V.cnt + BC_SPMV * V.nmesh + m, (unsigned)V.sl_count[m])) return;
+  double tot[1] = {0.0};
+  const int s0 = V.sl_first[m], nsm = V.sl_count[m];
+  for (int i = threadIdx.x; i < nsm; i += blockDim.x) tot[0] += __ldcg(V.part_sl + s0 + i);
+  bsum<1>(tot);
+  if (threadIdx.x != 0) return;
+  M->pq = tot[0];
+  if (tot[0] > 0.0 && isfinite(tot[0])) {
+    M->alpha_p = M->rz / tot[0];
+  } else {
+    M->alpha_p = 0.0;
+    M->done = 3;  // breakdown: H or the preconditioner is not positive definite
+  }
+}
+
+template <typename VT>
+__global__ void k_bupdate(BView V, int max_iter, const VT* __restrict__ dinv, Vec4<VT>* __restrict__ x,
+                          Vec4<VT>* __restrict__ r, Vec4<VT>* __restrict__ z, const Vec4<VT>* __restrict__ p,
+                          const Vec4<VT>* __restrict__ q) {
+  const int m = V.rb_mesh[blockIdx.x];
+  BMesh* M = V.M + m;
+  if (M->phase != BPH_ASSEMBLE || M->done) return;
+  const VT alpha = (VT)M->alpha_p;
+  double acc[2] = {0.0, 0.0};  // r.r, r.z
+  for (int v = V.rb_row0[blockIdx.x] + threadIdx.x; v < V.rb_row1[blockIdx.x]; v += blockDim.x) {
+    const Vec4<VT> pv = p[v], qv = q[v];
+    Vec4<VT> xv = x[v], rv = r[v];
+    xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z;
+    rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z;
+    x[v] = xv;
+    r[v] = rv;
+    const VT* D = dinv + (int64_t)v * 9;
+    const Vec4<VT> zv{D[0] * rv.x + D[1] * rv.y + D[2] * rv.z, D[3] * rv.x + D[4] * rv.y + D[5] * rv.z,
+                      D[6] * rv.x + D[7] * rv.y + D[8] * rv.z, VT(0)};
+    z[v] = zv;
+    acc[0] += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z;
+    acc[1] += (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z;
+  }
+  bsum<2>(acc);
+  double* part = V.part_rb + 4 * (int64_t)blockIdx.x;
+  if (threadIdx.x == 0) { part[0] = acc[0]; part[1] = acc[1]; }
+  if (!last_of_mesh(V.cnt + BC_UPD * V.nmesh + m, (unsigned)V.rb_count[m])) return;
+  double tot[2] = {0.0, 0.0};
+  const int rb0 = V.rb_first[m], nrbm = V.rb_count[m];
+  for (int i = threadIdx.x; i < nrbm; i += blockDim.x) {
+    tot[0] += __ldcg(V.part_rb + 4 * (int64_t)(rb0 + i));
+    tot[1] += __ldcg(V.part_rb + 4 * (int64_t)(rb0 + i) + 1);
+  }
+  bsum<2>(tot);
+  if (threadIdx.x != 0) return;
+  M->rr = tot[0];
+  M->iter += 1;
+  if (!isfinite(tot[0])) { M->done = 3; return; }
+  if (tot[0] <= M->tol2) { M->done = 1; return; }
+  if (M->iter >= max_iter) { M->done = 2; return; }
+  M->beta = tot[1] / M->rz;
+  M->rz = tot[1];
+}
+
+// ---- direction: step test, descent test, CCD bound -----------------------------------------
+template <typename VT>
+__global__ void k_bdir(BView V, BParams P, const Vec4<VT>* __restrict__ xs, const uint8_t* __restrict__ pinned,
+                       const Vec4d* __restrict__ grad, const Vec4d* __restrict__ xk, const Vec4d* __restrict__ xt,
+                       Vec4d* __restrict__ d) {
+  const int m = V.rb_mesh[blockIdx.x];
+  BMesh* M = V.M + m;
+  if (M->phase != BPH_ASSEMBLE) return;
+  double dinf = 0.0, xd = 0.0, tmin = 1e300;
+  double acc[1] = {0.0};
+  for (int v = V.rb_row0[blockIdx.x] + threadIdx.x; v < V.rb_row1[blockIdx.x]; v += blockDim.x) {
+    Vec4d dv{0.0, 0.0, 0.0, 0.0};
+    if (!pinned[v]) {
+      const Vec4<VT> s = xs[v];
+      dv = Vec4d{(double)s.x, (double)s.y, (double)s.z, 0.0};
+    }
+    d[v] = dv;
+    dinf = fmax(dinf, fmax(fabs(dv.x), fmax(fabs(dv.y), fabs(dv.z))));
+    const Vec4d a = xk[v], c = xt[v];
+    xd = fmax(xd, fmax(fabs(a.x - c.x), fmax(fabs(a.y - c.y), fabs(a.z - c.z))));
+    const Vec4d g = grad[v];
+    acc[0] += g.x * dv.x + g.y * dv.y + g.z * dv.z;
+    if (P.contact && !pinned[v]) {
+      const double nd = P.pn0 * dv.x + P.pn1 * dv.y + P.pn2 * dv.z;
+      if (nd < 0.0) {
+        const double dist = P.pn0 * a.x + P.pn1 * a.y + P.pn2 * a.z - P.po;
+        tmin = fmin(tmin, fmax(dist, 0.0) / (-nd));
+      }
+    }
+  }
+  bsum<1>(acc);
+  dinf = bmax(dinf);
+  xd = bmax(xd);
+  tmin = bmin(tmin);
+  double* part = V.part_rb + 4 * (int64_t)blockIdx.x;
+  if (threadIdx.x == 0) { part[0] = acc[0]; part[1] = dinf; part[2] = xd; part[3] = tmin; }
+  if (!last_of_mesh(V.cnt + BC_DIR * V.nmesh + m, (unsigned)V.rb_count[m])) return;
+  double tot[1] = {0.0};
+  double dm = 0.0, xm = 0.0, tm = 1e300;
+  const int rb0 = V.rb_first[m], nrbm = V.rb_count[m];
+  for (int i = threadIdx.x; i < nrbm; i += blockDim.x) {
+    const double* pp = V.part_rb + 4 * (int64_t)(rb0 + i);
+    tot[0] += __ldcg(pp);
+    dm = fmax(dm, __ldcg(pp + 1));
+    xm = fmax(xm, __ldcg(pp + 2));
+    tm = fmin(tm, __ldcg(pp + 3));
+  }
+  bsum<1>(tot);
+  dm = bmax(dm);
+  xm = bmax(xm);
+  tm = bmin(tm);
+  if (threadIdx.x != 0) return;
+  M->pcg += M->iter;
+  const int pcg_state = M->done;
+  M->done = 1;
+  // a breakdown of the solve (non-positive curvature or a non-finite value)
+  // fails the mesh's step, as in the single-mesh timestep
+  if (pcg_state == 3 || !isfinite(dm) || !isfinite(tot[0])) { M->status = MLS_ENONFINITE; M->phase = BPH_DONE; return; }
+  const double step_rel = dm / fmax(xm, P.scale0);
+  M->step_rel = step_rel;
+  M->gd = tot[0];
+  M->halvings = 0;
+  if (step_rel <= P.newton_tol) {
+    M->alpha = 1.0;
+    M->phase = BPH_FINAL;
+    return;
+  }
+  if (!(tot[0] < 0.0)) { M->status = MLS_ELINESEARCH; M->phase = BPH_DONE; return; }
+  M->alpha = (P.contact && tm < 1e299) ? fmin(1.0, 0.9 * tm) : 1.0;
+  M->phase = BPH_LS;
+}
+
+// ---- loop conditions (one block) ---------------------------------------------------------
+// which: 0 PCG (some mesh still iterating), 1 line search (some mesh still
+// searching; clears the accept flags), 2 Newton (some mesh not done; caps
+// the iteration count).  *trip counts the evaluations.
+__global__ void k_bcond(int nmesh, BMesh* __restrict__ M, int which, int max_newton, cudaGraphConditionalHandle h,
+                        int use_handle, int* __restrict__ any_out, int* __restrict__ trip) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  int mine = 0;
+  for (int m = threadIdx.x; m < nmesh; m += blockDim.x) {
+    BMesh* s = M + m;
+    if (which == 0) {
+      mine |= (s->phase == BPH_ASSEMBLE && !s->done) ? 1 : 0;
+    } else if (which == 1) {
+      s->apply = 0;
+      mine |= (s->phase == BPH_LS || s->phase == BPH_FINAL) ? 1 : 0;
+    } else {
+      if (s->phase == BPH_ASSEMBLE && s->newton >= max_newton) {
+        s->status = MLS_ENOTCONV;
+        s->phase = BPH_DONE;
+      }
+      mine |= s->phase != BPH_DONE ? 1 : 0;
+    }
+  }
+  if (mine) atomicOr(&any, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (use_handle) cudaGraphSetConditional(h, any ? 1u : 0u);
+    if (any_out) *any_out = any;
+    *trip += 1;
+  }
+}
+
+}  // namespace mls
+
+using namespace mls;
+
+// ---- the batch object ----------------------------------------------------------------------
+struct BShape {
+  int lanes = 4;        // lanes per row of the product (4 or 8)
+  int row_threads = 256;
+  int rows_per_thread = 1;
+};
+
+struct mls_batch {
+  mls_ctx* ctx = nullptr;
+  std::string err;
+  int nmesh = 0;
+  int n_user = 0;       // concatenated user vertices
+  int n = 0;            // padded internal vertices
+  std::vector<int> h_voff, h_toff, h_ioff, h_ipad;   // user vertex offsets, tet offsets, internal offsets, padded sizes
+  int* vmap = nullptr;  // [n] internal -> user vertex (-1: dummy)
+  double* bx = nullptr; // [n][3] packed x, v
+  double* bv = nullptr;
+  BMesh* M = nullptr;
+  BMesh* h_M = nullptr; // pinned
+  int* trips = nullptr; // [3] device
+  int* h_trips = nullptr;
+  int* any = nullptr;
+  double* mass_min = nullptr;
+  unsigned* cnt = nullptr;
+  double* part_rb = nullptr;
+  double* part_sl = nullptr;
+  double* part_e = nullptr;
+  // tables of the current shape
+  BShape shape;
+  bool tuned = false;
+  double tune_ms = 0.0;
+  std::vector<void*> tables;   // device allocations of the current tables
+  BView view{};
+  int nrb = 0, ntb = 0;
+  // graph
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double graph_dt = -1.0;
+  bool graph_dirty = true;
+  int64_t launches_fixed = 0, launches_newton = 0, launches_pcg = 0, launches_ls = 0;
+};
+
+namespace {
+
+mls_status bfail(mls_batch* b, mls_status st, const std::string& msg) {
+  b->err = msg;
+  return st;
+}
+
+mls_status bcheck(mls_batch* b, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return MLS_OK;
+  cudaGetLastError();
+  return bfail(b, MLS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+mls_status bupload(mls_batch* b, std::vector<void*>& list, T** dst, const std::vector<T>& src) {
+  void* p = nullptr;
+  const size_t bytes = sizeof(T) * std::max<size_t>(src.size(), 1);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return bfail(b, MLS_ENOMEM, "batch table allocation"); }
+  list.push_back(p);
+  *dst = (T*)p;
+  if (!src.empty()) return bcheck(b, cudaMemcpy(p, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice), "table upload");
+  return MLS_OK;
+}
+
+void free_tables(mls_batch* b) {
+  for (void* p : b->tables) cudaFree(p);
+  b->tables.clear();
+}
+
+// row blocks, slices and tet blocks for one launch shape
+mls_status build_tables(mls_batch* b, const BShape& sh) {
+  free_tables(b);
+  const int B = b->nmesh;
+  const int rows_per_block = sh.row_threads * sh.rows_per_thread;
+  std::vector<int> rb_mesh, rb_row0, rb_row1, rb_first(B), rb_count(B);
+  std::vector<int> sl_mesh(b->n / 32), sl_first(B), sl_count(B);
+  std::vector<int> tb_mesh, tb_t0, tb_t1, tb_first(B), tb_count(B);
+  for (int m = 0; m < B; ++m) {
+    const int r0 = b->h_ioff[m], r1 = r0 + b->h_ipad[m];
+    rb_first[m] = (int)rb_mesh.size();
+    for (int r = r0; r < r1; r += rows_per_block) {
+      rb_mesh.push_back(m);
+      rb_row0.push_back(r);
+      rb_row1.push_back(std::min(r1, r + rows_per_block));
+    }
+    rb_count[m] = (int)rb_mesh.size() - rb_first[m];
+    sl_first[m] = r0 / 32;
+    sl_count[m] = (r1 - r0) / 32;
+    for (int s = r0 / 32; s < r1 / 32; ++s) sl_mesh[s] = m;
+    const int t0 = b->h_toff[m], t1 = b->h_toff[m + 1];
+    tb_first[m] = (int)tb_mesh.size();
+    for (int e = t0; e < t1; e += kTetBlock) {
+      tb_mesh.push_back(m);
+      tb_t0.push_back(e);
+      tb_t1.push_back(std::min(t1, e + kTetBlock));
+    }
+    tb_count[m] = (int)tb_mesh.size() - tb_first[m];
+  }
+  BView& V = b->view;
+  V.nmesh = B;
+  V.nrb = (int)rb_mesh.size();
+  V.ntb = (int)tb_mesh.size();
+  mls_status st;
+  int* p;
+#define UP(field, vec) \
+  if ((st = bupload(b, b->tables, &p, vec)) != MLS_OK) return st; \
+  V.field = p;
+  UP(rb_mesh, rb_mesh) UP(rb_row0, rb_row0) UP(rb_row1, rb_row1) UP(rb_first, rb_first) UP(rb_count, rb_count)
+  UP(sl_mesh, sl_mesh) UP(sl_first, sl_first) UP(sl_count, sl_count)
+  UP(tb_mesh, tb_mesh) UP(tb_t0, tb_t0) UP(tb_t1, tb_t1) UP(tb_first, tb_first) UP(tb_count, tb_count)
+#undef UP
+  // partials: row-block partials sized for this shape; energy partials for tets + row blocks
+  if (b->part_rb) { cudaFree(b->part_rb); b->part_rb = nullptr; }
+  if (b->part_e) { cudaFree(b->part_e); b->part_e = nullptr; }
+  if (cudaMalloc(&b->part_rb, sizeof(double) * 4 * std::max(V.nrb, 1)) != cudaSuccess ||
+      cudaMalloc(&b->part_e, sizeof(double) * 2 * std::max(V.nrb + V.ntb, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, MLS_ENOMEM, "batch partials");
+  }
+  V.part_rb = b->part_rb;
+  V.part_tb = b->part_e;
+  V.part_sl = b->part_sl;
+  V.mass_min = b->mass_min;
+  V.cnt = b->cnt;
+  V.M = b->M;
+  b->nrb = V.nrb;
+  b->ntb = V.ntb;
+  b->shape = sh;
+  b->graph_dirty = true;
+  return MLS_OK;
+}
+
+BParams params(mls_batch* b, double dt) {
+  mls_ctx* c = b->ctx;
+  BParams P{};
+  P.h2 = dt * dt;
+  const double gm = std::sqrt(c->grav[0] * c->grav[0] + c->grav[1] * c->grav[1] + c->grav[2] * c->grav[2]);
+  P.scale0 = dt * dt * std::max(gm, 1e-30);
+  P.newton_tol = c->opt.newton_tol;
+  P.pcg_rtol = c->opt.pcg_rtol;
+  P.eta_floor = c->opt.precision == MLS_FP64 ? 1e-13 : 1e-6;
+  P.max_newton = c->opt.max_newton;
+  P.max_pcg = c->opt.max_pcg;
+  P.kappa = c->kappa; P.dhat = c->dhat; P.po = c->po;
+  P.pn0 = c->pn[0]; P.pn1 = c->pn[1]; P.pn2 = c->pn[2];
+  P.contact = c->contact;
+  return P;
+}
+
+BEnergyIn energy_in(mls_ctx* c) {
+  return BEnergyIn{c->t, c->tets, c->Dminv, c->vol, c->mu, c->lam, c->mass, c->pinned, c->xtil};
+}
+
+// launches counted into the per-loop tallies of the current capture
+struct Tally {
+  int64_t* where;
+  void add(int k = 1) { *where += k; }
+};
+
+template <typename VT, typename MT>
+mls_status launch_pcg_iter(mls_batch* b, cudaStream_t s) {
+  mls_ctx* c = b->ctx;
+  const BView& V = b->view;
+  const int ns = c->n_slices;
+  if (b->shape.lanes == 8)
+    k_bspmv<VT, MT, 8><<<ns, 256, 0, s>>>(V, c->n, c->slice_ptr, c->col, c->row_len, (const MT*)c->hval,
+                                          (const Vec4<VT>*)c->vz, (Vec4<VT>*)c->vp, (Vec4<VT>*)c->vq);
+  else
+    k_bspmv<VT, MT, 4><<<ns, 128, 0, s>>>(V, c->n, c->slice_ptr, c->col, c->row_len, (const MT*)c->hval,
+                                          (const Vec4<VT>*)c->vz, (Vec4<VT>*)c->vp, (Vec4<VT>*)c->vq);
+  k_bupdate<VT><<<V.nrb, b->shape.row_threads, 0, s>>>(V, c->opt.max_pcg, (const VT*)c->dinv, (Vec4<VT>*)c->vx,
+                                                      (Vec4<VT>*)c->vr, (Vec4<VT>*)c->vz, (const Vec4<VT>*)c->vp,
+                                                      (const Vec4<VT>*)c->vq);
+  return bcheck(b, cudaGetLastError(), "batched PCG iteration");
+}
+
+template <typename VT>
+mls_status launch_prep(mls_batch* b, cudaStream_t s, const BParams& P) {
+  mls_ctx* c = b->ctx;
+  k_bprep<VT><<<b->view.nrb, b->shape.row_threads, 0, s>>>(b->view, P, c->grad, (const Vec4<VT>*)c->vb,
+                                                          (const VT*)c->dinv, c->xk, c->xt, (Vec4<VT>*)c->vx,
+                                                          (Vec4<VT>*)c->vr, (Vec4<VT>*)c->vz, (Vec4<VT>*)c->vp,
+                                                          (Vec4<VT>*)c->vq);
+  return bcheck(b, cudaGetLastError(), "k_bprep");
+}
+
+template <typename VT>
+mls_status launch_dir(mls_batch* b, cudaStream_t s, const BParams& P) {
+  mls_ctx* c = b->ctx;
+  k_bdir<VT><<<b->view.nrb, b->shape.row_threads, 0, s>>>(b->view, P, (const Vec4<VT>*)c->vx, c->pinned, c->grad,
+                                                         c->xk, c->xt, c->dir);
+  return bcheck(b, cudaGetLastError(), "k_bdir");
+}
+
+// Conditional handle for a WHILE node to be added to the graph that stream s
+// is capturing into.  assign_default: the condition is reset to 1 at every
+// launch of the graph (the outermost loop); otherwise a kernel captured
+// before the node sets it.
+mls_status make_handle(mls_batch* b, cudaStream_t s, bool assign_default, cudaGraphConditionalHandle* h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  mls_status st = bcheck(b, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr), "capture info");
+  if (st != MLS_OK) return st;
+  return bcheck(b, cudaGraphConditionalHandleCreate(h, g, assign_default ? 1u : 0u,
+                                                    assign_default ? cudaGraphCondAssignDefault : 0u),
+                "conditional handle");
+}
+
+// Adds the WHILE node of handle h at the capture point of stream s and
+// starts capturing its body into stream body.
+mls_status begin_while(mls_batch* b, cudaStream_t s, cudaStream_t body, cudaGraphConditionalHandle h) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edges = nullptr;
+  size_t nd = 0;
+  mls_status st = bcheck(b, cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &edges, &nd), "capture info");
+  if (st != MLS_OK) return st;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((st = bcheck(b, cudaGraphAddNode(&node, g, deps, edges, nd, &cp), "conditional node")) != MLS_OK) return st;
+  if ((st = bcheck(b, cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies),
+                   "capture dependencies")) != MLS_OK)
+    return st;
+  return bcheck(b, cudaStreamBeginCaptureToGraph(body, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                 cudaStreamCaptureModeRelaxed),
+                "body capture");
+}
+
+mls_status end_body(mls_batch* b, cudaStream_t body) {
+  cudaGraph_t g;
+  return bcheck(b, cudaStreamEndCapture(body, &g), "body end");
+}
+
+void abandon_capture(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaGetLastError();
+}
+
+template <typename VT, typename MT>
+mls_status capture_step(mls_batch* b, double dt) {
+  mls_ctx* c = b->ctx;
+  const BParams P = params(b, dt);
+  const BEnergyIn EI = energy_in(c);
+  cudaStream_t s0 = b->cap;
+  cudaStream_t s1 = nullptr, s2 = nullptr;
+  mls_status st = MLS_OK;
+  if (cudaStreamCreateWithFlags(&s1, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    if (s1) cudaStreamDestroy(s1);
+    return bfail(b, MLS_ECUDA, "capture streams");
+  }
+  cudaStream_t saved = c->stream;
+  cudaGraph_t graph = nullptr;
+  const BView& V = b->view;
+  const int eb = V.ntb + V.nrb;
+  const int rt = b->shape.row_threads;
+  int* trips = b->trips;   // [0] PCG bodies, [1] line-search bodies, [2] Newton bodies, [3] loop entries
+  auto run = [&]() -> mls_status {
+    mls_status r;
+    if ((r = bcheck(b, cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed), "begin capture")) != MLS_OK) return r;
+    c->stream = s0;
+    // predictor and start states
+    k_breset<<<(b->nmesh + 127) / 128, 128, 0, s0>>>(b->nmesh, b->M);
+    if ((r = launch_predictor(c, b->bx, b->bv, dt)) != MLS_OK) return r;
+    k_benergy<0><<<eb, kTetBlock, 0, s0>>>(V, EI, P, c->xt, c->xt);
+    k_benergy<1><<<eb, kTetBlock, 0, s0>>>(V, EI, P, c->xk, c->xk);
+    k_bselect<<<V.nrb, rt, 0, s0>>>(V, c->xt, c->xk);
+    // Newton loop: entered with its condition at 1 on every launch
+    cudaGraphConditionalHandle hn, hp, hl;
+    if ((r = make_handle(b, s0, true, &hn)) != MLS_OK) return r;
+    if ((r = begin_while(b, s0, s1, hn)) != MLS_OK) return r;
+    c->stream = s1;
+    if ((r = launch_eval_elements(c, c->xk, nullptr)) != MLS_OK) return r;
+    if ((r = launch_gather_grad(c, c->xk, c->dscal + 2)) != MLS_OK) return r;
+    if ((r = launch_assemble(c, c->xk)) != MLS_OK) return r;
+    if ((r = launch_prep<VT>(b, s1, P)) != MLS_OK) return r;
+    // PCG loop
+    if ((r = make_handle(b, s1, false, &hp)) != MLS_OK) return r;
+    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 0, P.max_newton, hp, 1, nullptr, trips + 3);
+    if ((r = begin_while(b, s1, s2, hp)) != MLS_OK) return r;
+    if ((r = launch_pcg_iter<VT, MT>(b, s2)) != MLS_OK) return r;
+    if ((r = launch_pcg_iter<VT, MT>(b, s2)) != MLS_OK) return r;
+    k_bcond<<<1, 256, 0, s2>>>(b->nmesh, b->M, 0, P.max_newton, hp, 1, nullptr, trips + 0);
+    if ((r = end_body(b, s2)) != MLS_OK) return r;
+    if ((r = launch_dir<VT>(b, s1, P)) != MLS_OK) return r;
+    // line-search loop
+    if ((r = make_handle(b, s1, false, &hl)) != MLS_OK) return r;
+    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 1, P.max_newton, hl, 1, nullptr, trips + 3);
+    if ((r = begin_while(b, s1, s2, hl)) != MLS_OK) return r;
+    k_benergy<2><<<eb, kTetBlock, 0, s2>>>(V, EI, P, c->xk, c->dir);
+    k_bapply<<<V.nrb, rt, 0, s2>>>(V, c->xk, c->dir);
+    k_bcond<<<1, 256, 0, s2>>>(b->nmesh, b->M, 1, P.max_newton, hl, 1, nullptr, trips + 1);
+    if ((r = end_body(b, s2)) != MLS_OK) return r;
+    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 2, P.max_newton, hn, 1, nullptr, trips + 2);
+    if ((r = end_body(b, s1)) != MLS_OK) return r;
+    c->stream = s0;
+    return bcheck(b, cudaGetLastError(), "capture launches");
+  };
+  st = run();
+  c->stream = saved;
+  abandon_capture(s2);
+  abandon_capture(s1);
+  cudaError_t e = cudaStreamEndCapture(s0, &graph);
+  if (st == MLS_OK && e != cudaSuccess) st = bcheck(b, e, "end capture");
+  cudaGetLastError();
+  if (st == MLS_OK) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    st = bcheck(b, cudaGraphInstantiate(&b->exec, graph, 0), "graph instantiate");
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(s1);
+  cudaStreamDestroy(s2);
+  if (st == MLS_OK) {
+    b->graph_dt = dt;
+    b->graph_dirty = false;
+    // kernels per body: Newton = element, gradient, assembly, PCG set-up,
+    // two loop-entry conditions, direction, Newton condition; PCG = two
+    // iterations of two kernels + condition; line search = energy, apply,
+    // condition.  Outside the loops: reset, predictor, two energies, select.
+    b->launches_fixed = 5;
+    b->launches_newton = 8;
+    b->launches_pcg = 5;
+    b->launches_ls = 3;
+  }
+  return st;
+}
+
+// Times the PCG iteration of every candidate shape on the assembled system
+// of the current state and keeps the fastest.
+template <typename VT, typename MT>
+mls_status autotune(mls_batch* b, double dt) {
+  mls_ctx* c = b->ctx;
+  const BParams P = params(b, dt);
+  const BEnergyIn EI = energy_in(c);
+  cudaStream_t s = b->cap;
+  cudaStream_t saved = c->stream;
+  c->stream = s;
+  mls_status st;
+  // one assembled system from the predictor (meshes with an infeasible
+  // predictor are timed on it all the same)
+  if ((st = launch_predictor(c, b->bx, b->bv, dt)) != MLS_OK) { c->stream = saved; return st; }
+  if ((st = launch_eval_elements(c, c->xk, nullptr)) != MLS_OK) { c->stream = saved; return st; }
+  if ((st = launch_gather_grad(c, c->xk, c->dscal + 2)) != MLS_OK) { c->stream = saved; return st; }
+  if ((st = launch_assemble(c, c->xk)) != MLS_OK) { c->stream = saved; return st; }
+  (void)EI;
+  const BShape cands[] = {{4, 256, 1}, {4, 128, 1}, {4, 256, 2}, {4, 512, 1}, {8, 256, 1}, {8, 128, 1}, {8, 256, 2}};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  BShape win = cands[0];
+  BParams Pt = P;
+  Pt.pcg_rtol = 0.0;        // no mesh converges while timing
+  Pt.eta_floor = 0.0;
+  Pt.newton_tol = 0.0;
+  for (const BShape& sh : cands) {
+    if ((st = build_tables(b, sh)) != MLS_OK) break;
+    k_breset<<<(b->nmesh + 127) / 128, 128, 0, s>>>(b->nmesh, b->M);
+    if ((st = launch_prep<VT>(b, s, Pt)) != MLS_OK) break;
+    for (int w = 0; w < 2; ++w)
+      if ((st = launch_pcg_iter<VT, MT>(b, s)) != MLS_OK) break;
+    if (st != MLS_OK) break;
+    cudaEventRecord(e0, s);
+    for (int it = 0; it < 8; ++it)
+      if ((st = launch_pcg_iter<VT, MT>(b, s)) != MLS_OK) break;
+    if (st != MLS_OK) break;
+    cudaEventRecord(e1, s);
+    if ((st = bcheck(b, cudaEventSynchronize(e1), "autotune sync")) != MLS_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    b->tune_ms += ms;
+    if (ms < best) { best = ms; win = sh; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->stream = saved;
+  if (st != MLS_OK) return st;
+  if ((st = build_tables(b, win)) != MLS_OK) return st;
+  b->tuned = true;
+  return MLS_OK;
+}
+
+template <typename VT, typename MT>
+mls_status batch_step_t(mls_batch* b, const double* x, const double* v, double dt, double* dx) {
+  mls_ctx* c = b->ctx;
+  mls_status st;
+  cudaStream_t user = c->stream;
+  // order the internal stream after the caller's stream
+  cudaEvent_t ev;
+  if ((st = bcheck(b, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event")) != MLS_OK) return st;
+  cudaEventRecord(ev, user);
+  cudaStreamWaitEvent(b->cap, ev, 0);
+  k_bpack<<<(b->n + 255) / 256, 256, 0, b->cap>>>(b->n, b->vmap, x, v, b->bx, b->bv,
+                                                  c->pn[0] * (c->po + 1e3), c->pn[1] * (c->po + 1e3),
+                                                  c->pn[2] * (c->po + 1e3));
+  if ((st = bcheck(b, cudaGetLastError(), "k_bpack")) != MLS_OK) { cudaEventDestroy(ev); return st; }
+  if (!b->tuned) {
+    if ((st = autotune<VT, MT>(b, dt)) != MLS_OK) { cudaEventDestroy(ev); return st; }
+  }
+  if (b->graph_dirty || b->graph_dt != dt || !b->exec) {
+    if ((st = capture_step<VT, MT>(b, dt)) != MLS_OK) { cudaEventDestroy(ev); return st; }
+  }
+  cudaMemsetAsync(b->trips, 0, sizeof(int) * 4, b->cap);
+  if ((st = bcheck(b, cudaGraphLaunch(b->exec, b->cap), "graph launch")) != MLS_OK) { cudaEventDestroy(ev); return st; }
+  k_bunpack<<<(b->n + 255) / 256, 256, 0, b->cap>>>(b->n, b->vmap, c->xk, c->xt, dx);
+  cudaMemcpyAsync(b->h_M, b->M, sizeof(BMesh) * b->nmesh, cudaMemcpyDeviceToHost, b->cap);
+  cudaMemcpyAsync(b->h_trips, b->trips, sizeof(int) * 4, cudaMemcpyDeviceToHost, b->cap);
+  cudaEventRecord(ev, b->cap);
+  cudaStreamWaitEvent(user, ev, 0);
+  st = bcheck(b, cudaStreamSynchronize(b->cap), "batch step");
+  cudaEventDestroy(ev);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+mls_status mls_batch_create(mls_batch** out, const mls_options* opt) {
+  if (!out) return MLS_EINVAL;
+  *out = nullptr;
+  mls_options o;
+  if (opt) o = *opt;
+  else mls_default_options(&o);
+  if (o.preconditioner != MLS_PRECOND_BLOCK_JACOBI) return MLS_EINVAL;
+  mls_batch* b = new (std::nothrow) mls_batch();
+  if (!b) return MLS_ENOMEM;
+  mls_status st = mls_create(&b->ctx, &o);
+  if (st != MLS_OK) { delete b; return st; }
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    mls_destroy(b->ctx);
+    delete b;
+    return MLS_ECUDA;
+  }
+  *out = b;
+  return MLS_OK;
+}
+
+mls_status mls_batch_destroy(mls_batch* b) {
+  if (!b) return MLS_OK;
+  if (b->cap) cudaStreamSynchronize(b->cap);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  free_tables(b);
+  for (void* p : {(void*)b->vmap, (void*)b->bx, (void*)b->bv, (void*)b->M, (void*)b->trips, (void*)b->any,
+                  (void*)b->mass_min, (void*)b->cnt, (void*)b->part_rb, (void*)b->part_sl, (void*)b->part_e})
+    if (p) cudaFree(p);
+  if (b->h_M) cudaFreeHost(b->h_M);
+  if (b->h_trips) cudaFreeHost(b->h_trips);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  mls_destroy(b->ctx);
+  delete b;
+  return MLS_OK;
+}
+
+const char* mls_batch_last_error(const mls_batch* b) {
+  if (!b) return "null batch";
+  return b->err.empty() ? mls_last_error(b->ctx) : b->err.c_str();
+}
+
+mls_status mls_batch_upload(mls_batch* b, int32_t n_meshes, const int32_t* vert_offsets, const int32_t* tet_offsets,
+                            const double* rest_xyz, const int32_t* tets, const double* youngs,
+                            const double* poisson, const double* density, const uint8_t* dirichlet) {
+  if (!b) return MLS_EINVAL;
+  b->err.clear();
+  if (n_meshes < 1 || !vert_offsets || !tet_offsets || !rest_xyz || !tets || !youngs || !poisson || !density)
+    return bfail(b, MLS_EINVAL, "batch upload: no meshes or a null array");
+  if (vert_offsets[0] != 0 || tet_offsets[0] != 0) return bfail(b, MLS_EINVAL, "batch upload: offsets must start at 0");
+  for (int m = 0; m < n_meshes; ++m)
+    if (vert_offsets[m + 1] <= vert_offsets[m] || tet_offsets[m + 1] <= tet_offsets[m])
+      return bfail(b, MLS_EINVAL, "batch upload: mesh " + std::to_string(m) + " is empty");
+  const int nu = vert_offsets[n_meshes], nt = tet_offsets[n_meshes];
+  // tets reference vertices of their own mesh only
+  for (int m = 0; m < n_meshes; ++m)
+    for (int64_t k = 4 * (int64_t)tet_offsets[m]; k < 4 * (int64_t)tet_offsets[m + 1]; ++k)
+      if (tets[k] < vert_offsets[m] || tets[k] >= vert_offsets[m + 1])
+        return bfail(b, MLS_EINVAL, "batch upload: a tet of mesh " + std::to_string(m) + " references another mesh");
+  // padded internal layout
+  std::vector<int> ioff(n_meshes), ipad(n_meshes);
+  int n = 0;
+  for (int m = 0; m < n_meshes; ++m) {
+    const int nv = vert_offsets[m + 1] - vert_offsets[m];
+    ioff[m] = n;
+    ipad[m] = (nv + 31) / 32 * 32;
+    n += ipad[m];
+  }
+  std::vector<double> X(3 * (size_t)n, 0.0);
+  std::vector<uint8_t> pin(n, 1);
+  std::vector<int> vmap(n, -1);
+  for (int m = 0; m < n_meshes; ++m)
+    for (int u = vert_offsets[m]; u < vert_offsets[m + 1]; ++u) {
+      const int i = ioff[m] + (u - vert_offsets[m]);
+      vmap[i] = u;
+      for (int k = 0; k < 3; ++k) X[3 * (size_t)i + k] = rest_xyz[3 * (size_t)u + k];
+      pin[i] = dirichlet ? (dirichlet[u] ? 1 : 0) : 0;
+    }
+  for (int m = 0; m < n_meshes; ++m)   // dummy rows: rest at the mesh's first vertex
+    for (int i = ioff[m] + vert_offsets[m + 1] - vert_offsets[m]; i < ioff[m] + ipad[m]; ++i)
+      for (int k = 0; k < 3; ++k) X[3 * (size_t)i + k] = rest_xyz[3 * (size_t)vert_offsets[m] + k];
+  std::vector<int> T(4 * (size_t)nt);
+  for (int m = 0; m < n_meshes; ++m)
+    for (int64_t k = 4 * (int64_t)tet_offsets[m]; k < 4 * (int64_t)tet_offsets[m + 1]; ++k)
+      T[k] = ioff[m] + (tets[k] - vert_offsets[m]);
+  mls_status st = mls_upload_mesh(b->ctx, n, X.data(), nt, T.data(), youngs, poisson, density, pin.data());
+  if (st != MLS_OK) return bfail(b, st, std::string("batch upload: ") + mls_last_error(b->ctx));
+  // per-mesh smallest free-vertex lumped mass
+  std::vector<double> mass(n, 0.0);
+  for (int e = 0; e < nt; ++e) {
+    const double* p0 = X.data() + 3 * (size_t)T[4 * e];
+    double D[3][3];
+    for (int k = 0; k < 3; ++k)
+      for (int a = 0; a < 3; ++a) D[a][k] = X[3 * (size_t)T[4 * e + k + 1] + a] - p0[a];
+    const double det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) - D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                       D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+    for (int a = 0; a < 4; ++a) mass[T[4 * e + a]] += density[e] * det / 24.0;
+  }
+  std::vector<double> mmin(n_meshes, 0.0);
+  for (int m = 0; m < n_meshes; ++m) {
+    double lo = 1e300;
+    for (int i = ioff[m]; i < ioff[m] + vert_offsets[m + 1] - vert_offsets[m]; ++i)
+      if (!pin[i]) lo = std::min(lo, mass[i]);
+    mmin[m] = lo < 1e300 ? lo : 0.0;
+  }
+  // (re)allocate batch state
+  for (void** p : {(void**)&b->vmap, (void**)&b->bx, (void**)&b->bv, (void**)&b->M, (void**)&b->trips,
+                   (void**)&b->any, (void**)&b->mass_min, (void**)&b->cnt, (void**)&b->part_sl})
+    if (*p) { cudaFree(*p); *p = nullptr; }
+  if (b->h_M) { cudaFreeHost(b->h_M); b->h_M = nullptr; }
+  if (b->h_trips) { cudaFreeHost(b->h_trips); b->h_trips = nullptr; }
+  bool ok = cudaMalloc(&b->vmap, sizeof(int) * n) == cudaSuccess &&
+            cudaMalloc(&b->bx, sizeof(double) * 3 * n) == cudaSuccess &&
+            cudaMalloc(&b->bv, sizeof(double) * 3 * n) == cudaSuccess &&
+            cudaMalloc(&b->M, sizeof(BMesh) * n_meshes) == cudaSuccess &&
+            cudaMalloc(&b->trips, sizeof(int) * 4) == cudaSuccess &&
+            cudaMalloc(&b->any, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&b->mass_min, sizeof(double) * n_meshes) == cudaSuccess &&
+            cudaMalloc(&b->cnt, sizeof(unsigned) * BC_COUNT * n_meshes) == cudaSuccess &&
+            cudaMalloc(&b->part_sl, sizeof(double) * (n / 32)) == cudaSuccess &&
+            cudaMallocHost(&b->h_M, sizeof(BMesh) * n_meshes) == cudaSuccess &&
+            cudaMallocHost(&b->h_trips, sizeof(int) * 4) == cudaSuccess;
+  if (!ok) { cudaGetLastError(); return bfail(b, MLS_ENOMEM, "batch state allocation"); }
+  if ((st = bcheck(b, cudaMemcpy(b->vmap, vmap.data(), sizeof(int) * n, cudaMemcpyHostToDevice), "vmap")) != MLS_OK) return st;
+  if ((st = bcheck(b, cudaMemcpy(b->mass_min, mmin.data(), sizeof(double) * n_meshes, cudaMemcpyHostToDevice), "mass")) != MLS_OK) return st;
+  if ((st = bcheck(b, cudaMemset(b->cnt, 0, sizeof(unsigned) * BC_COUNT * n_meshes), "counters")) != MLS_OK) return st;
+  b->nmesh = n_meshes;
+  b->n_user = nu;
+  b->n = n;
+  b->h_voff.assign(vert_offsets, vert_offsets + n_meshes + 1);
+  b->h_toff.assign(tet_offsets, tet_offsets + n_meshes + 1);
+  b->h_ioff = ioff;
+  b->h_ipad = ipad;
+  b->tuned = false;
+  b->tune_ms = 0.0;
+  if ((st = build_tables(b, BShape{})) != MLS_OK) return st;
+  return MLS_OK;
+}
+
+mls_status mls_batch_set_forces(mls_batch* b, const double* gravity, int contact, const double* plane_n,
+                                double plane_o, double dhat, double kappa) {
+  if (!b) return MLS_EINVAL;
+  mls_status st = mls_set_forces(b->ctx, gravity, contact, plane_n, plane_o, dhat, kappa);
+  if (st != MLS_OK) return bfail(b, st, mls_last_error(b->ctx));
+  b->graph_dirty = true;
+  return MLS_OK;
+}
+
+mls_status mls_batch_retune(mls_batch* b) {
+  if (!b) return MLS_EINVAL;
+  b->tuned = false;
+  b->tune_ms = 0.0;
+  b->graph_dirty = true;
+  return MLS_OK;
+}
+
+mls_status mls_batch_step(mls_batch* b, const double* x, const double* v, double dt, double* dx_out,
+                          mls_batch_mesh_stats* stats, mls_batch_info* info) {
+  if (!b) return MLS_EINVAL;
+  b->err.clear();
+  if (b->nmesh < 1) return bfail(b, MLS_EINVAL, "no meshes uploaded");
+  if (!x || !v || !dx_out) return bfail(b, MLS_EINVAL, "null state pointer");
+  if (!(dt > 0)) return bfail(b, MLS_EINVAL, "dt must be positive");
+  b->ctx->h = dt;
+  mls_status st;
+  switch (b->ctx->opt.precision) {
+    case MLS_FP64: st = batch_step_t<double, double>(b, x, v, dt, dx_out); break;
+    case MLS_MIXED_FP32: st = batch_step_t<float, float>(b, x, v, dt, dx_out); break;
+    default: st = batch_step_t<float, __nv_bfloat16>(b, x, v, dt, dx_out); break;
+  }
+  if (st != MLS_OK) return st;
+  mls_status worst = MLS_OK;
+  for (int m = 0; m < b->nmesh; ++m) {
+    const BMesh& s = b->h_M[m];
+    if (stats) {
+      stats[m].status = s.status;
+      stats[m].newton_iters = s.newton;
+      stats[m].pcg_iters = s.pcg;
+      stats[m].line_search_trials = s.trials;
+      stats[m].step_rel = s.step_rel;
+      stats[m].grad_norm = s.gnorm;
+      stats[m].energy = s.E0;
+    }
+    if (s.status != MLS_OK && worst == MLS_OK) worst = (mls_status)s.status;
+  }
+  if (info) {
+    const int* t = b->h_trips;
+    // graph nodes run: fixed part + per Newton body (element, gradient,
+    // assembly, prep, PCG condition, direction, Newton condition) + per PCG
+    // body + per line-search body
+    info->kernel_launches = 2 + b->launches_fixed + (int64_t)t[2] * b->launches_newton +
+                            (int64_t)t[0] * b->launches_pcg + (int64_t)t[1] * b->launches_ls;
+    info->graph_launches = 1;
+    info->newton_rounds = t[2];
+    info->pcg_rounds = t[0];
+    info->line_search_rounds = t[1];
+    info->spmv_lanes = b->shape.lanes;
+    info->row_threads = b->shape.row_threads;
+    info->rows_per_thread = b->shape.rows_per_thread;
+    info->tune_ms = b->tune_ms;
+  }
+  if (worst != MLS_OK) {
+    if (worst == MLS_ENOTCONV) b->err = "a mesh reached its Newton iteration cap";
+    else b->err = "a mesh failed (see the per-mesh status)";
+  }
+  return worst;
+}
+
+}  // extern "C"
