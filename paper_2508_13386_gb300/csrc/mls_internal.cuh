@@ -59,6 +59,33 @@ template <typename A, typename T> __device__ __forceinline__ A load_as(T v) { re
 template <> __device__ __forceinline__ float load_as<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 template <> __device__ __forceinline__ double load_as<double, __nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
+// ---- programmatic dependent launch (chained kernels) ------------------------------------
+// A kernel launched with launch_chained() may be scheduled while its
+// predecessor in the stream is still running (its launch latency and block
+// scheduling overlap the predecessor's tail).  It must call chain_wait()
+// before reading or writing anything its predecessor touches; chain_wait()
+// returns once the predecessor grid has completed and its writes are
+// visible.  chain_release() lets the successor be scheduled.  Both are
+// no-ops in a kernel launched the ordinary way.
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void chain_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream,
+                                 Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---- deterministic grid-wide sums: block partials, reduced by the last block
 struct GridReduce {
   double* partials;        // [K][kMaxPartials]

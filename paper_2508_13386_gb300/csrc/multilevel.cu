@@ -275,7 +275,37 @@ struct BasisView {
   const double* __restrict__ hphi;
   const double* __restrict__ origins;
   const Vec4d* __restrict__ X;
+  int nrchunk;
 };
+
+// sum_j phi_j(v) (I_3 (x) a_vj^T) q_j for one vertex: the handle indices and
+// coefficients of four entries are loaded before their coarse vectors, so
+// the dependent gathers of a row are issued together
+template <typename VT>
+__device__ __forceinline__ void prolong_row(const BasisView& B, const VT* __restrict__ q, int v, VT& o0, VT& o1,
+                                            VT& o2) {
+  const Vec4<VT>* coef = (const Vec4<VT>*)B.vcoef;
+  const int k1 = B.vrow[v + 1];
+  for (int k0 = B.vrow[v]; k0 < k1; k0 += 4) {
+    int h[4];
+    Vec4<VT> a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const bool ok = k0 + u < k1;
+      h[u] = ok ? B.vh[k0 + u] : -1;
+      a[u] = ok ? coef[k0 + u] : Vec4<VT>{VT(0), VT(0), VT(0), VT(0)};
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (h[u] < 0) continue;
+      const Vec4<VT>* qj = (const Vec4<VT>*)(q + 12 * (int64_t)h[u]);
+      const Vec4<VT> q0 = qj[0], q1 = qj[1], q2 = qj[2];
+      o0 += a[u].x * q0.x + a[u].y * q0.y + a[u].z * q0.z + a[u].w * q0.w;
+      o1 += a[u].x * q1.x + a[u].y * q1.y + a[u].z * q1.z + a[u].w * q1.w;
+      o2 += a[u].x * q2.x + a[u].y * q2.y + a[u].z * q2.z + a[u].w * q2.w;
+    }
+  }
+}
 
 // w_v = [acc ? w_v : 0] + sum_j phi_j(v) (I_3 (x) a_vj^T) q_j  (+ omega D^-1 s_v)
 // (q may be null: then only the base and smoothing terms are applied; base
@@ -286,19 +316,13 @@ __global__ void __launch_bounds__(kBlock) k_prolong(BasisView B, const VT* __res
                                                     const VT* __restrict__ dinv, const Vec4<VT>* __restrict__ s,
                                                     VT omega, Vec4<VT>* w,
                                                     const PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
   if (S && S->done) return;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= B.n) return;
   VT o0 = VT(0), o1 = VT(0), o2 = VT(0);
-  const Vec4<VT>* coef = (const Vec4<VT>*)B.vcoef;
-  if (q) for (int k = B.vrow[v]; k < B.vrow[v + 1]; ++k) {
-    const Vec4<VT> a = coef[k];
-    const Vec4<VT>* qj = (const Vec4<VT>*)(q + 12 * (int64_t)B.vh[k]);
-    const Vec4<VT> q0 = qj[0], q1 = qj[1], q2 = qj[2];
-    o0 += a.x * q0.x + a.y * q0.y + a.z * q0.z + a.w * q0.w;
-    o1 += a.x * q1.x + a.y * q1.y + a.z * q1.z + a.w * q1.w;
-    o2 += a.x * q2.x + a.y * q2.y + a.z * q2.z + a.w * q2.w;
-  }
+  if (q) prolong_row<VT>(B, q, v, o0, o1, o2);
   if (base) {
     const Vec4<VT> b = base[v];
     o0 += b.x; o1 += b.y; o2 += b.z;
@@ -318,20 +342,14 @@ template <typename VT>
 __global__ void __launch_bounds__(kBlock) k_prolong_rz(BasisView B, const VT* __restrict__ q,
                                                        const Vec4<VT>* __restrict__ r, Vec4<VT>* z, int first,
                                                        GridReduce gr, PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
   if (S->done) return;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[1] = {0.0};
   if (v < B.n) {
     VT o0 = VT(0), o1 = VT(0), o2 = VT(0);
-    const Vec4<VT>* coef = (const Vec4<VT>*)B.vcoef;
-    for (int k = B.vrow[v]; k < B.vrow[v + 1]; ++k) {
-      const Vec4<VT> a = coef[k];
-      const Vec4<VT>* qj = (const Vec4<VT>*)(q + 12 * (int64_t)B.vh[k]);
-      const Vec4<VT> q0 = qj[0], q1 = qj[1], q2 = qj[2];
-      o0 += a.x * q0.x + a.y * q0.y + a.z * q0.z + a.w * q0.w;
-      o1 += a.x * q1.x + a.y * q1.y + a.z * q1.z + a.w * q1.w;
-      o2 += a.x * q2.x + a.y * q2.y + a.z * q2.z + a.w * q2.w;
-    }
+    prolong_row<VT>(B, q, v, o0, o1, o2);
     const Vec4<VT> zb = z[v], rv = r[v];
     const Vec4<VT> zo{zb.x + o0, zb.y + o1, zb.z + o2, VT(0)};
     z[v] = zo;
@@ -344,62 +362,77 @@ __global__ void __launch_bounds__(kBlock) k_prolong_rz(BasisView B, const VT* __
   }
 }
 
-// z_j = sum_{v in supp j} phi_j(v) r_v (x) a_vj.  One CTA per chunk of at most
-// kRestrictChunk entries of one handle (one entry per thread, coalesced
-// coefficients); chunk sums go to a per-chunk slot and the last chunk of a
-// handle to finish adds them in chunk order (deterministic).
+// z_j = sum_{v in supp j} phi_j(v) r_v (x) a_vj.  One warp per chunk of at
+// most kRestrictChunk entries of one handle: each lane takes every 32nd
+// entry (coalesced coefficients, eight independent gathers in flight), the
+// warp sums its 12 values with shuffles, and the chunk sum goes to a
+// per-chunk slot; the last chunk of a handle to finish adds the slots in
+// chunk order (deterministic).  No block-wide barrier.
+constexpr int kRestrictWarps = 8;
 template <typename VT>
-__global__ void __launch_bounds__(kRestrictChunk) k_restrict(BasisView B, const Vec4<VT>* __restrict__ r,
-                                                             VT* __restrict__ z, const PcgScalars* __restrict__ S) {
+__global__ void __launch_bounds__(32 * kRestrictWarps) k_restrict(BasisView B, const Vec4<VT>* __restrict__ r,
+                                                                  VT* __restrict__ z,
+                                                                  const PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
   if (S && S->done) return;
-  const int ch = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int ch = blockIdx.x * kRestrictWarps + (threadIdx.x >> 5);
+  if (ch >= B.nrchunk) return;
   const int j = B.rchunk_handle[ch];
-  const int p = B.rchunk_beg[ch] + threadIdx.x;
+  const int p0 = B.rchunk_beg[ch];
+  const int p1 = min(p0 + kRestrictChunk, B.hrow[j + 1]);
+  constexpr int U = kRestrictChunk / 32;
+  int hv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int p = p0 + lane + 32 * u;
+    hv[u] = p < p1 ? B.hv[p] : -1;
+  }
   VT acc[12];
 #pragma unroll
   for (int q = 0; q < 12; ++q) acc[q] = VT(0);
-  if (p < B.hrow[j + 1]) {
-    const Vec4<VT> a = ((const Vec4<VT>*)B.hcoef)[p];
-    const Vec4<VT> rv = r[B.hv[p]];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (hv[u] < 0) continue;
+    const Vec4<VT> a = ((const Vec4<VT>*)B.hcoef)[p0 + lane + 32 * u];
+    const Vec4<VT> rv = r[hv[u]];
     const VT rc[3] = {rv.x, rv.y, rv.z};
     const VT av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int l = 0; l < 4; ++l) acc[4 * c + l] = rc[c] * av[l];
+      for (int l = 0; l < 4; ++l) acc[4 * c + l] += rc[c] * av[l];
   }
-  __shared__ VT sh[12][kRestrictChunk / 32];
-  __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < 12; ++q) {
-    VT s = acc[q];
+  for (int q = 0; q < 12; ++q)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) sh[q][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x < 12) {
-    VT s = VT(0);
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[threadIdx.x][w];
-    B.rpart[12 * (int64_t)ch + threadIdx.x] = (double)s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  // lane q < 12 stores component q (the values are identical in every lane)
+  VT mine = acc[0];
+#pragma unroll
+  for (int q = 1; q < 12; ++q)
+    if (lane == q) mine = acc[q];
+  if (lane < 12) B.rpart[12 * (int64_t)ch + lane] = (double)mine;
+  __syncwarp();
+  unsigned last = 0;
+  if (lane == 0) {
     __threadfence();
     const unsigned nch = (unsigned)(B.rchunk_ptr[j + 1] - B.rchunk_ptr[j]);
-    last = (atomicAdd(B.rcount + j, 1u) == nch - 1);
+    last = atomicAdd(B.rcount + j, 1u) == nch - 1;
   }
-  __syncthreads();
+  last = __shfl_sync(0xffffffffu, last, 0);
   if (!last) return;
   __threadfence();
-  if (threadIdx.x < 12) {
-    double s = 0.0;
-    for (int c = B.rchunk_ptr[j]; c < B.rchunk_ptr[j + 1]; ++c) s += __ldcg(B.rpart + 12 * (int64_t)c + threadIdx.x);
-    z[12 * (int64_t)j + threadIdx.x] = (VT)s;
+  if (lane < 12) {
+    double t = 0.0;
+    for (int c = B.rchunk_ptr[j]; c < B.rchunk_ptr[j + 1]; ++c) t += __ldcg(B.rpart + 12 * (int64_t)c + lane);
+    z[12 * (int64_t)j + lane] = (VT)t;
   }
-  if (threadIdx.x == 0) B.rcount[j] = 0;
+  if (lane == 0) B.rcount[j] = 0;
 }
+
+static inline int restrict_blocks(int nrchunk) { return (nrchunk + kRestrictWarps - 1) / kRestrictWarps; }
 
 // ---- Galerkin: Y = H U ----------------------------------------------------------------
 struct GalerkinView {
@@ -701,35 +734,56 @@ __global__ void k_transpose(const VT* __restrict__ W, int r, VT* __restrict__ WT
 
 // y = W x restricted to the lower (lower = 1: columns <= row) or upper
 // (lower = 0: columns >= row) triangle, widened to 16-byte boundaries (W is
-// zero outside its triangle); one warp per row, 16-byte loads, unrolled
+// zero outside its triangle).  kTriWarps warps share a row (lane-strided
+// 16-byte loads, so each warp has few loads to wait for) and combine their
+// sums through shared memory; a 256-thread block covers 8 / kTriWarps rows.
+constexpr int kTriWarps = 4;
 template <typename VT>
 __global__ void __launch_bounds__(kBlock) k_trigemv(const VT* __restrict__ W, int r, int lower,
                                                     const VT* __restrict__ x, VT* __restrict__ y,
                                                     const PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
   if (S && S->done) return;
   constexpr int EV = 16 / sizeof(VT);
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= r) return;
-  const int v0 = lower ? 0 : row / EV;
-  const int v1 = lower ? (row + EV) / EV : r / EV;
-  using V16 = typename std::conditional<sizeof(VT) == 4, float4, double2>::type;
-  const V16* Wr = reinterpret_cast<const V16*>(W + (int64_t)row * r);
-  const V16* xv = reinterpret_cast<const V16*>(x);
+  constexpr int RPB = (kBlock / 32) / kTriWarps;
+  __shared__ VT part[kBlock / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * RPB + warp / kTriWarps;
+  const int sub = warp % kTriWarps;
   VT acc = VT(0);
+  if (row < r) {
+    const int v0 = lower ? 0 : row / EV;
+    const int v1 = lower ? (row + EV) / EV : r / EV;
+    using V16 = typename std::conditional<sizeof(VT) == 4, float4, double2>::type;
+    const V16* Wr = reinterpret_cast<const V16*>(W + (int64_t)row * r);
+    const V16* xv = reinterpret_cast<const V16*>(x);
 #pragma unroll 4
-  for (int c = v0 + lane; c < v1; c += 32) {
-    const V16 w = Wr[c];
-    const V16 b = xv[c];
-    if constexpr (sizeof(VT) == 4) {
-      acc += w.x * b.x + w.y * b.y + w.z * b.z + w.w * b.w;
-    } else {
-      acc += w.x * b.x + w.y * b.y;
+    for (int c = v0 + sub * 32 + lane; c < v1; c += 32 * kTriWarps) {
+      const V16 w = Wr[c];
+      const V16 b = xv[c];
+      if constexpr (sizeof(VT) == 4) {
+        acc += w.x * b.x + w.y * b.y + w.z * b.z + w.w * b.w;
+      } else {
+        acc += w.x * b.x + w.y * b.y;
+      }
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) y[row] = acc;
+  if (lane == 0) part[warp] = acc;
+  __syncthreads();
+  if (sub == 0 && lane == 0 && row < r) {
+    VT t = VT(0);
+#pragma unroll
+    for (int k = 0; k < kTriWarps; ++k) t += part[warp + k];
+    y[row] = t;
+  }
+}
+
+static inline int trigemv_blocks(int r) {
+  constexpr int RPB = (kBlock / 32) / kTriWarps;
+  return (r + RPB - 1) / RPB;
 }
 
 __global__ void k_ypair_rows(int n, const int* __restrict__ yrow, int* __restrict__ out) {
@@ -742,7 +796,7 @@ __global__ void k_ypair_rows(int n, const int* __restrict__ yrow, int* __restric
 static BasisView basis_view(mls_ctx* ctx) {
   const Basis& B = ctx->basis;
   return BasisView{ctx->n, B.m, B.vcoef, B.hcoef, B.rchunk_handle, B.rchunk_beg, B.rchunk_ptr, B.rpart, B.rcount,
-                   B.vrow, B.vh, B.vphi, B.hrow, B.hv, B.hphi, B.origins, ctx->X};
+                   B.vrow, B.vh, B.vphi, B.hrow, B.hv, B.hphi, B.origins, ctx->X, B.nrchunk};
 }
 
 mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate) {
@@ -759,9 +813,9 @@ mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate)
 mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   if (ctx->opt.precision == MLS_FP64)
-    { ++ctx->launches; k_restrict<double><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(basis_view(ctx), (const Vec4d*)r, (double*)q, nullptr); }
+    { ++ctx->launches; k_restrict<double><<<restrict_blocks(ctx->basis.nrchunk), 32 * kRestrictWarps, 0, ctx->stream>>>(basis_view(ctx), (const Vec4d*)r, (double*)q, nullptr); }
   else
-    { ++ctx->launches; k_restrict<float><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(basis_view(ctx), (const Vec4f*)r, (float*)q, nullptr); }
+    { ++ctx->launches; k_restrict<float><<<restrict_blocks(ctx->basis.nrchunk), 32 * kRestrictWarps, 0, ctx->stream>>>(basis_view(ctx), (const Vec4f*)r, (float*)q, nullptr); }
   return cuda_check(ctx, cudaGetLastError(), "k_restrict");
 }
 
@@ -852,8 +906,7 @@ static mls_status factor_t(mls_ctx* ctx) {
 
 // y = W^T (W x) with a dense inverse factor pair, solve precision
 mls_status dense_apply(mls_ctx* ctx, const void* W, const void* WT, int r, const void* x, void* tmp, void* y) {
-  const int rows_per_block = kBlock / 32;
-  const int nb = (r + rows_per_block - 1) / rows_per_block;
+  const int nb = trigemv_blocks(r);
   if (ctx->opt.precision == MLS_FP64) {
     { ++ctx->launches; k_trigemv<double><<<nb, kBlock, 0, ctx->stream>>>((const double*)W, r, 1, (const double*)x, (double*)tmp, nullptr); }
     { ++ctx->launches; k_trigemv<double><<<nb, kBlock, 0, ctx->stream>>>((const double*)WT, r, 0, (const double*)tmp, (double*)y, nullptr); }
@@ -885,11 +938,13 @@ mls_status build_coarse(mls_ctx* ctx) {
 template <typename VT>
 static mls_status coarse_apply_t(mls_ctx* ctx, const VT* c_in, VT* c_out, const PcgScalars* S) {
   const int r = 12 * ctx->basis.m;
-  const int rows_per_block = kBlock / 32;
-  const int nb = (r + rows_per_block - 1) / rows_per_block;
-  { ++ctx->launches; k_trigemv<VT><<<nb, kBlock, 0, ctx->stream>>>((const VT*)ctx->Linv, r, 1, c_in, (VT*)ctx->cvec2, S); }
-  { ++ctx->launches; k_trigemv<VT><<<nb, kBlock, 0, ctx->stream>>>((const VT*)ctx->LinvT, r, 0, (const VT*)ctx->cvec2, c_out, S); }
-  return cuda_check(ctx, cudaGetLastError(), "coarse apply");
+  const int nb = trigemv_blocks(r);
+  ctx->launches += 2;
+  mls_status st = cuda_check(ctx, launch_chained(k_trigemv<VT>, dim3(nb), dim3(kBlock), ctx->stream, (const VT*)ctx->Linv,
+                                                 r, 1, c_in, (VT*)ctx->cvec2, S), "k_trigemv");
+  if (st != MLS_OK) return st;
+  return cuda_check(ctx, launch_chained(k_trigemv<VT>, dim3(nb), dim3(kBlock), ctx->stream, (const VT*)ctx->LinvT, r, 0,
+                                        (const VT*)ctx->cvec2, c_out, S), "k_trigemv");
 }
 
 mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out) {
@@ -906,7 +961,7 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   VT* c = (VT*)ctx->cvec;
   const VT* dinv = (const VT*)ctx->dinv;
   if (ctx->opt.cycle == MLS_CYCLE_ADDITIVE) {
-    { ++ctx->launches; k_restrict<VT><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(BV, r, c, S); }
+    { ++ctx->launches; k_restrict<VT><<<restrict_blocks(ctx->basis.nrchunk), 32 * kRestrictWarps, 0, ctx->stream>>>(BV, r, c, S); }
     mls_status st = coarse_apply_t<VT>(ctx, c, c, S);
     if (st != MLS_OK) return st;
     { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, nullptr, dinv, r, omega, z, S); }
@@ -917,7 +972,7 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   mls_status st = launch_jacobi(ctx, r, z, ctx->opt.omega, S);
   if (st != MLS_OK) return st;
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
-  { ++ctx->launches; k_restrict<VT><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(BV, tmp, c, S); }
+  { ++ctx->launches; k_restrict<VT><<<restrict_blocks(ctx->basis.nrchunk), 32 * kRestrictWarps, 0, ctx->stream>>>(BV, tmp, c, S); }
   if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
   { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, z, nullptr, nullptr, omega, z, S); }
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
@@ -938,17 +993,28 @@ static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1
   const int m = ctx->basis.m;
   VT* c = (VT*)ctx->cvec;
   mls_status st;
+  const dim3 rgrid(restrict_blocks(ctx->basis.nrchunk)), rblock(32 * kRestrictWarps);
   if (ctx->opt.cycle == MLS_CYCLE_ADDITIVE) {
-    { ++ctx->launches; k_restrict<VT><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(BV, r, c, S); }
+    ++ctx->launches;
+    if ((st = cuda_check(ctx, launch_chained(k_restrict<VT>, rgrid, rblock, ctx->stream, BV, r, c, S), "k_restrict")) != MLS_OK)
+      return st;
     if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
-    { ++ctx->launches; k_prolong_rz<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, r, z1, first, ctx->red, S); }
-    return cuda_check(ctx, cudaGetLastError(), "two-level additive");
+    ++ctx->launches;
+    return cuda_check(ctx, launch_chained(k_prolong_rz<VT>, dim3(nblk(ctx->n)), dim3(kBlock), ctx->stream, BV,
+                                          (const VT*)c, r, z1, first, ctx->red, S), "k_prolong_rz");
   }
   Vec4<VT>* tmp = (Vec4<VT>*)ctx->vw;
   if ((st = launch_residual(ctx, r, z1, tmp, S)) != MLS_OK) return st;
-  { ++ctx->launches; k_restrict<VT><<<ctx->basis.nrchunk, kRestrictChunk, 0, ctx->stream>>>(BV, tmp, c, S); }
+  ++ctx->launches;
+  if ((st = cuda_check(ctx, launch_chained(k_restrict<VT>, rgrid, rblock, ctx->stream, BV, (const Vec4<VT>*)tmp, c, S),
+                       "k_restrict")) != MLS_OK)
+    return st;
   if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
-  { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, z1, nullptr, nullptr, VT(0), z1, S); }
+  ++ctx->launches;
+  if ((st = cuda_check(ctx, launch_chained(k_prolong<VT>, dim3(nblk(ctx->n)), dim3(kBlock), ctx->stream, BV, (const VT*)c,
+                                           (const Vec4<VT>*)z1, (const VT*)nullptr, (const Vec4<VT>*)nullptr, VT(0), z1,
+                                           S), "k_prolong")) != MLS_OK)
+    return st;
   return launch_post_smooth_rz(ctx, r, z1, zf, first, S);
 }
 

@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_residual(SellView A, co
                                                               const Vec4<VT>* __restrict__ x,
                                                               Vec4<VT>* __restrict__ out,
                                                               const PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
   if (S && S->done) return;
   VT r[3];
   spmv_quad<VT, MT>(A, val, blockIdx.x, x, r);
@@ -183,6 +185,8 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_post_smooth_rz(SellView
                                                                     const VT* __restrict__ dinv, VT omega,
                                                                     Vec4<VT>* __restrict__ zout, int first,
                                                                     GridReduce gr, PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
   if (S->done) return;
   double acc[1] = {0.0};
   VT hz[3];
@@ -232,6 +236,8 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_pcg_spmv(SellView A, co
                                                               const Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p,
                                                               Vec4<VT>* __restrict__ q, GridReduce gr,
                                                               PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
   if (S->done) return;
   double acc[1] = {0.0};
   VT w[3];
@@ -258,13 +264,18 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_pcg_spmv(SellView A, co
 }
 
 // x += alpha p; r -= alpha q; then by mode: 1 = block Jacobi z = D^{-1} r with
-// r.z and beta; 2 = the smoothing term z = omega D^{-1} r of a two-level cycle
+// r.z and beta; 2 = the smoothing term z = omega D^{-1} r of a two-level cycle.
+// One row per thread in 128-thread blocks: twice the blocks of a 256-thread
+// launch, to spread the rows over more SMs.
+constexpr int kUpdBlock = 128;
 template <typename VT>
-__global__ void __launch_bounds__(kBlock) k_pcg_update(int n, Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r,
+__global__ void __launch_bounds__(kUpdBlock) k_pcg_update(int n, Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r,
                                                        Vec4<VT>* __restrict__ z, const Vec4<VT>* __restrict__ p,
                                                        const Vec4<VT>* __restrict__ q, const VT* __restrict__ dinv,
                                                        int jacobi, VT omega, GridReduce gr,
                                                        PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
   if (S->done) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[2] = {0.0, 0.0};  // r.r, r.z
@@ -321,10 +332,10 @@ mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y) { return launch_spm
 
 template <typename VT, typename MT>
 mls_status launch_residual_t(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S) {
-  { ++ctx->launches; k_residual<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(sell_view(ctx), (const MT*)ctx->hval,
-                                                               (const Vec4<VT>*)b, (const Vec4<VT>*)x,
-                                                               (Vec4<VT>*)out, S); }
-  return cuda_check(ctx, cudaGetLastError(), "k_residual");
+  ++ctx->launches;
+  return cuda_check(ctx, launch_chained(k_residual<VT, MT>, dim3(ctx->n_slices), dim3(32 * kSpmvWarps), ctx->stream,
+                                        sell_view(ctx), (const MT*)ctx->hval, (const Vec4<VT>*)b, (const Vec4<VT>*)x,
+                                        (Vec4<VT>*)out, S), "k_residual");
 }
 
 mls_status launch_residual(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S) {
@@ -337,10 +348,11 @@ mls_status launch_residual(mls_ctx* ctx, const void* b, const void* x, void* out
 
 template <typename VT, typename MT>
 static mls_status post_smooth_t(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, PcgScalars* S) {
-  { ++ctx->launches; k_post_smooth_rz<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(
-      sell_view(ctx), (const MT*)ctx->hval, (const Vec4<VT>*)r, (const Vec4<VT>*)z2, (const VT*)ctx->dinv,
-      (VT)ctx->opt.omega, (Vec4<VT>*)zout, first, ctx->red, S); }
-  return cuda_check(ctx, cudaGetLastError(), "k_post_smooth_rz");
+  ++ctx->launches;
+  return cuda_check(ctx, launch_chained(k_post_smooth_rz<VT, MT>, dim3(ctx->n_slices), dim3(32 * kSpmvWarps), ctx->stream,
+                                        sell_view(ctx), (const MT*)ctx->hval, (const Vec4<VT>*)r, (const Vec4<VT>*)z2,
+                                        (const VT*)ctx->dinv, (VT)ctx->opt.omega, (Vec4<VT>*)zout, first, ctx->red, S),
+                    "k_post_smooth_rz");
 }
 
 mls_status launch_post_smooth_rz(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, PcgScalars* S) {
@@ -368,7 +380,8 @@ template <typename VT, typename MT>
 static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res) {
   const int n = ctx->n;
   const int nb = nblk(n);
-  if (nb > kMaxPartials || ctx->n_slices > kMaxPartials)
+  const int nb_upd = (n + kUpdBlock - 1) / kUpdBlock;
+  if (nb_upd > kMaxPartials || ctx->n_slices > kMaxPartials)
     return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
   const bool jacobi = ctx->opt.preconditioner == MLS_PRECOND_BLOCK_JACOBI;
   if (!jacobi && !ctx->coarse_ready) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_build_coarse");
@@ -415,10 +428,17 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
   for (; !ctx->opt.persistent;) {
     for (int c = 0; c < chunk; ++c) {
       int tk = prof_begin(ctx, MLS_PROF_SPMV);
-      { ++ctx->launches; k_pcg_spmv<VT, MT><<<ctx->n_slices, 32 * kSpmvWarps, 0, ctx->stream>>>(A, val, zf, p, q, ctx->red, S); }
+      ++ctx->launches;
+      if ((st = cuda_check(ctx, launch_chained(k_pcg_spmv<VT, MT>, dim3(ctx->n_slices), dim3(32 * kSpmvWarps), ctx->stream,
+                                               A, val, (const Vec4<VT>*)zf, p, q, ctx->red, S), "k_pcg_spmv")) != MLS_OK)
+        return st;
       prof_end(ctx, tk);
       tk = prof_begin(ctx, MLS_PROF_PCG_UPDATE);
-      { ++ctx->launches; k_pcg_update<VT><<<nb, kBlock, 0, ctx->stream>>>(n, x, r, z1, p, q, dinv, jacobi ? 1 : 2, omega, ctx->red, S); }
+      ++ctx->launches;
+      if ((st = cuda_check(ctx, launch_chained(k_pcg_update<VT>, dim3(nb_upd), dim3(kUpdBlock), ctx->stream, n, x, r, z1,
+                                               (const Vec4<VT>*)p, (const Vec4<VT>*)q, dinv, jacobi ? 1 : 2, omega,
+                                               ctx->red, S), "k_pcg_update")) != MLS_OK)
+        return st;
       prof_end(ctx, tk);
       if (!jacobi) {
         tk = prof_begin(ctx, MLS_PROF_PRECOND);
