@@ -87,6 +87,67 @@ __device__ __forceinline__ void spmv_quad(const SellView& A, const MT* __restric
   y[0] = y0; y[1] = y1; y[2] = y2;
 }
 
+// The same product split in two for chained launches: quad_load() reads the
+// column indices and values of a lane's first slots (H does not change
+// during a solve, so this may run before chain_wait(), while the previous
+// kernel finishes); quad_finish() gathers x after the wait, adds the
+// remaining slots, and combines the four lanes of a row.
+template <typename VT>
+struct QuadH {
+  static constexpr int PF = sizeof(VT) == 4 ? 4 : 2;   // slots per lane loaded ahead (register budget)
+  int len, rl, part;
+  int64_t g0;
+  int c[PF];
+  VT w[PF][9];
+};
+
+template <typename VT, typename MT>
+__device__ __forceinline__ void quad_load(const SellView& A, const MT* __restrict__ val, int slice, QuadH<VT>& h) {
+  h.part = threadIdx.x & 3;
+  h.rl = threadIdx.x >> 2;
+  const int row = slice * 32 + h.rl;
+  h.len = row < A.n ? A.row_len[row] : 0;
+  h.g0 = A.slice_ptr[slice];
+#pragma unroll
+  for (int u = 0; u < QuadH<VT>::PF; ++u) {
+    const int k = h.part + 4 * u;
+    const bool ok = k < h.len;
+    h.c[u] = ok ? __ldg(A.col + (h.g0 + k) * 32 + h.rl) : -1;
+    const MT* v = val + (h.g0 + (ok ? k : 0)) * 288 + h.rl;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) h.w[u][q] = ok ? load_as<VT>(v[32 * q]) : VT(0);
+  }
+}
+
+template <typename VT, typename MT>
+__device__ __forceinline__ void quad_finish(const SellView& A, const MT* __restrict__ val, const QuadH<VT>& h,
+                                            const Vec4<VT>* __restrict__ x, VT (&y)[3]) {
+  VT y0 = VT(0), y1 = VT(0), y2 = VT(0);
+#pragma unroll
+  for (int u = 0; u < QuadH<VT>::PF; ++u) {
+    if (h.c[u] < 0) continue;
+    const Vec4<VT> xv = x[h.c[u]];
+    y0 += h.w[u][0] * xv.x + h.w[u][1] * xv.y + h.w[u][2] * xv.z;
+    y1 += h.w[u][3] * xv.x + h.w[u][4] * xv.y + h.w[u][5] * xv.z;
+    y2 += h.w[u][6] * xv.x + h.w[u][7] * xv.y + h.w[u][8] * xv.z;
+  }
+  for (int k = h.part + 4 * QuadH<VT>::PF; k < h.len; k += 4) {
+    const int c = __ldg(A.col + (h.g0 + k) * 32 + h.rl);
+    const Vec4<VT> xv = x[c];
+    const MT* v = val + (h.g0 + k) * 288 + h.rl;
+    y0 += load_as<VT>(v[0]) * xv.x + load_as<VT>(v[32]) * xv.y + load_as<VT>(v[64]) * xv.z;
+    y1 += load_as<VT>(v[96]) * xv.x + load_as<VT>(v[128]) * xv.y + load_as<VT>(v[160]) * xv.z;
+    y2 += load_as<VT>(v[192]) * xv.x + load_as<VT>(v[224]) * xv.y + load_as<VT>(v[256]) * xv.z;
+  }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+  }
+  y[0] = y0; y[1] = y1; y[2] = y2;
+}
+
 // the row this thread finishes (part 0 of each quad), or -1
 __device__ __forceinline__ int quad_row(int slice, int n) {
   if (threadIdx.x & 3) return -1;
@@ -114,16 +175,18 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_spmv(SellView A, const 
 
 // out = b - H x
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_residual(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_residual(SellView A, const MT* __restrict__ val,
                                                               const Vec4<VT>* __restrict__ b,
                                                               const Vec4<VT>* __restrict__ x,
                                                               Vec4<VT>* __restrict__ out,
                                                               const PcgScalars* __restrict__ S) {
+  QuadH<VT> hq;
+  quad_load<VT, MT>(A, val, blockIdx.x, hq);
   chain_wait();
   chain_release();
   if (S && S->done) return;
   VT r[3];
-  spmv_quad<VT, MT>(A, val, blockIdx.x, x, r);
+  quad_finish<VT, MT>(A, val, hq, x, r);
   const int row = quad_row(blockIdx.x, A.n);
   if (row < 0) return;
   const Vec4<VT> bb = b[row];
@@ -179,18 +242,20 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(int n, const Vec4<VT>* __re
 // zout = z2 + omega D^{-1} (r - H z2) (the post-smoothing of the symmetric
 // two-level cycle), fused with r.zout and beta (0 on the first call)
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_post_smooth_rz(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_post_smooth_rz(SellView A, const MT* __restrict__ val,
                                                                     const Vec4<VT>* __restrict__ r,
                                                                     const Vec4<VT>* __restrict__ z2,
                                                                     const VT* __restrict__ dinv, VT omega,
                                                                     Vec4<VT>* __restrict__ zout, int first,
                                                                     GridReduce gr, PcgScalars* __restrict__ S) {
+  QuadH<VT> hq;
+  quad_load<VT, MT>(A, val, blockIdx.x, hq);
   chain_wait();
   chain_release();
   if (S->done) return;
   double acc[1] = {0.0};
   VT hz[3];
-  spmv_quad<VT, MT>(A, val, blockIdx.x, z2, hz);
+  quad_finish<VT, MT>(A, val, hq, z2, hz);
   const int row = quad_row(blockIdx.x, A.n);
   if (row >= 0) {
     const Vec4<VT> rv = r[row], zv = z2[row];
@@ -232,16 +297,18 @@ __global__ void __launch_bounds__(kBlock) k_pcg_rz(int n, const Vec4<VT>* __rest
 
 // w = H z; p = z + beta p; q = w + beta q; alpha = r.z / p.q
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_pcg_spmv(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_pcg_spmv(SellView A, const MT* __restrict__ val,
                                                               const Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p,
                                                               Vec4<VT>* __restrict__ q, GridReduce gr,
                                                               PcgScalars* __restrict__ S) {
+  QuadH<VT> hq;
+  quad_load<VT, MT>(A, val, blockIdx.x, hq);
   chain_wait();
   chain_release();
   if (S->done) return;
   double acc[1] = {0.0};
   VT w[3];
-  spmv_quad<VT, MT>(A, val, blockIdx.x, z, w);
+  quad_finish<VT, MT>(A, val, hq, z, w);
   const int row = quad_row(blockIdx.x, A.n);
   if (row >= 0) {
     const VT beta = (VT)S->beta;
