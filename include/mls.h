@@ -353,15 +353,18 @@ mls_status mls_coarse_project(mls_ctx* ctx, const double* x, double* q);
  * launch shapes of the PCG kernels on the assembled system and keeps the
  * fastest (mls_batch_retune forgets the choice).
  *
- * Options as for mls_create; the preconditioner must be block Jacobi
- * (otherwise MLS_EINVAL); cycle, omega, coarse_refresh and the persistent
- * settings are ignored.  Forces (gravity, ground plane, barrier) are shared by
+ * Options as for mls_create.  preconditioner: block Jacobi, or two-level
+ * with per-mesh bases (mls_batch_upload_basis; the symmetric multiplicative
+ * cycle with damping omega, coarse operators U_m^T H U_m built and factored
+ * once per step at the start iterate, in float64, one block per mesh).
+ * cycle, coarse_refresh and the persistent settings are ignored.  Forces (gravity, ground plane, barrier) are shared by
  * all meshes.  The batch owns a context and an internal stream, ordered after
  * opt->stream on every step.  Not in the paper. */
 typedef struct mls_batch mls_batch;
 
 typedef struct mls_batch_mesh_stats {
-  int32_t status;             /* MLS_OK, MLS_ENOTCONV, MLS_ELINESEARCH, MLS_ENONFINITE, MLS_EINVERTED */
+  int32_t status;             /* MLS_OK, MLS_ENOTCONV, MLS_ELINESEARCH, MLS_ENONFINITE, MLS_EINVERTED,
+                                 MLS_ECHOL (a coarse block not positive definite) */
   int32_t newton_iters;
   int32_t pcg_iters;          /* summed over the mesh's Newton iterations */
   int32_t line_search_trials;
@@ -395,6 +398,14 @@ mls_status mls_batch_upload(mls_batch* b, int32_t n_meshes, const int32_t* vert_
                             const int32_t* tet_offsets, const double* rest_xyz, const int32_t* tets,
                             const double* youngs, const double* poisson, const double* density,
                             const uint8_t* dirichlet);
+/* Per-mesh SMS bases (Sec. 3.5-3.6) for two-level preconditioning: mesh m
+ * owns handles [handle_offsets[m], handle_offsets[m+1]) (1 to 128 per mesh);
+ * origins [n_handles][3]; vrow [V+1], handle [nnz] (global handle ids, each
+ * vertex's handles within its own mesh), phi [nnz] in the batch's vertex
+ * numbering; HOST arrays, copied.  MLS_EINVAL on any violation. */
+mls_status mls_batch_upload_basis(mls_batch* b, int32_t n_handles, const int32_t* handle_offsets,
+                                  const double* origins, const int32_t* vrow, const int32_t* handle,
+                                  const double* phi);
 mls_status mls_batch_set_forces(mls_batch* b, const double* gravity, int contact, const double* plane_n,
                                 double plane_o, double dhat, double kappa);
 mls_status mls_batch_retune(mls_batch* b);

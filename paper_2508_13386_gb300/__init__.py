@@ -300,14 +300,15 @@ class Batch:
     """Many independent meshes advanced together (``mls_batch``): one graph
     launch per timestep, block-Jacobi PCG, per-mesh Newton decisions."""
 
-    def __init__(self, precision="fp32", newton_tol=1e-5, pcg_rtol=1e-4, max_newton=50, max_pcg=20000,
-                 stream=None):
+    def __init__(self, precision="fp32", preconditioner="jacobi", omega=0.5, newton_tol=1e-5, pcg_rtol=1e-4,
+                 max_newton=50, max_pcg=20000, stream=None):
         self._l = _get_lib()
         self._b = C.c_void_p()
         opt = _lib.Options()
         self._l.mls_default_options(C.byref(opt))
         opt.precision = _lib.PRECISION[precision]
-        opt.preconditioner = _lib.PRECOND["jacobi"]
+        opt.preconditioner = _lib.PRECOND[preconditioner]
+        opt.omega = float(omega)
         opt.newton_tol = float(newton_tol)
         opt.pcg_rtol = float(pcg_rtol)
         opt.max_newton = int(max_newton)
@@ -370,6 +371,26 @@ class Batch:
         self.n_meshes = len(vo) - 1
         self.vert_offsets = vo.copy()
         self.n = int(vo[-1])
+
+    def upload_bases(self, bases):
+        """Per-mesh bases (dicts with origins, vrow, handle, phi in each mesh's
+        own vertex and handle numbering), concatenated in mesh order."""
+        hoff, O, VR, H, PH = [0], [], [np.zeros(1, dtype=np.int64)], [], []
+        nnz = 0
+        for B in bases:
+            O.append(np.asarray(B["origins"], dtype=np.float64))
+            vr = np.asarray(B["vrow"], dtype=np.int64)
+            VR.append(vr[1:] + nnz)
+            H.append(np.asarray(B["handle"], dtype=np.int64) + hoff[-1])
+            PH.append(np.asarray(B["phi"], dtype=np.float64))
+            nnz += int(vr[-1])
+            hoff.append(hoff[-1] + len(B["origins"]))
+        ho, pho = _host(hoff, np.int32)
+        o, po = _host(np.concatenate(O), np.float64)
+        vr, pvr = _host(np.concatenate(VR), np.int32)
+        h, ph = _host(np.concatenate(H), np.int32)
+        f, pf = _host(np.concatenate(PH), np.float64)
+        self._check(self._l.mls_batch_upload_basis(self._b, int(hoff[-1]), pho, po, pvr, ph, pf))
 
     def set_forces(self, gravity=(0.0, 0.0, -9.81), contact=False, plane_n=(0.0, 0.0, 1.0), plane_o=0.0,
                    dhat=1e-3, kappa=1e5):

@@ -32,7 +32,7 @@
 namespace mls {
 
 enum { BPH_ASSEMBLE = 0, BPH_LS = 1, BPH_FINAL = 2, BPH_DONE = 3 };
-enum { BC_PREP = 0, BC_SPMV, BC_UPD, BC_DIR, BC_ENERGY, BC_COUNT };
+enum { BC_PREP = 0, BC_SPMV, BC_UPD, BC_DIR, BC_ENERGY, BC_SMOOTH, BC_COUNT };
 
 // per-mesh state (device)
 struct BMesh {
@@ -320,11 +320,14 @@ __global__ void k_bapply(BView V, Vec4d* __restrict__ xk, const Vec4d* __restric
 }
 
 // ---- Newton iteration start: PCG initialisation and tolerance per mesh ---------------------
+// two_level: z receives the smoothing term omega D^{-1} b of the first cycle
+// (r.z then comes from the cycle's post-smoothing); otherwise z = D^{-1} b
+// and r.z are formed here.
 template <typename VT>
-__global__ void k_bprep(BView V, BParams P, const Vec4d* __restrict__ grad, const Vec4<VT>* __restrict__ b,
-                        const VT* __restrict__ dinv, const Vec4d* __restrict__ xk, const Vec4d* __restrict__ xt,
-                        Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r, Vec4<VT>* __restrict__ z,
-                        Vec4<VT>* __restrict__ p, Vec4<VT>* __restrict__ q) {
+__global__ void k_bprep(BView V, BParams P, int two_level, VT omega, const Vec4d* __restrict__ grad,
+                        const Vec4<VT>* __restrict__ b, const VT* __restrict__ dinv, const Vec4d* __restrict__ xk,
+                        const Vec4d* __restrict__ xt, Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r,
+                        Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p, Vec4<VT>* __restrict__ q) {
   const int m = V.rb_mesh[blockIdx.x];
   BMesh* M = V.M + m;
   if (M->phase != BPH_ASSEMBLE) return;
@@ -336,12 +339,13 @@ __global__ void k_bprep(BView V, BParams P, const Vec4d* __restrict__ grad, cons
     acc[0] += g.x * g.x + g.y * g.y + g.z * g.z;
     const Vec4<VT> bv = b[v];
     const VT* D = dinv + (int64_t)v * 9;
-    const Vec4<VT> zv{D[0] * bv.x + D[1] * bv.y + D[2] * bv.z, D[3] * bv.x + D[4] * bv.y + D[5] * bv.z,
-                      D[6] * bv.x + D[7] * bv.y + D[8] * bv.z, VT(0)};
+    const VT w = two_level ? omega : VT(1);
+    const Vec4<VT> zv{w * (D[0] * bv.x + D[1] * bv.y + D[2] * bv.z), w * (D[3] * bv.x + D[4] * bv.y + D[5] * bv.z),
+                      w * (D[6] * bv.x + D[7] * bv.y + D[8] * bv.z), VT(0)};
     x[v] = zero; p[v] = zero; q[v] = zero;
     r[v] = bv;
     z[v] = zv;
-    acc[1] += (double)bv.x * zv.x + (double)bv.y * zv.y + (double)bv.z * zv.z;
+    if (!two_level) acc[1] += (double)bv.x * zv.x + (double)bv.y * zv.y + (double)bv.z * zv.z;
     const Vec4d a = xk[v], c = xt[v];
     xd = fmax(xd, fmax(fabs(a.x - c.x), fmax(fabs(a.y - c.y), fabs(a.z - c.z))));
   }
@@ -390,6 +394,8 @@ __global__ void __launch_bounds__(32 * LANES) k_bspmv(BView V, int n, const int*
                                                       const int* __restrict__ col, const int* __restrict__ row_len,
                                                       const MT* __restrict__ val, const Vec4<VT>* __restrict__ z,
                                                       Vec4<VT>* __restrict__ p, Vec4<VT>* __restrict__ q) {
+  chain_wait();
+  chain_release();
   const int s = blockIdx.x;
   const int m = V.sl_mesh[s];
   BMesh* M = V.M + m;
@@ -454,10 +460,14 @@ __global__ void __launch_bounds__(32 * LANES) k_bspmv(BView V, int n, const int*
   }
 }
 
+// two_level: z = omega D^{-1} r (the cycle's pre-smoothing; r.z and beta
+// come from its post-smoothing); otherwise z = D^{-1} r with r.z and beta
 template <typename VT>
-__global__ void k_bupdate(BView V, int max_iter, const VT* __restrict__ dinv, Vec4<VT>* __restrict__ x,
-                          Vec4<VT>* __restrict__ r, Vec4<VT>* __restrict__ z, const Vec4<VT>* __restrict__ p,
-                          const Vec4<VT>* __restrict__ q) {
+__global__ void k_bupdate(BView V, int max_iter, int two_level, VT omega, const VT* __restrict__ dinv,
+                          Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r, Vec4<VT>* __restrict__ z,
+                          const Vec4<VT>* __restrict__ p, const Vec4<VT>* __restrict__ q) {
+  chain_wait();
+  chain_release();
   const int m = V.rb_mesh[blockIdx.x];
   BMesh* M = V.M + m;
   if (M->phase != BPH_ASSEMBLE || M->done) return;
@@ -471,8 +481,9 @@ __global__ void k_bupdate(BView V, int max_iter, const VT* __restrict__ dinv, Ve
     x[v] = xv;
     r[v] = rv;
     const VT* D = dinv + (int64_t)v * 9;
-    const Vec4<VT> zv{D[0] * rv.x + D[1] * rv.y + D[2] * rv.z, D[3] * rv.x + D[4] * rv.y + D[5] * rv.z,
-                      D[6] * rv.x + D[7] * rv.y + D[8] * rv.z, VT(0)};
+    const VT w = two_level ? omega : VT(1);
+    const Vec4<VT> zv{w * (D[0] * rv.x + D[1] * rv.y + D[2] * rv.z), w * (D[3] * rv.x + D[4] * rv.y + D[5] * rv.z),
+                      w * (D[6] * rv.x + D[7] * rv.y + D[8] * rv.z), VT(0)};
     z[v] = zv;
     acc[0] += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z;
     acc[1] += (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z;
@@ -494,6 +505,7 @@ __global__ void k_bupdate(BView V, int max_iter, const VT* __restrict__ dinv, Ve
   if (!isfinite(tot[0])) { M->done = 3; return; }
   if (tot[0] <= M->tol2) { M->done = 1; return; }
   if (M->iter >= max_iter) { M->done = 2; return; }
+  if (two_level) return;
   M->beta = tot[1] / M->rz;
   M->rz = tot[1];
 }
@@ -574,11 +586,16 @@ __global__ void k_bdir(BView V, BParams P, const Vec4<VT>* __restrict__ xs, cons
 // which: 0 PCG (some mesh still iterating), 1 line search (some mesh still
 // searching; clears the accept flags), 2 Newton (some mesh not done; caps
 // the iteration count).  *trip counts the evaluations.
+// trip_cap bounds the evaluations of one loop condition per timestep (the
+// largest count the per-mesh iteration caps allow): should it ever be
+// reached, the loop ends and the meshes still in it are marked not converged,
+// so a graph loop cannot run without end.
 __global__ void k_bcond(int nmesh, BMesh* __restrict__ M, int which, int max_newton, cudaGraphConditionalHandle h,
-                        int use_handle, int* __restrict__ any_out, int* __restrict__ trip) {
+                        int use_handle, int* __restrict__ any_out, int* __restrict__ trip, int trip_cap) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
+  const bool capped = *trip >= trip_cap;
   int mine = 0;
   for (int m = threadIdx.x; m < nmesh; m += blockDim.x) {
     BMesh* s = M + m;
@@ -597,11 +614,369 @@ __global__ void k_bcond(int nmesh, BMesh* __restrict__ M, int which, int max_new
   }
   if (mine) atomicOr(&any, 1);
   __syncthreads();
+  if (capped && any) {
+    for (int m = threadIdx.x; m < nmesh; m += blockDim.x) {
+      BMesh* s = M + m;
+      if (s->phase != BPH_DONE) {
+        s->status = MLS_ENOTCONV;
+        s->phase = BPH_DONE;
+        s->done = 1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
     if (use_handle) cudaGraphSetConditional(h, any ? 1u : 0u);
     if (any_out) *any_out = any;
     *trip += 1;
   }
+}
+
+
+// ---- two-level preconditioning per mesh --------------------------------------------------
+// Each mesh has its own SMS basis (handles numbered globally, a mesh's
+// handles contiguous); U is block diagonal, so U^T H U is block diagonal too
+// and the dense Galerkin product leaves only each mesh's diagonal block
+// non-zero.  Each block is factored in float64 by one CTA (right-looking
+// Cholesky), its inverse factor W_m = L_m^{-1} formed column by column, and
+// the coarse solve is W_m^T (W_m c_m) per mesh.
+constexpr int kMaxCoarseRows = 1536;   // 128 handles per mesh
+
+struct BCoarse {
+  int r;                   // total coarse rows (12 x handles)
+  const int* coff;         // [nmesh] first coarse row of each mesh
+  const int* csz;          // [nmesh] coarse rows of each mesh
+  const int64_t* woff;     // [nmesh] first entry of the mesh's W block (csz^2 entries)
+  const int* crow_mesh;    // [r] mesh of each coarse row
+  const int* hmesh;        // [m] mesh of each handle
+};
+
+__device__ __forceinline__ bool pcg_active(const BMesh* M) { return M->phase == BPH_ASSEMBLE && !M->done; }
+
+// right-looking Cholesky of the mesh's diagonal block of A (float64, leading
+// dimension ld), in place; a non-positive pivot fails the mesh (MLS_ECHOL)
+__global__ void __launch_bounds__(256) k_bchol(BView V, BCoarse C, double* __restrict__ A, int ld) {
+  const int m = blockIdx.x;
+  BMesh* M = V.M + m;
+  if (M->phase == BPH_DONE) return;
+  const int o = C.coff[m], n = C.csz[m];
+  double* a = A + (int64_t)o * ld + o;
+  __shared__ double col[kMaxCoarseRows];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = 0; j < n; ++j) {
+    __syncthreads();
+    const double d = a[(int64_t)j * ld + j];
+    if (!(d > 0.0) || !isfinite(d)) {
+      if (threadIdx.x == 0) bad = j + 1;
+      break;
+    }
+    const double piv = sqrt(d), inv = 1.0 / piv;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = a[(int64_t)i * ld + j] * inv;
+      a[(int64_t)i * ld + j] = v;
+      col[i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a[(int64_t)j * ld + j] = piv;
+    for (int i = j + 1 + warp; i < n; i += nw) {
+      const double li = col[i];
+      double* ai = a + (int64_t)i * ld;
+      for (int k = j + 1 + lane; k <= i; k += 32) ai[k] -= li * col[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && bad) {
+    M->status = MLS_ECHOL;
+    M->phase = BPH_DONE;
+    M->done = 1;
+  }
+}
+
+// W_m = L_m^{-1} (lower triangular) by forward substitution, one column per
+// thread, in float64 (scratch S, same layout as A), then W and W^T in solve
+// precision (row-major csz x csz blocks at woff)
+template <typename VT>
+__global__ void __launch_bounds__(256) k_btrinv(BView V, BCoarse C, const double* __restrict__ A,
+                                                double* __restrict__ S, int ld, VT* __restrict__ W,
+                                                VT* __restrict__ WT) {
+  const int m = blockIdx.x;
+  if (V.M[m].phase == BPH_DONE) return;
+  const int o = C.coff[m], n = C.csz[m];
+  const double* L = A + (int64_t)o * ld + o;
+  double* w = S + (int64_t)o * ld + o;
+  VT* Wm = W + C.woff[m];
+  VT* WTm = WT + C.woff[m];
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int i = 0; i < n; ++i) {
+      double v = 0.0;
+      if (i == c) {
+        v = 1.0 / L[(int64_t)i * ld + i];
+      } else if (i > c) {
+        double acc = 0.0;
+        const double* Li = L + (int64_t)i * ld;
+        for (int k = c; k < i; ++k) acc += Li[k] * w[(int64_t)k * ld + c];
+        v = -acc / Li[i];
+      }
+      w[(int64_t)i * ld + c] = v;
+      Wm[(int64_t)i * n + c] = (VT)v;
+      WTm[(int64_t)c * n + i] = (VT)v;
+    }
+  }
+}
+
+// y = W x (lower = 1) or W^T x (lower = 0) per mesh block; four warps per
+// coarse row, 16-byte loads over the row's triangle
+template <typename VT>
+__global__ void __launch_bounds__(256) k_btrigemv(BView V, BCoarse C, const VT* __restrict__ W, int lower,
+                                                  const VT* __restrict__ x, VT* __restrict__ y) {
+  chain_wait();
+  chain_release();
+  constexpr int EV = 16 / sizeof(VT);
+  constexpr int WPR = 4;
+  __shared__ VT part[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * (8 / WPR) + warp / WPR;
+  const int sub = warp % WPR;
+  VT acc = VT(0);
+  bool on = false;
+  if (g < C.r) {
+    const int m = C.crow_mesh[g];
+    on = pcg_active(V.M + m);
+    if (on) {
+      const int o = C.coff[m], n = C.csz[m], i = g - o;
+      const int v0 = lower ? 0 : i / EV;
+      const int v1 = lower ? (i + EV) / EV : n / EV;
+      using V16 = typename std::conditional<sizeof(VT) == 4, float4, double2>::type;
+      const V16* Wr = reinterpret_cast<const V16*>(W + C.woff[m] + (int64_t)i * n);
+      const V16* xv = reinterpret_cast<const V16*>(x + o);
+      for (int c = v0 + sub * 32 + lane; c < v1; c += 32 * WPR) {
+        const V16 a = Wr[c];
+        const V16 b = xv[c];
+        if constexpr (sizeof(VT) == 4) acc += a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+        else acc += a.x * b.x + a.y * b.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
+  if (lane == 0) part[warp] = acc;
+  __syncthreads();
+  if (on && sub == 0 && lane == 0) {
+    VT t = VT(0);
+#pragma unroll
+    for (int k = 0; k < WPR; ++k) t += part[warp + k];
+    y[g] = t;
+  }
+}
+
+// c_j = sum_{v in supp j} phi_j(v) t_v (x) a_vj, one warp per chunk of a
+// handle's entries (as the single-mesh restriction), meshes done skipped
+struct BBasisView {
+  const void* vcoef; const void* hcoef;
+  const int* vrow; const int* vh; const int* hrow; const int* hv;
+  const int* rchunk_handle; const int* rchunk_beg; const int* rchunk_ptr;
+  double* rpart; unsigned* rcount; int nrchunk;
+};
+constexpr int kBRestrictChunk = 256;
+
+template <typename VT>
+__global__ void __launch_bounds__(256) k_brestrict(BView V, BCoarse C, BBasisView B, const Vec4<VT>* __restrict__ t,
+                                                   VT* __restrict__ c) {
+  chain_wait();
+  chain_release();
+  const int lane = threadIdx.x & 31;
+  const int ch = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (ch >= B.nrchunk) return;
+  const int j = B.rchunk_handle[ch];
+  if (!pcg_active(V.M + C.hmesh[j])) return;
+  const int p0 = B.rchunk_beg[ch];
+  const int p1 = min(p0 + kBRestrictChunk, B.hrow[j + 1]);
+  constexpr int U = kBRestrictChunk / 32;
+  int hv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int p = p0 + lane + 32 * u;
+    hv[u] = p < p1 ? B.hv[p] : -1;
+  }
+  VT acc[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) acc[q] = VT(0);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (hv[u] < 0) continue;
+    const Vec4<VT> a = ((const Vec4<VT>*)B.hcoef)[p0 + lane + 32 * u];
+    const Vec4<VT> rv = t[hv[u]];
+    const VT rc[3] = {rv.x, rv.y, rv.z};
+    const VT av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) acc[4 * cc + l] += rc[cc] * av[l];
+  }
+#pragma unroll
+  for (int q = 0; q < 12; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  VT mine = acc[0];
+#pragma unroll
+  for (int q = 1; q < 12; ++q)
+    if (lane == q) mine = acc[q];
+  if (lane < 12) B.rpart[12 * (int64_t)ch + lane] = (double)mine;
+  __syncwarp();
+  unsigned last = 0;
+  if (lane == 0) {
+    __threadfence();
+    const unsigned nch = (unsigned)(B.rchunk_ptr[j + 1] - B.rchunk_ptr[j]);
+    last = atomicAdd(B.rcount + j, 1u) == nch - 1;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  if (lane < 12) {
+    double s = 0.0;
+    for (int k = B.rchunk_ptr[j]; k < B.rchunk_ptr[j + 1]; ++k) s += __ldcg(B.rpart + 12 * (int64_t)k + lane);
+    c[12 * (int64_t)j + lane] = (VT)s;
+  }
+  if (lane == 0) B.rcount[j] = 0;
+}
+
+// z1 += U c over the rows of active meshes
+template <typename VT>
+__global__ void k_bprolong(BView V, BBasisView B, const VT* __restrict__ c, Vec4<VT>* __restrict__ z1) {
+  chain_wait();
+  chain_release();
+  const int m = V.rb_mesh[blockIdx.x];
+  if (!pcg_active(V.M + m)) return;
+  const Vec4<VT>* coef = (const Vec4<VT>*)B.vcoef;
+  for (int v = V.rb_row0[blockIdx.x] + threadIdx.x; v < V.rb_row1[blockIdx.x]; v += blockDim.x) {
+    VT o0 = VT(0), o1 = VT(0), o2 = VT(0);
+    const int k1 = B.vrow[v + 1];
+    for (int k0 = B.vrow[v]; k0 < k1; k0 += 4) {
+      int h[4];
+      Vec4<VT> a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = k0 + u < k1;
+        h[u] = ok ? B.vh[k0 + u] : -1;
+        a[u] = ok ? coef[k0 + u] : Vec4<VT>{VT(0), VT(0), VT(0), VT(0)};
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (h[u] < 0) continue;
+        const Vec4<VT>* qj = (const Vec4<VT>*)(c + 12 * (int64_t)h[u]);
+        const Vec4<VT> q0 = qj[0], q1 = qj[1], q2 = qj[2];
+        o0 += a[u].x * q0.x + a[u].y * q0.y + a[u].z * q0.z + a[u].w * q0.w;
+        o1 += a[u].x * q1.x + a[u].y * q1.y + a[u].z * q1.z + a[u].w * q1.w;
+        o2 += a[u].x * q2.x + a[u].y * q2.y + a[u].z * q2.z + a[u].w * q2.w;
+      }
+    }
+    const Vec4<VT> zb = z1[v];
+    z1[v] = Vec4<VT>{zb.x + o0, zb.y + o1, zb.z + o2, VT(0)};
+  }
+}
+
+// product of one slice of H with z (four lanes per row); rows of the slice
+// returned in y of the lane with part == 0
+template <typename VT, typename MT>
+__device__ __forceinline__ void bslice_product(int n, const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                               const int* __restrict__ row_len, const MT* __restrict__ val, int s,
+                                               const Vec4<VT>* __restrict__ z, VT (&y)[3]) {
+  const int part = threadIdx.x & 3, rl = threadIdx.x >> 2;
+  const int row = s * 32 + rl;
+  const int len = row < n ? row_len[row] : 0;
+  const int64_t g0 = slice_ptr[s];
+  VT y0 = VT(0), y1 = VT(0), y2 = VT(0);
+  for (int k0 = part; k0 < len; k0 += 16) {
+    int cc[4];
+    bool ok[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 4 * u;
+      ok[u] = k < len;
+      cc[u] = ok[u] ? __ldg(col + (g0 + k) * 32 + rl) : 0;
+    }
+    Vec4<VT> xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = ok[u] ? z[cc[u]] : Vec4<VT>{VT(0), VT(0), VT(0), VT(0)};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!ok[u]) continue;
+      const MT* v = val + (g0 + k0 + 4 * u) * 288 + rl;
+      y0 += load_as<VT>(v[0]) * xv[u].x + load_as<VT>(v[32]) * xv[u].y + load_as<VT>(v[64]) * xv[u].z;
+      y1 += load_as<VT>(v[96]) * xv[u].x + load_as<VT>(v[128]) * xv[u].y + load_as<VT>(v[160]) * xv[u].z;
+      y2 += load_as<VT>(v[192]) * xv[u].x + load_as<VT>(v[224]) * xv[u].y + load_as<VT>(v[256]) * xv[u].z;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o <= 2; o <<= 1) {
+    y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+    y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    y2 += __shfl_xor_sync(0xffffffffu, y2, o);
+  }
+  y[0] = y0; y[1] = y1; y[2] = y2;
+}
+
+// t = r - H z1 (the residual of the pre-smoothed iterate), active meshes
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(128) k_bresidual(BView V, int n, const int* __restrict__ slice_ptr,
+                                                   const int* __restrict__ col, const int* __restrict__ row_len,
+                                                   const MT* __restrict__ val, const Vec4<VT>* __restrict__ r,
+                                                   const Vec4<VT>* __restrict__ z1, Vec4<VT>* __restrict__ t) {
+  chain_wait();
+  chain_release();
+  const int s = blockIdx.x;
+  if (!pcg_active(V.M + V.sl_mesh[s])) return;
+  VT y[3];
+  bslice_product<VT, MT>(n, slice_ptr, col, row_len, val, s, z1, y);
+  const int row = s * 32 + (threadIdx.x >> 2);
+  if ((threadIdx.x & 3) == 0 && row < n) {
+    const Vec4<VT> rv = r[row];
+    t[row] = Vec4<VT>{rv.x - y[0], rv.y - y[1], rv.z - y[2], VT(0)};
+  }
+}
+
+// zf = z1 + omega D^{-1} (r - H z1) and r.zf per mesh (beta = 0 when first)
+template <typename VT, typename MT>
+__global__ void __launch_bounds__(128) k_bpost_smooth(BView V, int first, VT omega, int n,
+                                                      const int* __restrict__ slice_ptr, const int* __restrict__ col,
+                                                      const int* __restrict__ row_len, const MT* __restrict__ val,
+                                                      const VT* __restrict__ dinv, const Vec4<VT>* __restrict__ r,
+                                                      const Vec4<VT>* __restrict__ z1, Vec4<VT>* __restrict__ zf) {
+  chain_wait();
+  chain_release();
+  const int s = blockIdx.x;
+  const int m = V.sl_mesh[s];
+  BMesh* M = V.M + m;
+  if (!pcg_active(M)) return;
+  VT y[3];
+  bslice_product<VT, MT>(n, slice_ptr, col, row_len, val, s, z1, y);
+  const int row = s * 32 + (threadIdx.x >> 2);
+  double acc[1] = {0.0};
+  if ((threadIdx.x & 3) == 0 && row < n) {
+    const Vec4<VT> rv = r[row], zv = z1[row];
+    const VT t0 = rv.x - y[0], t1 = rv.y - y[1], t2 = rv.z - y[2];
+    const VT* D = dinv + (int64_t)row * 9;
+    const Vec4<VT> zo{zv.x + omega * (D[0] * t0 + D[1] * t1 + D[2] * t2),
+                      zv.y + omega * (D[3] * t0 + D[4] * t1 + D[5] * t2),
+                      zv.z + omega * (D[6] * t0 + D[7] * t1 + D[8] * t2), VT(0)};
+    zf[row] = zo;
+    acc[0] = (double)rv.x * zo.x + (double)rv.y * zo.y + (double)rv.z * zo.z;
+  }
+  bsum<1>(acc);
+  if (threadIdx.x == 0) V.part_sl[s] = acc[0];
+  if (!last_of_mesh(V.cnt + BC_SMOOTH * V.nmesh + m, (unsigned)V.sl_count[m])) return;
+  double tot[1] = {0.0};
+  const int s0 = V.sl_first[m], nsm = V.sl_count[m];
+  for (int i = threadIdx.x; i < nsm; i += blockDim.x) tot[0] += __ldcg(V.part_sl + s0 + i);
+  bsum<1>(tot);
+  if (threadIdx.x != 0) return;
+  M->beta = first ? 0.0 : tot[0] / M->rz;
+  M->rz = tot[0];
+  if (!(tot[0] > 0.0) || !isfinite(tot[0])) M->done = (M->rr <= M->tol2) ? 1 : 3;
 }
 
 }  // namespace mls
@@ -622,6 +997,7 @@ struct mls_batch {
   int n_user = 0;       // concatenated user vertices
   int n = 0;            // padded internal vertices
   std::vector<int> h_voff, h_toff, h_ioff, h_ipad;   // user vertex offsets, tet offsets, internal offsets, padded sizes
+  std::vector<int> h_vmap;
   int* vmap = nullptr;  // [n] internal -> user vertex (-1: dummy)
   double* bx = nullptr; // [n][3] packed x, v
   double* bv = nullptr;
@@ -648,6 +1024,14 @@ struct mls_batch {
   double graph_dt = -1.0;
   bool graph_dirty = true;
   int64_t launches_fixed = 0, launches_newton = 0, launches_pcg = 0, launches_ls = 0;
+  // two-level preconditioning (per-mesh bases)
+  bool two_level = false;
+  bool has_basis = false;
+  BCoarse coarse{};
+  std::vector<void*> coarse_alloc;
+  void* W = nullptr;      // block-diagonal inverse factors, solve precision
+  void* WT = nullptr;
+  bool galerkin_warm = false;
 };
 
 namespace {
@@ -770,29 +1154,94 @@ struct Tally {
 };
 
 template <typename VT, typename MT>
+mls_status launch_cycle(mls_batch* b, cudaStream_t s, int first);
+
+BBasisView bbasis(mls_ctx* c) {
+  const Basis& B = c->basis;
+  return BBasisView{B.vcoef, B.hcoef, B.vrow, B.vh, B.hrow, B.hv, B.rchunk_handle, B.rchunk_beg, B.rchunk_ptr,
+                    B.rpart, B.rcount, B.nrchunk};
+}
+
+// one PCG iteration for every active mesh: product and direction update,
+// vector update, and (two-level) the multiplicative cycle
+template <typename VT, typename MT>
 mls_status launch_pcg_iter(mls_batch* b, cudaStream_t s) {
   mls_ctx* c = b->ctx;
   const BView& V = b->view;
   const int ns = c->n_slices;
+  const bool tl = b->two_level;
+  const Vec4<VT>* zin = (const Vec4<VT>*)(tl ? c->vz2 : c->vz);
+  cudaError_t e;
   if (b->shape.lanes == 8)
-    k_bspmv<VT, MT, 8><<<ns, 256, 0, s>>>(V, c->n, c->slice_ptr, c->col, c->row_len, (const MT*)c->hval,
-                                          (const Vec4<VT>*)c->vz, (Vec4<VT>*)c->vp, (Vec4<VT>*)c->vq);
+    e = launch_chained(k_bspmv<VT, MT, 8>, dim3(ns), dim3(256), s, V, c->n, (const int*)c->slice_ptr,
+                       (const int*)c->col, (const int*)c->row_len, (const MT*)c->hval, zin, (Vec4<VT>*)c->vp,
+                       (Vec4<VT>*)c->vq);
   else
-    k_bspmv<VT, MT, 4><<<ns, 128, 0, s>>>(V, c->n, c->slice_ptr, c->col, c->row_len, (const MT*)c->hval,
-                                          (const Vec4<VT>*)c->vz, (Vec4<VT>*)c->vp, (Vec4<VT>*)c->vq);
-  k_bupdate<VT><<<V.nrb, b->shape.row_threads, 0, s>>>(V, c->opt.max_pcg, (const VT*)c->dinv, (Vec4<VT>*)c->vx,
-                                                      (Vec4<VT>*)c->vr, (Vec4<VT>*)c->vz, (const Vec4<VT>*)c->vp,
-                                                      (const Vec4<VT>*)c->vq);
-  return bcheck(b, cudaGetLastError(), "batched PCG iteration");
+    e = launch_chained(k_bspmv<VT, MT, 4>, dim3(ns), dim3(128), s, V, c->n, (const int*)c->slice_ptr,
+                       (const int*)c->col, (const int*)c->row_len, (const MT*)c->hval, zin, (Vec4<VT>*)c->vp,
+                       (Vec4<VT>*)c->vq);
+  mls_status st = bcheck(b, e, "k_bspmv");
+  if (st != MLS_OK) return st;
+  st = bcheck(b, launch_chained(k_bupdate<VT>, dim3(V.nrb), dim3(b->shape.row_threads), s, V, c->opt.max_pcg,
+                                tl ? 1 : 0, (VT)c->opt.omega, (const VT*)c->dinv, (Vec4<VT>*)c->vx,
+                                (Vec4<VT>*)c->vr, (Vec4<VT>*)c->vz, (const Vec4<VT>*)c->vp,
+                                (const Vec4<VT>*)c->vq), "k_bupdate");
+  if (st != MLS_OK || !tl) return st;
+  return launch_cycle<VT, MT>(b, s, 0);
+}
+
+// the symmetric multiplicative two-level cycle on r with the pre-smoothed
+// z1 = omega D^{-1} r in vz: t = r - H z1; c = W^T W U^T t; z1 += U c;
+// zf = z1 + omega D^{-1} (r - H z1) into vz2, with r.zf and beta
+template <typename VT, typename MT>
+mls_status launch_cycle(mls_batch* b, cudaStream_t s, int first) {
+  mls_ctx* c = b->ctx;
+  const BView& V = b->view;
+  const int ns = c->n_slices;
+  mls_status st = bcheck(b, launch_chained(k_bresidual<VT, MT>, dim3(ns), dim3(128), s, V, c->n,
+                                           (const int*)c->slice_ptr, (const int*)c->col, (const int*)c->row_len,
+                                           (const MT*)c->hval, (const Vec4<VT>*)c->vr, (const Vec4<VT>*)c->vz,
+                                           (Vec4<VT>*)c->vw), "k_bresidual");
+  if (st != MLS_OK) return st;
+  const BBasisView BB = bbasis(c);
+  if ((st = bcheck(b, launch_chained(k_brestrict<VT>, dim3((BB.nrchunk + 7) / 8), dim3(256), s, V, b->coarse, BB,
+                                     (const Vec4<VT>*)c->vw, (VT*)c->cvec), "k_brestrict")) != MLS_OK)
+    return st;
+  const int rg = (b->coarse.r + 1) / 2;
+  if ((st = bcheck(b, launch_chained(k_btrigemv<VT>, dim3(rg), dim3(256), s, V, b->coarse, (const VT*)b->W, 1,
+                                     (const VT*)c->cvec, (VT*)c->cvec2), "k_btrigemv")) != MLS_OK)
+    return st;
+  if ((st = bcheck(b, launch_chained(k_btrigemv<VT>, dim3(rg), dim3(256), s, V, b->coarse, (const VT*)b->WT, 0,
+                                     (const VT*)c->cvec2, (VT*)c->cvec), "k_btrigemv")) != MLS_OK)
+    return st;
+  if ((st = bcheck(b, launch_chained(k_bprolong<VT>, dim3(V.nrb), dim3(b->shape.row_threads), s, V, BB,
+                                     (const VT*)c->cvec, (Vec4<VT>*)c->vz), "k_bprolong")) != MLS_OK)
+    return st;
+  return bcheck(b, launch_chained(k_bpost_smooth<VT, MT>, dim3(ns), dim3(128), s, V, first, (VT)c->opt.omega, c->n,
+                                  (const int*)c->slice_ptr, (const int*)c->col, (const int*)c->row_len,
+                                  (const MT*)c->hval, (const VT*)c->dinv, (const Vec4<VT>*)c->vr,
+                                  (const Vec4<VT>*)c->vz, (Vec4<VT>*)c->vz2), "k_bpost_smooth");
+}
+
+// Galerkin operator of every mesh (dense product, block diagonal), its
+// per-mesh float64 Cholesky and inverse factors
+template <typename VT>
+mls_status launch_coarse(mls_batch* b, cudaStream_t s) {
+  mls_ctx* c = b->ctx;
+  mls_status st = build_galerkin(c);
+  if (st != MLS_OK) return bfail(b, st, mls_last_error(c));
+  k_bchol<<<b->nmesh, 256, 0, s>>>(b->view, b->coarse, c->Ac, b->coarse.r);
+  k_btrinv<VT><<<b->nmesh, 256, 0, s>>>(b->view, b->coarse, c->Ac, c->Acopy, b->coarse.r, (VT*)b->W, (VT*)b->WT);
+  return bcheck(b, cudaGetLastError(), "batched coarse factor");
 }
 
 template <typename VT>
 mls_status launch_prep(mls_batch* b, cudaStream_t s, const BParams& P) {
   mls_ctx* c = b->ctx;
-  k_bprep<VT><<<b->view.nrb, b->shape.row_threads, 0, s>>>(b->view, P, c->grad, (const Vec4<VT>*)c->vb,
-                                                          (const VT*)c->dinv, c->xk, c->xt, (Vec4<VT>*)c->vx,
-                                                          (Vec4<VT>*)c->vr, (Vec4<VT>*)c->vz, (Vec4<VT>*)c->vp,
-                                                          (Vec4<VT>*)c->vq);
+  k_bprep<VT><<<b->view.nrb, b->shape.row_threads, 0, s>>>(b->view, P, b->two_level ? 1 : 0, (VT)c->opt.omega,
+                                                          c->grad, (const Vec4<VT>*)c->vb, (const VT*)c->dinv,
+                                                          c->xk, c->xt, (Vec4<VT>*)c->vx, (Vec4<VT>*)c->vr,
+                                                          (Vec4<VT>*)c->vz, (Vec4<VT>*)c->vp, (Vec4<VT>*)c->vq);
   return bcheck(b, cudaGetLastError(), "k_bprep");
 }
 
@@ -878,6 +1327,11 @@ mls_status capture_step(mls_batch* b, double dt) {
   const int eb = V.ntb + V.nrb;
   const int rt = b->shape.row_threads;
   int* trips = b->trips;   // [0] PCG bodies, [1] line-search bodies, [2] Newton bodies, [3] loop entries
+  // worst-case loop trips per timestep allowed by the per-mesh caps
+  const int cap_newton = P.max_newton + 1;
+  const int cap_pcg = std::min<int64_t>(INT32_MAX / 2, ((int64_t)P.max_pcg / 2 + 2) * cap_newton);
+  const int cap_ls = 64 * cap_newton;
+  const int cap_entry = 4 * cap_newton;
   auto run = [&]() -> mls_status {
     mls_status r;
     if ((r = bcheck(b, cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed), "begin capture")) != MLS_OK) return r;
@@ -888,6 +1342,13 @@ mls_status capture_step(mls_batch* b, double dt) {
     k_benergy<0><<<eb, kTetBlock, 0, s0>>>(V, EI, P, c->xt, c->xt);
     k_benergy<1><<<eb, kTetBlock, 0, s0>>>(V, EI, P, c->xk, c->xk);
     k_bselect<<<V.nrb, rt, 0, s0>>>(V, c->xt, c->xk);
+    if (b->two_level) {
+      // coarse operators once per step, at the start iterate
+      if ((r = launch_eval_elements(c, c->xk, nullptr)) != MLS_OK) return r;
+      if ((r = launch_gather_grad(c, c->xk, c->dscal + 2)) != MLS_OK) return r;
+      if ((r = launch_assemble(c, c->xk)) != MLS_OK) return r;
+      if ((r = launch_coarse<VT>(b, s0)) != MLS_OK) return r;
+    }
     // Newton loop: entered with its condition at 1 on every launch
     cudaGraphConditionalHandle hn, hp, hl;
     if ((r = make_handle(b, s0, true, &hn)) != MLS_OK) return r;
@@ -897,24 +1358,25 @@ mls_status capture_step(mls_batch* b, double dt) {
     if ((r = launch_gather_grad(c, c->xk, c->dscal + 2)) != MLS_OK) return r;
     if ((r = launch_assemble(c, c->xk)) != MLS_OK) return r;
     if ((r = launch_prep<VT>(b, s1, P)) != MLS_OK) return r;
+    if (b->two_level && (r = launch_cycle<VT, MT>(b, s1, 1)) != MLS_OK) return r;
     // PCG loop
     if ((r = make_handle(b, s1, false, &hp)) != MLS_OK) return r;
-    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 0, P.max_newton, hp, 1, nullptr, trips + 3);
+    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 0, P.max_newton, hp, 1, nullptr, trips + 3, cap_entry);
     if ((r = begin_while(b, s1, s2, hp)) != MLS_OK) return r;
     if ((r = launch_pcg_iter<VT, MT>(b, s2)) != MLS_OK) return r;
     if ((r = launch_pcg_iter<VT, MT>(b, s2)) != MLS_OK) return r;
-    k_bcond<<<1, 256, 0, s2>>>(b->nmesh, b->M, 0, P.max_newton, hp, 1, nullptr, trips + 0);
+    k_bcond<<<1, 256, 0, s2>>>(b->nmesh, b->M, 0, P.max_newton, hp, 1, nullptr, trips + 0, cap_pcg);
     if ((r = end_body(b, s2)) != MLS_OK) return r;
     if ((r = launch_dir<VT>(b, s1, P)) != MLS_OK) return r;
     // line-search loop
     if ((r = make_handle(b, s1, false, &hl)) != MLS_OK) return r;
-    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 1, P.max_newton, hl, 1, nullptr, trips + 3);
+    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 1, P.max_newton, hl, 1, nullptr, trips + 3, cap_entry);
     if ((r = begin_while(b, s1, s2, hl)) != MLS_OK) return r;
     k_benergy<2><<<eb, kTetBlock, 0, s2>>>(V, EI, P, c->xk, c->dir);
     k_bapply<<<V.nrb, rt, 0, s2>>>(V, c->xk, c->dir);
-    k_bcond<<<1, 256, 0, s2>>>(b->nmesh, b->M, 1, P.max_newton, hl, 1, nullptr, trips + 1);
+    k_bcond<<<1, 256, 0, s2>>>(b->nmesh, b->M, 1, P.max_newton, hl, 1, nullptr, trips + 1, cap_ls);
     if ((r = end_body(b, s2)) != MLS_OK) return r;
-    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 2, P.max_newton, hn, 1, nullptr, trips + 2);
+    k_bcond<<<1, 256, 0, s1>>>(b->nmesh, b->M, 2, P.max_newton, hn, 1, nullptr, trips + 2, cap_newton);
     if ((r = end_body(b, s1)) != MLS_OK) return r;
     c->stream = s0;
     return bcheck(b, cudaGetLastError(), "capture launches");
@@ -937,12 +1399,15 @@ mls_status capture_step(mls_batch* b, double dt) {
     b->graph_dt = dt;
     b->graph_dirty = false;
     // kernels per body: Newton = element, gradient, assembly, PCG set-up,
-    // two loop-entry conditions, direction, Newton condition; PCG = two
-    // iterations of two kernels + condition; line search = energy, apply,
-    // condition.  Outside the loops: reset, predictor, two energies, select.
-    b->launches_fixed = 5;
-    b->launches_newton = 8;
-    b->launches_pcg = 5;
+    // two loop-entry conditions, direction, Newton condition (+ the first
+    // cycle of six kernels with two levels); PCG = two iterations of two
+    // kernels (+ six cycle kernels each) + condition; line search = energy,
+    // apply, condition.  Outside the loops: reset, predictor, two energies,
+    // select (+ element, gradient, assembly, three Galerkin kernels, the
+    // per-mesh Cholesky and inverse with two levels).
+    b->launches_fixed = b->two_level ? 5 + 3 + 3 + 2 : 5;
+    b->launches_newton = b->two_level ? 8 + 6 : 8;
+    b->launches_pcg = b->two_level ? 2 * 8 + 1 : 5;
     b->launches_ls = 3;
   }
   return st;
@@ -966,6 +1431,11 @@ mls_status autotune(mls_batch* b, double dt) {
   if ((st = launch_gather_grad(c, c->xk, c->dscal + 2)) != MLS_OK) { c->stream = saved; return st; }
   if ((st = launch_assemble(c, c->xk)) != MLS_OK) { c->stream = saved; return st; }
   (void)EI;
+  if (b->two_level) {
+    k_breset<<<(b->nmesh + 127) / 128, 128, 0, s>>>(b->nmesh, b->M);
+    if ((st = launch_coarse<VT>(b, s)) != MLS_OK) { c->stream = saved; return st; }
+    b->galerkin_warm = true;
+  }
   const BShape cands[] = {{4, 256, 1}, {4, 128, 1}, {4, 256, 2}, {4, 512, 1}, {8, 256, 1}, {8, 128, 1}, {8, 256, 2}};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
@@ -1017,8 +1487,21 @@ mls_status batch_step_t(mls_batch* b, const double* x, const double* v, double d
                                                   c->pn[0] * (c->po + 1e3), c->pn[1] * (c->po + 1e3),
                                                   c->pn[2] * (c->po + 1e3));
   if ((st = bcheck(b, cudaGetLastError(), "k_bpack")) != MLS_OK) { cudaEventDestroy(ev); return st; }
+  if (b->two_level && !b->has_basis) {
+    cudaEventDestroy(ev);
+    return bfail(b, MLS_EINVAL, "two-level batch: upload the per-mesh bases first");
+  }
   if (!b->tuned) {
     if ((st = autotune<VT, MT>(b, dt)) != MLS_OK) { cudaEventDestroy(ev); return st; }
+  }
+  if (b->two_level && !b->galerkin_warm) {
+    // first Galerkin product outside capture (it allocates its row table)
+    cudaStream_t saved = c->stream;
+    c->stream = b->cap;
+    st = build_galerkin(c);
+    c->stream = saved;
+    if (st != MLS_OK) { cudaEventDestroy(ev); return bfail(b, st, mls_last_error(c)); }
+    b->galerkin_warm = true;
   }
   if (b->graph_dirty || b->graph_dt != dt || !b->exec) {
     if ((st = capture_step<VT, MT>(b, dt)) != MLS_OK) { cudaEventDestroy(ev); return st; }
@@ -1045,11 +1528,12 @@ mls_status mls_batch_create(mls_batch** out, const mls_options* opt) {
   mls_options o;
   if (opt) o = *opt;
   else mls_default_options(&o);
-  if (o.preconditioner != MLS_PRECOND_BLOCK_JACOBI) return MLS_EINVAL;
+  if (o.preconditioner != MLS_PRECOND_BLOCK_JACOBI && o.preconditioner != MLS_PRECOND_TWO_LEVEL) return MLS_EINVAL;
   mls_batch* b = new (std::nothrow) mls_batch();
   if (!b) return MLS_ENOMEM;
   mls_status st = mls_create(&b->ctx, &o);
   if (st != MLS_OK) { delete b; return st; }
+  b->two_level = o.preconditioner == MLS_PRECOND_TWO_LEVEL;
   if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     mls_destroy(b->ctx);
@@ -1065,6 +1549,9 @@ mls_status mls_batch_destroy(mls_batch* b) {
   if (b->cap) cudaStreamSynchronize(b->cap);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   free_tables(b);
+  for (void* p : b->coarse_alloc) cudaFree(p);
+  if (b->W) cudaFree(b->W);
+  if (b->WT) cudaFree(b->WT);
   for (void* p : {(void*)b->vmap, (void*)b->bx, (void*)b->bv, (void*)b->M, (void*)b->trips, (void*)b->any,
                   (void*)b->mass_min, (void*)b->cnt, (void*)b->part_rb, (void*)b->part_sl, (void*)b->part_e})
     if (p) cudaFree(p);
@@ -1172,9 +1659,95 @@ mls_status mls_batch_upload(mls_batch* b, int32_t n_meshes, const int32_t* vert_
   b->h_toff.assign(tet_offsets, tet_offsets + n_meshes + 1);
   b->h_ioff = ioff;
   b->h_ipad = ipad;
+  b->h_vmap = vmap;
+  b->has_basis = false;
+  b->galerkin_warm = false;
   b->tuned = false;
   b->tune_ms = 0.0;
   if ((st = build_tables(b, BShape{})) != MLS_OK) return st;
+  return MLS_OK;
+}
+
+mls_status mls_batch_upload_basis(mls_batch* b, int32_t n_handles, const int32_t* handle_offsets,
+                                  const double* origins, const int32_t* vrow, const int32_t* handle,
+                                  const double* phi) {
+  if (!b) return MLS_EINVAL;
+  b->err.clear();
+  if (b->nmesh < 1) return bfail(b, MLS_EINVAL, "batch basis: upload the meshes first");
+  if (n_handles < 1 || !handle_offsets || !origins || !vrow || !handle || !phi)
+    return bfail(b, MLS_EINVAL, "batch basis: no handles or a null array");
+  const int B = b->nmesh;
+  if (handle_offsets[0] != 0 || handle_offsets[B] != n_handles)
+    return bfail(b, MLS_EINVAL, "batch basis: handle offsets must run from 0 to n_handles");
+  for (int m = 0; m < B; ++m) {
+    const int hm = handle_offsets[m + 1] - handle_offsets[m];
+    if (hm < 1 || 12 * hm > kMaxCoarseRows)
+      return bfail(b, MLS_EINVAL, "batch basis: mesh " + std::to_string(m) + " needs 1 to " +
+                                      std::to_string(kMaxCoarseRows / 12) + " handles");
+  }
+  const int nu = b->n_user;
+  if (vrow[0] != 0) return bfail(b, MLS_EINVAL, "batch basis: vrow must start at 0");
+  for (int u = 0; u < nu; ++u)
+    if (vrow[u + 1] < vrow[u]) return bfail(b, MLS_EINVAL, "batch basis: vrow must be non-decreasing");
+  // every vertex's handles belong to its own mesh
+  for (int m = 0; m < B; ++m)
+    for (int u = b->h_voff[m]; u < b->h_voff[m + 1]; ++u)
+      for (int k = vrow[u]; k < vrow[u + 1]; ++k)
+        if (handle[k] < handle_offsets[m] || handle[k] >= handle_offsets[m + 1])
+          return bfail(b, MLS_EINVAL, "batch basis: a vertex of mesh " + std::to_string(m) +
+                                          " references a handle of another mesh");
+  // internal (padded) vertex numbering
+  std::vector<int> ivrow(b->n + 1, 0), ih;
+  std::vector<double> iphi;
+  ih.reserve(vrow[nu]);
+  iphi.reserve(vrow[nu]);
+  for (int i = 0; i < b->n; ++i) {
+    const int u = b->h_vmap[i];
+    if (u >= 0)
+      for (int k = vrow[u]; k < vrow[u + 1]; ++k) { ih.push_back(handle[k]); iphi.push_back(phi[k]); }
+    ivrow[i + 1] = (int)ih.size();
+  }
+  mls_status st = mls_upload_basis(b->ctx, n_handles, origins, ivrow.data(), ih.data(), iphi.data());
+  if (st != MLS_OK) return bfail(b, st, std::string("batch basis: ") + mls_last_error(b->ctx));
+  // block-diagonal coarse layout
+  for (void* p : b->coarse_alloc) cudaFree(p);
+  b->coarse_alloc.clear();
+  if (b->W) { cudaFree(b->W); b->W = nullptr; }
+  if (b->WT) { cudaFree(b->WT); b->WT = nullptr; }
+  std::vector<int> coff(B), csz(B), crow(12 * n_handles), hmesh(n_handles);
+  std::vector<int64_t> woff(B);
+  int64_t wtot = 0;
+  for (int m = 0; m < B; ++m) {
+    coff[m] = 12 * handle_offsets[m];
+    csz[m] = 12 * (handle_offsets[m + 1] - handle_offsets[m]);
+    woff[m] = wtot;
+    wtot += (int64_t)csz[m] * csz[m];
+    for (int j = handle_offsets[m]; j < handle_offsets[m + 1]; ++j) hmesh[j] = m;
+    for (int g = coff[m]; g < coff[m] + csz[m]; ++g) crow[g] = m;
+  }
+  BCoarse& C = b->coarse;
+  C.r = 12 * n_handles;
+  int* p;
+  int64_t* q;
+  if ((st = bupload(b, b->coarse_alloc, &p, coff)) != MLS_OK) return st;
+  C.coff = p;
+  if ((st = bupload(b, b->coarse_alloc, &p, csz)) != MLS_OK) return st;
+  C.csz = p;
+  if ((st = bupload(b, b->coarse_alloc, &q, woff)) != MLS_OK) return st;
+  C.woff = q;
+  if ((st = bupload(b, b->coarse_alloc, &p, crow)) != MLS_OK) return st;
+  C.crow_mesh = p;
+  if ((st = bupload(b, b->coarse_alloc, &p, hmesh)) != MLS_OK) return st;
+  C.hmesh = p;
+  const size_t vb = b->ctx->opt.precision == MLS_FP64 ? sizeof(double) : sizeof(float);
+  if (cudaMalloc(&b->W, vb * wtot) != cudaSuccess || cudaMalloc(&b->WT, vb * wtot) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, MLS_ENOMEM, "batch basis: inverse factors");
+  }
+  b->has_basis = true;
+  b->galerkin_warm = false;
+  b->tuned = false;
+  b->graph_dirty = true;
   return MLS_OK;
 }
 

@@ -392,6 +392,7 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
 mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate);
 mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q);
 mls_status build_coarse(mls_ctx* ctx);
+mls_status build_galerkin(mls_ctx* ctx);   // U^T H U into the dense Ac only (no factorisation)
 mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out);
 mls_status warm_start_begin(mls_ctx* ctx, int* used);
 mls_status warm_start_first_iteration(mls_ctx* ctx);

@@ -917,6 +917,15 @@ mls_status dense_apply(mls_ctx* ctx, const void* W, const void* WT, int r, const
   return cuda_check(ctx, cudaGetLastError(), "dense apply");
 }
 
+mls_status build_galerkin(mls_ctx* ctx) {
+  if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
+  switch (ctx->opt.precision) {
+    case MLS_FP64: return galerkin_t<double, double>(ctx);
+    case MLS_MIXED_FP32: return galerkin_t<float, float>(ctx);
+    default: return galerkin_t<float, __nv_bfloat16>(ctx);
+  }
+}
+
 mls_status build_coarse(mls_ctx* ctx) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "assemble H before building the coarse operator");
