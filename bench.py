@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--coarse-refresh", type=int, default=1000,
                     help="rebuild U^T H U every k Newton iterations (>= the Newton count: once per step)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="plain FP64 steps timed for comparison")
+    ap.add_argument("--paper-steps", type=int, default=3,
+                    help="steps timed with the paper's inexact direction (20 CG refinement iterations, 1e-3 m/s)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end pass")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
@@ -447,6 +449,37 @@ def main():
         fp64_stats.append(st)
         v.copy_(dx / h)
         x.add_(dx)
+    # the paper's inexact direction (Alg. 1, Alg. 2) over the first steps of
+    # the same segment, and its error against the plain FP64 step
+    paper = None
+    if not args.profile_run and args.paper_steps > 0:
+        pap = mls.Solver(precision=args.precision, preconditioner="two_level", cycle=args.cycle, omega=args.omega,
+                         coarse_refresh=args.coarse_refresh, direction="paper", refine_iters=20, paper_tol=1e-3,
+                         stream=stream)
+        pap.setup_scene(scene)
+        pap.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+        xp, vp = x_s.clone(), v_s.clone()
+        dxp, _ = pap.newton_step(x_s.clone(), v_s.clone(), h)
+        dx64, _ = fp64.newton_step(x_s.clone(), v_s.clone(), h)
+        perr = float(torch.linalg.norm(dxp - dx64) / torch.linalg.norm(dx64))
+        pms, pst = [], []
+        for k in range(args.paper_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = pap.newton_step(xp, vp, h, dx=dx)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms.append(e0.elapsed_time(e1))
+            pst.append(st)
+            vp.copy_(dx / h)
+            xp.add_(dx)
+        paper = {"value": 1e3 / float(np.mean(pms)), "unit": UNIT, "ms_per_step": float(np.mean(pms)),
+                 "steps": len(pms), "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in pst])),
+                 "cg_iters_per_step": float(np.mean([s["pcg_iters"] for s in pst])),
+                 "disp_err_vs_fp64_first_step": perr,
+                 "settings": "subspace direction from the factored Galerkin operator + 20 block-Jacobi CG "
+                             "iterations; stop when sum_v |d_s,v| / (h n) < 1e-3 m/s"}
     # end to end through the host-pointer entry point, the timed segment again
     xh = x_s.cpu().numpy().copy()
     vh = v_s.cpu().numpy().copy()
@@ -513,6 +546,7 @@ def main():
         "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in stats])),
         "pcg_iters_per_step": pcg_total / args.steps,
         "disp_err_vs_fp64": disp_err,
+        "paper_direction": paper,
         "fp64_plain": {"value": 1e3 / float(np.mean(fp64_ms)) if fp64_ms else None, "unit": UNIT,
                        "ms_per_step": float(np.mean(fp64_ms)) if fp64_ms else None,
                        "steps": len(fp64_ms),

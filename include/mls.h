@@ -96,6 +96,18 @@ typedef struct mls_options {
                           kernel per solve; 0 (default): one launch per phase */
   int persist_blocks_per_sm; /* resident blocks per SM of the persistent kernel
                           (0: the library's choice; capped by occupancy) */
+  int direction;       /* 0 (default): each Newton direction solves H d = -g by PCG
+                          to the forcing tolerance, and Newton stops on the step
+                          test newton_tol.  1: the paper's inexact direction
+                          (Alg. 1, Alg. 2; two-level preconditioner required):
+                          d_s = U (U^T H U)^{-1} U^T (-g) from the factored
+                          Galerkin operator, plus refine_iters block-Jacobi CG
+                          iterations on H d_f = -g - H d_s from d_f = 0;
+                          Newton stops after the update when the mean vertex
+                          speed of the subspace step, sum_v |d_s,v|_2 /
+                          (h n_vertices), is below paper_tol (m/s, Sec. 3.9) */
+  int refine_iters;    /* direction 1: fixed full-space CG iterations (20-40) */
+  double paper_tol;    /* direction 1: subspace-decrement tolerance (1e-3) */
   void* stream;        /* cudaStream_t the context runs on (0 = legacy default) */
 } mls_options;
 
@@ -104,7 +116,8 @@ typedef struct mls_stats {
   int pcg_iters;           /* PCG iterations summed over the Newton iterations */
   int line_search_trials;  /* energy evaluations in the line search */
   int coarse_builds;       /* Galerkin builds + factorisations */
-  double step_rel;         /* final |d|_inf / max(|x - x^t|_inf, h^2 |g|) */
+  double step_rel;         /* final |d|_inf / max(|x - x^t|_inf, h^2 |g|); with the
+                              paper's direction, sum_v |d_s,v|_2 / (h n_vertices) */
   double grad_norm;        /* |g|_2 at the last evaluated iterate */
   double energy;           /* E at the returned iterate */
   int64_t kernel_launches; /* CUDA kernels this call launched */

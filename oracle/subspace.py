@@ -116,3 +116,26 @@ def two_level_apply(H, U, Ac, r, mode="multiplicative", omega=1.0, Dinv=None):
     if mode == "coarse":
         return Q(r)
     raise ValueError(mode)
+
+
+def paper_direction(H, g, U, n_cg):
+    """One direction of the paper's inexact Newton iteration (Alg. 1,
+    Alg. 2), with the two subspace levels solved exactly: the affine level
+    lies in span U (the SMS basis reproduces affine motions, Sec. 3.5), so
+    an exact solve in span U already contains it.
+
+        d_s = U (U^T H U)^{-1} U^T (-g)                 (subspace direction)
+        d_f = n_cg iterations of block-Jacobi PCG on H d_f = -g - H d_s,
+              started from d_f = 0                       (full-space refinement)
+
+    Returns (d_s, d_f) as flat arrays.  Test infrastructure only."""
+    from . import pcg as opcg
+    g = np.asarray(g, dtype=np.float64).ravel()
+    Ac = galerkin(H, U)
+    ds = U @ coarse_solve(Ac, U.T @ (-g))
+    r = -g - H @ ds
+    Dinv = block_diagonal_inverse(H)
+    # (stops early only at a relative residual of 1e-14, where a fixed
+    # iteration count has nothing left to do)
+    df, _ = opcg.pcg(lambda v: H @ v, r, lambda v: Dinv @ v, rtol=1e-14, max_iter=n_cg)
+    return np.asarray(ds).ravel(), df

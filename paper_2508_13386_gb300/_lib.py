@@ -37,6 +37,9 @@ class Options(C.Structure):
         ("pcg_check_every", C.c_int),
         ("persistent", C.c_int),
         ("persist_blocks_per_sm", C.c_int),
+        ("direction", C.c_int),
+        ("refine_iters", C.c_int),
+        ("paper_tol", C.c_double),
         ("stream", C.c_void_p),
     ]
 

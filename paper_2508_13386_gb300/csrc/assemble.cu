@@ -267,6 +267,17 @@ __global__ void k_from_solve(int n, const Vec4<VT>* __restrict__ src, const uint
   }
 }
 
+template <typename VT>
+__global__ void k_add_solve(int n, Vec4<VT>* __restrict__ y, const Vec4<VT>* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    Vec4<VT> a = y[i];
+    const Vec4<VT> b = x[i];
+    a.x += b.x; a.y += b.y; a.z += b.z;
+    y[i] = a;
+  }
+}
+
 // ---- launchers -----------------------------------------------------------------------
 static AsmIn asm_in(mls_ctx* ctx) {
   return AsmIn{ctx->n, ctx->t, ctx->mass, ctx->pinned, ctx->xtil, ctx->vt_ptr, ctx->vt_code, ctx->egrad,
@@ -344,6 +355,14 @@ mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double sca
   else
     { ++ctx->launches; k_to_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, (Vec4f*)dst, scale); }
   return cuda_check(ctx, cudaGetLastError(), "k_to_solve");
+}
+
+mls_status launch_add_solve(mls_ctx* ctx, void* y, const void* x) {
+  if (ctx->opt.precision == MLS_FP64)
+    { ++ctx->launches; k_add_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (Vec4d*)y, (const Vec4d*)x); }
+  else
+    { ++ctx->launches; k_add_solve<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (Vec4f*)y, (const Vec4f*)x); }
+  return cuda_check(ctx, cudaGetLastError(), "k_add_solve");
 }
 
 mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst) {

@@ -61,6 +61,27 @@ __global__ void __launch_bounds__(kBlock) k_dot4(int n, const Vec4d* __restrict_
   if (grid_sum<1>(acc, gr, RS_MISC) && threadIdx.x == 0) *out = acc[0];
 }
 
+static mls_status read_scalar(mls_ctx* ctx, const double* dev, double* host_out);
+
+// sum over vertices of |d_v|_2 (float64)
+__global__ void k_vnorm_sum(int n, const Vec4d* __restrict__ d, GridReduce gr, double* __restrict__ out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (v < n) {
+    const Vec4d a = d[v];
+    acc[0] = sqrt(a.x * a.x + a.y * a.y + a.z * a.z);
+  }
+  if (grid_sum<1>(acc, gr, RS_MISC) && threadIdx.x == 0) *out = acc[0];
+}
+
+static mls_status vnorm_sum(mls_ctx* ctx, const Vec4d* d, double* out) {
+  const int nb = (ctx->n + kBlock - 1) / kBlock;
+  { ++ctx->launches; k_vnorm_sum<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, d, ctx->red, ctx->dscal + 9); }
+  mls_status st = cuda_check(ctx, cudaGetLastError(), "k_vnorm_sum");
+  if (st != MLS_OK) return st;
+  return read_scalar(ctx, ctx->dscal + 9, out);
+}
+
 static mls_status dot4(mls_ctx* ctx, const Vec4d* a, const Vec4d* b, double* out) {
   const int nb = (ctx->n + kBlock - 1) / kBlock;
   { ++ctx->launches; k_dot4<<<nb, kBlock, 0, ctx->stream>>>(ctx->n, a, b, ctx->red, ctx->dscal + 8); }
@@ -149,6 +170,9 @@ mls_status mls_default_options(mls_options* opt) {
   opt->pcg_check_every = 16;
   opt->persistent = 0;
   opt->persist_blocks_per_sm = 0;
+  opt->direction = 0;
+  opt->refine_iters = 20;
+  opt->paper_tol = 1e-3;
   opt->stream = nullptr;
   return MLS_OK;
 }
@@ -161,6 +185,7 @@ static mls_status check_options(const mls_options* o) {
   if (!(o->omega > 0) || o->coarse_refresh < 0 || o->pcg_check_every < 1) return MLS_EINVAL;
   if (o->persistent < 0 || o->persistent > 1 || o->persist_blocks_per_sm < 0 || o->persist_blocks_per_sm > 32)
     return MLS_EINVAL;
+  if (o->direction < 0 || o->direction > 1 || o->refine_iters < 0 || !(o->paper_tol > 0)) return MLS_EINVAL;
   return MLS_OK;
 }
 
@@ -445,6 +470,40 @@ static mls_status assemble_at(mls_ctx* ctx, const Vec4d* x, double* gnorm) {
   return MLS_OK;
 }
 
+// The paper's inexact direction (Alg. 1, Alg. 2): the subspace direction
+// d_s = U (U^T H U)^{-1} U^T (-g) with the factored Galerkin operator (the
+// affine level adds nothing to an exact solve in span U, which contains the
+// affine motions), then refine_iters block-Jacobi CG iterations on
+// H d_f = -g - H d_s from d_f = 0 (Sec. 3.8: a fixed count of Jacobi-
+// preconditioned CG iterations).  Leaves d = d_s + d_f in vx (solve
+// precision) and returns sum_v |d_s,v|_2 and the CG iterations run.
+static mls_status paper_direction(mls_ctx* ctx, double* ds_norm, int* cg_iters) {
+  mls_status st;
+  if ((st = launch_restrict(ctx, ctx->vb, ctx->cvec)) != MLS_OK) return st;
+  if ((st = coarse_apply(ctx, ctx->cvec, ctx->cvec)) != MLS_OK) return st;
+  if ((st = launch_prolong(ctx, ctx->cvec, ctx->vw, false)) != MLS_OK) return st;
+  if ((st = launch_from_solve(ctx, ctx->vw, ctx->dir)) != MLS_OK) return st;
+  if ((st = vnorm_sum(ctx, ctx->dir, ds_norm)) != MLS_OK) return st;
+  // right-hand side of the refinement: vb = -g - H d_s (through vz2)
+  const size_t vbytes = (size_t)ctx->n * (ctx->opt.precision == MLS_FP64 ? sizeof(Vec4d) : sizeof(Vec4f));
+  if ((st = launch_residual(ctx, ctx->vb, ctx->vw, ctx->vz2, nullptr)) != MLS_OK) return st;
+  if ((st = cuda_check(ctx, cudaMemcpyAsync(ctx->vb, ctx->vz2, vbytes, cudaMemcpyDeviceToDevice, ctx->stream),
+                       "refinement rhs")) != MLS_OK)
+    return st;
+  const int pc = ctx->opt.preconditioner;
+  ctx->opt.preconditioner = MLS_PRECOND_BLOCK_JACOBI;
+  double rel = 0;
+  *cg_iters = 0;
+  if (ctx->opt.refine_iters > 0) {
+    st = pcg_solve(ctx, 0.0, ctx->opt.refine_iters, cg_iters, &rel);
+  } else {
+    st = cuda_check(ctx, cudaMemsetAsync(ctx->vx, 0, vbytes, ctx->stream), "zero d_f");
+  }
+  ctx->opt.preconditioner = pc;
+  if (st != MLS_OK && st != MLS_ENOTCONV) return st;
+  return launch_add_solve(ctx, ctx->vx, ctx->vw);
+}
+
 static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
   mls_stats S{};
   mls_status st;
@@ -465,6 +524,8 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
   }
   const bool two_level = ctx->opt.preconditioner == MLS_PRECOND_TWO_LEVEL;
   if (two_level && !ctx->has_basis) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_upload_basis");
+  const bool paper = ctx->opt.direction == 1;
+  if (paper && !two_level) return fail(ctx, MLS_EINVAL, "the paper's direction needs the two-level preconditioner");
   {
     int used = 0;
     if ((st = warm_start_begin(ctx, &used)) != MLS_OK) return st;
@@ -489,6 +550,37 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
       }
     }
     if (it == 0 && (st = warm_start_first_iteration(ctx)) != MLS_OK) return st;
+    if (paper) {
+      double ds_norm = 0;
+      int cg = 0;
+      if ((st = paper_direction(ctx, &ds_norm, &cg)) != MLS_OK) return st;
+      S.pcg_iters += cg;
+      if ((st = launch_from_solve(ctx, ctx->vx, ctx->dir)) != MLS_OK) return st;
+      double gd = 0;
+      if ((st = dot4(ctx, ctx->grad, ctx->dir, &gd)) != MLS_OK) return st;
+      if (!std::isfinite(gd)) return fail(ctx, MLS_ENONFINITE, "non-finite Newton direction");
+      if (!(gd < 0)) return fail(ctx, MLS_ELINESEARCH, "Newton direction is not a descent direction");
+      double alpha = 1.0;
+      if ((st = launch_ccd(ctx, ctx->xk, ctx->dir, &alpha)) != MLS_OK) return st;
+      double E0 = 0;
+      if ((st = launch_energy(ctx, ctx->xk, ctx->dir, 0.0, &E0, &infeasible)) != MLS_OK) return st;
+      bool accepted = false;
+      for (int hv = 0; hv <= kMaxHalvings; ++hv) {
+        if ((st = launch_energy(ctx, ctx->xk, ctx->dir, alpha, &E, &infeasible)) != MLS_OK) return st;
+        S.line_search_trials++;
+        if (!infeasible && (std::fabs(kArmijo * alpha * gd) <= kRoundingRegime * std::fabs(E0) ||
+                            E <= E0 + kArmijo * alpha * gd)) {
+          accepted = true;
+          break;
+        }
+        alpha *= 0.5;
+      }
+      if (!accepted) return fail(ctx, MLS_ELINESEARCH, "line search found no acceptable step");
+      if ((st = launch_axpy_state(ctx, ctx->xk, ctx->dir, alpha)) != MLS_OK) return st;
+      S.step_rel = ds_norm / (h * ctx->n);
+      if (S.step_rel < ctx->opt.paper_tol) { result = MLS_OK; break; }
+      continue;
+    }
     double eta = std::min(ctx->opt.pcg_rtol, std::sqrt(gnorm / g0));
     eta = std::max(eta, eta_floor);
     // absolute floor: H >= M, so |d - d*|_2 <= |r|_2 / m_min; a residual below

@@ -381,9 +381,11 @@ mls_status launch_disp_out(mls_ctx* ctx, double* dx_out);
 mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y);  // solve-precision vectors
 mls_status launch_spmv_values(mls_ctx* ctx, const void* values, const void* x, void* y);
 mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double scale);
-mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst);      // zero on Dirichlet vertices
+mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst);
+mls_status launch_add_solve(mls_ctx* ctx, void* y, const void* x);       // y += x, solve precision      // zero on Dirichlet vertices
 mls_status launch_from_solve_raw(mls_ctx* ctx, const void* src, Vec4d* dst);  // no masking
 mls_status pcg_solve(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res);
+mls_status launch_residual(mls_ctx* ctx, const void* b, const void* x, void* out, const PcgScalars* S);
 mls_status launch_persistent_pcg(mls_ctx* ctx, int cycle, int iters);
 mls_status precond_apply(mls_ctx* ctx, const void* r, void* z);
 

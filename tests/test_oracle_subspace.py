@@ -115,3 +115,30 @@ def test_multilevel_pcg_beats_jacobi_on_stiff_beam_slice():
                     lambda r: subspace.two_level_apply(H, U, Ac, r, omega=0.5, Dinv=Dinv), rtol=1e-8)
     assert ml["converged"] and jac["converged"]
     assert ml["iters"] < jac["iters"]
+
+
+def test_paper_direction_limits():
+    """Pins of the paper-direction oracle: with U spanning the whole space
+    the subspace direction is already the Newton direction and leaves no
+    residual to refine; with no refinement and a one-column-block
+    basis, d_s is the exact minimiser of the quadratic model in span U
+    (Galerkin orthogonality U^T (g + H d_s) = 0); with many refinement
+    iterations d_s + d_f is the Newton direction whatever U is."""
+    import scipy.sparse as sp
+    from oracle import subspace
+    rng = np.random.default_rng(3)
+    n3 = 36
+    A = rng.normal(size=(n3, n3))
+    H = sp.csr_matrix(A @ A.T + n3 * np.eye(n3))
+    g = rng.normal(size=n3)
+    d_newton = np.linalg.solve(H.toarray(), -g)
+    full = sp.csr_matrix(np.eye(n3))
+    ds, df = subspace.paper_direction(H, g, full, 0)
+    assert np.allclose(ds, d_newton, rtol=1e-10, atol=1e-12)
+    assert np.linalg.norm(-g - H @ ds) <= 1e-10 * np.linalg.norm(g)   # nothing left to refine
+    U = sp.csr_matrix(rng.normal(size=(n3, 12)))
+    ds, df = subspace.paper_direction(H, g, U, 0)
+    assert np.linalg.norm(df) == 0.0
+    assert np.linalg.norm(U.T @ (g + H @ ds)) <= 1e-10 * np.linalg.norm(U.T @ g)
+    ds, df = subspace.paper_direction(H, g, U, 200)
+    assert np.allclose(ds + df, d_newton, rtol=1e-8, atol=1e-10)
