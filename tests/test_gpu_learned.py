@@ -85,6 +85,22 @@ def test_warm_start_on_held_out_steps(beam_basis):
     print(f"held-out relative prediction error {pred_err:.3f}; warm start used {used}/30, "
           f"Newton {newton_p} -> {newton_w}, PCG {pcg_p} -> {pcg_w}, "
           f"time {res['plain_s']:.3f}s -> {res['warm_s']:.3f}s")
+    # the same network with the paper's inexact direction (20 CG iterations,
+    # stop on the subspace step), where the start carries more of the work
+    popts = dict(opts, direction="paper", refine_iters=20, paper_tol=1e-3)
+    pplain = solver_for(s, **popts)
+    pplain.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    pwarm = solver_for(s, **popts)
+    pwarm.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    pwarm.warm_start_enable(True)
+    pwarm.warm_start_attach(net)
+    pres = learned.evaluate(pplain, pwarm, s, n_steps=30, seed=40, device=device)
+    pn_p = sum(st["newton_iters"] for st in pres["plain"])
+    pn_w = sum(st["newton_iters"] for st in pres["warm"])
+    pused = sum(st["warm_start_used"] for st in pres["warm"])
+    print(f"paper direction: warm start used {pused}/30, Newton {pn_p} -> {pn_w}, CG "
+          f"{sum(st['pcg_iters'] for st in pres['plain'])} -> {sum(st['pcg_iters'] for st in pres['warm'])}, "
+          f"time {pres['plain_s']:.3f}s -> {pres['warm_s']:.3f}s, warm vs plain step {pres['max_rel_diff']:.3e}")
     # the network learned the coarse step: far better than the zero prediction
     assert pred_err < 0.5
     # the fallback keeps the solve no worse than the plain start (to within
