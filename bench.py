@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--coarse-refresh", type=int, default=1000,
                     help="rebuild U^T H U every k Newton iterations (>= the Newton count: once per step)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="plain FP64 steps timed for comparison")
+    ap.add_argument("--newton-tol", type=float, default=1e-5,
+                    help="Newton step tolerance of the mixed arm (the FP64 arm uses 1e-10)")
     ap.add_argument("--paper-steps", type=int, default=3,
                     help="steps timed with the paper's inexact direction (20 CG refinement iterations, 1e-3 m/s)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -341,7 +343,7 @@ def main():
 
     def make(precision, precond):
         s = mls.Solver(precision=precision, preconditioner=precond, cycle=args.cycle, omega=args.omega,
-                       newton_tol=1e-5 if precision != "fp64" else 1e-10,
+                       newton_tol=args.newton_tol if precision != "fp64" else 1e-10,
                        coarse_refresh=args.coarse_refresh, persistent=bool(args.persistent),
                        persist_blocks_per_sm=args.blocks_per_sm, stream=stream)
         s.setup_scene(scene)
@@ -539,6 +541,7 @@ def main():
                                f"implicit Euler h=1/60, dropped at 1 m/s from 0.05 m (timed steps {args.warmup}..)",
                    "solver": f"{args.precision} two-level PCG ({args.cycle}), SMS basis m={len(B['origins'])} "
                              f"(r={12 * len(B['origins'])}), coarse refresh every {args.coarse_refresh}, "
+                             f"Newton step tolerance {args.newton_tol:g}, "
                              + ("persistent PCG kernel" if args.persistent else "one launch per PCG phase"),
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -480,8 +480,8 @@ static mls_status assemble_at(mls_ctx* ctx, const Vec4d* x, double* gnorm) {
 static mls_status paper_direction(mls_ctx* ctx, double* ds_norm, int* cg_iters) {
   mls_status st;
   if ((st = launch_restrict(ctx, ctx->vb, ctx->cvec)) != MLS_OK) return st;
-  if ((st = coarse_apply(ctx, ctx->cvec, ctx->cvec)) != MLS_OK) return st;
-  if ((st = launch_prolong(ctx, ctx->cvec, ctx->vw, false)) != MLS_OK) return st;
+  if ((st = coarse_apply(ctx, ctx->cvec, ctx->cvec2)) != MLS_OK) return st;
+  if ((st = launch_prolong(ctx, ctx->cvec2, ctx->vw, false)) != MLS_OK) return st;
   if ((st = launch_from_solve(ctx, ctx->vw, ctx->dir)) != MLS_OK) return st;
   if ((st = vnorm_sum(ctx, ctx->dir, ds_norm)) != MLS_OK) return st;
   // right-hand side of the refinement: vb = -g - H d_s (through vz2)
@@ -706,7 +706,7 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
                    B.ent_ptr, B.ent_y, B.ent_v, B.ent_phi, B.ypair_row, B.chunk_ptr, B.chunk_beg, B.slot_row,
                    B.vcoef, B.hcoef, B.rchunk_handle, B.rchunk_beg, B.rchunk_ptr, B.rpart, B.rcount,
                    ctx->gpart, ctx->yval, ctx->Ac, ctx->Acopy,
-                   ctx->Linv, ctx->LinvT, ctx->cvec, ctx->cvec2, ctx->chol_info, ctx->chol_tinv,
+                   ctx->Linv, ctx->LinvT, ctx->Ainv, ctx->cvec, ctx->cvec2, ctx->chol_info, ctx->chol_tinv,
                    ctx->Am, ctx->Wm, ctx->WmT, ctx->ws_c, ctx->ws_c2, ctx->ws_tmp, ctx->ws_hist, ctx->ws_qg,
                    ctx->ws_qtilde, ctx->ws_qnext, ctx->ws_feat, ctx->ws_target, ctx->ws_pred, ctx->ws_hsave};
     for (void* p : old) dfree(ctx, p);

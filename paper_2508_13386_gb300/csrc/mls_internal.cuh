@@ -305,6 +305,7 @@ struct mls_ctx {
   double* Ac = nullptr;            // [r][r] float64 Galerkin operator, then its Cholesky factor
   void* Linv = nullptr;            // [r][r] W = L^{-1} in solve precision (lower)
   void* LinvT = nullptr;           // [r][r] W^T (upper)
+  void* Ainv = nullptr;            // [r][r] W^T W = (U^T H U)^{-1}, dense, solve precision
   double* Acopy = nullptr;         // [r][r] copy of the operator before factorisation
   void* yval = nullptr;            // [ny][36] H U blocks (solve precision)
   void* gpart = nullptr;           // [nchunk][144] Galerkin chunk partial sums

@@ -248,6 +248,7 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   if ((st = dalloc(ctx, (void**)&ctx->Acopy, (size_t)r * r * sizeof(double))) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->Linv, (size_t)r * r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->LinvT, (size_t)r * r * vb)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->Ainv, (size_t)r * r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->cvec, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->cvec2, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->chol_info, sizeof(int) * 4)) != MLS_OK) return st;
@@ -732,9 +733,62 @@ __global__ void k_transpose(const VT* __restrict__ W, int r, VT* __restrict__ WT
   }
 }
 
+// C = W^T W for lower-triangular W (r x r): the inverse of the coarse
+// operator, A^{-1} = L^{-T} L^{-1}.  64 x 64 output tiles (I, J), J <= I, each
+// also written mirrored; 256 threads, 4 x 4 outputs each; rows k of W below
+// the tile's first row I*64 are zero in column block I and skipped.
+constexpr int kGramTile = 64;
+template <typename VT>
+__global__ void __launch_bounds__(256) k_gram_lower(const VT* __restrict__ W, int r, VT* __restrict__ C) {
+  const int T = (r + kGramTile - 1) / kGramTile;
+  int idx = blockIdx.x, I = 0;
+  while (idx > I) { idx -= I + 1; ++I; }
+  const int J = idx;  // 0 <= J <= I < T
+  (void)T;
+  __shared__ VT As[16][kGramTile];
+  __shared__ VT Bs[16][kGramTile];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  VT acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = VT(0);
+  const int i0 = I * kGramTile, j0 = J * kGramTile;
+  for (int k0 = i0; k0 < r; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * kGramTile; e += 256) {
+      const int kk = e / kGramTile, c = e % kGramTile;
+      const int k = k0 + kk;
+      As[kk][c] = (k < r && i0 + c < r) ? W[(int64_t)k * r + i0 + c] : VT(0);
+      Bs[kk][c] = (k < r && j0 + c < r) ? W[(int64_t)k * r + j0 + c] : VT(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      VT a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { a[u] = As[kk][ty * 4 + u]; b[u] = Bs[kk][tx * 4 + u]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+      if (i < r && j < r) {
+        C[(int64_t)i * r + j] = acc[u][v];
+        C[(int64_t)j * r + i] = acc[u][v];
+      }
+    }
+}
+
 // y = W x restricted to the lower (lower = 1: columns <= row) or upper
 // (lower = 0: columns >= row) triangle, widened to 16-byte boundaries (W is
-// zero outside its triangle).  kTriWarps warps share a row (lane-strided
+// zero outside its triangle); lower = 2: the whole row (dense W).  kTriWarps warps share a row (lane-strided
 // 16-byte loads, so each warp has few loads to wait for) and combine their
 // sums through shared memory; a 256-thread block covers 8 / kTriWarps rows.
 constexpr int kTriWarps = 4;
@@ -754,7 +808,7 @@ __global__ void __launch_bounds__(kBlock) k_trigemv(const VT* __restrict__ W, in
   VT acc = VT(0);
   if (row < r) {
     const int v0 = lower ? 0 : row / EV;
-    const int v1 = lower ? (row + EV) / EV : r / EV;
+    const int v1 = lower == 1 ? (row + EV) / EV : r / EV;
     using V16 = typename std::conditional<sizeof(VT) == 4, float4, double2>::type;
     const V16* Wr = reinterpret_cast<const V16*>(W + (int64_t)row * r);
     const V16* xv = reinterpret_cast<const V16*>(x);
@@ -899,6 +953,11 @@ template <typename VT>
 static mls_status factor_t(mls_ctx* ctx) {
   const int r = 12 * ctx->basis.m;
   mls_status st = factor_dense_t<VT>(ctx, ctx->Ac, r, ctx->Acopy, ctx->Linv, ctx->LinvT);
+  if (st == MLS_OK) {
+    const int T = (r + kGramTile - 1) / kGramTile;
+    { ++ctx->launches; k_gram_lower<VT><<<T * (T + 1) / 2, 256, 0, ctx->stream>>>((const VT*)ctx->Linv, r, (VT*)ctx->Ainv); }
+    st = cuda_check(ctx, cudaGetLastError(), "k_gram_lower");
+  }
   ctx->coarse_ready = (st == MLS_OK);
   if (st == MLS_ECHOL) return fail(ctx, MLS_ECHOL, "coarse operator U^T H U: " + ctx->err);
   return st;
@@ -944,20 +1003,20 @@ mls_status build_coarse(mls_ctx* ctx) {
   return st;
 }
 
+// c_out = A^{-1} c_in with the dense inverse W^T W (one product; c_out must
+// not alias c_in)
 template <typename VT>
 static mls_status coarse_apply_t(mls_ctx* ctx, const VT* c_in, VT* c_out, const PcgScalars* S) {
   const int r = 12 * ctx->basis.m;
   const int nb = trigemv_blocks(r);
-  ctx->launches += 2;
-  mls_status st = cuda_check(ctx, launch_chained(k_trigemv<VT>, dim3(nb), dim3(kBlock), ctx->stream, (const VT*)ctx->Linv,
-                                                 r, 1, c_in, (VT*)ctx->cvec2, S), "k_trigemv");
-  if (st != MLS_OK) return st;
-  return cuda_check(ctx, launch_chained(k_trigemv<VT>, dim3(nb), dim3(kBlock), ctx->stream, (const VT*)ctx->LinvT, r, 0,
-                                        (const VT*)ctx->cvec2, c_out, S), "k_trigemv");
+  ++ctx->launches;
+  return cuda_check(ctx, launch_chained(k_trigemv<VT>, dim3(nb), dim3(kBlock), ctx->stream, (const VT*)ctx->Ainv, r, 2,
+                                        c_in, c_out, S), "coarse product");
 }
 
 mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out) {
   if (!ctx->coarse_ready) return fail(ctx, MLS_EINVAL, "coarse operator not built");
+  if (c_in == c_out) return fail(ctx, MLS_EINVAL, "coarse_apply: output must not alias the input");
   if (ctx->opt.precision == MLS_FP64) return coarse_apply_t<double>(ctx, (const double*)c_in, (double*)c_out, nullptr);
   return coarse_apply_t<float>(ctx, (const float*)c_in, (float*)c_out, nullptr);
 }
@@ -971,9 +1030,10 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   const VT* dinv = (const VT*)ctx->dinv;
   if (ctx->opt.cycle == MLS_CYCLE_ADDITIVE) {
     { ++ctx->launches; k_restrict<VT><<<restrict_blocks(ctx->basis.nrchunk), 32 * kRestrictWarps, 0, ctx->stream>>>(BV, r, c, S); }
-    mls_status st = coarse_apply_t<VT>(ctx, c, c, S);
+    VT* c2 = (VT*)ctx->cvec2;
+    mls_status st = coarse_apply_t<VT>(ctx, c, c2, S);
     if (st != MLS_OK) return st;
-    { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, nullptr, dinv, r, omega, z, S); }
+    { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c2, nullptr, dinv, r, omega, z, S); }
     return cuda_check(ctx, cudaGetLastError(), "two-level additive");
   }
   // multiplicative: z1 = S r; t = r - H z1; z2 = z1 + Q t; t = r - H z2; z = z2 + S t
@@ -982,8 +1042,8 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   if (st != MLS_OK) return st;
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
   { ++ctx->launches; k_restrict<VT><<<restrict_blocks(ctx->basis.nrchunk), 32 * kRestrictWarps, 0, ctx->stream>>>(BV, tmp, c, S); }
-  if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
-  { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c, z, nullptr, nullptr, omega, z, S); }
+  if ((st = coarse_apply_t<VT>(ctx, c, (VT*)ctx->cvec2, S)) != MLS_OK) return st;
+  { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, (const VT*)ctx->cvec2, z, nullptr, nullptr, omega, z, S); }
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
   { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, nullptr, z, dinv, tmp, omega, z, S); }
   return cuda_check(ctx, cudaGetLastError(), "two-level multiplicative");
@@ -1007,10 +1067,10 @@ static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1
     ++ctx->launches;
     if ((st = cuda_check(ctx, launch_chained(k_restrict<VT>, rgrid, rblock, ctx->stream, BV, r, c, S), "k_restrict")) != MLS_OK)
       return st;
-    if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
+    if ((st = coarse_apply_t<VT>(ctx, c, (VT*)ctx->cvec2, S)) != MLS_OK) return st;
     ++ctx->launches;
     return cuda_check(ctx, launch_chained(k_prolong_rz<VT>, dim3(nblk(ctx->n)), dim3(kBlock), ctx->stream, BV,
-                                          (const VT*)c, r, z1, first, ctx->red, S), "k_prolong_rz");
+                                          (const VT*)ctx->cvec2, r, z1, first, ctx->red, S), "k_prolong_rz");
   }
   Vec4<VT>* tmp = (Vec4<VT>*)ctx->vw;
   if ((st = launch_residual(ctx, r, z1, tmp, S)) != MLS_OK) return st;
@@ -1018,9 +1078,9 @@ static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1
   if ((st = cuda_check(ctx, launch_chained(k_restrict<VT>, rgrid, rblock, ctx->stream, BV, (const Vec4<VT>*)tmp, c, S),
                        "k_restrict")) != MLS_OK)
     return st;
-  if ((st = coarse_apply_t<VT>(ctx, c, c, S)) != MLS_OK) return st;
+  if ((st = coarse_apply_t<VT>(ctx, c, (VT*)ctx->cvec2, S)) != MLS_OK) return st;
   ++ctx->launches;
-  if ((st = cuda_check(ctx, launch_chained(k_prolong<VT>, dim3(nblk(ctx->n)), dim3(kBlock), ctx->stream, BV, (const VT*)c,
+  if ((st = cuda_check(ctx, launch_chained(k_prolong<VT>, dim3(nblk(ctx->n)), dim3(kBlock), ctx->stream, BV, (const VT*)ctx->cvec2,
                                            (const Vec4<VT>*)z1, (const VT*)nullptr, (const Vec4<VT>*)nullptr, VT(0), z1,
                                            S), "k_prolong")) != MLS_OK)
     return st;
