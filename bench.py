@@ -40,6 +40,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_2508_13386_gb300.replicas import lpt_shards, max_over_ranks  # noqa: E402
+
 # iteration counts of the FP64 block-Jacobi GPU path on this workload, used to
 # scale the oracle sample in the reference arm (the main arm measures them live)
 REF_NEWTON = 4
@@ -240,11 +242,20 @@ def run_batch(args):
     handles each) or block Jacobi, in the chosen precision; reported per
     whole batch."""
     import torch
+    import torch.distributed as dist
     import synth
     import paper_2508_13386_gb300 as mls
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
     scenes = synth.batched_lattice_scenes()
+    # several GPUs: each rank advances its share of the meshes (longest-
+    # processing-time by tet count), no exchange during a step
+    n_all, tets_all = len(scenes), sum(sc.n_tets for sc in scenes)
+    scenes = [scenes[i] for i in lpt_shards([sc.n_tets for sc in scenes], world)[rank]]
     for sc in scenes:
         sc.x0 = sc.x0 - np.array([0.0, 0.0, 0.0495])   # start just above the plane: contact from step 1
     basis_s = 0.0
@@ -274,6 +285,9 @@ def run_batch(args):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     infos, stats = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     with ClockSampler(dev.index) as clocks:
         for k in range(args.steps):
             flush.zero_()
@@ -286,11 +300,17 @@ def run_batch(args):
             x.add_(dx)
         torch.cuda.synchronize()
     total_s = sum(a.elapsed_time(c) for a, c in ev) / 1e3
-    tets = sum(sc.n_tets for sc in scenes)
+    total_s = max_over_ranks(total_s, dist if world > 1 else None, dev)
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return
+    tets = tets_all
     line = {
         "metric": "timesteps/s of a 64-mesh batch (every mesh advanced per step)", "value": args.steps / total_s,
-        "unit": "timesteps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "unit": "timesteps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32+f64", "bf16": "bf16+f32+f64", "fp64": "f64"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"64 seeded lattices, {tets} tets total (2K-60K each), E in {{1e5, 1e9}}, ground "
@@ -300,7 +320,7 @@ def run_batch(args):
                               if bases is not None else f"{args.precision} block-Jacobi PCG per mesh, ")
                              + "one graph launch per step",
                    "l2": "flushed (256 MB write) before every timed step"},
-        "mesh_steps_per_s": len(scenes) * args.steps / total_s,
+        "mesh_steps_per_s": n_all * args.steps / total_s,
         "newton_rounds_per_step": float(np.mean([i["newton_rounds"] for i in infos])),
         "pcg_rounds_per_step": float(np.mean([i["pcg_rounds"] for i in infos])),
         "pcg_iters_per_step_sum_over_meshes": float(np.mean([sum(m["pcg_iters"] for m in st) for st in stats])),
@@ -311,8 +331,12 @@ def run_batch(args):
                   "rows_per_thread": infos[-1]["rows_per_thread"], "tune_ms": infos[-1]["tune_ms"]},
         "clocks": clocks.summary(),
         "setup": {"basis_build_s": basis_s},
+        "sharding": f"{n_all} meshes over {world} GPU(s), longest-processing-time by tet count"
+                    if world > 1 else None,
     }
     print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
 
 
 def main():
@@ -421,10 +445,7 @@ def main():
     x.copy_(x_end)
     v.copy_(v_end)
     total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, dist if world > 1 else None, dev)
     value = world * args.steps / total_s
     # per kernel-class breakdown on one extra (untimed) step from the start state
     breakdown = None
