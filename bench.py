@@ -271,7 +271,7 @@ def run_batch(args):
         basis_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
     b = mls.Batch(precision=args.precision, preconditioner=args.batch_precond, omega=args.omega,
-                  newton_tol=1e-5 if args.precision != "fp64" else 1e-10, stream=stream)
+                  newton_tol=args.newton_tol if args.precision != "fp64" else 1e-10, stream=stream)
     b.upload_scenes(scenes)
     if bases is not None:
         b.upload_bases(bases)
@@ -320,7 +320,7 @@ def run_batch(args):
                    "solver": (f"{args.precision} two-level PCG per mesh (SMS bases, "
                               f"{sum(len(B['origins']) for B in bases)} handles in all, multiplicative cycle), "
                               if bases is not None else f"{args.precision} block-Jacobi PCG per mesh, ")
-                             + "one graph launch per step",
+                             + f"Newton step tolerance {args.newton_tol:g}, one graph launch per step",
                    "l2": "flushed (256 MB write) before every timed step"},
         "mesh_steps_per_s": n_all * args.steps / total_s,
         "newton_rounds_per_step": float(np.mean([i["newton_rounds"] for i in infos])),

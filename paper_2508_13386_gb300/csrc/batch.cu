@@ -697,8 +697,9 @@ __global__ void __launch_bounds__(256) k_bchol(BView V, BCoarse C, double* __res
 }
 
 // W_m = L_m^{-1} (lower triangular) by forward substitution, one column per
-// thread, in float64 (scratch S, same layout as A), then W and W^T in solve
-// precision (row-major csz x csz blocks at woff)
+// thread, in float64 (scratch S, same layout as A), stored in solve
+// precision in W; then the dense block inverse A_m^{-1} = W_m^T W_m into WT
+// (row-major csz x csz blocks at woff)
 template <typename VT>
 __global__ void __launch_bounds__(256) k_btrinv(BView V, BCoarse C, const double* __restrict__ A,
                                                 double* __restrict__ S, int ld, VT* __restrict__ W,
@@ -723,13 +724,23 @@ __global__ void __launch_bounds__(256) k_btrinv(BView V, BCoarse C, const double
       }
       w[(int64_t)i * ld + c] = v;
       Wm[(int64_t)i * n + c] = (VT)v;
-      WTm[(int64_t)c * n + i] = (VT)v;
     }
+  }
+  __syncthreads();
+  // the block's dense inverse A_m^{-1} = W_m^T W_m (solve precision, into WT):
+  // entry (i, j), j <= i, sums W[k][i] W[k][j] over k >= i; mirrored
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    if (j > i) continue;
+    VT acc = VT(0);
+    for (int k = i; k < n; ++k) acc += Wm[(int64_t)k * n + i] * Wm[(int64_t)k * n + j];
+    WTm[(int64_t)i * n + j] = acc;
+    WTm[(int64_t)j * n + i] = acc;
   }
 }
 
-// y = W x (lower = 1) or W^T x (lower = 0) per mesh block; four warps per
-// coarse row, 16-byte loads over the row's triangle
+// y = W x (lower = 1), W^T x (lower = 0) or, lower = 2, the dense block
+// product per mesh; four warps per coarse row, 16-byte loads
 template <typename VT>
 __global__ void __launch_bounds__(256) k_btrigemv(BView V, BCoarse C, const VT* __restrict__ W, int lower,
                                                   const VT* __restrict__ x, VT* __restrict__ y) {
@@ -749,7 +760,7 @@ __global__ void __launch_bounds__(256) k_btrigemv(BView V, BCoarse C, const VT* 
     if (on) {
       const int o = C.coff[m], n = C.csz[m], i = g - o;
       const int v0 = lower ? 0 : i / EV;
-      const int v1 = lower ? (i + EV) / EV : n / EV;
+      const int v1 = lower == 1 ? (i + EV) / EV : n / EV;
       using V16 = typename std::conditional<sizeof(VT) == 4, float4, double2>::type;
       const V16* Wr = reinterpret_cast<const V16*>(W + C.woff[m] + (int64_t)i * n);
       const V16* xv = reinterpret_cast<const V16*>(x + o);
@@ -1208,14 +1219,11 @@ mls_status launch_cycle(mls_batch* b, cudaStream_t s, int first) {
                                      (const Vec4<VT>*)c->vw, (VT*)c->cvec), "k_brestrict")) != MLS_OK)
     return st;
   const int rg = (b->coarse.r + 1) / 2;
-  if ((st = bcheck(b, launch_chained(k_btrigemv<VT>, dim3(rg), dim3(256), s, V, b->coarse, (const VT*)b->W, 1,
+  if ((st = bcheck(b, launch_chained(k_btrigemv<VT>, dim3(rg), dim3(256), s, V, b->coarse, (const VT*)b->WT, 2,
                                      (const VT*)c->cvec, (VT*)c->cvec2), "k_btrigemv")) != MLS_OK)
     return st;
-  if ((st = bcheck(b, launch_chained(k_btrigemv<VT>, dim3(rg), dim3(256), s, V, b->coarse, (const VT*)b->WT, 0,
-                                     (const VT*)c->cvec2, (VT*)c->cvec), "k_btrigemv")) != MLS_OK)
-    return st;
   if ((st = bcheck(b, launch_chained(k_bprolong<VT>, dim3(V.nrb), dim3(b->shape.row_threads), s, V, BB,
-                                     (const VT*)c->cvec, (Vec4<VT>*)c->vz), "k_bprolong")) != MLS_OK)
+                                     (const VT*)c->cvec2, (Vec4<VT>*)c->vz), "k_bprolong")) != MLS_OK)
     return st;
   return bcheck(b, launch_chained(k_bpost_smooth<VT, MT>, dim3(ns), dim3(128), s, V, first, (VT)c->opt.omega, c->n,
                                   (const int*)c->slice_ptr, (const int*)c->col, (const int*)c->row_len,
@@ -1400,14 +1408,14 @@ mls_status capture_step(mls_batch* b, double dt) {
     b->graph_dirty = false;
     // kernels per body: Newton = element, gradient, assembly, PCG set-up,
     // two loop-entry conditions, direction, Newton condition (+ the first
-    // cycle of six kernels with two levels); PCG = two iterations of two
-    // kernels (+ six cycle kernels each) + condition; line search = energy,
+    // cycle of five kernels with two levels); PCG = two iterations of two
+    // kernels (+ five cycle kernels each) + condition; line search = energy,
     // apply, condition.  Outside the loops: reset, predictor, two energies,
     // select (+ element, gradient, assembly, three Galerkin kernels, the
     // per-mesh Cholesky and inverse with two levels).
     b->launches_fixed = b->two_level ? 5 + 3 + 3 + 2 : 5;
-    b->launches_newton = b->two_level ? 8 + 6 : 8;
-    b->launches_pcg = b->two_level ? 2 * 8 + 1 : 5;
+    b->launches_newton = b->two_level ? 8 + 5 : 8;
+    b->launches_pcg = b->two_level ? 2 * 7 + 1 : 5;
     b->launches_ls = 3;
   }
   return st;
