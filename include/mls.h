@@ -430,6 +430,21 @@ mls_status mls_batch_retune(mls_batch* b);
 mls_status mls_batch_step(mls_batch* b, const double* x, const double* v, double dt, double* dx_out,
                           mls_batch_mesh_stats* stats, mls_batch_info* info);
 
+/* ---- Self-test of the bounded device wait -------------------------------
+ * The persistent PCG kernel separates its phases with a grid barrier whose
+ * wait is bounded: a block that polls more than a limit flags an error and
+ * the kernel returns (the solve reports MLS_ETIMEOUT) instead of hanging.
+ * This entry point exercises that path on its own: `blocks` co-resident
+ * blocks of 256 threads each arrive once at a barrier expecting `expected`
+ * arrivals, polling at most spin_limit times.  With expected <= blocks the
+ * barrier releases (MLS_OK, *gave_up = 0); with expected > blocks every
+ * block gives up (MLS_ETIMEOUT, *gave_up = blocks).  Allocates 128 bytes of
+ * device memory for the call; waits on `stream` (a cudaStream_t, NULL =
+ * legacy default).  MLS_EINVAL for non-positive arguments; MLS_ECUDA when
+ * the blocks cannot all be resident.  Not in the paper. */
+mls_status mls_selftest_barrier(int32_t blocks, int32_t expected, int32_t spin_limit, int32_t* gave_up,
+                                void* stream);
+
 /* ---- Allocation-free elastic energy ------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory while they run (a fixed memory budget, a

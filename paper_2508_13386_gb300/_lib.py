@@ -107,6 +107,7 @@ SIGNATURES = {
     "mls_warm_start_attach": [_P, _P],
     "mls_warm_start_sample": [_P, _P, _P],
     "mls_coarse_project": [_P, _P, _P],
+    "mls_selftest_barrier": [_I32, _I32, _I32, C.POINTER(_I32), _P],
     "mls_batch_create": [C.POINTER(_P), _P],
     "mls_batch_last_error": [_P],
     "mls_batch_destroy": [_P],

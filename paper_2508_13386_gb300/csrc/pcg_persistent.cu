@@ -32,7 +32,8 @@ struct GridBarrier {
   int error;
 };
 
-__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks) {
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks,
+                                             unsigned spin_limit = kBarrierSpinLimit) {
   __syncthreads();
   __shared__ int s_err;
   if (threadIdx.x == 0) {
@@ -46,7 +47,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, unsigned nblocks)
     } else {
       unsigned spins = 0;
       while (*vgen == g) {
-        if (++spins > kBarrierSpinLimit || *(volatile int*)&bar->error) {
+        if (++spins > spin_limit || *(volatile int*)&bar->error) {
           atomicExch(&bar->error, 1);
           break;
         }
@@ -503,6 +504,16 @@ static mls_status launch_persistent_t(mls_ctx* ctx, int cycle, int iters) {
   return cuda_check(ctx, e, "persistent PCG launch");
 }
 
+// Self-test of the bounded wait: every block arrives once at a barrier that
+// expects `expected` arrivals.  With expected > gridDim.x no release comes;
+// each waiting block gives up after spin_limit polls (or once another block
+// has flagged the error), counts itself in gave_up and returns, so the kernel
+// always ends.
+__global__ void k_barrier_probe(GridBarrier* bar, unsigned expected, unsigned spin_limit, int* gave_up) {
+  const bool ok = grid_barrier(bar, expected, spin_limit);
+  if (threadIdx.x == 0 && !ok) atomicAdd(gave_up, 1);
+}
+
 mls_status launch_persistent_pcg(mls_ctx* ctx, int cycle, int iters) {
   switch (ctx->opt.precision) {
     case MLS_FP64: return launch_persistent_t<double, double>(ctx, cycle, iters);
@@ -512,3 +523,30 @@ mls_status launch_persistent_pcg(mls_ctx* ctx, int cycle, int iters) {
 }
 
 }  // namespace mls
+
+extern "C" mls_status mls_selftest_barrier(int32_t blocks, int32_t expected, int32_t spin_limit, int32_t* gave_up,
+                                           void* stream) {
+  if (!gave_up || blocks < 1 || expected < 1 || spin_limit < 1) return MLS_EINVAL;
+  *gave_up = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, 128) != cudaSuccess) { cudaGetLastError(); return MLS_ENOMEM; }
+  GridBarrier* bar = (GridBarrier*)mem;
+  int* count = (int*)((char*)mem + 64);
+  mls_status st = MLS_OK;
+  if (cudaMemsetAsync(mem, 0, 128, s) != cudaSuccess) st = MLS_ECUDA;
+  unsigned ex = (unsigned)expected, sl = (unsigned)spin_limit;
+  void* args[] = {&bar, &ex, &sl, &count};
+  if (st == MLS_OK &&
+      cudaLaunchCooperativeKernel((void*)k_barrier_probe, dim3(blocks), dim3(kPersistThreads), args, 0, s) != cudaSuccess)
+    st = MLS_ECUDA;   // e.g. more blocks than can be co-resident
+  int host = 0;
+  if (st == MLS_OK && (cudaMemcpyAsync(&host, count, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                       cudaStreamSynchronize(s) != cudaSuccess))
+    st = MLS_ECUDA;
+  cudaGetLastError();
+  cudaFree(mem);
+  if (st != MLS_OK) return st;
+  *gave_up = host;
+  return host > 0 ? MLS_ETIMEOUT : MLS_OK;
+}

@@ -309,3 +309,24 @@ def test_invalid_inputs_rejected():
     x[:, 0] *= -1.0
     with pytest.raises(mls.MLSError, match="EINVERTED"):
         solver.newton_step(dev(x), dev(s.v0), s.dt)
+
+
+# ---- bounded device waits ---------------------------------------------------------------------
+def test_bounded_barrier_wait_gives_up_and_context_survives():
+    """The grid barrier of the persistent PCG kernel bounds its wait: with
+    one arrival more than there are blocks nothing releases it, every block
+    gives up after its poll limit and the call reports MLS_ETIMEOUT; with
+    the right count it releases.  The context stays usable afterwards."""
+    import ctypes as C
+    import paper_2508_13386_gb300 as mls
+    lib = mls._get_lib()
+    gave = C.c_int32(-1)
+    assert lib.mls_selftest_barrier(8, 9, 20000, C.byref(gave), None) == -8
+    assert gave.value == 8
+    assert lib.mls_selftest_barrier(8, 8, 20000, C.byref(gave), None) == 0
+    assert gave.value == 0
+    s = synth.tiny_scene(3, 2, 2, seed=4)
+    x_o, _ = newton.timestep(ip.Problem(s))
+    solver = solver_for(s, precision="fp64")
+    dx, st = solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    assert rel_disp_error(s.x0 + host(dx), x_o, s.x0) <= 1e-9
