@@ -313,7 +313,7 @@ struct mls_ctx {
   void* cvec2 = nullptr;
   bool coarse_ready = false;
   int* chol_info = nullptr;        // device: first non-positive pivot + 1, or 0
-  double* chol_tinv = nullptr;     // [32][32] inverse of the current diagonal factor tile
+  double* chol_tinv = nullptr;     // [tiles][32][32] inverses of the diagonal factor tiles
 
   // learned warm start (coarse projection with U^T M U, history, features)
   double* Am = nullptr;            // [r][r] U^T M U, factored in place

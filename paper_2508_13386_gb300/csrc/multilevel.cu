@@ -252,7 +252,8 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   if ((st = dalloc(ctx, &ctx->cvec, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->cvec2, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->chol_info, sizeof(int) * 4)) != MLS_OK) return st;
-  if ((st = dalloc(ctx, (void**)&ctx->chol_tinv, sizeof(double) * 32 * 32)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->chol_tinv, sizeof(double) * 32 * 32 * (size_t)((r + 31) / 32))) != MLS_OK)
+    return st;
   ctx->has_basis = true;
   ctx->coarse_ready = false;
   return MLS_OK;
@@ -561,48 +562,77 @@ __global__ void __launch_bounds__(144) k_galerkin_reduce(const int* __restrict__
 // ---- dense Cholesky (float64), blocked right-looking ---------------------------------------
 constexpr int NB = 32;
 
-// factor the diagonal tile (k, k) in place and write the inverse of its
-// lower-triangular factor to tinv (32 x 32, row-major); one CTA of 32x32 threads
+// 1/sqrt(d) for a positive float64 d: a float seed (rsqrtf) refined by two
+// Newton steps on f(y) = 1/y^2 - d, y <- y + y (1 - d y^2) / 2.  Each step
+// squares the relative error: the seed's ~2^-22 becomes ~2^-44 and then
+// falls below float64 rounding.  Outside the float range of the seed the
+// library's own 1/sqrt is taken.
+__device__ __forceinline__ double rsqrt_refined(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  const double hd = 0.5 * d;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = fma(y, fma(-hd * y, y, 0.5), y);
+  return y;
+}
+
+// pivot p of a diagonal tile: d = a_pp after the p earlier elimination
+// steps; records the first non-positive pivot in info and continues with 1
+__device__ __forceinline__ void tile_pivot(double d, int p, int base, int* __restrict__ info,
+                                           double* __restrict__ rd, double* __restrict__ rd2) {
+  if (!(d > 0.0)) {
+    if (*info == 0) *info = base + p + 1;
+    d = 1.0;
+  }
+  const double y = rsqrt_refined(d);
+  rd[p] = y;       // 1/sqrt(a_pp)
+  rd2[p] = y * y;  // 1/a_pp
+}
+
+// Factor the diagonal tile (k, k) in place (lower factor; upper part set to
+// 0) and write the inverse of that factor to tinv[k] (32 x 32, row-major).
+// Right-looking elimination on the unscaled tile: step p subtracts
+// m_ip * (row p) from every row i > p of the trailing part, m_ip = a_ip / a_pp,
+// and applies the same row operation to G (initially I).  Afterwards
+// A = Lt D Lt^T with unit lower Lt, G = Lt^{-1} and D the pivots, so
+// L = Lt D^{1/2} (L_ij = a_ij / sqrt(a_jj), the column scaled once at the
+// end) and L^{-1} = D^{-1/2} G.  The G update takes the lanes left of column
+// p that the trailing update leaves idle.  Thread (ty, tx) owns element
+// (ty, tx) of both; the thread that produces a_{p+1,p+1} computes the next
+// pivot at once, so each column costs one barrier.  One CTA of 32x32 threads.
 __global__ void k_potrf_tile(double* __restrict__ A, int r, int k, int* __restrict__ info,
                              double* __restrict__ tinv) {
   __shared__ double T[NB][NB + 1];
-  __shared__ double Ti[NB][NB + 1];
-  __shared__ double rd[NB];
+  __shared__ double G[NB][NB + 1];
+  __shared__ double rd[NB], rd2[NB];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int base = k * NB;
   const int nr = min(NB, r - base);
   T[ty][tx] = (ty < nr && tx < nr) ? A[(int64_t)(base + ty) * r + base + tx] : (ty == tx ? 1.0 : 0.0);
+  G[ty][tx] = (ty == tx) ? 1.0 : 0.0;
+  if (ty == 0) { rd[tx] = 1.0; rd2[tx] = 1.0; }  // rows past the matrix edge
+  __syncthreads();
+  if (tx == 0 && ty == 0) tile_pivot(T[0][0], 0, base, info, rd, rd2);
   __syncthreads();
   for (int p = 0; p < nr; ++p) {
-    if (tx == 0 && ty == 0) {
-      const double d = T[p][p];
-      if (!(d > 0.0)) {
-        if (*info == 0) *info = base + p + 1;
-        T[p][p] = 1.0;
+    if (ty > p) {
+      const double m = T[ty][p] * rd2[p];
+      if (tx > p) {
+        if (tx <= ty) {
+          const double v = fma(-m, T[tx][p], T[ty][tx]);
+          T[ty][tx] = v;
+          if (tx == p + 1 && ty == p + 1 && p + 1 < nr) tile_pivot(v, p + 1, base, info, rd, rd2);
+        }
+      } else if (tx < p) {
+        G[ty][tx] = fma(-m, G[p][tx], G[ty][tx]);
       } else {
-        T[p][p] = sqrt(d);
+        G[ty][p] = -m;
       }
-      rd[p] = 1.0 / T[p][p];
     }
     __syncthreads();
-    if (tx == 0 && ty > p && ty < nr) T[ty][p] *= rd[p];
-    __syncthreads();
-    if (ty > p && tx > p && tx <= ty && ty < nr) T[ty][tx] -= T[ty][p] * T[tx][p];
-    __syncthreads();
   }
-  if (ty < nr && tx < nr) A[(int64_t)(base + ty) * r + base + tx] = (tx <= ty) ? T[ty][tx] : 0.0;
-  // inverse of the factor: column j solved by forward substitution (lane j of warp 0)
-  if (ty == 0) {
-    const int j = tx;
-    for (int i = 0; i < NB; ++i) {
-      double v = (i == j) ? 1.0 : 0.0;
-      if (i >= nr) { Ti[i][j] = v; continue; }
-      for (int q = j; q < i; ++q) v -= T[i][q] * Ti[q][j];
-      Ti[i][j] = (i < j) ? 0.0 : v * rd[i];
-    }
-  }
-  __syncthreads();
-  tinv[ty * NB + tx] = Ti[ty][tx];
+  if (ty < nr && tx < nr) A[(int64_t)(base + ty) * r + base + tx] = (tx <= ty) ? T[ty][tx] * rd[tx] : 0.0;
+  tinv[(int64_t)k * NB * NB + ty * NB + tx] = (tx < ty) ? G[ty][tx] * rd[ty] : (tx == ty ? rd[ty] : 0.0);
 }
 
 // L_ik = A_ik L_kk^{-T} = A_ik (tinv)^T for tiles i > k; one CTA (32x32) per tile
@@ -613,7 +643,7 @@ __global__ void k_trsm_tiles(double* __restrict__ A, int r, int k, const double*
   const int i = k + 1 + blockIdx.x;
   const int bk = k * NB, bi = i * NB;
   const int nk = min(NB, r - bk), ni = min(NB, r - bi);
-  Li[ty][tx] = tinv[ty * NB + tx];
+  Li[ty][tx] = tinv[(int64_t)k * NB * NB + ty * NB + tx];
   X[ty][tx] = (ty < ni && tx < nk) ? A[(int64_t)(bi + ty) * r + bk + tx] : 0.0;
   __syncthreads();
   double s = 0.0;
@@ -656,35 +686,32 @@ __global__ void k_syrk_tiles(double* __restrict__ A, int r, int k, int ntiles) {
 }
 
 // W = L^{-1} by a right-looking blocked solve of L W = I over tile rows:
-// step i solves the tile row in place, W_ic = L_ii^{-1} B_ic for c <= i
-// (k_trinv_solve), then updates the rows below, B_qc -= L_qi W_ic for q > i,
-// c <= i (k_trinv_update).  W starts as the identity; its upper part stays 0.
+// step i solves the tile row in place, W_ic = L_ii^{-1} B_ic for c <= i, with
+// the diagonal tile's inverse from the factorisation (k_trinv_solve), then
+// updates the rows below, B_qc -= L_qi W_ic for q > i, c <= i
+// (k_trinv_update).  W starts as the identity; its upper part stays 0.
 template <typename VT>
 __global__ void k_eye(VT* __restrict__ W, int r) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < r) W[k * r + k] = VT(1);
 }
 
+// W_ic = tinv[i] B_ic for one column tile c <= i; one CTA of 32x32 threads
 template <typename VT>
-__global__ void k_trinv_solve(const double* __restrict__ L, int r, int i, VT* __restrict__ W) {
-  __shared__ VT Lii[NB][NB + 1];
+__global__ void k_trinv_solve(const double* __restrict__ tinv, int r, int i, VT* __restrict__ W) {
+  __shared__ VT Ti[NB][NB + 1];
   __shared__ VT X[NB][NB + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int c = blockIdx.x;  // column tile, c <= i
   const int bi = i * NB, bc = c * NB;
   const int ni = min(NB, r - bi), nc = min(NB, r - bc);
-  Lii[ty][tx] = (ty < ni && tx < ni) ? (VT)L[(int64_t)(bi + ty) * r + bi + tx] : (ty == tx ? VT(1) : VT(0));
+  Ti[ty][tx] = (VT)tinv[(int64_t)i * NB * NB + ty * NB + tx];
   X[ty][tx] = (ty < ni && tx < nc) ? W[(int64_t)(bi + ty) * r + bc + tx] : VT(0);
   __syncthreads();
-  if (ty == 0 && tx < nc) {
-    for (int rr = 0; rr < ni; ++rr) {
-      VT v = X[rr][tx];
-      for (int q = 0; q < rr; ++q) v -= Lii[rr][q] * X[q][tx];
-      X[rr][tx] = v / Lii[rr][rr];
-    }
-  }
-  __syncthreads();
-  if (ty < ni && tx < nc) W[(int64_t)(bi + ty) * r + bc + tx] = X[ty][tx];
+  VT v = VT(0);
+#pragma unroll 8
+  for (int q = 0; q <= ty; ++q) v += Ti[ty][q] * X[q][tx];
+  if (ty < ni && tx < nc) W[(int64_t)(bi + ty) * r + bc + tx] = v;
 }
 
 // B_qc -= L_qi W_ic for q in (i, nt), c in [0, i]; one CTA (32x8 threads,
@@ -925,7 +952,7 @@ static mls_status factor_dense_t(mls_ctx* ctx, double* A, int r, double* Acopy, 
   if (st != MLS_OK) return st;
   { ++ctx->launches; k_eye<VT><<<(r + 255) / 256, 256, 0, ctx->stream>>>((VT*)W, r); }
   for (int i = 0; i < nt; ++i) {
-    { ++ctx->launches; k_trinv_solve<VT><<<i + 1, dim3(NB, NB), 0, ctx->stream>>>(A, r, i, (VT*)W); }
+    { ++ctx->launches; k_trinv_solve<VT><<<i + 1, dim3(NB, NB), 0, ctx->stream>>>(ctx->chol_tinv, r, i, (VT*)W); }
     if (i + 1 < nt) {
       { ++ctx->launches; k_trinv_update<VT><<<(nt - i - 1) * (i + 1), dim3(32, 8), 0, ctx->stream>>>(A, r, i, nt, (VT*)W); }
     }

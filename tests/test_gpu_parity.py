@@ -279,6 +279,45 @@ def test_two_level_apply_matches_oracle(cycle):
     assert np.max(np.abs(z - z_o)) <= 1e-8 * np.abs(z_o).max()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 2e-3)])
+def test_two_level_apply_many_coarse_tiles(precision, tol):
+    """A 516 x 516 coarse operator (16 full 32 x 32 tiles of the blocked
+    Cholesky and a ragged 4-row one; condition number ~2e4 from E in
+    [1e5, 1e9]): the preconditioner apply through the factor and its inverse
+    matches the oracle's dense solve."""
+    s = synth.tiny_scene(12, 8, 6, seed=18, E_range=(1e5, 1e9), pinned=False)
+    p = ip.Problem(s)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=43, k=4, seed=6)
+    U = subspace.lbs_basis_matrix(s.X, origins, vrow, handle, phi)
+    solver = solver_for(s, precision=precision, preconditioner="two_level", cycle="multiplicative", omega=0.5)
+    solver.upload_basis(origins, vrow, handle, phi)
+    solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
+    solver.build_coarse()
+    H = p.hessian(p.x_tilde)
+    r = rng.normal(size=s.X.shape)
+    z = host(solver.precond_apply(dev(r)))
+    z_o = subspace.two_level_apply(H, U, subspace.galerkin(H, U), r.ravel(), mode="multiplicative",
+                                   omega=0.5).reshape(-1, 3)
+    assert np.max(np.abs(z - z_o)) <= tol * np.abs(z_o).max()
+
+
+def test_singular_coarse_operator_reported():
+    """A handle that no vertex uses makes U^T H U singular (12 zero rows):
+    the factorisation meets a zero pivot and the library reports
+    MLS_ECHOL (-6) instead of returning a factor."""
+    import paper_2508_13386_gb300 as mls
+    s = synth.tiny_scene(6, 4, 3, seed=19)
+    p = ip.Problem(s)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=7, k=3, seed=7)
+    origins = np.vstack([origins, s.X.mean(axis=0)])  # handle 7: no vertices
+    solver = solver_for(s, precision="fp64", preconditioner="two_level")
+    solver.upload_basis(origins, vrow, handle, phi)
+    solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
+    with pytest.raises(mls.MLSError) as e:
+        solver.build_coarse()
+    assert e.value.status == -6
+
+
 def test_two_level_timestep_fp64_beam_slice():
     s = synth.tiny_scene(8, 3, 3, seed=17, E_range=(1e5, 1e9))
     p = ip.Problem(s)
