@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--omega", type=float, default=0.5, help="block-Jacobi damping in the cycle")
     ap.add_argument("--coarse-refresh", type=int, default=1000,
                     help="rebuild U^T H U every k Newton iterations (>= the Newton count: once per step)")
+    ap.add_argument("--coarse-lag", type=int, default=3,
+                    help="timesteps a coarse factor may be reused at a step's first Newton iteration (0: rebuilt every step)")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="plain FP64 steps timed for comparison (the mixed step error is checked on each)")
     ap.add_argument("--newton-tol", type=float, default=1e-3,
@@ -371,7 +373,7 @@ def main():
         s = mls.Solver(precision=precision, preconditioner=precond, cycle=args.cycle, omega=args.omega,
                        newton_tol=args.newton_tol if precision != "fp64" else 1e-10,
                        coarse_refresh=args.coarse_refresh, persistent=bool(args.persistent),
-                       persist_blocks_per_sm=args.blocks_per_sm, stream=stream)
+                       persist_blocks_per_sm=args.blocks_per_sm, stream=stream, coarse_lag_steps=args.coarse_lag)
         s.setup_scene(scene)
         if precond == "two_level":
             s.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
@@ -570,14 +572,16 @@ def main():
                                f"E log-uniform 1e5-1e8 (32 Voronoi cells), ground barrier dhat=1e-3 kappa=1e5, "
                                f"implicit Euler h=1/60, dropped at 1 m/s from 0.05 m (timed steps {args.warmup}..)",
                    "solver": f"{args.precision} two-level PCG ({args.cycle}), SMS basis m={len(B['origins'])} "
-                             f"(r={12 * len(B['origins'])}), coarse refresh every {args.coarse_refresh}, "
-                             f"Newton step tolerance {args.newton_tol:g}, "
+                             f"(r={12 * len(B['origins'])}), coarse refresh every {args.coarse_refresh}"
+                             + (f" and reused over {args.coarse_lag} further steps, " if args.coarse_lag else ", ")
+                             + f"Newton step tolerance {args.newton_tol:g}, "
                              + ("persistent PCG kernel" if args.persistent else "one launch per PCG phase"),
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "pcg_iters_per_s": pcg_total / total_s,
         "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in stats])),
         "pcg_iters_per_step": pcg_total / args.steps,
+        "coarse_builds_per_step": float(np.mean([s["coarse_builds"] for s in stats])),
         "disp_err_vs_fp64": disp_err,
         "disp_err_vs_fp64_steps": step_errs,
         "paper_direction": paper,

@@ -90,6 +90,14 @@ typedef struct mls_options {
   int max_pcg;         /* PCG iteration cap per Newton iteration */
   int coarse_refresh;  /* 0: rebuild U^T H U and its factor every Newton iteration;
                           k > 0: at the first iteration of a step and then every k */
+  int coarse_lag_steps; /* 0 (default): a step's first Newton iteration always
+                          rebuilds the coarse operator; s > 0: it keeps a factor
+                          built at most s steps earlier (a lagged preconditioner:
+                          PCG still solves the current Newton system; ignored
+                          with direction 1).  If that first solve takes more
+                          than 1.5 x + 8 the PCG iterations of the first
+                          solve of the first step after the last build, the
+                          factor is rebuilt at the next Newton iteration. */
   int pcg_check_every; /* PCG iterations launched between host convergence checks
                           (separate-kernel mode) */
   int persistent;      /* 1: run the PCG iterations in one cooperative persistent

@@ -53,14 +53,14 @@ class Solver:
     def __init__(self, precision="fp64", preconditioner="jacobi", cycle="additive", omega=1.0,
                  newton_tol=1e-10, pcg_rtol=1e-4, max_newton=50, max_pcg=20000,
                  coarse_refresh=0, pcg_check_every=16, persistent=False, persist_blocks_per_sm=0,
-                 direction="pcg", refine_iters=20, paper_tol=1e-3, stream=None):
+                 direction="pcg", refine_iters=20, paper_tol=1e-3, stream=None, coarse_lag_steps=0):
         self._l = _get_lib()
         self._ctx = C.c_void_p()
         self.opt = _lib.Options()
         self._l.mls_default_options(C.byref(self.opt))
         self._fill(precision, preconditioner, cycle, omega, newton_tol, pcg_rtol, max_newton, max_pcg,
                    coarse_refresh, pcg_check_every, persistent, persist_blocks_per_sm, direction, refine_iters,
-                   paper_tol, stream)
+                   paper_tol, stream, coarse_lag_steps)
         st = self._l.mls_create(C.byref(self._ctx), C.byref(self.opt))
         if st != _lib.MLS_OK:
             raise MLSError(st, "mls_create failed")
@@ -70,7 +70,7 @@ class Solver:
 
     def _fill(self, precision, preconditioner, cycle, omega, newton_tol, pcg_rtol, max_newton, max_pcg,
               coarse_refresh, pcg_check_every, persistent, persist_blocks_per_sm, direction, refine_iters,
-              paper_tol, stream):
+              paper_tol, stream, coarse_lag_steps=0):
         o = self.opt
         o.precision = _lib.PRECISION[precision]
         o.preconditioner = _lib.PRECOND[preconditioner]
@@ -81,6 +81,7 @@ class Solver:
         o.max_newton = int(max_newton)
         o.max_pcg = int(max_pcg)
         o.coarse_refresh = int(coarse_refresh)
+        o.coarse_lag_steps = int(coarse_lag_steps)
         o.pcg_check_every = int(pcg_check_every)
         o.persistent = 1 if persistent else 0
         o.persist_blocks_per_sm = int(persist_blocks_per_sm)
@@ -101,7 +102,8 @@ class Solver:
                    coarse_refresh=self.opt.coarse_refresh, pcg_check_every=self.opt.pcg_check_every,
                    persistent=bool(self.opt.persistent),
                    persist_blocks_per_sm=self.opt.persist_blocks_per_sm, direction=self.opt.direction,
-                   refine_iters=self.opt.refine_iters, paper_tol=self.opt.paper_tol, stream=self.opt.stream)
+                   refine_iters=self.opt.refine_iters, paper_tol=self.opt.paper_tol, stream=self.opt.stream,
+                   coarse_lag_steps=self.opt.coarse_lag_steps)
         cur.update(kw)
         self._fill(**cur)
         self._check(self._l.mls_set_options(self._ctx, C.byref(self.opt)))

@@ -34,6 +34,7 @@ class Options(C.Structure):
         ("max_newton", C.c_int),
         ("max_pcg", C.c_int),
         ("coarse_refresh", C.c_int),
+        ("coarse_lag_steps", C.c_int),
         ("pcg_check_every", C.c_int),
         ("persistent", C.c_int),
         ("persist_blocks_per_sm", C.c_int),

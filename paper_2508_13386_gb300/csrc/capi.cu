@@ -167,6 +167,7 @@ mls_status mls_default_options(mls_options* opt) {
   opt->max_newton = 50;
   opt->max_pcg = 20000;
   opt->coarse_refresh = 0;
+  opt->coarse_lag_steps = 0;
   opt->pcg_check_every = 16;
   opt->persistent = 0;
   opt->persist_blocks_per_sm = 0;
@@ -182,7 +183,8 @@ static mls_status check_options(const mls_options* o) {
   if (o->preconditioner < 0 || o->preconditioner > 1) return MLS_EINVAL;
   if (o->cycle < 0 || o->cycle > 1) return MLS_EINVAL;
   if (!(o->newton_tol > 0) || !(o->pcg_rtol > 0) || o->max_newton < 1 || o->max_pcg < 1) return MLS_EINVAL;
-  if (!(o->omega > 0) || o->coarse_refresh < 0 || o->pcg_check_every < 1) return MLS_EINVAL;
+  if (!(o->omega > 0) || o->coarse_refresh < 0 || o->coarse_lag_steps < 0 || o->pcg_check_every < 1)
+    return MLS_EINVAL;
   if (o->persistent < 0 || o->persistent > 1 || o->persist_blocks_per_sm < 0 || o->persist_blocks_per_sm > 32)
     return MLS_EINVAL;
   if (o->direction < 0 || o->direction > 1 || o->refine_iters < 0 || !(o->paper_tol > 0)) return MLS_EINVAL;
@@ -504,9 +506,15 @@ static mls_status paper_direction(mls_ctx* ctx, double* ds_norm, int* cg_iters) 
   return launch_add_solve(ctx, ctx->vx, ctx->vw);
 }
 
+// a lagged coarse factor is stale when the first PCG solve of a step takes
+// more than kLagStaleRatio x (iterations after the last build) + kLagStaleSlack
+constexpr double kLagStaleRatio = 1.5;
+constexpr int kLagStaleSlack = 8;
+
 static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
   mls_stats S{};
   mls_status st;
+  if (ctx->coarse_ready) ctx->coarse_age_steps++;
   const double h = ctx->h;
   const double gmag = std::sqrt(ctx->grav[0] * ctx->grav[0] + ctx->grav[1] * ctx->grav[1] + ctx->grav[2] * ctx->grav[2]);
   const double scale0 = h * h * std::max(gmag, 1e-30);
@@ -542,12 +550,19 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
     S.grad_norm = gnorm;
     S.newton_iters = it + 1;
     if (gnorm == 0.0) { S.step_rel = 0.0; result = MLS_OK; break; }
+    bool lagged_first = false;
     if (two_level) {
       const int k = ctx->opt.coarse_refresh;
-      if (k == 0 || it % k == 0 || !ctx->coarse_ready) {
+      bool rebuild = k == 0 || it % k == 0 || !ctx->coarse_ready || ctx->coarse_stale;
+      // a lagged factor only preconditions: the paper's direction solves with it
+      if (it == 0 && !paper && ctx->coarse_ready && !ctx->coarse_stale &&
+          ctx->coarse_age_steps <= ctx->opt.coarse_lag_steps)
+        rebuild = false;
+      if (rebuild) {
         if ((st = build_coarse(ctx)) != MLS_OK) return st;
         S.coarse_builds++;
       }
+      lagged_first = it == 0 && !rebuild;
     }
     if (it == 0 && (st = warm_start_first_iteration(ctx)) != MLS_OK) return st;
     if (paper) {
@@ -594,6 +609,17 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
     st = pcg_solve(ctx, eta, ctx->opt.max_pcg, &iters, &rel);
     S.pcg_iters += iters;
     if (st != MLS_OK && st != MLS_ENOTCONV) return st;
+    // quality of a lagged coarse factor: the first solve of a step against
+    // the first solve of a step after the last build; a much harder solve
+    // marks the factor stale, and the next Newton iteration rebuilds it
+    if (it == 0 && two_level) {
+      if (ctx->coarse_ref_pending) {
+        ctx->coarse_ref_iters = iters;
+        ctx->coarse_ref_pending = false;
+      } else if (lagged_first && iters > kLagStaleRatio * ctx->coarse_ref_iters + kLagStaleSlack) {
+        ctx->coarse_stale = true;
+      }
+    }
     if ((st = launch_from_solve(ctx, ctx->vx, ctx->dir)) != MLS_OK) return st;
     double dinf = 0, xdisp = 0;
     if ((st = launch_norms(ctx, ctx->dir, &dinf, &xdisp)) != MLS_OK) return st;

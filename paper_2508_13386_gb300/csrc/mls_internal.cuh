@@ -312,6 +312,10 @@ struct mls_ctx {
   void* cvec = nullptr;            // [r] coarse vectors (solve precision)
   void* cvec2 = nullptr;
   bool coarse_ready = false;
+  int coarse_age_steps = 0;       // timesteps begun since the coarse factor was built
+  int coarse_ref_iters = 0;       // PCG iterations of a step's first solve after that build
+  bool coarse_ref_pending = false; // the next step's first solve sets coarse_ref_iters
+  bool coarse_stale = false;      // a lagged factor slowed PCG down: rebuild next iteration
   int* chol_info = nullptr;        // device: first non-positive pivot + 1, or 0
   double* chol_tinv = nullptr;     // [tiles][32][32] inverses of the diagonal factor tiles
 

@@ -986,6 +986,9 @@ static mls_status factor_t(mls_ctx* ctx) {
     st = cuda_check(ctx, cudaGetLastError(), "k_gram_lower");
   }
   ctx->coarse_ready = (st == MLS_OK);
+  ctx->coarse_age_steps = 0;
+  ctx->coarse_stale = false;
+  ctx->coarse_ref_pending = true;
   if (st == MLS_ECHOL) return fail(ctx, MLS_ECHOL, "coarse operator U^T H U: " + ctx->err);
   return st;
 }

@@ -318,6 +318,29 @@ def test_singular_coarse_operator_reported():
     assert e.value.status == -6
 
 
+def test_lagged_coarse_factor_keeps_the_timestep():
+    """coarse_lag_steps = 2: a step's first Newton iteration reuses a coarse
+    factor built at most two steps earlier, so over four steps the factor is
+    built on steps 0 and 3 only.  The lagged factor only preconditions: each
+    step still matches the oracle's timestep from the same state."""
+    s = synth.tiny_scene(8, 3, 3, seed=21, E_range=(1e5, 1e9))
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=6, k=3, seed=5)
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", newton_tol=1e-10,
+                        coarse_refresh=1000, coarse_lag_steps=2)
+    solver.upload_basis(origins, vrow, handle, phi)
+    x, v = s.x0.copy(), s.v0.copy()
+    builds = []
+    for _ in range(4):
+        dx, st = solver.newton_step(dev(x), dev(v), s.dt)
+        builds.append(st["coarse_builds"])
+        x_o, _ = newton.timestep(ip.Problem(s, x_t=x, v_t=v))
+        x_new = x + host(dx)
+        assert rel_disp_error(x_new, x_o, x) <= 1e-9
+        v = (x_new - x) / s.dt
+        x = x_new
+    assert builds == [1, 0, 0, 1]
+
+
 def test_two_level_timestep_fp64_beam_slice():
     s = synth.tiny_scene(8, 3, 3, seed=17, E_range=(1e5, 1e9))
     p = ip.Problem(s)
