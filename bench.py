@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--handles", type=int, default=160)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--cycle", default="multiplicative", choices=["additive", "multiplicative"])
-    ap.add_argument("--omega", type=float, default=0.5, help="block-Jacobi damping in the cycle")
+    ap.add_argument("--omega", type=float, default=0.0,
+                    help="block-Jacobi damping in the cycle (0: 0.9 x 2 / the Lanczos estimate of lambda_max(D^-1 H))")
     ap.add_argument("--coarse-refresh", type=int, default=1000,
                     help="rebuild U^T H U every k Newton iterations (>= the Newton count: once per step)")
     ap.add_argument("--coarse-lag", type=int, default=3,
@@ -272,7 +273,7 @@ def run_batch(args):
             bases = pool.map(_sms_job, jobs)
         basis_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
-    b = mls.Batch(precision=args.precision, preconditioner=args.batch_precond, omega=args.omega,
+    b = mls.Batch(precision=args.precision, preconditioner=args.batch_precond, omega=args.omega if args.omega > 0 else 0.5,
                   newton_tol=args.newton_tol if args.precision != "fp64" else 1e-10, stream=stream)
     b.upload_scenes(scenes)
     if bases is not None:
@@ -571,7 +572,9 @@ def main():
         "config": {"workload": f"lattice{args.grid}^3 p=0.55 seed 3: {scene.n_tets} tets, {scene.n_verts} verts, "
                                f"E log-uniform 1e5-1e8 (32 Voronoi cells), ground barrier dhat=1e-3 kappa=1e5, "
                                f"implicit Euler h=1/60, dropped at 1 m/s from 0.05 m (timed steps {args.warmup}..)",
-                   "solver": f"{args.precision} two-level PCG ({args.cycle}), SMS basis m={len(B['origins'])} "
+                   "solver": f"{args.precision} two-level PCG ({args.cycle}, "
+                             + (f"omega {args.omega:g}), " if args.omega > 0 else "omega 0.9 x 2 / Lanczos lambda_max(D^-1 H)), ")
+                             + f"SMS basis m={len(B['origins'])} "
                              f"(r={12 * len(B['origins'])}), coarse refresh every {args.coarse_refresh}"
                              + (f" and reused over {args.coarse_lag} further steps, " if args.coarse_lag else ", ")
                              + f"Newton step tolerance {args.newton_tol:g}, "
@@ -582,6 +585,8 @@ def main():
         "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in stats])),
         "pcg_iters_per_step": pcg_total / args.steps,
         "coarse_builds_per_step": float(np.mean([s["coarse_builds"] for s in stats])),
+        "step_ms": [round(t, 3) for t in step_ms],
+        "smoother": dict(zip(("omega", "lambda_max_estimate"), ours.smoother_omega())),
         "disp_err_vs_fp64": disp_err,
         "disp_err_vs_fp64_steps": step_errs,
         "paper_direction": paper,

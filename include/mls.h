@@ -83,7 +83,13 @@ typedef struct mls_options {
   int precision;       /* MLS_FP64 | MLS_MIXED_FP32 | MLS_MIXED_BF16 */
   int preconditioner;  /* MLS_PRECOND_BLOCK_JACOBI | MLS_PRECOND_TWO_LEVEL */
   int cycle;           /* MLS_CYCLE_* (two-level only) */
-  double omega;        /* block-Jacobi damping in the two-level cycle */
+  double omega;        /* block-Jacobi damping in the two-level cycle; 0 chooses it at
+                          every coarse build: 0.9 x 2 / lambda, lambda the largest
+                          Ritz value of 20 Lanczos steps on D^-1 H (D the 3x3 block
+                          diagonal of H).  The symmetric cycle is positive
+                          definite only while omega lambda_max(D^-1 H) < 2; a PCG
+                          breakdown with the automatic choice retries the solve
+                          with omega x 0.8 (up to three times).  Not for batches. */
   double newton_tol;   /* stop when |d|_inf <= newton_tol * max(|x - x^t|_inf, h^2 |g|) */
   double pcg_rtol;     /* PCG stops at |r|_2 <= eta |b|_2, eta = min(pcg_rtol, forcing term) */
   int max_newton;      /* Newton iteration cap per timestep */
@@ -152,6 +158,18 @@ const char* mls_last_error(const mls_ctx* ctx);
 
 /* Change options after creation (same meaning as in mls_create). */
 mls_status mls_set_options(mls_ctx* ctx, const mls_options* opt);
+
+/* The block-Jacobi damping the two-level cycle applies now (*omega, HOST):
+ * opt.omega, or with opt.omega = 0 the choice made at the last coarse
+ * build, whose estimate of lambda_max(D^-1 H) goes to *lambda_max (HOST,
+ * nullable; 0 before any automatic choice). */
+mls_status mls_smoother_omega(mls_ctx* ctx, double* omega, double* lambda_max);
+
+/* Largest eigenvalue of the symmetric tridiagonal matrix with diagonal
+ * d[0..k-1] and off-diagonal e[0..k-2] (HOST arrays), by bisection on the
+ * Sturm count; the result bounds it from above to rounding.  NaN for k < 1
+ * or null arrays.  Used by the automatic damping; exported for testing. */
+double mls_tridiag_max_eig(const double* d, const double* e, int k);
 
 /* Upload the tet mesh and its materials (Sec. 3.1 discretisation; Sec. 4
  * material model).  All HOST pointers:

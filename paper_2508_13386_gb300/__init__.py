@@ -25,6 +25,15 @@ def _get_lib():
     return lib
 
 
+def tridiag_max_eig(d, e):
+    """Largest eigenvalue of the symmetric tridiagonal (d, e) by the library's
+    Sturm bisection (mls_tridiag_max_eig)."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    P = C.POINTER(C.c_double)
+    return float(_get_lib().mls_tridiag_max_eig(d.ctypes.data_as(P), e.ctypes.data_as(P), int(d.size)))
+
+
 class MLSError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{_lib.STATUS.get(status, status)}: {message}")
@@ -251,6 +260,12 @@ class Solver:
 
     def build_coarse(self):
         self._check(self._l.mls_build_coarse(self._ctx))
+
+    def smoother_omega(self):
+        """(omega, lambda_max estimate) of the two-level smoother; see mls_smoother_omega."""
+        om, lm = C.c_double(), C.c_double()
+        self._check(self._l.mls_smoother_omega(self._ctx, C.byref(om), C.byref(lm)))
+        return om.value, lm.value
 
     def get_coarse(self):
         r = 12 * self.m

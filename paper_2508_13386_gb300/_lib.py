@@ -73,6 +73,8 @@ SIGNATURES = {
     "mls_destroy": [_P],
     "mls_last_error": [_P],
     "mls_set_options": [_P, C.POINTER(Options)],
+    "mls_smoother_omega": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "mls_tridiag_max_eig": [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int],
     "mls_upload_mesh": [_P, _I32, _P, _I32, _P, _P, _P, _P, _P],
     "mls_upload_basis": [_P, _I32, _P, _P, _P, _P],
     "mls_set_forces": [_P, _P, _I, _P, _D, _D, _D],
@@ -158,5 +160,5 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = {"mls_last_error": C.c_char_p, "mls_batch_last_error": C.c_char_p,
-                      "mls_mlp_param_count": C.c_int64}.get(name, C.c_int)
+                      "mls_mlp_param_count": C.c_int64, "mls_tridiag_max_eig": C.c_double}.get(name, C.c_int)
     return lib

@@ -1537,6 +1537,7 @@ mls_status mls_batch_create(mls_batch** out, const mls_options* opt) {
   if (opt) o = *opt;
   else mls_default_options(&o);
   if (o.preconditioner != MLS_PRECOND_BLOCK_JACOBI && o.preconditioner != MLS_PRECOND_TWO_LEVEL) return MLS_EINVAL;
+  if (!(o.omega > 0.0)) return MLS_EINVAL;  // the automatic damping is a single-mesh option
   mls_batch* b = new (std::nothrow) mls_batch();
   if (!b) return MLS_ENOMEM;
   mls_status st = mls_create(&b->ctx, &o);

@@ -183,7 +183,7 @@ static mls_status check_options(const mls_options* o) {
   if (o->preconditioner < 0 || o->preconditioner > 1) return MLS_EINVAL;
   if (o->cycle < 0 || o->cycle > 1) return MLS_EINVAL;
   if (!(o->newton_tol > 0) || !(o->pcg_rtol > 0) || o->max_newton < 1 || o->max_pcg < 1) return MLS_EINVAL;
-  if (!(o->omega > 0) || o->coarse_refresh < 0 || o->coarse_lag_steps < 0 || o->pcg_check_every < 1)
+  if (!(o->omega >= 0.0) || o->coarse_refresh < 0 || o->coarse_lag_steps < 0 || o->pcg_check_every < 1)
     return MLS_EINVAL;
   if (o->persistent < 0 || o->persistent > 1 || o->persist_blocks_per_sm < 0 || o->persist_blocks_per_sm > 32)
     return MLS_EINVAL;
@@ -202,6 +202,7 @@ mls_status mls_create(mls_ctx** out, const mls_options* opt) {
   } else {
     mls_default_options(&ctx->opt);
   }
+  ctx->omega_eff = ctx->opt.omega > 0.0 ? ctx->opt.omega : 0.5;
   ctx->stream = (cudaStream_t)ctx->opt.stream;
   if (cudaGetDevice(&ctx->device) != cudaSuccess) { cudaGetLastError(); delete ctx; return MLS_ECUDA; }
   void* h = nullptr;
@@ -239,7 +240,20 @@ mls_status mls_set_options(mls_ctx* ctx, const mls_options* opt) {
   ctx->opt = *opt;
   ctx->stream = (cudaStream_t)opt->stream;
   ctx->coarse_ready = false;
+  ctx->omega_eff = opt->omega > 0.0 ? opt->omega : 0.5;
   return MLS_OK;
+}
+
+mls_status mls_smoother_omega(mls_ctx* ctx, double* omega, double* lambda_max) {
+  if (!ctx || !omega) return MLS_EINVAL;
+  *omega = ctx->omega_eff;
+  if (lambda_max) *lambda_max = ctx->omega_lmax;
+  return MLS_OK;
+}
+
+double mls_tridiag_max_eig(const double* d, const double* e, int k) {
+  if (!d || k < 1 || (k > 1 && !e)) return std::nan("");
+  return tridiag_max_eig(d, e, k);
 }
 
 mls_status mls_set_forces(mls_ctx* ctx, const double* gravity, int contact, const double* plane_n,
@@ -419,6 +433,36 @@ mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n, const double* X, int32_t t, 
 }  // extern "C"
 
 namespace mls {
+// number of eigenvalues of the symmetric tridiagonal (d, e) below x: the
+// negative pivots of the LDL^T factorisation of T - x I (Sturm sequence)
+static int sturm_below(const double* d, const double* e, int k, double x) {
+  int count = 0;
+  double q = 1.0;
+  for (int i = 0; i < k; ++i) {
+    q = (d[i] - x) - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++count;
+  }
+  return count;
+}
+
+double tridiag_max_eig(const double* d, const double* e, int k) {
+  double lo = INFINITY, hi = -INFINITY;  // Gershgorin interval
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  // largest eigenvalue: the infimum of {x : all k eigenvalues lie below x}
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(mid > lo && mid < hi)) break;
+    if (sturm_below(d, e, k, mid) == k) hi = mid;
+    else lo = mid;
+  }
+  return hi;
+}
+
 static mls_status alloc_state(mls_ctx* ctx) {
   const int n = ctx->n, t = ctx->t;
   mls_status st;
@@ -436,6 +480,10 @@ static mls_status alloc_state(mls_ctx* ctx) {
   for (void** b : sv)
     if ((st = dalloc(ctx, b, (size_t)vb * 4 * n)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->pcg, sizeof(PcgScalars))) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->lz, sizeof(double) * (2 * kLanczosSteps + 1))) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->pcg_fix, sizeof(unsigned long long) * kFixWords)) != MLS_OK) return st;
+  if ((st = cuda_check(ctx, cudaMemset(ctx->pcg_fix, 0, sizeof(unsigned long long) * kFixWords), "sum init")) != MLS_OK)
+    return st;
   if ((st = dalloc(ctx, (void**)&ctx->persist_part, sizeof(double) * 4 * kMaxPersistBlocks)) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->persist_bar, 64)) != MLS_OK) return st;
   if ((st = cuda_check(ctx, cudaMemset(ctx->persist_bar, 0, 64), "barrier init")) != MLS_OK) return st;
@@ -607,6 +655,13 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
     int iters = 0;
     double rel = 0;
     st = pcg_solve(ctx, eta, ctx->opt.max_pcg, &iters, &rel);
+    // automatic damping: a breakdown means omega lambda_max(D^{-1} H) reached 2
+    // since the estimate (taken at the last coarse build); retry with a smaller omega
+    for (int retry = 0; st == MLS_ENONFINITE && two_level && ctx->opt.omega == 0.0 && retry < 3; ++retry) {
+      S.pcg_iters += iters;
+      ctx->omega_eff *= 0.8;
+      st = pcg_solve(ctx, eta, ctx->opt.max_pcg, &iters, &rel);
+    }
     S.pcg_iters += iters;
     if (st != MLS_OK && st != MLS_ENOTCONV) return st;
     // quality of a lagged coarse factor: the first solve of a step against

@@ -175,11 +175,223 @@ __device__ __forceinline__ void atomic_min_nonneg(double* addr, double v) {
   atomicMin((unsigned long long*)addr, (unsigned long long)__double_as_longlong(v));
 }
 
-// PCG scalars kept on the device so iterations run without host round trips
+// PCG scalars kept on the device so iterations run without host round trips.
+// rzv/rrv hold r.z and r.r of iteration i in entry i & 1: the kernel that
+// opens iteration i writes entry i & 1 while the others read entry
+// (i - 1) & 1, the scale of the sums that iteration i produces.
 struct PcgScalars {
   double rz, pq, rr, bb, alpha, beta, tol2;
   int iter, max_iter, done;
+  double rzv[2], rrv[2];
 };
+
+// ---- order-independent sums for the PCG loop -------------------------------------------
+// A block's partial x joins a sum as the 128-bit integer round(x 2^(80-e)),
+// split into four 32-bit limbs that are added into four 64-bit accumulators
+// by fire-and-forget atomics.  Integer addition is associative, so the total
+// does not depend on the order in which blocks arrive, and no block waits:
+// there is no arrival counter, fence or final pass.  The consumer (a later
+// kernel) rebuilds the total from the limbs.  The exponent e comes from an
+// estimate of the sum's magnitude that producers and consumer read from the
+// same place (the value of the same quantity one iteration earlier): a block
+// partial up to 2^30 times the estimate fits (beyond that, or not finite, it
+// sets the slot's overflow word), and sums down to 2^-27 times the estimate
+// keep all 53 bits.  Each limb accumulates fewer than 2^16 terms below 2^33,
+// so no accumulator overflows.  The conversions work on the bit patterns
+// with integer instructions: one thread per block runs them, and float64
+// instructions issue slowly on this GPU.
+constexpr int kFixStride = 4;                  // words between limbs (32 bytes)
+constexpr int kFixSlotWords = 5 * kFixStride;  // four limbs + the overflow word
+enum { FX_PQ = 0, FX_RR, FX_RZ, FX_KINDS };
+constexpr int kFixWords = FX_KINDS * 2 * kFixSlotWords;  // two slots (parities) per kind
+
+__device__ __forceinline__ unsigned long long* fix_slot(unsigned long long* base, int kind, int parity) {
+  return base + (kind * 2 + parity) * kFixSlotWords;
+}
+
+// floor(log2 x) of a positive normal double below 2^997 (the scale of a
+// sum); 0 for anything else
+__device__ __forceinline__ int fix_exponent(double estimate) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(estimate);
+  const int E = (int)((b >> 52) & 0x7ff);
+  return ((b >> 63) || E == 0 || E >= 2020) ? 0 : E - 1023;
+}
+
+__device__ __forceinline__ void fix_add(unsigned long long* slot, double x, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0x7ff) {  // infinite or NaN
+    atomicOr(slot + 4 * kFixStride, 1ull);
+    return;
+  }
+  if (E == 0) return;  // zero or subnormal: below 2^-1022, under the last place of any scale used
+  const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  const int sh = E - 1075 + 80 - e;  // |x| 2^(80-e) = m 2^sh
+  unsigned __int128 y;
+  if (sh >= 0) {
+    if (sh > 57) {  // at or beyond 2^110
+      atomicOr(slot + 4 * kFixStride, 1ull);
+      return;
+    }
+    y = (unsigned __int128)m << sh;
+  } else {
+    const int k = -sh;
+    if (k > 54) return;  // below half of the last place
+    const unsigned long long q = m >> k, rem = m & ((1ull << k) - 1), half = 1ull << (k - 1);
+    y = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);  // nearest, ties to even
+  }
+  const bool neg = (b >> 63) != 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned long long l = (unsigned long long)(y >> (32 * k)) & 0xffffffffull;
+    if (l) atomicAdd(slot + k * kFixStride, neg ? 0ull - l : l);
+  }
+}
+
+// raw words of a slot, read through L2 (a later kernel than the producers)
+struct FixRaw {
+  unsigned long long w[5];
+};
+__device__ __forceinline__ FixRaw fix_load(const unsigned long long* slot) {
+  FixRaw r;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) r.w[k] = __ldcg(slot + k * kFixStride);
+  return r;
+}
+
+// the total held by a slot's words, rounded to the nearest double (ties to
+// even; outside the normal range 0 or infinity); bad is set if a producer
+// overflowed
+__device__ __forceinline__ double fix_value(const FixRaw& r, int e, bool& bad) {
+  bad = r.w[4] != 0ull;
+  unsigned __int128 u = 0;  // limbs are signed: sign-extend, add modulo 2^128
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u += (unsigned __int128)(__int128)(long long)r.w[k] << (32 * k);
+  const bool neg = (__int128)u < 0;
+  const unsigned __int128 M = neg ? (unsigned __int128)0 - u : u;
+  if (M == 0) return 0.0;
+  const unsigned long long hi = (unsigned long long)(M >> 64), lo = (unsigned long long)M;
+  const int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading bit
+  unsigned long long mant;
+  if (p > 52) {
+    const int k = p - 52;
+    mant = (unsigned long long)(M >> k);
+    const unsigned __int128 rem = M & ((((unsigned __int128)1) << k) - 1), half = ((unsigned __int128)1) << (k - 1);
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+  } else {
+    mant = (unsigned long long)M << (52 - p);
+  }
+  int field = p + e - 80 + 1023;
+  if (mant >> 53) {
+    mant >>= 1;
+    ++field;
+  }
+  const unsigned long long sign = neg ? (1ull << 63) : 0ull;
+  if (field <= 0) return __longlong_as_double((long long)sign);
+  if (field >= 2047) return __longlong_as_double((long long)(sign | (0x7ffull << 52)));
+  return __longlong_as_double((long long)(sign | ((unsigned long long)field << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+__device__ __forceinline__ void fix_clear(unsigned long long* slot) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) slot[k * kFixStride] = 0ull;
+}
+
+// double -> float, nearest with ties to even, by integer instructions
+// (outside the normal float range: 0 or infinity)
+__device__ __forceinline__ float dbl_to_flt(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const int E = (int)((b >> 52) & 0x7ff) - 1023;
+  if (E < -126) return __uint_as_float(sign);
+  if (E > 127) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned long long m = b & ((1ull << 52) - 1), rem = m & ((1ull << 29) - 1), half = 1ull << 28;
+  unsigned mant = (unsigned)(m >> 29);
+  unsigned fe = (unsigned)(E + 127);
+  if (rem > half || (rem == half && (mant & 1u))) ++mant;
+  if (mant >> 23) {
+    mant = 0;
+    ++fe;
+  }
+  if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | (fe << 23) | mant);
+}
+
+// tests on the bit patterns of doubles (no float64 instructions)
+__device__ __forceinline__ bool dbl_finite(double x) {
+  return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+__device__ __forceinline__ bool dbl_positive(double x) {  // > 0 and finite
+  const long long b = __double_as_longlong(x);
+  return b > 0 && dbl_finite(x);
+}
+// a <= b for non-negative finite doubles: their bit patterns order like the values
+__device__ __forceinline__ bool dbl_le_nonneg(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
+
+// a / b in the solve precision: float division for float vectors (float64
+// division issues slowly), float64 for float64 vectors
+template <typename VT>
+__device__ __forceinline__ VT ratio(double a, double b) {
+  if constexpr (sizeof(VT) == 4) return dbl_to_flt(a) / dbl_to_flt(b);
+  else return a / b;
+}
+
+// The state that opens PCG iteration i: r.z and r.r of the iterate, the
+// step beta_i = rz_i / rz_{i-1} (0 for i = 0) in the solve precision, and
+// the stopping decision (1 converged, 2 iteration cap, 3 breakdown or
+// non-finite value).
+template <typename VT>
+struct PcgHead {
+  double rz, rr;
+  VT beta;
+  int done;
+};
+struct PcgHeadRaw {
+  FixRaw rz, rr;
+};
+__device__ __forceinline__ PcgHeadRaw pcg_head_load(const unsigned long long* fix, int i) {
+  PcgHeadRaw raw;
+  raw.rz = fix_load(fix_slot(const_cast<unsigned long long*>(fix), FX_RZ, i & 1));
+  raw.rr = fix_load(fix_slot(const_cast<unsigned long long*>(fix), FX_RR, i & 1));
+  return raw;
+}
+template <typename VT>
+__device__ __forceinline__ PcgHead<VT> pcg_head(const PcgScalars* S, const PcgHeadRaw& raw, int i) {
+  PcgHead<VT> h;
+  bool bad = false;
+  if (i == 0) {
+    h.rz = S->rzv[0];
+    h.rr = S->rrv[0];
+    h.beta = VT(0);
+  } else {
+    const double rzp = S->rzv[(i - 1) & 1], rrp = S->rrv[(i - 1) & 1];
+    bool b1, b2;
+    h.rz = fix_value(raw.rz, fix_exponent(rzp), b1);
+    h.rr = fix_value(raw.rr, fix_exponent(rrp), b2);
+    h.beta = ratio<VT>(h.rz, rzp);
+    bad = b1 || b2;
+  }
+  h.done = 0;
+  if (bad || !dbl_finite(h.rr)) h.done = 3;
+  else if (dbl_le_nonneg(h.rr, S->tol2)) h.done = 1;
+  else if (!dbl_positive(h.rz)) h.done = 3;
+  else if (i >= S->max_iter) h.done = 2;
+  return h;
+}
+// written once per iteration (block 0 of the opening kernel): the state for
+// later kernels and the host, and the PQ slot of iteration i - 1 cleared
+template <typename VT>
+__device__ __forceinline__ void pcg_head_publish(PcgScalars* S, unsigned long long* fix, int i, const PcgHead<VT>& h) {
+  if (i > 0) {
+    S->rzv[i & 1] = h.rz;
+    S->rrv[i & 1] = h.rr;
+    fix_clear(fix_slot(fix, FX_PQ, (i - 1) & 1));
+  }
+  S->rz = h.rz;
+  S->rr = h.rr;
+  S->iter = i;
+  if (h.done) S->done = h.done;
+}
 
 // Reduction slots (one counter each)
 enum { RS_PCG_PQ = 0, RS_PCG_RR, RS_PCG_RZ, RS_ENERGY, RS_MISC, RS_GRAD, RS_COUNT };
@@ -282,7 +494,11 @@ struct mls_ctx {
   void* vq = nullptr;
   void* vw = nullptr;
   void* vz2 = nullptr;             // preconditioned residual of the multiplicative cycle
+  double omega_eff = 0.5;          // damping the two-level cycle applies (opt.omega or the automatic choice)
+  double omega_lmax = 0.0;         // the automatic choice's estimate of lambda_max(D^{-1} H)
+  double* lz = nullptr;            // device: Lanczos alpha[kLanczosSteps], beta[kLanczosSteps + 1]
   mls::PcgScalars* pcg = nullptr;  // device
+  unsigned long long* pcg_fix = nullptr;  // device: [kFixWords] order-independent PCG sums
   double* persist_part = nullptr;  // [kMaxPersistBlocks][4] persistent-PCG block partials
   void* persist_bar = nullptr;     // persistent-PCG grid barrier state
   int persist_blocks = 0;          // cooperative grid size (0 = not yet sized)
@@ -384,6 +600,10 @@ mls_status launch_unpack(mls_ctx* ctx, const Vec4d* src, double* dst);
 mls_status launch_disp_out(mls_ctx* ctx, double* dx_out);
 
 mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y);  // solve-precision vectors
+constexpr int kLanczosSteps = 20;  // Lanczos steps of the automatic smoother damping
+// largest eigenvalue of the symmetric tridiagonal matrix with diagonal d[0..k-1]
+// and off-diagonal e[0..k-2] (Sturm-count bisection), from above to rounding
+double tridiag_max_eig(const double* d, const double* e, int k);
 mls_status launch_spmv_values(mls_ctx* ctx, const void* values, const void* x, void* y);
 mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double scale);
 mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst);

@@ -339,11 +339,14 @@ __global__ void __launch_bounds__(kBlock) k_prolong(BasisView B, const VT* __res
   w[v] = Vec4<VT>{o0, o1, o2, VT(0)};
 }
 
-// z1 += U y in place, then r.z1 and beta (the end of the additive cycle)
+// z1 += U y in place, then r.z1 (the end of the additive cycle): inside the
+// loop (first = 0, iteration it) into the sum that opens iteration it + 1,
+// before it (first = 1) by a grid sum that sets rz_0
 template <typename VT>
 __global__ void __launch_bounds__(kBlock) k_prolong_rz(BasisView B, const VT* __restrict__ q,
                                                        const Vec4<VT>* __restrict__ r, Vec4<VT>* z, int first,
-                                                       GridReduce gr, PcgScalars* __restrict__ S) {
+                                                       int it, GridReduce gr, unsigned long long* __restrict__ fix,
+                                                       PcgScalars* __restrict__ S) {
   chain_wait();
   chain_release();
   if (S->done) return;
@@ -357,9 +360,16 @@ __global__ void __launch_bounds__(kBlock) k_prolong_rz(BasisView B, const VT* __
     z[v] = zo;
     acc[0] = (double)rv.x * zo.x + (double)rv.y * zo.y + (double)rv.z * zo.z;
   }
+  if (!first) {
+    __shared__ double sh[1][32];
+    block_sum<1>(acc, sh);
+    if (threadIdx.x == 0) fix_add(fix_slot(fix, FX_RZ, (it + 1) & 1), acc[0], fix_exponent(S->rzv[it & 1]));
+    return;
+  }
   if (grid_sum<1>(acc, gr, RS_PCG_RZ) && threadIdx.x == 0) {
-    S->beta = first ? 0.0 : acc[0] / S->rz;
+    S->beta = 0.0;
     S->rz = acc[0];
+    S->rzv[0] = acc[0];
     if (!(acc[0] > 0.0) || !isfinite(acc[0])) S->done = (S->rr <= S->tol2) ? 1 : 3;
   }
 }
@@ -1015,10 +1025,169 @@ mls_status build_galerkin(mls_ctx* ctx) {
   }
 }
 
+// ---- damping of the block-Jacobi smoother ------------------------------------------------
+// The symmetric two-level cycle (pre- and post-smoothing with omega D^{-1},
+// D the 3x3 block diagonal of H) is positive definite if and only if
+// omega lambda_max(D^{-1} H) < 2.  With omega = 0 the library takes
+// omega = kOmegaFrac * 2 / theta, theta the largest Ritz value of
+// kLanczosSteps Lanczos steps on C^T H C, where D^{-1} = C C^T per vertex:
+// C^T H C is symmetric and similar to D^{-1} H, and a Ritz value never
+// exceeds lambda_max, so kOmegaFrac is the margin to the limit.
+constexpr double kOmegaFrac = 0.9;
+
+// C with C C^T = D^{-1} (lower, row-major 3x3) from the stored D^{-1} block;
+// a non-positive pivot zeroes the rest of the factor
+template <typename VT>
+__device__ __forceinline__ void dinv_factor(const VT* __restrict__ A, VT (&C)[9]) {
+  const VT a00 = A[0], a10 = A[3], a11 = A[4], a20 = A[6], a21 = A[7], a22 = A[8];
+  const VT l00 = a00 > VT(0) ? sqrt(a00) : VT(0);
+  const VT l10 = l00 > VT(0) ? a10 / l00 : VT(0), l20 = l00 > VT(0) ? a20 / l00 : VT(0);
+  const VT d11 = a11 - l10 * l10;
+  const VT l11 = d11 > VT(0) ? sqrt(d11) : VT(0);
+  const VT l21 = l11 > VT(0) ? (a21 - l20 * l10) / l11 : VT(0);
+  const VT d22 = a22 - l20 * l20 - l21 * l21;
+  const VT l22 = d22 > VT(0) ? sqrt(d22) : VT(0);
+  C[0] = l00; C[1] = VT(0); C[2] = VT(0);
+  C[3] = l10; C[4] = l11; C[5] = VT(0);
+  C[6] = l20; C[7] = l21; C[8] = l22;
+}
+
+// starting vector: a fixed hash of the component index in [-1, 1]; |w|^2
+// into beta[0] (as its square root)
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_lz_seed(int n, Vec4<VT>* __restrict__ w, GridReduce gr,
+                                                    double* __restrict__ beta) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (v < n) {
+    VT c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      unsigned h = (unsigned)(3 * v + k) * 2654435761u;  // multiplicative hash, then xorshift mixing
+      h ^= h >> 16; h *= 2246822519u; h ^= h >> 13; h *= 3266489917u; h ^= h >> 16;
+      c[k] = VT((double)h * (2.0 / 4294967295.0) - 1.0);
+      acc[0] += (double)c[k] * c[k];
+    }
+    w[v] = Vec4<VT>{c[0], c[1], c[2], VT(0)};
+  }
+  if (grid_sum<1>(acc, gr, RS_MISC) && threadIdx.x == 0) beta[0] = sqrt(acc[0]);
+}
+
+// v = w / beta[j] (in place) and t = C v
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_lz_scale(int n, const VT* __restrict__ dinv, Vec4<VT>* __restrict__ wv,
+                                                     const double* __restrict__ beta, int j, Vec4<VT>* __restrict__ t) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const double b = beta[j];
+  const VT s = b > 0.0 ? VT(1.0 / b) : VT(0);
+  const Vec4<VT> x = wv[v];
+  const VT x0 = s * x.x, x1 = s * x.y, x2 = s * x.z;
+  wv[v] = Vec4<VT>{x0, x1, x2, VT(0)};
+  VT C[9];
+  dinv_factor<VT>(dinv + (int64_t)v * 9, C);
+  t[v] = Vec4<VT>{C[0] * x0, C[3] * x0 + C[4] * x1, C[6] * x0 + C[7] * x1 + C[8] * x2, VT(0)};
+}
+
+// alpha[j] = t . y  (= v^T C^T H C v)
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_lz_alpha(int n, const Vec4<VT>* __restrict__ t, const Vec4<VT>* __restrict__ y,
+                                                     GridReduce gr, double* __restrict__ alpha, int j) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (v < n) {
+    const Vec4<VT> a = t[v], b = y[v];
+    acc[0] = (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z;
+  }
+  if (grid_sum<1>(acc, gr, RS_MISC) && threadIdx.x == 0) alpha[j] = acc[0];
+}
+
+// w = C^T y - alpha[j] v - beta[j] v_prev, written over v_prev (j > 0; for
+// j = 0 the last term is absent); |w| into beta[j + 1]
+template <typename VT>
+__global__ void __launch_bounds__(kBlock) k_lz_residual(int n, const VT* __restrict__ dinv, const Vec4<VT>* __restrict__ y,
+                                                        const Vec4<VT>* __restrict__ vc, Vec4<VT>* __restrict__ vp,
+                                                        const double* __restrict__ alpha,
+                                                        const double* __restrict__ beta, int j, GridReduce gr,
+                                                        double* __restrict__ beta_out) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (v < n) {
+    VT C[9];
+    dinv_factor<VT>(dinv + (int64_t)v * 9, C);
+    const Vec4<VT> yy = y[v], x = vc[v];
+    const VT a = (VT)alpha[j], b = j > 0 ? (VT)beta[j] : VT(0);
+    const Vec4<VT> xp = j > 0 ? vp[v] : Vec4<VT>{VT(0), VT(0), VT(0), VT(0)};
+    const VT w0 = C[0] * yy.x + C[3] * yy.y + C[6] * yy.z - a * x.x - b * xp.x;
+    const VT w1 = C[4] * yy.y + C[7] * yy.z - a * x.y - b * xp.y;
+    const VT w2 = C[8] * yy.z - a * x.z - b * xp.z;
+    vp[v] = Vec4<VT>{w0, w1, w2, VT(0)};
+    acc[0] = (double)w0 * w0 + (double)w1 * w1 + (double)w2 * w2;
+  }
+  if (grid_sum<1>(acc, gr, RS_MISC) && threadIdx.x == 0) beta_out[j + 1] = sqrt(acc[0]);
+}
+
+template <typename VT>
+static mls_status lanczos_t(mls_ctx* ctx, double* alpha_h, double* beta_h) {
+  const int n = ctx->n;
+  const int nb = nblk(n);
+  const VT* dinv = (const VT*)ctx->dinv;
+  Vec4<VT>* buf[2] = {(Vec4<VT>*)ctx->vp, (Vec4<VT>*)ctx->vq};  // v_j and v_{j-1} / w, alternating
+  Vec4<VT>* t = (Vec4<VT>*)ctx->vw;
+  Vec4<VT>* y = (Vec4<VT>*)ctx->vz2;
+  double* alpha = ctx->lz;
+  double* beta = ctx->lz + kLanczosSteps;
+  { ++ctx->launches; k_lz_seed<VT><<<nb, kBlock, 0, ctx->stream>>>(n, buf[0], ctx->red, beta); }
+  int cur = 0;
+  for (int j = 0; j < kLanczosSteps; ++j) {
+    { ++ctx->launches; k_lz_scale<VT><<<nb, kBlock, 0, ctx->stream>>>(n, dinv, buf[cur], beta, j, t); }
+    mls_status st = launch_spmv(ctx, t, y);
+    if (st != MLS_OK) return st;
+    { ++ctx->launches; k_lz_alpha<VT><<<nb, kBlock, 0, ctx->stream>>>(n, t, y, ctx->red, alpha, j); }
+    { ++ctx->launches; k_lz_residual<VT><<<nb, kBlock, 0, ctx->stream>>>(n, dinv, y, buf[cur], buf[cur ^ 1], alpha,
+                                                                      beta, j, ctx->red, beta); }
+    cur ^= 1;
+  }
+  mls_status st = cuda_check(ctx, cudaGetLastError(), "lanczos");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemcpyAsync(alpha_h, alpha, sizeof(double) * kLanczosSteps, cudaMemcpyDeviceToHost, ctx->stream),
+                  "lanczos readback");
+  if (st != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemcpyAsync(beta_h, beta, sizeof(double) * (kLanczosSteps + 1), cudaMemcpyDeviceToHost,
+                                       ctx->stream), "lanczos readback");
+  if (st != MLS_OK) return st;
+  return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "lanczos sync");
+}
+
+// omega_eff from the Lanczos estimate (opt.omega = 0), else opt.omega
+static mls_status choose_omega(mls_ctx* ctx) {
+  if (ctx->opt.omega > 0.0) {
+    ctx->omega_eff = ctx->opt.omega;
+    return MLS_OK;
+  }
+  double a[kLanczosSteps], b[kLanczosSteps + 1];
+  mls_status st = ctx->opt.precision == MLS_FP64 ? lanczos_t<double>(ctx, a, b) : lanczos_t<float>(ctx, a, b);
+  if (st != MLS_OK) return st;
+  // b[0] normalises the start vector; T_k has diagonal a[0..k-1] and
+  // off-diagonal b[1..k-1].  Stop at an invariant subspace or a bad value.
+  int k = 0;
+  while (k < kLanczosSteps && std::isfinite(a[k]) && std::isfinite(b[k]) && b[k] > 0.0) {
+    ++k;
+    if (!(b[k] > 1e-12 * std::fabs(a[k - 1]))) break;
+  }
+  if (k == 0) return fail(ctx, MLS_ENONFINITE, "smoother damping: Lanczos estimate failed");
+  const double theta = tridiag_max_eig(a, b + 1, k);
+  if (!(theta > 0.0) || !std::isfinite(theta)) return fail(ctx, MLS_ENONFINITE, "smoother damping: bad estimate");
+  ctx->omega_lmax = theta;
+  ctx->omega_eff = std::min(1.0, kOmegaFrac * 2.0 / theta);
+  return MLS_OK;
+}
+
 mls_status build_coarse(mls_ctx* ctx) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "assemble H before building the coarse operator");
   mls_status st;
+  if ((st = choose_omega(ctx)) != MLS_OK) return st;
   int tk = prof_begin(ctx, MLS_PROF_GALERKIN);
   switch (ctx->opt.precision) {
     case MLS_FP64: st = galerkin_t<double, double>(ctx); break;
@@ -1054,7 +1223,7 @@ mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out) {
 template <typename VT>
 static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, const PcgScalars* S) {
   const BasisView BV = basis_view(ctx);
-  const VT omega = (VT)ctx->opt.omega;
+  const VT omega = (VT)ctx->omega_eff;
   const int m = ctx->basis.m;
   VT* c = (VT*)ctx->cvec;
   const VT* dinv = (const VT*)ctx->dinv;
@@ -1068,7 +1237,7 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   }
   // multiplicative: z1 = S r; t = r - H z1; z2 = z1 + Q t; t = r - H z2; z = z2 + S t
   Vec4<VT>* tmp = (Vec4<VT>*)ctx->vw;
-  mls_status st = launch_jacobi(ctx, r, z, ctx->opt.omega, S);
+  mls_status st = launch_jacobi(ctx, r, z, ctx->omega_eff, S);
   if (st != MLS_OK) return st;
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
   { ++ctx->launches; k_restrict<VT><<<restrict_blocks(ctx->basis.nrchunk), 32 * kRestrictWarps, 0, ctx->stream>>>(BV, tmp, c, S); }
@@ -1079,14 +1248,15 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   return cuda_check(ctx, cudaGetLastError(), "two-level multiplicative");
 }
 
-mls_status launch_post_smooth_rz(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, PcgScalars* S);
+mls_status launch_post_smooth_rz(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, int it,
+                                 PcgScalars* S);
 
 // One application of the two-level cycle inside PCG, with z1 = omega D^{-1} r
 // already in place: additive z = z1 + U A^{-1} U^T r; multiplicative
 // z2 = z1 + U A^{-1} U^T (r - H z1), zf = z2 + omega D^{-1} (r - H z2).  Ends
 // with r.zf and beta.
 template <typename VT>
-static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1, Vec4<VT>* zf, int first,
+static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1, Vec4<VT>* zf, int first, int it,
                                    PcgScalars* S) {
   const BasisView BV = basis_view(ctx);
   const int m = ctx->basis.m;
@@ -1100,7 +1270,8 @@ static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1
     if ((st = coarse_apply_t<VT>(ctx, c, (VT*)ctx->cvec2, S)) != MLS_OK) return st;
     ++ctx->launches;
     return cuda_check(ctx, launch_chained(k_prolong_rz<VT>, dim3(nblk(ctx->n)), dim3(kBlock), ctx->stream, BV,
-                                          (const VT*)ctx->cvec2, r, z1, first, ctx->red, S), "k_prolong_rz");
+                                          (const VT*)ctx->cvec2, r, z1, first, it, ctx->red, ctx->pcg_fix, S),
+                      "k_prolong_rz");
   }
   Vec4<VT>* tmp = (Vec4<VT>*)ctx->vw;
   if ((st = launch_residual(ctx, r, z1, tmp, S)) != MLS_OK) return st;
@@ -1114,13 +1285,13 @@ static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1
                                            (const Vec4<VT>*)z1, (const VT*)nullptr, (const Vec4<VT>*)nullptr, VT(0), z1,
                                            S), "k_prolong")) != MLS_OK)
     return st;
-  return launch_post_smooth_rz(ctx, r, z1, zf, first, S);
+  return launch_post_smooth_rz(ctx, r, z1, zf, first, it, S);
 }
 
-mls_status two_level_pcg_step(mls_ctx* ctx, const void* r, void* z1, void* zf, int first, PcgScalars* S) {
+mls_status two_level_pcg_step(mls_ctx* ctx, const void* r, void* z1, void* zf, int first, int it, PcgScalars* S) {
   if (ctx->opt.precision == MLS_FP64)
-    return two_level_step_t<double>(ctx, (const Vec4d*)r, (Vec4d*)z1, (Vec4d*)zf, first, S);
-  return two_level_step_t<float>(ctx, (const Vec4f*)r, (Vec4f*)z1, (Vec4f*)zf, first, S);
+    return two_level_step_t<double>(ctx, (const Vec4d*)r, (Vec4d*)z1, (Vec4d*)zf, first, it, S);
+  return two_level_step_t<float>(ctx, (const Vec4f*)r, (Vec4f*)z1, (Vec4f*)zf, first, it, S);
 }
 
 mls_status precond_apply_dev(mls_ctx* ctx, const void* r, void* z, const PcgScalars* S) {

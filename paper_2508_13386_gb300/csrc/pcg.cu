@@ -210,8 +210,11 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(int n, const Vec4<VT>* __re
                                                      Vec4<VT>* __restrict__ r, Vec4<VT>* __restrict__ z,
                                                      Vec4<VT>* __restrict__ p, Vec4<VT>* __restrict__ q,
                                                      const VT* __restrict__ dinv, int jacobi, double rtol,
-                                                     int max_iter, GridReduce gr, PcgScalars* __restrict__ S) {
+                                                     int max_iter, GridReduce gr, unsigned long long* __restrict__ fix,
+                                                     PcgScalars* __restrict__ S) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.x == 0)
+    for (int w = threadIdx.x; w < kFixWords; w += blockDim.x) fix[w] = 0ull;
   double acc[2] = {0.0, 0.0};  // b.b, r.z
   if (row < n) {
     const Vec4<VT> bv = b[row];
@@ -229,6 +232,8 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(int n, const Vec4<VT>* __re
     S->bb = acc[0];
     S->rr = acc[0];
     S->rz = acc[1];
+    S->rrv[0] = acc[0];
+    S->rzv[0] = acc[1];
     S->beta = 0.0;
     S->alpha = 0.0;
     S->pq = 0.0;
@@ -240,14 +245,17 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(int n, const Vec4<VT>* __re
 }
 
 // zout = z2 + omega D^{-1} (r - H z2) (the post-smoothing of the symmetric
-// two-level cycle), fused with r.zout and beta (0 on the first call)
+// two-level cycle), fused with r.zout.  Inside the loop (first = 0, iteration
+// it) r.zout goes to the order-independent sum that opens iteration it + 1;
+// on the application before the loop (first = 1) a grid sum sets rz_0.
 template <typename VT, typename MT>
 __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_post_smooth_rz(SellView A, const MT* __restrict__ val,
                                                                     const Vec4<VT>* __restrict__ r,
                                                                     const Vec4<VT>* __restrict__ z2,
                                                                     const VT* __restrict__ dinv, VT omega,
-                                                                    Vec4<VT>* __restrict__ zout, int first,
-                                                                    GridReduce gr, PcgScalars* __restrict__ S) {
+                                                                    Vec4<VT>* __restrict__ zout, int first, int it,
+                                                                    GridReduce gr, unsigned long long* __restrict__ fix,
+                                                                    PcgScalars* __restrict__ S) {
   QuadH<VT> hq;
   quad_load<VT, MT>(A, val, blockIdx.x, hq);
   chain_wait();
@@ -265,53 +273,61 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_post_smooth_rz(SellView 
     zout[row] = zo;
     acc[0] = (double)rv.x * zo.x + (double)rv.y * zo.y + (double)rv.z * zo.z;
   }
+  if (!first) {
+    __shared__ double sh[1][32];
+    block_sum<1>(acc, sh);
+    if (threadIdx.x == 0) fix_add(fix_slot(fix, FX_RZ, (it + 1) & 1), acc[0], fix_exponent(S->rzv[it & 1]));
+    return;
+  }
   if (grid_sum<1>(acc, gr, RS_PCG_RZ) && threadIdx.x == 0) {
-    S->beta = first ? 0.0 : acc[0] / S->rz;
+    S->beta = 0.0;
     S->rz = acc[0];
+    S->rzv[0] = acc[0];
     if (!(acc[0] > 0.0) || !isfinite(acc[0])) S->done = (S->rr <= S->tol2) ? 1 : 3;
   }
 }
 
-// r.z after a non-local preconditioner; sets beta (0 on the first call)
-template <typename VT>
-__global__ void __launch_bounds__(kBlock) k_pcg_rz(int n, const Vec4<VT>* __restrict__ r,
-                                                   const Vec4<VT>* __restrict__ z, int first, GridReduce gr,
-                                                   PcgScalars* __restrict__ S) {
-  if (S->done) return;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0.0};
-  if (row < n) {
-    const Vec4<VT> rv = r[row], zv = z[row];
-    acc[0] = (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z;
-  }
-  if (grid_sum<1>(acc, gr, RS_PCG_RZ) && threadIdx.x == 0) {
-    if (first) {
-      S->beta = 0.0;
-    } else {
-      S->beta = acc[0] / S->rz;
-    }
-    S->rz = acc[0];
-    if (!(acc[0] > 0.0) || !isfinite(acc[0])) S->done = (S->rr <= S->tol2) ? 1 : 3;
-  }
-}
-
-// w = H z; p = z + beta p; q = w + beta q; alpha = r.z / p.q
+// w = H z; p = z + beta p; q = w + beta q; p.q into the sum that k_pcg_update
+// reads.  Opens iteration it: every block rebuilds rz_it, rr_it and beta_it
+// from the sums of iteration it - 1 (the same words, so the same values) and
+// stops on convergence, the iteration cap or breakdown; block 0 publishes
+// them.
 template <typename VT, typename MT>
 __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_pcg_spmv(SellView A, const MT* __restrict__ val,
                                                               const Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p,
-                                                              Vec4<VT>* __restrict__ q, GridReduce gr,
+                                                              Vec4<VT>* __restrict__ q, int it,
+                                                              unsigned long long* __restrict__ fix,
                                                               PcgScalars* __restrict__ S) {
   QuadH<VT> hq;
   quad_load<VT, MT>(A, val, blockIdx.x, hq);
   chain_wait();
   chain_release();
-  if (S->done) return;
-  double acc[1] = {0.0};
+  // block 0 of this kernel may set S->done while other blocks start: one
+  // thread reads it for the whole block, so the block stays uniform
+  __shared__ VT s_beta;
+  __shared__ int s_done, s_e;
+  PcgHeadRaw raw;
+  if (threadIdx.x == 0) {
+    s_done = S->done;
+    raw = pcg_head_load(fix, it);
+  }
+  __syncthreads();
+  if (s_done) return;
   VT w[3];
   quad_finish<VT, MT>(A, val, hq, z, w);
+  if (threadIdx.x == 0) {
+    const PcgHead<VT> h = pcg_head<VT>(S, raw, it);
+    if (blockIdx.x == 0) pcg_head_publish<VT>(S, fix, it, h);
+    s_beta = h.beta;
+    s_done = h.done;
+    s_e = fix_exponent(h.rz);
+  }
+  __syncthreads();
+  if (s_done) return;
+  double acc[1] = {0.0};
   const int row = quad_row(blockIdx.x, A.n);
   if (row >= 0) {
-    const VT beta = (VT)S->beta;
+    const VT beta = s_beta;
     const Vec4<VT> zv = z[row], pv = p[row], qv = q[row];
     const Vec4<VT> pn{zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, VT(0)};
     const Vec4<VT> qn{w[0] + beta * qv.x, w[1] + beta * qv.y, w[2] + beta * qv.z, VT(0)};
@@ -319,37 +335,66 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_pcg_spmv(SellView A, con
     q[row] = qn;
     acc[0] = (double)pn.x * qn.x + (double)pn.y * qn.y + (double)pn.z * qn.z;
   }
-  if (grid_sum<1>(acc, gr, RS_PCG_PQ) && threadIdx.x == 0) {
-    S->pq = acc[0];
-    if (acc[0] > 0.0 && isfinite(acc[0])) {
-      S->alpha = S->rz / acc[0];
-    } else {
-      S->alpha = 0.0;
-      S->done = 3;  // breakdown: H or the preconditioner is not positive definite
-    }
-  }
+  __shared__ double sh[1][32];
+  block_sum<1>(acc, sh);
+  if (threadIdx.x == 0) fix_add(fix_slot(fix, FX_PQ, it & 1), acc[0], s_e);
+}
+
+// the opening decision of iteration it on its own (one thread), launched at
+// the end of each chunk of iterations before the host reads the scalars
+__global__ void k_pcg_check(int it, unsigned long long* __restrict__ fix, PcgScalars* __restrict__ S) {
+  chain_wait();
+  chain_release();
+  if (threadIdx.x != 0 || S->done) return;
+  const PcgHeadRaw raw = pcg_head_load(fix, it);
+  pcg_head_publish<double>(S, fix, it, pcg_head<double>(S, raw, it));
 }
 
 // x += alpha p; r -= alpha q; then by mode: 1 = block Jacobi z = D^{-1} r with
-// r.z and beta; 2 = the smoothing term z = omega D^{-1} r of a two-level cycle.
-// One row per thread in 128-thread blocks: twice the blocks of a 256-thread
-// launch, to spread the rows over more SMs.
+// r.z; 2 = the smoothing term z = omega D^{-1} r of a two-level cycle.  r.r
+// (and r.z in mode 1) go to the sums that open iteration it + 1; alpha =
+// rz_it / p.q from the sum of k_pcg_spmv.  Block 0 clears the RR and RZ slots
+// that k_pcg_spmv consumed.  One row per thread in 128-thread blocks: twice
+// the blocks of a 256-thread launch, to spread the rows over more SMs.
 constexpr int kUpdBlock = 128;
 template <typename VT>
 __global__ void __launch_bounds__(kUpdBlock) k_pcg_update(int n, Vec4<VT>* __restrict__ x, Vec4<VT>* __restrict__ r,
                                                        Vec4<VT>* __restrict__ z, const Vec4<VT>* __restrict__ p,
                                                        const Vec4<VT>* __restrict__ q, const VT* __restrict__ dinv,
-                                                       int jacobi, VT omega, GridReduce gr,
+                                                       int jacobi, VT omega, int it,
+                                                       unsigned long long* __restrict__ fix,
                                                        PcgScalars* __restrict__ S) {
   chain_wait();
   chain_release();
-  if (S->done) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  Vec4<VT> pv{}, qv{}, xv{}, rv{};
+  if (row < n) { pv = p[row]; qv = q[row]; xv = x[row]; rv = r[row]; }
+  __shared__ VT s_alpha;
+  __shared__ int s_go;
+  if (threadIdx.x == 0) {
+    int go = 0;
+    VT alpha = VT(0);
+    if (!S->done) {  // block 0 may set it on breakdown: read once per block
+      const double rz = S->rzv[it & 1];
+      bool bad;
+      const double pq = fix_value(fix_load(fix_slot(fix, FX_PQ, it & 1)), fix_exponent(rz), bad);
+      go = !bad && dbl_positive(pq);
+      if (go) alpha = ratio<VT>(rz, pq);
+      if (blockIdx.x == 0) {
+        S->pq = pq;
+        if (!go) S->done = 3;  // breakdown: H or the preconditioner is not positive definite
+        fix_clear(fix_slot(fix, FX_RR, it & 1));
+        fix_clear(fix_slot(fix, FX_RZ, it & 1));
+      }
+    }
+    s_go = go;
+    s_alpha = alpha;
+  }
+  __syncthreads();
+  if (!s_go) return;
   double acc[2] = {0.0, 0.0};  // r.r, r.z
   if (row < n) {
-    const VT alpha = (VT)S->alpha;
-    const Vec4<VT> pv = p[row], qv = q[row];
-    Vec4<VT> xv = x[row], rv = r[row];
+    const VT alpha = s_alpha;
     xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z;
     rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z;
     x[row] = xv;
@@ -363,16 +408,11 @@ __global__ void __launch_bounds__(kUpdBlock) k_pcg_update(int n, Vec4<VT>* __res
       z[row] = dinv_apply<VT>(dinv, row, rv, omega);
     }
   }
-  if (grid_sum<2>(acc, gr, RS_PCG_RR) && threadIdx.x == 0) {
-    S->rr = acc[0];
-    S->iter += 1;
-    if (jacobi == 1) {
-      S->beta = acc[1] / S->rz;
-      S->rz = acc[1];
-    }
-    if (!isfinite(acc[0])) S->done = 3;
-    else if (acc[0] <= S->tol2) S->done = 1;
-    else if (S->iter >= S->max_iter) S->done = 2;
+  __shared__ double sh[2][32];
+  block_sum<2>(acc, sh);
+  if (threadIdx.x == 0) {
+    fix_add(fix_slot(fix, FX_RR, (it + 1) & 1), acc[0], fix_exponent(S->rrv[it & 1]));
+    if (jacobi == 1) fix_add(fix_slot(fix, FX_RZ, (it + 1) & 1), acc[1], fix_exponent(S->rzv[it & 1]));
   }
 }
 
@@ -414,19 +454,22 @@ mls_status launch_residual(mls_ctx* ctx, const void* b, const void* x, void* out
 }
 
 template <typename VT, typename MT>
-static mls_status post_smooth_t(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, PcgScalars* S) {
+static mls_status post_smooth_t(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, int it,
+                                PcgScalars* S) {
   ++ctx->launches;
   return cuda_check(ctx, launch_chained(k_post_smooth_rz<VT, MT>, dim3(ctx->n_slices), dim3(32 * kSpmvWarps), ctx->stream,
                                         sell_view(ctx), (const MT*)ctx->hval, (const Vec4<VT>*)r, (const Vec4<VT>*)z2,
-                                        (const VT*)ctx->dinv, (VT)ctx->opt.omega, (Vec4<VT>*)zout, first, ctx->red, S),
+                                        (const VT*)ctx->dinv, (VT)ctx->omega_eff, (Vec4<VT>*)zout, first, it, ctx->red,
+                                        ctx->pcg_fix, S),
                     "k_post_smooth_rz");
 }
 
-mls_status launch_post_smooth_rz(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, PcgScalars* S) {
+mls_status launch_post_smooth_rz(mls_ctx* ctx, const void* r, const void* z2, void* zout, int first, int it,
+                                 PcgScalars* S) {
   switch (ctx->opt.precision) {
-    case MLS_FP64: return post_smooth_t<double, double>(ctx, r, z2, zout, first, S);
-    case MLS_MIXED_FP32: return post_smooth_t<float, float>(ctx, r, z2, zout, first, S);
-    default: return post_smooth_t<float, __nv_bfloat16>(ctx, r, z2, zout, first, S);
+    case MLS_FP64: return post_smooth_t<double, double>(ctx, r, z2, zout, first, it, S);
+    case MLS_MIXED_FP32: return post_smooth_t<float, float>(ctx, r, z2, zout, first, it, S);
+    default: return post_smooth_t<float, __nv_bfloat16>(ctx, r, z2, zout, first, it, S);
   }
 }
 
@@ -441,7 +484,7 @@ mls_status launch_jacobi(mls_ctx* ctx, const void* r, void* z, double omega, con
 }
 
 mls_status precond_apply_dev(mls_ctx* ctx, const void* r, void* z, const PcgScalars* S);
-mls_status two_level_pcg_step(mls_ctx* ctx, const void* r, void* z1, void* zfinal, int first, PcgScalars* S);
+mls_status two_level_pcg_step(mls_ctx* ctx, const void* r, void* z1, void* zfinal, int first, int it, PcgScalars* S);
 
 template <typename VT, typename MT>
 static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, double* rel_res) {
@@ -463,7 +506,7 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
   SellView A = sell_view(ctx);
   const MT* val = (const MT*)ctx->hval;
   { ++ctx->launches; k_pcg_init<VT><<<nb, kBlock, 0, ctx->stream>>>(n, b, x, r, z, p, q, dinv, jacobi ? 1 : 0, rtol, max_iter,
-                                                 ctx->red, S); }
+                                                 ctx->red, ctx->pcg_fix, S); }
   mls_status st = cuda_check(ctx, cudaGetLastError(), "k_pcg_init");
   if (st != MLS_OK) return st;
   // two-level: z1 (in vz) holds the smoothing term and then U-corrected
@@ -472,8 +515,8 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
   Vec4<VT>* z1 = z;
   Vec4<VT>* zf = (!jacobi && mult) ? (Vec4<VT>*)ctx->vz2 : z;
   if (!jacobi) {
-    if ((st = launch_jacobi(ctx, r, z1, ctx->opt.omega, S)) != MLS_OK) return st;
-    if ((st = two_level_pcg_step(ctx, r, z1, zf, 1, S)) != MLS_OK) return st;
+    if ((st = launch_jacobi(ctx, r, z1, ctx->omega_eff, S)) != MLS_OK) return st;
+    if ((st = two_level_pcg_step(ctx, r, z1, zf, 1, 0, S)) != MLS_OK) return st;
   }
   if (ctx->opt.persistent) {
     const int cycle = jacobi ? 0 : (mult ? 2 : 1);
@@ -491,28 +534,35 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
     }
   }
   const int chunk = ctx->opt.pcg_check_every > 0 ? ctx->opt.pcg_check_every : 16;
-  const VT omega = (VT)ctx->opt.omega;
+  const VT omega = (VT)ctx->omega_eff;
+  int it = 0;  // iteration index; its parity selects the sums' slots
   for (; !ctx->opt.persistent;) {
-    for (int c = 0; c < chunk; ++c) {
+    for (int c = 0; c < chunk; ++c, ++it) {
       int tk = prof_begin(ctx, MLS_PROF_SPMV);
       ++ctx->launches;
       if ((st = cuda_check(ctx, launch_chained(k_pcg_spmv<VT, MT>, dim3(ctx->n_slices), dim3(32 * kSpmvWarps), ctx->stream,
-                                               A, val, (const Vec4<VT>*)zf, p, q, ctx->red, S), "k_pcg_spmv")) != MLS_OK)
+                                               A, val, (const Vec4<VT>*)zf, p, q, it, ctx->pcg_fix, S),
+                           "k_pcg_spmv")) != MLS_OK)
         return st;
       prof_end(ctx, tk);
       tk = prof_begin(ctx, MLS_PROF_PCG_UPDATE);
       ++ctx->launches;
       if ((st = cuda_check(ctx, launch_chained(k_pcg_update<VT>, dim3(nb_upd), dim3(kUpdBlock), ctx->stream, n, x, r, z1,
                                                (const Vec4<VT>*)p, (const Vec4<VT>*)q, dinv, jacobi ? 1 : 2, omega,
-                                               ctx->red, S), "k_pcg_update")) != MLS_OK)
+                                               it, ctx->pcg_fix, S), "k_pcg_update")) != MLS_OK)
         return st;
       prof_end(ctx, tk);
       if (!jacobi) {
         tk = prof_begin(ctx, MLS_PROF_PRECOND);
-        if ((st = two_level_pcg_step(ctx, r, z1, zf, 0, S)) != MLS_OK) return st;
+        if ((st = two_level_pcg_step(ctx, r, z1, zf, 0, it, S)) != MLS_OK) return st;
         prof_end(ctx, tk);
       }
     }
+    // the decision that opens the next iteration, before the host reads it
+    ++ctx->launches;
+    if ((st = cuda_check(ctx, launch_chained(k_pcg_check, dim3(1), dim3(32), ctx->stream, it, ctx->pcg_fix, S),
+                         "k_pcg_check")) != MLS_OK)
+      return st;
     st = cuda_check(ctx, cudaGetLastError(), "pcg iteration");
     if (st != MLS_OK) return st;
     st = cuda_check(ctx, cudaMemcpyAsync(ctx->pcg_host, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost,

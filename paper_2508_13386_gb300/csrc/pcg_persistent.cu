@@ -453,7 +453,7 @@ static mls_status launch_persistent_t(mls_ctx* ctx, int cycle, int iters) {
   a.col = ctx->col;
   a.row_len = ctx->row_len;
   a.dinv = (const VT*)ctx->dinv;
-  a.omega = (VT)ctx->opt.omega;
+  a.omega = (VT)ctx->omega_eff;
   a.x = (Vec4<VT>*)ctx->vx;
   a.r = (Vec4<VT>*)ctx->vr;
   a.p = (Vec4<VT>*)ctx->vp;

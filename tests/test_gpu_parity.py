@@ -140,7 +140,39 @@ def test_persistent_two_level_pcg_matches_phase_kernels(precision, cycle):
     (d1, i1), (d2, i2) = out
     assert abs(i1 - i2) <= 1
     if i1 == i2:   # same iteration: only reduction rounding separates the iterates
-        assert np.linalg.norm(d1 - d2) <= (1e-10 if precision == "fp64" else 1e-4) * np.linalg.norm(d2)
+        assert np.linalg.norm(d1 - d2) <= (rtol if precision == "fp64" else 1e-4) * np.linalg.norm(d2)
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "two_level"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pcg_repeats_bitwise_and_stops_at_the_cap(precision, precond):
+    """The dot products of the PCG loop are summed as integers in fixed
+    point, so the order in which blocks add them does not matter: the same
+    solve twice gives the same bits and the same count.  A cap below the
+    converged count stops with MLS_ENOTCONV after exactly that many
+    iterations, inside a host check chunk (16 iterations) and at its ends."""
+    s = synth.tiny_scene(9, 4, 3, seed=21, E_range=(1e5, 1e9))
+    p = ip.Problem(s)
+    H = p.hessian(p.x_tilde)
+    b = -p.gradient(p.x_tilde)
+    solver = solver_for(s, precision=precision, preconditioner=precond, cycle="multiplicative", omega=0.5)
+    if precond == "two_level":
+        origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=7, k=3, seed=2)
+        solver.upload_basis(origins, vrow, handle, phi)
+    solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
+    if precond == "two_level":
+        solver.build_coarse()
+    rtol = 1e-9 if precision == "fp64" else 1e-5
+    d1, i1, r1, st1 = solver.pcg_solve(dev(b), rtol=rtol, max_iter=5000)
+    d2, i2, r2, st2 = solver.pcg_solve(dev(b), rtol=rtol, max_iter=5000)
+    assert st1 == 0 and st2 == 0 and i1 == i2 and r1 == r2
+    assert np.array_equal(host(d1), host(d2))
+    assert np.linalg.norm(b.ravel() - H @ host(d1).ravel()) <= 10 * rtol * np.linalg.norm(b)
+    for cap in (1, 7, 15, 16, 17, 32):
+        if cap < i1:
+            d, it, rel, st = solver.pcg_solve(dev(b), rtol=rtol, max_iter=cap)
+            assert st == -4 and it == cap, (cap, it, st)
+            assert rel > rtol
 
 
 def test_pcg_zero_rhs():
@@ -339,6 +371,34 @@ def test_lagged_coarse_factor_keeps_the_timestep():
         v = (x_new - x) / s.dt
         x = x_new
     assert builds == [1, 0, 0, 1]
+
+
+def test_automatic_smoother_damping_tracks_lambda_max():
+    """omega = 0: at the coarse build the library estimates lambda_max(D^-1 H)
+    (D the 3x3 block diagonal) by 20 Lanczos steps and damps the smoother
+    with omega = 0.9 x 2 / lambda.  The estimate matches the largest
+    generalized eigenvalue of (H, D) from the oracle's Hessian, never exceeds
+    it, and a timestep with that damping matches the oracle's timestep."""
+    import scipy.linalg as sla
+    s = synth.tiny_scene(8, 3, 3, seed=17, E_range=(1e5, 1e9))
+    p = ip.Problem(s)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=6, k=3, seed=5)
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", cycle="multiplicative", omega=0.0,
+                        newton_tol=1e-10)
+    solver.upload_basis(origins, vrow, handle, phi)
+    solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
+    solver.build_coarse()
+    omega, lam = solver.smoother_omega()
+    H = p.hessian(p.x_tilde).toarray()
+    D = np.zeros_like(H)
+    for v in range(s.n_verts):
+        D[3 * v:3 * v + 3, 3 * v:3 * v + 3] = H[3 * v:3 * v + 3, 3 * v:3 * v + 3]
+    lam_o = sla.eigh(H, D, eigvals_only=True).max()
+    assert lam_o * (1 - 1e-3) <= lam <= lam_o * (1 + 1e-9), (lam, lam_o)
+    assert omega == pytest.approx(1.8 / lam, rel=1e-12)
+    x_o, _ = newton.timestep(p)
+    dx, st = solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    assert rel_disp_error(s.x0 + host(dx), x_o, s.x0) <= 1e-9
 
 
 def test_two_level_timestep_fp64_beam_slice():

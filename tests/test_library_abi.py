@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     text = open(os.path.join(ROOT, "include", "mls.h")).read()
-    return set(re.findall(r"^(?:mls_status|const char\*|int64_t)\s+(mls_\w+)\(", text, re.M))
+    return set(re.findall(r"^(?:mls_status|const char\*|int64_t|double)\s+(mls_\w+)\(", text, re.M))
 
 
 def test_library_exports_every_declared_symbol():
@@ -42,3 +42,26 @@ def test_options_roundtrip_on_cpu():
     assert lib.mls_default_options(C.byref(o)) == 0
     assert o.precision == 0 and o.pcg_rtol == 1e-4 and o.max_newton == 50
     assert lib.mls_default_options(None) == -1
+
+
+def test_tridiagonal_max_eigenvalue_matches_dense_solver():
+    """The Sturm-bisection bound behind the automatic smoother damping
+    (host code, no GPU): against numpy's dense eigenvalues for random,
+    clustered, split (zero off-diagonal) and 1 x 1 tridiagonals."""
+    import numpy as np
+    import paper_2508_13386_gb300 as mls
+    rng = np.random.default_rng(7)
+    cases = [(np.array([2.5]), np.zeros(0))]
+    for k in (2, 5, 20, 40):
+        cases.append((rng.normal(size=k) * 3, rng.normal(size=k - 1)))
+        cases.append((np.full(k, 2.0) + 1e-9 * rng.normal(size=k), np.full(k - 1, 1.0)))
+        e = rng.normal(size=k - 1)
+        e[k // 2 - 1] = 0.0
+        cases.append((rng.uniform(0.1, 3.0, size=k), e))
+    for d, e in cases:
+        T = np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+        lam = np.linalg.eigvalsh(T).max()
+        got = mls.tridiag_max_eig(d, e)
+        scale = np.abs(T).max()
+        assert got >= lam - 1e-13 * scale and got - lam <= 1e-12 * scale, (got, lam)
+    assert np.isnan(mls.tridiag_max_eig(np.zeros(0), np.zeros(0)))
