@@ -69,13 +69,15 @@ def parse():
                     help="block-Jacobi damping in the cycle (0: 0.9 x 2 / the Lanczos estimate of lambda_max(D^-1 H))")
     ap.add_argument("--coarse-refresh", type=int, default=1000,
                     help="rebuild U^T H U every k Newton iterations (>= the Newton count: once per step)")
-    ap.add_argument("--coarse-lag", type=int, default=3,
+    ap.add_argument("--coarse-lag", type=int, default=7,
                     help="timesteps a coarse factor may be reused at a step's first Newton iteration (0: rebuilt every step)")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="plain FP64 steps timed for comparison (the mixed step error is checked on each)")
     ap.add_argument("--newton-tol", type=float, default=1e-3,
                     help="Newton step tolerance of the mixed arm (the FP64 arm uses 1e-10); the per-step "
                          "displacement error against the FP64 arm is measured and reported")
+    ap.add_argument("--pcg-rtol", type=float, default=1e-2,
+                    help="PCG relative tolerance cap of the mixed arm (the forcing term can only tighten it)")
     ap.add_argument("--paper-steps", type=int, default=3,
                     help="steps timed with the paper's inexact direction (20 CG refinement iterations, 1e-3 m/s)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -373,6 +375,7 @@ def main():
     def make(precision, precond):
         s = mls.Solver(precision=precision, preconditioner=precond, cycle=args.cycle, omega=args.omega,
                        newton_tol=args.newton_tol if precision != "fp64" else 1e-10,
+                       pcg_rtol=args.pcg_rtol if precision != "fp64" else 1e-4,
                        coarse_refresh=args.coarse_refresh, persistent=bool(args.persistent),
                        persist_blocks_per_sm=args.blocks_per_sm, stream=stream, coarse_lag_steps=args.coarse_lag)
         s.setup_scene(scene)
@@ -577,7 +580,7 @@ def main():
                              + f"SMS basis m={len(B['origins'])} "
                              f"(r={12 * len(B['origins'])}), coarse refresh every {args.coarse_refresh}"
                              + (f" and reused over {args.coarse_lag} further steps, " if args.coarse_lag else ", ")
-                             + f"Newton step tolerance {args.newton_tol:g}, "
+                             + f"Newton step tolerance {args.newton_tol:g}, PCG tolerance cap {args.pcg_rtol:g}, "
                              + ("persistent PCG kernel" if args.persistent else "one launch per PCG phase"),
                    "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
