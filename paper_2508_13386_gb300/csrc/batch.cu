@@ -848,8 +848,7 @@ __global__ void __launch_bounds__(256) k_brestrict(BView V, BCoarse C, BBasisVie
   if (!last) return;
   __threadfence();
   if (lane < 12) {
-    double s = 0.0;
-    for (int k = B.rchunk_ptr[j]; k < B.rchunk_ptr[j + 1]; ++k) s += __ldcg(B.rpart + 12 * (int64_t)k + lane);
+    const double s = ordered_sum_ldcg(B.rpart + lane, 12, B.rchunk_ptr[j], B.rchunk_ptr[j + 1]);
     c[12 * (int64_t)j + lane] = (VT)s;
   }
   if (lane == 0) B.rcount[j] = 0;

@@ -120,6 +120,20 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double (&sh)[K][32]) {
   __syncthreads();
 }
 
+// sum of base[stride k] over k in [k0, k1), added in index order (so the
+// result is the sequential sum's), with eight loads in flight through L2
+__device__ __forceinline__ double ordered_sum_ldcg(const double* base, int64_t stride, int k0, int k1) {
+  double t = 0.0;
+  for (int k = k0; k < k1; k += 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = k + u < k1 ? __ldcg(base + stride * (k + u)) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t += v[u];
+  }
+  return t;
+}
+
 // Sums v over the whole grid.  Returns true in exactly one block (the last
 // to arrive), where thread 0 holds the totals in v.  Partials are summed in
 // block order, so the result does not depend on scheduling.

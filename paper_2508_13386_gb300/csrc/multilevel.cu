@@ -437,8 +437,7 @@ __global__ void __launch_bounds__(32 * kRestrictWarps) k_restrict(BasisView B, c
   if (!last) return;
   __threadfence();
   if (lane < 12) {
-    double t = 0.0;
-    for (int c = B.rchunk_ptr[j]; c < B.rchunk_ptr[j + 1]; ++c) t += __ldcg(B.rpart + 12 * (int64_t)c + lane);
+    const double t = ordered_sum_ldcg(B.rpart + lane, 12, B.rchunk_ptr[j], B.rchunk_ptr[j + 1]);
     z[12 * (int64_t)j + lane] = (VT)t;
   }
   if (lane == 0) B.rcount[j] = 0;

@@ -338,8 +338,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_pcg_persistent(PersistArgs<
       if (last) {
         __threadfence();
         if (tid < 12) {
-          double sv = 0.0;
-          for (int c2 = a.rchunk_ptr[j]; c2 < a.rchunk_ptr[j + 1]; ++c2) sv += __ldcg(a.rpart + 12 * (int64_t)c2 + tid);
+          const double sv = ordered_sum_ldcg(a.rpart + tid, 12, a.rchunk_ptr[j], a.rchunk_ptr[j + 1]);
           a.c[12 * (int64_t)j + tid] = (VT)sv;
         }
         if (tid == 0) a.rcount[j] = 0;
