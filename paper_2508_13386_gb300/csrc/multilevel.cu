@@ -309,9 +309,41 @@ __device__ __forceinline__ void prolong_row(const BasisView& B, const VT* __rest
   }
 }
 
+// half of the row: the vertex's handles at even (half = 0) or odd (half =
+// 1) positions of its list, four at a time
+template <typename VT>
+__device__ __forceinline__ void prolong_row_half(const BasisView& B, const VT* __restrict__ q, int v, int half,
+                                                 VT& o0, VT& o1, VT& o2) {
+  const Vec4<VT>* coef = (const Vec4<VT>*)B.vcoef;
+  const int k1 = B.vrow[v + 1];
+  for (int k0 = B.vrow[v] + half; k0 < k1; k0 += 8) {
+    int h[4];
+    Vec4<VT> a[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + 2 * u;
+      const bool ok = k < k1;
+      h[u] = ok ? B.vh[k] : -1;
+      a[u] = ok ? coef[k] : Vec4<VT>{VT(0), VT(0), VT(0), VT(0)};
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (h[u] < 0) continue;
+      const Vec4<VT>* qj = (const Vec4<VT>*)(q + 12 * (int64_t)h[u]);
+      const Vec4<VT> q0 = qj[0], q1 = qj[1], q2 = qj[2];
+      o0 += a[u].x * q0.x + a[u].y * q0.y + a[u].z * q0.z + a[u].w * q0.w;
+      o1 += a[u].x * q1.x + a[u].y * q1.y + a[u].z * q1.z + a[u].w * q1.w;
+      o2 += a[u].x * q2.x + a[u].y * q2.y + a[u].z * q2.z + a[u].w * q2.w;
+    }
+  }
+}
+
 // w_v = [acc ? w_v : 0] + sum_j phi_j(v) (I_3 (x) a_vj^T) q_j  (+ omega D^-1 s_v)
 // (q may be null: then only the base and smoothing terms are applied; base
-// and w may alias, each thread reads its own entry before writing it)
+// and w may alias, each vertex's entry is read before it is written).  Two
+// adjacent lanes per vertex split its handles and add their sums with one
+// shuffle, so twice the threads keep the dependent gathers in flight.
+// Launch with prolong_blocks(n).
 template <typename VT>
 __global__ void __launch_bounds__(kBlock) k_prolong(BasisView B, const VT* __restrict__ q,
                                                     const Vec4<VT>* base,
@@ -321,10 +353,14 @@ __global__ void __launch_bounds__(kBlock) k_prolong(BasisView B, const VT* __res
   chain_wait();
   chain_release();
   if (S && S->done) return;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= B.n) return;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = (int)(gt >> 1), half = (int)(gt & 1);
   VT o0 = VT(0), o1 = VT(0), o2 = VT(0);
-  if (q) prolong_row<VT>(B, q, v, o0, o1, o2);
+  if (q && v < B.n) prolong_row_half<VT>(B, q, v, half, o0, o1, o2);
+  o0 += __shfl_xor_sync(0xffffffffu, o0, 1);
+  o1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+  o2 += __shfl_xor_sync(0xffffffffu, o2, 1);
+  if (v >= B.n || half) return;
   if (base) {
     const Vec4<VT> b = base[v];
     o0 += b.x; o1 += b.y; o2 += b.z;
@@ -338,6 +374,8 @@ __global__ void __launch_bounds__(kBlock) k_prolong(BasisView B, const VT* __res
   }
   w[v] = Vec4<VT>{o0, o1, o2, VT(0)};
 }
+
+static inline int prolong_blocks(int n) { return nblk(2 * (int64_t)n); }
 
 // z1 += U y in place, then r.z1 (the end of the additive cycle): inside the
 // loop (first = 0, iteration it) into the sum that opens iteration it + 1,
@@ -892,10 +930,10 @@ static BasisView basis_view(mls_ctx* ctx) {
 mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   if (ctx->opt.precision == MLS_FP64)
-    { ++ctx->launches; k_prolong<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const double*)q,
+    { ++ctx->launches; k_prolong<double><<<prolong_blocks(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const double*)q,
         accumulate ? (const Vec4d*)w : nullptr, nullptr, nullptr, 0.0, (Vec4d*)w, nullptr); }
   else
-    { ++ctx->launches; k_prolong<float><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const float*)q,
+    { ++ctx->launches; k_prolong<float><<<prolong_blocks(ctx->n), kBlock, 0, ctx->stream>>>(basis_view(ctx), (const float*)q,
         accumulate ? (const Vec4f*)w : nullptr, nullptr, nullptr, 0.0f, (Vec4f*)w, nullptr); }
   return cuda_check(ctx, cudaGetLastError(), "k_prolong");
 }
@@ -1231,7 +1269,7 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
     VT* c2 = (VT*)ctx->cvec2;
     mls_status st = coarse_apply_t<VT>(ctx, c, c2, S);
     if (st != MLS_OK) return st;
-    { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, c2, nullptr, dinv, r, omega, z, S); }
+    { ++ctx->launches; k_prolong<VT><<<prolong_blocks(ctx->n), kBlock, 0, ctx->stream>>>(BV, c2, nullptr, dinv, r, omega, z, S); }
     return cuda_check(ctx, cudaGetLastError(), "two-level additive");
   }
   // multiplicative: z1 = S r; t = r - H z1; z2 = z1 + Q t; t = r - H z2; z = z2 + S t
@@ -1241,9 +1279,9 @@ static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, cons
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
   { ++ctx->launches; k_restrict<VT><<<restrict_blocks(ctx->basis.nrchunk), 32 * kRestrictWarps, 0, ctx->stream>>>(BV, tmp, c, S); }
   if ((st = coarse_apply_t<VT>(ctx, c, (VT*)ctx->cvec2, S)) != MLS_OK) return st;
-  { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, (const VT*)ctx->cvec2, z, nullptr, nullptr, omega, z, S); }
+  { ++ctx->launches; k_prolong<VT><<<prolong_blocks(ctx->n), kBlock, 0, ctx->stream>>>(BV, (const VT*)ctx->cvec2, z, nullptr, nullptr, omega, z, S); }
   if ((st = launch_residual(ctx, r, z, tmp, S)) != MLS_OK) return st;
-  { ++ctx->launches; k_prolong<VT><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(BV, nullptr, z, dinv, tmp, omega, z, S); }
+  { ++ctx->launches; k_prolong<VT><<<prolong_blocks(ctx->n), kBlock, 0, ctx->stream>>>(BV, nullptr, z, dinv, tmp, omega, z, S); }
   return cuda_check(ctx, cudaGetLastError(), "two-level multiplicative");
 }
 
@@ -1280,7 +1318,7 @@ static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1
     return st;
   if ((st = coarse_apply_t<VT>(ctx, c, (VT*)ctx->cvec2, S)) != MLS_OK) return st;
   ++ctx->launches;
-  if ((st = cuda_check(ctx, launch_chained(k_prolong<VT>, dim3(nblk(ctx->n)), dim3(kBlock), ctx->stream, BV, (const VT*)ctx->cvec2,
+  if ((st = cuda_check(ctx, launch_chained(k_prolong<VT>, dim3(prolong_blocks(ctx->n)), dim3(kBlock), ctx->stream, BV, (const VT*)ctx->cvec2,
                                            (const Vec4<VT>*)z1, (const VT*)nullptr, (const Vec4<VT>*)nullptr, VT(0), z1,
                                            S), "k_prolong")) != MLS_OK)
     return st;
