@@ -275,8 +275,10 @@ def run_batch(args):
             bases = pool.map(_sms_job, jobs)
         basis_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream(dev)
-    b = mls.Batch(precision=args.precision, preconditioner=args.batch_precond, omega=args.omega if args.omega > 0 else 0.5,
-                  newton_tol=args.newton_tol if args.precision != "fp64" else 1e-10, stream=stream)
+    omega_b = args.omega if args.omega > 0 else 0.5   # the automatic damping is a single-mesh option
+    b = mls.Batch(precision=args.precision, preconditioner=args.batch_precond, omega=omega_b,
+                  newton_tol=args.newton_tol if args.precision != "fp64" else 1e-10,
+                  pcg_rtol=args.pcg_rtol if args.precision != "fp64" else 1e-4, stream=stream)
     b.upload_scenes(scenes)
     if bases is not None:
         b.upload_bases(bases)
@@ -290,6 +292,7 @@ def run_batch(args):
         v.copy_(dx / h)
         x.add_(dx)
     torch.cuda.synchronize()
+    x_s, v_s = x.clone(), v.clone()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     infos, stats = [], []
     if world > 1:
@@ -308,6 +311,24 @@ def run_batch(args):
         torch.cuda.synchronize()
     total_s = sum(a.elapsed_time(c) for a, c in ev) / 1e3
     total_s = max_over_ranks(total_s, dist if world > 1 else None, dev)
+    # accuracy of the timed settings: the step from the post-warm-up state
+    # against an FP64 batch solved to Newton tolerance 1e-10, per mesh
+    disp_err = None
+    if args.precision != "fp64":
+        ref = mls.Batch(precision="fp64", preconditioner=args.batch_precond, omega=omega_b, newton_tol=1e-10,
+                        pcg_rtol=1e-4, stream=stream)
+        ref.upload_scenes(scenes)
+        if bases is not None:
+            ref.upload_bases(bases)
+        dxm, dxr = torch.empty_like(x), torch.empty_like(x)
+        b.step(x_s.clone(), v_s.clone(), h, dx=dxm)
+        ref.step(x_s.clone(), v_s.clone(), h, dx=dxr)
+        dm, dr = dxm.cpu().numpy(), dxr.cpu().numpy()
+        vo = b.vert_offsets
+        errs = [float(np.linalg.norm(dm[vo[m]:vo[m + 1]] - dr[vo[m]:vo[m + 1]])
+                      / max(np.linalg.norm(dr[vo[m]:vo[m + 1]]), 1e-300)) for m in range(len(vo) - 1)]
+        disp_err = {"max": max(errs), "mean": float(np.mean(errs)), "meshes": len(errs), "steps": 1}
+        ref.close()
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -325,13 +346,15 @@ def run_batch(args):
                    "solver": (f"{args.precision} two-level PCG per mesh (SMS bases, "
                               f"{sum(len(B['origins']) for B in bases)} handles in all, multiplicative cycle), "
                               if bases is not None else f"{args.precision} block-Jacobi PCG per mesh, ")
-                             + f"Newton step tolerance {args.newton_tol:g}, one graph launch per step",
+                             + f"Newton step tolerance {args.newton_tol:g}, PCG tolerance cap {args.pcg_rtol:g}, "
+                               f"omega {omega_b:g}, one graph launch per step",
                    "l2": "flushed (256 MB write) before every timed step"},
         "mesh_steps_per_s": n_all * args.steps / total_s,
         "newton_rounds_per_step": float(np.mean([i["newton_rounds"] for i in infos])),
         "pcg_rounds_per_step": float(np.mean([i["pcg_rounds"] for i in infos])),
         "pcg_iters_per_step_sum_over_meshes": float(np.mean([sum(m["pcg_iters"] for m in st) for st in stats])),
         "mesh_status_ok": int(sum(all(m["status"] == 0 for m in st) for st in stats)),
+        "disp_err_vs_fp64": disp_err,
         "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
         "graph_launches": int(sum(i["graph_launches"] for i in infos)),
         "tuned": {"spmv_lanes": infos[-1]["spmv_lanes"], "row_threads": infos[-1]["row_threads"],

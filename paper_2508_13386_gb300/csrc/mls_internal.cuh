@@ -342,12 +342,31 @@ __device__ __forceinline__ bool dbl_positive(double x) {  // > 0 and finite
 // a <= b for non-negative finite doubles: their bit patterns order like the values
 __device__ __forceinline__ bool dbl_le_nonneg(double a, double b) { return __double_as_longlong(a) <= __double_as_longlong(b); }
 
-// a / b in the solve precision: float division for float vectors (float64
-// division issues slowly), float64 for float64 vectors
+// x 2^d for a normal double x by moving its exponent field (0 or infinity
+// when the result leaves the normal range), integer instructions only
+__device__ __forceinline__ double dbl_scale2(double x, int d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0 || E == 0x7ff) return x;
+  const int F = E + d;
+  const unsigned long long sign = b & (1ull << 63);
+  if (F <= 0) return __longlong_as_double((long long)sign);
+  if (F >= 0x7ff) return __longlong_as_double((long long)(sign | (0x7ffull << 52)));
+  return __longlong_as_double((long long)((b & ~(0x7ffull << 52)) | ((unsigned long long)F << 52)));
+}
+
+// a / b in the solve precision: for float vectors a float division after
+// both operands are scaled by the same power of two (b to [1, 2)), so dot
+// products beyond the float range still give their ratio (float64 division
+// issues slowly); float64 division for float64 vectors
 template <typename VT>
 __device__ __forceinline__ VT ratio(double a, double b) {
-  if constexpr (sizeof(VT) == 4) return dbl_to_flt(a) / dbl_to_flt(b);
-  else return a / b;
+  if constexpr (sizeof(VT) == 4) {
+    const int eb = (int)(((unsigned long long)__double_as_longlong(b) >> 52) & 0x7ff);
+    return dbl_to_flt(dbl_scale2(a, 1023 - eb)) / dbl_to_flt(dbl_scale2(b, 1023 - eb));
+  } else {
+    return a / b;
+  }
 }
 
 // The state that opens PCG iteration i: r.z and r.r of the iterate, the

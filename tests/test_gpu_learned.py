@@ -103,6 +103,14 @@ def test_warm_start_on_held_out_steps(beam_basis):
           f"time {pres['plain_s']:.3f}s -> {pres['warm_s']:.3f}s, warm vs plain step {pres['max_rel_diff']:.3e}")
     # the network learned the coarse step: far better than the zero prediction
     assert pred_err < 0.5
-    # the fallback keeps the solve no worse than the plain start (to within
-    # the small variation of an inexact solve started elsewhere)
-    assert newton_w <= newton_p + 3
+    # where the prediction is rejected, the warm-started solver runs the plain
+    # solve from the same state: the deterministic sums make it the same
+    # solve, iteration for iteration
+    for sp, sw in zip(res["plain"], res["warm"]):
+        if not sw["warm_start_used"]:
+            assert (sw["newton_iters"], sw["pcg_iters"]) == (sp["newton_iters"], sp["pcg_iters"])
+    # an accepted start (feasible, lower energy) may take a few more Newton
+    # iterations from its different starting point, never many
+    extra = sum(sw["newton_iters"] - sp["newton_iters"]
+                for sp, sw in zip(res["plain"], res["warm"]) if sw["warm_start_used"])
+    assert extra <= 5 * max(used, 1)

@@ -175,6 +175,35 @@ def test_pcg_repeats_bitwise_and_stops_at_the_cap(precision, precond):
             assert rel > rtol
 
 
+@pytest.mark.parametrize("precond", ["jacobi", "two_level"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pcg_fixed_point_sums_follow_the_scale(precision, precond):
+    """The fixed-point PCG sums take their scale from the previous value of
+    each dot product.  Scaling the right-hand side by 2^k scales every dot
+    product by 2^2k and nothing else: the solve takes the same iterations and
+    returns the scaled solution bit for bit (powers of two are exact).
+    k = +-80 for float64 vectors; k = +-40 for float vectors, which keeps
+    their smallest entries normal."""
+    s = synth.tiny_scene(9, 4, 3, seed=21, E_range=(1e5, 1e9))
+    p = ip.Problem(s)
+    b = -p.gradient(p.x_tilde)
+    solver = solver_for(s, precision=precision, preconditioner=precond, cycle="multiplicative", omega=0.5)
+    if precond == "two_level":
+        origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=7, k=3, seed=2)
+        solver.upload_basis(origins, vrow, handle, phi)
+    solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
+    if precond == "two_level":
+        solver.build_coarse()
+    rtol = 1e-9 if precision == "fp64" else 1e-5
+    d0, i0, r0, st0 = solver.pcg_solve(dev(b), rtol=rtol, max_iter=5000)
+    assert st0 == 0
+    k = 80 if precision == "fp64" else 40
+    for scale in (2.0 ** k, 2.0 ** -k):
+        d, i, r, st = solver.pcg_solve(dev(b * scale), rtol=rtol, max_iter=5000)
+        assert st == 0 and i == i0
+        assert np.array_equal(host(d), host(d0) * scale)
+
+
 def test_pcg_zero_rhs():
     s = synth.tiny_scene(2, 2, 2, seed=1)
     p = ip.Problem(s)
