@@ -1157,12 +1157,6 @@ BEnergyIn energy_in(mls_ctx* c) {
   return BEnergyIn{c->t, c->tets, c->Dminv, c->vol, c->mu, c->lam, c->mass, c->pinned, c->xtil};
 }
 
-// launches counted into the per-loop tallies of the current capture
-struct Tally {
-  int64_t* where;
-  void add(int k = 1) { *where += k; }
-};
-
 template <typename VT, typename MT>
 mls_status launch_cycle(mls_batch* b, cudaStream_t s, int first);
 

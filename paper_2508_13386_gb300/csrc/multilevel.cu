@@ -1261,7 +1261,6 @@ template <typename VT>
 static mls_status two_level_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z, const PcgScalars* S) {
   const BasisView BV = basis_view(ctx);
   const VT omega = (VT)ctx->omega_eff;
-  const int m = ctx->basis.m;
   VT* c = (VT*)ctx->cvec;
   const VT* dinv = (const VT*)ctx->dinv;
   if (ctx->opt.cycle == MLS_CYCLE_ADDITIVE) {
@@ -1296,7 +1295,6 @@ template <typename VT>
 static mls_status two_level_step_t(mls_ctx* ctx, const Vec4<VT>* r, Vec4<VT>* z1, Vec4<VT>* zf, int first, int it,
                                    PcgScalars* S) {
   const BasisView BV = basis_view(ctx);
-  const int m = ctx->basis.m;
   VT* c = (VT*)ctx->cvec;
   mls_status st;
   const dim3 rgrid(restrict_blocks(ctx->basis.nrchunk)), rblock(32 * kRestrictWarps);
