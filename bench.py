@@ -50,7 +50,7 @@ REF_PCG = 1000
 # cold-cache ncu capture inside the timed step) of the dominant kernel on the
 # 41^3 lattice, keyed by (kernel, precision); valid for the kernel version it
 # was taken on and reported as null for anything else
-MEASURED_TRAFFIC = {("k_pcg_spmv", "fp32", 41): 46_776_576}
+MEASURED_TRAFFIC = {}  # the product kernel's opening step changed (scale-safe float ratios) after the last capture
 METRIC = "timesteps/s at 220K tets: plain FP64 vs mixed+learned PCG at 1e-4 disp error"
 UNIT = "timesteps/s"
 
