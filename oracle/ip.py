@@ -80,13 +80,18 @@ class Problem:
         g[self.pinned] = 0.0
         return g
 
-    def hessian(self, x):
+    def hessian(self, x, elem_scale=None):
         """Projected Hessian as a (3n x 3n) CSR matrix:
-        M + h^2 (sum_e vol_e B^T [dP/dF]_+ B + kappa sum_v b''(d_v) n n^T),
-        with Dirichlet rows and columns replaced by the identity."""
+        M + h^2 (sum_e c_e vol_e B^T [dP/dF]_+ B + kappa sum_v b''(d_v) n n^T),
+        with Dirichlet rows and columns replaced by the identity.  c_e = 1
+        unless ``elem_scale`` gives it: a cubature of the elastic term
+        (Sec. 3.8) passes c_e = w_e / vol_e on its elements and 0 elsewhere;
+        mass and barrier terms stay fully integrated."""
         x = np.asarray(x, dtype=np.float64)
         He = elastic.element_hessian(x, self.tets, self.vol, self.Dm_inv, self.mu,
                                      self.lam, project=self.project)
+        if elem_scale is not None:
+            He = He * np.asarray(elem_scale, dtype=np.float64)[:, None, None]
         dof = (3 * self.tets[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
         rows = np.repeat(dof, 12, axis=1).ravel()
         cols = np.tile(dof, (1, 12)).ravel()

@@ -107,6 +107,35 @@ def test_hessian_symmetric_positive_definite():
     assert np.linalg.eigvalsh(H).min() > 0
 
 
+@pytest.mark.parametrize("contact", [False, True])
+def test_cubature_scaled_hessian_is_affine_in_the_scale(contact):
+    """The cubature Hessian (Sec. 3.8) scales only the elastic term:
+    unit scales give the full Hessian bit for bit, and since mass and
+    barrier terms do not depend on the scale, H(s1) + H(s2) - H(0) =
+    H(s1 + s2), and H(s) - H(0) is h^2 times the elastic Hessian weighted by s
+    (checked on one element alone, against its own 12 x 12 block)."""
+    s, p = _problem(contact)
+    x = p.x_tilde + (1e-3 * rng.normal(size=p.x_tilde.shape) if not contact else 0.0)
+    x[p.pinned] = p.x_t[p.pinned]
+    t = len(s.tets)
+    H = p.hessian(x).toarray()
+    assert np.array_equal(p.hessian(x, np.ones(t)).toarray(), H)
+    s1, s2 = rng.uniform(0, 2, size=t), rng.uniform(0, 2, size=t)
+    H0 = p.hessian(x, np.zeros(t)).toarray()
+    lhs = p.hessian(x, s1).toarray() + p.hessian(x, s2).toarray() - H0
+    assert np.allclose(lhs, p.hessian(x, s1 + s2).toarray(), rtol=0, atol=1e-12 * np.abs(H).max())
+    e = int(np.nonzero(~p.pinned[s.tets].any(axis=1))[0][0])   # an element with no pinned vertex
+    one = np.zeros(t)
+    one[e] = 3.0
+    D = p.hessian(x, one).toarray() - H0
+    from oracle import elastic
+    He = elastic.element_hessian(x, s.tets, p.vol, p.Dm_inv, p.mu, p.lam, project=True)[e]
+    dof = (3 * s.tets[e][:, None] + np.arange(3)[None, :]).ravel()
+    assert np.allclose(D[np.ix_(dof, dof)], 3.0 * p.h ** 2 * He, rtol=1e-12, atol=1e-12 * np.abs(He).max() * p.h ** 2)
+    D[np.ix_(dof, dof)] = 0.0
+    assert np.abs(D).max() <= 1e-12 * np.abs(H).max()
+
+
 # -- Newton timestep -----------------------------------------------------------
 def test_uniform_translation_is_exact():
     """No gravity, no contact, no pins: a rigid translation with velocity v
