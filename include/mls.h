@@ -199,6 +199,16 @@ mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n_verts, const double* rest_xyz
 mls_status mls_upload_basis(mls_ctx* ctx, int32_t n_handles, const double* origins,
                             const int32_t* vrow, const int32_t* handle, const double* phi);
 
+/* Cubature of the elastic term in the coarse operator (Sec. 3.8): scale
+ * [n_tets] HOST, per element the factor w_e / vol_e of a cubature with
+ * weights w_e (0 off the cubature; see paper_2508_13386_gb300/cubature.py for
+ * the modal moment fitting of Alg. 3).  From the next coarse build on,
+ * U^T H U is built from H_cub = M + h^2 (sum_e scale_e H_e + barrier), the
+ * mass and barrier terms whole; the fine H and every other use of H are
+ * unchanged.  NULL removes the cubature.  MLS_EINVAL for a negative or
+ * non-finite factor or a call before mls_upload_mesh. */
+mls_status mls_upload_cubature(mls_ctx* ctx, const double* scale);
+
 /* External loads (HOST arrays of 3): gravity g (m/s^2); when contact != 0 the
  * ground plane {x : n . x = o} with unit normal plane_n, barrier distance
  * dhat > 0 and stiffness kappa > 0.  Defaults: g = (0, 0, -9.81), no contact. */

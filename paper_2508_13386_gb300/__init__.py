@@ -156,6 +156,15 @@ class Solver:
         self._check(self._l.mls_upload_basis(self._ctx, origins.shape[0], pO, pV, pH, pP))
         self.m = origins.shape[0]
 
+    def upload_cubature(self, scale):
+        """Per-element factor w_e / vol_e of an elastic-term cubature for the
+        coarse operator (``cubature.build_cubature(...)["scale"]``), or None."""
+        if scale is None:
+            self._check(self._l.mls_upload_cubature(self._ctx, None))
+            return
+        scale, ps = _host(scale, np.float64)
+        self._check(self._l.mls_upload_cubature(self._ctx, ps))
+
     def set_forces(self, gravity=(0.0, 0.0, -9.81), contact=False, plane_n=(0.0, 0.0, 1.0), plane_o=0.0,
                    dhat=1e-3, kappa=1e5):
         g, pg = _host(gravity, np.float64)

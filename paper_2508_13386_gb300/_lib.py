@@ -74,6 +74,7 @@ SIGNATURES = {
     "mls_last_error": [_P],
     "mls_set_options": [_P, C.POINTER(Options)],
     "mls_smoother_omega": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+    "mls_upload_cubature": [_P, _P],
     "mls_tridiag_max_eig": [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int],
     "mls_upload_mesh": [_P, _I32, _P, _I32, _P, _P, _P, _P, _P],
     "mls_upload_basis": [_P, _I32, _P, _P, _P, _P],

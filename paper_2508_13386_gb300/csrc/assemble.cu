@@ -132,11 +132,14 @@ __device__ __forceinline__ void inv3(const T (&A)[9], T (&R)[9]) {
 
 // One thread per block slot of H.  AT: accumulation type, ET: element
 // Hessian type, MT: storage type of H, VT: solve type (for D^{-1}).
+// escale (nullable): a factor per element on its elastic Hessian (a
+// cubature of the elastic term, Sec. 3.8; mass and barrier stay whole).
+// dinv (nullable): the block-Jacobi inverse of the stored diagonal blocks.
 template <typename AT, typename ET, typename MT, typename VT>
 __global__ void __launch_bounds__(kBlock) k_assemble(SellAsmIn in, int64_t n_slots,
                                                      const Vec4d* __restrict__ x,
                                                      const ET* __restrict__ hs, MT* __restrict__ val,
-                                                     VT* __restrict__ dinv) {
+                                                     VT* __restrict__ dinv, const double* __restrict__ escale) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_slots) return;
   const int64_t g = s >> 5;
@@ -161,7 +164,18 @@ __global__ void __launch_bounds__(kBlock) k_assemble(SellAsmIn in, int64_t n_slo
   } else {
     for (int q = in.asm_ptr[s]; q < in.asm_ptr[s + 1]; ++q) {
       const int code = in.asm_code[q];
-      add_elem_block<AT, ET>(acc, hs, in.t, code >> 4, (code >> 2) & 3, code & 3);
+      if (escale) {
+        const double se = escale[code >> 4];
+        if (se == 0.0) continue;
+        AT part[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) part[k] = AT(0);
+        add_elem_block<AT, ET>(part, hs, in.t, code >> 4, (code >> 2) & 3, code & 3);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[k] += (AT)se * part[k];
+      } else {
+        add_elem_block<AT, ET>(acc, hs, in.t, code >> 4, (code >> 2) & 3, code & 3);
+      }
     }
     const AT h2 = (AT)in.h2;
 #pragma unroll
@@ -185,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(SellAsmIn in, int64_t n_slo
   }
 #pragma unroll
   for (int q = 0; q < 9; ++q) out[q * 32] = from_d<MT>((double)acc[q]);
-  if (c == row) {
+  if (c == row && dinv) {
     // block-Jacobi inverse of the diagonal block as stored
     VT A[9], R[9];
 #pragma unroll
@@ -299,7 +313,9 @@ mls_status launch_gather_grad(mls_ctx* ctx, const Vec4d* x, double* gnorm2_out) 
   return cuda_check(ctx, cudaGetLastError(), "k_gather_grad");
 }
 
-mls_status launch_assemble(mls_ctx* ctx, const Vec4d* x) {
+// H (or, with escale, the cubature H of the coarse operator) at x into val;
+// dinv (nullable) receives the block-Jacobi inverse
+static mls_status assemble_into(mls_ctx* ctx, const Vec4d* x, void* val, void* dinv, const double* escale) {
   SellAsmIn in{ctx->n, ctx->t, ctx->group_slice, ctx->col, ctx->row_len, ctx->slice_ptr, ctx->asm_ptr,
                ctx->asm_code, ctx->mass, ctx->pinned, ctx->h * ctx->h, ctx->kappa, ctx->dhat, ctx->po,
                ctx->pn[0], ctx->pn[1], ctx->pn[2], ctx->contact};
@@ -308,18 +324,27 @@ mls_status launch_assemble(mls_ctx* ctx, const Vec4d* x) {
   switch (ctx->opt.precision) {
     case MLS_FP64:
       { ++ctx->launches; k_assemble<double, double, double, double><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const double*)ctx->ehess, (double*)ctx->hval, (double*)ctx->dinv); }
+          in, n_slots, x, (const double*)ctx->ehess, (double*)val, (double*)dinv, escale); }
       break;
     case MLS_MIXED_FP32:
       { ++ctx->launches; k_assemble<float, float, float, float><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const float*)ctx->ehess, (float*)ctx->hval, (float*)ctx->dinv); }
+          in, n_slots, x, (const float*)ctx->ehess, (float*)val, (float*)dinv, escale); }
       break;
     default:
       { ++ctx->launches; k_assemble<float, float, __nv_bfloat16, float><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)ctx->hval, (float*)ctx->dinv); }
+          in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)val, (float*)dinv, escale); }
       break;
   }
   return cuda_check(ctx, cudaGetLastError(), "k_assemble");
+}
+
+mls_status launch_assemble(mls_ctx* ctx, const Vec4d* x) {
+  return assemble_into(ctx, x, ctx->hval, ctx->dinv, nullptr);
+}
+
+mls_status launch_assemble_cubature(mls_ctx* ctx, const Vec4d* x) {
+  if (!ctx->cub_scale || !ctx->hval_cub) return fail(ctx, MLS_EINVAL, "no cubature uploaded");
+  return assemble_into(ctx, x, ctx->hval_cub, nullptr, ctx->cub_scale);
 }
 
 mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, double dt) {

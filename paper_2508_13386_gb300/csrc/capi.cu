@@ -148,6 +148,8 @@ static void free_all(mls_ctx* ctx) {
   ctx->has_basis = false;
   ctx->coarse_ready = false;
   ctx->assembled = false;
+  ctx->cub_scale = nullptr;
+  ctx->hval_cub = nullptr;
 }
 
 static mls_status alloc_state(mls_ctx* ctx);
@@ -802,6 +804,23 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
     ctx->coarse_ready = false;
   }
   return basis_upload(ctx, m, origins, vrow, handle, phi);
+}
+
+mls_status mls_upload_cubature(mls_ctx* ctx, const double* scale) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (ctx->cub_scale) dfree(ctx, ctx->cub_scale);
+  if (ctx->hval_cub) dfree(ctx, ctx->hval_cub);
+  ctx->cub_scale = nullptr;
+  ctx->hval_cub = nullptr;
+  ctx->coarse_ready = false;
+  if (!scale) return MLS_OK;
+  for (int e = 0; e < ctx->t; ++e)
+    if (!(scale[e] >= 0.0) || !std::isfinite(scale[e])) return fail(ctx, MLS_EINVAL, "cubature scale must be finite and >= 0");
+  if ((st = dalloc(ctx, (void**)&ctx->cub_scale, sizeof(double) * (size_t)ctx->t)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->hval_cub, (size_t)storage_bytes(ctx) * 288 * ctx->n_groups)) != MLS_OK) return st;
+  return cuda_check(ctx, cudaMemcpy(ctx->cub_scale, scale, sizeof(double) * (size_t)ctx->t, cudaMemcpyHostToDevice),
+                    "cubature upload");
 }
 
 mls_status mls_eval_elements(mls_ctx* ctx, const double* x, double* energy, double* grad, double* hess) {

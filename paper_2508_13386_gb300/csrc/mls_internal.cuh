@@ -527,6 +527,8 @@ struct mls_ctx {
   void* vq = nullptr;
   void* vw = nullptr;
   void* vz2 = nullptr;             // preconditioned residual of the multiplicative cycle
+  double* cub_scale = nullptr;     // device [t]: cubature factor per element on its elastic Hessian (nullable)
+  void* hval_cub = nullptr;        // the cubature H the coarse operator is built from (with cub_scale)
   double omega_eff = 0.5;          // damping the two-level cycle applies (opt.omega or the automatic choice)
   double omega_lmax = 0.0;         // the automatic choice's estimate of lambda_max(D^{-1} H)
   double* lz = nullptr;            // device: Lanczos alpha[kLanczosSteps], beta[kLanczosSteps + 1]
@@ -633,6 +635,7 @@ mls_status launch_unpack(mls_ctx* ctx, const Vec4d* src, double* dst);
 mls_status launch_disp_out(mls_ctx* ctx, double* dx_out);
 
 mls_status launch_spmv(mls_ctx* ctx, const void* x, void* y);  // solve-precision vectors
+mls_status launch_assemble_cubature(mls_ctx* ctx, const Vec4d* x);  // cubature H into hval_cub
 constexpr int kLanczosSteps = 20;  // Lanczos steps of the automatic smoother damping
 // largest eigenvalue of the symmetric tridiagonal matrix with diagonal d[0..k-1]
 // and off-diagonal e[0..k-2] (Sturm-count bisection), from above to rounding

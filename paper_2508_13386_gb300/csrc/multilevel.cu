@@ -957,7 +957,9 @@ static mls_status galerkin_t(mls_ctx* ctx) {
     if (st != MLS_OK) return st;
     { ++ctx->launches; k_ypair_rows<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, B.yrow, B.ypair_row); }
   }
-  { ++ctx->launches; k_galerkin_y<VT, MT><<<nblk(B.ny), kBlock, 0, ctx->stream>>>(basis_view(ctx), G, (const MT*)ctx->hval,
+  // with a cubature the coarse operator is built from the cubature H (Sec. 3.8)
+  const MT* hv = (const MT*)(ctx->cub_scale ? ctx->hval_cub : ctx->hval);
+  { ++ctx->launches; k_galerkin_y<VT, MT><<<nblk(B.ny), kBlock, 0, ctx->stream>>>(basis_view(ctx), G, hv,
                                                                B.ypair_row, B.ny, (VT*)ctx->yval); }
   mls_status st = cuda_check(ctx, cudaMemsetAsync(ctx->Ac, 0, sizeof(double) * r * r, ctx->stream), "Ac clear");
   if (st != MLS_OK) return st;
@@ -1226,6 +1228,7 @@ mls_status build_coarse(mls_ctx* ctx) {
   mls_status st;
   if ((st = choose_omega(ctx)) != MLS_OK) return st;
   int tk = prof_begin(ctx, MLS_PROF_GALERKIN);
+  if (ctx->cub_scale && (st = launch_assemble_cubature(ctx, ctx->xk)) != MLS_OK) return st;
   switch (ctx->opt.precision) {
     case MLS_FP64: st = galerkin_t<double, double>(ctx); break;
     case MLS_MIXED_FP32: st = galerkin_t<float, float>(ctx); break;

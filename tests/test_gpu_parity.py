@@ -322,6 +322,41 @@ def test_galerkin_matches_oracle(precision, tol):
     assert np.max(np.abs(A - A_o)) <= tol * np.abs(A_o).max()
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("contact", [False, True])
+def test_cubature_galerkin_matches_oracle(precision, tol, contact):
+    """With a cubature of the elastic term (Sec. 3.8) the coarse operator is
+    U^T H_cub U, H_cub = M + h^2 (sum_e s_e H_e + barrier): random factors,
+    half of them zero, against the oracle's scaled Hessian; the fine H stays
+    the full one, and removing the cubature restores the full operator."""
+    s = synth.tiny_scene(6, 4, 3, seed=15, E_range=(1e5, 1e8), contact=contact, pinned=not contact)
+    p = ip.Problem(s)
+    x = p.x_tilde.copy()
+    if contact:
+        x[:, 2] = np.maximum(x[:, 2], 2e-4)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=7, k=3, seed=3)
+    U = subspace.lbs_basis_matrix(s.X, origins, vrow, handle, phi)
+    t = len(s.tets)
+    cub = rng.uniform(0.0, 2.0, size=t) * (rng.random(t) < 0.5)
+    solver = solver_for(s, precision=precision, preconditioner="two_level")
+    solver.upload_basis(origins, vrow, handle, phi)
+    solver.upload_cubature(cub)
+    solver.assemble(dev(x), dev(s.x0), dev(s.v0), s.dt)
+    solver.build_coarse()
+    A = solver.get_coarse()
+    A_o = subspace.galerkin(p.hessian(x, cub), U)
+    assert np.max(np.abs(A - A_o)) <= tol * np.abs(A_o).max()
+    import scipy.sparse as sp
+    rp, col, val = solver.get_hessian()
+    H = sp.bsr_matrix((val, col, rp), shape=(3 * s.n_verts, 3 * s.n_verts)).toarray()
+    H_o = p.hessian(x).toarray()
+    assert np.max(np.abs(H - H_o)) <= {"fp64": 1e-11, "fp32": 2e-5}[precision] * np.abs(H_o).max()
+    solver.upload_cubature(None)
+    solver.build_coarse()
+    A_full = subspace.galerkin(p.hessian(x), U)
+    assert np.max(np.abs(solver.get_coarse() - A_full)) <= tol * np.abs(A_full).max()
+
+
 @pytest.mark.parametrize("cycle", ["additive", "multiplicative"])
 def test_two_level_apply_matches_oracle(cycle):
     s = synth.tiny_scene(6, 4, 3, seed=16, E_range=(1e5, 1e8), pinned=False)

@@ -50,6 +50,22 @@ def test_beam_timestep(beam, precision, precond, tol):
     assert err <= tol, (err, stats)
 
 
+def test_beam_timestep_with_cubature_coarse_operator(beam):
+    """The SMS basis with its modal moment-fitting cubature (Sec. 3.8, Alg.
+    3) building the coarse operator: the preconditioner changes, the
+    timestep does not (it matches the oracle's), and the cubature keeps a
+    small fraction of the elements."""
+    from paper_2508_13386_gb300 import cubature
+    s, p, x_o, B = beam
+    C = cubature.build_cubature(s.X, s.tets, B, seed=0, workers=1)
+    assert len(C["elem"]) < len(s.tets) // 4
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", newton_tol=1e-10)
+    solver.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+    solver.upload_cubature(C["scale"])
+    dx, stats = solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    assert rel_disp_error(s.x0 + host(dx), x_o, s.x0) <= 1e-9, stats
+
+
 def test_beam_bf16_reports_indefinite_operator(beam):
     """bfloat16 keeps 8 mantissa bits: with E = 1e9 next to E = 1e5 the
     rounded H is indefinite (its rounding error exceeds the mass term in the
