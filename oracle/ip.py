@@ -1,19 +1,25 @@
-"""Incremental potential for one implicit-Euler timestep (oracle).
+"""Incremental potential for one timestep (oracle).
 
-Eq. IP with implicit Euler (Sec. 3.1): alpha = 1, predictor
-x_tilde = x^t + h v^t, velocity update v^{t+1} = (x^{t+1} - x^t) / h.
+Eq. IP (Sec. 3.1) with implicit Euler: alpha = 1, predictor
+x_tilde = x^t + h v^t, velocity update v^{t+1} = (x^{t+1} - x^t) / h; or
+with BDF2: alpha = 4/9, x_tilde = (4 x^t - x^{t-1}) / 3 + (2h/9)(4 v^t -
+v^{t-1}), v^{t+1} = (4 v^t - v^{t-1}) / 3 + (2h/3) a^{t+1}.  The printed
+acceleration a^{t+1} = (4h^2/9)(x^{t+1} - x_tilde) is dimensionally garbled;
+the reading a^{t+1} = (9 / (4 h^2)) (x^{t+1} - x_tilde) is the one that makes
+x_tilde + (4h^2/9) a^{t+1} = x^{t+1} (the BDF2 position update), and with it
+v^{t+1} = (3 x^{t+1} - 4 x^t + x^{t-1}) / (2h), the BDF2 velocity.
 Readings used where the paper is silent:
 
 * mass: lumped, m_v = sum over tets e containing v of rho_e vol_e / 4;
-* gravity g enters through the predictor, x_tilde = x^t + h v^t + h^2 g
-  (equivalent to the potential -M g . x in the h^2-scaled bracket);
+* gravity g enters through the predictor, x_tilde += alpha h^2 g
+  (equivalent to the potential -M g . x in the alpha h^2-scaled bracket);
 * friction D = 0 (no workload uses friction);
 * Dirichlet vertices are held at x^t: they are not unknowns, their inertia
   term is dropped, their gradient entries are zero and their Hessian rows
   and columns are the identity.
 
     E(x) = 1/2 sum_{v free} m_v |x_v - x_tilde_v|^2
-           + h^2 ( sum_e vol_e psi(F_e(x)) + kappa sum_v b(n . x_v - o) ).
+           + alpha h^2 ( sum_e vol_e psi(F_e(x)) + kappa sum_v b(n . x_v - o) ).
 """
 from __future__ import annotations
 
@@ -26,7 +32,8 @@ from . import barrier, elastic
 class Problem:
     """One timestep's incremental potential built from a synthetic scene."""
 
-    def __init__(self, scene, x_t=None, v_t=None, dt=None, project=True):
+    def __init__(self, scene, x_t=None, v_t=None, dt=None, project=True, integrator="ie", x_prev=None,
+                 v_prev=None):
         self.X = np.asarray(scene.X, dtype=np.float64)
         self.tets = np.asarray(scene.tets, dtype=np.int64)
         self.n = self.X.shape[0]
@@ -47,8 +54,29 @@ class Problem:
         self.project = project
         self.x_t = np.array(scene.x0 if x_t is None else x_t, dtype=np.float64)
         self.v_t = np.array(scene.v0 if v_t is None else v_t, dtype=np.float64)
-        self.x_tilde = self.x_t + self.h * self.v_t + self.h ** 2 * self.gravity[None, :]
+        self.integrator = integrator
+        if integrator == "ie":
+            self.alpha = 1.0
+            self.x_tilde = self.x_t + self.h * self.v_t + self.h ** 2 * self.gravity[None, :]
+        elif integrator == "bdf2":
+            if x_prev is None or v_prev is None:
+                raise ValueError("BDF2 needs x^{t-1} and v^{t-1}")
+            self.alpha = 4.0 / 9.0
+            self.x_prev = np.array(x_prev, dtype=np.float64)
+            self.v_prev = np.array(v_prev, dtype=np.float64)
+            self.x_tilde = ((4.0 * self.x_t - self.x_prev) / 3.0 + (2.0 * self.h / 9.0) * (4.0 * self.v_t - self.v_prev)
+                            + self.alpha * self.h ** 2 * self.gravity[None, :])
+        else:
+            raise ValueError(f"unknown integrator {integrator!r}")
+        self.ah2 = self.alpha * self.h ** 2   # the factor on the potentials
         self.x_tilde[self.pinned] = self.x_t[self.pinned]
+
+    def velocity(self, x_new):
+        """v^{t+1} of the integrator from the step's solution."""
+        x_new = np.asarray(x_new, dtype=np.float64)
+        if self.integrator == "ie":
+            return (x_new - self.x_t) / self.h
+        return (3.0 * x_new - 4.0 * self.x_t + self.x_prev) / (2.0 * self.h)
 
     # -- pieces -----------------------------------------------------------
     def distances(self, x):
@@ -64,7 +92,7 @@ class Problem:
         B = 0.0
         if self.contact:
             B = self.kappa * np.sum(barrier.b(self.distances(x), self.dhat))
-        return K + self.h ** 2 * (Psi + B)
+        return K + self.ah2 * (Psi + B)
 
     def gradient(self, x):
         """dE/dx as [n,3]; zero on Dirichlet vertices."""
@@ -76,7 +104,7 @@ class Problem:
         if self.contact:
             gel += self.kappa * barrier.db(self.distances(x), self.dhat)[:, None] \
                 * self.plane_n[None, :]
-        g += self.h ** 2 * gel
+        g += self.ah2 * gel
         g[self.pinned] = 0.0
         return g
 
@@ -95,7 +123,7 @@ class Problem:
         dof = (3 * self.tets[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
         rows = np.repeat(dof, 12, axis=1).ravel()
         cols = np.tile(dof, (1, 12)).ravel()
-        vals = (self.h ** 2 * He).ravel()
+        vals = (self.ah2 * He).ravel()
         diag_idx = np.arange(3 * self.n)
         diag_val = np.repeat(self.mass, 3)
         rows = np.concatenate([rows, diag_idx])
@@ -109,7 +137,7 @@ class Problem:
             c = (3 * act[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1)
             rows = np.concatenate([rows, r.ravel()])
             cols = np.concatenate([cols, c.ravel()])
-            vals = np.concatenate([vals, (self.h ** 2 * k2[act, None, None] * nn[None]).ravel()])
+            vals = np.concatenate([vals, (self.ah2 * k2[act, None, None] * nn[None]).ravel()])
         H = sp.coo_matrix((vals, (rows, cols)), shape=(3 * self.n, 3 * self.n)).tocsr()
         fixed = np.repeat(self.pinned, 3)
         if fixed.any():

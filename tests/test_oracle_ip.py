@@ -136,6 +136,49 @@ def test_cubature_scaled_hessian_is_affine_in_the_scale(contact):
     assert np.abs(D).max() <= 1e-12 * np.abs(H).max()
 
 
+def test_bdf2_free_fall_is_exact():
+    """BDF2 (Eq. IP with alpha = 4/9, Sec. 3.1) is exact for a quadratic
+    trajectory: an undeformed mesh falling freely with exact history
+    (x^{t-1}, v^{t-1}) = (x_0, v_0), (x^t, v^t) = (x_0 + v_0 h + g h^2 / 2,
+    v_0 + g h) lands on x_0 + 2 v_0 h + 2 g h^2 with v_0 + 2 g h.  Every
+    coefficient of the predictor and the velocity update (read from the
+    garbled acceleration formula) enters."""
+    s = synth.tiny_scene(3, 2, 2, seed=5, pinned=False)
+    h = s.dt
+    g = np.asarray(s.gravity, dtype=np.float64)
+    x0 = s.X + np.array([0.3, -0.2, 1.0])
+    v0 = np.tile(np.array([0.5, 0.1, -0.25]), (s.n_verts, 1))
+    xt = x0 + v0 * h + 0.5 * g * h * h
+    vt = v0 + g * h
+    p = ip.Problem(s, x_t=xt, v_t=vt, integrator="bdf2", x_prev=x0, v_prev=v0)
+    assert p.alpha == pytest.approx(4.0 / 9.0, rel=0, abs=0)
+    x1, info = newton.timestep(p)
+    assert np.allclose(x1, x0 + 2 * v0 * h + 2 * g * h * h, rtol=0, atol=1e-12)
+    assert np.allclose(p.velocity(x1), v0 + 2 * g * h, rtol=0, atol=1e-10)
+
+
+def test_bdf2_energy_weights_potentials_by_four_ninths():
+    """E = K + (4/9) h^2 (Psi + B) for BDF2 against the same pieces
+    computed directly, at a deformed state with contact; the step is a
+    minimiser (gradient ~ 0) and its velocity is the BDF2 difference."""
+    s = synth.tiny_scene(3, 2, 2, seed=6, contact=True, pinned=False)
+    h = s.dt
+    rng_l = np.random.default_rng(3)
+    xp = s.x0 + 1e-3 * rng_l.normal(size=s.x0.shape)
+    vp = 0.1 * rng_l.normal(size=s.x0.shape)
+    p = ip.Problem(s, x_t=s.x0, v_t=s.v0, integrator="bdf2", x_prev=xp, v_prev=vp)
+    from oracle import elastic
+    x = p.x_tilde + 2e-4 * rng_l.normal(size=p.x_tilde.shape)
+    x[:, 2] = np.maximum(x[:, 2], 2e-4)
+    K = 0.5 * np.sum(p.mass[:, None] * (x - p.x_tilde) ** 2)
+    Psi = np.sum(elastic.element_energy(x, s.tets, p.vol, p.Dm_inv, p.mu, p.lam))
+    B = p.kappa * np.sum(barrier.b(p.distances(x), p.dhat))
+    assert p.energy(x) == pytest.approx(K + (4.0 / 9.0) * h * h * (Psi + B), rel=1e-13)
+    x1, info = newton.timestep(p)
+    assert np.abs(p.gradient(x1)).max() <= 1e-6 * np.abs(p.gradient(p.x_t)).max()
+    assert np.allclose(p.velocity(x1), (3 * x1 - 4 * s.x0 + xp) / (2 * h), rtol=1e-14, atol=0)
+
+
 # -- Newton timestep -----------------------------------------------------------
 def test_uniform_translation_is_exact():
     """No gravity, no contact, no pins: a rigid translation with velocity v
