@@ -13,7 +13,8 @@ Readings used where the paper is silent:
 * mass: lumped, m_v = sum over tets e containing v of rho_e vol_e / 4;
 * gravity g enters through the predictor, x_tilde += alpha h^2 g
   (equivalent to the potential -M g . x in the alpha h^2-scaled bracket);
-* friction D = 0 (no workload uses friction);
+* friction D = 0 unless ``mu`` > 0 is given (no workload uses friction);
+  then D is the lagged, mollified point-plane friction of ``friction.py``;
 * Dirichlet vertices are held at x^t: they are not unknowns, their inertia
   term is dropped, their gradient entries are zero and their Hessian rows
   and columns are the identity.
@@ -26,14 +27,14 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-from . import barrier, elastic
+from . import barrier, elastic, friction
 
 
 class Problem:
     """One timestep's incremental potential built from a synthetic scene."""
 
     def __init__(self, scene, x_t=None, v_t=None, dt=None, project=True, integrator="ie", x_prev=None,
-                 v_prev=None):
+                 v_prev=None, mu=0.0, eps_v=1e-3):
         self.X = np.asarray(scene.X, dtype=np.float64)
         self.tets = np.asarray(scene.tets, dtype=np.int64)
         self.n = self.X.shape[0]
@@ -70,6 +71,10 @@ class Problem:
             raise ValueError(f"unknown integrator {integrator!r}")
         self.ah2 = self.alpha * self.h ** 2   # the factor on the potentials
         self.x_tilde[self.pinned] = self.x_t[self.pinned]
+        self.friction = None
+        if mu > 0 and self.contact:
+            self.friction = friction.GroundFriction(mu, eps_v, self.h, self.kappa, self.dhat, self.plane_n,
+                                                    self.plane_o, self.x_t)
 
     def velocity(self, x_new):
         """v^{t+1} of the integrator from the step's solution."""
@@ -92,7 +97,8 @@ class Problem:
         B = 0.0
         if self.contact:
             B = self.kappa * np.sum(barrier.b(self.distances(x), self.dhat))
-        return K + self.ah2 * (Psi + B)
+        D = self.friction.energy(x) if self.friction is not None else 0.0
+        return K + self.ah2 * (Psi + B + D)
 
     def gradient(self, x):
         """dE/dx as [n,3]; zero on Dirichlet vertices."""
@@ -104,6 +110,8 @@ class Problem:
         if self.contact:
             gel += self.kappa * barrier.db(self.distances(x), self.dhat)[:, None] \
                 * self.plane_n[None, :]
+        if self.friction is not None:
+            gel += self.friction.gradient(x)
         g += self.ah2 * gel
         g[self.pinned] = 0.0
         return g
@@ -138,6 +146,14 @@ class Problem:
             rows = np.concatenate([rows, r.ravel()])
             cols = np.concatenate([cols, c.ravel()])
             vals = np.concatenate([vals, (self.ah2 * k2[act, None, None] * nn[None]).ravel()])
+        if self.friction is not None:
+            Hf = self.friction.hessian_blocks(x)
+            act = np.nonzero(self.friction.lam > 0)[0]
+            r = (3 * act[:, None, None] + np.arange(3)[None, :, None]).repeat(3, 2)
+            c = (3 * act[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1)
+            rows = np.concatenate([rows, r.ravel()])
+            cols = np.concatenate([cols, c.ravel()])
+            vals = np.concatenate([vals, (self.ah2 * Hf[act]).ravel()])
         H = sp.coo_matrix((vals, (rows, cols)), shape=(3 * self.n, 3 * self.n)).tocsr()
         fixed = np.repeat(self.pinned, 3)
         if fixed.any():
