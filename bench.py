@@ -44,8 +44,8 @@ from paper_2508_13386_gb300.replicas import lpt_shards, max_over_ranks  # noqa: 
 
 # iteration counts of the FP64 block-Jacobi GPU path on this workload, used to
 # scale the oracle sample in the reference arm (the main arm measures them live)
-REF_NEWTON = 4
-REF_PCG = 1000
+REF_NEWTON = 11
+REF_PCG = 1252
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
 # cold-cache ncu capture inside the timed step) of the dominant kernel on the
 # 41^3 lattice, keyed by (kernel, precision); valid for the kernel version it
@@ -102,6 +102,12 @@ def parse():
 def workload(grid):
     import synth
     return synth.lattice_scene(n=grid, seed=3, v_down=1.0)
+
+
+def workload_desc(args, scene):
+    return (f"lattice{args.grid}^3 p=0.55 seed 3: {scene.n_tets} tets, {scene.n_verts} verts, "
+            f"E log-uniform 1e5-1e8 (32 Voronoi cells), ground barrier dhat=1e-3 kappa=1e5, "
+            f"implicit Euler h=1/60, dropped at 1 m/s from 0.05 m (timed steps {args.warmup}..)")
 
 
 def cpu_sample(scene, newton_iters, pcg_iters_per_newton, cg_sample=60):
@@ -230,8 +236,7 @@ def run_reference(args):
     v = float(np.median(vals))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"lattice{args.grid}^3 p=0.55 seed 3, "
-                                                       f"{scene.n_tets} tets, ground barrier, IE h=1/60"},
+            "data": "synthetic", "config": {"workload": workload_desc(args, scene)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -613,9 +618,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32+f64", "bf16": "bf16+f32+f64", "fp64": "f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"lattice{args.grid}^3 p=0.55 seed 3: {scene.n_tets} tets, {scene.n_verts} verts, "
-                               f"E log-uniform 1e5-1e8 (32 Voronoi cells), ground barrier dhat=1e-3 kappa=1e5, "
-                               f"implicit Euler h=1/60, dropped at 1 m/s from 0.05 m (timed steps {args.warmup}..)",
+        "config": {"workload": workload_desc(args, scene),
                    "solver": f"{args.precision} two-level PCG ({args.cycle}, "
                              + (f"omega {args.omega:g}), " if args.omega > 0 else "omega 0.9 x 2 / Lanczos lambda_max(D^-1 H)), ")
                              + f"SMS basis m={len(B['origins'])} "
