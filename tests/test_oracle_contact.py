@@ -1,0 +1,154 @@
+"""Pins for the oracle's mesh-mesh contact primitives (no GPU): closest
+distances against dense sampling and closed forms, the barrier gradient
+against finite differences, and the conservative CCD against exact times of
+impact."""
+import numpy as np
+import pytest
+
+from oracle import contact
+
+rng = np.random.default_rng(21)
+
+
+def _tri_samples(a, b, c, k=120):
+    u, v = np.meshgrid(np.linspace(0, 1, k), np.linspace(0, 1, k))
+    m = (u + v) <= 1
+    u, v = u[m], v[m]
+    return a[None] + u[:, None] * (b - a)[None] + v[:, None] * (c - a)[None]
+
+
+def test_point_triangle_distance_against_sampling():
+    for _ in range(60):
+        a, b, c = rng.normal(size=(3, 3))
+        p = rng.normal(size=3) * 1.5
+        d = contact.point_triangle_distance(p, a, b, c)
+        S = _tri_samples(a, b, c)
+        ds = np.linalg.norm(S - p, axis=1).min()
+        assert d <= ds + 1e-12                      # no sample is closer
+        h = max(np.linalg.norm(b - a), np.linalg.norm(c - a)) / 119
+        assert ds - d <= 2 * h                      # and the sampling gets within its spacing
+
+
+def test_point_triangle_closed_forms():
+    a, b, c = np.array([0.0, 0, 0]), np.array([1.0, 0, 0]), np.array([0.0, 1, 0])
+    assert contact.point_triangle_distance([0.2, 0.3, 0.7], a, b, c) == pytest.approx(0.7, abs=1e-15)
+    assert contact.point_triangle_distance([-1.0, -1.0, 0.0], a, b, c) == pytest.approx(np.sqrt(2), abs=1e-15)
+    assert contact.point_triangle_distance([1.0, 1.0, 0.0], a, b, c) == pytest.approx(np.sqrt(0.5), abs=1e-15)
+    assert contact.point_triangle_distance([0.5, -2.0, 1.0], a, b, c) == pytest.approx(np.sqrt(5), abs=1e-15)
+
+
+def test_edge_edge_distance_against_sampling_and_closed_forms():
+    t = np.linspace(0, 1, 401)
+    for _ in range(60):
+        p0, p1, q0, q1 = rng.normal(size=(4, 3))
+        d = contact.edge_edge_distance(p0, p1, q0, q1)
+        P = p0[None] + t[:, None] * (p1 - p0)[None]
+        Q = q0[None] + t[:, None] * (q1 - q0)[None]
+        ds = np.linalg.norm(P[:, None] - Q[None], axis=2).min()
+        assert d <= ds + 1e-12
+        assert ds - d <= (np.linalg.norm(p1 - p0) + np.linalg.norm(q1 - q0)) / 400
+    # skew and perpendicular, offset 0.5; parallel, separation 0.3; crossing
+    assert contact.edge_edge_distance([0, 0, 0], [1, 0, 0], [0.5, -1, 0.5], [0.5, 1, 0.5]) == pytest.approx(0.5)
+    assert contact.edge_edge_distance([0, 0, 0], [1, 0, 0], [0.2, 0.3, 0], [2.0, 0.3, 0]) == pytest.approx(0.3)
+    assert contact.edge_edge_distance([0, 0, 0], [1, 0, 0], [0.5, -1, 0], [0.5, 1, 0]) == pytest.approx(0.0, abs=1e-15)
+    # segments whose lines meet outside both: endpoint to endpoint
+    assert contact.edge_edge_distance([0, 0, 0], [1, 0, 0], [2, 1, 0], [2, 3, 0]) == pytest.approx(np.sqrt(2))
+
+
+def test_boundary_faces_of_one_tet_and_two_glued_tets():
+    assert len(contact.boundary_faces(np.array([[0, 1, 2, 3]]))) == 4
+    f = contact.boundary_faces(np.array([[0, 1, 2, 3], [1, 2, 3, 4]]))
+    assert len(f) == 6 and not any(set(r) == {1, 2, 3} for r in f.tolist())
+    assert len(contact.face_edges(f)) == 9
+
+
+def _two_tets(gap):
+    """Two separate tets (bodies 0 and 1), the second above the first with a
+    vertex pointing down at the first's top face; ``gap`` between them."""
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0.3, 0.3, -0.5],
+                  [0.3, 0.3, 0], [1.3, 0.3, 0.6], [0.3, 1.3, 0.6], [0.6, 0.6, 0.9]], dtype=np.float64)
+    X[4:, 2] += gap
+    X[4:, :2] += np.array([0.02, -0.01])
+    tets = np.array([[0, 1, 2, 3], [4, 5, 6, 7]])
+    body = np.array([0, 0, 0, 0, 1, 1, 1, 1])
+    return X, tets, body
+
+
+def test_pair_gradient_matches_finite_differences():
+    dhat, kappa = 0.05, 1e3
+    X, tets, body = _two_tets(0.01)
+    X = X + 1e-3 * rng.normal(size=X.shape)
+    faces = contact.boundary_faces(tets)
+    edges = contact.face_edges(faces)
+    pt, ee = contact.contact_pairs(X, faces, edges, body, dhat)
+    assert len(pt) + len(ee) > 0
+    g = contact.pair_gradient(X, faces, edges, pt, ee, kappa, dhat)
+    e = 1e-7
+    for v in range(len(X)):
+        for c in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[v, c] += e
+            Xm[v, c] -= e
+            fd = (contact.pair_energy(Xp, faces, edges, pt, ee, kappa, dhat)
+                  - contact.pair_energy(Xm, faces, edges, pt, ee, kappa, dhat)) / (2 * e)
+            assert fd == pytest.approx(g[v, c], rel=1e-5, abs=1e-6 * np.abs(g).max())
+    # Newton's third law: the pair forces sum to zero
+    assert np.allclose(g.sum(axis=0), 0, atol=1e-9 * np.abs(g).max())
+
+
+def test_ccd_exact_time_of_impact():
+    """A point falling at constant speed onto a resting triangle from height
+    h0 by a displacement 2 h0: with s = 0.1 the admissible fraction is the
+    time at which the height is 0.1 h0, exactly (the rate bound is exact for
+    a pure translation)."""
+    f = lambda P: contact.point_triangle_distance(*P)
+    xs0 = np.array([[0.2, 0.2, 0.8], [0, 0, 0], [1, 0, 0], [0, 1, 0]])
+    dxs = np.zeros_like(xs0)
+    dxs[0, 2] = -1.6
+    assert contact.ccd_pair(f, xs0, dxs, 1, s=0.1) == pytest.approx(0.45, abs=1e-9)
+    # moving away or parallel: the whole step
+    dxs[0, 2] = +1.0
+    assert contact.ccd_pair(f, xs0, dxs, 1) == 1.0
+    # two edges closing head on: distance 1 shrinking at rate 4 -> 0.1 at t = 0.225
+    g = lambda P: contact.edge_edge_distance(*P)
+    xs = np.array([[0, 0, 0], [1, 0, 0], [0.5, -1, 1], [0.5, 1, 1]], dtype=np.float64)
+    dx = np.array([[0, 0, 2], [0, 0, 2], [0, 0, -2], [0, 0, -2]], dtype=np.float64)
+    assert contact.ccd_pair(g, xs, dx, 2, s=0.1) == pytest.approx(0.225, abs=1e-9)
+
+
+def test_ccd_step_keeps_every_pair_apart():
+    """Random displacements of two nearby tets closing on each other: along
+    the returned fraction of the step, no point-triangle or edge-edge pair of
+    different bodies gets closer than s times its starting distance (checked
+    on a fine sampling of the path).  The fraction is conservative: the rate
+    bound over-estimates how fast rotating primitives close, so the cut may
+    come before the first sampled violation, never after it."""
+    s = 0.1
+    for trial in range(4):
+        X, tets, body = _two_tets(0.02)
+        faces = contact.boundary_faces(tets)
+        edges = contact.face_edges(faces)
+        dx = np.zeros_like(X)
+        dx[4:] = np.array([0.0, 0.0, -0.3]) + 0.05 * rng.normal(size=(4, 3))
+        alpha = contact.ccd_step(X, dx, faces, edges, body, s=s)
+        assert 0 < alpha < 1
+
+        def min_ratio(t):
+            r = np.inf
+            Xt = X + t * dx
+            for v in np.unique(faces):
+                for f in faces:
+                    if body[v] != body[f[0]]:
+                        r = min(r, contact.point_triangle_distance(Xt[v], *Xt[f])
+                                / contact.point_triangle_distance(X[v], *X[f]))
+            for i in range(len(edges)):
+                for j in range(i + 1, len(edges)):
+                    if body[edges[i][0]] != body[edges[j][0]]:
+                        r = min(r, contact.edge_edge_distance(*Xt[edges[i]], *Xt[edges[j]])
+                                / contact.edge_edge_distance(*X[edges[i]], *X[edges[j]]))
+            return r
+
+        assert min(min_ratio(t) for t in np.linspace(0, alpha, 25)) >= s * (1 - 1e-9)
+        ts = np.linspace(0, 1, 201)
+        bad = [t for t in ts if min_ratio(t) < s]
+        assert not bad or alpha <= bad[0]
