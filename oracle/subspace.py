@@ -139,3 +139,43 @@ def paper_direction(H, g, U, n_cg):
     # iteration count has nothing left to do)
     df, _ = opcg.pcg(lambda v: H @ v, r, lambda v: Dinv @ v, rtol=1e-14, max_iter=n_cg)
     return np.asarray(ds).ravel(), df
+
+
+def handle_block_jacobi(A, block=12):
+    """Inverse of the 12 x 12 diagonal blocks of a subspace matrix, the
+    preconditioner of the subspace PCG solves (Sec. 3.7.1: one block per
+    handle's degrees of freedom), as a function v -> D^{-1} v."""
+    A = sp.csr_matrix(A) if sp.issparse(A) else sp.csr_matrix(np.asarray(A))
+    r = A.shape[0]
+    inv = [np.linalg.inv(A[k:k + block, k:k + block].toarray()) for k in range(0, r, block)]
+
+    def apply(v):
+        v = np.asarray(v, dtype=np.float64)
+        return np.concatenate([Bi @ v[k * block:(k + 1) * block] for k, Bi in enumerate(inv)])
+    return apply
+
+
+def subspace_direction_literal(H, g, Ua, Us, rtol=1e-4):
+    """SolveSubspaceDirection of Alg. 2 as printed, both levels by PCG:
+
+        (Ua^T H Ua) q_a = Ua^T (-g)        PCG, 12 x 12 block Jacobi, to rtol
+        d_s = Ua q_a;  r = -g - H d_s
+        (Us^T H Us) q_s = Us^T r           PCG, 12 x 12 block Jacobi, to rtol
+        d_s = d_s + Us q_s
+
+    The subspace products are matrix-free, U^T (H (U q)) (Sec. 3.7.1).
+    (The printed algorithm writes g for the right-hand side; the direction
+    of descent takes -g.)  Returns (d_s flat, (iters_a, iters_s))."""
+    from . import pcg as opcg
+    g = np.asarray(g, dtype=np.float64).ravel()
+    out_iters = []
+    ds = np.zeros_like(g)
+    r = -g
+    for U in (Ua, Us):
+        A_blocks = galerkin(H, U)               # only its diagonal blocks are used, as the preconditioner
+        Minv = handle_block_jacobi(A_blocks)
+        q, info = opcg.pcg(lambda v: U.T @ (H @ (U @ v)), U.T @ r, Minv, rtol=rtol, max_iter=100000)
+        ds = ds + U @ q
+        r = -g - H @ ds
+        out_iters.append(info["iters"])
+    return ds, tuple(out_iters)
