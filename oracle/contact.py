@@ -238,3 +238,173 @@ def ccd_step(x, dx, faces, edges, body, s=0.1):
             idx = np.array([*edges[i], *edges[j]])
             alpha = min(alpha, ccd_pair(lambda P: edge_edge_distance(*P), x[idx], dx[idx], 2, s))
     return alpha
+
+
+# ---- exact second derivatives: hyper-dual numbers ------------------------------------------------
+class _HD:
+    """Hyper-dual number r + a e1 + b e2 + c e1 e2 (e1^2 = e2^2 = 0): evaluating
+    f at x + e1 u + e2 v gives f(x), the directional derivatives along u and
+    v, and u^T (d2 f) v exactly, with no truncation error."""
+
+    __slots__ = ("r", "a", "b", "c")
+
+    def __init__(self, r, a=0.0, b=0.0, c=0.0):
+        self.r, self.a, self.b, self.c = r, a, b, c
+
+    def __add__(self, o):
+        if not isinstance(o, _HD):
+            return _HD(self.r + o, self.a, self.b, self.c)
+        return _HD(self.r + o.r, self.a + o.a, self.b + o.b, self.c + o.c)
+
+    __radd__ = __add__
+
+    def __neg__(self):
+        return _HD(-self.r, -self.a, -self.b, -self.c)
+
+    def __sub__(self, o):
+        return self + (-o)
+
+    def __rsub__(self, o):
+        return (-self) + o
+
+    def __mul__(self, o):
+        if not isinstance(o, _HD):
+            return _HD(self.r * o, self.a * o, self.b * o, self.c * o)
+        return _HD(self.r * o.r, self.r * o.a + self.a * o.r, self.r * o.b + self.b * o.r,
+                   self.r * o.c + self.a * o.b + self.b * o.a + self.c * o.r)
+
+    __rmul__ = __mul__
+
+    def inv(self):
+        r = 1.0 / self.r
+        return _HD(r, -self.a * r * r, -self.b * r * r, -self.c * r * r + 2.0 * self.a * self.b * r * r * r)
+
+    def __truediv__(self, o):
+        return self * (o.inv() if isinstance(o, _HD) else 1.0 / o)
+
+    def sqrt(self):
+        s = np.sqrt(self.r)
+        return _HD(s, self.a / (2 * s), self.b / (2 * s), self.c / (2 * s) - self.a * self.b / (4 * s * s * s))
+
+
+def _dot(u, v):
+    return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]
+
+
+def _cross(u, v):
+    return [u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]]
+
+
+def _sub(u, v):
+    return [u[k] - v[k] for k in range(3)]
+
+
+def _norm(u):
+    return _dot(u, u).sqrt()
+
+
+def _d_pp(P):            # point-point
+    return _norm(_sub(P[0], P[1]))
+
+
+def _d_pe(P):            # point P0 to the line through P1 P2
+    e = _sub(P[2], P[1])
+    return _norm(_cross(_sub(P[0], P[1]), e)) / _norm(e)
+
+
+def _d_pt(P, sgn):       # point P0 to the plane of P1 P2 P3 (sgn: side of P0)
+    n = _cross(_sub(P[2], P[1]), _sub(P[3], P[1]))
+    return _dot(_sub(P[0], P[1]), n) * sgn / _norm(n)
+
+
+def _d_ee(P, sgn):       # line P0 P1 to line P2 P3 (sgn: sign of the triple product)
+    n = _cross(_sub(P[1], P[0]), _sub(P[3], P[2]))
+    return _dot(_sub(P[2], P[0]), n) * sgn / _norm(n)
+
+
+def _derivatives(fn, X):
+    """Value, gradient and Hessian of fn over the stacked coordinates of the
+    vertices X [k, 3], evaluated once on (m x m) arrays of hyper-dual parts."""
+    X = np.asarray(X, dtype=np.float64)
+    m = X.size
+    I = np.eye(m)
+    ones = np.ones(m)
+    flat = X.ravel()
+    P = [[_HD(np.full((m, m), flat[3 * i + c]), np.outer(I[:, 3 * i + c], ones), np.outer(ones, I[:, 3 * i + c]),
+              np.zeros((m, m))) for c in range(3)] for i in range(len(X))]
+    f = fn(P)
+    return float(f.r[0, 0]), f.a[:, 0].copy(), 0.5 * (f.c + f.c.T)
+
+
+def _pt_type(p, a, b, c):
+    """The closest feature of triangle abc to p: ('pt',), ('pe', i, j) or ('pp', i)
+    with local indices 0..2 of the triangle's vertices."""
+    q = closest_point_triangle(p, a, b, c)
+    w = _triangle_weights(q, a, b, c)
+    zero = np.abs(w) <= 1e-12
+    if not zero.any():
+        return ("pt",)
+    if zero.sum() == 1:
+        i, j = [k for k in range(3) if not zero[k]]
+        return ("pe", i, j)
+    return ("pp", int(np.argmax(w)))
+
+
+def _ee_type(p0, p1, q0, q1):
+    """('ee',) or a reduced pair: ('pe', point, seg_a, seg_b) / ('pp', i, j)
+    with local indices 0..3 (p0, p1, q0, q1)."""
+    y, z = closest_points_segments(p0, p1, q0, q1)
+    s = _segment_weight(y, p0, p1)
+    t = _segment_weight(z, q0, q1)
+    s_end = s <= 1e-12 or s >= 1 - 1e-12
+    t_end = t <= 1e-12 or t >= 1 - 1e-12
+    if not s_end and not t_end:
+        return ("ee",)
+    if s_end and t_end:
+        return ("pp", 0 if s < 0.5 else 1, 2 if t < 0.5 else 3)
+    if s_end:
+        return ("pe", 0 if s < 0.5 else 1, 2, 3)
+    return ("pe", 2 if t < 0.5 else 3, 0, 1)
+
+
+def pair_distance_derivatives(kind, X):
+    """Distance of a point-triangle (kind 'pt', X = [p, a, b, c]) or
+    edge-edge (kind 'ee', X = [p0, p1, q0, q1]) pair with its gradient and
+    Hessian over the 12 stacked coordinates, from the formula of the closest
+    feature (plane, line or point) evaluated in hyper-dual numbers."""
+    X = np.asarray(X, dtype=np.float64)
+    if kind == "pt":
+        t = _pt_type(*X)
+        if t[0] == "pt":
+            n = np.cross(X[2] - X[1], X[3] - X[1])
+            sgn = 1.0 if (X[0] - X[1]) @ n >= 0 else -1.0
+            return _derivatives(lambda P: _d_pt(P, sgn), X)
+        idx = [0, 1 + t[1], 1 + t[2]] if t[0] == "pe" else [0, 1 + t[1]]
+    else:
+        t = _ee_type(*X)
+        if t[0] == "ee":
+            n = np.cross(X[1] - X[0], X[3] - X[2])
+            sgn = 1.0 if (X[2] - X[0]) @ n >= 0 else -1.0
+            return _derivatives(lambda P: _d_ee(P, sgn), X)
+        idx = list(t[1:])
+    sub = X[idx]
+    val, g_sub, H_sub = _derivatives(_d_pe if len(idx) == 3 else _d_pp, sub)
+    g = np.zeros(12)
+    H = np.zeros((12, 12))
+    cols = np.concatenate([np.arange(3 * k, 3 * k + 3) for k in idx])
+    g[cols] = g_sub
+    H[np.ix_(cols, cols)] = H_sub
+    return val, g, H
+
+
+def pair_barrier_hessian(kind, X, kappa, dhat, project=True):
+    """kappa (b''(d) grad d grad d^T + b'(d) Hess d) over the pair's 12
+    coordinates, projected to the positive semi-definite cone per pair
+    (eigenvalues clamped at zero) unless project is False."""
+    d, g, Hd = pair_distance_derivatives(kind, X)
+    da = np.array([d])
+    H = kappa * (barrier.d2b(da, dhat)[0] * np.outer(g, g) + barrier.db(da, dhat)[0] * Hd)
+    if project:
+        w, V = np.linalg.eigh(0.5 * (H + H.T))
+        H = (V * np.maximum(w, 0.0)) @ V.T
+    return H

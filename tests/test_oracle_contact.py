@@ -152,3 +152,57 @@ def test_ccd_step_keeps_every_pair_apart():
         ts = np.linspace(0, 1, 201)
         bad = [t for t in ts if min_ratio(t) < s]
         assert not bad or alpha <= bad[0]
+
+
+def _configs():
+    """Point-triangle and edge-edge pairs whose closest features are, in
+    turn, the plane / the two lines, a line, and a point."""
+    tri = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=np.float64)
+    yield "pt", np.vstack([[0.2, 0.3, 0.05], tri])                 # over the face
+    yield "pt", np.vstack([[0.5, -0.2, 0.05], tri])                # beside edge 0-1
+    yield "pt", np.vstack([[-0.2, -0.1, 0.05], tri])               # beyond vertex 0
+    yield "ee", np.array([[0, 0, 0], [1, 0, 0], [0.4, -1, 0.05], [0.6, 1, 0.05]], dtype=np.float64)
+    yield "ee", np.array([[0, 0, 0], [1, 0, 0], [1.2, -1, 0.05], [1.3, 1, 0.05]], dtype=np.float64)
+    yield "ee", np.array([[0, 0, 0], [1, 0, 0], [1.2, 0.1, 0.05], [2.0, 0.5, 0.05]], dtype=np.float64)
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_pair_distance_derivatives_match_finite_differences(case):
+    kind, X = list(_configs())[case]
+    X = X + 1e-4 * rng.normal(size=X.shape)
+    dist = (lambda Y: contact.point_triangle_distance(*Y.reshape(4, 3))) if kind == "pt" else \
+        (lambda Y: contact.edge_edge_distance(*Y.reshape(4, 3)))
+    d, g, H = contact.pair_distance_derivatives(kind, X)
+    x = X.ravel()
+    assert d == pytest.approx(dist(x), rel=1e-13)
+    e = 1e-6
+    E = np.eye(12)
+    fd = np.array([(dist(x + e * E[k]) - dist(x - e * E[k])) / (2 * e) for k in range(12)])
+    assert np.allclose(fd, g, rtol=0, atol=1e-8)
+    gfun = lambda Y: contact.pair_distance_derivatives(kind, Y.reshape(4, 3))[1]
+    fdH = np.array([(gfun(x + e * E[k]) - gfun(x - e * E[k])) / (2 * e) for k in range(12)])
+    assert np.allclose(fdH, H, rtol=0, atol=1e-5 * max(np.abs(H).max(), 1.0))
+    assert np.allclose(H, H.T, atol=1e-14 * max(np.abs(H).max(), 1.0))
+    # a rigid translation changes no distance
+    for c in range(3):
+        t = np.tile(np.eye(3)[c], 4)
+        assert abs(g @ t) <= 1e-12 and np.abs(H @ t).max() <= 1e-9 * max(np.abs(H).max(), 1.0)
+
+
+def test_pair_barrier_hessian_is_the_gradients_derivative_then_projected():
+    kind, X = list(_configs())[0]
+    dhat, kappa = 0.1, 1e3
+    faces = np.array([[1, 2, 3]])
+    edges = np.zeros((0, 2), dtype=np.int64)
+    H = contact.pair_barrier_hessian(kind, X, kappa, dhat, project=False)
+    e = 1e-7
+    x = X.ravel()
+    gb = lambda Y: contact.pair_gradient(Y.reshape(4, 3), faces, edges, [(0, 0)], [], kappa, dhat).ravel()
+    fdH = np.array([(gb(x + e * np.eye(12)[k]) - gb(x - e * np.eye(12)[k])) / (2 * e) for k in range(12)])
+    assert np.allclose(fdH, H, rtol=1e-5, atol=1e-6 * np.abs(H).max())
+    Hp = contact.pair_barrier_hessian(kind, X, kappa, dhat)
+    w = np.linalg.eigvalsh(Hp)
+    assert w.min() >= -1e-9 * w.max() and np.allclose(Hp, Hp.T)
+    # the projection keeps the non-negative part of the spectrum
+    w0 = np.linalg.eigvalsh(H)
+    assert np.allclose(np.sort(w), np.sort(np.maximum(w0, 0)), atol=1e-9 * np.abs(w0).max())
