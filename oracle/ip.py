@@ -27,14 +27,14 @@ from __future__ import annotations
 import numpy as np
 import scipy.sparse as sp
 
-from . import barrier, elastic, friction
+from . import barrier, contact, elastic, friction
 
 
 class Problem:
     """One timestep's incremental potential built from a synthetic scene."""
 
     def __init__(self, scene, x_t=None, v_t=None, dt=None, project=True, integrator="ie", x_prev=None,
-                 v_prev=None, mu=0.0, eps_v=1e-3):
+                 v_prev=None, mu=0.0, eps_v=1e-3, body=None):
         self.X = np.asarray(scene.X, dtype=np.float64)
         self.tets = np.asarray(scene.tets, dtype=np.int64)
         self.n = self.X.shape[0]
@@ -71,6 +71,11 @@ class Problem:
             raise ValueError(f"unknown integrator {integrator!r}")
         self.ah2 = self.alpha * self.h ** 2   # the factor on the potentials
         self.x_tilde[self.pinned] = self.x_t[self.pinned]
+        # mesh-mesh contact between the bodies ``body`` labels (contact.py)
+        self.body = None if body is None else np.asarray(body, dtype=np.int64)
+        if self.body is not None:
+            self.faces = contact.boundary_faces(self.tets)
+            self.edges = contact.face_edges(self.faces)
         self.friction = None
         if mu > 0 and self.contact:
             self.friction = friction.GroundFriction(mu, eps_v, self.h, self.kappa, self.dhat, self.plane_n,
@@ -98,7 +103,14 @@ class Problem:
         if self.contact:
             B = self.kappa * np.sum(barrier.b(self.distances(x), self.dhat))
         D = self.friction.energy(x) if self.friction is not None else 0.0
+        if self.body is not None:
+            pt, ee = self.pairs(x)
+            B = B + contact.pair_energy(x, self.faces, self.edges, pt, ee, self.kappa, self.dhat)
         return K + self.ah2 * (Psi + B + D)
+
+    def pairs(self, x):
+        """Mesh-mesh pairs of different bodies closer than dhat at x."""
+        return contact.contact_pairs(x, self.faces, self.edges, self.body, self.dhat)
 
     def gradient(self, x):
         """dE/dx as [n,3]; zero on Dirichlet vertices."""
@@ -112,6 +124,9 @@ class Problem:
                 * self.plane_n[None, :]
         if self.friction is not None:
             gel += self.friction.gradient(x)
+        if self.body is not None:
+            pt, ee = self.pairs(x)
+            gel += contact.pair_gradient(x, self.faces, self.edges, pt, ee, self.kappa, self.dhat)
         g += self.ah2 * gel
         g[self.pinned] = 0.0
         return g
@@ -146,6 +161,16 @@ class Problem:
             rows = np.concatenate([rows, r.ravel()])
             cols = np.concatenate([cols, c.ravel()])
             vals = np.concatenate([vals, (self.ah2 * k2[act, None, None] * nn[None]).ravel()])
+        if self.body is not None:
+            pt, ee = self.pairs(x)
+            items = [("pt", np.array([v, *self.faces[k]])) for v, k in pt]
+            items += [("ee", np.array([*self.edges[i], *self.edges[j]])) for i, j in ee]
+            for kind, vids in items:
+                Hp = contact.pair_barrier_hessian(kind, x[vids], self.kappa, self.dhat)
+                dof = (3 * vids[:, None] + np.arange(3)[None, :]).ravel()
+                rows = np.concatenate([rows, np.repeat(dof, 12)])
+                cols = np.concatenate([cols, np.tile(dof, 12)])
+                vals = np.concatenate([vals, (self.ah2 * Hp).ravel()])
         if self.friction is not None:
             Hf = self.friction.hessian_blocks(x)
             act = np.nonzero(self.friction.lam > 0)[0]
@@ -164,11 +189,15 @@ class Problem:
         return H
 
     def feasible(self, x):
-        """True when every tet has J > 0 and, with contact, every vertex is
-        strictly above the plane."""
+        """True when every tet has J > 0, with contact every vertex is
+        strictly above the plane, and with bodies no two of them touch."""
         F = elastic.deformation_gradient(x, self.tets, self.Dm_inv)
         if np.any(np.linalg.det(F) <= 0):
             return False
         if self.contact and np.any(self.distances(x) <= 0):
             return False
+        if self.body is not None:
+            pt, ee = contact.contact_pairs(x, self.faces, self.edges, self.body, 1e-300)
+            if pt or ee:          # touching pairs (the CCD filter keeps them from crossing)
+                return False
         return True

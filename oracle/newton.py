@@ -47,16 +47,21 @@ def solve_spd(H, rhs, method="auto", rtol=1e-13):
 
 
 def ccd_step_bound(prob, x, d):
-    """Largest step fraction allowed by the point-plane CCD filter:
-    min(1, 0.9 * min over approaching vertices of dist_v / (-n . d_v))."""
-    if not prob.contact:
-        return 1.0
-    dist = prob.distances(x)
-    nd = d @ prob.plane_n
-    app = nd < 0
-    if not np.any(app):
-        return 1.0
-    return float(min(1.0, CCD_FRACTION * np.min(dist[app] / (-nd[app]))))
+    """Largest step fraction allowed by the CCD filter: for the plane,
+    min(1, 0.9 * min over approaching vertices of dist_v / (-n . d_v)); with
+    bodies, also the mesh-mesh conservative advancement keeping every pair
+    at >= 0.1 of its distance (contact.ccd_step)."""
+    alpha = 1.0
+    if prob.contact:
+        dist = prob.distances(x)
+        nd = d @ prob.plane_n
+        app = nd < 0
+        if np.any(app):
+            alpha = float(min(1.0, CCD_FRACTION * np.min(dist[app] / (-nd[app]))))
+    if getattr(prob, "body", None) is not None:
+        from . import contact
+        alpha = min(alpha, contact.ccd_step(x, d, prob.faces, prob.edges, prob.body, s=1.0 - CCD_FRACTION))
+    return alpha
 
 
 ROUNDING_REGIME = 1e-13
@@ -78,8 +83,13 @@ def line_search(prob, x, d, g, E0):
 
 
 def initial_guess(prob):
-    """x_tilde with Dirichlet vertices at x^t; x^t if x_tilde is infeasible."""
+    """x_tilde with Dirichlet vertices at x^t; x^t if x_tilde is infeasible.
+    With mesh-mesh contact the path from x^t to x_tilde is first cut by the
+    CCD filter (a straight move could pass one body through another)."""
     x0 = prob.x_tilde.copy()
+    if getattr(prob, "body", None) is not None:
+        a = ccd_step_bound(prob, prob.x_t, x0 - prob.x_t)
+        x0 = prob.x_t + a * (x0 - prob.x_t)
     if prob.feasible(x0):
         return x0
     return prob.x_t.copy()

@@ -20,6 +20,7 @@ from .workloads import (  # noqa: F401
     lattice_scene,
     batched_lattice_scenes,
     tiny_scene,
+    two_block_scene,
     random_sparse_basis,
     mlp_init,
 )

@@ -159,6 +159,30 @@ def tiny_scene(nx: int = 3, ny: int = 2, nz: int = 2, seed: int = 0, contact: bo
                  dt=1.0 / 60.0, contact=contact)
 
 
+def two_block_scene(gap: float = 0.01, speed: float = 1.0, seed: int = 0):
+    """Two separate blocks of 2 x 2 x 1 voxels (edge 0.1 m), one above the
+    other with ``gap`` between them and a small horizontal offset; the upper
+    block moves down at ``speed`` m/s, the lower one rests.  No gravity, no
+    ground plane, no pins (a mesh-mesh contact input).  Returns (scene,
+    body) with ``body`` [n] the block of each vertex."""
+    lower = kuhn_voxel_mesh(np.ones((2, 2, 1), dtype=bool), voxel=0.1)
+    upper_X = lower.X + np.array([0.013, -0.007, 0.1 + gap])
+    n0 = lower.n_verts
+    X = np.vstack([lower.X, upper_X])
+    tets = np.vstack([lower.tets, lower.tets + n0]).astype(np.int32)
+    mesh = Mesh(X=X, tets=tets, lattice_index=np.vstack([lower.lattice_index, lower.lattice_index]),
+                voxel_of_tet=np.concatenate([lower.voxel_of_tet, lower.voxel_of_tet]))
+    t = len(tets)
+    v0 = np.zeros_like(X)
+    v0[n0:, 2] = -speed
+    body = np.concatenate([np.zeros(n0, np.int64), np.ones(n0, np.int64)])
+    scene = Scene(name=f"two_blocks_g{gap:g}_v{speed:g}", mesh=mesh, E=np.full(t, 1e5),
+                  nu=np.full(t, 0.4), rho=np.full(t, 1000.0), dirichlet=np.zeros(len(X), np.uint8),
+                  x0=X.copy(), v0=v0, dt=1.0 / 60.0, gravity=(0.0, 0.0, 0.0), contact=False,
+                  dhat=1e-3, kappa=1e5, meta={"seed": seed})
+    return scene, body
+
+
 def random_sparse_basis(X: np.ndarray, m: int, k: int, seed: int):
     """A synthetic sparse handle basis for kernel tests (not the paper's
     construction): ``m`` handle origins at random vertices, each vertex tied

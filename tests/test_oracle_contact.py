@@ -206,3 +206,56 @@ def test_pair_barrier_hessian_is_the_gradients_derivative_then_projected():
     # the projection keeps the non-negative part of the spectrum
     w0 = np.linalg.eigvalsh(H)
     assert np.allclose(np.sort(w), np.sort(np.maximum(w0, 0)), atol=1e-9 * np.abs(w0).max())
+
+
+def test_problem_with_mesh_contact_gradient_and_collision_step():
+    """Eq. IP with the mesh-mesh barrier: the gradient is the derivative of
+    E near contact, and a step of a block driven into another ends at a
+    minimiser with the blocks apart, where the same step without the
+    barrier passes one into the other."""
+    import synth
+    from oracle import ip, newton
+    s, body = synth.two_block_scene(gap=0.004, speed=0.6)
+    p = ip.Problem(s, body=body)
+    n0 = int((body == 0).sum())
+    # near contact: the upper block lowered to 0.5 mm above the lower one
+    x = s.x0.copy()
+    x[n0:, 2] -= 0.0035
+    x += 1e-5 * rng.normal(size=x.shape)
+    pt, ee = p.pairs(x)
+    assert pt or ee
+    g = p.gradient(x)
+    e = 1e-8
+    near = np.unique([v for v, _ in pt] + [int(w) for i, j in ee for w in (*p.edges[i], *p.edges[j])])
+    for v in list(near[:6]) + [0, len(x) - 1]:
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, c] += e
+            xm[v, c] -= e
+            fd = (p.energy(xp) - p.energy(xm)) / (2 * e)
+            assert fd == pytest.approx(g[v, c], rel=1e-4, abs=1e-6 * np.abs(g).max())
+    H = p.hessian(x).toarray()
+    assert np.allclose(H, H.T, atol=1e-12 * np.abs(H).max())
+    assert np.linalg.eigvalsh(H).min() > 0
+    # the collision step
+    x1, info = newton.timestep(p)
+    assert p.feasible(x1)
+    assert np.abs(p.gradient(x1)).max() <= 1e-6 * max(np.abs(p.gradient(s.x0)).max(), 1e-300) + 1e-9
+    assert _vertices_inside_other_body(x1, s.tets, body) == 0
+    x_free, _ = newton.timestep(ip.Problem(s))
+    assert _vertices_inside_other_body(x_free, s.tets, body) > 0
+
+
+def _vertices_inside_other_body(x, tets, body):
+    """How many vertices lie strictly inside a tet of another body."""
+    count = 0
+    for v in range(len(x)):
+        for t in tets:
+            if body[t[0]] == body[v]:
+                continue
+            T = np.stack([x[t[1]] - x[t[0]], x[t[2]] - x[t[0]], x[t[3]] - x[t[0]]], axis=1)
+            lam = np.linalg.solve(T, x[v] - x[t[0]])
+            if lam.min() > 0 and lam.sum() < 1:
+                count += 1
+                break
+    return count
