@@ -2,10 +2,12 @@
 // preconditioned conjugate gradient loop on it (the Newton linear solve
 // H d = -g of Eq. 5, preconditioned as in Sec. 3.7).
 //
-// PCG runs entirely on the device: the scalars alpha, beta, r.z, |r|^2 live in
-// device memory and are produced by the last block of each reduction, so one
-// iteration is two (block Jacobi) or more (two-level) kernel launches with no
-// host round trip.  The direction update p = z + beta p is folded into the
+// PCG runs entirely on the device: the dot products p.q, r.r and r.z are
+// order-independent fixed-point sums that every block adds to with
+// fire-and-forget atomics, and the kernel that needs alpha or beta rebuilds it
+// from the sum (one thread per block), so one iteration is two (block
+// Jacobi) or more (two-level) kernel launches with no host round trip and no
+// arrival counter.  The direction update p = z + beta p is folded into the
 // product kernel through q = H p = H z + beta q_old, so the kernel that reads
 // neighbours (the product) needs only z, which is complete when it starts.
 // Dot products and norms accumulate in float64 in every precision mode.
