@@ -125,3 +125,41 @@ def timestep(prob, xtol_rel=1e-12, max_iter=100, method="auto", x_init=None):
         x = x + alpha * d
     info["gnorm_final"] = float(np.linalg.norm(prob.gradient(x)))
     return x, info
+
+
+def paper_timestep(prob, U, n_cg=20, tol=1e-3, max_iter=100):
+    """The paper's inexact multilevel timestep (Alg. 1 with Alg. 2's
+    directions, Sec. 3.9), as the readings of this oracle state it:
+
+    * each iteration: d_s = U (U^T H U)^{-1} U^T (-g) (the subspace levels
+      solved exactly, reading 10), d_f = n_cg block-Jacobi CG iterations on
+      H d_f = -g - H d_s from zero with the fresh H (reading 22), d = d_s + d_f;
+    * the same filtered line search as ``timestep`` (CCD cut, feasibility,
+      Armijo);
+    * after the update, stop when the mean vertex speed of the subspace
+      step, sum_v |d_s,v|_2 / (h n), is below ``tol`` (m/s, reading 21).
+
+    Returns (x^{t+1}, info) with per-iteration step sizes and decrements."""
+    from . import subspace
+    x = initial_guess(prob)
+    info = {"iters": 0, "alpha": [], "decrement": [], "converged": False}
+    for it in range(max_iter):
+        g = prob.gradient(x)
+        g[prob.pinned] = 0.0
+        H = prob.hessian(x)
+        ds, df = subspace.paper_direction(H, g.ravel(), U, n_cg)
+        d = (ds + df).reshape(-1, 3)
+        d[prob.pinned] = 0.0
+        info["iters"] = it + 1
+        gd = float(np.sum(g * d))
+        if not gd < 0:
+            raise RuntimeError("paper direction is not a descent direction")
+        alpha = line_search(prob, x, d, g, prob.energy(x))
+        info["alpha"].append(alpha)
+        x = x + alpha * d
+        dec = float(np.sum(np.linalg.norm(ds.reshape(-1, 3), axis=1)) / (prob.h * prob.n))
+        info["decrement"].append(dec)
+        if dec < tol:
+            info["converged"] = True
+            break
+    return x, info

@@ -266,3 +266,28 @@ def test_pcg_exact_preconditioner_one_iteration():
     Ainv = np.linalg.inv(A)
     x, info = pcg.pcg(lambda v: A @ v, b, lambda r: Ainv @ r, rtol=1e-10)
     assert info["iters"] == 1
+
+
+def test_paper_timestep_limits():
+    """The paper's inexact timestep: with a basis spanning every free degree
+    of freedom the subspace direction is the Newton direction, so with a
+    vanishing tolerance it reaches the exact timestep's minimiser; with a
+    small basis and the paper's settings (20 CG iterations, 1e-3 m/s) it
+    stops on its decrement, lowers the energy, and its result is close to
+    (but not at) the minimiser."""
+    import scipy.sparse as sp
+    from oracle import subspace
+    s = synth.tiny_scene(4, 2, 2, seed=12, E_range=(1e5, 1e7))
+    p = ip.Problem(s)
+    x_o, _ = newton.timestep(p)
+    full = sp.csr_matrix(np.eye(3 * s.n_verts))
+    x1, info = newton.paper_timestep(p, full, n_cg=0, tol=1e-13)
+    assert info["converged"]
+    assert np.linalg.norm(x1 - x_o) <= 1e-9 * np.linalg.norm(x_o - s.x0)
+    o, vr, h, ph = synth.random_sparse_basis(s.X, m=4, k=2, seed=1)
+    U = subspace.lbs_basis_matrix(s.X, o, vr, h, ph)
+    x2, info2 = newton.paper_timestep(p, U, n_cg=20, tol=1e-3)
+    assert info2["converged"] and info2["decrement"][-1] < 1e-3
+    assert p.energy(x2) < p.energy(newton.initial_guess(p))
+    err = np.linalg.norm(x2 - x_o) / np.linalg.norm(x_o - s.x0)
+    assert 0 < err < 0.5
