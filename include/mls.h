@@ -215,6 +215,22 @@ mls_status mls_upload_cubature(mls_ctx* ctx, const double* scale);
 mls_status mls_set_forces(mls_ctx* ctx, const double* gravity, int contact,
                           const double* plane_n, double plane_o, double dhat, double kappa);
 
+/* Lagged point-plane friction, the term D of Eq. IP (Sec. 3.1, which takes
+ * IPC's mollified friction potential without writing it out).  For each
+ * vertex v, with distance d_v^t = n . x_v^t - o to the plane of
+ * mls_set_forces and h the timestep:
+ *   lam_v = -kappa b'(d_v^t)                   normal force, lagged at x^t
+ *   u_v   = (I - n n^T)(x_v - x_v^t),  y = |u_v|   tangential slip
+ *   D     = sum_v mu lam_v f0(y),  f0' = f1 = 2y/eps - y^2/eps^2 (y < eps), 1 (y >= eps),
+ *           f0(0) = eps / 3,  eps = eps_v h,
+ * added to E with the same h^2 (BDF2: (4/9) h^2) factor as the elastic energy;
+ * its gradient, its (PSD) diagonal Hessian blocks and its energy enter the
+ * assembly and the line search.  mu = 0 turns it off (the default).
+ * MLS_EINVAL for mu < 0, eps_v <= 0 with mu > 0, or mu > 0 while contact is
+ * off (call mls_set_forces with contact first; turning contact off later
+ * suspends the term). */
+mls_status mls_set_friction(mls_ctx* ctx, double mu, double eps_v);
+
 /* One implicit-Euler timestep.  DEVICE pointers:
  *   x [n][3] positions x^t, v [n][3] velocities v^t (read only),
  *   dx_out [n][3] receives x^{t+1} - x^t.
@@ -229,6 +245,19 @@ mls_status mls_newton_step(mls_ctx* ctx, const double* x, const double* v, doubl
  * device and dx back inside the call. */
 mls_status mls_newton_step_host(mls_ctx* ctx, const double* x, const double* v, double dt,
                                 double* dx_out, mls_stats* stats_out);
+
+/* One BDF2 timestep (Sec. 3.1, Eq. IP with alpha = 4/9).  DEVICE pointers:
+ *   x, v [n][3]            x^t and v^t,
+ *   x_prev, v_prev [n][3]  x^{t-1} and v^{t-1} (read only),
+ *   dx_out [n][3]          receives x^{t+1} - x^t.
+ * The predictor is x_tilde = (4 x^t - x^{t-1}) / 3 + (2 dt / 9)(4 v^t - v^{t-1})
+ * + (4/9) dt^2 g, and E = 1/2 |x - x_tilde|_M^2 + (4/9) dt^2 (Psi + B + D):
+ * the implicit-Euler potential of the step 2 dt / 3, so the Newton loop,
+ * its options, line search and stopping test (scaled by dt) are those of
+ * mls_newton_step.  The caller forms v^{t+1} = (3 x^{t+1} - 4 x^t + x^{t-1}) / (2 dt).
+ * Statuses as mls_newton_step. */
+mls_status mls_newton_step_bdf2(mls_ctx* ctx, const double* x, const double* v, const double* x_prev,
+                                const double* v_prev, double dt, double* dx_out, mls_stats* stats_out);
 
 /* ---- Stage entry points: one step of the path on the context's state ----
  * These run single rows of the hot path so each can be checked on its own.

@@ -172,6 +172,11 @@ class Solver:
         self._check(self._l.mls_set_forces(self._ctx, pg, 1 if contact else 0, ppn, float(plane_o),
                                            float(dhat), float(kappa)))
 
+    def set_friction(self, mu, eps_v=1e-3):
+        """Lagged point-plane friction (coefficient mu, mollifier velocity eps_v);
+        needs contact on (set_forces).  mu = 0 turns it off."""
+        self._check(self._l.mls_set_friction(self._ctx, float(mu), float(eps_v)))
+
     def setup_scene(self, scene):
         """Upload a ``synth.Scene``-like object's mesh, materials and loads."""
         self.upload_mesh(scene.X, scene.tets, scene.E, scene.nu, scene.rho, scene.dirichlet)
@@ -186,6 +191,22 @@ class Solver:
         allow = (-4,) if allow_notconv else ()
         status = self._check(self._l.mls_newton_step(self._ctx, _dev(x, (self.n, 3)), _dev(v, (self.n, 3)),
                                                      float(dt), _dev(dx, (self.n, 3)), C.byref(st)), allow)
+        out = st.as_dict()
+        out["status"] = status
+        return dx, out
+
+    def newton_step_bdf2(self, x, v, x_prev, v_prev, dt, dx=None, allow_notconv=False):
+        """One BDF2 timestep from (x^t, v^t) and (x^{t-1}, v^{t-1}); returns
+        dx = x^{t+1} - x^t (device) and the stats."""
+        import torch
+        if dx is None:
+            dx = torch.empty_like(x)
+        st = _lib.Stats()
+        allow = (-4,) if allow_notconv else ()
+        shape = (self.n, 3)
+        status = self._check(self._l.mls_newton_step_bdf2(self._ctx, _dev(x, shape), _dev(v, shape),
+                                                          _dev(x_prev, shape), _dev(v_prev, shape), float(dt),
+                                                          _dev(dx, shape), C.byref(st)), allow)
         out = st.as_dict()
         out["status"] = status
         return dx, out

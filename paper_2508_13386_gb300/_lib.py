@@ -79,8 +79,10 @@ SIGNATURES = {
     "mls_upload_mesh": [_P, _I32, _P, _I32, _P, _P, _P, _P, _P],
     "mls_upload_basis": [_P, _I32, _P, _P, _P, _P],
     "mls_set_forces": [_P, _P, _I, _P, _D, _D, _D],
+    "mls_set_friction": [_P, _D, _D],
     "mls_newton_step": [_P, _P, _P, _D, _P, C.POINTER(Stats)],
     "mls_newton_step_host": [_P, _P, _P, _D, _P, C.POINTER(Stats)],
+    "mls_newton_step_bdf2": [_P, _P, _P, _P, _P, _D, _P, C.POINTER(Stats)],
     "mls_eval_elements": [_P, _P, _P, _P, _P],
     "mls_assemble": [_P, _P, _P, _P, _D, _P],
     "mls_get_hessian": [_P, _P, _P, _P, C.POINTER(C.c_int64)],

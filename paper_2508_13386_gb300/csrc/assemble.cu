@@ -1,10 +1,13 @@
 // Gradient and Hessian assembly of the incremental potential (Eq. IP with
 // implicit Euler, Sec. 3.1), and the state-vector helpers of the timestep.
 //
-//   g = M (x - x_tilde) + h^2 (sum_e grad_e + kappa b'(d_v) n),  g_v = 0 on
-//       Dirichlet vertices;
-//   H = M + h^2 (sum_e H_e + kappa b''(d_v) n n^T), Dirichlet rows and
-//       columns replaced by the identity.
+//   g = M (x - x_tilde) + h^2 (sum_e grad_e + kappa b'(d_v) n + grad D_v),
+//       g_v = 0 on Dirichlet vertices;
+//   H = M + h^2 (sum_e H_e + kappa b''(d_v) n n^T + hess D_v), Dirichlet rows
+//       and columns replaced by the identity.
+// D_v is the lagged point-plane friction (zero unless a friction coefficient
+// is set).  With BDF2 the same forms hold with h = 2/3 of the timestep and
+// the BDF2 predictor x_tilde.
 //
 // Both are deterministic gathers (no floating-point atomics): every vertex
 // sums its incident element gradients through a precomputed incidence list
@@ -23,6 +26,8 @@ struct AsmIn {
   const double* __restrict__ egrad;
   double h2, kappa, dhat, po, pn0, pn1, pn2;
   int contact;
+  const Vec4d* __restrict__ xt;  // x^t, the friction lag state
+  double fmu, feps;              // friction coefficient (0: none) and mollifier width
 };
 
 __device__ __forceinline__ double bar_db(double d, double dhat) {
@@ -36,8 +41,9 @@ __device__ __forceinline__ double bar_d2b(double d, double dhat) {
   return -2.0 * log(d / dhat) - 4.0 * r / d + r * r / (d * d);
 }
 
-// g (float64) and the PCG right-hand side b = -g in solve precision
-template <typename VT>
+// g (float64) and the PCG right-hand side b = -g in solve precision; FRIC
+// compiles the friction term in (the instance without it is the plain kernel)
+template <typename VT, bool FRIC>
 __global__ void __launch_bounds__(kBlock) k_gather_grad(AsmIn in, const Vec4d* __restrict__ x,
                                                         Vec4d* __restrict__ g, Vec4<VT>* __restrict__ b,
                                                         GridReduce gr, double* __restrict__ gnorm2) {
@@ -60,6 +66,17 @@ __global__ void __launch_bounds__(kBlock) k_gather_grad(AsmIn in, const Vec4d* _
         const double dist = in.pn0 * xv.x + in.pn1 * xv.y + in.pn2 * xv.z - in.po;
         const double k1 = in.kappa * bar_db(dist, in.dhat);
         sx += k1 * in.pn0; sy += k1 * in.pn1; sz += k1 * in.pn2;
+        if constexpr (FRIC) {
+          const Vec4d xtv = in.xt[v];
+          const double lam = fric_lambda(in.pn0 * xtv.x + in.pn1 * xtv.y + in.pn2 * xtv.z - in.po, in.dhat,
+                                         in.kappa);
+          if (lam > 0.0) {
+            double u[3];
+            const double y = fric_slip(xv, xtv, in.pn0, in.pn1, in.pn2, u);
+            const double f = in.fmu * lam * fric_ratio(y, in.feps);
+            sx += f * u[0]; sy += f * u[1]; sz += f * u[2];
+          }
+        }
       }
       const Vec4d xt = in.xtil[v];
       const double m = in.mass[v];
@@ -86,6 +103,8 @@ struct SellAsmIn {
   const uint8_t* __restrict__ pinned;
   double h2, kappa, dhat, po, pn0, pn1, pn2;
   int contact;
+  const Vec4d* __restrict__ xt;  // x^t, the friction lag state
+  double fmu, feps;              // friction coefficient (0: none) and mollifier width
 };
 
 template <typename AT, typename ET>
@@ -135,7 +154,8 @@ __device__ __forceinline__ void inv3(const T (&A)[9], T (&R)[9]) {
 // escale (nullable): a factor per element on its elastic Hessian (a
 // cubature of the elastic term, Sec. 3.8; mass and barrier stay whole).
 // dinv (nullable): the block-Jacobi inverse of the stored diagonal blocks.
-template <typename AT, typename ET, typename MT, typename VT>
+// FRIC compiles the friction blocks in (the instance without it is the plain kernel).
+template <typename AT, typename ET, typename MT, typename VT, bool FRIC>
 __global__ void __launch_bounds__(kBlock) k_assemble(SellAsmIn in, int64_t n_slots,
                                                      const Vec4d* __restrict__ x,
                                                      const ET* __restrict__ hs, MT* __restrict__ val,
@@ -194,6 +214,27 @@ __global__ void __launch_bounds__(kBlock) k_assemble(SellAsmIn in, int64_t n_slo
 #pragma unroll
             for (int b = 0; b < 3; ++b) acc[3 * a + b] += (AT)(k2 * nn[a] * nn[b]);
         }
+        if constexpr (FRIC) {
+          const Vec4d xtv = in.xt[row];
+          const double lam = fric_lambda(in.pn0 * xtv.x + in.pn1 * xtv.y + in.pn2 * xtv.z - in.po, in.dhat,
+                                         in.kappa);
+          if (lam > 0.0) {
+            double u[3];
+            const double y = fric_slip(xv, xtv, in.pn0, in.pn1, in.pn2, u);
+            const double w = in.h2 * in.fmu * lam;
+            const double r = fric_ratio(y, in.feps);
+            // (slope - ratio) u^ u^T; at y = 0 the two factors are equal and the term vanishes
+            const double su = y > 0.0 ? fric_slope(y, in.feps) - r : 0.0;
+            const double iy = y > 0.0 ? 1.0 / y : 0.0;
+            const double uh[3] = {u[0] * iy, u[1] * iy, u[2] * iy};
+            const double nn[3] = {in.pn0, in.pn1, in.pn2};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+              for (int b = 0; b < 3; ++b)
+                acc[3 * a + b] += (AT)(w * (r * ((a == b ? 1.0 : 0.0) - nn[a] * nn[b]) + su * uh[a] * uh[b]));
+          }
+        }
       }
     }
   }
@@ -225,6 +266,27 @@ __global__ void k_predictor(int n, const double* __restrict__ x, const double* _
     q.x = p.x + h * v[3 * i] + h2 * gx;
     q.y = p.y + h * v[3 * i + 1] + h2 * gy;
     q.z = p.z + h * v[3 * i + 2] + h2 * gz;
+  }
+  xtil[i] = q;
+  xk[i] = q;
+}
+
+// BDF2 predictor (Sec. 3.1): x_tilde = (4 x^t - x^{t-1}) / 3 + (2h/9)(4 v^t - v^{t-1})
+// + (4/9) h^2 g on free vertices, x^t on Dirichlet vertices; h is the timestep
+__global__ void k_predictor_bdf2(int n, const double* __restrict__ x, const double* __restrict__ v,
+                                 const double* __restrict__ xp, const double* __restrict__ vp,
+                                 const uint8_t* __restrict__ pinned, double h, double gx, double gy, double gz,
+                                 Vec4d* __restrict__ xt, Vec4d* __restrict__ xtil, Vec4d* __restrict__ xk) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Vec4d p{x[3 * i], x[3 * i + 1], x[3 * i + 2], 0.0};
+  xt[i] = p;
+  Vec4d q = p;
+  if (!pinned[i]) {
+    const double a = 2.0 * h / 9.0, b = 4.0 * h * h / 9.0;
+    q.x = (4.0 * p.x - xp[3 * i]) / 3.0 + a * (4.0 * v[3 * i] - vp[3 * i]) + b * gx;
+    q.y = (4.0 * p.y - xp[3 * i + 1]) / 3.0 + a * (4.0 * v[3 * i + 1] - vp[3 * i + 1]) + b * gy;
+    q.z = (4.0 * p.z - xp[3 * i + 2]) / 3.0 + a * (4.0 * v[3 * i + 2] - vp[3 * i + 2]) + b * gz;
   }
   xtil[i] = q;
   xk[i] = q;
@@ -296,7 +358,7 @@ __global__ void k_add_solve(int n, Vec4<VT>* __restrict__ y, const Vec4<VT>* __r
 static AsmIn asm_in(mls_ctx* ctx) {
   return AsmIn{ctx->n, ctx->t, ctx->mass, ctx->pinned, ctx->xtil, ctx->vt_ptr, ctx->vt_code, ctx->egrad,
                ctx->h * ctx->h, ctx->kappa, ctx->dhat, ctx->po, ctx->pn[0], ctx->pn[1], ctx->pn[2],
-               ctx->contact};
+               ctx->contact, ctx->xt, ctx->contact ? ctx->fric_mu : 0.0, ctx->fric_eps_v * ctx->h_step};
 }
 
 static inline int nblk(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
@@ -304,12 +366,16 @@ static inline int nblk(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b
 mls_status launch_gather_grad(mls_ctx* ctx, const Vec4d* x, double* gnorm2_out) {
   const int nb = nblk(ctx->n);
   if (nb > kMaxPartials) return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
-  if (ctx->opt.precision == MLS_FP64)
-    { ++ctx->launches; k_gather_grad<double><<<nb, kBlock, 0, ctx->stream>>>(asm_in(ctx), x, ctx->grad, (Vec4d*)ctx->vb,
-                                                          ctx->red, gnorm2_out); }
-  else
-    { ++ctx->launches; k_gather_grad<float><<<nb, kBlock, 0, ctx->stream>>>(asm_in(ctx), x, ctx->grad, (Vec4f*)ctx->vb,
-                                                         ctx->red, gnorm2_out); }
+  const AsmIn in = asm_in(ctx);
+  const bool fric = in.fmu > 0.0;
+  ++ctx->launches;
+  if (ctx->opt.precision == MLS_FP64) {
+    if (fric) k_gather_grad<double, true><<<nb, kBlock, 0, ctx->stream>>>(in, x, ctx->grad, (Vec4d*)ctx->vb, ctx->red, gnorm2_out);
+    else k_gather_grad<double, false><<<nb, kBlock, 0, ctx->stream>>>(in, x, ctx->grad, (Vec4d*)ctx->vb, ctx->red, gnorm2_out);
+  } else {
+    if (fric) k_gather_grad<float, true><<<nb, kBlock, 0, ctx->stream>>>(in, x, ctx->grad, (Vec4f*)ctx->vb, ctx->red, gnorm2_out);
+    else k_gather_grad<float, false><<<nb, kBlock, 0, ctx->stream>>>(in, x, ctx->grad, (Vec4f*)ctx->vb, ctx->red, gnorm2_out);
+  }
   return cuda_check(ctx, cudaGetLastError(), "k_gather_grad");
 }
 
@@ -318,21 +384,36 @@ mls_status launch_gather_grad(mls_ctx* ctx, const Vec4d* x, double* gnorm2_out) 
 static mls_status assemble_into(mls_ctx* ctx, const Vec4d* x, void* val, void* dinv, const double* escale) {
   SellAsmIn in{ctx->n, ctx->t, ctx->group_slice, ctx->col, ctx->row_len, ctx->slice_ptr, ctx->asm_ptr,
                ctx->asm_code, ctx->mass, ctx->pinned, ctx->h * ctx->h, ctx->kappa, ctx->dhat, ctx->po,
-               ctx->pn[0], ctx->pn[1], ctx->pn[2], ctx->contact};
+               ctx->pn[0], ctx->pn[1], ctx->pn[2], ctx->contact, ctx->xt,
+               ctx->contact ? ctx->fric_mu : 0.0, ctx->fric_eps_v * ctx->h_step};
   const int64_t n_slots = ctx->n_groups * kSlice;
   const int nb = nblk(n_slots);
+  const bool fric = in.fmu > 0.0;
+  ++ctx->launches;
   switch (ctx->opt.precision) {
     case MLS_FP64:
-      { ++ctx->launches; k_assemble<double, double, double, double><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const double*)ctx->ehess, (double*)val, (double*)dinv, escale); }
+      if (fric)
+        k_assemble<double, double, double, double, true><<<nb, kBlock, 0, ctx->stream>>>(
+            in, n_slots, x, (const double*)ctx->ehess, (double*)val, (double*)dinv, escale);
+      else
+        k_assemble<double, double, double, double, false><<<nb, kBlock, 0, ctx->stream>>>(
+            in, n_slots, x, (const double*)ctx->ehess, (double*)val, (double*)dinv, escale);
       break;
     case MLS_MIXED_FP32:
-      { ++ctx->launches; k_assemble<float, float, float, float><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const float*)ctx->ehess, (float*)val, (float*)dinv, escale); }
+      if (fric)
+        k_assemble<float, float, float, float, true><<<nb, kBlock, 0, ctx->stream>>>(
+            in, n_slots, x, (const float*)ctx->ehess, (float*)val, (float*)dinv, escale);
+      else
+        k_assemble<float, float, float, float, false><<<nb, kBlock, 0, ctx->stream>>>(
+            in, n_slots, x, (const float*)ctx->ehess, (float*)val, (float*)dinv, escale);
       break;
     default:
-      { ++ctx->launches; k_assemble<float, float, __nv_bfloat16, float><<<nb, kBlock, 0, ctx->stream>>>(
-          in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)val, (float*)dinv, escale); }
+      if (fric)
+        k_assemble<float, float, __nv_bfloat16, float, true><<<nb, kBlock, 0, ctx->stream>>>(
+            in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)val, (float*)dinv, escale);
+      else
+        k_assemble<float, float, __nv_bfloat16, float, false><<<nb, kBlock, 0, ctx->stream>>>(
+            in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)val, (float*)dinv, escale);
       break;
   }
   return cuda_check(ctx, cudaGetLastError(), "k_assemble");
@@ -352,6 +433,14 @@ mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, doub
                                                        ctx->grav[1], ctx->grav[2], ctx->xt, ctx->xtil,
                                                        ctx->xk); }
   return cuda_check(ctx, cudaGetLastError(), "k_predictor");
+}
+
+mls_status launch_predictor_bdf2(mls_ctx* ctx, const double* x, const double* v, const double* x_prev,
+                                 const double* v_prev, double dt) {
+  { ++ctx->launches; k_predictor_bdf2<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(
+        ctx->n, x, v, x_prev, v_prev, ctx->pinned, dt, ctx->grav[0], ctx->grav[1], ctx->grav[2], ctx->xt,
+        ctx->xtil, ctx->xk); }
+  return cuda_check(ctx, cudaGetLastError(), "k_predictor_bdf2");
 }
 
 mls_status launch_pack(mls_ctx* ctx, const double* src, Vec4d* dst) {

@@ -1778,6 +1778,7 @@ mls_status mls_batch_step(mls_batch* b, const double* x, const double* v, double
   if (!x || !v || !dx_out) return bfail(b, MLS_EINVAL, "null state pointer");
   if (!(dt > 0)) return bfail(b, MLS_EINVAL, "dt must be positive");
   b->ctx->h = dt;
+  b->ctx->h_step = dt;
   mls_status st;
   switch (b->ctx->opt.precision) {
     case MLS_FP64: st = batch_step_t<double, double>(b, x, v, dt, dx_out); break;

@@ -565,7 +565,7 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
   mls_stats S{};
   mls_status st;
   if (ctx->coarse_ready) ctx->coarse_age_steps++;
-  const double h = ctx->h;
+  const double h = ctx->h_step;  // the timestep (ctx->h is the potential's step, 2h/3 for BDF2)
   const double gmag = std::sqrt(ctx->grav[0] * ctx->grav[0] + ctx->grav[1] * ctx->grav[1] + ctx->grav[2] * ctx->grav[2]);
   const double scale0 = h * h * std::max(gmag, 1e-30);
   double E = 0;
@@ -735,7 +735,18 @@ static mls_status check_mesh(mls_ctx* ctx) {
 static mls_status set_timestep(mls_ctx* ctx, const double* x_t, const double* v_t, double dt) {
   if (!(dt > 0)) return fail(ctx, MLS_EINVAL, "dt must be positive");
   ctx->h = dt;
+  ctx->h_step = dt;
   return launch_predictor(ctx, x_t, v_t, dt);
+}
+
+// BDF2 (Sec. 3.1): Eq. IP with alpha = 4/9 is the implicit-Euler potential of
+// the step 2 dt / 3 around the BDF2 predictor, so the Newton loop runs unchanged
+static mls_status set_timestep_bdf2(mls_ctx* ctx, const double* x_t, const double* v_t, const double* x_prev,
+                                    const double* v_prev, double dt) {
+  if (!(dt > 0)) return fail(ctx, MLS_EINVAL, "dt must be positive");
+  ctx->h = 2.0 * dt / 3.0;
+  ctx->h_step = dt;
+  return launch_predictor_bdf2(ctx, x_t, v_t, x_prev, v_prev, dt);
 }
 
 }  // namespace mls
@@ -755,6 +766,32 @@ mls_status mls_newton_step(mls_ctx* ctx, const double* x, const double* v, doubl
   if (stats_out) stats_out->kernel_launches = ctx->launches - l0;
   st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "newton_step sync");
   return st != MLS_OK ? st : res;
+}
+
+mls_status mls_newton_step_bdf2(mls_ctx* ctx, const double* x, const double* v, const double* x_prev,
+                                const double* v_prev, double dt, double* dx_out, mls_stats* stats_out) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!x || !v || !x_prev || !v_prev || !dx_out) return fail(ctx, MLS_EINVAL, "null state pointer");
+  const int64_t l0 = ctx->launches;
+  if ((st = set_timestep_bdf2(ctx, x, v, x_prev, v_prev, dt)) != MLS_OK) return st;
+  mls_status res = newton(ctx, stats_out);
+  if (res != MLS_OK && res != MLS_ENOTCONV) return res;
+  if ((st = launch_disp_out(ctx, dx_out)) != MLS_OK) return st;
+  if (stats_out) stats_out->kernel_launches = ctx->launches - l0;
+  st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "newton_step_bdf2 sync");
+  return st != MLS_OK ? st : res;
+}
+
+mls_status mls_set_friction(mls_ctx* ctx, double mu, double eps_v) {
+  if (!ctx) return MLS_EINVAL;
+  if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(ctx, MLS_EINVAL, "friction coefficient must be >= 0");
+  if (mu > 0.0 && !(eps_v > 0.0 && std::isfinite(eps_v)))
+    return fail(ctx, MLS_EINVAL, "friction needs a positive mollifier velocity eps_v");
+  if (mu > 0.0 && !ctx->contact) return fail(ctx, MLS_EINVAL, "friction needs the contact plane (mls_set_forces)");
+  ctx->fric_mu = mu;
+  if (mu > 0.0) ctx->fric_eps_v = eps_v;
+  return MLS_OK;
 }
 
 mls_status mls_newton_step_host(mls_ctx* ctx, const double* x, const double* v, double dt, double* dx_out,

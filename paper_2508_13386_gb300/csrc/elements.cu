@@ -1,7 +1,8 @@
 // Per-tet Neo-Hookean energy, gradient and PSD-projected Hessian (the
 // material model of Sec. 4: non-inverting Neo-Hookean, psi = mu/2 (|F|^2 - 3)
 // - mu ln J + lam/2 ln^2 J), the point-plane barrier terms of Eq. IP, the
-// line-search energy and the point-plane CCD bound (Sec. 3.9).
+// line-search energy (with the lagged friction term D when it is on) and the
+// point-plane CCD bound (Sec. 3.9).
 //
 // Hessian projection.  dP/dF of an isotropic energy is block diagonal in the
 // frame of the SVD F = U diag(s) V^T.  Writing c3 = lam ln J - mu:
@@ -371,6 +372,8 @@ struct EnergyIn {
   const Vec4d* __restrict__ xtil;
   double h2, kappa, dhat, po, pn0, pn1, pn2;
   int contact;
+  const Vec4d* __restrict__ xt;  // x^t, the friction lag state
+  double fmu, feps;              // friction coefficient (0: none) and mollifier width
 };
 
 __device__ __forceinline__ double barrier_b(double d, double dhat) {
@@ -447,6 +450,18 @@ __global__ void __launch_bounds__(kBlock) k_energy(EnergyIn in, const Vec4d* __r
       const double dist = in.pn0 * xv.x + in.pn1 * xv.y + in.pn2 * xv.z - in.po;
       if (dist <= 0.0) acc[1] = 1.0;
       else acc[0] += in.h2 * in.kappa * barrier_b(dist, in.dhat);
+      if (in.fmu > 0.0) {
+        // lagged friction mu lam f0(|slip|) on every vertex in contact at x^t (Dirichlet ones included:
+        // their slip is zero and the term is the constant mu lam eps / 3)
+        const Vec4d xtv = in.xt[v];
+        const double lam = fric_lambda(in.pn0 * xtv.x + in.pn1 * xtv.y + in.pn2 * xtv.z - in.po, in.dhat,
+                                       in.kappa);
+        if (lam > 0.0) {
+          double u[3];
+          const double y = fric_slip(xv, xtv, in.pn0, in.pn1, in.pn2, u);
+          acc[0] += in.h2 * in.fmu * lam * fric_f0(y, in.feps);
+        }
+      }
     }
   }
   if (grid_sum<2>(acc, gr, RS_ENERGY) && threadIdx.x == 0) {
@@ -527,7 +542,8 @@ mls_status launch_expand_hessian(mls_ctx* ctx, double* hess_out) {
 mls_status launch_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double alpha, double* E,
                          int* infeasible) {
   EnergyIn in{elem_in(ctx), ctx->n, ctx->mass, ctx->pinned, ctx->xtil, ctx->h * ctx->h,
-              ctx->kappa, ctx->dhat, ctx->po, ctx->pn[0], ctx->pn[1], ctx->pn[2], ctx->contact};
+              ctx->kappa, ctx->dhat, ctx->po, ctx->pn[0], ctx->pn[1], ctx->pn[2], ctx->contact,
+              ctx->xt, ctx->contact ? ctx->fric_mu : 0.0, ctx->fric_eps_v * ctx->h_step};
   const int total = ctx->t + ctx->n;
   const int nb = (total + kBlock - 1) / kBlock;
   if (nb > kMaxPartials) return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");

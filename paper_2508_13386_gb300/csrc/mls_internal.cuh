@@ -470,6 +470,42 @@ struct Basis {
   std::vector<double> h_vphi, h_origins;
 };
 
+// ---- lagged point-plane friction (Eq. IP, term D) ------------------------------------
+// The IPC-style friction of a vertex v against the ground plane (unit normal n,
+// offset o), lagged at x^t once per timestep:
+//   lam_v = -kappa b'(n . x_v^t - o)   the normal force at x^t (0 outside (0, dhat))
+//   u_v   = (I - n n^T)(x_v - x_v^t)   the tangential slip over the step, y = |u_v|
+//   D_v   = mu lam_v f0(y)             with the C1 mollifier of width eps = eps_v h:
+//   f0(y) = -y^3 / (3 eps^2) + y^2 / eps + eps / 3,   f1 = f0' = 2y/eps - y^2/eps^2   (y < eps)
+//   f0(y) = y,                                        f1 = 1                         (y >= eps)
+// so grad D_v = mu lam_v (f1(y) / y) u_v and the Hessian block is
+//   mu lam_v [ (f1/y) (I - n n^T) + (f1' - f1/y) u^ u^T ],  u^ = u_v / y,
+// positive semi-definite (f1' >= 0, f1/y > 0); at y = 0 both factors are 2/eps.
+__device__ __forceinline__ double fric_lambda(double d_t, double dhat, double kappa) {
+  if (d_t >= dhat || d_t <= 0.0) return 0.0;
+  const double r = d_t - dhat;
+  return -kappa * (-2.0 * r * log(d_t / dhat) - r * r / d_t);
+}
+// tangential slip u (returned in u[3]) and its length
+__device__ __forceinline__ double fric_slip(const Vec4d& xv, const Vec4d& xtv, double n0, double n1, double n2,
+                                            double (&u)[3]) {
+  const double dx = xv.x - xtv.x, dy = xv.y - xtv.y, dz = xv.z - xtv.z;
+  const double un = n0 * dx + n1 * dy + n2 * dz;
+  u[0] = dx - un * n0; u[1] = dy - un * n1; u[2] = dz - un * n2;
+  return sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+// f1(y) / y, finite at y = 0
+__device__ __forceinline__ double fric_ratio(double y, double eps) {
+  return y < eps ? 2.0 / eps - y / (eps * eps) : 1.0 / y;
+}
+// f1'(y)
+__device__ __forceinline__ double fric_slope(double y, double eps) {
+  return y < eps ? 2.0 / eps - 2.0 * y / (eps * eps) : 0.0;
+}
+__device__ __forceinline__ double fric_f0(double y, double eps) {
+  return y < eps ? -y * y * y / (3.0 * eps * eps) + y * y / eps + eps / 3.0 : y;
+}
+
 }  // namespace mls
 
 struct mls_mlp;
@@ -507,7 +543,9 @@ struct mls_ctx {
   std::vector<int> h_slice_ptr, h_row_len, h_col;
 
   // per-timestep / per-iteration state
-  double h = 1.0 / 60.0;
+  double h = 1.0 / 60.0;           // step of the implicit-Euler potential the Newton loop minimises
+                                   // (2 h_step / 3 for BDF2: its potential carries (4/9) h_step^2)
+  double h_step = 1.0 / 60.0;      // the timestep itself (stopping scale, friction mollifier width)
   mls::Vec4d* xk = nullptr;        // current iterate
   mls::Vec4d* xt = nullptr;        // x^t
   mls::Vec4d* xtil = nullptr;      // predictor
@@ -549,6 +587,8 @@ struct mls_ctx {
   int contact = 0;
   double pn[3] = {0.0, 0.0, 1.0};
   double po = 0.0, dhat = 1e-3, kappa = 1e5;
+  double fric_mu = 0.0;            // lagged point-plane friction coefficient (0: no friction term)
+  double fric_eps_v = 1e-3;        // friction mollifier width as a velocity (width eps_v h_step)
 
   // basis / coarse level
   mls::Basis basis;
@@ -630,6 +670,9 @@ mls_status launch_ccd(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double* alph
 mls_status launch_norms(mls_ctx* ctx, const Vec4d* d, double* dinf, double* xdisp_inf);
 mls_status launch_axpy_state(mls_ctx* ctx, Vec4d* x, const Vec4d* d, double alpha);
 mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, double dt);
+// BDF2 predictor from (x^t, v^t) and (x^{t-1}, v^{t-1}) with timestep dt
+mls_status launch_predictor_bdf2(mls_ctx* ctx, const double* x, const double* v, const double* x_prev,
+                                 const double* v_prev, double dt);
 mls_status launch_pack(mls_ctx* ctx, const double* src, Vec4d* dst);
 mls_status launch_unpack(mls_ctx* ctx, const Vec4d* src, double* dst);
 mls_status launch_disp_out(mls_ctx* ctx, double* dx_out);
