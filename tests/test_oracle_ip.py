@@ -179,6 +179,41 @@ def test_bdf2_energy_weights_potentials_by_four_ninths():
     assert np.allclose(p.velocity(x1), (3 * x1 - 4 * s.x0 + xp) / (2 * h), rtol=1e-14, atol=0)
 
 
+def test_bdf2_is_implicit_euler_of_two_thirds_step():
+    """The reading the GPU's BDF2 step rests on: Eq. IP with alpha = 4/9 is
+    the implicit-Euler potential of the step h' = 2h/3 around the BDF2
+    predictor.  An implicit-Euler problem with h' and the velocity v' that
+    puts its predictor x^t + h' v' + h'^2 g on the BDF2 one has the same E,
+    gradient, Hessian and minimiser, friction included (its mollifier width
+    eps_v h' matched by eps_v' = 3 eps_v / 2).  A wrong alpha, predictor
+    coefficient or width breaks the equality."""
+    s = synth.tiny_scene(3, 2, 2, seed=7, contact=True, pinned=False)
+    h = s.dt
+    g = np.asarray(s.gravity, dtype=np.float64)
+    rng_l = np.random.default_rng(4)
+    s.v0 = np.tile(np.array([0.4, -0.1, 0.0]), (s.n_verts, 1)) + 0.05 * rng_l.normal(size=s.x0.shape)
+    xp = s.x0 - h * s.v0 + 1e-4 * rng_l.normal(size=s.x0.shape)
+    vp = s.v0 + 0.05 * rng_l.normal(size=s.x0.shape)
+    pb = ip.Problem(s, integrator="bdf2", x_prev=xp, v_prev=vp, mu=0.4, eps_v=1e-3)
+    h2 = 2.0 * h / 3.0
+    v_eq = (pb.x_tilde - s.x0 - h2 * h2 * g[None, :]) / h2
+    pe = ip.Problem(s, v_t=v_eq, dt=h2, mu=0.4, eps_v=1.5e-3)
+    assert np.allclose(pe.x_tilde, pb.x_tilde, rtol=0, atol=1e-15)
+    assert pe.ah2 == pytest.approx(pb.ah2, rel=1e-15)
+    x = pb.x_tilde + 3e-4 * rng_l.normal(size=s.x0.shape)
+    # every other vertex inside the mollifier (slip < eps = 1.7e-5), where D depends on its width
+    x[::2] = s.x0[::2] + 3e-6 * rng_l.normal(size=s.x0[::2].shape)
+    x[:, 2] = np.maximum(x[:, 2], 2e-4)
+    assert pe.energy(x) == pytest.approx(pb.energy(x), rel=1e-13)
+    gb = pb.gradient(x)
+    assert np.allclose(pe.gradient(x), gb, rtol=0, atol=1e-12 * np.abs(gb).max())
+    Hb = pb.hessian(x).toarray()
+    assert np.allclose(pe.hessian(x).toarray(), Hb, rtol=0, atol=1e-12 * np.abs(Hb).max())
+    xb, _ = newton.timestep(pb)
+    xe, _ = newton.timestep(pe)
+    assert np.linalg.norm(xe - xb) <= 1e-9 * np.linalg.norm(xb - s.x0)
+
+
 # -- Newton timestep -----------------------------------------------------------
 def test_uniform_translation_is_exact():
     """No gravity, no contact, no pins: a rigid translation with velocity v
