@@ -14,9 +14,14 @@ Modules:
   elastic    non-inverting Neo-Hookean energy, stress, stress derivative,
              per-element PSD-projected Hessian (Sec. 4 material model)
   barrier    point-plane IPC log barrier (Eq. IP, contact term B)
-  ip         incremental potential E, gradient, Hessian (Eq. IP, implicit Euler)
+  friction   lagged, mollified point-plane friction D (Eq. IP, term D)
+  contact    mesh-mesh point-triangle and edge-edge barrier pairs and their
+             conservative CCD (Eq. IP term B, Sec. 3.9 CCD filter)
+  ip         incremental potential E, gradient, Hessian (Eq. IP, implicit
+             Euler or BDF2, Sec. 3.1)
   newton     projected Newton timestep with filtered backtracking line search
-             (Eq. 5 linear solve; Sec. 3.9 line search)
+             (Eq. 5 linear solve; Sec. 3.9 line search), and the paper's
+             inexact timestep (Alg. 1 with Alg. 2's directions)
   subspace   LBS basis matrix U (Eq. LBS, SMS basis), restriction/prolongation,
              Galerkin operator U^T H U, two-level preconditioner algebra
              (Alg. 2, Sec. 3.7.1)

@@ -13,7 +13,7 @@
 // With a trained network attached, the step starts from x_tilde + U dq_hat
 // when that point is feasible and has lower energy than x_tilde, and from
 // x_tilde otherwise (the plain start stays the fallback and the Newton/PCG
-// solve the judge: the converged x^{t+1} does not depend on the start).
+// solve the arbiter: the converged x^{t+1} does not depend on the start).
 #include "mls_internal.cuh"
 
 #include <cstring>

@@ -1,6 +1,6 @@
 """The learned warm start on the beam workload: coarse projection parity
 against the oracle, and what a trained network gains over the plain start on
-held-out steps (with the plain Newton/PCG solve as the judge of its result).
+held-out steps (with the plain Newton/PCG solve as the arbiter of its result).
 
 What the network gains is measured, not assumed: its held-out prediction of
 the coarse step against the zero prediction (the plain start), how often its
@@ -71,7 +71,7 @@ def test_warm_start_on_held_out_steps(beam_basis):
     rec.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
     rec.warm_start_enable(True, record=True)
     res = learned.evaluate(plain, warm, s, n_steps=30, seed=40, device=device, recorder=rec)
-    # the judge: both starts converge to the same step
+    # the arbiter: both starts converge to the same step
     assert res["max_rel_diff"] <= 1e-4
     # held-out prediction error against the zero prediction (the plain start)
     Y = net.forward(res["features"])
