@@ -1,4 +1,4 @@
-"""The friction arithmetic of the CUDA kernels, checked on the CPU.
+"""Kernel arithmetic checked on the CPU: friction terms and the BDF2 predictor.
 
 The lagged point-plane friction term (Eq. IP, term D) enters three kernels:
 the gradient gather (``k_gather_grad``), the diagonal Hessian blocks
@@ -16,6 +16,10 @@ sides, and the terms agree to rounding (1e-14 of the largest entry).  On a
 tilted plane, the distance n . x - o loses digits to cancellation when it is
 small, and the normal force grows like 1/d.  With d >= 1e-4 m and positions
 of order 1 m, 1e-11 covers that.
+
+The BDF2 predictor kernel (``k_predictor_bdf2``, one thread per vertex) is
+checked the same way: its body runs in a loop over the vertices and must
+reproduce the oracle's BDF2 predictor (Sec. 3.1) to rounding.
 """
 import ctypes as C
 import os
@@ -155,3 +159,55 @@ def test_kernel_friction_terms_match_oracle(kernels, plane, slip, bdf2):
     assert np.abs(g - g_o).max() <= tol * np.abs(g_o).max()
     assert np.abs(H - H_o).max() <= tol * np.abs(H_o).max()
     assert E.sum() == pytest.approx(h2 * F.energy(x), rel=tol)
+
+
+_PREDICTOR_DRIVER = r'''
+extern "C" void predictor_bdf2(int n, const double* x, const double* v, const double* xp, const double* vp,
+                               const uint8_t* pinned, double h, double gx, double gy, double gz,
+                               double* xt_out, double* xtil_out) {
+  std::vector<Vec4d> xt(n), xtil(n), xk(n);
+  auto body = [&](int i) PREDICTOR_BODY;
+  for (int i = 0; i < n; ++i) body(i);
+  for (int i = 0; i < n; ++i) {
+    xt_out[3 * i] = xt[i].x; xt_out[3 * i + 1] = xt[i].y; xt_out[3 * i + 2] = xt[i].z;
+    xtil_out[3 * i] = xtil[i].x; xtil_out[3 * i + 1] = xtil[i].y; xtil_out[3 * i + 2] = xtil[i].z;
+    if (xk[i].x != xtil[i].x || xk[i].y != xtil[i].y || xk[i].z != xtil[i].z) xtil_out[3 * i] = NAN;
+  }
+}
+'''
+
+
+def test_kernel_bdf2_predictor_matches_oracle(tmp_path):
+    """k_predictor_bdf2's body (one thread per vertex) against the oracle's
+    BDF2 predictor (Sec. 3.1): x_tilde on free vertices, x^t on Dirichlet
+    ones, and the Newton start equal to x_tilde."""
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    import synth
+    from oracle import ip
+    asm = open(os.path.join(CSRC, "assemble.cu")).read()
+    body = _block(asm, "__global__ void k_predictor_bdf2(", 0)
+    body = body.replace("const int i = blockIdx.x * blockDim.x + threadIdx.x;", "")
+    src, so = tmp_path / "pred.cpp", tmp_path / "pred.so"
+    src.write_text(_PRELUDE + _PREDICTOR_DRIVER.replace("PREDICTOR_BODY", body))
+    res = subprocess.run(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-o", str(so), str(src)],
+                         capture_output=True, text=True)
+    assert res.returncode == 0, res.stderr
+    lib = C.CDLL(str(so))
+    s = synth.tiny_scene(4, 3, 2, seed=11)                         # x = 0 face pinned
+    rng = np.random.default_rng(12)
+    x_prev = s.x0 + 1e-3 * rng.normal(size=s.x0.shape)
+    v_prev = 0.3 * rng.normal(size=s.x0.shape)
+    p = ip.Problem(s, integrator="bdf2", x_prev=x_prev, v_prev=v_prev)
+    n = s.n_verts
+    pinned = np.ascontiguousarray(s.dirichlet, dtype=np.uint8)
+    assert pinned.any() and not pinned.all()
+    xt, xtil = np.zeros((n, 3)), np.zeros((n, 3))
+    P = C.POINTER(C.c_double)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (s.x0, s.v0, x_prev, v_prev)]
+    g = [float(c) for c in s.gravity]
+    lib.predictor_bdf2(C.c_int(n), *[a.ctypes.data_as(P) for a in arrs], pinned.ctypes.data_as(C.c_void_p),
+                       C.c_double(s.dt), *[C.c_double(c) for c in g], xt.ctypes.data_as(P), xtil.ctypes.data_as(P))
+    assert np.array_equal(xt, s.x0)
+    assert np.allclose(xtil, p.x_tilde, rtol=0, atol=1e-15 * np.abs(p.x_tilde).max())
+    assert np.array_equal(xtil[pinned.astype(bool)], s.x0[pinned.astype(bool)])
