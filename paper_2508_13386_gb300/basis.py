@@ -13,9 +13,12 @@ This is the untimed precompute whose output the library uploads with
    Distances: the paper uses heat-method geodesics with a stiffness-weighted
    Laplacian (diffusion coefficient ~ stiffness).  Heat travel time over an
    edge of length l with diffusivity k scales as l^2 / k, i.e. the metric is
-   ds / sqrt(k); this implementation computes the graph geodesic of exactly
-   that metric on the tet edge graph (multi-source Dijkstra), which gives the
-   labels of a whole Lloyd assignment step in one pass.
+   ds / sqrt(k).  Two realisations of that metric: the default computes its
+   graph geodesic on the tet edge graph (multi-source Dijkstra), which gives
+   the labels of a whole Lloyd assignment step in one pass; ``distance="heat"``
+   uses the heat method itself (``HeatDistance``: heat flow with the
+   stiffness-weighted Laplacian, then a Poisson fit to the unit flow direction
+   scaled by the slowness 1/sqrt(k)), one pair of sparse solves per centre.
 2. Handles (Sec. 3.5): one per partition, at the mesh vertex of the partition
    nearest its volume-weighted centroid.
 3. Weights (Sec. 3.5): for partition i, the subdomain T_i is the partition
@@ -93,26 +96,115 @@ def geodesic_graph(X, tets, w_geo):
     return G
 
 
+class HeatDistance:
+    """Heat-method geodesic distances (Sec. 3.6, after Crane et al.'s heat
+    method) for the stiffness metric ds / sqrt(k) that ``geodesic_graph``
+    uses on edges.
+
+    For a source vertex s:
+      1. heat flow: (M + t L_k) u = e_s, with L_k the P1 stiffness matrix
+         weighted by k (diffusion faster in stiff tets), M the lumped volume
+         mass, t = (mean edge length)^2;
+      2. per tet, the unit direction X = -grad u / |grad u|, scaled by the
+         local slowness: Y = X / sqrt(k);
+      3. Poisson: the phi whose gradient fits Y in the k-weighted least-squares
+         sense, L_k phi = sum_e k_e vol_e G_e^T Y_e (G_e the P1 gradients);
+      4. shift so that phi(s) = 0 and clip at 0.
+    Step 3 fixes phi up to one constant per connected piece of the mesh; one
+    vertex per piece is pinned, and the shift of step 4 removes the constant
+    of the source's piece (vertices in other pieces get +inf).  Both systems
+    are factored once; sources are solved in chunks of ``chunk`` right-hand
+    sides."""
+
+    def __init__(self, X, tets, w_geo, chunk=16):
+        X = np.asarray(X, dtype=np.float64)
+        tets = np.asarray(tets, dtype=np.int64)
+        self.n = n = X.shape[0]
+        self.tets = tets
+        vol, Dinv = _rest(X, tets)
+        self.grads = np.concatenate([-Dinv.sum(axis=1, keepdims=True), Dinv], axis=1)   # [t, 4, 3]
+        self.w = np.asarray(w_geo, dtype=np.float64)
+        self.kvol = self.w * vol
+        L, Mv = p1_stiffness(X, tets, self.w)
+        pairs = _edges(tets)
+        t_heat = float(np.mean(np.linalg.norm(X[pairs[:, 0]] - X[pairs[:, 1]], axis=1))) ** 2
+        self.heat = spla.splu((sp.diags(Mv) + t_heat * L).tocsc())
+        adj = sp.coo_matrix((np.ones(len(pairs)), (pairs[:, 0], pairs[:, 1])), shape=(n, n))
+        _, self.piece = csg.connected_components(adj, directed=False)
+        first = np.unique(self.piece, return_index=True)[1]
+        self.free = np.setdiff1d(np.arange(n), first)
+        self.poisson = spla.splu(L[self.free][:, self.free].tocsc())
+        self.chunk = chunk
+
+    def __call__(self, sources):
+        """Distances [n, len(sources)] from each source vertex."""
+        sources = np.atleast_1d(np.asarray(sources, dtype=np.int64))
+        out = np.empty((self.n, len(sources)))
+        for c0 in range(0, len(sources), self.chunk):
+            src = sources[c0:c0 + self.chunk]
+            rhs = np.zeros((self.n, len(src)))
+            rhs[src, np.arange(len(src))] = 1.0
+            u = self.heat.solve(rhs)                                           # [n, c]
+            gu = np.einsum("tac,tas->tcs", self.grads, u[self.tets])           # [t, 3, c]
+            mag = np.linalg.norm(gu, axis=1, keepdims=True)
+            Y = -gu / np.where(mag > 0, mag, 1.0) / np.sqrt(self.w)[:, None, None]
+            nodal = np.einsum("tac,tcs->tas", self.grads, Y) * self.kvol[:, None, None]
+            b = np.zeros((self.n, len(src)))
+            np.add.at(b, self.tets.ravel(), nodal.reshape(-1, len(src)))
+            phi = np.zeros((self.n, len(src)))
+            phi[self.free] = self.poisson.solve(np.ascontiguousarray(b[self.free]))
+            phi -= phi[src, np.arange(len(src))][None, :]
+            phi = np.maximum(phi, 0.0)
+            phi[self.piece[:, None] != self.piece[src][None, :]] = np.inf
+            out[:, c0:c0 + len(src)] = phi
+        return out
+
+
 def _vertex_volume(n, tets, vol):
     vv = np.zeros(n)
     np.add.at(vv, tets.ravel(), np.repeat(vol / 4.0, 4))
     return vv
 
 
-def kmeans_partition(X, tets, E, m_target, seed=0, max_iter=40):
+def kmeans_partition(X, tets, E, m_target, seed=0, max_iter=40, distance="graph"):
     """Stiffness-aware geodesic K-means on vertices; returns vertex labels
-    (0..k-1) and the centre vertex of each cluster."""
+    (0..k-1) and the centre vertex of each cluster.  ``distance``: "graph"
+    (edge-graph geodesics of the metric ds / sqrt(k), the default) or "heat"
+    (heat-method geodesics of the same metric, ``HeatDistance``)."""
     n = X.shape[0]
     vol, _ = _rest(X, tets)
     vv = _vertex_volume(n, tets, vol)
     _, w_geo = stiffness_weights(tets, E)
-    G = geodesic_graph(X, tets, w_geo)
+    if distance == "graph":
+        G = geodesic_graph(X, tets, w_geo)
+    elif distance == "heat":
+        heat = HeatDistance(X, tets, w_geo)
+    else:
+        raise ValueError(f"unknown distance {distance!r}")
+
+    def nearest(centers):
+        """Index into ``centers`` of each vertex's nearest centre (-1: unreachable)."""
+        if distance == "graph":
+            _, _, src = csg.dijkstra(G, indices=centers, min_only=True, return_predecessors=True)
+            pos = {int(c): k for k, c in enumerate(centers)}
+            return np.array([pos.get(int(s), -1) for s in src])
+        best = np.full(n, np.inf)
+        lab = np.full(n, -1)
+        for c0 in range(0, len(centers), heat.chunk):
+            D = heat(centers[c0:c0 + heat.chunk])
+            j = np.argmin(D, axis=1)
+            d = D[np.arange(n), j]
+            better = d < best
+            best[better] = d[better]
+            lab[better] = c0 + j[better]
+        return lab
+
     rng = np.random.default_rng(seed)
     k0 = int(np.ceil(OVERSAMPLE * m_target))
     k0 = max(1, min(k0, n))
     # kmeans++ seeding with the same distance
     centers = [int(rng.integers(n))]
-    D = csg.dijkstra(G, indices=centers[0])
+    D = csg.dijkstra(G, indices=centers[0]) if distance == "graph" else heat([centers[0]])[:, 0]
     for _ in range(1, k0):
         p = vv * D ** 2
         s = p.sum()
@@ -120,13 +212,14 @@ def kmeans_partition(X, tets, E, m_target, seed=0, max_iter=40):
             break
         c = int(rng.choice(n, p=p / s))
         centers.append(c)
-        D = np.minimum(D, csg.dijkstra(G, indices=c, limit=float(D.max())))
+        if distance == "graph":
+            D = np.minimum(D, csg.dijkstra(G, indices=c, limit=float(D.max())))
+        else:
+            D = np.minimum(D, heat([c])[:, 0])
     centers = np.array(centers)
     labels = None
     for it in range(max_iter):
-        _, _, src = csg.dijkstra(G, indices=centers, min_only=True, return_predecessors=True)
-        pos = {int(c): k for k, c in enumerate(centers)}
-        new_labels = np.array([pos.get(int(s), -1) for s in src])
+        new_labels = nearest(centers)
         # unreachable vertices (disconnected pieces) join the nearest centre in space
         bad = new_labels < 0
         if bad.any():
@@ -159,9 +252,7 @@ def kmeans_partition(X, tets, E, m_target, seed=0, max_iter=40):
         if converged:
             break
     if labels is None:
-        _, _, src = csg.dijkstra(G, indices=centers, min_only=True, return_predecessors=True)
-        pos = {int(c): k for k, c in enumerate(centers)}
-        labels = np.array([pos.get(int(s), 0) for s in src])
+        labels = np.maximum(nearest(centers), 0)
     # while the sampling is still denser than the target, merge the smallest
     # clusters into their neighbours by dropping their centres
     while len(centers) > m_target:
@@ -169,9 +260,7 @@ def kmeans_partition(X, tets, E, m_target, seed=0, max_iter=40):
         cvol = np.bincount(labels, weights=vv, minlength=k)
         drop = np.argsort(cvol)[:min(PRUNE_COUNT, k - m_target)]
         centers = np.delete(centers, drop)
-        _, _, src = csg.dijkstra(G, indices=centers, min_only=True, return_predecessors=True)
-        pos = {int(c): kk for kk, c in enumerate(centers)}
-        labels = np.array([pos.get(int(s), 0) for s in src])
+        labels = np.maximum(nearest(centers), 0)
     return labels, centers
 
 
@@ -270,16 +359,17 @@ def _run_jobs(jobs, workers):
         return pool.map(_biharmonic_job, jobs, chunksize=max(1, len(jobs) // (4 * workers)))
 
 
-def build_sms_basis(X, tets, E, m_target, dirichlet=None, seed=0, workers=None):
+def build_sms_basis(X, tets, E, m_target, dirichlet=None, seed=0, workers=None, distance="graph"):
     """Build the SMS basis.  Returns a dict with ``origins`` [m,3], per-vertex
     CSR ``vrow``/``handle``/``phi``, the vertex ``labels`` and tet
     ``partition`` used, and ``u_dbc`` (per-vertex Dirichlet weight, zeros
-    without Dirichlet vertices)."""
+    without Dirichlet vertices).  ``distance`` selects the K-means distance
+    ("graph" or "heat", see ``kmeans_partition``)."""
     X = np.asarray(X, dtype=np.float64)
     tets = np.asarray(tets, dtype=np.int64)
     n = X.shape[0]
     pinned = np.zeros(n, bool) if dirichlet is None else np.asarray(dirichlet).astype(bool)
-    vlabels, _ = kmeans_partition(X, tets, E, m_target, seed=seed)
+    vlabels, _ = kmeans_partition(X, tets, E, m_target, seed=seed, distance=distance)
     part = tet_partition(tets, vlabels)
     used = np.unique(part)
     remap = -np.ones(part.max() + 1, dtype=np.int64)
