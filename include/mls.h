@@ -486,6 +486,11 @@ mls_status mls_batch_upload_basis(mls_batch* b, int32_t n_handles, const int32_t
                                   const double* phi);
 mls_status mls_batch_set_forces(mls_batch* b, const double* gravity, int contact, const double* plane_n,
                                 double plane_o, double dhat, double kappa);
+/* Lagged point-plane friction for every mesh of the batch: the term and the
+ * arguments of mls_set_friction (Eq. IP, term D), with the mollifier width
+ * eps_v dt of each step's dt.  Call after mls_batch_set_forces with contact;
+ * the next step rebuilds its graph.  MLS_EINVAL as mls_set_friction. */
+mls_status mls_batch_set_friction(mls_batch* b, double mu, double eps_v);
 mls_status mls_batch_retune(mls_batch* b);
 /* One timestep of every mesh from DEVICE x, v [V][3] (float64, concatenated)
  * into DEVICE dx [V][3].  stats (HOST [B], nullable) receives per-mesh

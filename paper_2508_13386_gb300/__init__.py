@@ -452,6 +452,10 @@ class Batch:
         self._check(self._l.mls_batch_set_forces(self._b, pg, 1 if contact else 0, ppn, float(plane_o),
                                                  float(dhat), float(kappa)))
 
+    def set_friction(self, mu, eps_v=1e-3):
+        """Lagged point-plane friction for every mesh (as ``Solver.set_friction``)."""
+        self._check(self._l.mls_batch_set_friction(self._b, float(mu), float(eps_v)))
+
     def retune(self):
         self._check(self._l.mls_batch_retune(self._b))
 

@@ -119,6 +119,7 @@ SIGNATURES = {
     "mls_batch_destroy": [_P],
     "mls_batch_upload": [_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P],
     "mls_batch_set_forces": [_P, _P, C.c_int, _P, C.c_double, C.c_double, C.c_double],
+    "mls_batch_set_friction": [_P, _D, _D],
     "mls_batch_upload_basis": [_P, _I32, _P, _P, _P, _P, _P],
     "mls_batch_retune": [_P],
     "mls_batch_step": [_P, _P, _P, C.c_double, _P, _P, _P],

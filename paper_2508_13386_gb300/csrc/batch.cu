@@ -47,6 +47,7 @@ struct BParams {        // per-timestep constants
   int max_newton, max_pcg;
   double kappa, dhat, po, pn0, pn1, pn2;
   int contact;
+  double fmu, feps;       // lagged point-plane friction: coefficient (0: none), mollifier width
 };
 
 struct BView {
@@ -177,6 +178,7 @@ struct BEnergyIn {
   int t;
   const int* tets; const double* Dminv; const double* vol; const double* mu; const double* lam;
   const double* mass; const uint8_t* pinned; const Vec4d* xtil;
+  const Vec4d* xt;        // x^t, the friction lag state
 };
 
 template <int MODE>
@@ -248,6 +250,16 @@ __global__ void __launch_bounds__(kTetBlock) k_benergy(BView V, BEnergyIn in, BP
         } else if (dist < P.dhat) {
           const double r = dist - P.dhat;
           acc[0] += P.h2 * P.kappa * (-r * r * log(dist / P.dhat));
+        }
+        if (P.fmu > 0.0) {
+          // lagged friction mu lam f0(|slip|) (Eq. IP, term D), as in the single-mesh energy
+          const Vec4d xtv = in.xt[v];
+          const double lam = fric_lambda(P.pn0 * xtv.x + P.pn1 * xtv.y + P.pn2 * xtv.z - P.po, P.dhat, P.kappa);
+          if (lam > 0.0) {
+            double u[3];
+            const double y = fric_slip(xv, xtv, P.pn0, P.pn1, P.pn2, u);
+            acc[0] += P.h2 * P.fmu * lam * fric_f0(y, P.feps);
+          }
         }
       }
     }
@@ -1150,11 +1162,13 @@ BParams params(mls_batch* b, double dt) {
   P.kappa = c->kappa; P.dhat = c->dhat; P.po = c->po;
   P.pn0 = c->pn[0]; P.pn1 = c->pn[1]; P.pn2 = c->pn[2];
   P.contact = c->contact;
+  P.fmu = c->contact ? c->fric_mu : 0.0;
+  P.feps = c->fric_eps_v * dt;
   return P;
 }
 
 BEnergyIn energy_in(mls_ctx* c) {
-  return BEnergyIn{c->t, c->tets, c->Dminv, c->vol, c->mu, c->lam, c->mass, c->pinned, c->xtil};
+  return BEnergyIn{c->t, c->tets, c->Dminv, c->vol, c->mu, c->lam, c->mass, c->pinned, c->xtil, c->xt};
 }
 
 template <typename VT, typename MT>
@@ -1757,6 +1771,14 @@ mls_status mls_batch_set_forces(mls_batch* b, const double* gravity, int contact
                                 double plane_o, double dhat, double kappa) {
   if (!b) return MLS_EINVAL;
   mls_status st = mls_set_forces(b->ctx, gravity, contact, plane_n, plane_o, dhat, kappa);
+  if (st != MLS_OK) return bfail(b, st, mls_last_error(b->ctx));
+  b->graph_dirty = true;
+  return MLS_OK;
+}
+
+mls_status mls_batch_set_friction(mls_batch* b, double mu, double eps_v) {
+  if (!b) return MLS_EINVAL;
+  mls_status st = mls_set_friction(b->ctx, mu, eps_v);
   if (st != MLS_OK) return bfail(b, st, mls_last_error(b->ctx));
   b->graph_dirty = true;
   return MLS_OK;

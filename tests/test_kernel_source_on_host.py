@@ -2,7 +2,8 @@
 
 The lagged point-plane friction term (Eq. IP, term D) enters three kernels:
 the gradient gather (``k_gather_grad``), the diagonal Hessian blocks
-(``k_assemble``) and the line-search energy (``k_energy``).  Their friction
+(``k_assemble``) and the line-search energies (``k_energy``, and
+``k_benergy`` of the batched path).  Their friction
 branches and the helpers they call are plain double-precision arithmetic.
 This test takes their exact source text from the ``.cu`` files, compiles it
 as host C++ with g++, and compares the per-vertex results with the oracle's
@@ -89,6 +90,18 @@ extern "C" void block_terms(int n, const double* xs, const double* xts, const do
     for (int q = 0; q < 9; ++q) out[9 * row + q] = acc[q];
   }
 }
+extern "C" void batch_energy_terms(int n, const double* xs, const double* xts, const double* Pv, double* out) {
+  std::vector<Vec4d> X = pack(n, xs), XT = pack(n, xts);
+  struct { double pn0, pn1, pn2, po, dhat, kappa, fmu, feps, h2; } P{Pv[0], Pv[1], Pv[2], Pv[3], Pv[4], Pv[5],
+                                                                   Pv[6], Pv[7], Pv[8]};
+  struct { const Vec4d* xt; } in{XT.data()};
+  for (int v = 0; v < n; ++v) {
+    const Vec4d xv = X[v];
+    double acc[2] = {0, 0};
+    BATCH_ENERGY_BRANCH
+    out[v] = acc[0];
+  }
+}
 extern "C" void energy_terms(int n, const double* xs, const double* xts, const double* P, double* out) {
   SETUP
   for (int v = 0; v < n; ++v) {
@@ -110,8 +123,10 @@ def kernels(tmp_path_factory):
     helpers = hdr[a:hdr.index("}  // namespace mls", a)].replace("__device__ __forceinline__", "inline")
     asm = open(os.path.join(CSRC, "assemble.cu")).read()
     ele = open(os.path.join(CSRC, "elements.cu")).read()
+    bat = open(os.path.join(CSRC, "batch.cu")).read()
     driver = (_DRIVER.replace("GRAD_BRANCH", _block(asm, "if constexpr (FRIC)", 0))
               .replace("BLOCK_BRANCH", _block(asm, "if constexpr (FRIC)", 1))
+              .replace("BATCH_ENERGY_BRANCH", _block(bat, "if (P.fmu > 0.0)", 0))
               .replace("ENERGY_BRANCH", _block(ele, "if (in.fmu > 0.0)", 0)))
     d = tmp_path_factory.mktemp("friction_host")
     src, so = d / "friction_host.cpp", d / "friction_host.so"
@@ -155,10 +170,12 @@ def test_kernel_friction_terms_match_oracle(kernels, plane, slip, bdf2):
     g = kernels("grad_terms", x, xt, params, 3)
     H = kernels("block_terms", x, xt, params, 9).reshape(N, 3, 3)
     E = kernels("energy_terms", x, xt, params, 1)[:, 0]
+    E_batch = kernels("batch_energy_terms", x, xt, params, 1)[:, 0]
     g_o, H_o = F.gradient(x), h2 * F.hessian_blocks(x)
     assert np.abs(g - g_o).max() <= tol * np.abs(g_o).max()
     assert np.abs(H - H_o).max() <= tol * np.abs(H_o).max()
     assert E.sum() == pytest.approx(h2 * F.energy(x), rel=tol)
+    assert E_batch.sum() == pytest.approx(h2 * F.energy(x), rel=tol)
 
 
 _PREDICTOR_DRIVER = r'''
