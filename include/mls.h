@@ -360,6 +360,7 @@ typedef struct mls_mlp mls_mlp;
  * on stream (cudaStream_t, NULL = legacy default). */
 mls_status mls_mlp_create(mls_mlp** out, int32_t n_in, int32_t n_hidden, int32_t n_out,
                           int32_t max_batch, const float* init_params, void* stream);
+/* Free the network's device buffers; NULL is accepted. */
 mls_status mls_mlp_destroy(mls_mlp* mlp);
 /* Number of parameters (length of the flat array). */
 int64_t mls_mlp_param_count(const mls_mlp* mlp);
@@ -463,8 +464,14 @@ typedef struct mls_batch_info {
   double tune_ms;             /* time spent timing candidates (first step) */
 } mls_batch_info;
 
+/* Create an empty batch with options opt (HOST; NULL = mls_default_options)
+ * on opt->stream.  MLS_EINVAL for invalid options, MLS_ENOMEM / MLS_ECUDA when
+ * the context or the internal stream cannot be made. */
 mls_status mls_batch_create(mls_batch** out, const mls_options* opt);
+/* Free the batch, its context, graph and device buffers; NULL is accepted. */
 mls_status mls_batch_destroy(mls_batch* b);
+/* The message of the batch's last failing call (owned by the batch, valid
+ * until its next call); "" when there is none. */
 const char* mls_batch_last_error(const mls_batch* b);
 /* B meshes concatenated: mesh m owns vertices [vert_offsets[m],
  * vert_offsets[m+1]) and tets [tet_offsets[m], tet_offsets[m+1]); tets hold
@@ -484,6 +491,9 @@ mls_status mls_batch_upload(mls_batch* b, int32_t n_meshes, const int32_t* vert_
 mls_status mls_batch_upload_basis(mls_batch* b, int32_t n_handles, const int32_t* handle_offsets,
                                   const double* origins, const int32_t* vrow, const int32_t* handle,
                                   const double* phi);
+/* Loads shared by every mesh: the arguments and errors of mls_set_forces
+ * (Eq. IP: gravity in the predictor, the point-plane barrier B).  The next
+ * step rebuilds its graph. */
 mls_status mls_batch_set_forces(mls_batch* b, const double* gravity, int contact, const double* plane_n,
                                 double plane_o, double dhat, double kappa);
 /* Lagged point-plane friction for every mesh of the batch: the term and the
@@ -491,6 +501,8 @@ mls_status mls_batch_set_forces(mls_batch* b, const double* gravity, int contact
  * eps_v dt of each step's dt.  Call after mls_batch_set_forces with contact;
  * the next step rebuilds its graph.  MLS_EINVAL as mls_set_friction. */
 mls_status mls_batch_set_friction(mls_batch* b, double mu, double eps_v);
+/* Forget the tuned launch shape: the next step times the candidates again
+ * and rebuilds its graph. */
 mls_status mls_batch_retune(mls_batch* b);
 /* One timestep of every mesh from DEVICE x, v [V][3] (float64, concatenated)
  * into DEVICE dx [V][3].  stats (HOST [B], nullable) receives per-mesh
