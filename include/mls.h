@@ -511,6 +511,16 @@ mls_status mls_batch_retune(mls_batch* b);
  * for all meshes; a mesh with MLS_ENOTCONV returns its last iterate). */
 mls_status mls_batch_step(mls_batch* b, const double* x, const double* v, double dt, double* dx_out,
                           mls_batch_mesh_stats* stats, mls_batch_info* info);
+/* One BDF2 timestep of every mesh (Sec. 3.1, Eq. IP with alpha = 4/9), as
+ * mls_newton_step_bdf2 for each mesh: DEVICE x, v [V][3] (x^t, v^t) and
+ * x_prev, v_prev [V][3] (x^{t-1}, v^{t-1}), concatenated like x.  The first
+ * call allocates two history buffers of [V][3] float64 (kept until the
+ * next mls_batch_upload or mls_batch_destroy).  Switching between this and
+ * mls_batch_step rebuilds the step graph.  Statuses as mls_batch_step, and
+ * MLS_ENOMEM when the history buffers cannot be allocated. */
+mls_status mls_batch_step_bdf2(mls_batch* b, const double* x, const double* v, const double* x_prev,
+                               const double* v_prev, double dt, double* dx_out, mls_batch_mesh_stats* stats,
+                               mls_batch_info* info);
 
 /* ---- Self-test of the bounded device wait -------------------------------
  * The persistent PCG kernel separates its phases with a grid barrier whose

@@ -474,6 +474,23 @@ class Batch:
         inf["status"] = status
         return dx, per, inf
 
+    def step_bdf2(self, x, v, x_prev, v_prev, dt, dx=None, allow=(-4,)):
+        """One BDF2 timestep of every mesh from (x^t, v^t) and (x^{t-1}, v^{t-1});
+        returns (dx, per-mesh stats, info) as ``step``."""
+        import torch
+        if dx is None:
+            dx = torch.empty_like(x)
+        stats = (_lib.BatchMeshStats * self.n_meshes)()
+        info = _lib.BatchInfo()
+        shape = (self.n, 3)
+        status = self._check(self._l.mls_batch_step_bdf2(self._b, _dev(x, shape), _dev(v, shape), _dev(x_prev, shape),
+                                                         _dev(v_prev, shape), float(dt), _dev(dx, shape), stats,
+                                                         C.byref(info)), allow)
+        per = [{k: getattr(s, k) for k, _ in _lib.BatchMeshStats._fields_} for s in stats]
+        inf = {k: getattr(info, k) for k, _ in _lib.BatchInfo._fields_}
+        inf["status"] = status
+        return dx, per, inf
+
 
 class MLP:
     """A network trained and run by the library's kernels (``mls_mlp_*``)."""

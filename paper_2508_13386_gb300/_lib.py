@@ -123,6 +123,7 @@ SIGNATURES = {
     "mls_batch_upload_basis": [_P, _I32, _P, _P, _P, _P, _P],
     "mls_batch_retune": [_P],
     "mls_batch_step": [_P, _P, _P, C.c_double, _P, _P, _P],
+    "mls_batch_step_bdf2": [_P, _P, _P, _P, _P, C.c_double, _P, _P, _P],
 }
 class BatchMeshStats(C.Structure):
     _fields_ = [

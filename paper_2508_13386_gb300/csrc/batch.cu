@@ -1023,6 +1023,9 @@ struct mls_batch {
   int* vmap = nullptr;  // [n] internal -> user vertex (-1: dummy)
   double* bx = nullptr; // [n][3] packed x, v
   double* bv = nullptr;
+  double* bxp = nullptr; // [n][3] packed x^{t-1}, v^{t-1} (BDF2 steps; allocated on the first one)
+  double* bvp = nullptr;
+  bool bdf2 = false;     // the current step integrates with BDF2
   BMesh* M = nullptr;
   BMesh* h_M = nullptr; // pinned
   int* trips = nullptr; // [3] device
@@ -1044,6 +1047,7 @@ struct mls_batch {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   double graph_dt = -1.0;
+  bool graph_bdf2 = false;  // the integrator the graph was captured for
   bool graph_dirty = true;
   int64_t launches_fixed = 0, launches_newton = 0, launches_pcg = 0, launches_ls = 0;
   // two-level preconditioning (per-mesh bases)
@@ -1151,7 +1155,8 @@ mls_status build_tables(mls_batch* b, const BShape& sh) {
 BParams params(mls_batch* b, double dt) {
   mls_ctx* c = b->ctx;
   BParams P{};
-  P.h2 = dt * dt;
+  // BDF2: Eq. IP with alpha = 4/9 is the implicit-Euler potential of the step 2 dt / 3
+  P.h2 = b->bdf2 ? (2.0 * dt / 3.0) * (2.0 * dt / 3.0) : dt * dt;
   const double gm = std::sqrt(c->grav[0] * c->grav[0] + c->grav[1] * c->grav[1] + c->grav[2] * c->grav[2]);
   P.scale0 = dt * dt * std::max(gm, 1e-30);
   P.newton_tol = c->opt.newton_tol;
@@ -1353,7 +1358,9 @@ mls_status capture_step(mls_batch* b, double dt) {
     c->stream = s0;
     // predictor and start states
     k_breset<<<(b->nmesh + 127) / 128, 128, 0, s0>>>(b->nmesh, b->M);
-    if ((r = launch_predictor(c, b->bx, b->bv, dt)) != MLS_OK) return r;
+    if ((r = b->bdf2 ? launch_predictor_bdf2(c, b->bx, b->bv, b->bxp, b->bvp, dt)
+                     : launch_predictor(c, b->bx, b->bv, dt)) != MLS_OK)
+      return r;
     k_benergy<0><<<eb, kTetBlock, 0, s0>>>(V, EI, P, c->xt, c->xt);
     k_benergy<1><<<eb, kTetBlock, 0, s0>>>(V, EI, P, c->xk, c->xk);
     k_bselect<<<V.nrb, rt, 0, s0>>>(V, c->xt, c->xk);
@@ -1412,6 +1419,7 @@ mls_status capture_step(mls_batch* b, double dt) {
   cudaStreamDestroy(s2);
   if (st == MLS_OK) {
     b->graph_dt = dt;
+    b->graph_bdf2 = b->bdf2;
     b->graph_dirty = false;
     // kernels per body: Newton = element, gradient, assembly, PCG set-up,
     // two loop-entry conditions, direction, Newton condition (+ the first
@@ -1489,7 +1497,8 @@ mls_status autotune(mls_batch* b, double dt) {
 }
 
 template <typename VT, typename MT>
-mls_status batch_step_t(mls_batch* b, const double* x, const double* v, double dt, double* dx) {
+mls_status batch_step_t(mls_batch* b, const double* x, const double* v, const double* xp, const double* vp,
+                        double dt, double* dx) {
   mls_ctx* c = b->ctx;
   mls_status st;
   cudaStream_t user = c->stream;
@@ -1502,6 +1511,12 @@ mls_status batch_step_t(mls_batch* b, const double* x, const double* v, double d
                                                   c->pn[0] * (c->po + 1e3), c->pn[1] * (c->po + 1e3),
                                                   c->pn[2] * (c->po + 1e3));
   if ((st = bcheck(b, cudaGetLastError(), "k_bpack")) != MLS_OK) { cudaEventDestroy(ev); return st; }
+  if (b->bdf2) {
+    k_bpack<<<(b->n + 255) / 256, 256, 0, b->cap>>>(b->n, b->vmap, xp, vp, b->bxp, b->bvp,
+                                                    c->pn[0] * (c->po + 1e3), c->pn[1] * (c->po + 1e3),
+                                                    c->pn[2] * (c->po + 1e3));
+    if ((st = bcheck(b, cudaGetLastError(), "k_bpack history")) != MLS_OK) { cudaEventDestroy(ev); return st; }
+  }
   if (b->two_level && !b->has_basis) {
     cudaEventDestroy(ev);
     return bfail(b, MLS_EINVAL, "two-level batch: upload the per-mesh bases first");
@@ -1518,7 +1533,7 @@ mls_status batch_step_t(mls_batch* b, const double* x, const double* v, double d
     if (st != MLS_OK) { cudaEventDestroy(ev); return bfail(b, st, mls_last_error(c)); }
     b->galerkin_warm = true;
   }
-  if (b->graph_dirty || b->graph_dt != dt || !b->exec) {
+  if (b->graph_dirty || b->graph_dt != dt || b->graph_bdf2 != b->bdf2 || !b->exec) {
     if ((st = capture_step<VT, MT>(b, dt)) != MLS_OK) { cudaEventDestroy(ev); return st; }
   }
   cudaMemsetAsync(b->trips, 0, sizeof(int) * 4, b->cap);
@@ -1568,7 +1583,8 @@ mls_status mls_batch_destroy(mls_batch* b) {
   for (void* p : b->coarse_alloc) cudaFree(p);
   if (b->W) cudaFree(b->W);
   if (b->WT) cudaFree(b->WT);
-  for (void* p : {(void*)b->vmap, (void*)b->bx, (void*)b->bv, (void*)b->M, (void*)b->trips, (void*)b->any,
+  for (void* p : {(void*)b->vmap, (void*)b->bx, (void*)b->bv, (void*)b->bxp, (void*)b->bvp, (void*)b->M,
+                  (void*)b->trips, (void*)b->any,
                   (void*)b->mass_min, (void*)b->cnt, (void*)b->part_rb, (void*)b->part_sl, (void*)b->part_e})
     if (p) cudaFree(p);
   if (b->h_M) cudaFreeHost(b->h_M);
@@ -1648,7 +1664,8 @@ mls_status mls_batch_upload(mls_batch* b, int32_t n_meshes, const int32_t* vert_
     mmin[m] = lo < 1e300 ? lo : 0.0;
   }
   // (re)allocate batch state
-  for (void** p : {(void**)&b->vmap, (void**)&b->bx, (void**)&b->bv, (void**)&b->M, (void**)&b->trips,
+  for (void** p : {(void**)&b->vmap, (void**)&b->bx, (void**)&b->bv, (void**)&b->bxp, (void**)&b->bvp,
+                   (void**)&b->M, (void**)&b->trips,
                    (void**)&b->any, (void**)&b->mass_min, (void**)&b->cnt, (void**)&b->part_sl})
     if (*p) { cudaFree(*p); *p = nullptr; }
   if (b->h_M) { cudaFreeHost(b->h_M); b->h_M = nullptr; }
@@ -1792,20 +1809,33 @@ mls_status mls_batch_retune(mls_batch* b) {
   return MLS_OK;
 }
 
-mls_status mls_batch_step(mls_batch* b, const double* x, const double* v, double dt, double* dx_out,
-                          mls_batch_mesh_stats* stats, mls_batch_info* info) {
+// one step of every mesh: implicit Euler (xp = vp = NULL) or BDF2 from the
+// history (xp, vp) = (x^{t-1}, v^{t-1})
+static mls_status batch_step_entry(mls_batch* b, const double* x, const double* v, const double* xp,
+                                   const double* vp, double dt, double* dx_out, mls_batch_mesh_stats* stats,
+                                   mls_batch_info* info) {
   if (!b) return MLS_EINVAL;
   b->err.clear();
   if (b->nmesh < 1) return bfail(b, MLS_EINVAL, "no meshes uploaded");
   if (!x || !v || !dx_out) return bfail(b, MLS_EINVAL, "null state pointer");
   if (!(dt > 0)) return bfail(b, MLS_EINVAL, "dt must be positive");
-  b->ctx->h = dt;
+  const bool bdf2 = xp != nullptr;
+  if (bdf2 && !b->bxp) {
+    if (cudaMalloc(&b->bxp, sizeof(double) * 3 * b->n) != cudaSuccess ||
+        cudaMalloc(&b->bvp, sizeof(double) * 3 * b->n) != cudaSuccess) {
+      cudaGetLastError();
+      if (b->bxp) { cudaFree(b->bxp); b->bxp = nullptr; }
+      return bfail(b, MLS_ENOMEM, "BDF2 history buffers");
+    }
+  }
+  b->bdf2 = bdf2;
+  b->ctx->h = bdf2 ? 2.0 * dt / 3.0 : dt;
   b->ctx->h_step = dt;
   mls_status st;
   switch (b->ctx->opt.precision) {
-    case MLS_FP64: st = batch_step_t<double, double>(b, x, v, dt, dx_out); break;
-    case MLS_MIXED_FP32: st = batch_step_t<float, float>(b, x, v, dt, dx_out); break;
-    default: st = batch_step_t<float, __nv_bfloat16>(b, x, v, dt, dx_out); break;
+    case MLS_FP64: st = batch_step_t<double, double>(b, x, v, xp, vp, dt, dx_out); break;
+    case MLS_MIXED_FP32: st = batch_step_t<float, float>(b, x, v, xp, vp, dt, dx_out); break;
+    default: st = batch_step_t<float, __nv_bfloat16>(b, x, v, xp, vp, dt, dx_out); break;
   }
   if (st != MLS_OK) return st;
   mls_status worst = MLS_OK;
@@ -1843,6 +1873,19 @@ mls_status mls_batch_step(mls_batch* b, const double* x, const double* v, double
     else b->err = "a mesh failed (see the per-mesh status)";
   }
   return worst;
+}
+
+mls_status mls_batch_step(mls_batch* b, const double* x, const double* v, double dt, double* dx_out,
+                          mls_batch_mesh_stats* stats, mls_batch_info* info) {
+  return batch_step_entry(b, x, v, nullptr, nullptr, dt, dx_out, stats, info);
+}
+
+mls_status mls_batch_step_bdf2(mls_batch* b, const double* x, const double* v, const double* x_prev,
+                               const double* v_prev, double dt, double* dx_out, mls_batch_mesh_stats* stats,
+                               mls_batch_info* info) {
+  if (!b) return MLS_EINVAL;
+  if (!x_prev || !v_prev) return bfail(b, MLS_EINVAL, "null history pointer");
+  return batch_step_entry(b, x, v, x_prev, v_prev, dt, dx_out, stats, info);
 }
 
 }  // extern "C"

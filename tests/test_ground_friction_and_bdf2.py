@@ -191,3 +191,35 @@ def test_batch_with_friction_matches_oracle_per_mesh():
         assert st["status"] == 0
         x_o, _ = newton.timestep(ip.Problem(sc, mu=MU, eps_v=EPS_V))
         assert rel_disp_error(sc.x0 + dxh[sl], x_o, sc.x0) <= 1e-9
+
+
+def test_batch_bdf2_with_friction_matches_oracle_and_switches_back():
+    """BDF2 steps of a batch with friction, each mesh against the oracle's
+    BDF2 step; then an implicit-Euler step on the same batch (the step graph
+    is rebuilt for each integrator) against the oracle's implicit Euler."""
+    import paper_2508_13386_gb300 as mls
+    scenes = [_ground_block(0.6, seed=4), synth.tiny_scene(4, 3, 2, seed=6, contact=True, pinned=True)]
+    h = scenes[0].dt
+    b = mls.Batch(precision="fp64", newton_tol=1e-10)
+    b.upload_scenes(scenes)
+    b.set_friction(MU, EPS_V)
+    x_prev = [s.x0 - h * s.v0 for s in scenes]
+    for sc, xp in zip(scenes, x_prev):
+        xp[np.asarray(sc.dirichlet, bool)] = sc.x0[np.asarray(sc.dirichlet, bool)]
+    cat = lambda arrs: dev(np.concatenate(arrs))            # noqa: E731
+    x, v = cat([s.x0 for s in scenes]), cat([s.v0 for s in scenes])
+    dx, stats, info = b.step_bdf2(x, v, cat(x_prev), cat([s.v0 for s in scenes]), h)
+    assert info["status"] == 0
+    dx_ie, stats_ie, info_ie = b.step(x, v, h)
+    assert info_ie["status"] == 0
+    dxh, dxh_ie = host(dx), host(dx_ie)
+    k = 0
+    for sc, xp, st in zip(scenes, x_prev, stats):
+        sl = slice(k, k + sc.n_verts)
+        k += sc.n_verts
+        assert st["status"] == 0
+        p = ip.Problem(sc, integrator="bdf2", x_prev=xp, v_prev=sc.v0, mu=MU, eps_v=EPS_V)
+        x_o, _ = newton.timestep(p)
+        assert rel_disp_error(sc.x0 + dxh[sl], x_o, sc.x0) <= 1e-9
+        x_ie, _ = newton.timestep(ip.Problem(sc, mu=MU, eps_v=EPS_V))
+        assert rel_disp_error(sc.x0 + dxh_ie[sl], x_ie, sc.x0) <= 1e-9
