@@ -136,6 +136,14 @@ typedef struct mls_stats {
   double energy;           /* E at the returned iterate */
   int64_t kernel_launches; /* CUDA kernels this call launched */
   int warm_start_used;     /* 1 if the step started from the network's prediction */
+  int coarse_shifts;       /* coarse factorisations retried with a diagonal shift:
+                              a non-positive pivot in U^T H U is retried on
+                              U^T H U + sigma diag(U^T H U), sigma = 1e-7, 1e-5,
+                              1e-3, 1e-1 (the operator only preconditions, so the
+                              converged direction does not change) */
+  int coarse_fallbacks;    /* Newton iterations preconditioned by block Jacobi
+                              because U^T H U stayed indefinite after the shift
+                              retries (the next iteration builds it again) */
 } mls_stats;
 
 typedef struct mls_ctx mls_ctx;
@@ -302,12 +310,20 @@ mls_status mls_prolong(mls_ctx* ctx, const double* q, double* w);
 /* z = U^T r (restriction): r [n][3] -> z [m][12]. */
 mls_status mls_restrict(mls_ctx* ctx, const double* r, double* z);
 
-/* Build the Galerkin operator A_c = U^T H U from the assembled H and factor
- * it (dense Cholesky, float64).  MLS_ECHOL if a pivot is not positive. */
+/* Build the Galerkin operator A_c = U^T H U from the assembled H (summed in
+ * float64 from H's stored values in every precision) and factor it (dense
+ * Cholesky, float64).  A non-positive pivot retries the factorisation of
+ * A_c + sigma diag(A_c) for sigma = 1e-7, 1e-5, 1e-3, 1e-1; MLS_ECHOL if the
+ * last retry fails too.  mls_get_coarse returns the unshifted A_c. */
 mls_status mls_build_coarse(mls_ctx* ctx);
 
 /* Copy A_c (HOST, [12m][12m] float64, before factorisation) out. */
 mls_status mls_get_coarse(mls_ctx* ctx, double* A);
+
+/* *sigma (HOST) = the relative diagonal shift of the current coarse factor:
+ * 0 when U^T H U factored as built, else the sigma of the retry that
+ * succeeded (see mls_build_coarse).  MLS_EINVAL for a null argument. */
+mls_status mls_coarse_shift(mls_ctx* ctx, double* sigma);
 
 /* Energy E(x + alpha d) for the current timestep (after mls_assemble) and
  * whether the point is feasible (every J > 0 and every vertex above the
@@ -344,6 +360,21 @@ mls_status mls_profile_enable(mls_ctx* ctx, uint32_t mask);
 /* Read accumulated totals: ms[MLS_PROF_COUNT] milliseconds and
  * launches[MLS_PROF_COUNT] launch counts (HOST arrays, either nullable). */
 mls_status mls_profile_read(mls_ctx* ctx, double* ms, int64_t* launches);
+
+/* ---- Dense bf16 product on the tensor cores ------------------------------
+ * Not in the paper: the matrix product under the learned warm start's
+ * network (and exported so that it can be tested on its own).
+ *   C[M x N] = A[M x K] B[N x K]^T
+ * with A [M][lda] and B [N][ldb] bfloat16 row-major DEVICE arrays (K
+ * contiguous; lda, ldb >= K and multiples of 8; 16-byte aligned) and C
+ * float32 [M][ldc] (DEVICE, ldc >= N).  Products of bf16 values are exact
+ * and sums accumulate in float32 (tcgen05 with a tensor-memory accumulator,
+ * operands staged by TMA).  Waits for completion on stream (cudaStream_t,
+ * NULL = legacy default).  MLS_EINVAL for bad sizes, pitches or alignment;
+ * MLS_ETIMEOUT if a bounded device wait gave up (the result is then
+ * undefined).  Calls from several host threads are serialised. */
+mls_status mls_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, const void* B, int32_t ldb,
+                         float* C, int32_t ldc, void* stream);
 
 /* ---- Learned warm start: MLP trained and run by the library's kernels ----
  * Not in the paper (an extension): a 3-layer MLP, h1 = relu(x W1^T + b1),
@@ -443,7 +474,8 @@ typedef struct mls_batch mls_batch;
 
 typedef struct mls_batch_mesh_stats {
   int32_t status;             /* MLS_OK, MLS_ENOTCONV, MLS_ELINESEARCH, MLS_ENONFINITE, MLS_EINVERTED,
-                                 MLS_ECHOL (a coarse block not positive definite) */
+                                 MLS_ECHOL (a coarse block not positive definite after
+                                 the diagonal-shift retries of mls_build_coarse) */
   int32_t newton_iters;
   int32_t pcg_iters;          /* summed over the mesh's Newton iterations */
   int32_t line_search_trials;
@@ -560,7 +592,9 @@ mls_status mls_selftest_barrier(int32_t blocks, int32_t expected, int32_t spin_l
  * the scratch: calls whose kernels can overlap on the GPU (other streams or
  * host threads on the same device) race and must be serialised.  The first
  * call on each device looks up the scratch address with that device current;
- * make it before any stream capture. */
+ * make it before any stream capture.  That address belongs to the device's
+ * primary context and stays cached for the life of the process: after
+ * cudaDeviceReset on a device, do not call this entry point on it again. */
 #define MLS_NOALLOC_MAX_TETS (4096 * 256)
 mls_status mls_elastic_energy_noalloc(int32_t n_verts, int32_t n_tets, const double* rest_xyz,
                                       const int32_t* tets, const double* mu, const double* lam,

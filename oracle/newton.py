@@ -129,15 +129,19 @@ def timestep(prob, xtol_rel=1e-12, max_iter=100, method="auto", x_init=None):
 
 def paper_timestep(prob, U, n_cg=20, tol=1e-3, max_iter=100):
     """The paper's inexact multilevel timestep (Alg. 1 with Alg. 2's
-    directions, Sec. 3.9), as the readings of this oracle state it:
+    directions, Sec. 3.9):
 
-    * each iteration: d_s = U (U^T H U)^{-1} U^T (-g) (the subspace levels
-      solved exactly, reading 10), d_f = n_cg block-Jacobi CG iterations on
-      H d_f = -g - H d_s from zero with the fresh H (reading 22), d = d_s + d_f;
+    * each iteration: d_s = U (U^T H U)^{-1} U^T (-g), the subspace levels of
+      Alg. 2 solved exactly (with partition-of-unity SMS weights the affine
+      space lies inside the SMS space, so the two tight subspace solves give
+      this Galerkin direction); d_f = n_cg block-Jacobi CG iterations on
+      H d_f = -g - H d_s from zero (Sec. 3.7.2) with the Hessian freshly
+      evaluated at the iterate rather than lagged; d = d_s + d_f;
     * the same filtered line search as ``timestep`` (CCD cut, feasibility,
       Armijo);
     * after the update, stop when the mean vertex speed of the subspace
-      step, sum_v |d_s,v|_2 / (h n), is below ``tol`` (m/s, reading 21).
+      step, sum_v |d_s,v|_2 / (h n), is below ``tol`` (m/s): the paper's
+      test |d_s| / (h |V|) < tol of Sec. 3.9 with |d_s| read per vertex.
 
     Returns (x^{t+1}, info) with per-iteration step sizes and decrements."""
     from . import subspace

@@ -297,6 +297,12 @@ class Solver:
         self._check(self._l.mls_smoother_omega(self._ctx, C.byref(om), C.byref(lm)))
         return om.value, lm.value
 
+    def coarse_shift(self):
+        """Relative diagonal shift of the current coarse factor (0: none); see mls_coarse_shift."""
+        sig = C.c_double()
+        self._check(self._l.mls_coarse_shift(self._ctx, C.byref(sig)))
+        return sig.value
+
     def get_coarse(self):
         r = 12 * self.m
         A = np.zeros((r, r), dtype=np.float64)

@@ -56,6 +56,8 @@ class Stats(C.Structure):
         ("energy", C.c_double),
         ("kernel_launches", C.c_int64),
         ("warm_start_used", C.c_int),
+        ("coarse_shifts", C.c_int),
+        ("coarse_fallbacks", C.c_int),
     ]
 
     def as_dict(self):
@@ -93,11 +95,13 @@ SIGNATURES = {
     "mls_restrict": [_P, _P, _P],
     "mls_build_coarse": [_P],
     "mls_get_coarse": [_P, _P],
+    "mls_coarse_shift": [_P, _P],
     "mls_energy": [_P, _P, _P, _D, C.POINTER(_D), C.POINTER(_I)],
     "mls_ccd_bound": [_P, _P, _P, C.POINTER(_D)],
     "mls_profile_enable": [_P, C.c_uint32],
     "mls_profile_read": [_P, _P, _P],
     "mls_elastic_energy_noalloc": [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P],
+    "mls_gemm_bf16": [_I32, _I32, _I32, _P, _I32, _P, _I32, _P, _I32, _P],
     "mls_mlp_create": [C.POINTER(_P), _I32, _I32, _I32, _I32, _P, _P],
     "mls_mlp_destroy": [_P],
     "mls_mlp_param_count": [_P],

@@ -668,39 +668,60 @@ struct BCoarse {
 __device__ __forceinline__ bool pcg_active(const BMesh* M) { return M->phase == BPH_ASSEMBLE && !M->done; }
 
 // right-looking Cholesky of the mesh's diagonal block of A (float64, leading
-// dimension ld), in place; a non-positive pivot fails the mesh (MLS_ECHOL)
-__global__ void __launch_bounds__(256) k_bchol(BView V, BCoarse C, double* __restrict__ A, int ld) {
+// dimension ld), in place.  The block's lower triangle is saved to the same
+// place in S first; a non-positive pivot restores it with the diagonal
+// scaled by 1 + sigma and factors again (kShiftTries retries, sigma from
+// kShiftFirst growing kShiftGrowth-fold); if the last retry fails too, the
+// mesh fails (MLS_ECHOL)
+__global__ void __launch_bounds__(256) k_bchol(BView V, BCoarse C, double* __restrict__ A, double* __restrict__ S,
+                                               int ld) {
   const int m = blockIdx.x;
   BMesh* M = V.M + m;
   if (M->phase == BPH_DONE) return;
   const int o = C.coff[m], n = C.csz[m];
   double* a = A + (int64_t)o * ld + o;
+  double* sv = S + (int64_t)o * ld + o;
   __shared__ double col[kMaxCoarseRows];
   __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = 0; j < n; ++j) {
+  for (int i = warp; i < n; i += nw)
+    for (int k = lane; k <= i; k += 32) sv[(int64_t)i * ld + k] = a[(int64_t)i * ld + k];
+  double sigma = 0.0;
+  for (int attempt = 0; attempt <= kShiftTries; ++attempt) {
+    if (attempt > 0) {
+      sigma = attempt == 1 ? kShiftFirst : sigma * kShiftGrowth;
+      __syncthreads();
+      for (int i = warp; i < n; i += nw)
+        for (int k = lane; k <= i; k += 32) {
+          const double s0 = sv[(int64_t)i * ld + k];
+          a[(int64_t)i * ld + k] = (k == i) ? s0 + sigma * fmax(s0, 0.0) : s0;
+        }
+    }
+    if (threadIdx.x == 0) bad = 0;
+    for (int j = 0; j < n; ++j) {
+      __syncthreads();
+      const double d = a[(int64_t)j * ld + j];
+      if (!(d > 0.0) || !isfinite(d)) {
+        if (threadIdx.x == 0) bad = j + 1;
+        break;
+      }
+      const double piv = sqrt(d), inv = 1.0 / piv;
+      for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const double v = a[(int64_t)i * ld + j] * inv;
+        a[(int64_t)i * ld + j] = v;
+        col[i] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) a[(int64_t)j * ld + j] = piv;
+      for (int i = j + 1 + warp; i < n; i += nw) {
+        const double li = col[i];
+        double* ai = a + (int64_t)i * ld;
+        for (int k = j + 1 + lane; k <= i; k += 32) ai[k] -= li * col[k];
+      }
+    }
     __syncthreads();
-    const double d = a[(int64_t)j * ld + j];
-    if (!(d > 0.0) || !isfinite(d)) {
-      if (threadIdx.x == 0) bad = j + 1;
-      break;
-    }
-    const double piv = sqrt(d), inv = 1.0 / piv;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
-      const double v = a[(int64_t)i * ld + j] * inv;
-      a[(int64_t)i * ld + j] = v;
-      col[i] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) a[(int64_t)j * ld + j] = piv;
-    for (int i = j + 1 + warp; i < n; i += nw) {
-      const double li = col[i];
-      double* ai = a + (int64_t)i * ld;
-      for (int k = j + 1 + lane; k <= i; k += 32) ai[k] -= li * col[k];
-    }
+    if (!bad) break;
   }
-  __syncthreads();
   if (threadIdx.x == 0 && bad) {
     M->status = MLS_ECHOL;
     M->phase = BPH_DONE;
@@ -1250,7 +1271,7 @@ mls_status launch_coarse(mls_batch* b, cudaStream_t s) {
   mls_ctx* c = b->ctx;
   mls_status st = build_galerkin(c);
   if (st != MLS_OK) return bfail(b, st, mls_last_error(c));
-  k_bchol<<<b->nmesh, 256, 0, s>>>(b->view, b->coarse, c->Ac, b->coarse.r);
+  k_bchol<<<b->nmesh, 256, 0, s>>>(b->view, b->coarse, c->Ac, c->Acopy, b->coarse.r);
   k_btrinv<VT><<<b->nmesh, 256, 0, s>>>(b->view, b->coarse, c->Ac, c->Acopy, b->coarse.r, (VT*)b->W, (VT*)b->WT);
   return bcheck(b, cudaGetLastError(), "batched coarse factor");
 }

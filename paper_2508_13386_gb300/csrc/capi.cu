@@ -142,6 +142,8 @@ static void free_all(mls_ctx* ctx) {
   ctx->ws_hist = ctx->ws_qg = ctx->ws_qtilde = ctx->ws_qnext = nullptr;
   ctx->ws_feat = ctx->ws_target = ctx->ws_pred = nullptr;
   ctx->ws_hsave = nullptr;
+  ctx->oz_fwd = ctx->oz_rev = nullptr;
+  ctx->oz_e = ctx->umma_err = nullptr;
   ctx->ws_ready = ctx->ws_enabled = ctx->ws_hist_valid = ctx->ws_record = false;
   ctx->ws_mlp = nullptr;
   ctx->basis = Basis{};
@@ -561,9 +563,10 @@ static mls_status paper_direction(mls_ctx* ctx, double* ds_norm, int* cg_iters) 
 constexpr double kLagStaleRatio = 1.5;
 constexpr int kLagStaleSlack = 8;
 
-static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
+static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
   mls_stats S{};
   mls_status st;
+  const int64_t shifts0 = ctx->coarse_shift_count;
   if (ctx->coarse_ready) ctx->coarse_age_steps++;
   const double h = ctx->h_step;  // the timestep (ctx->h is the potential's step, 2h/3 for BDF2)
   const double gmag = std::sqrt(ctx->grav[0] * ctx->grav[0] + ctx->grav[1] * ctx->grav[1] + ctx->grav[2] * ctx->grav[2]);
@@ -609,8 +612,19 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
           ctx->coarse_age_steps <= ctx->opt.coarse_lag_steps)
         rebuild = false;
       if (rebuild) {
-        if ((st = build_coarse(ctx)) != MLS_OK) return st;
-        S.coarse_builds++;
+        st = build_coarse(ctx);
+        // a coarse operator that stays indefinite after the shift retries:
+        // this Newton iteration preconditions with block Jacobi, and the
+        // next one tries the coarse build again at its own iterate
+        if (st == MLS_ECHOL && !paper) {
+          ctx->coarse_fallback = true;
+          S.coarse_fallbacks++;
+        } else if (st != MLS_OK) {
+          return st;
+        } else {
+          ctx->coarse_fallback = false;
+          S.coarse_builds++;
+        }
       }
       lagged_first = it == 0 && !rebuild;
     }
@@ -720,9 +734,18 @@ static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
   if (result == MLS_OK && (st = warm_start_end(ctx)) != MLS_OK) return st;
   prof_flush(ctx);
   S.energy = E;
+  S.coarse_shifts = (int)(ctx->coarse_shift_count - shifts0);
   if (stats) *stats = S;
   if (result != MLS_OK) return fail(ctx, result, "Newton reached its iteration cap");
   return MLS_OK;
+}
+
+// The block-Jacobi fallback of a failed coarse build lasts one Newton loop
+static mls_status newton(mls_ctx* ctx, mls_stats* stats) {
+  ctx->coarse_fallback = false;
+  const mls_status st = newton_loop(ctx, stats);
+  ctx->coarse_fallback = false;
+  return st;
 }
 
 static mls_status check_mesh(mls_ctx* ctx) {
@@ -827,6 +850,7 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
                    B.vcoef, B.hcoef, B.rchunk_handle, B.rchunk_beg, B.rchunk_ptr, B.rpart, B.rcount,
                    ctx->gpart, ctx->yval, ctx->Ac, ctx->Acopy,
                    ctx->Linv, ctx->LinvT, ctx->Ainv, ctx->cvec, ctx->cvec2, ctx->chol_info, ctx->chol_tinv,
+                   ctx->oz_fwd, ctx->oz_rev, ctx->oz_e,
                    ctx->Am, ctx->Wm, ctx->WmT, ctx->ws_c, ctx->ws_c2, ctx->ws_tmp, ctx->ws_hist, ctx->ws_qg,
                    ctx->ws_qtilde, ctx->ws_qnext, ctx->ws_feat, ctx->ws_target, ctx->ws_pred, ctx->ws_hsave};
     for (void* p : old) dfree(ctx, p);
@@ -834,6 +858,8 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
     ctx->ws_hist = ctx->ws_qg = ctx->ws_qtilde = ctx->ws_qnext = nullptr;
     ctx->ws_feat = ctx->ws_target = ctx->ws_pred = nullptr;
     ctx->ws_hsave = nullptr;
+    ctx->oz_fwd = ctx->oz_rev = nullptr;
+    ctx->oz_e = nullptr;
     ctx->ws_ready = ctx->ws_enabled = ctx->ws_hist_valid = ctx->ws_record = false;
     ctx->ws_mlp = nullptr;
     ctx->basis = Basis{};
@@ -1034,6 +1060,12 @@ mls_status mls_build_coarse(mls_ctx* ctx) {
   st = build_coarse(ctx);
   if (st != MLS_OK) return st;
   return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "coarse sync");
+}
+
+mls_status mls_coarse_shift(mls_ctx* ctx, double* sigma) {
+  if (!ctx || !sigma) return MLS_EINVAL;
+  *sigma = ctx->coarse_sigma;
+  return MLS_OK;
 }
 
 mls_status mls_get_coarse(mls_ctx* ctx, double* A) {

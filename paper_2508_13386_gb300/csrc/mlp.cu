@@ -5,9 +5,12 @@
 //   L  = 1/(2B) sum_b |y_b - t_b|^2,  Adam (beta1 0.9, beta2 0.999, eps 1e-8)
 //
 // Weights are kept as FP32 master copies (for Adam) and as BF16 copies that
-// the matrix products read; products run on the tensor cores with BF16
-// operands and FP32 accumulation (mma.sync m16n8k16), activations and
-// gradients are FP32 in memory and rounded to BF16 when staged as operands.
+// the matrix products read (row-major and, for the backward products,
+// transposed); every product runs on the tensor cores (umma.cu: tcgen05 with
+// TMA-staged bf16 operands and FP32 accumulation in tensor memory).
+// Activations and back-propagated errors are kept in FP32 and, as the
+// operands of the next products, rounded to BF16 by the product that forms
+// them (row-major and transposed copies).
 #include "mls_internal.cuh"
 
 #include <algorithm>
@@ -16,129 +19,24 @@
 
 namespace mls {
 
-// ---- generic tensor-core GEMM: C[M x N] = A[M x K] B[K x N] ---------------------------
-// Element (m, k) of A is A[m * sam + k * sak] and (k, n) of B is B[k * sbk + n * sbn],
-// so any transposition is a choice of strides.  Epilogue:
-//   C[m * ldc + n] = acc (+ bias[n]) (then relu) (then * (mask[m * ldc + n] > 0))
-//                    (then * oscale[n] + oshift[n])
-// and A's elements may be standardised on load: (A - amu[k]) * aisd[k].
-constexpr int GBM = 64, GBN = 64, GBK = 32;
-
-template <typename T> __device__ __forceinline__ __nv_bfloat16 to_bf16(T v);
-template <> __device__ __forceinline__ __nv_bfloat16 to_bf16<float>(float v) { return __float2bfloat16(v); }
-template <> __device__ __forceinline__ __nv_bfloat16 to_bf16<__nv_bfloat16>(__nv_bfloat16 v) { return v; }
-
-__device__ __forceinline__ uint32_t pack2(const __nv_bfloat16* p) {
-  return *reinterpret_cast<const uint32_t*>(p);
-}
-
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(128) k_gemm_bf16(int M, int N, int K, const TA* __restrict__ A, int64_t sam,
-                                                   int64_t sak, const TB* __restrict__ B, int64_t sbk, int64_t sbn,
-                                                   float* __restrict__ C, int ldc, const float* __restrict__ bias,
-                                                   int relu, const float* __restrict__ mask,
-                                                   const float* __restrict__ amu, const float* __restrict__ aisd,
-                                                   const float* __restrict__ oscale, const float* __restrict__ oshift) {
-  __shared__ __align__(16) __nv_bfloat16 As[GBM][GBK + 8];
-  __shared__ __align__(16) __nv_bfloat16 Bs[GBN][GBK + 8];  // stored [n][k]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  const int g = lane >> 2, tq = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += GBK) {
-    for (int idx = tid; idx < GBM * GBK; idx += 128) {
-      const int mm = idx / GBK, kk = idx % GBK;
-      const int gm = m0 + mm, gk = k0 + kk;
-      if (gm < M && gk < K) {
-        if (amu) As[mm][kk] = __float2bfloat16(((float)A[gm * sam + gk * sak] - amu[gk]) * aisd[gk]);
-        else As[mm][kk] = to_bf16<TA>(A[gm * sam + gk * sak]);
-      } else {
-        As[mm][kk] = __float2bfloat16(0.f);
-      }
-    }
-    for (int idx = tid; idx < GBN * GBK; idx += 128) {
-      const int nn = idx / GBK, kk = idx % GBK;
-      const int gn = n0 + nn, gk = k0 + kk;
-      Bs[nn][kk] = (gn < N && gk < K) ? to_bf16<TB>(B[gk * sbk + gn * sbn]) : __float2bfloat16(0.f);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < GBK; ks += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + 16 * i + g;
-        a[i][0] = pack2(&As[r][ks + 2 * tq]);
-        a[i][1] = pack2(&As[r + 8][ks + 2 * tq]);
-        a[i][2] = pack2(&As[r][ks + 2 * tq + 8]);
-        a[i][3] = pack2(&As[r + 8][ks + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + 8 * j + g;
-        b[j][0] = pack2(&Bs[c][ks + 2 * tq]);
-        b[j][1] = pack2(&Bs[c][ks + 2 * tq + 8]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-              "{%0,%1,%2,%3};\n"
-              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int m = m0 + wm + 16 * i + g + (q >= 2 ? 8 : 0);
-        const int n = n0 + wn + 8 * j + 2 * tq + (q & 1);
-        if (m < M && n < N) {
-          float v = acc[i][j][q];
-          if (bias) v += bias[n];
-          if (relu) v = fmaxf(v, 0.f);
-          if (mask && !(mask[(int64_t)m * ldc + n] > 0.f)) v = 0.f;
-          if (oscale) v = v * oscale[n] + oshift[n];
-          C[(int64_t)m * ldc + n] = v;
-        }
-      }
-}
-
-template <typename TA, typename TB>
-static void gemm(cudaStream_t s, int M, int N, int K, const TA* A, int64_t sam, int64_t sak, const TB* B,
-                 int64_t sbk, int64_t sbn, float* C, int ldc, const float* bias, int relu, const float* mask,
-                 const float* amu = nullptr, const float* aisd = nullptr, const float* oscale = nullptr,
-                 const float* oshift = nullptr) {
-  dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
-  k_gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, relu, mask, amu, aisd,
-                                          oscale, oshift);
-}
-
 // dY = (Y - That) / B with That = (T - tmu) * tisd (standardised targets, when
-// tmu is given; cols = width of a row), loss partials
+// tmu is given; cols = width of a row), loss partials; dY is also written
+// rounded to bf16, row-major [B][ld16] and transposed [cols][ld16t]
 __global__ void k_mlp_dy(int n, int cols, float invB, const float* __restrict__ Y, const float* __restrict__ T,
                          const float* __restrict__ tmu, const float* __restrict__ tisd, float* __restrict__ dY,
+                         __nv_bfloat16* __restrict__ dy16, int ld16, __nv_bfloat16* __restrict__ dy16t, int ld16t,
                          double* __restrict__ loss) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double l = 0.0;
   if (i < n) {
-    const int c = i % cols;
+    const int r = i / cols, c = i % cols;
     const float t = tmu ? (T[i] - tmu[c]) * tisd[c] : T[i];
     const float d = Y[i] - t;
-    dY[i] = d * invB;
+    const float g = d * invB;
+    dY[i] = g;
+    const __nv_bfloat16 gb = __float2bfloat16(g);
+    dy16[(int64_t)r * ld16 + c] = gb;
+    dy16t[(int64_t)c * ld16t + r] = gb;
     l = 0.5 * (double)d * d * invB;
   }
 #pragma unroll
@@ -155,10 +53,9 @@ __global__ void k_colsum(int rows, int cols, const float* __restrict__ D, float*
   out[c] = s;
 }
 
-// Adam on a flat parameter array, refreshing the BF16 copy
-__global__ void k_adam(int64_t n, float* __restrict__ w, __nv_bfloat16* __restrict__ wb, const float* __restrict__ g,
-                       float* __restrict__ m, float* __restrict__ v, float lr, float b1, float b2, float c1, float c2,
-                       float eps) {
+// Adam on a flat parameter array
+__global__ void k_adam(int64_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float c1, float c2, float eps) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
@@ -168,7 +65,6 @@ __global__ void k_adam(int64_t n, float* __restrict__ w, __nv_bfloat16* __restri
   v[i] = vi;
   const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
   w[i] = wi;
-  if (wb) wb[i] = __float2bfloat16(wi);
 }
 
 // rows order[0..B) of X [n][cols] -> out [B][cols]
@@ -180,9 +76,20 @@ __global__ void k_gather_rows(int B, int cols, const int* __restrict__ order, co
   out[i] = X[(int64_t)order[r] * cols + c];
 }
 
-__global__ void k_to_bf16(int64_t n, const float* __restrict__ a, __nv_bfloat16* __restrict__ b) {
+// bf16 copy of a row-major FP32 matrix [rows][cols] with row pitch ld (dst,
+// nullable) and of its transpose [cols][ldt] (dst_t, nullable); with mu the
+// columns are standardised first, (a - mu[c]) isd[c]
+__global__ void k_to_bf16_2d(int rows, int cols, const float* __restrict__ a, const float* __restrict__ mu,
+                             const float* __restrict__ isd, __nv_bfloat16* __restrict__ dst, int ld,
+                             __nv_bfloat16* __restrict__ dst_t, int ldt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = __float2bfloat16(a[i]);
+  if (i >= (int64_t)rows * cols) return;
+  const int r = (int)(i / cols), c = (int)(i % cols);
+  float v = a[i];
+  if (mu) v = (v - mu[c]) * isd[c];
+  const __nv_bfloat16 b = __float2bfloat16(v);
+  if (dst) dst[(int64_t)r * ld + c] = b;
+  if (dst_t) dst_t[(int64_t)c * ldt + r] = b;
 }
 
 }  // namespace mls
@@ -210,13 +117,22 @@ struct mls_mlp {
   int in = 0, hid = 0, out = 0, max_batch = 0;
   cudaStream_t stream = nullptr;
   MlpLayout L{};
+  int in_p = 0, hid_p = 0, out_p = 0, bat_p = 0;  // row pitches of the bf16 operands (multiples of 8)
   float* w = nullptr;            // FP32 master parameters
-  __nv_bfloat16* wb = nullptr;   // BF16 copies read by the products
+  // BF16 copies read by the products: W1 [hid][in_p], W2 [hid][hid_p],
+  // W3 [out][hid_p], W2^T [hid][hid_p], W3^T [hid][out_p]
+  __nv_bfloat16 *w1b = nullptr, *w2b = nullptr, *w3b = nullptr, *w2tb = nullptr, *w3tb = nullptr;
+  // bf16 operands: (standardised) input, hidden activations and errors,
+  // row-major [B][.] and transposed [.][bat_p]
+  __nv_bfloat16 *xs16 = nullptr, *xs16t = nullptr, *z1_16 = nullptr, *z1_16t = nullptr, *z2_16 = nullptr,
+                *z2_16t = nullptr, *dy16 = nullptr, *dy16t = nullptr, *d2_16 = nullptr, *d2_16t = nullptr,
+                *d1_16t = nullptr;
+  int* err = nullptr;            // set by a product whose bounded wait gave up
   float* grad = nullptr;
   float* m = nullptr;
   float* v = nullptr;
   float *z1 = nullptr, *z2 = nullptr, *y = nullptr, *dy = nullptr, *d2 = nullptr, *d1 = nullptr;
-  float *xb = nullptr, *tb = nullptr;  // gathered minibatch
+  float* tb = nullptr;                  // gathered minibatch targets
   float* xg = nullptr;                  // gathered (raw) minibatch input
   // standardisation: inputs (x - mu_in) / sd_in, outputs y_raw = y sd_out + mu_out
   float *mu_in = nullptr, *isd_in = nullptr, *mu_out = nullptr, *isd_out = nullptr, *sd_out = nullptr;
@@ -239,63 +155,97 @@ static bool mlp_alloc(mls_mlp* p, void** dst, size_t bytes) {
   return true;
 }
 
+static inline int pad8(int v) { return (v + 7) & ~7; }
+
+// the BF16 copies of the weights (and of W2^T, W3^T) from the FP32 masters
+static void mlp_refresh_bf16(mls_mlp* p) {
+  const MlpLayout& L = p->L;
+  cudaStream_t s = p->stream;
+  auto conv = [&](int rows, int cols, const float* a, __nv_bfloat16* d, int ld, __nv_bfloat16* dt, int ldt) {
+    const int64_t n = (int64_t)rows * cols;
+    k_to_bf16_2d<<<(int)((n + 255) / 256), 256, 0, s>>>(rows, cols, a, nullptr, nullptr, d, ld, dt, ldt);
+  };
+  conv(p->hid, p->in, p->w + L.w1, p->w1b, p->in_p, nullptr, 0);
+  conv(p->hid, p->hid, p->w + L.w2, p->w2b, p->hid_p, p->w2tb, p->hid_p);
+  conv(p->out, p->hid, p->w + L.w3, p->w3b, p->hid_p, p->w3tb, p->out_p);
+}
+
+static void gemm(mls_mlp* p, int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+                 float* C, int ldc, const GemmEpilogue& ep) {
+  gemm_bf16_tn(p->stream, M, N, K, A, lda, B, ldb, C, ldc, ep, p->err);
+}
+
 // forward pass for B rows of X (float [B][in]); leaves z1, z2 (post-ReLU) and y
 // (standardised outputs, or raw outputs when raw_out is set and the network
-// carries a standardisation)
-static void mlp_forward(mls_mlp* p, const float* X, int B, bool raw_out = false) {
+// carries a standardisation), and the bf16 operands of the next products;
+// with `train` also the transposed copies the weight gradients read
+static void mlp_forward(mls_mlp* p, const float* X, int B, bool raw_out = false, bool train = false) {
   const MlpLayout& L = p->L;
   cudaStream_t s = p->stream;
   const bool nrm = p->normalised;
-  gemm<float, __nv_bfloat16>(s, B, p->hid, p->in, X, p->in, 1, p->wb + L.w1, 1, p->in, p->z1, p->hid,
-                             p->w + L.b1, 1, nullptr, nrm ? p->mu_in : nullptr, nrm ? p->isd_in : nullptr);
-  gemm<float, __nv_bfloat16>(s, B, p->hid, p->hid, p->z1, p->hid, 1, p->wb + L.w2, 1, p->hid, p->z2, p->hid,
-                             p->w + L.b2, 1, nullptr);
-  gemm<float, __nv_bfloat16>(s, B, p->out, p->hid, p->z2, p->hid, 1, p->wb + L.w3, 1, p->hid, p->y, p->out,
-                             p->w + L.b3, 0, nullptr, nullptr, nullptr, (raw_out && nrm) ? p->sd_out : nullptr,
-                             (raw_out && nrm) ? p->mu_out : nullptr);
+  const int64_t nx = (int64_t)B * p->in;
+  k_to_bf16_2d<<<(int)((nx + 255) / 256), 256, 0, s>>>(B, p->in, X, nrm ? p->mu_in : nullptr,
+                                                      nrm ? p->isd_in : nullptr, p->xs16, p->in_p,
+                                                      train ? p->xs16t : nullptr, p->bat_p);
+  GemmEpilogue e1;
+  e1.bias = p->w + L.b1; e1.relu = 1;
+  e1.out16 = p->z1_16; e1.ld16 = p->hid_p;
+  if (train) { e1.out16t = p->z1_16t; e1.ld16t = p->bat_p; }
+  gemm(p, B, p->hid, p->in, p->xs16, p->in_p, p->w1b, p->in_p, p->z1, p->hid, e1);
+  GemmEpilogue e2;
+  e2.bias = p->w + L.b2; e2.relu = 1;
+  e2.out16 = p->z2_16; e2.ld16 = p->hid_p;
+  if (train) { e2.out16t = p->z2_16t; e2.ld16t = p->bat_p; }
+  gemm(p, B, p->hid, p->hid, p->z1_16, p->hid_p, p->w2b, p->hid_p, p->z2, p->hid, e2);
+  GemmEpilogue e3;
+  e3.bias = p->w + L.b3;
+  if (raw_out && nrm) { e3.oscale = p->sd_out; e3.oshift = p->mu_out; }
+  gemm(p, B, p->out, p->hid, p->z2_16, p->hid_p, p->w3b, p->hid_p, p->y, p->out, e3);
 }
 
-// standardised copy of the network input X [B][in] (for the first layer's
-// weight gradient, which needs the same operand the forward pass used)
-__global__ void k_standardise(int64_t n, int cols, const float* __restrict__ X, const float* __restrict__ mu,
-                              const float* __restrict__ isd, float* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) {
-    const int c = (int)(i % cols);
-    out[i] = (X[i] - mu[c]) * isd[c];
-  }
-}
-
-// gradients of the loss for targets T into p->grad; loss accumulated in p->loss
-static void mlp_backward(mls_mlp* p, const float* X, const float* T, int B) {
+// gradients of the loss for targets T into p->grad after a training forward
+// pass on the same rows; loss accumulated in p->loss
+static void mlp_backward(mls_mlp* p, const float* T, int B) {
   const MlpLayout& L = p->L;
   cudaStream_t s = p->stream;
   const int no = B * p->out;
   const bool nrm = p->normalised;
   k_mlp_dy<<<(no + 255) / 256, 256, 0, s>>>(no, p->out, 1.f / B, p->y, T, nrm ? p->mu_out : nullptr,
-                                            nrm ? p->isd_out : nullptr, p->dy, p->loss);
+                                            nrm ? p->isd_out : nullptr, p->dy, p->dy16, p->out_p, p->dy16t, p->bat_p,
+                                            p->loss);
   // layer 3: dW3 = dY^T h2, db3 = colsum dY, d2 = (dY W3) * [h2 > 0]
-  gemm<float, float>(s, p->out, p->hid, B, p->dy, 1, p->out, p->z2, p->hid, 1, p->grad + L.w3, p->hid, nullptr, 0,
-                     nullptr);
+  gemm(p, p->out, p->hid, B, p->dy16t, p->bat_p, p->z2_16t, p->bat_p, p->grad + L.w3, p->hid, GemmEpilogue{});
   k_colsum<<<(p->out + 127) / 128, 128, 0, s>>>(B, p->out, p->dy, p->grad + L.b3);
-  gemm<float, __nv_bfloat16>(s, B, p->hid, p->out, p->dy, p->out, 1, p->wb + L.w3, p->hid, 1, p->d2, p->hid,
-                             nullptr, 0, p->z2);
+  GemmEpilogue e2;
+  e2.mask = p->z2;
+  e2.out16 = p->d2_16; e2.ld16 = p->hid_p;
+  e2.out16t = p->d2_16t; e2.ld16t = p->bat_p;
+  gemm(p, B, p->hid, p->out, p->dy16, p->out_p, p->w3tb, p->out_p, p->d2, p->hid, e2);
   // layer 2
-  gemm<float, float>(s, p->hid, p->hid, B, p->d2, 1, p->hid, p->z1, p->hid, 1, p->grad + L.w2, p->hid, nullptr, 0,
-                     nullptr);
+  gemm(p, p->hid, p->hid, B, p->d2_16t, p->bat_p, p->z1_16t, p->bat_p, p->grad + L.w2, p->hid, GemmEpilogue{});
   k_colsum<<<(p->hid + 127) / 128, 128, 0, s>>>(B, p->hid, p->d2, p->grad + L.b2);
-  gemm<float, __nv_bfloat16>(s, B, p->hid, p->hid, p->d2, p->hid, 1, p->wb + L.w2, p->hid, 1, p->d1, p->hid,
-                             nullptr, 0, p->z1);
-  // layer 1 (against the standardised input when the network carries one)
-  const float* Xop = X;
-  if (nrm) {
-    const int64_t nx = (int64_t)B * p->in;
-    k_standardise<<<(int)((nx + 255) / 256), 256, 0, s>>>(nx, p->in, X, p->mu_in, p->isd_in, p->xb);
-    Xop = p->xb;
-  }
-  gemm<float, float>(s, p->hid, p->in, B, p->d1, 1, p->hid, Xop, p->in, 1, p->grad + L.w1, p->in, nullptr, 0,
-                     nullptr);
+  GemmEpilogue e1;
+  e1.mask = p->z1;
+  e1.out16t = p->d1_16t; e1.ld16t = p->bat_p;
+  gemm(p, B, p->hid, p->hid, p->d2_16, p->hid_p, p->w2tb, p->hid_p, p->d1, p->hid, e1);
+  // layer 1, against the (standardised) input the forward pass used
+  gemm(p, p->hid, p->in, B, p->d1_16t, p->bat_p, p->xs16t, p->bat_p, p->grad + L.w1, p->in, GemmEpilogue{});
   k_colsum<<<(p->hid + 127) / 128, 128, 0, s>>>(B, p->hid, p->d1, p->grad + L.b1);
+}
+
+// the error flag of the products: cleared, and read after a synchronisation
+static mls_status mlp_check(mls_mlp* p) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+      cudaStreamSynchronize(p->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return MLS_ECUDA;
+  }
+  if (h) {
+    cudaMemsetAsync(p->err, 0, sizeof(int), p->stream);
+    return MLS_ETIMEOUT;
+  }
+  return MLS_OK;
 }
 
 extern "C" {
@@ -309,15 +259,27 @@ mls_status mls_mlp_create(mls_mlp** out, int32_t n_in, int32_t n_hidden, int32_t
   p->in = n_in; p->hid = n_hidden; p->out = n_out; p->max_batch = max_batch;
   p->stream = (cudaStream_t)stream;
   p->L = layout(n_in, n_hidden, n_out);
+  p->in_p = pad8(n_in); p->hid_p = pad8(n_hidden); p->out_p = pad8(n_out); p->bat_p = pad8(max_batch);
   const int64_t P = p->L.total;
   const int64_t act = (int64_t)max_batch * std::max(n_hidden, n_out);
-  bool ok = mlp_alloc(p, (void**)&p->w, 4 * P) && mlp_alloc(p, (void**)&p->wb, 2 * P) &&
+  const size_t bat = (size_t)p->bat_p, mb = (size_t)max_batch;
+  bool ok = mlp_alloc(p, (void**)&p->w, 4 * P) &&
+            mlp_alloc(p, (void**)&p->w1b, 2 * (size_t)n_hidden * p->in_p) &&
+            mlp_alloc(p, (void**)&p->w2b, 2 * (size_t)n_hidden * p->hid_p) &&
+            mlp_alloc(p, (void**)&p->w3b, 2 * (size_t)n_out * p->hid_p) &&
+            mlp_alloc(p, (void**)&p->w2tb, 2 * (size_t)n_hidden * p->hid_p) &&
+            mlp_alloc(p, (void**)&p->w3tb, 2 * (size_t)n_hidden * p->out_p) &&
+            mlp_alloc(p, (void**)&p->xs16, 2 * mb * p->in_p) && mlp_alloc(p, (void**)&p->xs16t, 2 * (size_t)n_in * bat) &&
+            mlp_alloc(p, (void**)&p->z1_16, 2 * mb * p->hid_p) && mlp_alloc(p, (void**)&p->z1_16t, 2 * (size_t)n_hidden * bat) &&
+            mlp_alloc(p, (void**)&p->z2_16, 2 * mb * p->hid_p) && mlp_alloc(p, (void**)&p->z2_16t, 2 * (size_t)n_hidden * bat) &&
+            mlp_alloc(p, (void**)&p->dy16, 2 * mb * p->out_p) && mlp_alloc(p, (void**)&p->dy16t, 2 * (size_t)n_out * bat) &&
+            mlp_alloc(p, (void**)&p->d2_16, 2 * mb * p->hid_p) && mlp_alloc(p, (void**)&p->d2_16t, 2 * (size_t)n_hidden * bat) &&
+            mlp_alloc(p, (void**)&p->d1_16t, 2 * (size_t)n_hidden * bat) && mlp_alloc(p, (void**)&p->err, sizeof(int)) &&
             mlp_alloc(p, (void**)&p->grad, 4 * P) && mlp_alloc(p, (void**)&p->m, 4 * P) &&
             mlp_alloc(p, (void**)&p->v, 4 * P) && mlp_alloc(p, (void**)&p->z1, 4 * act) &&
             mlp_alloc(p, (void**)&p->z2, 4 * act) && mlp_alloc(p, (void**)&p->y, 4 * act) &&
             mlp_alloc(p, (void**)&p->dy, 4 * act) && mlp_alloc(p, (void**)&p->d2, 4 * act) &&
             mlp_alloc(p, (void**)&p->d1, 4 * act) && mlp_alloc(p, (void**)&p->loss, 8) &&
-            mlp_alloc(p, (void**)&p->xb, 4 * (size_t)max_batch * n_in) &&
             mlp_alloc(p, (void**)&p->tb, 4 * (size_t)max_batch * n_out) &&
             mlp_alloc(p, (void**)&p->xg, 4 * (size_t)max_batch * n_in) &&
             mlp_alloc(p, (void**)&p->mu_in, 4 * (size_t)n_in) && mlp_alloc(p, (void**)&p->isd_in, 4 * (size_t)n_in) &&
@@ -326,12 +288,13 @@ mls_status mls_mlp_create(mls_mlp** out, int32_t n_in, int32_t n_hidden, int32_t
   if (ok && cudaMallocHost((void**)&p->loss_host, 8) != cudaSuccess) { cudaGetLastError(); ok = false; }
   if (!ok) { mlp_free(p); return MLS_ENOMEM; }
   if (cudaMemcpy(p->w, init_params, 4 * P, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(p->m, 0, 4 * P) != cudaSuccess || cudaMemset(p->v, 0, 4 * P) != cudaSuccess) {
+      cudaMemset(p->m, 0, 4 * P) != cudaSuccess || cudaMemset(p->v, 0, 4 * P) != cudaSuccess ||
+      cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     mlp_free(p);
     return MLS_ECUDA;
   }
-  k_to_bf16<<<(int)((P + 255) / 256), 256, 0, p->stream>>>(P, p->w, p->wb);
+  mlp_refresh_bf16(p);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess) {
     cudaGetLastError();
     mlp_free(p);
@@ -358,7 +321,7 @@ mls_status mlp_forward_raw(mls_mlp* p, const float* X, int32_t batch, float* Y, 
   if (!p || batch < 1 || batch > p->max_batch) return MLS_EINVAL;
   cudaStream_t keep = p->stream;
   p->stream = stream;
-  mlp_forward(p, X, batch, true);
+  mlp_forward(p, X, batch, true, false);
   cudaMemcpyAsync(Y, p->y, 4 * (size_t)batch * p->out, cudaMemcpyDeviceToDevice, stream);
   p->stream = keep;
   return cudaGetLastError() == cudaSuccess ? MLS_OK : MLS_ECUDA;
@@ -374,32 +337,28 @@ mls_status mls_mlp_forward(mls_mlp* p, const float* X, int32_t batch, float* Y) 
   if (!p || !X || !Y || batch < 1) return MLS_EINVAL;
   for (int b0 = 0; b0 < batch; b0 += p->max_batch) {
     const int B = std::min(p->max_batch, batch - b0);
-    mlp_forward(p, X + (int64_t)b0 * p->in, B, true);
+    mlp_forward(p, X + (int64_t)b0 * p->in, B, true, false);
     if (cudaMemcpyAsync(Y + (int64_t)b0 * p->out, p->y, 4 * (size_t)B * p->out, cudaMemcpyDeviceToDevice,
                         p->stream) != cudaSuccess) {
       cudaGetLastError();
       return MLS_ECUDA;
     }
   }
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return MLS_ECUDA;
-  }
-  return MLS_OK;
+  if (cudaGetLastError() != cudaSuccess) return MLS_ECUDA;
+  return mlp_check(p);
 }
 
 mls_status mls_mlp_gradients(mls_mlp* p, const float* X, const float* T, int32_t batch, float* grad_out,
                              double* loss_out) {
   if (!p || !X || !T || batch < 1 || batch > p->max_batch) return MLS_EINVAL;
   cudaMemsetAsync(p->loss, 0, 8, p->stream);
-  mlp_forward(p, X, batch);
-  mlp_backward(p, X, T, batch);
+  mlp_forward(p, X, batch, false, true);
+  mlp_backward(p, T, batch);
   if (grad_out) cudaMemcpyAsync(grad_out, p->grad, 4 * (size_t)p->L.total, cudaMemcpyDeviceToDevice, p->stream);
   cudaMemcpyAsync(p->loss_host, p->loss, 8, cudaMemcpyDeviceToHost, p->stream);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess) {
-    cudaGetLastError();
-    return MLS_ECUDA;
-  }
+  if (cudaGetLastError() != cudaSuccess) return MLS_ECUDA;
+  const mls_status st = mlp_check(p);
+  if (st != MLS_OK) return st;
   if (loss_out) *loss_out = *p->loss_host;
   return MLS_OK;
 }
@@ -415,20 +374,20 @@ mls_status mls_mlp_train(mls_mlp* p, const float* X, const float* T, int32_t n_s
     const int64_t nx = (int64_t)batch * p->in, nt = (int64_t)batch * p->out;
     k_gather_rows<<<(int)((nx + 255) / 256), 256, 0, s>>>(batch, p->in, order + b0, X, p->xg);
     k_gather_rows<<<(int)((nt + 255) / 256), 256, 0, s>>>(batch, p->out, order + b0, T, p->tb);
-    mlp_forward(p, p->xg, batch);
-    mlp_backward(p, p->xg, p->tb, batch);
+    mlp_forward(p, p->xg, batch, false, true);
+    mlp_backward(p, p->tb, batch);
     ++p->step;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)p->step), c2 = 1.f - powf(b2, (float)p->step);
-    k_adam<<<(int)((p->L.total + 255) / 256), 256, 0, s>>>(p->L.total, p->w, p->wb, p->grad, p->m, p->v, lr, b1,
-                                                          b2, c1, c2, 1e-8f);
+    k_adam<<<(int)((p->L.total + 255) / 256), 256, 0, s>>>(p->L.total, p->w, p->grad, p->m, p->v, lr, b1, b2, c1,
+                                                          c2, 1e-8f);
+    mlp_refresh_bf16(p);
     ++nsteps;
   }
   cudaMemcpyAsync(p->loss_host, p->loss, 8, cudaMemcpyDeviceToHost, s);
-  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaGetLastError();
-    return MLS_ECUDA;
-  }
+  if (cudaGetLastError() != cudaSuccess) return MLS_ECUDA;
+  const mls_status st = mlp_check(p);
+  if (st != MLS_OK) return st;
   if (loss_out) *loss_out = nsteps ? *p->loss_host / nsteps : 0.0;
   return MLS_OK;
 }
@@ -439,8 +398,9 @@ mls_status mls_mlp_adam_step(mls_mlp* p, const float* grad, float lr) {
   ++p->step;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)p->step), c2 = 1.f - powf(b2, (float)p->step);
-  k_adam<<<(int)((p->L.total + 255) / 256), 256, 0, p->stream>>>(p->L.total, p->w, p->wb, p->grad, p->m, p->v, lr,
-                                                                b1, b2, c1, c2, 1e-8f);
+  k_adam<<<(int)((p->L.total + 255) / 256), 256, 0, p->stream>>>(p->L.total, p->w, p->grad, p->m, p->v, lr, b1, b2,
+                                                                c1, c2, 1e-8f);
+  mlp_refresh_bf16(p);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(p->stream) != cudaSuccess) {
     cudaGetLastError();
     return MLS_ECUDA;

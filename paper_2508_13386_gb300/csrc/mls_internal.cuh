@@ -34,6 +34,17 @@ constexpr int kBlock = 256;
 constexpr int kSlice = 32;
 constexpr int kMaxPartials = 8192;
 constexpr int kGalerkinChunk = 128;
+// Diagonal-shift retries of a coarse factorisation.  The coarse operator
+// only preconditions, so A_c + sigma diag(A_c) serves as well as A_c once
+// sigma exceeds the relative indefiniteness that rounding left in it; the
+// Newton direction PCG converges to does not depend on the shift.  sigma
+// starts at float32 rounding and grows 100x per try.
+// Tensor-core trailing updates of the coarse Cholesky (multilevel.cu):
+// panel width, bf16 slices per float64 value and bits per slice
+constexpr int kOzSlices = 8, kOzBits = 7, kOzPanel = 128;
+constexpr int kShiftTries = 4;
+constexpr double kShiftFirst = 1e-7;
+constexpr double kShiftGrowth = 100.0;
 constexpr int kRestrictChunk = 256;
 constexpr int kMaxPersistBlocks = 4096;
 
@@ -445,6 +456,7 @@ struct Basis {
   int64_t ny = 0;
   int16_t* yslot = nullptr;   // [n_slots * maxk] local index into row v's Y list per (slot, basis entry)
   int maxk = 0;               // max handles per vertex
+  int maxkv = 0;              // max K_v: handles reachable from one row of H
   int* hn_row = nullptr;      // [m+1] coarse block-row neighbours (CSR)
   int* hn = nullptr;          // [nb] neighbour handle
   int nb = 0;
@@ -602,7 +614,14 @@ struct mls_ctx {
   void* gpart = nullptr;           // [nchunk][144] Galerkin chunk partial sums
   void* cvec = nullptr;            // [r] coarse vectors (solve precision)
   void* cvec2 = nullptr;
+  __nv_bfloat16* oz_fwd = nullptr;  // [r][8 x 128] bf16 slices of a Cholesky panel (tensor-core update)
+  __nv_bfloat16* oz_rev = nullptr;  // the same slices in reversed order
+  int* oz_e = nullptr;              // [r] row exponents of the panel
+  int* umma_err = nullptr;          // set by a tensor-core product whose bounded wait gave up
   bool coarse_ready = false;
+  bool coarse_fallback = false;    // this Newton iteration preconditions with block Jacobi (coarse factor failed)
+  int64_t coarse_shift_count = 0;  // diagonal-shift retries of the coarse factorisation so far
+  double coarse_sigma = 0.0;       // relative diagonal shift of the current coarse factor (0: none)
   int coarse_age_steps = 0;       // timesteps begun since the coarse factor was built
   int coarse_ref_iters = 0;       // PCG iterations of a step's first solve after that build
   bool coarse_ref_pending = false; // the next step's first solve sets coarse_ref_iters
@@ -698,6 +717,33 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
 mls_status launch_prolong(mls_ctx* ctx, const void* q, void* w, bool accumulate);
 mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q);
 mls_status build_coarse(mls_ctx* ctx);
+
+// C = epilogue(A B^T) on the tensor cores (umma.cu): A [M][lda], B [N][ldb]
+// bf16 row-major (pitches multiples of 8 elements, 16-byte aligned), C
+// float32 [M][ldc]; *err (device) is set if a bounded wait gave up
+struct GemmEpilogue {
+  const float* bias = nullptr;    // [N]: + bias[n]
+  int relu = 0;                   // then max(., 0)
+  const float* mask = nullptr;    // [M][ldc]: then zero where mask <= 0
+  const float* oscale = nullptr;  // [N]: then x oscale[n] + oshift[n]
+  const float* oshift = nullptr;
+  __nv_bfloat16* out16 = nullptr;   // [M][ld16]: the result rounded to bf16 as well
+  int ld16 = 0;
+  __nv_bfloat16* out16t = nullptr;  // [N][ld16t]: its transpose rounded to bf16
+  int ld16t = 0;
+  // float64 accumulation instead of the float32 store (the slice products of
+  // the emulated float64 product): acc64[m][n] += sign x 2^(ea[m] + eb[n] -
+  // ebias) x result, exact scaling and one float64 addition
+  double* acc64 = nullptr;
+  int ld64 = 0;
+  const int* ea = nullptr;
+  const int* eb = nullptr;
+  int ebias = 0;
+  double sign = 1.0;
+  int lower = 0;                    // only tiles that meet the lower triangle n <= m
+};
+mls_status gemm_bf16_tn(cudaStream_t stream, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                        const __nv_bfloat16* B, int ldb, float* C, int ldc, const GemmEpilogue& ep, int* err);
 mls_status build_galerkin(mls_ctx* ctx);   // U^T H U into the dense Ac only (no factorisation)
 mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out);
 mls_status warm_start_begin(mls_ctx* ctx, int* used);

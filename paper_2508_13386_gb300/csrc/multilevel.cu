@@ -106,6 +106,7 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
     }
     h_yrow[v + 1] = h_yrow[v] + (int)Kv.size();
     h_yh.insert(h_yh.end(), Kv.begin(), Kv.end());
+    B.maxkv = std::max(B.maxkv, (int)Kv.size());
   }
   const int64_t ny = h_yrow[n];
   // coarse block-row neighbours N_i = union of K_v over v in supp(i), and the
@@ -242,8 +243,9 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   B.h_origins.assign(origins, origins + 3 * (size_t)m);
   const int r = 12 * m;
   const int vb = solve_bytes(ctx);
-  if ((st = dalloc(ctx, &ctx->yval, (size_t)ny * 36 * vb)) != MLS_OK) return st;
-  if ((st = dalloc(ctx, &ctx->gpart, (size_t)std::max(nchunk, 1) * 144 * vb)) != MLS_OK) return st;
+  // Y = H U and the Galerkin chunk partials are float64 in every precision
+  if ((st = dalloc(ctx, &ctx->yval, (size_t)ny * 36 * sizeof(double))) != MLS_OK) return st;
+  if ((st = dalloc(ctx, &ctx->gpart, (size_t)std::max(nchunk, 1) * 144 * sizeof(double))) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->Ac, (size_t)r * r * sizeof(double))) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->Acopy, (size_t)r * r * sizeof(double))) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->Linv, (size_t)r * r * vb)) != MLS_OK) return st;
@@ -252,6 +254,13 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   if ((st = dalloc(ctx, &ctx->cvec, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, &ctx->cvec2, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->chol_info, sizeof(int) * 4)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->oz_fwd, sizeof(__nv_bfloat16) * (size_t)r * kOzSlices * kOzPanel)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->oz_rev, sizeof(__nv_bfloat16) * (size_t)r * kOzSlices * kOzPanel)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&ctx->oz_e, sizeof(int) * (size_t)r)) != MLS_OK) return st;
+  if (!ctx->umma_err) {
+    if ((st = dalloc(ctx, (void**)&ctx->umma_err, sizeof(int))) != MLS_OK) return st;
+    if ((st = cuda_check(ctx, cudaMemset(ctx->umma_err, 0, sizeof(int)), "flag")) != MLS_OK) return st;
+  }
   if ((st = dalloc(ctx, (void**)&ctx->chol_tinv, sizeof(double) * 32 * 32 * (size_t)((r + 31) / 32))) != MLS_OK)
     return st;
   ctx->has_basis = true;
@@ -536,6 +545,55 @@ __global__ void __launch_bounds__(kBlock) k_galerkin_y(BasisView B, GalerkinView
   for (int k = 0; k < 36; ++k) Y[idx * 36 + k] = acc[k];
 }
 
+// The same Y = H U in float64, one warp per vertex row v: the warp walks the
+// row's blocks H_vw in slot order; for each block, lanes 0..26 take one of
+// the nine values H_vw[c][d] for one of three basis entries (j, phi_j(w)) of
+// w at a time and add H_vw[c][d] phi_j(w) a_l(w) (l = 0..3) to the row's
+// accumulator for handle j, which lives in shared memory (K_v x 36 doubles
+// per warp).  The entries of one block belong to different handles, so no
+// two lanes update the same word, and the blocks are added in slot order:
+// the sums are deterministic.  Every lane of the warp does the same loop
+// trip count, so the float64 work is not serialised by divergence.
+constexpr int kGalYWarps = 4;
+template <typename MT>
+__global__ void __launch_bounds__(32 * kGalYWarps) k_galerkin_y64(BasisView B, GalerkinView G,
+                                                                 const MT* __restrict__ val, int maxkv,
+                                                                 double* __restrict__ Y) {
+  extern __shared__ double s_yacc[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int v = blockIdx.x * kGalYWarps + warp;
+  if (v >= G.n) return;
+  double* acc = s_yacc + (size_t)warp * maxkv * 36;
+  const int y0 = G.yrow[v], kv = G.yrow[v + 1] - y0;
+  for (int t = lane; t < kv * 36; t += 32) acc[t] = 0.0;
+  __syncwarp();
+  const int cd = lane % 9, eo = lane / 9;  // eo = 3: lanes 27..31 only help with the final copy
+  const int slice = v >> 5, sl = v & 31;
+  const int g0 = G.slice_ptr[slice];
+  const int len = G.row_len[v];
+  for (int k = 0; k < len; ++k) {
+    const int64_t slot = ((int64_t)g0 + k) * 32 + sl;
+    const int w = G.col[slot];
+    const int kb = B.vrow[w], ke = B.vrow[w + 1];
+    if (eo < 3) {
+      const double h = load_as<double>(val[((int64_t)g0 + k) * 288 + cd * 32 + sl]);
+      const Vec4d Xw = B.X[w];
+      for (int e = kb + eo; e < ke; e += 3) {
+        const int q = G.yslot[slot * G.maxk + (e - kb)];
+        const int j = B.vh[e];
+        const double ph = B.vphi[e];
+        double* a = acc + q * 36 + cd * 4;
+        a[0] += h * ph;
+        a[1] += h * (ph * (Xw.x - B.origins[3 * j]));
+        a[2] += h * (ph * (Xw.y - B.origins[3 * j + 1]));
+        a[3] += h * (ph * (Xw.z - B.origins[3 * j + 2]));
+      }
+    }
+    __syncwarp();
+  }
+  for (int t = lane; t < kv * 36; t += 32) Y[(int64_t)y0 * 36 + t] = acc[t];
+}
+
 // A_ij (12x12) = sum over entries (v, y) of phi_i(v) a_vi (x) Y_y.  Pass 1:
 // one 144-thread team per chunk of at most kGalerkinChunk entries of one
 // coarse block (two teams per CTA), each thread owning one of the 144
@@ -730,6 +788,79 @@ __global__ void k_syrk_tiles(double* __restrict__ A, int r, int k, int ntiles) {
     const int rr = ty + 8 * u;
     if (rr < ni && tx < nj) A[(int64_t)(bi + rr) * r + bj + tx] -= acc[u];
   }
+}
+
+// ---- float64 trailing updates on the tensor cores ------------------------------------
+// The rank-128 update A22 -= L21 L21^T of the blocked Cholesky is computed
+// as an error-free sum of bf16 products (the splitting scheme of Ozaki,
+// Ogita, Oishi and Rump, 2012): each row i of L21 is scaled by 2^-e_i (e_i
+// the exponent of its largest entry, so the row lies in (-1, 1)) and cut
+// into kOzSlices slices of kOzBits bits, a_p = trunc(2^beta r_{p-1}),
+// r_p = 2^beta r_{p-1} - a_p (exact in float64).  Every slice entry is an
+// integer of magnitude < 2^7, exact in bf16, and a product of two slices
+// summed over at most 1024 terms stays below 2^24, exact in the float32
+// accumulator.  So S_d = sum_{p+q=d} a_p a_q^T, one tensor-core product per
+// d with the slices concatenated along K, is exact, and
+//   (L21 L21^T)_ij = 2^(e_i + e_j) sum_d 2^(-beta d) S_d,ij
+// up to the dropped terms p + q > kOzSlices + 1, below 2^-56 relative to the
+// row scales.  Each S_d is scaled exactly by a power of two and subtracted
+// from A22 in float64.
+// slices of the rows of an FP64 block [rows][K] (pitch lda): forward order
+// (slice p at columns p K of fwd) and reversed (slice p at (S - 1 - p) K of
+// rev), row pitch opitch; the row exponents to e
+__global__ void k_ozaki_split(int rows, int K, const double* __restrict__ A, int lda, int opitch,
+                              __nv_bfloat16* __restrict__ fwd, __nv_bfloat16* __restrict__ rev, int* __restrict__ e) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (i >= rows) return;
+  const double* a = A + (int64_t)i * lda;
+  double mx = 0.0;
+  for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(a[k]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1): every |a_k| < 2^ex
+  if (lane == 0) e[i] = ex;
+  __nv_bfloat16* f = fwd + (int64_t)i * opitch;
+  __nv_bfloat16* b = rev + (int64_t)i * opitch;
+  for (int k = lane; k < K; k += 32) {
+    double r = ldexp(a[k], -ex);
+#pragma unroll
+    for (int p = 0; p < kOzSlices; ++p) {
+      r = ldexp(r, kOzBits);
+      const double t = trunc(r);
+      r -= t;
+      const __nv_bfloat16 v = __double2bfloat16(t);
+      f[p * K + k] = v;
+      b[(kOzSlices - 1 - p) * K + k] = v;
+    }
+  }
+}
+
+// A[r1:, r1:] -= L21 L21^T (lower triangle), L21 = A[r1:, c0:c0+w], w <= 128
+static mls_status ozaki_trailing_update(mls_ctx* ctx, double* A, int r, int c0, int w, int r1) {
+  const int n = r - r1;
+  if (n <= 0) return MLS_OK;
+  const int opitch = kOzSlices * kOzPanel;
+  { ++ctx->launches; k_ozaki_split<<<(n + 7) / 8, 256, 0, ctx->stream>>>(n, w, A + (int64_t)r1 * r + c0, r, opitch,
+                                                                        ctx->oz_fwd, ctx->oz_rev, ctx->oz_e); }
+  mls_status st = cuda_check(ctx, cudaGetLastError(), "k_ozaki_split");
+  if (st != MLS_OK) return st;
+  for (int d = kOzSlices + 1; d >= 2; --d) {  // least significant first
+    GemmEpilogue ep;
+    ep.acc64 = A + (int64_t)r1 * r + r1;
+    ep.ld64 = r;
+    ep.ea = ctx->oz_e;
+    ep.eb = ctx->oz_e;
+    ep.ebias = kOzBits * d;
+    ep.sign = -1.0;
+    ep.lower = 1;
+    ++ctx->launches;
+    st = gemm_bf16_tn(ctx->stream, n, n, (d - 1) * w, ctx->oz_fwd, opitch, ctx->oz_rev + (kOzSlices - d + 1) * w,
+                      opitch, nullptr, 0, ep, ctx->umma_err);
+    if (st != MLS_OK) return fail(ctx, st, "tensor-core trailing update");
+  }
+  return MLS_OK;
 }
 
 // W = L^{-1} by a right-looking blocked solve of L W = I over tile rows:
@@ -947,6 +1078,11 @@ mls_status launch_restrict(mls_ctx* ctx, const void* r, void* q) {
   return cuda_check(ctx, cudaGetLastError(), "k_restrict");
 }
 
+// A_c = U^T H U accumulated in float64 from H's stored values (float64,
+// float32 or bfloat16): the coarse operator's smallest eigenvalues are
+// differences of large terms (near-rigid motions of stiff regions, whose
+// elastic parts cancel down to the mass), and float32 sums of those terms
+// can leave U^T H U indefinite when the stiffness contrast is large.
 template <typename VT, typename MT>
 static mls_status galerkin_t(mls_ctx* ctx) {
   Basis& B = ctx->basis;
@@ -959,8 +1095,20 @@ static mls_status galerkin_t(mls_ctx* ctx) {
   }
   // with a cubature the coarse operator is built from the cubature H (Sec. 3.8)
   const MT* hv = (const MT*)(ctx->cub_scale ? ctx->hval_cub : ctx->hval);
-  { ++ctx->launches; k_galerkin_y<VT, MT><<<nblk(B.ny), kBlock, 0, ctx->stream>>>(basis_view(ctx), G, hv,
-                                                               B.ypair_row, B.ny, (VT*)ctx->yval); }
+  // the warp-per-row kernel while its accumulators fit in shared memory
+  const size_t ysmem = (size_t)kGalYWarps * std::max(B.maxkv, 1) * 36 * sizeof(double);
+  if (std::is_same<VT, double>::value && ysmem <= 200 * 1024) {
+    if (ysmem > 48 * 1024) {
+      mls_status st0 = cuda_check(ctx, cudaFuncSetAttribute(k_galerkin_y64<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                            (int)ysmem), "galerkin smem");
+      if (st0 != MLS_OK) return st0;
+    }
+    { ++ctx->launches; k_galerkin_y64<MT><<<(ctx->n + kGalYWarps - 1) / kGalYWarps, 32 * kGalYWarps, ysmem, ctx->stream>>>(
+        basis_view(ctx), G, hv, std::max(B.maxkv, 1), (double*)ctx->yval); }
+  } else {
+    { ++ctx->launches; k_galerkin_y<VT, MT><<<nblk(B.ny), kBlock, 0, ctx->stream>>>(basis_view(ctx), G, hv,
+                                                                 B.ypair_row, B.ny, (VT*)ctx->yval); }
+  }
   mls_status st = cuda_check(ctx, cudaMemsetAsync(ctx->Ac, 0, sizeof(double) * r * r, ctx->stream), "Ac clear");
   if (st != MLS_OK) return st;
   if (B.nchunk > 0) {
@@ -987,12 +1135,26 @@ static mls_status factor_dense_t(mls_ctx* ctx, double* A, int r, double* Acopy, 
   }
   st = cuda_check(ctx, cudaMemsetAsync(ctx->chol_info, 0, sizeof(int), ctx->stream), "info clear");
   if (st != MLS_OK) return st;
+  // Above kOzMinTiles tiles the factorisation goes by 128-wide panels: the
+  // tile steps inside a panel update only the panel's own columns, and the
+  // rest of the trailing matrix takes the panel's rank-128 update on the
+  // tensor cores at the panel's end (the same sum of updates, delayed).
+  constexpr int kOzMinTiles = 8;
+  const int tpp = kOzPanel / NB;  // tiles per panel
+  const bool oz = nt > kOzMinTiles && ctx->oz_fwd;
   for (int k = 0; k < nt; ++k) {
     { ++ctx->launches; k_potrf_tile<<<1, dim3(NB, NB), 0, ctx->stream>>>(A, r, k, ctx->chol_info, ctx->chol_tinv); }
     if (k + 1 < nt) {
       { ++ctx->launches; k_trsm_tiles<<<nt - k - 1, dim3(NB, NB), 0, ctx->stream>>>(A, r, k, ctx->chol_tinv); }
-      const int m = nt - k - 1;
-      { ++ctx->launches; k_syrk_tiles<<<m * (m + 1) / 2, dim3(32, 8), 0, ctx->stream>>>(A, r, k, nt); }
+      // tile pairs (i, j), k < j < jmax, j <= i < nt
+      const int jmax = oz ? std::min(nt, (k / tpp + 1) * tpp) : nt;
+      int pairs = 0;
+      for (int j = k + 1; j < jmax; ++j) pairs += nt - j;
+      if (pairs > 0) { ++ctx->launches; k_syrk_tiles<<<pairs, dim3(32, 8), 0, ctx->stream>>>(A, r, k, nt); }
+      if (oz && k + 1 == jmax && jmax < nt) {
+        const int c0 = (jmax - tpp) * NB;
+        if ((st = ozaki_trailing_update(ctx, A, r, c0, kOzPanel, jmax * NB)) != MLS_OK) return st;
+      }
     }
   }
   st = cuda_check(ctx, cudaGetLastError(), "cholesky");
@@ -1016,6 +1178,15 @@ static mls_status factor_dense_t(mls_ctx* ctx, double* A, int r, double* Acopy, 
   st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "cholesky sync");
   if (st != MLS_OK) return st;
   memcpy(&info, &ctx->dscal_host[12], sizeof(int));
+  if (oz) {
+    int uerr = 0;
+    st = cuda_check(ctx, cudaMemcpy(&uerr, ctx->umma_err, sizeof(int), cudaMemcpyDeviceToHost), "umma flag");
+    if (st != MLS_OK) return st;
+    if (uerr) {
+      cudaMemset(ctx->umma_err, 0, sizeof(int));
+      return fail(ctx, MLS_ETIMEOUT, "tensor-core trailing update: a bounded wait gave up");
+    }
+  }
   if (info != 0) return fail(ctx, MLS_ECHOL, "matrix is not positive definite (pivot " + std::to_string(info - 1) + ")");
   return MLS_OK;
 }
@@ -1025,10 +1196,30 @@ mls_status factor_dense(mls_ctx* ctx, double* A, int r, double* Acopy, void* W, 
                                         : factor_dense_t<float>(ctx, A, r, Acopy, W, WT);
 }
 
+// A = A0 + sigma diag(A0) from the saved operator A0 (row-major r x r)
+__global__ void k_shift_restore(double* __restrict__ A, const double* __restrict__ A0, int r, double sigma) {
+  const int64_t nn = (int64_t)r * r;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = A0[i];
+    A[i] = (i / r == i % r) ? a + sigma * fmax(a, 0.0) : a;
+  }
+}
+
 template <typename VT>
 static mls_status factor_t(mls_ctx* ctx) {
   const int r = 12 * ctx->basis.m;
   mls_status st = factor_dense_t<VT>(ctx, ctx->Ac, r, ctx->Acopy, ctx->Linv, ctx->LinvT);
+  ctx->coarse_sigma = 0.0;
+  double sigma = kShiftFirst;
+  for (int k = 0; st == MLS_ECHOL && k < kShiftTries; ++k, sigma *= kShiftGrowth) {
+    const int nb = (int)std::min<int64_t>(((int64_t)r * r + kBlock - 1) / kBlock, 4096);
+    { ++ctx->launches; k_shift_restore<<<nb, kBlock, 0, ctx->stream>>>(ctx->Ac, ctx->Acopy, r, sigma); }
+    if ((st = cuda_check(ctx, cudaGetLastError(), "k_shift_restore")) != MLS_OK) return st;
+    ctx->coarse_shift_count++;
+    ctx->coarse_sigma = sigma;
+    // Acopy keeps the unshifted operator
+    st = factor_dense_t<VT>(ctx, ctx->Ac, r, nullptr, ctx->Linv, ctx->LinvT);
+  }
   if (st == MLS_OK) {
     const int T = (r + kGramTile - 1) / kGramTile;
     { ++ctx->launches; k_gram_lower<VT><<<T * (T + 1) / 2, 256, 0, ctx->stream>>>((const VT*)ctx->Linv, r, (VT*)ctx->Ainv); }
@@ -1059,8 +1250,8 @@ mls_status build_galerkin(mls_ctx* ctx) {
   if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
   switch (ctx->opt.precision) {
     case MLS_FP64: return galerkin_t<double, double>(ctx);
-    case MLS_MIXED_FP32: return galerkin_t<float, float>(ctx);
-    default: return galerkin_t<float, __nv_bfloat16>(ctx);
+    case MLS_MIXED_FP32: return galerkin_t<double, float>(ctx);
+    default: return galerkin_t<double, __nv_bfloat16>(ctx);
   }
 }
 
@@ -1229,11 +1420,7 @@ mls_status build_coarse(mls_ctx* ctx) {
   if ((st = choose_omega(ctx)) != MLS_OK) return st;
   int tk = prof_begin(ctx, MLS_PROF_GALERKIN);
   if (ctx->cub_scale && (st = launch_assemble_cubature(ctx, ctx->xk)) != MLS_OK) return st;
-  switch (ctx->opt.precision) {
-    case MLS_FP64: st = galerkin_t<double, double>(ctx); break;
-    case MLS_MIXED_FP32: st = galerkin_t<float, float>(ctx); break;
-    default: st = galerkin_t<float, __nv_bfloat16>(ctx); break;
-  }
+  st = build_galerkin(ctx);
   if (st != MLS_OK) return st;
   prof_end(ctx, tk);
   tk = prof_begin(ctx, MLS_PROF_CHOLESKY);

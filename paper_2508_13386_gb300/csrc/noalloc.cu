@@ -19,7 +19,10 @@
 //    wrong results; serialise them;
 //  * the first call on a device looks up the scratch's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
+//    before any stream capture.  The address belongs to the device's
+//    primary context and is cached for the life of the process, so a
+//    caller that resets the device (cudaDeviceReset) must not call this
+//    entry point on it afterwards.
 #include "mls_internal.cuh"
 
 #include <mutex>

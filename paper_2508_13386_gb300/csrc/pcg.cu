@@ -89,11 +89,11 @@ __device__ __forceinline__ void spmv_quad(const SellView& A, const MT* __restric
   y[0] = y0; y[1] = y1; y[2] = y2;
 }
 
-// The same product split in two for chained launches: quad_load() reads the
+// The same product split for chained launches: quad_load() reads the
 // column indices and values of a lane's first slots (H does not change
 // during a solve, so this may run before chain_wait(), while the previous
-// kernel finishes); quad_finish() gathers x after the wait, adds the
-// remaining slots, and combines the four lanes of a row.
+// kernel finishes); after the wait quad_gather() and quad_combine() below
+// finish the rows.
 template <typename VT>
 struct QuadH {
   static constexpr int PF = sizeof(VT) == 4 ? 4 : 2;   // slots per lane loaded ahead (register budget)
@@ -121,14 +121,29 @@ __device__ __forceinline__ void quad_load(const SellView& A, const MT* __restric
   }
 }
 
+// The rest of the product in two halves, so that a kernel can put other
+// loads in flight between them: quad_gather() issues the x gathers of the
+// slots that quad_load() holds; quad_combine() multiplies, adds the remaining
+// slots (rows longer than 4 PF) and combines the four lanes of a row.
+template <typename VT>
+struct QuadX {
+  Vec4<VT> x[QuadH<VT>::PF];
+};
+
+template <typename VT>
+__device__ __forceinline__ void quad_gather(const QuadH<VT>& h, const Vec4<VT>* __restrict__ x, QuadX<VT>& g) {
+#pragma unroll
+  for (int u = 0; u < QuadH<VT>::PF; ++u)
+    g.x[u] = h.c[u] >= 0 ? x[h.c[u]] : Vec4<VT>{VT(0), VT(0), VT(0), VT(0)};
+}
+
 template <typename VT, typename MT>
-__device__ __forceinline__ void quad_finish(const SellView& A, const MT* __restrict__ val, const QuadH<VT>& h,
-                                            const Vec4<VT>* __restrict__ x, VT (&y)[3]) {
+__device__ __forceinline__ void quad_combine(const SellView& A, const MT* __restrict__ val, const QuadH<VT>& h,
+                                             const QuadX<VT>& g, const Vec4<VT>* __restrict__ x, VT (&y)[3]) {
   VT y0 = VT(0), y1 = VT(0), y2 = VT(0);
 #pragma unroll
   for (int u = 0; u < QuadH<VT>::PF; ++u) {
-    if (h.c[u] < 0) continue;
-    const Vec4<VT> xv = x[h.c[u]];
+    const Vec4<VT>& xv = g.x[u];   // zero for the empty slots, whose weights are zero too
     y0 += h.w[u][0] * xv.x + h.w[u][1] * xv.y + h.w[u][2] * xv.z;
     y1 += h.w[u][3] * xv.x + h.w[u][4] * xv.y + h.w[u][5] * xv.z;
     y2 += h.w[u][6] * xv.x + h.w[u][7] * xv.y + h.w[u][8] * xv.z;
@@ -186,12 +201,17 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_residual(SellView A, con
   quad_load<VT, MT>(A, val, blockIdx.x, hq);
   chain_wait();
   chain_release();
-  if (S && S->done) return;
-  VT r[3];
-  quad_finish<VT, MT>(A, val, hq, x, r);
+  // the gathers, b and the stop flag are loaded together; no barrier
+  // follows, so each thread may act on its own read of the flag
+  QuadX<VT> gx;
+  quad_gather<VT>(hq, x, gx);
   const int row = quad_row(blockIdx.x, A.n);
-  if (row < 0) return;
-  const Vec4<VT> bb = b[row];
+  Vec4<VT> bb{};
+  if (row >= 0) bb = b[row];
+  const int done = S ? S->done : 0;
+  VT r[3];
+  quad_combine<VT, MT>(A, val, hq, gx, x, r);
+  if (row < 0 || done) return;
   out[row] = Vec4<VT>{bb.x - r[0], bb.y - r[1], bb.z - r[2], VT(0)};
 }
 
@@ -262,13 +282,22 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_post_smooth_rz(SellView 
   quad_load<VT, MT>(A, val, blockIdx.x, hq);
   chain_wait();
   chain_release();
-  if (S->done) return;
+  // gathers, this row's r and z2 and the block's stop flag in flight together
+  QuadX<VT> gx;
+  quad_gather<VT>(hq, z2, gx);
+  const int row = quad_row(blockIdx.x, A.n);
+  Vec4<VT> rv{};
+  if (row >= 0) rv = r[row];
+  // a row's first slot is its diagonal block: the row's own z2 is gathered
+  const Vec4<VT> zv = gx.x[0];
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_done = S->done;
+  __syncthreads();
+  if (s_done) return;
   double acc[1] = {0.0};
   VT hz[3];
-  quad_finish<VT, MT>(A, val, hq, z2, hz);
-  const int row = quad_row(blockIdx.x, A.n);
+  quad_combine<VT, MT>(A, val, hq, gx, z2, hz);
   if (row >= 0) {
-    const Vec4<VT> rv = r[row], zv = z2[row];
     const Vec4<VT> t{rv.x - hz[0], rv.y - hz[1], rv.z - hz[2], VT(0)};
     const Vec4<VT> s = dinv_apply<VT>(dinv, row, t, omega);
     const Vec4<VT> zo{zv.x + s.x, zv.y + s.y, zv.z + s.z, VT(0)};
@@ -304,33 +333,38 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_pcg_spmv(SellView A, con
   quad_load<VT, MT>(A, val, blockIdx.x, hq);
   chain_wait();
   chain_release();
-  // block 0 of this kernel may set S->done while other blocks start: one
-  // thread reads it for the whole block, so the block stays uniform
+  // The x gathers and (thread 0) the stop flag and the sums that open the
+  // iteration are loaded together, before the block's barrier.  Block 0 of
+  // this kernel may set S->done while other blocks start: one thread reads it
+  // and takes the decision for the whole block, so the block stays uniform.
+  QuadX<VT> gx;
+  quad_gather<VT>(hq, z, gx);
+  const int row = quad_row(blockIdx.x, A.n);
   __shared__ VT s_beta;
   __shared__ int s_done, s_e;
-  PcgHeadRaw raw;
   if (threadIdx.x == 0) {
-    s_done = S->done;
-    raw = pcg_head_load(fix, it);
+    const int done0 = S->done;
+    const PcgHeadRaw raw = pcg_head_load(fix, it);
+    int done = done0;
+    if (!done0) {
+      const PcgHead<VT> h = pcg_head<VT>(S, raw, it);
+      if (blockIdx.x == 0) pcg_head_publish<VT>(S, fix, it, h);
+      s_beta = h.beta;
+      s_e = fix_exponent(h.rz);
+      done = h.done;
+    }
+    s_done = done;
   }
   __syncthreads();
   if (s_done) return;
+  // a row's first slot is its diagonal block: the row's own z is gathered
+  const Vec4<VT> zv = gx.x[0];
   VT w[3];
-  quad_finish<VT, MT>(A, val, hq, z, w);
-  if (threadIdx.x == 0) {
-    const PcgHead<VT> h = pcg_head<VT>(S, raw, it);
-    if (blockIdx.x == 0) pcg_head_publish<VT>(S, fix, it, h);
-    s_beta = h.beta;
-    s_done = h.done;
-    s_e = fix_exponent(h.rz);
-  }
-  __syncthreads();
-  if (s_done) return;
+  quad_combine<VT, MT>(A, val, hq, gx, z, w);
   double acc[1] = {0.0};
-  const int row = quad_row(blockIdx.x, A.n);
   if (row >= 0) {
     const VT beta = s_beta;
-    const Vec4<VT> zv = z[row], pv = p[row], qv = q[row];
+    const Vec4<VT> pv = p[row], qv = q[row];
     const Vec4<VT> pn{zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, VT(0)};
     const Vec4<VT> qn{w[0] + beta * qv.x, w[1] + beta * qv.y, w[2] + beta * qv.z, VT(0)};
     p[row] = pn;
@@ -495,7 +529,7 @@ static mls_status pcg_t(mls_ctx* ctx, double rtol, int max_iter, int* iters, dou
   const int nb_upd = (n + kUpdBlock - 1) / kUpdBlock;
   if (nb_upd > kMaxPartials || ctx->n_slices > kMaxPartials)
     return fail(ctx, MLS_EINVAL, "mesh too large for one reduction grid");
-  const bool jacobi = ctx->opt.preconditioner == MLS_PRECOND_BLOCK_JACOBI;
+  const bool jacobi = ctx->opt.preconditioner == MLS_PRECOND_BLOCK_JACOBI || ctx->coarse_fallback;
   if (!jacobi && !ctx->coarse_ready) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_build_coarse");
   auto* b = (const Vec4<VT>*)ctx->vb;
   auto* x = (Vec4<VT>*)ctx->vx;

@@ -39,6 +39,31 @@ def random_loads(scene, rng):
     return g, v0
 
 
+def drop_loads(scene, rng):
+    """Gravity and initial velocity of one trajectory of a free body dropped
+    onto the ground plane (seeded inputs): gravity within 30 degrees of -z,
+    magnitude 9.81 x U[0.5, 1.5]; a rigid initial velocity, downward speed
+    U[0.5, 1.5] m/s, lateral N(0, 0.3) m/s, and a spin N(0, 2) rad/s about
+    each axis through the centroid."""
+    theta = np.deg2rad(30.0) * np.sqrt(rng.random())
+    phi = 2 * np.pi * rng.random()
+    mag = 9.81 * rng.uniform(0.5, 1.5)
+    g = mag * np.array([np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi), -np.cos(theta)])
+    lin = np.array([rng.normal(scale=0.3), rng.normal(scale=0.3), -rng.uniform(0.5, 1.5)])
+    omega = rng.normal(scale=2.0, size=3)
+    c = scene.X.mean(axis=0)
+    v0 = lin[None, :] + np.cross(omega[None, :], scene.X - c[None, :])
+    return g, v0
+
+
+def scene_loads(scene, rng):
+    """The load generator of the scene's kind: clamped bodies (Dirichlet
+    vertices) take random_loads, free bodies over a ground plane drop_loads."""
+    if np.any(np.asarray(scene.dirichlet)) or not scene.contact:
+        return random_loads(scene, rng)
+    return drop_loads(scene, rng)
+
+
 def collect(solver, scene, n_traj, n_steps, seed, device):
     """Run trajectories and return (features [N, 3r], targets [N, r]) as
     float32 CUDA tensors plus per-step solver statistics."""
@@ -50,7 +75,7 @@ def collect(solver, scene, n_traj, n_steps, seed, device):
     stats = []
     k = 0
     for tr in range(n_traj):
-        g, v0 = random_loads(scene, rng)
+        g, v0 = scene_loads(scene, rng)
         solver.set_forces(tuple(g), scene.contact, scene.plane_n, scene.plane_o, scene.dhat, scene.kappa)
         solver.warm_start_reset()
         x = torch.as_tensor(scene.x0, device=device).contiguous()
@@ -94,7 +119,7 @@ def evaluate(solver_plain, solver_ws, scene, n_steps, seed, device, recorder=Non
     measured."""
     import torch
     rng = np.random.default_rng(seed)
-    g, v0 = random_loads(scene, rng)
+    g, v0 = scene_loads(scene, rng)
     solvers = (solver_plain, solver_ws) + ((recorder,) if recorder is not None else ())
     for s in solvers:
         s.set_forces(tuple(g), scene.contact, scene.plane_n, scene.plane_o, scene.dhat, scene.kappa)

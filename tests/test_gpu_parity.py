@@ -379,8 +379,9 @@ def test_two_level_apply_matches_oracle(cycle):
 def test_two_level_apply_many_coarse_tiles(precision, tol):
     """A 516 x 516 coarse operator (16 full 32 x 32 tiles of the blocked
     Cholesky and a ragged 4-row one; condition number ~2e4 from E in
-    [1e5, 1e9]): the preconditioner apply through the factor and its inverse
-    matches the oracle's dense solve."""
+    [1e5, 1e9]; four 128-wide panels, whose trailing updates run on the
+    tensor cores in sliced bf16 products): the preconditioner apply through
+    the factor and its inverse matches the oracle's dense solve."""
     s = synth.tiny_scene(12, 8, 6, seed=18, E_range=(1e5, 1e9), pinned=False)
     p = ip.Problem(s)
     origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=43, k=4, seed=6)
@@ -395,6 +396,30 @@ def test_two_level_apply_many_coarse_tiles(precision, tol):
     z_o = subspace.two_level_apply(H, U, subspace.galerkin(H, U), r.ravel(), mode="multiplicative",
                                    omega=0.5).reshape(-1, 3)
     assert np.max(np.abs(z - z_o)) <= tol * np.abs(z_o).max()
+
+
+def test_tensor_core_coarse_factor_float64_accuracy():
+    """A 1,320 x 1,320 coarse operator (110 handles; 42 tiles of 32, ten
+    128-wide panels whose rank-128 trailing updates are exact sums of bf16
+    slice products on the tensor cores, E in [1e5, 1e9]): the FP64 two-level
+    apply, which solves with the factor and its inverse, matches the
+    oracle's dense solve to 1e-9, as a float64 factorisation must."""
+    s = synth.tiny_scene(16, 12, 8, seed=23, E_range=(1e5, 1e9), pinned=False)
+    p = ip.Problem(s)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=110, k=4, seed=9)
+    U = subspace.lbs_basis_matrix(s.X, origins, vrow, handle, phi)
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", cycle="multiplicative", omega=0.5)
+    solver.upload_basis(origins, vrow, handle, phi)
+    solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
+    solver.build_coarse()
+    assert solver.coarse_shift() == 0.0
+    H = p.hessian(p.x_tilde)
+    Ac = subspace.galerkin(H, U)
+    for seed in range(2):
+        r = np.random.default_rng(100 + seed).normal(size=s.X.shape)
+        z = host(solver.precond_apply(dev(r)))
+        z_o = subspace.two_level_apply(H, U, Ac, r.ravel(), mode="multiplicative", omega=0.5).reshape(-1, 3)
+        assert np.max(np.abs(z - z_o)) <= 1e-9 * np.abs(z_o).max()
 
 
 def test_singular_coarse_operator_reported():
@@ -412,6 +437,25 @@ def test_singular_coarse_operator_reported():
     with pytest.raises(mls.MLSError) as e:
         solver.build_coarse()
     assert e.value.status == -6
+
+
+def test_indefinite_coarse_operator_falls_back_to_block_jacobi():
+    """A timestep whose coarse operator stays singular after every
+    diagonal-shift retry (a handle with no vertices: 12 zero rows, which a
+    relative diagonal shift cannot lift) preconditions each Newton iteration
+    with block Jacobi instead of failing; the stats count the four shifted
+    retries and the fallback of every iteration, and the step still matches
+    the oracle's minimiser."""
+    s = synth.tiny_scene(6, 4, 3, seed=19)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=7, k=3, seed=7)
+    origins = np.vstack([origins, s.X.mean(axis=0)])  # handle 7: no vertices
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", newton_tol=1e-10)
+    solver.upload_basis(origins, vrow, handle, phi)
+    dx, st = solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    x_o, _ = newton.timestep(ip.Problem(s))
+    assert rel_disp_error(s.x0 + host(dx), x_o, s.x0) <= 1e-9
+    assert st["coarse_fallbacks"] >= 1 and st["coarse_builds"] == 0
+    assert st["coarse_shifts"] == 4 * st["coarse_fallbacks"]
 
 
 def test_lagged_coarse_factor_keeps_the_timestep():

@@ -4,8 +4,8 @@ It exists for callers that cannot allocate device memory while they run; its
 reduction scratch is a file-scope device array.  This file is collected last
 so that a failure here comes after every other test has run.  It checks the
 entry point against the per-tet energies of mls_eval_elements (summed on the
-host) on two calls in a row, so that scratch left by the first call cannot
-leak into the second.
+host) and against the oracle's Neo-Hookean energy sum, on two calls in a row,
+so that scratch left by the first call cannot leak into the second.
 """
 import ctypes as C
 
@@ -37,6 +37,7 @@ def test_noalloc_energy_matches_existing_entry_point():
     out_e = torch.zeros(1, dtype=torch.float64, device=dev)
     out_b = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    vol, Dm_inv = elastic.rest_shape(s.X, s.tets)
     for call in range(2):
         x = s.X + 0.01 * (call + 1) * rng.normal(size=s.X.shape) * 0.1
         xt = torch.as_tensor(x, device=dev).contiguous()
@@ -50,6 +51,8 @@ def test_noalloc_energy_matches_existing_entry_point():
         torch.cuda.synchronize()
         assert int(out_b.item()) == 0
         assert float(out_e.item()) == pytest.approx(ref, rel=1e-10)
+        E_orc = float(elastic.element_energy(x, s.tets, vol, Dm_inv, mu, lam).sum())
+        assert float(out_e.item()) == pytest.approx(E_orc, rel=1e-10)
 
 
 def test_noalloc_rejects_oversized_and_null():
