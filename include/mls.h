@@ -119,10 +119,28 @@ typedef struct mls_options {
                           iterations on H d_f = -g - H d_s from d_f = 0;
                           Newton stops after the update when the mean vertex
                           speed of the subspace step, sum_v |d_s,v|_2 /
-                          (h n_vertices), is below paper_tol (m/s, Sec. 3.9) */
-  int refine_iters;    /* direction 1: fixed full-space CG iterations (20-40) */
-  double paper_tol;    /* direction 1: subspace-decrement tolerance (1e-3) */
+                          (h n_vertices), is below paper_tol (m/s, Sec. 3.9).
+                          2: as 1, with the subspace direction of Alg. 2 as
+                          printed: the affine level (one handle at the centre
+                          of mass, phi = 1; left out when the mesh has
+                          Dirichlet vertices) solved on its 12 x 12 operator,
+                          then PCG on (U^T H U) q = U^T (-g - H d_a) with 12 x 12
+                          block-Jacobi preconditioning and the matrix-free
+                          product U^T (H (U q)), to relative residual sub_rtol;
+                          no coarse factorisation */
+  int refine_iters;    /* directions 1, 2: fixed full-space CG iterations (20-40) */
+  double paper_tol;    /* directions 1, 2: subspace-decrement tolerance (1e-3) */
   void* stream;        /* cudaStream_t the context runs on (0 = legacy default) */
+  double sub_rtol;     /* direction 2: relative residual of the subspace PCG (1e-4,
+                          Sec. 3.7.1) */
+  int hessian_lag;     /* directions 1, 2: 1 = the refinement CG solves with H_lag
+                          (Sec. 3.7.2): the element Hessians saved at the last
+                          refresh, with the mass, contact and friction blocks
+                          of the current iterate.  H_lag is refreshed at the
+                          first Newton iteration of a step and whenever the
+                          mean of the last three line-search step sizes falls
+                          below 0.5, at most once every five iterations.
+                          0 (default): the refinement uses the fresh H */
 } mls_options;
 
 typedef struct mls_stats {
@@ -144,6 +162,10 @@ typedef struct mls_stats {
   int coarse_fallbacks;    /* Newton iterations preconditioned by block Jacobi
                               because U^T H U stayed indefinite after the shift
                               retries (the next iteration builds it again) */
+  int subspace_iters;      /* direction 2: subspace PCG iterations summed over the
+                              Newton iterations (the affine level counts one per
+                              Newton iteration) */
+  int hessian_refreshes;   /* hessian_lag: refreshes of H_lag in the step */
 } mls_stats;
 
 typedef struct mls_ctx mls_ctx;

@@ -34,7 +34,11 @@ class Problem:
     """One timestep's incremental potential built from a synthetic scene."""
 
     def __init__(self, scene, x_t=None, v_t=None, dt=None, project=True, integrator="ie", x_prev=None,
-                 v_prev=None, mu=0.0, eps_v=1e-3, body=None):
+                 v_prev=None, mu=0.0, eps_v=1e-3, body=None, threads=1):
+        # threads > 1: the per-element terms are evaluated on contiguous
+        # chunks of the tets by a thread pool and concatenated in tet order;
+        # every element's arithmetic is the same as in one call
+        self.threads = max(1, int(threads))
         self.X = np.asarray(scene.X, dtype=np.float64)
         self.tets = np.asarray(scene.tets, dtype=np.int64)
         self.n = self.X.shape[0]
@@ -89,6 +93,18 @@ class Problem:
         return (3.0 * x_new - 4.0 * self.x_t + self.x_prev) / (2.0 * self.h)
 
     # -- pieces -----------------------------------------------------------
+    def _elements(self, fn, x, **kw):
+        """fn(x, tets, vol, Dm_inv, mu, lam, **kw) over all tets, by chunks
+        on self.threads threads when there are more than one."""
+        if self.threads <= 1:
+            return fn(x, self.tets, self.vol, self.Dm_inv, self.mu, self.lam, **kw)
+        from concurrent.futures import ThreadPoolExecutor
+        chunks = np.array_split(np.arange(len(self.tets)), 4 * self.threads)
+        with ThreadPoolExecutor(self.threads) as ex:
+            parts = list(ex.map(lambda c: fn(x, self.tets[c], self.vol[c], self.Dm_inv[c], self.mu[c],
+                                             self.lam[c], **kw), chunks))
+        return np.concatenate(parts)
+
     def distances(self, x):
         return x @ self.plane_n - self.plane_o
 
@@ -97,8 +113,7 @@ class Problem:
         x = np.asarray(x, dtype=np.float64)
         dx = x[self.free] - self.x_tilde[self.free]
         K = 0.5 * np.sum(self.mass[self.free] * np.sum(dx * dx, axis=1))
-        Psi = np.sum(elastic.element_energy(x, self.tets, self.vol, self.Dm_inv,
-                                            self.mu, self.lam))
+        Psi = np.sum(self._elements(elastic.element_energy, x))
         B = 0.0
         if self.contact:
             B = self.kappa * np.sum(barrier.b(self.distances(x), self.dhat))
@@ -116,7 +131,7 @@ class Problem:
         """dE/dx as [n,3]; zero on Dirichlet vertices."""
         x = np.asarray(x, dtype=np.float64)
         g = self.mass[:, None] * (x - self.x_tilde)
-        ge = elastic.element_gradient(x, self.tets, self.vol, self.Dm_inv, self.mu, self.lam)
+        ge = self._elements(elastic.element_gradient, x)
         gel = np.zeros((self.n, 3))
         np.add.at(gel, self.tets.ravel(), ge.reshape(-1, 3))
         if self.contact:
@@ -139,8 +154,7 @@ class Problem:
         (Sec. 3.8) passes c_e = w_e / vol_e on its elements and 0 elsewhere;
         mass and barrier terms stay fully integrated."""
         x = np.asarray(x, dtype=np.float64)
-        He = elastic.element_hessian(x, self.tets, self.vol, self.Dm_inv, self.mu,
-                                     self.lam, project=self.project)
+        He = self._elements(elastic.element_hessian, x, project=self.project)
         if elem_scale is not None:
             He = He * np.asarray(elem_scale, dtype=np.float64)[:, None, None]
         dof = (3 * self.tets[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)

@@ -62,14 +62,15 @@ class Solver:
     def __init__(self, precision="fp64", preconditioner="jacobi", cycle="additive", omega=1.0,
                  newton_tol=1e-10, pcg_rtol=1e-4, max_newton=50, max_pcg=20000,
                  coarse_refresh=0, pcg_check_every=16, persistent=False, persist_blocks_per_sm=0,
-                 direction="pcg", refine_iters=20, paper_tol=1e-3, stream=None, coarse_lag_steps=0):
+                 direction="pcg", refine_iters=20, paper_tol=1e-3, stream=None, coarse_lag_steps=0,
+                 sub_rtol=1e-4, hessian_lag=False):
         self._l = _get_lib()
         self._ctx = C.c_void_p()
         self.opt = _lib.Options()
         self._l.mls_default_options(C.byref(self.opt))
         self._fill(precision, preconditioner, cycle, omega, newton_tol, pcg_rtol, max_newton, max_pcg,
                    coarse_refresh, pcg_check_every, persistent, persist_blocks_per_sm, direction, refine_iters,
-                   paper_tol, stream, coarse_lag_steps)
+                   paper_tol, stream, coarse_lag_steps, sub_rtol, hessian_lag)
         st = self._l.mls_create(C.byref(self._ctx), C.byref(self.opt))
         if st != _lib.MLS_OK:
             raise MLSError(st, "mls_create failed")
@@ -79,7 +80,7 @@ class Solver:
 
     def _fill(self, precision, preconditioner, cycle, omega, newton_tol, pcg_rtol, max_newton, max_pcg,
               coarse_refresh, pcg_check_every, persistent, persist_blocks_per_sm, direction, refine_iters,
-              paper_tol, stream, coarse_lag_steps=0):
+              paper_tol, stream, coarse_lag_steps=0, sub_rtol=1e-4, hessian_lag=False):
         o = self.opt
         o.precision = _lib.PRECISION[precision]
         o.preconditioner = _lib.PRECOND[preconditioner]
@@ -94,9 +95,12 @@ class Solver:
         o.pcg_check_every = int(pcg_check_every)
         o.persistent = 1 if persistent else 0
         o.persist_blocks_per_sm = int(persist_blocks_per_sm)
-        o.direction = {"pcg": 0, "paper": 1}[direction] if isinstance(direction, str) else int(direction)
+        o.direction = ({"pcg": 0, "paper": 1, "paper_literal": 2}[direction] if isinstance(direction, str)
+                       else int(direction))
         o.refine_iters = int(refine_iters)
         o.paper_tol = float(paper_tol)
+        o.sub_rtol = float(sub_rtol)
+        o.hessian_lag = 1 if hessian_lag else 0
         if stream is None:
             o.stream = None
         else:
@@ -112,7 +116,8 @@ class Solver:
                    persistent=bool(self.opt.persistent),
                    persist_blocks_per_sm=self.opt.persist_blocks_per_sm, direction=self.opt.direction,
                    refine_iters=self.opt.refine_iters, paper_tol=self.opt.paper_tol, stream=self.opt.stream,
-                   coarse_lag_steps=self.opt.coarse_lag_steps)
+                   coarse_lag_steps=self.opt.coarse_lag_steps, sub_rtol=self.opt.sub_rtol,
+                   hessian_lag=bool(self.opt.hessian_lag))
         cur.update(kw)
         self._fill(**cur)
         self._check(self._l.mls_set_options(self._ctx, C.byref(self.opt)))

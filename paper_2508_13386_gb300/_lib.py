@@ -42,6 +42,8 @@ class Options(C.Structure):
         ("refine_iters", C.c_int),
         ("paper_tol", C.c_double),
         ("stream", C.c_void_p),
+        ("sub_rtol", C.c_double),
+        ("hessian_lag", C.c_int),
     ]
 
 
@@ -58,6 +60,8 @@ class Stats(C.Structure):
         ("warm_start_used", C.c_int),
         ("coarse_shifts", C.c_int),
         ("coarse_fallbacks", C.c_int),
+        ("subspace_iters", C.c_int),
+        ("hessian_refreshes", C.c_int),
     ]
 
     def as_dict(self):

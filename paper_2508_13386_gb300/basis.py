@@ -474,6 +474,37 @@ def build_sms_basis(X, tets, E, m_target, dirichlet=None, seed=0, workers=None, 
             "phi_dbc": phi_dbc, "neighbours": [sorted(s) for s in nb_sets], "supports": supports}
 
 
+def refinement_cg_iterations(tets, partition, handle_vertex):
+    """The refinement's CG count (Sec. 3.7.2): for each partition, the largest
+    number of mesh-edge hops from its handle vertex (the vertex nearest its
+    centroid) to a vertex of the partition, the path running through the
+    partition's own tets; the mean over partitions; and the fixed count of
+    full-space CG iterations, 20 or 40, whichever is nearer that mean.
+    Vertices that the partition's tets do not connect to the handle vertex
+    are left out.  Returns (mean hops, per-partition hops, 20 or 40)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+    tets = np.asarray(tets, dtype=np.int64)
+    partition = np.asarray(partition, dtype=np.int64)
+    hops = []
+    for i, hv in enumerate(np.asarray(handle_vertex, dtype=np.int64)):
+        sub = tets[partition == i]
+        if len(sub) == 0:
+            continue
+        verts, local = np.unique(sub, return_inverse=True)
+        lt = local.reshape(-1, 4)
+        a = np.concatenate([lt[:, p] for p in range(4) for q in range(4) if p != q])
+        b = np.concatenate([lt[:, q] for p in range(4) for q in range(4) if p != q])
+        G = sp.coo_matrix((np.ones(len(a)), (a, b)), shape=(len(verts), len(verts))).tocsr()
+        src = np.searchsorted(verts, hv)
+        if src >= len(verts) or verts[src] != hv:
+            continue
+        d = shortest_path(G, unweighted=True, indices=src)
+        hops.append(int(np.max(d[np.isfinite(d)])))
+    mean = float(np.mean(hops)) if hops else 0.0
+    return mean, hops, (20 if abs(mean - 20) <= abs(mean - 40) else 40)
+
+
 def vlabels_to_part(verts, tets, part):
     """Partition of some tet containing each vertex (first such tet)."""
     n = int(tets.max()) + 1

@@ -381,7 +381,8 @@ mls_status launch_gather_grad(mls_ctx* ctx, const Vec4d* x, double* gnorm2_out) 
 
 // H (or, with escale, the cubature H of the coarse operator) at x into val;
 // dinv (nullable) receives the block-Jacobi inverse
-static mls_status assemble_into(mls_ctx* ctx, const Vec4d* x, void* val, void* dinv, const double* escale) {
+static mls_status assemble_into(mls_ctx* ctx, const Vec4d* x, const void* eh, void* val, void* dinv,
+                                const double* escale) {
   SellAsmIn in{ctx->n, ctx->t, ctx->group_slice, ctx->col, ctx->row_len, ctx->slice_ptr, ctx->asm_ptr,
                ctx->asm_code, ctx->mass, ctx->pinned, ctx->h * ctx->h, ctx->kappa, ctx->dhat, ctx->po,
                ctx->pn[0], ctx->pn[1], ctx->pn[2], ctx->contact, ctx->xt,
@@ -394,38 +395,44 @@ static mls_status assemble_into(mls_ctx* ctx, const Vec4d* x, void* val, void* d
     case MLS_FP64:
       if (fric)
         k_assemble<double, double, double, double, true><<<nb, kBlock, 0, ctx->stream>>>(
-            in, n_slots, x, (const double*)ctx->ehess, (double*)val, (double*)dinv, escale);
+            in, n_slots, x, (const double*)eh, (double*)val, (double*)dinv, escale);
       else
         k_assemble<double, double, double, double, false><<<nb, kBlock, 0, ctx->stream>>>(
-            in, n_slots, x, (const double*)ctx->ehess, (double*)val, (double*)dinv, escale);
+            in, n_slots, x, (const double*)eh, (double*)val, (double*)dinv, escale);
       break;
     case MLS_MIXED_FP32:
       if (fric)
         k_assemble<float, float, float, float, true><<<nb, kBlock, 0, ctx->stream>>>(
-            in, n_slots, x, (const float*)ctx->ehess, (float*)val, (float*)dinv, escale);
+            in, n_slots, x, (const float*)eh, (float*)val, (float*)dinv, escale);
       else
         k_assemble<float, float, float, float, false><<<nb, kBlock, 0, ctx->stream>>>(
-            in, n_slots, x, (const float*)ctx->ehess, (float*)val, (float*)dinv, escale);
+            in, n_slots, x, (const float*)eh, (float*)val, (float*)dinv, escale);
       break;
     default:
       if (fric)
         k_assemble<float, float, __nv_bfloat16, float, true><<<nb, kBlock, 0, ctx->stream>>>(
-            in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)val, (float*)dinv, escale);
+            in, n_slots, x, (const float*)eh, (__nv_bfloat16*)val, (float*)dinv, escale);
       else
         k_assemble<float, float, __nv_bfloat16, float, false><<<nb, kBlock, 0, ctx->stream>>>(
-            in, n_slots, x, (const float*)ctx->ehess, (__nv_bfloat16*)val, (float*)dinv, escale);
+            in, n_slots, x, (const float*)eh, (__nv_bfloat16*)val, (float*)dinv, escale);
       break;
   }
   return cuda_check(ctx, cudaGetLastError(), "k_assemble");
 }
 
 mls_status launch_assemble(mls_ctx* ctx, const Vec4d* x) {
-  return assemble_into(ctx, x, ctx->hval, ctx->dinv, nullptr);
+  return assemble_into(ctx, x, ctx->ehess, ctx->hval, ctx->dinv, nullptr);
 }
 
 mls_status launch_assemble_cubature(mls_ctx* ctx, const Vec4d* x) {
   if (!ctx->cub_scale || !ctx->hval_cub) return fail(ctx, MLS_EINVAL, "no cubature uploaded");
-  return assemble_into(ctx, x, ctx->hval_cub, nullptr, ctx->cub_scale);
+  return assemble_into(ctx, x, ctx->ehess, ctx->hval_cub, nullptr, ctx->cub_scale);
+}
+
+// H_lag of the paper's refinement (Sec. 3.7.2): the element Hessians saved at
+// the last refresh with the mass and the contact and friction blocks of x
+mls_status launch_assemble_lagged(mls_ctx* ctx, const Vec4d* x) {
+  return assemble_into(ctx, x, ctx->ehess_lag, ctx->hval_lag, ctx->dinv_lag, nullptr);
 }
 
 mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, double dt) {

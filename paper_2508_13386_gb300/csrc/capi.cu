@@ -144,11 +144,16 @@ static void free_all(mls_ctx* ctx) {
   ctx->ws_hsave = nullptr;
   ctx->oz_fwd = ctx->oz_rev = nullptr;
   ctx->oz_e = ctx->umma_err = nullptr;
+  ctx->sms_buf = nullptr;
+  ctx->sms_cg = nullptr;
+  ctx->sms_m = nullptr;
+  ctx->ehess_lag = ctx->hval_lag = ctx->dinv_lag = nullptr;
   ctx->ws_ready = ctx->ws_enabled = ctx->ws_hist_valid = ctx->ws_record = false;
   ctx->ws_mlp = nullptr;
   ctx->basis = Basis{};
   ctx->has_basis = false;
   ctx->coarse_ready = false;
+  ctx->galerkin_ready = false;
   ctx->assembled = false;
   ctx->cub_scale = nullptr;
   ctx->hval_cub = nullptr;
@@ -178,6 +183,8 @@ mls_status mls_default_options(mls_options* opt) {
   opt->direction = 0;
   opt->refine_iters = 20;
   opt->paper_tol = 1e-3;
+  opt->sub_rtol = 1e-4;
+  opt->hessian_lag = 0;
   opt->stream = nullptr;
   return MLS_OK;
 }
@@ -191,7 +198,8 @@ static mls_status check_options(const mls_options* o) {
     return MLS_EINVAL;
   if (o->persistent < 0 || o->persistent > 1 || o->persist_blocks_per_sm < 0 || o->persist_blocks_per_sm > 32)
     return MLS_EINVAL;
-  if (o->direction < 0 || o->direction > 1 || o->refine_iters < 0 || !(o->paper_tol > 0)) return MLS_EINVAL;
+  if (o->direction < 0 || o->direction > 2 || o->refine_iters < 0 || !(o->paper_tol > 0)) return MLS_EINVAL;
+  if (o->direction == 2 && !(o->sub_rtol > 0 && o->sub_rtol < 1)) return MLS_EINVAL;
   return MLS_OK;
 }
 
@@ -244,6 +252,7 @@ mls_status mls_set_options(mls_ctx* ctx, const mls_options* opt) {
   ctx->opt = *opt;
   ctx->stream = (cudaStream_t)opt->stream;
   ctx->coarse_ready = false;
+  ctx->galerkin_ready = false;
   ctx->omega_eff = opt->omega > 0.0 ? opt->omega : 0.5;
   return MLS_OK;
 }
@@ -413,6 +422,7 @@ mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n, const double* X, int32_t t, 
   if ((st = up((void**)&ctx->lam, h_lam.data(), sizeof(double) * t)) != MLS_OK) return st;
   if ((st = up((void**)&ctx->mass, h_mass.data(), sizeof(double) * n)) != MLS_OK) return st;
   if ((st = up((void**)&ctx->pinned, pin.data(), n)) != MLS_OK) return st;
+  ctx->h_pinned = pin;
   if ((st = up((void**)&ctx->X, Xp.data(), sizeof(Vec4d) * n)) != MLS_OK) return st;
   if ((st = up((void**)&ctx->slice_ptr, slice_ptr.data(), sizeof(int) * (n_slices + 1))) != MLS_OK) return st;
   if ((st = up((void**)&ctx->group_slice, group_slice.data(), sizeof(int) * n_groups)) != MLS_OK) return st;
@@ -531,11 +541,157 @@ static mls_status assemble_at(mls_ctx* ctx, const Vec4d* x, double* gnorm) {
 // H d_f = -g - H d_s from d_f = 0 (Sec. 3.8: a fixed count of Jacobi-
 // preconditioned CG iterations).  Leaves d = d_s + d_f in vx (solve
 // precision) and returns sum_v |d_s,v|_2 and the CG iterations run.
-static mls_status paper_direction(mls_ctx* ctx, double* ds_norm, int* cg_iters) {
+// H_lag refresh: the current element Hessians become the lagged ones
+constexpr double kLagAlpha = 0.5;
+constexpr int kLagMinAge = 5;
+static mls_status hessian_lag_refresh(mls_ctx* ctx) {
   mls_status st;
-  if ((st = launch_restrict(ctx, ctx->vb, ctx->cvec)) != MLS_OK) return st;
-  if ((st = coarse_apply(ctx, ctx->cvec, ctx->cvec2)) != MLS_OK) return st;
-  if ((st = launch_prolong(ctx, ctx->cvec2, ctx->vw, false)) != MLS_OK) return st;
+  const size_t eb = (size_t)78 * ctx->t * (ctx->opt.precision == MLS_FP64 ? 8 : 4);
+  if (!ctx->ehess_lag) {
+    if ((st = dalloc(ctx, &ctx->ehess_lag, eb)) != MLS_OK) return st;
+    if ((st = dalloc(ctx, &ctx->hval_lag, (size_t)storage_bytes(ctx) * 288 * ctx->n_groups)) != MLS_OK) return st;
+    if ((st = dalloc(ctx, &ctx->dinv_lag, (size_t)solve_bytes(ctx) * 9 * ctx->n)) != MLS_OK) return st;
+  }
+  ctx->lag_age = 0;
+  ctx->lag_nalpha = 0;
+  return cuda_check(ctx, cudaMemcpyAsync(ctx->ehess_lag, ctx->ehess, eb, cudaMemcpyDeviceToDevice, ctx->stream),
+                    "H_lag refresh");
+}
+
+// The subspace direction of Alg. 2 as printed (direction 2), into vw:
+// the affine level (one handle at the centre of mass, phi = 1, Sec. 3.4)
+// solved on its 12 x 12 operator A_a = T^T (U^T H U) T, T the coordinates of
+// an affine motion in the SMS basis (the SMS weights sum to one), then the
+// SMS level by block-Jacobi PCG on the residual (sms_pcg).  The affine level
+// is left out on meshes with Dirichlet vertices, whose SMS weights do not
+// sum to one there.
+static mls_status subspace_direction_literal(mls_ctx* ctx, int* sub_iters) {
+  mls_status st;
+  const Basis& B = ctx->basis;
+  const int m = B.m, r = 12 * m;
+  const bool fp64 = ctx->opt.precision == MLS_FP64;
+  const size_t vb = fp64 ? sizeof(double) : sizeof(float);
+  if ((st = launch_restrict(ctx, ctx->vb, ctx->cvec)) != MLS_OK) return st;  // U^T (-g)
+  bool affine = true;
+  for (int v = 0; v < ctx->n && affine; ++v) affine = !ctx->h_pinned[v];
+  *sub_iters = 0;
+  std::vector<double> ca(r, 0.0);
+  if (affine) {
+    // centre of mass and the offsets d_j = o_j - o_a
+    double om[3] = {0, 0, 0}, mt = 0;
+    for (int v = 0; v < ctx->n; ++v) {
+      mt += ctx->h_mass[v];
+      for (int c = 0; c < 3; ++c) om[c] += ctx->h_mass[v] * ctx->h_X[3 * (size_t)v + c];
+    }
+    for (int c = 0; c < 3; ++c) om[c] /= mt;
+    std::vector<double> d(3 * (size_t)m);
+    for (int j = 0; j < m; ++j)
+      for (int c = 0; c < 3; ++c) d[3 * j + c] = B.h_origins[3 * (size_t)j + c] - om[c];
+    // M = A_s T on the device, then A_a = T^T M and b_a = T^T U^T(-g) here
+    if ((st = affine_operator(ctx, om)) != MLS_OK) return st;
+    std::vector<double> M((size_t)r * 12), cg(r);
+    std::vector<float> cgf;
+    if ((st = cuda_check(ctx, cudaMemcpyAsync(M.data(), ctx->sms_m, sizeof(double) * M.size(), cudaMemcpyDeviceToHost,
+                                              ctx->stream), "affine operator")) != MLS_OK)
+      return st;
+    if (fp64) {
+      st = cuda_check(ctx, cudaMemcpyAsync(cg.data(), ctx->cvec, sizeof(double) * r, cudaMemcpyDeviceToHost, ctx->stream),
+                      "U^T g");
+    } else {
+      cgf.resize(r);
+      st = cuda_check(ctx, cudaMemcpyAsync(cgf.data(), ctx->cvec, sizeof(float) * r, cudaMemcpyDeviceToHost, ctx->stream),
+                      "U^T g");
+    }
+    if (st != MLS_OK) return st;
+    if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "affine sync")) != MLS_OK) return st;
+    if (!fp64)
+      for (int i = 0; i < r; ++i) cg[i] = cgf[i];
+    // T^T applied to a coarse vector y (length r) and to the columns of M:
+    // (T^T y)[(c, 0)] = sum_j y[12j+4c]; (T^T y)[(c, l)] = sum_j y[12j+4c+l] + d_{j,l} y[12j+4c]
+    auto tt = [&](auto get, double out[12]) {
+      for (int k = 0; k < 12; ++k) out[k] = 0.0;
+      for (int j = 0; j < m; ++j)
+        for (int c = 0; c < 3; ++c) {
+          const double y0 = get(12 * j + 4 * c);
+          out[4 * c] += y0;
+          for (int l = 1; l < 4; ++l) out[4 * c + l] += get(12 * j + 4 * c + l) + d[3 * j + l - 1] * y0;
+        }
+    };
+    double Aa[12][12], ba[12];
+    for (int col = 0; col < 12; ++col) {
+      double out[12];
+      tt([&](int i) { return M[(size_t)i * 12 + col]; }, out);
+      for (int k = 0; k < 12; ++k) Aa[k][col] = out[k];
+    }
+    tt([&](int i) { return cg[i]; }, ba);
+    // 12 x 12 Cholesky solve of A_a q_a = b_a (the block-Jacobi PCG of a
+    // single 12 x 12 block converges in one step)
+    double L[12][12] = {};
+    for (int i = 0; i < 12; ++i)
+      for (int j = 0; j <= i; ++j) {
+        double sum = 0.5 * (Aa[i][j] + Aa[j][i]);
+        for (int k = 0; k < j; ++k) sum -= L[i][k] * L[j][k];
+        if (i == j) {
+          if (!(sum > 0.0)) return fail(ctx, MLS_ECHOL, "affine level: operator not positive definite");
+          L[i][i] = std::sqrt(sum);
+        } else {
+          L[i][j] = sum / L[j][j];
+        }
+      }
+    double y[12], qa[12];
+    for (int i = 0; i < 12; ++i) {
+      double sum = ba[i];
+      for (int k = 0; k < i; ++k) sum -= L[i][k] * y[k];
+      y[i] = sum / L[i][i];
+    }
+    for (int i = 11; i >= 0; --i) {
+      double sum = y[i];
+      for (int k = i + 1; k < 12; ++k) sum -= L[k][i] * qa[k];
+      qa[i] = sum / L[i][i];
+    }
+    // c_a = T q_a
+    for (int j = 0; j < m; ++j)
+      for (int c = 0; c < 3; ++c) {
+        double t0 = qa[4 * c];
+        for (int l = 1; l < 4; ++l) {
+          t0 += d[3 * j + l - 1] * qa[4 * c + l];
+          ca[12 * j + 4 * c + l] = qa[4 * c + l];
+        }
+        ca[12 * j + 4 * c] = t0;
+      }
+    *sub_iters += 1;
+    // d_a = U c_a into vw; right-hand side of the SMS level U^T (-g - H d_a)
+    if (fp64) {
+      st = cuda_check(ctx, cudaMemcpyAsync(ctx->cvec2, ca.data(), vb * r, cudaMemcpyHostToDevice, ctx->stream), "c_a");
+    } else {
+      cgf.assign(ca.begin(), ca.end());
+      st = cuda_check(ctx, cudaMemcpyAsync(ctx->cvec2, cgf.data(), vb * r, cudaMemcpyHostToDevice, ctx->stream), "c_a");
+    }
+    if (st != MLS_OK) return st;
+    if ((st = launch_prolong(ctx, ctx->cvec2, ctx->vw, false)) != MLS_OK) return st;
+    if ((st = launch_residual(ctx, ctx->vb, ctx->vw, ctx->vz2, nullptr)) != MLS_OK) return st;
+    if ((st = launch_restrict(ctx, ctx->vz2, ctx->cvec)) != MLS_OK) return st;
+    if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "affine upload")) != MLS_OK) return st;
+  } else {
+    if ((st = cuda_check(ctx, cudaMemsetAsync(ctx->vw, 0, (size_t)ctx->n * 4 * vb, ctx->stream), "d_a = 0")) != MLS_OK)
+      return st;
+  }
+  int it = 0;
+  if ((st = sms_pcg(ctx, ctx->cvec, ctx->opt.sub_rtol, 100000, &it)) != MLS_OK) return st;
+  *sub_iters += it;
+  return launch_prolong(ctx, ctx->cvec, ctx->vw, true);  // d_s = d_a + U q
+}
+
+static mls_status paper_direction(mls_ctx* ctx, double* ds_norm, int* cg_iters, int* sub_iters) {
+  mls_status st;
+  *sub_iters = 0;
+  if (ctx->opt.direction == 2) {
+    if ((st = subspace_direction_literal(ctx, sub_iters)) != MLS_OK) return st;
+  } else {
+    if ((st = launch_restrict(ctx, ctx->vb, ctx->cvec)) != MLS_OK) return st;
+    if ((st = coarse_apply(ctx, ctx->cvec, ctx->cvec2)) != MLS_OK) return st;
+    if ((st = launch_prolong(ctx, ctx->cvec2, ctx->vw, false)) != MLS_OK) return st;
+  }
   if ((st = launch_from_solve(ctx, ctx->vw, ctx->dir)) != MLS_OK) return st;
   if ((st = vnorm_sum(ctx, ctx->dir, ds_norm)) != MLS_OK) return st;
   // right-hand side of the refinement: vb = -g - H d_s (through vz2)
@@ -546,12 +702,21 @@ static mls_status paper_direction(mls_ctx* ctx, double* ds_norm, int* cg_iters) 
     return st;
   const int pc = ctx->opt.preconditioner;
   ctx->opt.preconditioner = MLS_PRECOND_BLOCK_JACOBI;
+  const bool lag = ctx->opt.hessian_lag && ctx->hval_lag;
+  if (lag) {  // the refinement solves H_lag d_f = r (Sec. 3.7.2)
+    std::swap(ctx->hval, ctx->hval_lag);
+    std::swap(ctx->dinv, ctx->dinv_lag);
+  }
   double rel = 0;
   *cg_iters = 0;
   if (ctx->opt.refine_iters > 0) {
     st = pcg_solve(ctx, 0.0, ctx->opt.refine_iters, cg_iters, &rel);
   } else {
     st = cuda_check(ctx, cudaMemsetAsync(ctx->vx, 0, vbytes, ctx->stream), "zero d_f");
+  }
+  if (lag) {
+    std::swap(ctx->hval, ctx->hval_lag);
+    std::swap(ctx->dinv, ctx->dinv_lag);
   }
   ctx->opt.preconditioner = pc;
   if (st != MLS_OK && st != MLS_ENOTCONV) return st;
@@ -585,7 +750,7 @@ static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
   }
   const bool two_level = ctx->opt.preconditioner == MLS_PRECOND_TWO_LEVEL;
   if (two_level && !ctx->has_basis) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_upload_basis");
-  const bool paper = ctx->opt.direction == 1;
+  const bool paper = ctx->opt.direction >= 1;
   if (paper && !two_level) return fail(ctx, MLS_EINVAL, "the paper's direction needs the two-level preconditioner");
   {
     int used = 0;
@@ -606,13 +771,15 @@ static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
     bool lagged_first = false;
     if (two_level) {
       const int k = ctx->opt.coarse_refresh;
-      bool rebuild = k == 0 || it % k == 0 || !ctx->coarse_ready || ctx->coarse_stale;
+      const bool ready = ctx->opt.direction == 2 ? ctx->galerkin_ready : ctx->coarse_ready;
+      bool rebuild = k == 0 || it % k == 0 || !ready || ctx->coarse_stale;
       // a lagged factor only preconditions: the paper's direction solves with it
       if (it == 0 && !paper && ctx->coarse_ready && !ctx->coarse_stale &&
           ctx->coarse_age_steps <= ctx->opt.coarse_lag_steps)
         rebuild = false;
       if (rebuild) {
-        st = build_coarse(ctx);
+        // the literal subspace solve needs U^T H U itself, not a factor
+        st = ctx->opt.direction == 2 ? build_coarse_unfactored(ctx) : build_coarse(ctx);
         // a coarse operator that stays indefinite after the shift retries:
         // this Newton iteration preconditions with block Jacobi, and the
         // next one tries the coarse build again at its own iterate
@@ -630,10 +797,26 @@ static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
     }
     if (it == 0 && (st = warm_start_first_iteration(ctx)) != MLS_OK) return st;
     if (paper) {
+      if (ctx->opt.hessian_lag) {
+        // H_lag (Sec. 3.7.2): refreshed at the step's first iteration and when
+        // the mean of the last three step sizes falls below kLagAlpha, at most
+        // once every kLagMinAge iterations; contact and friction blocks fresh
+        double ma = 0.0;
+        const int na = std::min(ctx->lag_nalpha, 3);
+        for (int k = 0; k < na; ++k) ma += ctx->lag_alpha[k];
+        ma = na ? ma / na : 1.0;
+        if (it == 0 || (na == 3 && ma < kLagAlpha && ctx->lag_age >= kLagMinAge)) {
+          if ((st = hessian_lag_refresh(ctx)) != MLS_OK) return st;
+          S.hessian_refreshes++;
+        }
+        if ((st = launch_assemble_lagged(ctx, ctx->xk)) != MLS_OK) return st;
+        ctx->lag_age++;
+      }
       double ds_norm = 0;
-      int cg = 0;
-      if ((st = paper_direction(ctx, &ds_norm, &cg)) != MLS_OK) return st;
+      int cg = 0, sub = 0;
+      if ((st = paper_direction(ctx, &ds_norm, &cg, &sub)) != MLS_OK) return st;
       S.pcg_iters += cg;
+      S.subspace_iters += sub;
       if ((st = launch_from_solve(ctx, ctx->vx, ctx->dir)) != MLS_OK) return st;
       double gd = 0;
       if ((st = dot4(ctx, ctx->grad, ctx->dir, &gd)) != MLS_OK) return st;
@@ -656,6 +839,8 @@ static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
       }
       if (!accepted) return fail(ctx, MLS_ELINESEARCH, "line search found no acceptable step");
       if ((st = launch_axpy_state(ctx, ctx->xk, ctx->dir, alpha)) != MLS_OK) return st;
+      ctx->lag_alpha[ctx->lag_nalpha % 3] = alpha;
+      ctx->lag_nalpha++;
       S.step_rel = ds_norm / (h * ctx->n);
       if (S.step_rel < ctx->opt.paper_tol) { result = MLS_OK; break; }
       continue;
@@ -850,7 +1035,7 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
                    B.vcoef, B.hcoef, B.rchunk_handle, B.rchunk_beg, B.rchunk_ptr, B.rpart, B.rcount,
                    ctx->gpart, ctx->yval, ctx->Ac, ctx->Acopy,
                    ctx->Linv, ctx->LinvT, ctx->Ainv, ctx->cvec, ctx->cvec2, ctx->chol_info, ctx->chol_tinv,
-                   ctx->oz_fwd, ctx->oz_rev, ctx->oz_e,
+                   ctx->oz_fwd, ctx->oz_rev, ctx->oz_e, ctx->sms_buf, ctx->sms_cg, ctx->sms_m,
                    ctx->Am, ctx->Wm, ctx->WmT, ctx->ws_c, ctx->ws_c2, ctx->ws_tmp, ctx->ws_hist, ctx->ws_qg,
                    ctx->ws_qtilde, ctx->ws_qnext, ctx->ws_feat, ctx->ws_target, ctx->ws_pred, ctx->ws_hsave};
     for (void* p : old) dfree(ctx, p);
@@ -860,11 +1045,15 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
     ctx->ws_hsave = nullptr;
     ctx->oz_fwd = ctx->oz_rev = nullptr;
     ctx->oz_e = nullptr;
+    ctx->sms_buf = nullptr;
+    ctx->sms_cg = nullptr;
+    ctx->sms_m = nullptr;
     ctx->ws_ready = ctx->ws_enabled = ctx->ws_hist_valid = ctx->ws_record = false;
     ctx->ws_mlp = nullptr;
     ctx->basis = Basis{};
     ctx->has_basis = false;
     ctx->coarse_ready = false;
+    ctx->galerkin_ready = false;
   }
   return basis_upload(ctx, m, origins, vrow, handle, phi);
 }
@@ -877,6 +1066,7 @@ mls_status mls_upload_cubature(mls_ctx* ctx, const double* scale) {
   ctx->cub_scale = nullptr;
   ctx->hval_cub = nullptr;
   ctx->coarse_ready = false;
+  ctx->galerkin_ready = false;
   if (!scale) return MLS_OK;
   for (int e = 0; e < ctx->t; ++e)
     if (!(scale[e] >= 0.0) || !std::isfinite(scale[e])) return fail(ctx, MLS_EINVAL, "cubature scale must be finite and >= 0");

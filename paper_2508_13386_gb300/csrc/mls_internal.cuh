@@ -422,6 +422,69 @@ __device__ __forceinline__ PcgHead<VT> pcg_head(const PcgScalars* S, const PcgHe
   else if (i >= S->max_iter) h.done = 2;
   return h;
 }
+// The same loads spread over the lanes of one warp, so that they take one
+// round trip instead of a chain: lanes 0-4 and 5-9 read the r.z and r.r
+// slots, lanes 10-16 the stop flag and the scalars the decision needs, and
+// every lane gets every value by shuffles.  Call with a whole warp.
+struct PcgOpen {
+  FixRaw rz, rr;
+  double rzp, rrp, tol2, rz0, rr0;
+  int max_iter, done;
+};
+__device__ __forceinline__ PcgOpen pcg_open_load_warp(const unsigned long long* fix, const PcgScalars* S, int i) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long* rzs = fix_slot(const_cast<unsigned long long*>(fix), FX_RZ, i & 1);
+  const unsigned long long* rrs = fix_slot(const_cast<unsigned long long*>(fix), FX_RR, i & 1);
+  const int ip = (i - 1) & 1;
+  unsigned long long w = 0ull;
+  if (lane < 5) w = __ldcg(rzs + lane * kFixStride);
+  else if (lane < 10) w = __ldcg(rrs + (lane - 5) * kFixStride);
+  else if (lane == 10) w = (unsigned long long)(unsigned)__ldcg(&S->done);
+  else if (lane == 11) w = (unsigned long long)__double_as_longlong(__ldcg(&S->rzv[ip]));
+  else if (lane == 12) w = (unsigned long long)__double_as_longlong(__ldcg(&S->rrv[ip]));
+  else if (lane == 13) w = (unsigned long long)__double_as_longlong(__ldcg(&S->tol2));
+  else if (lane == 14) w = (unsigned long long)(unsigned)__ldcg(&S->max_iter);
+  else if (lane == 15) w = (unsigned long long)__double_as_longlong(__ldcg(&S->rzv[0]));
+  else if (lane == 16) w = (unsigned long long)__double_as_longlong(__ldcg(&S->rrv[0]));
+  PcgOpen o;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    o.rz.w[k] = __shfl_sync(0xffffffffu, w, k);
+    o.rr.w[k] = __shfl_sync(0xffffffffu, w, 5 + k);
+  }
+  o.done = (int)__shfl_sync(0xffffffffu, w, 10);
+  o.rzp = __longlong_as_double((long long)__shfl_sync(0xffffffffu, w, 11));
+  o.rrp = __longlong_as_double((long long)__shfl_sync(0xffffffffu, w, 12));
+  o.tol2 = __longlong_as_double((long long)__shfl_sync(0xffffffffu, w, 13));
+  o.max_iter = (int)__shfl_sync(0xffffffffu, w, 14);
+  o.rz0 = __longlong_as_double((long long)__shfl_sync(0xffffffffu, w, 15));
+  o.rr0 = __longlong_as_double((long long)__shfl_sync(0xffffffffu, w, 16));
+  return o;
+}
+// pcg_head() from the values pcg_open_load_warp() read
+template <typename VT>
+__device__ __forceinline__ PcgHead<VT> pcg_head_open(const PcgOpen& o, int i) {
+  PcgHead<VT> h;
+  bool bad = false;
+  if (i == 0) {
+    h.rz = o.rz0;
+    h.rr = o.rr0;
+    h.beta = VT(0);
+  } else {
+    bool b1, b2;
+    h.rz = fix_value(o.rz, fix_exponent(o.rzp), b1);
+    h.rr = fix_value(o.rr, fix_exponent(o.rrp), b2);
+    h.beta = ratio<VT>(h.rz, o.rzp);
+    bad = b1 || b2;
+  }
+  h.done = 0;
+  if (bad || !dbl_finite(h.rr)) h.done = 3;
+  else if (dbl_le_nonneg(h.rr, o.tol2)) h.done = 1;
+  else if (!dbl_positive(h.rz)) h.done = 3;
+  else if (i >= o.max_iter) h.done = 2;
+  return h;
+}
+
 // written once per iteration (block 0 of the opening kernel): the state for
 // later kernels and the host, and the PQ slot of iteration i - 1 cleared
 template <typename VT>
@@ -567,6 +630,12 @@ struct mls_ctx {
   double* stage = nullptr;         // [3][n][3] staging for host-pointer timesteps
   double* egrad = nullptr;         // [12][t]
   void* ehess = nullptr;           // [78][t] element precision
+  void* ehess_lag = nullptr;       // element Hessians of the last H_lag refresh (hessian_lag)
+  void* hval_lag = nullptr;        // H_lag values and its block-Jacobi inverse
+  void* dinv_lag = nullptr;
+  int lag_age = 0;                 // Newton iterations since the last refresh
+  int lag_nalpha = 0;              // line-search step sizes since the refresh (up to 3 kept)
+  double lag_alpha[3] = {1.0, 1.0, 1.0};
   void* hval = nullptr;            // [n_groups * 288] storage precision
   void* dinv = nullptr;            // [n][9] solve precision
   void* vb = nullptr;              // PCG vectors in solve precision: b, x, r, z, p, q, w
@@ -618,6 +687,10 @@ struct mls_ctx {
   __nv_bfloat16* oz_rev = nullptr;  // the same slices in reversed order
   int* oz_e = nullptr;              // [r] row exponents of the panel
   int* umma_err = nullptr;          // set by a tensor-core product whose bounded wait gave up
+  double* sms_buf = nullptr;        // Alg. 2 subspace PCG: [r] q, res, z, p and the [m][144] block inverses
+  void* sms_cg = nullptr;           // its scalars
+  double* sms_m = nullptr;          // [r][12] U^T H U T (the affine level's operator before T^T)
+  bool galerkin_ready = false;      // Acopy holds U^T H U of the current iterate (direction 2)
   bool coarse_ready = false;
   bool coarse_fallback = false;    // this Newton iteration preconditions with block Jacobi (coarse factor failed)
   int64_t coarse_shift_count = 0;  // diagonal-shift retries of the coarse factorisation so far
@@ -648,6 +721,7 @@ struct mls_ctx {
   bool ws_record = false;          // record training targets (keeps H(x_tilde))
   void* ws_hsave = nullptr;        // copy of H's values at the first Newton iterate
   std::vector<double> h_mass, h_X; // host copies for assembling U^T M U
+  std::vector<uint8_t> h_pinned;   // host copy of the Dirichlet mask
 
   // kernel-class timing
   uint32_t prof_mask = 0;
@@ -746,6 +820,10 @@ mls_status gemm_bf16_tn(cudaStream_t stream, int M, int N, int K, const __nv_bfl
                         const __nv_bfloat16* B, int ldb, float* C, int ldc, const GemmEpilogue& ep, int* err);
 mls_status build_galerkin(mls_ctx* ctx);   // U^T H U into the dense Ac only (no factorisation)
 mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out);
+mls_status sms_pcg(mls_ctx* ctx, const void* b, double rtol, int max_iter, int* iters);
+mls_status build_coarse_unfactored(mls_ctx* ctx);
+mls_status launch_assemble_lagged(mls_ctx* ctx, const Vec4d* x);
+mls_status affine_operator(mls_ctx* ctx, const double om[3]);
 mls_status warm_start_begin(mls_ctx* ctx, int* used);
 mls_status warm_start_first_iteration(mls_ctx* ctx);
 mls_status warm_start_end(mls_ctx* ctx);

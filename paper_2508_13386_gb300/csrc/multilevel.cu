@@ -265,6 +265,7 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
     return st;
   ctx->has_basis = true;
   ctx->coarse_ready = false;
+  ctx->galerkin_ready = false;
   return MLS_OK;
 }
 
@@ -1253,6 +1254,269 @@ mls_status build_galerkin(mls_ctx* ctx) {
     case MLS_MIXED_FP32: return galerkin_t<double, float>(ctx);
     default: return galerkin_t<double, __nv_bfloat16>(ctx);
   }
+}
+
+// ---- Alg. 2's subspace PCG (the paper's literal subspace solve) ---------------------------
+// (U^T H U) q = b by conjugate gradient with the 12 x 12 block-Jacobi
+// preconditioner (one block per handle, Sec. 3.7.1) and the matrix-free
+// product U^T (H (U p)), which runs through the prolongation, the sparse
+// product and the restriction kernels; the short coarse vectors (length
+// r = 12 m) are updated by one block in float64.
+
+// inverse of each handle's 12 x 12 diagonal block of the dense coarse
+// operator (row-major r x r) by Gauss-Jordan elimination with partial
+// pivoting, one thread per handle; a zero pivot leaves the identity block
+__global__ void k_block_jacobi12(const double* __restrict__ A, int r, double* __restrict__ Binv) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (12 * j >= r) return;
+  double a[12][24];
+  for (int i = 0; i < 12; ++i)
+    for (int k = 0; k < 12; ++k) {
+      a[i][k] = A[(int64_t)(12 * j + i) * r + 12 * j + k];
+      a[i][12 + k] = (i == k) ? 1.0 : 0.0;
+    }
+  bool ok = true;
+  for (int c = 0; c < 12 && ok; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < 12; ++i)
+      if (fabs(a[i][c]) > fabs(a[piv][c])) piv = i;
+    if (!(fabs(a[piv][c]) > 0.0)) { ok = false; break; }
+    if (piv != c)
+      for (int k = 0; k < 24; ++k) { const double t = a[c][k]; a[c][k] = a[piv][k]; a[piv][k] = t; }
+    const double inv = 1.0 / a[c][c];
+    for (int k = 0; k < 24; ++k) a[c][k] *= inv;
+    for (int i = 0; i < 12; ++i) {
+      if (i == c) continue;
+      const double f = a[i][c];
+      if (f != 0.0)
+        for (int k = 0; k < 24; ++k) a[i][k] -= f * a[c][k];
+    }
+  }
+  double* B = Binv + (int64_t)j * 144;
+  for (int i = 0; i < 12; ++i)
+    for (int k = 0; k < 12; ++k) B[i * 12 + k] = ok ? a[i][12 + k] : (i == k ? 1.0 : 0.0);
+}
+
+struct SmsCg {
+  double rz, bb, tol2;
+  int iter, max_iter, done;  // done: 1 converged, 2 iteration cap, 3 breakdown
+};
+
+// z = blockdiag(Binv) res, r entries, one block; returns res.z and res.res
+// reduced over the block (valid in thread 0)
+__device__ __forceinline__ void sms_precond(int r, const double* __restrict__ Binv, const double* res, double* z) {
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    const int j = i / 12, a = i % 12;
+    const double* B = Binv + (int64_t)j * 144 + a * 12;
+    double s = 0.0;
+    for (int k = 0; k < 12; ++k) s += B[k] * res[12 * j + k];
+    z[i] = s;
+  }
+}
+
+__device__ __forceinline__ double block_dot(const double* a, const double* b, int r, double* sh) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) s += a[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];  // same order in every thread
+  return t;
+}
+
+// init: q = 0, res = b, z = B^{-1} res, p = z (and its solve-precision copy)
+template <typename VT>
+__global__ void __launch_bounds__(256) k_sms_init(int r, const VT* __restrict__ b, const double* __restrict__ Binv,
+                                                  double rtol, int max_iter, double* __restrict__ q,
+                                                  double* __restrict__ res, double* __restrict__ z,
+                                                  double* __restrict__ p, VT* __restrict__ pv, SmsCg* __restrict__ C,
+                                                  PcgScalars* __restrict__ S) {
+  __shared__ double sh[8];
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    q[i] = 0.0;
+    res[i] = (double)b[i];
+  }
+  __syncthreads();
+  sms_precond(r, Binv, res, z);
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    p[i] = z[i];
+    pv[i] = (VT)z[i];
+  }
+  const double rz = block_dot(res, z, r, sh);
+  const double bb = block_dot(res, res, r, sh);
+  if (threadIdx.x == 0) {
+    C->rz = rz;
+    C->bb = bb;
+    C->tol2 = rtol * rtol * bb;
+    C->iter = 0;
+    C->max_iter = max_iter;
+    C->done = (bb == 0.0) ? 1 : (!(rz > 0.0) || !isfinite(rz) ? 3 : 0);
+    S->done = C->done;  // the product kernels skip work once the solve is done
+  }
+}
+
+template <typename VT>
+__global__ void k_cast_coarse(int r, const double* __restrict__ a, VT* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < r) b[i] = (VT)a[i];
+}
+
+// one CG step once s = (U^T H U) p is in sn (solve precision)
+template <typename VT>
+__global__ void __launch_bounds__(256) k_sms_step(int r, const VT* __restrict__ sn, const double* __restrict__ Binv,
+                                                  double* __restrict__ q, double* __restrict__ res,
+                                                  double* __restrict__ z, double* __restrict__ p,
+                                                  VT* __restrict__ pv, SmsCg* __restrict__ C,
+                                                  PcgScalars* __restrict__ S) {
+  __shared__ double sh[8];
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_done = C->done;
+  __syncthreads();
+  if (s_done) return;
+  double ps = 0.0;  // p . (U^T H U) p
+  for (int i = threadIdx.x; i < r; i += blockDim.x) ps += p[i] * (double)sn[i];
+  for (int o = 16; o > 0; o >>= 1) ps += __shfl_xor_sync(0xffffffffu, ps, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = ps;
+  __syncthreads();
+  double pq = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pq += sh[w];
+  const double rz = C->rz;
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    if (threadIdx.x == 0) { C->done = 3; S->done = 3; }
+    return;
+  }
+  const double alpha = rz / pq;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    q[i] += alpha * p[i];
+    res[i] -= alpha * (double)sn[i];
+  }
+  __syncthreads();
+  const double rr = block_dot(res, res, r, sh);
+  sms_precond(r, Binv, res, z);
+  __syncthreads();
+  const double rzn = block_dot(res, z, r, sh);
+  const double beta = rzn / rz;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    const double pn = z[i] + beta * p[i];
+    p[i] = pn;
+    pv[i] = (VT)pn;
+  }
+  if (threadIdx.x == 0) {
+    C->rz = rzn;
+    C->iter += 1;
+    int d = 0;
+    if (!isfinite(rr)) d = 3;
+    else if (rr <= C->tol2) d = 1;
+    else if (!(rzn > 0.0)) d = 3;
+    else if (C->iter >= C->max_iter) d = 2;
+    C->done = d;
+    S->done = d;
+  }
+}
+
+template <typename VT>
+static mls_status sms_pcg_t(mls_ctx* ctx, const void* b, double rtol, int max_iter, int* iters) {
+  const int r = 12 * ctx->basis.m;
+  mls_status st;
+  if (!ctx->sms_buf) {
+    if ((st = dalloc(ctx, (void**)&ctx->sms_buf, sizeof(double) * (size_t)r * (4 + 12))) != MLS_OK) return st;
+    if ((st = dalloc(ctx, (void**)&ctx->sms_cg, sizeof(SmsCg) + sizeof(PcgScalars))) != MLS_OK) return st;
+  }
+  double* q = ctx->sms_buf;
+  double* res = q + r;
+  double* z = res + r;
+  double* p = z + r;
+  double* Binv = p + r;  // [m][144]
+  SmsCg* C = (SmsCg*)ctx->sms_cg;
+  PcgScalars* S = (PcgScalars*)((char*)ctx->sms_cg + sizeof(SmsCg));
+  { ++ctx->launches; k_block_jacobi12<<<(ctx->basis.m + 63) / 64, 64, 0, ctx->stream>>>(ctx->Acopy, r, Binv); }
+  VT* pv = (VT*)ctx->cvec2;
+  VT* sn = (VT*)ctx->cvec;
+  { ++ctx->launches; k_sms_init<VT><<<1, 256, 0, ctx->stream>>>(r, (const VT*)b, Binv, rtol, max_iter, q, res, z, p, pv, C, S); }
+  if ((st = cuda_check(ctx, cudaGetLastError(), "k_sms_init")) != MLS_OK) return st;
+  const BasisView BV = basis_view(ctx);
+  const dim3 rgrid(restrict_blocks(ctx->basis.nrchunk)), rblock(32 * kRestrictWarps);
+  const int chunk = 8;
+  SmsCg h{};
+  for (int it = 0; it < max_iter; it += chunk) {
+    for (int c = 0; c < chunk; ++c) {
+      // w = U p, y = H w, sn = U^T y = (U^T H U) p
+      { ++ctx->launches; k_prolong<VT><<<prolong_blocks(ctx->n), kBlock, 0, ctx->stream>>>(BV, pv, nullptr, nullptr, nullptr,
+                                                                                   VT(0), (Vec4<VT>*)ctx->vp, S); }
+      if ((st = launch_spmv(ctx, ctx->vp, ctx->vq)) != MLS_OK) return st;
+      { ++ctx->launches; k_restrict<VT><<<rgrid, rblock, 0, ctx->stream>>>(BV, (const Vec4<VT>*)ctx->vq, sn, S); }
+      { ++ctx->launches; k_sms_step<VT><<<1, 256, 0, ctx->stream>>>(r, sn, Binv, q, res, z, p, pv, C, S); }
+    }
+    if ((st = cuda_check(ctx, cudaMemcpyAsync(&h, C, sizeof(SmsCg), cudaMemcpyDeviceToHost, ctx->stream), "sms state")) != MLS_OK)
+      return st;
+    if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sms sync")) != MLS_OK) return st;
+    if (h.done) break;
+  }
+  *iters = h.iter;
+  if (h.done == 3) return fail(ctx, MLS_ENONFINITE, "subspace PCG breakdown");
+  // the solution, in solve precision, into cvec
+  { ++ctx->launches; k_cast_coarse<VT><<<(r + 255) / 256, 256, 0, ctx->stream>>>(r, q, (VT*)ctx->cvec); }
+  return cuda_check(ctx, cudaGetLastError(), "sms solution");
+}
+
+// M = A T (A = U^T H U, row-major r x r; T the SMS coordinates of an affine
+// motion about o_a): for row i and component c, M[i][4c] = sum_j A[i][12j+4c]
+// and M[i][4c+l] = sum_j (A[i][12j+4c+l] + d_jl A[i][12j+4c]), d_j = o_j - o_a
+__global__ void k_affine_mt(const double* __restrict__ A, int r, int m, const double* __restrict__ origins,
+                            double o0, double o1, double o2, double* __restrict__ M) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 3 * r) return;
+  const int i = idx / 3, c = idx % 3;
+  const double* a = A + (int64_t)i * r;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int j = 0; j < m; ++j) {
+    const double a0 = a[12 * j + 4 * c];
+    s0 += a0;
+    s1 += a[12 * j + 4 * c + 1] + (origins[3 * j] - o0) * a0;
+    s2 += a[12 * j + 4 * c + 2] + (origins[3 * j + 1] - o1) * a0;
+    s3 += a[12 * j + 4 * c + 3] + (origins[3 * j + 2] - o2) * a0;
+  }
+  double* out = M + (int64_t)i * 12 + 4 * c;
+  out[0] = s0; out[1] = s1; out[2] = s2; out[3] = s3;
+}
+
+mls_status affine_operator(mls_ctx* ctx, const double om[3]) {
+  const int m = ctx->basis.m, r = 12 * m;
+  mls_status st;
+  if (!ctx->sms_m && (st = dalloc(ctx, (void**)&ctx->sms_m, sizeof(double) * (size_t)r * 12)) != MLS_OK) return st;
+  { ++ctx->launches; k_affine_mt<<<(3 * r + 127) / 128, 128, 0, ctx->stream>>>(ctx->Acopy, r, m, ctx->basis.origins,
+                                                                              om[0], om[1], om[2], ctx->sms_m); }
+  return cuda_check(ctx, cudaGetLastError(), "k_affine_mt");
+}
+
+// U^T H U into Ac and its copy Acopy, without a factorisation (the literal
+// subspace solve of direction 2 needs the operator's blocks, not a factor)
+mls_status build_coarse_unfactored(mls_ctx* ctx) {
+  if (!ctx->has_basis) return fail(ctx, MLS_EINVAL, "no basis uploaded");
+  if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "assemble H before building the coarse operator");
+  const int r = 12 * ctx->basis.m;
+  int tk = prof_begin(ctx, MLS_PROF_GALERKIN);
+  mls_status st;
+  if (ctx->cub_scale && (st = launch_assemble_cubature(ctx, ctx->xk)) != MLS_OK) return st;
+  if ((st = build_galerkin(ctx)) != MLS_OK) return st;
+  st = cuda_check(ctx, cudaMemcpyAsync(ctx->Acopy, ctx->Ac, sizeof(double) * r * r, cudaMemcpyDeviceToDevice,
+                                       ctx->stream), "A copy");
+  prof_end(ctx, tk);
+  ctx->galerkin_ready = (st == MLS_OK);
+  ctx->coarse_ready = false;
+  return st;
+}
+
+// (U^T H U) q = b (b: [r] coarse vector in solve precision) by Alg. 2's
+// subspace PCG to relative residual rtol; the operator's diagonal blocks come
+// from the Galerkin product's unfactored copy (Acopy).  The solution lands in
+// cvec (solve precision); the full-space vectors vp and vq are scratch.
+mls_status sms_pcg(mls_ctx* ctx, const void* b, double rtol, int max_iter, int* iters) {
+  return ctx->opt.precision == MLS_FP64 ? sms_pcg_t<double>(ctx, b, rtol, max_iter, iters)
+                                        : sms_pcg_t<float>(ctx, b, rtol, max_iter, iters);
 }
 
 // ---- damping of the block-Jacobi smoother ------------------------------------------------

@@ -290,8 +290,13 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_post_smooth_rz(SellView 
   if (row >= 0) rv = r[row];
   // a row's first slot is its diagonal block: the row's own z2 is gathered
   const Vec4<VT> zv = gx.x[0];
-  __shared__ int s_done;
-  if (threadIdx.x == 0) s_done = S->done;
+  __shared__ int s_done, s_e;
+  if (threadIdx.x == 0) {
+    const int d = __ldcg(&S->done);
+    const double rzp = __ldcg(&S->rzv[it & 1]);
+    s_done = d;
+    s_e = fix_exponent(rzp);
+  }
   __syncthreads();
   if (s_done) return;
   double acc[1] = {0.0};
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_post_smooth_rz(SellView 
   if (!first) {
     __shared__ double sh[1][32];
     block_sum<1>(acc, sh);
-    if (threadIdx.x == 0) fix_add(fix_slot(fix, FX_RZ, (it + 1) & 1), acc[0], fix_exponent(S->rzv[it & 1]));
+    if (threadIdx.x == 0) fix_add(fix_slot(fix, FX_RZ, (it + 1) & 1), acc[0], s_e);
     return;
   }
   if (grid_sum<1>(acc, gr, RS_PCG_RZ) && threadIdx.x == 0) {
@@ -381,9 +386,9 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_pcg_spmv(SellView A, con
 __global__ void k_pcg_check(int it, unsigned long long* __restrict__ fix, PcgScalars* __restrict__ S) {
   chain_wait();
   chain_release();
-  if (threadIdx.x != 0 || S->done) return;
-  const PcgHeadRaw raw = pcg_head_load(fix, it);
-  pcg_head_publish<double>(S, fix, it, pcg_head<double>(S, raw, it));
+  const PcgOpen o = pcg_open_load_warp(fix, S, it);  // one warp
+  if (threadIdx.x != 0 || o.done) return;
+  pcg_head_publish<double>(S, fix, it, pcg_head_open<double>(o, it));
 }
 
 // x += alpha p; r -= alpha q; then by mode: 1 = block Jacobi z = D^{-1} r with
@@ -406,25 +411,44 @@ __global__ void __launch_bounds__(kUpdBlock) k_pcg_update(int n, Vec4<VT>* __res
   Vec4<VT> pv{}, qv{}, xv{}, rv{};
   if (row < n) { pv = p[row]; qv = q[row]; xv = x[row]; rv = r[row]; }
   __shared__ VT s_alpha;
-  __shared__ int s_go;
-  if (threadIdx.x == 0) {
-    int go = 0;
-    VT alpha = VT(0);
-    if (!S->done) {  // block 0 may set it on breakdown: read once per block
-      const double rz = S->rzv[it & 1];
-      bool bad;
-      const double pq = fix_value(fix_load(fix_slot(fix, FX_PQ, it & 1)), fix_exponent(rz), bad);
-      go = !bad && dbl_positive(pq);
-      if (go) alpha = ratio<VT>(rz, pq);
-      if (blockIdx.x == 0) {
-        S->pq = pq;
-        if (!go) S->done = 3;  // breakdown: H or the preconditioner is not positive definite
-        fix_clear(fix_slot(fix, FX_RR, it & 1));
-        fix_clear(fix_slot(fix, FX_RZ, it & 1));
+  __shared__ int s_go, s_erz, s_err;
+  if (threadIdx.x < 32) {
+    // lanes 0-4: the p.q slot, lane 5: the stop flag, lanes 6-7: rz_it and
+    // rr_it (the scale estimates of the sums this kernel adds to), in one
+    // round trip
+    const int lane = threadIdx.x;
+    const unsigned long long* pqs = fix_slot(fix, FX_PQ, it & 1);
+    unsigned long long w = 0ull;
+    if (lane < 5) w = __ldcg(pqs + lane * kFixStride);
+    else if (lane == 5) w = (unsigned long long)(unsigned)__ldcg(&S->done);
+    else if (lane == 6) w = (unsigned long long)__double_as_longlong(__ldcg(&S->rzv[it & 1]));
+    else if (lane == 7) w = (unsigned long long)__double_as_longlong(__ldcg(&S->rrv[it & 1]));
+    FixRaw pqr;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) pqr.w[k] = __shfl_sync(0xffffffffu, w, k);
+    const int done0 = (int)__shfl_sync(0xffffffffu, w, 5);
+    const double rz = __longlong_as_double((long long)__shfl_sync(0xffffffffu, w, 6));
+    const double rr = __longlong_as_double((long long)__shfl_sync(0xffffffffu, w, 7));
+    if (threadIdx.x == 0) {
+      int go = 0;
+      VT alpha = VT(0);
+      if (!done0) {  // block 0 may set it on breakdown: read once per block
+        bool bad;
+        const double pq = fix_value(pqr, fix_exponent(rz), bad);
+        go = !bad && dbl_positive(pq);
+        if (go) alpha = ratio<VT>(rz, pq);
+        if (blockIdx.x == 0) {
+          S->pq = pq;
+          if (!go) S->done = 3;  // breakdown: H or the preconditioner is not positive definite
+          fix_clear(fix_slot(fix, FX_RR, it & 1));
+          fix_clear(fix_slot(fix, FX_RZ, it & 1));
+        }
       }
+      s_go = go;
+      s_alpha = alpha;
+      s_erz = fix_exponent(rz);
+      s_err = fix_exponent(rr);
     }
-    s_go = go;
-    s_alpha = alpha;
   }
   __syncthreads();
   if (!s_go) return;
@@ -447,8 +471,8 @@ __global__ void __launch_bounds__(kUpdBlock) k_pcg_update(int n, Vec4<VT>* __res
   __shared__ double sh[2][32];
   block_sum<2>(acc, sh);
   if (threadIdx.x == 0) {
-    fix_add(fix_slot(fix, FX_RR, (it + 1) & 1), acc[0], fix_exponent(S->rrv[it & 1]));
-    if (jacobi == 1) fix_add(fix_slot(fix, FX_RZ, (it + 1) & 1), acc[1], fix_exponent(S->rzv[it & 1]));
+    fix_add(fix_slot(fix, FX_RR, (it + 1) & 1), acc[0], s_err);
+    if (jacobi == 1) fix_add(fix_slot(fix, FX_RZ, (it + 1) & 1), acc[1], s_erz);
   }
 }
 

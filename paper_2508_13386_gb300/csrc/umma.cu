@@ -122,10 +122,21 @@ __global__ void __launch_bounds__(128, 1) k_gemm_umma(const __grid_constant__ CU
         if (m < M) {
           double* arow = ep.acc64 + (int64_t)m * ep.ld64;
           const int em = ep.ea[m] - ep.ebias;
+          const unsigned flip = ep.sign < 0.0 ? 0x80000000u : 0u;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int n = n0 + c0 + j;
-            if (n < N && (!ep.lower || n <= m)) arow[n] += ep.sign * ldexp((double)v[j], em + ep.eb[n]);
+            const unsigned fb = __float_as_uint(v[j]) ^ flip;
+            if (n < N && (!ep.lower || n <= m) && (fb & 0x7fffffffu)) {
+              // sign x 2^e x v as a double built from v's bits with integer
+              // instructions (v is an integer below 2^24, a normal float;
+              // float64 instructions issue at 1/64 rate here), then one add
+              const int ex = (int)((fb >> 23) & 0xffu) - 127 + 1023 + em + ep.eb[n];
+              const unsigned long long db = ((unsigned long long)(fb >> 31) << 63) |
+                                            ((unsigned long long)(ex < 1 ? 0 : (ex > 2046 ? 2047 : ex)) << 52) |
+                                            ((unsigned long long)(fb & 0x7fffffu) << 29);
+              arow[n] += __longlong_as_double((long long)db);
+            }
           }
         }
         continue;

@@ -155,3 +155,27 @@ def test_heat_kmeans_gives_a_valid_partition():
     assert all(labels[c] == i for i, c in enumerate(centers))
     with pytest.raises(ValueError):
         basis.kmeans_partition(s.X, s.tets, s.E, 6, distance="euclid")
+
+
+def test_refinement_cg_iterations_counts_edge_hops():
+    """Sec. 3.7.2's count: hops from the handle vertex to the farthest vertex
+    of its partition through the partition's tets, averaged, binned to 20
+    or 40.  On the Kuhn split of a grid a hop moves by any vector of 0/1
+    components (or its negative) along the split diagonal, so from the
+    centre (2,2,2) of a 4^3-voxel block the farthest vertices, e.g.
+    (4,0,0), are 2 + 2 = 4 hops away; along an 80-voxel bar from one end
+    the far end is 80 hops away."""
+    from paper_2508_13386_gb300 import basis
+    cube = synth.kuhn_voxel_mesh(np.ones((4, 4, 4), bool))
+    centre = int(np.argmin(((cube.X - 0.5 * cube.X.max(axis=0)) ** 2).sum(1)))
+    mean, hops, n_cg = basis.refinement_cg_iterations(cube.tets, np.zeros(len(cube.tets), int), [centre])
+    assert hops == [4] and mean == 4.0 and n_cg == 20
+    bar = synth.kuhn_voxel_mesh(np.ones((80, 1, 1), bool))
+    end = int(np.argmin((bar.X ** 2).sum(1)))
+    mean, hops, n_cg = basis.refinement_cg_iterations(bar.tets, np.zeros(len(bar.tets), int), [end])
+    assert hops == [80] and n_cg == 40
+    # two partitions: the mean of their maxima
+    half = (bar.X[bar.tets].mean(axis=1)[:, 0] > bar.X[:, 0].max() / 2).astype(int)
+    mid = int(np.argmin(((bar.X - [bar.X[:, 0].max() / 2, 0, 0]) ** 2).sum(1)))
+    mean, hops, _ = basis.refinement_cg_iterations(bar.tets, half, [end, mid])
+    assert hops == [40, 40] and mean == 40.0

@@ -46,10 +46,47 @@ def test_spmv_bytes_scale_with_the_matrix_and_vectors():
 
 
 def test_cpu_sample_on_a_small_scene():
+    """The oracle sample: one full Newton iteration from the given state
+    (threaded element loops, PCG to 1e-13, line search), scaled by the
+    Newton count; a capped solve scales to a known iteration count."""
     s = synth.tiny_scene(3, 2, 2, seed=2, contact=True, pinned=False)
-    rate, desc, spent = bench.cpu_sample(s, newton_iters=3, pcg_iters_per_newton=40, cg_sample=10)
-    assert rate > 0 and np.isfinite(rate) and spent > 0
-    assert "3 Newton" in desc and "40 CG" in desc
-    # more work per step: a lower rate
-    rate2, _, _ = bench.cpu_sample(s, newton_iters=30, pcg_iters_per_newton=400, cg_sample=10)
-    assert rate2 < rate
+    res = bench.cpu_sample(s, s.x0, s.v0, newton_iters=3, threads=2)
+    assert res["value"] > 0 and np.isfinite(res["value"]) and res["spent_s"] > 0
+    assert res["cores"] == 2 and res["pcg_iters"] > 0
+    assert "3 such iterations" in res["sample"] and "2 threads" in res["sample"]
+    assert res["value"] == pytest.approx(1.0 / (3 * res["newton_iteration_s"]))
+    # more Newton iterations per step: a lower rate
+    res2 = bench.cpu_sample(s, s.x0, s.v0, newton_iters=30, threads=1)
+    assert res2["value"] < res["value"]
+    # a capped solve is scaled to the known count
+    res3 = bench.cpu_sample(s, s.x0, s.v0, newton_iters=3, threads=1, pcg_iters_known=res["pcg_iters"], pcg_cap=2)
+    assert res3["pcg_iters"] == res["pcg_iters"]
+
+
+def test_threaded_oracle_evaluation_is_bitwise_serial():
+    """The oracle's element loops on several threads (contiguous tet chunks,
+    concatenated in order) give the serial results bit for bit."""
+    from oracle import ip
+    s = synth.tiny_scene(6, 4, 3, seed=5, contact=True, pinned=False)
+    x = ip.Problem(s).x_tilde + 1e-3 * np.random.default_rng(1).normal(size=s.X.shape)
+    x[:, 2] = np.maximum(x[:, 2], 2e-4)
+    p1, p4 = ip.Problem(s), ip.Problem(s, threads=4)
+    assert p1.energy(x) == p4.energy(x)
+    assert np.array_equal(p1.gradient(x), p4.gradient(x))
+    assert (p1.hessian(x) != p4.hessian(x)).nnz == 0
+
+
+def test_oracle_error_estimate_is_zero_at_the_minimiser_and_scales():
+    """The Newton-correction estimate of a step's error: ~0 at the oracle's
+    minimiser, and for x* + e it recovers |e| / |x* + e - x^t| to the
+    linearisation."""
+    from oracle import ip, newton
+    s = synth.tiny_scene(3, 2, 2, seed=4, pinned=True)
+    p = ip.Problem(s)
+    xs, _ = newton.timestep(p)
+    assert bench.oracle_error_estimate(s, s.x0, s.v0, xs, threads=1) < 1e-9
+    e = np.zeros_like(xs)
+    e[~p.pinned] = 1e-6 * np.random.default_rng(0).normal(size=(int((~p.pinned).sum()), 3))
+    est = bench.oracle_error_estimate(s, s.x0, s.v0, xs + e, threads=1)
+    ref = np.linalg.norm(e) / np.linalg.norm(xs + e - s.x0)
+    assert est == pytest.approx(ref, rel=2e-2)

@@ -75,3 +75,101 @@ def test_paper_direction_first_iteration_matches_oracle():
     ds, df = subspace.paper_direction(p.hessian(x0), p.gradient(x0), U, 20)
     dx_o = (x0 + (ds + df).reshape(-1, 3)) - s.x0
     assert np.linalg.norm(host(dx) - dx_o) <= 1e-9 * np.linalg.norm(dx_o)
+
+
+def _literal_problem():
+    s = synth.tiny_scene(6, 3, 3, seed=23, pinned=False, E_range=(1e5, 1e7))
+    s.gravity = (0.0, 0.0, -9.81)
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=6, k=3, seed=9)
+    return s, (origins, vrow, handle, phi)
+
+
+def test_literal_subspace_direction_matches_oracle_alg2():
+    """direction 2 (Alg. 2 as printed): the affine level on its 12 x 12
+    operator, then block-Jacobi PCG on the SMS level with matrix-free
+    products, to the paper's relative residual 1e-4, and no refinement: the
+    first Newton step is the subspace direction, which matches the oracle's
+    subspace_direction_literal from the same iterate (the same PCG from the
+    same start; 1e-3 covers a stop one iteration apart), with the same
+    iteration count within one."""
+    from oracle import subspace
+    s, bas = _literal_problem()
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", direction="paper_literal",
+                        refine_iters=0, paper_tol=1e-12, max_newton=1, sub_rtol=1e-4)
+    solver.upload_basis(*bas)
+    dx, st = solver.newton_step(dev(s.x0), dev(s.v0), s.dt, allow_notconv=True)
+    assert st["line_search_trials"] == 1
+    p = ip.Problem(s)
+    x0 = newton.initial_guess(p)
+    Us = subspace.lbs_basis_matrix(s.X, *bas)
+    _, Ua = subspace.affine_basis_matrix(s.X, mass=p.mass)
+    ds, (ia, isms) = subspace.subspace_direction_literal(p.hessian(x0), p.gradient(x0), Ua, Us, rtol=1e-4)
+    dx_o = (x0 + ds.reshape(-1, 3)) - s.x0
+    assert np.linalg.norm(host(dx) - dx_o) <= 1e-3 * np.linalg.norm(dx_o)
+    assert abs(st["subspace_iters"] - (1 + isms)) <= 1
+
+
+def test_literal_subspace_direction_solved_tightly_is_the_galerkin_direction():
+    """With the subspace PCG solved to 1e-12 the literal direction is the
+    exact Galerkin direction (the affine space lies in the SMS space), so
+    with 20 refinement iterations the first step matches the oracle's
+    paper_direction, as direction 1 does."""
+    from oracle import subspace
+    s, bas = _literal_problem()
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", direction="paper_literal",
+                        refine_iters=20, paper_tol=1e-12, max_newton=1, sub_rtol=1e-12)
+    solver.upload_basis(*bas)
+    dx, st = solver.newton_step(dev(s.x0), dev(s.v0), s.dt, allow_notconv=True)
+    assert st["line_search_trials"] == 1 and st["subspace_iters"] > 1
+    p = ip.Problem(s)
+    x0 = newton.initial_guess(p)
+    U = subspace.lbs_basis_matrix(s.X, *bas)
+    ds, df = subspace.paper_direction(p.hessian(x0), p.gradient(x0), U, 20)
+    dx_o = (x0 + (ds + df).reshape(-1, 3)) - s.x0
+    assert np.linalg.norm(host(dx) - dx_o) <= 1e-7 * np.linalg.norm(dx_o)
+
+
+def test_literal_direction_converges_to_the_minimiser():
+    """Many refinement iterations and vanishing tolerances: a Newton method,
+    which reaches the oracle's minimiser."""
+    s = synth.tiny_scene(8, 3, 3, seed=17, E_range=(1e5, 1e9), pinned=False)
+    x_o, _ = newton.timestep(ip.Problem(s))
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=6, k=3, seed=5)
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", direction="paper_literal",
+                        refine_iters=400, paper_tol=1e-13, max_newton=60, sub_rtol=1e-10)
+    solver.upload_basis(origins, vrow, handle, phi)
+    dx, st = solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    assert st["status"] == 0
+    assert rel_disp_error(s.x0 + host(dx), x_o, s.x0) <= 1e-8
+
+
+def test_hessian_lag_first_iteration_equals_the_fresh_hessian():
+    """H_lag (Sec. 3.7.2) is refreshed at the first Newton iteration of a step,
+    so one iteration with the lag solves with the same operator as without
+    it: the same step to rounding, and one refresh reported."""
+    s, bas = _literal_problem()
+    out = []
+    for lag in (False, True):
+        solver = solver_for(s, precision="fp64", preconditioner="two_level", direction="paper", refine_iters=20,
+                            paper_tol=1e-12, max_newton=1, hessian_lag=lag)
+        solver.upload_basis(*bas)
+        dx, st = solver.newton_step(dev(s.x0), dev(s.v0), s.dt, allow_notconv=True)
+        out.append((host(dx), st))
+    (d0, s0), (d1, s1) = out
+    assert s0["hessian_refreshes"] == 0 and s1["hessian_refreshes"] == 1
+    assert np.linalg.norm(d1 - d0) <= 1e-13 * np.linalg.norm(d0)
+
+
+def test_hessian_lag_step_reaches_the_minimiser():
+    """With the lagged elastic Hessian in the refinement (contact blocks fresh)
+    and tight tolerances the Newton loop still reaches the oracle's
+    minimiser: the lag changes the directions, not the fixed point."""
+    s = synth.tiny_scene(6, 4, 3, seed=8, contact=True, pinned=False, E_range=(1e5, 1e7))
+    x_o, _ = newton.timestep(ip.Problem(s))
+    origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=6, k=3, seed=5)
+    solver = solver_for(s, precision="fp64", preconditioner="two_level", direction="paper_literal",
+                        refine_iters=400, paper_tol=1e-13, max_newton=80, sub_rtol=1e-10, hessian_lag=True)
+    solver.upload_basis(origins, vrow, handle, phi)
+    dx, st = solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    assert st["status"] == 0 and st["hessian_refreshes"] >= 1
+    assert rel_disp_error(s.x0 + host(dx), x_o, s.x0) <= 1e-8
