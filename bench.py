@@ -213,6 +213,11 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # nvidia-smi's start-up (driver and NVML initialisation) stalls the
+            # GPU host API for up to ~0.1 s: let it finish before timing starts
+            t_end = time.perf_counter() + 10.0
+            while not self.samples and time.perf_counter() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self

@@ -166,6 +166,7 @@ typedef struct mls_stats {
                               Newton iterations (the affine level counts one per
                               Newton iteration) */
   int hessian_refreshes;   /* hessian_lag: refreshes of H_lag in the step */
+  int contact_pairs;       /* mesh-mesh pairs within dhat at the last assembly (mls_set_bodies) */
 } mls_stats;
 
 typedef struct mls_ctx mls_ctx;
@@ -260,6 +261,29 @@ mls_status mls_set_forces(mls_ctx* ctx, const double* gravity, int contact,
  * off (call mls_set_forces with contact first; turning contact off later
  * suspends the term). */
 mls_status mls_set_friction(mls_ctx* ctx, double mu, double eps_v);
+
+/* Mesh-mesh contact (Eq. IP term B, Sec. 3.1, which takes IPC's barrier on
+ * surface primitives without writing it out; the CCD filter of Sec. 3.9).
+ * body [n_verts] HOST labels each vertex with its body (>= 0).  The surface
+ * is the set of faces that belong to one tet only, their edges and their
+ * vertices.  Every point-triangle pair (surface vertex, face) and edge-edge
+ * pair of different bodies at distance d < dhat adds
+ *     kappa b(d),  b(d) = -(d - dhat)^2 ln(d / dhat),
+ * to E with the same h^2 factor as the elastic energy; d is the distance of
+ * the closest points of the closed primitives.  The Hessian of each pair is
+ * projected to the positive semi-definite cone (12 x 12 per pair).  The line
+ * search's first step is also bounded by conservative advancement, which
+ * keeps every pair of different bodies at >= 0.1 of its distance, and the
+ * start iterate is x^t + a (x_tilde - x^t) with a that bound.
+ * Blocks of H between vertices of different bodies go to spare slots of the
+ * surface-vertex rows: spare slots per row (0 = 32).  Call after
+ * mls_upload_mesh and before mls_upload_basis / mls_upload_cubature; it
+ * rebuilds H's sparsity.  body = NULL turns mesh-mesh contact off.
+ * MLS_EINVAL for a negative label, dhat <= 0 or kappa <= 0, spare < 0, no
+ * mesh, or an uploaded basis or cubature.  A timestep fails with MLS_ENOMEM
+ * when a vertex touches more vertices of other bodies than its spare slots
+ * hold. */
+mls_status mls_set_bodies(mls_ctx* ctx, const int32_t* body, double dhat, double kappa, int32_t spare);
 
 /* One implicit-Euler timestep.  DEVICE pointers:
  *   x [n][3] positions x^t, v [n][3] velocities v^t (read only),
@@ -382,6 +406,29 @@ mls_status mls_profile_enable(mls_ctx* ctx, uint32_t mask);
 /* Read accumulated totals: ms[MLS_PROF_COUNT] milliseconds and
  * launches[MLS_PROF_COUNT] launch counts (HOST arrays, either nullable). */
 mls_status mls_profile_read(mls_ctx* ctx, double* ms, int64_t* launches);
+
+/* Mesh-mesh contact pairs (stage entry point, for testing): the broad and
+ * narrow phase over x [n][3] (DEVICE) with d = NULL (pairs of different
+ * bodies at distance < dhat), or over the segment x -> x + d (d DEVICE
+ * [n][3]: every pair whose boxes, grown by dhat, meet on the segment, the
+ * candidates of the CCD filter and the line search).  Writes up to cap
+ * pairs each as HOST int32 [cap][4]: point-triangle (v, a, b, c) and
+ * edge-edge (p0, p1, q0, q1) vertex indices; *npt and *nee receive the full
+ * counts.  MLS_EINVAL without mls_set_bodies. */
+mls_status mls_contact_pairs(mls_ctx* ctx, const double* x, const double* d, int64_t cap, int32_t* pt, int64_t* npt,
+                             int32_t* ee, int64_t* nee);
+
+/* Distance derivatives of n primitive pairs (for testing; no context).
+ * DEVICE arrays: kind [n] (0 point-triangle with X = (p, a, b, c), 1
+ * edge-edge with X = (p0, p1, q0, q1)), X [n][4][3]; outputs dist [n],
+ * grad [n][12] and hess_d [n][12][12] of the distance over the 12 stacked
+ * coordinates (the formula of the closest feature: plane, line or point),
+ * and hess_b [n][12][12] = kappa (b''(d) grad grad^T + b'(d) hess_d)
+ * projected to the positive semi-definite cone.  Runs on the legacy
+ * default stream and waits.  MLS_EINVAL for n < 0, null arrays, dhat <= 0 or
+ * kappa <= 0; MLS_ECUDA on a launch error. */
+mls_status mls_contact_pair_derivatives(const int32_t* kind, const double* X, int32_t n, double kappa, double dhat,
+                                        double* dist, double* grad, double* hess_d, double* hess_b);
 
 /* ---- Dense bf16 product on the tensor cores ------------------------------
  * Not in the paper: the matrix product under the learned warm start's

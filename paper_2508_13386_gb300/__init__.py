@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 
-__all__ = ["Solver", "MLP", "MLSError", "lib"]
+__all__ = ["Solver", "MLP", "MLSError", "lib", "contact_pair_derivatives"]
 
 lib = None
 
@@ -358,6 +358,55 @@ class Solver:
         a = C.c_double()
         self._check(self._l.mls_ccd_bound(self._ctx, _dev(x, (self.n, 3)), _dev(d, (self.n, 3)), C.byref(a)))
         return a.value
+
+    # ---- mesh-mesh contact ---------------------------------------------------------
+    def set_bodies(self, body, dhat=1e-3, kappa=1e5, spare=0):
+        """Mesh-mesh contact between the bodies ``body`` [n] labels (None: off);
+        see mls_set_bodies.  Call after upload_mesh, before upload_basis."""
+        if body is None:
+            self._check(self._l.mls_set_bodies(self._ctx, None, float(dhat), float(kappa), 0))
+            return
+        b, pb = _host(body, np.int32)
+        if b.shape != (self.n,):
+            raise ValueError(f"expected {self.n} body labels")
+        self._check(self._l.mls_set_bodies(self._ctx, pb, float(dhat), float(kappa), int(spare)))
+
+    def contact_pairs(self, x, d=None):
+        """(pt [k, 4], ee [k, 4]) vertex indices of the contact pairs at x
+        (d None: distance < dhat) or the candidates over x -> x + d."""
+        npt, nee = C.c_int64(), C.c_int64()
+        dd = None if d is None else _dev(d, (self.n, 3))
+        self._check(self._l.mls_contact_pairs(self._ctx, _dev(x, (self.n, 3)), dd, 0, None, C.byref(npt), None,
+                                              C.byref(nee)))
+        cap = max(npt.value, nee.value, 1)
+        pt = np.zeros((cap, 4), np.int32)
+        ee = np.zeros((cap, 4), np.int32)
+        self._check(self._l.mls_contact_pairs(self._ctx, _dev(x, (self.n, 3)), dd, int(cap),
+                                              pt.ctypes.data_as(C.c_void_p), C.byref(npt),
+                                              ee.ctypes.data_as(C.c_void_p), C.byref(nee)))
+        return pt[:npt.value], ee[:nee.value]
+
+
+def contact_pair_derivatives(kind, X, kappa, dhat):
+    """Per-pair distance derivatives on the GPU (mls_contact_pair_derivatives):
+    kind [P] (0 point-triangle, 1 edge-edge), X [P, 4, 3] -> (d [P],
+    grad d [P, 12], Hess d [P, 12, 12], projected barrier Hessian [P, 12, 12])."""
+    import torch
+    kind = torch.as_tensor(np.asarray(kind, np.int32), device="cuda:0").contiguous()
+    X = torch.as_tensor(np.asarray(X, np.float64), device="cuda:0").contiguous()
+    P = int(kind.shape[0])
+    d = torch.empty(P, dtype=torch.float64, device="cuda:0")
+    g = torch.empty((P, 12), dtype=torch.float64, device="cuda:0")
+    Hd = torch.empty((P, 12, 12), dtype=torch.float64, device="cuda:0")
+    Hb = torch.empty((P, 12, 12), dtype=torch.float64, device="cuda:0")
+    torch.cuda.synchronize()
+    st = _get_lib().mls_contact_pair_derivatives(C.c_void_p(kind.data_ptr()), C.c_void_p(X.data_ptr()), P,
+                                                float(kappa), float(dhat), C.c_void_p(d.data_ptr()),
+                                                C.c_void_p(g.data_ptr()), C.c_void_p(Hd.data_ptr()),
+                                                C.c_void_p(Hb.data_ptr()))
+    if st != 0:
+        raise MLSError(st, "contact_pair_derivatives")
+    return d.cpu().numpy(), g.cpu().numpy(), Hd.cpu().numpy(), Hb.cpu().numpy()
 
 
 class Batch:

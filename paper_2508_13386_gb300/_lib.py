@@ -62,6 +62,7 @@ class Stats(C.Structure):
         ("coarse_fallbacks", C.c_int),
         ("subspace_iters", C.c_int),
         ("hessian_refreshes", C.c_int),
+        ("contact_pairs", C.c_int),
     ]
 
     def as_dict(self):
@@ -102,6 +103,9 @@ SIGNATURES = {
     "mls_coarse_shift": [_P, _P],
     "mls_energy": [_P, _P, _P, _D, C.POINTER(_D), C.POINTER(_I)],
     "mls_ccd_bound": [_P, _P, _P, C.POINTER(_D)],
+    "mls_set_bodies": [_P, _P, _D, _D, _I32],
+    "mls_contact_pairs": [_P, _P, _P, C.c_int64, _P, C.POINTER(C.c_int64), _P, C.POINTER(C.c_int64)],
+    "mls_contact_pair_derivatives": [_P, _P, _I32, _D, _D, _P, _P, _P, _P],
     "mls_profile_enable": [_P, C.c_uint32],
     "mls_profile_read": [_P, _P, _P],
     "mls_elastic_energy_noalloc": [_I32, _I32, _P, _P, _P, _P, _P, _P, _P, _P],

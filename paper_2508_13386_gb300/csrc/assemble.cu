@@ -28,6 +28,7 @@ struct AsmIn {
   int contact;
   const Vec4d* __restrict__ xt;  // x^t, the friction lag state
   double fmu, feps;              // friction coefficient (0: none) and mollifier width
+  const Vec4d* __restrict__ cgrad;  // mesh-mesh barrier gradient per vertex (nullable)
 };
 
 __device__ __forceinline__ double bar_db(double d, double dhat) {
@@ -77,6 +78,10 @@ __global__ void __launch_bounds__(kBlock) k_gather_grad(AsmIn in, const Vec4d* _
             sx += f * u[0]; sy += f * u[1]; sz += f * u[2];
           }
         }
+      }
+      if (in.cgrad) {
+        const Vec4d cg = in.cgrad[v];
+        sx += cg.x; sy += cg.y; sz += cg.z;
       }
       const Vec4d xt = in.xtil[v];
       const double m = in.mass[v];
@@ -354,11 +359,29 @@ __global__ void k_add_solve(int n, Vec4<VT>* __restrict__ y, const Vec4<VT>* __r
   }
 }
 
+__global__ void k_diff_state(int n, const Vec4d* __restrict__ a, const Vec4d* __restrict__ b, Vec4d* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const Vec4d p = a[i], q = b[i];
+    out[i] = Vec4d{p.x - q.x, p.y - q.y, p.z - q.z, 0.0};
+  }
+}
+
+__global__ void k_xpay_state(int n, const Vec4d* __restrict__ x, const Vec4d* __restrict__ d, double alpha,
+                             Vec4d* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const Vec4d p = x[i], q = d[i];
+    out[i] = Vec4d{p.x + alpha * q.x, p.y + alpha * q.y, p.z + alpha * q.z, 0.0};
+  }
+}
+
 // ---- launchers -----------------------------------------------------------------------
 static AsmIn asm_in(mls_ctx* ctx) {
   return AsmIn{ctx->n, ctx->t, ctx->mass, ctx->pinned, ctx->xtil, ctx->vt_ptr, ctx->vt_code, ctx->egrad,
                ctx->h * ctx->h, ctx->kappa, ctx->dhat, ctx->po, ctx->pn[0], ctx->pn[1], ctx->pn[2],
-               ctx->contact, ctx->xt, ctx->contact ? ctx->fric_mu : 0.0, ctx->fric_eps_v * ctx->h_step};
+               ctx->contact, ctx->xt, ctx->contact ? ctx->fric_mu : 0.0, ctx->fric_eps_v * ctx->h_step,
+               ctx->cs.on ? ctx->cs.cgrad : nullptr};
 }
 
 static inline int nblk(int64_t n, int b = kBlock) { return (int)((n + b - 1) / b); }
@@ -426,16 +449,21 @@ mls_status launch_assemble(mls_ctx* ctx, const Vec4d* x) {
 
 mls_status launch_assemble_cubature(mls_ctx* ctx, const Vec4d* x) {
   if (!ctx->cub_scale || !ctx->hval_cub) return fail(ctx, MLS_EINVAL, "no cubature uploaded");
-  return assemble_into(ctx, x, ctx->ehess, ctx->hval_cub, nullptr, ctx->cub_scale);
+  mls_status st = assemble_into(ctx, x, ctx->ehess, ctx->hval_cub, nullptr, ctx->cub_scale);
+  if (st != MLS_OK) return st;
+  return contact_merge(ctx, ctx->hval_cub, nullptr, false);
 }
 
 // H_lag of the paper's refinement (Sec. 3.7.2): the element Hessians saved at
 // the last refresh with the mass and the contact and friction blocks of x
 mls_status launch_assemble_lagged(mls_ctx* ctx, const Vec4d* x) {
-  return assemble_into(ctx, x, ctx->ehess_lag, ctx->hval_lag, ctx->dinv_lag, nullptr);
+  mls_status st = assemble_into(ctx, x, ctx->ehess_lag, ctx->hval_lag, ctx->dinv_lag, nullptr);
+  if (st != MLS_OK) return st;
+  return contact_merge(ctx, ctx->hval_lag, ctx->dinv_lag, false);
 }
 
 mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, double dt) {
+  contact_invalidate(ctx);
   { ++ctx->launches; k_predictor<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, v, ctx->pinned, dt, ctx->grav[0],
                                                        ctx->grav[1], ctx->grav[2], ctx->xt, ctx->xtil,
                                                        ctx->xk); }
@@ -444,6 +472,7 @@ mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, doub
 
 mls_status launch_predictor_bdf2(mls_ctx* ctx, const double* x, const double* v, const double* x_prev,
                                  const double* v_prev, double dt) {
+  contact_invalidate(ctx);
   { ++ctx->launches; k_predictor_bdf2<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(
         ctx->n, x, v, x_prev, v_prev, ctx->pinned, dt, ctx->grav[0], ctx->grav[1], ctx->grav[2], ctx->xt,
         ctx->xtil, ctx->xk); }
@@ -451,6 +480,7 @@ mls_status launch_predictor_bdf2(mls_ctx* ctx, const double* x, const double* v,
 }
 
 mls_status launch_pack(mls_ctx* ctx, const double* src, Vec4d* dst) {
+  contact_invalidate(ctx);
   { ++ctx->launches; k_pack<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, src, dst); }
   return cuda_check(ctx, cudaGetLastError(), "k_pack");
 }
@@ -466,8 +496,21 @@ mls_status launch_disp_out(mls_ctx* ctx, double* dx_out) {
 }
 
 mls_status launch_axpy_state(mls_ctx* ctx, Vec4d* x, const Vec4d* d, double alpha) {
+  contact_invalidate(ctx);
   { ++ctx->launches; k_axpy_state<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, d, alpha); }
   return cuda_check(ctx, cudaGetLastError(), "k_axpy_state");
+}
+
+mls_status launch_diff_state(mls_ctx* ctx, const Vec4d* a, const Vec4d* b, Vec4d* out) {
+  contact_invalidate(ctx);
+  { ++ctx->launches; k_diff_state<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, a, b, out); }
+  return cuda_check(ctx, cudaGetLastError(), "k_diff_state");
+}
+
+mls_status launch_xpay_state(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double alpha, Vec4d* out) {
+  contact_invalidate(ctx);
+  { ++ctx->launches; k_xpay_state<<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, x, d, alpha, out); }
+  return cuda_check(ctx, cudaGetLastError(), "k_xpay_state");
 }
 
 mls_status launch_to_solve(mls_ctx* ctx, const Vec4d* src, void* dst, double scale) {
@@ -487,6 +530,7 @@ mls_status launch_add_solve(mls_ctx* ctx, void* y, const void* x) {
 }
 
 mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst) {
+  contact_invalidate(ctx);
   if (ctx->opt.precision == MLS_FP64)
     { ++ctx->launches; k_from_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4d*)src, ctx->pinned, dst); }
   else
@@ -495,6 +539,7 @@ mls_status launch_from_solve(mls_ctx* ctx, const void* src, Vec4d* dst) {
 }
 
 mls_status launch_from_solve_raw(mls_ctx* ctx, const void* src, Vec4d* dst) {
+  contact_invalidate(ctx);
   if (ctx->opt.precision == MLS_FP64)
     { ++ctx->launches; k_from_solve<double><<<nblk(ctx->n), kBlock, 0, ctx->stream>>>(ctx->n, (const Vec4d*)src, nullptr, dst); }
   else

@@ -135,6 +135,98 @@ void prof_flush(mls_ctx* ctx) {
   ctx->prof_pending.clear();
 }
 
+// SELL-32 sparsity of H from the tet adjacency (diagonal block first, then
+// ascending columns), with spare[v] (nullable) empty slots after row v's
+// blocks, and the per-slot lists of element blocks that assembly sums.
+// Replaces the previous pattern arrays.
+mls_status build_pattern(mls_ctx* ctx, const std::vector<int>* spare) {
+  const int n = ctx->n, t = ctx->t;
+  const int* tets = ctx->h_tets.data();
+  std::vector<std::vector<int>> nbr(n);
+  for (int e = 0; e < t; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) nbr[tets[4 * e + a]].push_back(tets[4 * e + b]);
+  std::vector<int> row_len(n);
+  for (int v = 0; v < n; ++v) {
+    auto& L = nbr[v];
+    std::sort(L.begin(), L.end());
+    L.erase(std::unique(L.begin(), L.end()), L.end());
+    auto it = std::find(L.begin(), L.end(), v);
+    if (it == L.end()) L.insert(L.begin(), v);
+    else std::rotate(L.begin(), it, it + 1);
+    row_len[v] = (int)L.size();
+  }
+  const int n_slices = (n + kSlice - 1) / kSlice;
+  std::vector<int> slice_ptr(n_slices + 1, 0);
+  for (int s = 0; s < n_slices; ++s) {
+    int w = 0;
+    for (int v = s * kSlice; v < std::min(n, (s + 1) * kSlice); ++v)
+      w = std::max(w, row_len[v] + (spare ? (*spare)[v] : 0));
+    slice_ptr[s + 1] = slice_ptr[s] + w;
+  }
+  const int64_t n_groups = slice_ptr[n_slices];
+  const int64_t n_slots = n_groups * kSlice;
+  if (n_slots + 1 > INT32_MAX) return fail(ctx, MLS_EINVAL, "sparsity pattern of H too large");
+  std::vector<int> group_slice(n_groups), col(n_slots);
+  for (int s = 0; s < n_slices; ++s)
+    for (int g = slice_ptr[s]; g < slice_ptr[s + 1]; ++g) group_slice[g] = s;
+  int64_t nnzb = 0;
+  for (int v = 0; v < n; ++v) {
+    const int s = v / kSlice, lane = v % kSlice;
+    const int w = slice_ptr[s + 1] - slice_ptr[s];
+    for (int k = 0; k < w; ++k)
+      col[((int64_t)slice_ptr[s] + k) * kSlice + lane] = k < row_len[v] ? nbr[v][k] : v;
+    nnzb += row_len[v];
+  }
+  // element-block contributions per slot (CSR over slots)
+  std::vector<int> asm_cnt(n_slots + 1, 0);
+  std::vector<int64_t> code_slot(16 * (size_t)t);
+  for (int e = 0; e < t; ++e)
+    for (int a = 0; a < 4; ++a) {
+      const int v = tets[4 * e + a];
+      const auto& L = nbr[v];
+      const int s = v / kSlice, lane = v % kSlice;
+      for (int b = 0; b < 4; ++b) {
+        const int w = tets[4 * e + b];
+        const int k = (int)(std::find(L.begin(), L.end(), w) - L.begin());
+        const int64_t slot = ((int64_t)slice_ptr[s] + k) * kSlice + lane;
+        code_slot[16 * (size_t)e + 4 * a + b] = slot;
+        asm_cnt[slot + 1]++;
+      }
+    }
+  for (int64_t s = 0; s < n_slots; ++s) asm_cnt[s + 1] += asm_cnt[s];
+  std::vector<int> asm_code(16 * (size_t)t);
+  {
+    std::vector<int> fill(asm_cnt.begin(), asm_cnt.end() - 1);
+    for (int e = 0; e < t; ++e)
+      for (int ab = 0; ab < 16; ++ab) asm_code[fill[code_slot[16 * (size_t)e + ab]]++] = 16 * e + ab;
+  }
+  int** old[] = {&ctx->slice_ptr, &ctx->group_slice, &ctx->col, &ctx->row_len, &ctx->asm_ptr, &ctx->asm_code};
+  for (int** p : old) {
+    dfree(ctx, *p);
+    *p = nullptr;
+  }
+  auto up = [&](void** dst, const void* src, size_t bytes) -> mls_status {
+    mls_status st = dalloc(ctx, dst, bytes);
+    if (st != MLS_OK) return st;
+    return cuda_check(ctx, cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "pattern upload");
+  };
+  mls_status st;
+  if ((st = up((void**)&ctx->slice_ptr, slice_ptr.data(), sizeof(int) * (n_slices + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->group_slice, group_slice.data(), sizeof(int) * n_groups)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->col, col.data(), sizeof(int) * n_slots)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->row_len, row_len.data(), sizeof(int) * n)) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->asm_ptr, asm_cnt.data(), sizeof(int) * (n_slots + 1))) != MLS_OK) return st;
+  if ((st = up((void**)&ctx->asm_code, asm_code.data(), sizeof(int) * 16 * (size_t)t)) != MLS_OK) return st;
+  ctx->n_slices = n_slices;
+  ctx->n_groups = n_groups;
+  ctx->nnzb = nnzb;
+  ctx->h_slice_ptr = slice_ptr;
+  ctx->h_row_len = row_len;
+  ctx->h_col = col;
+  return MLS_OK;
+}
+
 static void free_all(mls_ctx* ctx) {
   for (void* p : ctx->allocs) cudaFree(p);
   ctx->allocs.clear();
@@ -157,6 +249,9 @@ static void free_all(mls_ctx* ctx) {
   ctx->assembled = false;
   ctx->cub_scale = nullptr;
   ctx->hval_cub = nullptr;
+  int* keep = ctx->cs.cnt_host;  // pinned, freed with the context
+  ctx->cs = mls::ContactState{};
+  ctx->cs.cnt_host = keep;
 }
 
 static mls_status alloc_state(mls_ctx* ctx);
@@ -333,64 +428,6 @@ mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n, const double* X, int32_t t, 
     h_lam[e] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     for (int a = 0; a < 4; ++a) h_mass[tets[4 * e + a]] += density[e] * h_vol[e] / 4.0;
   }
-  // vertex adjacency through tets (diagonal first, then ascending)
-  std::vector<std::vector<int>> nbr(n);
-  for (int e = 0; e < t; ++e)
-    for (int a = 0; a < 4; ++a)
-      for (int b = 0; b < 4; ++b) nbr[tets[4 * e + a]].push_back(tets[4 * e + b]);
-  std::vector<int> row_len(n);
-  for (int v = 0; v < n; ++v) {
-    auto& L = nbr[v];
-    std::sort(L.begin(), L.end());
-    L.erase(std::unique(L.begin(), L.end()), L.end());
-    auto it = std::find(L.begin(), L.end(), v);
-    if (it == L.end()) L.insert(L.begin(), v);
-    else std::rotate(L.begin(), it, it + 1);
-    row_len[v] = (int)L.size();
-  }
-  const int n_slices = (n + kSlice - 1) / kSlice;
-  std::vector<int> slice_ptr(n_slices + 1, 0);
-  for (int s = 0; s < n_slices; ++s) {
-    int w = 0;
-    for (int v = s * kSlice; v < std::min(n, (s + 1) * kSlice); ++v) w = std::max(w, row_len[v]);
-    slice_ptr[s + 1] = slice_ptr[s] + w;
-  }
-  const int64_t n_groups = slice_ptr[n_slices];
-  const int64_t n_slots = n_groups * kSlice;
-  std::vector<int> group_slice(n_groups), col(n_slots);
-  for (int s = 0; s < n_slices; ++s)
-    for (int g = slice_ptr[s]; g < slice_ptr[s + 1]; ++g) group_slice[g] = s;
-  int64_t nnzb = 0;
-  for (int v = 0; v < n; ++v) {
-    const int s = v / kSlice, lane = v % kSlice;
-    const int w = slice_ptr[s + 1] - slice_ptr[s];
-    for (int k = 0; k < w; ++k)
-      col[((int64_t)slice_ptr[s] + k) * kSlice + lane] = k < row_len[v] ? nbr[v][k] : v;
-    nnzb += row_len[v];
-  }
-  // element-block contributions per slot (CSR over slots)
-  std::vector<int> asm_cnt(n_slots + 1, 0);
-  std::vector<int64_t> code_slot(16 * (size_t)t);
-  for (int e = 0; e < t; ++e)
-    for (int a = 0; a < 4; ++a) {
-      const int v = tets[4 * e + a];
-      const auto& L = nbr[v];
-      const int s = v / kSlice, lane = v % kSlice;
-      for (int b = 0; b < 4; ++b) {
-        const int w = tets[4 * e + b];
-        const int k = (int)(std::find(L.begin(), L.end(), w) - L.begin());
-        const int64_t slot = ((int64_t)slice_ptr[s] + k) * kSlice + lane;
-        code_slot[16 * (size_t)e + 4 * a + b] = slot;
-        asm_cnt[slot + 1]++;
-      }
-    }
-  for (int64_t s = 0; s < n_slots; ++s) asm_cnt[s + 1] += asm_cnt[s];
-  std::vector<int> asm_code(16 * (size_t)t);
-  {
-    std::vector<int> fill(asm_cnt.begin(), asm_cnt.end() - 1);
-    for (int e = 0; e < t; ++e)
-      for (int ab = 0; ab < 16; ++ab) asm_code[fill[code_slot[16 * (size_t)e + ab]]++] = 16 * e + ab;
-  }
   std::vector<int> vt_ptr(n + 1, 0), vt_code(4 * (size_t)t);
   for (int e = 0; e < t; ++e)
     for (int a = 0; a < 4; ++a) vt_ptr[tets[4 * e + a] + 1]++;
@@ -424,23 +461,13 @@ mls_status mls_upload_mesh(mls_ctx* ctx, int32_t n, const double* X, int32_t t, 
   if ((st = up((void**)&ctx->pinned, pin.data(), n)) != MLS_OK) return st;
   ctx->h_pinned = pin;
   if ((st = up((void**)&ctx->X, Xp.data(), sizeof(Vec4d) * n)) != MLS_OK) return st;
-  if ((st = up((void**)&ctx->slice_ptr, slice_ptr.data(), sizeof(int) * (n_slices + 1))) != MLS_OK) return st;
-  if ((st = up((void**)&ctx->group_slice, group_slice.data(), sizeof(int) * n_groups)) != MLS_OK) return st;
-  if ((st = up((void**)&ctx->col, col.data(), sizeof(int) * n_slots)) != MLS_OK) return st;
-  if ((st = up((void**)&ctx->row_len, row_len.data(), sizeof(int) * n)) != MLS_OK) return st;
-  if ((st = up((void**)&ctx->asm_ptr, asm_cnt.data(), sizeof(int) * (n_slots + 1))) != MLS_OK) return st;
-  if ((st = up((void**)&ctx->asm_code, asm_code.data(), sizeof(int) * 16 * (size_t)t)) != MLS_OK) return st;
   if ((st = up((void**)&ctx->vt_ptr, vt_ptr.data(), sizeof(int) * (n + 1))) != MLS_OK) return st;
   if ((st = up((void**)&ctx->vt_code, vt_code.data(), sizeof(int) * 4 * (size_t)t)) != MLS_OK) return st;
   ctx->mass_min = *std::min_element(h_mass.begin(), h_mass.end());
   ctx->h_mass = h_mass;
   ctx->h_X.assign(X, X + 3 * (size_t)n);
-  ctx->n_slices = n_slices;
-  ctx->n_groups = n_groups;
-  ctx->nnzb = nnzb;
-  ctx->h_slice_ptr = slice_ptr;
-  ctx->h_row_len = row_len;
-  ctx->h_col = col;
+  ctx->h_tets.assign(tets, tets + 4 * (size_t)t);
+  if ((st = build_pattern(ctx, nullptr)) != MLS_OK) return st;
   return alloc_state(ctx);
 }
 
@@ -522,8 +549,11 @@ static mls_status assemble_at(mls_ctx* ctx, const Vec4d* x, double* gnorm) {
   if ((st = launch_eval_elements(ctx, x, nullptr)) != MLS_OK) return st;
   prof_end(ctx, tk);
   tk = prof_begin(ctx, MLS_PROF_ASSEMBLE);
+  // mesh-mesh pairs first: their gradient enters the gather, their blocks H
+  if ((st = contact_assemble(ctx, x)) != MLS_OK) return st;
   if ((st = launch_gather_grad(ctx, x, ctx->dscal + 2)) != MLS_OK) return st;
   if ((st = launch_assemble(ctx, x)) != MLS_OK) return st;
+  if ((st = contact_merge(ctx, ctx->hval, ctx->dinv, true)) != MLS_OK) return st;
   prof_end(ctx, tk);
   ctx->assembled = true;
   if (gnorm) {
@@ -742,11 +772,20 @@ static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
   if ((st = launch_energy(ctx, ctx->xt, ctx->tmp4, 0.0, &E, &infeasible)) != MLS_OK) return st;
   if (infeasible) return fail(ctx, MLS_EINVERTED, "x^t has an inverted tet or a vertex on/below the plane");
   if (!std::isfinite(E)) return fail(ctx, MLS_ENONFINITE, "non-finite energy at x^t");
+  if (ctx->cs.on) {
+    // with bodies the straight path x^t -> x_tilde is cut by the CCD filter
+    // first (a straight move could pass one body through another)
+    if ((st = launch_diff_state(ctx, ctx->xk, ctx->xt, ctx->dir)) != MLS_OK) return st;
+    double a0 = 1.0;
+    if ((st = launch_ccd(ctx, ctx->xt, ctx->dir, &a0)) != MLS_OK) return st;
+    if ((st = launch_xpay_state(ctx, ctx->xt, ctx->dir, a0, ctx->xk)) != MLS_OK) return st;
+  }
   if ((st = launch_energy(ctx, ctx->xk, ctx->tmp4, 0.0, &E, &infeasible)) != MLS_OK) return st;
   if (infeasible || !std::isfinite(E)) {
     st = cuda_check(ctx, cudaMemcpyAsync(ctx->xk, ctx->xt, sizeof(Vec4d) * ctx->n, cudaMemcpyDeviceToDevice,
                                          ctx->stream), "restart from x^t");
     if (st != MLS_OK) return st;
+    contact_invalidate(ctx);
   }
   const bool two_level = ctx->opt.preconditioner == MLS_PRECOND_TWO_LEVEL;
   if (two_level && !ctx->has_basis) return fail(ctx, MLS_EINVAL, "two-level preconditioner needs mls_upload_basis");
@@ -920,6 +959,7 @@ static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
   prof_flush(ctx);
   S.energy = E;
   S.coarse_shifts = (int)(ctx->coarse_shift_count - shifts0);
+  S.contact_pairs = ctx->cs.npt + ctx->cs.nee;
   if (stats) *stats = S;
   if (result != MLS_OK) return fail(ctx, result, "Newton reached its iteration cap");
   return MLS_OK;
@@ -1117,7 +1157,25 @@ mls_status mls_assemble(mls_ctx* ctx, const double* x, const double* x_t, const 
 mls_status mls_get_hessian(mls_ctx* ctx, int32_t* row_ptr, int32_t* colout, double* val, int64_t* nnzb) {
   mls_status st = check_mesh(ctx);
   if (st != MLS_OK) return st;
-  if (nnzb) *nnzb = ctx->nnzb;
+  // with bodies, rows of surface vertices carry the contact blocks claimed at the last assembly
+  const int* rl = ctx->h_row_len.data();
+  const int* cl = ctx->h_col.data();
+  std::vector<int> rl_dyn, col_dyn;
+  int64_t nz = ctx->nnzb;
+  if (ctx->cs.on && ctx->assembled) {
+    rl_dyn.resize(ctx->n);
+    col_dyn.resize((size_t)ctx->n_groups * kSlice);
+    st = cuda_check(ctx, cudaMemcpy(rl_dyn.data(), ctx->row_len, sizeof(int) * ctx->n, cudaMemcpyDeviceToHost), "rows");
+    if (st != MLS_OK) return st;
+    st = cuda_check(ctx, cudaMemcpy(col_dyn.data(), ctx->col, sizeof(int) * col_dyn.size(), cudaMemcpyDeviceToHost),
+                    "cols");
+    if (st != MLS_OK) return st;
+    rl = rl_dyn.data();
+    cl = col_dyn.data();
+    nz = 0;
+    for (int v = 0; v < ctx->n; ++v) nz += rl[v];
+  }
+  if (nnzb) *nnzb = nz;
   if (!row_ptr && !colout && !val) return MLS_OK;
   if (!ctx->assembled) return fail(ctx, MLS_EINVAL, "H not assembled");
   const int sb = storage_bytes(ctx);
@@ -1130,8 +1188,7 @@ mls_status mls_get_hessian(mls_ctx* ctx, int32_t* row_ptr, int32_t* colout, doub
     const int s = v / kSlice, lane = v % kSlice;
     // ascending column order for the exported CSR
     std::vector<std::pair<int, int>> order;
-    for (int k = 0; k < ctx->h_row_len[v]; ++k)
-      order.emplace_back(ctx->h_col[((size_t)ctx->h_slice_ptr[s] + k) * kSlice + lane], k);
+    for (int k = 0; k < rl[v]; ++k) order.emplace_back(cl[((size_t)ctx->h_slice_ptr[s] + k) * kSlice + lane], k);
     std::sort(order.begin(), order.end());
     for (auto& ck : order) {
       const int64_t g = (int64_t)ctx->h_slice_ptr[s] + ck.second;

@@ -557,11 +557,26 @@ mls_status launch_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double al
   if (st != MLS_OK) return st;
   *E = ctx->dscal_host[0];
   *infeasible = ctx->dscal_host[1] > 0.5 ? 1 : 0;
+  if (ctx->cs.on) {  // mesh-mesh pairs over the candidates of x -> x + d
+    double Ec = 0.0;
+    int ic = 0;
+    if ((st = contact_energy(ctx, x, d, alpha, &Ec, &ic)) != MLS_OK) return st;
+    *E += Ec;
+    *infeasible |= ic;
+  }
   return MLS_OK;
 }
 
+// Largest step fraction the CCD filter allows (Sec. 3.9): for the plane,
+// 0.9 of the fraction at which the first vertex reaches it; with bodies,
+// also the mesh-mesh conservative advancement (contact.cu)
 mls_status launch_ccd(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double* alpha) {
-  if (!ctx->contact) { *alpha = 1.0; return MLS_OK; }
+  double tm = 1.0;
+  if (ctx->cs.on) {
+    mls_status st = contact_ccd(ctx, x, d, &tm);
+    if (st != MLS_OK) return st;
+  }
+  if (!ctx->contact) { *alpha = tm; return MLS_OK; }
   const double big = 1e300;
   mls_status st = cuda_check(ctx, cudaMemcpyAsync(ctx->dscal + 4, &big, sizeof(double),
                                                   cudaMemcpyHostToDevice, ctx->stream), "ccd init");
@@ -577,7 +592,7 @@ mls_status launch_ccd(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double* alph
   st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "ccd sync");
   if (st != MLS_OK) return st;
   const double tmin = ctx->dscal_host[4];
-  *alpha = tmin >= 1e299 ? 1.0 : fmin(1.0, 0.9 * tmin);
+  *alpha = fmin(tmin >= 1e299 ? 1.0 : fmin(1.0, 0.9 * tmin), tm);
   return MLS_OK;
 }
 

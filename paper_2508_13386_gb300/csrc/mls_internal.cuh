@@ -501,7 +501,7 @@ __device__ __forceinline__ void pcg_head_publish(PcgScalars* S, unsigned long lo
 }
 
 // Reduction slots (one counter each)
-enum { RS_PCG_PQ = 0, RS_PCG_RR, RS_PCG_RZ, RS_ENERGY, RS_MISC, RS_GRAD, RS_COUNT };
+enum { RS_PCG_PQ = 0, RS_PCG_RR, RS_PCG_RZ, RS_ENERGY, RS_MISC, RS_GRAD, RS_CONTACT, RS_COUNT };
 
 struct Basis {
   int m = 0;                  // handles
@@ -585,6 +585,55 @@ __device__ __forceinline__ double fric_f0(double y, double eps) {
 
 struct mls_mlp;
 
+namespace mls {
+// Mesh-mesh contact (contact.cu): the surface primitives of the bodies, the
+// hashed grid of the broad phase, the candidate pairs and the coupling
+// blocks of the last assembly
+struct ContactState {
+  bool on = false;
+  int nf = 0, ne = 0, nsv = 0;       // boundary faces, their edges, surface vertices
+  int4* faces = nullptr;             // [nf] {a, b, c, body}
+  int4* edges = nullptr;             // [ne] {a, b, body, 0}
+  int2* sverts = nullptr;            // [nsv] {v, body}
+  int* row_len0 = nullptr;           // [n] row lengths of H's element pattern
+  double dhat = 1e-3, kappa = 1e5;   // barrier of the pairs
+  double cell0 = 0.0;                // mean rest length of the surface edges
+  int spare = 0;                     // spare block slots per surface-vertex row
+  // hashed grid: bucket heads, entries {primitive, ix, iy, iz} and chain links
+  int* head = nullptr;
+  int hbits = 0;
+  int4* ent = nullptr;
+  int* next = nullptr;
+  int64_t ecap = 0;
+  double* boxes = nullptr;           // [nf + ne][6] grown boxes of the entered primitives
+  int* cnt = nullptr;                // device counters
+  int* cnt_host = nullptr;           // pinned mirror
+  int2* pt = nullptr;                // point-triangle pairs {v, face} within dhat at the assembly iterate
+  int2* ee = nullptr;                // edge-edge pairs {edge, edge}
+  int64_t pcap = 0;
+  int npt = 0, nee = 0;
+  int2* spt = nullptr;               // candidates over the segment x -> x + d (CCD, line search)
+  int2* see = nullptr;
+  int64_t scap = 0;
+  int nspt = 0, nsee = 0;
+  bool sweep_valid = false;
+  const void* sweep_x = nullptr;
+  const void* sweep_d = nullptr;
+  double* pg = nullptr;              // [pbuf_cap][12] barrier gradient of each pair
+  double* pH = nullptr;              // [pbuf_cap][144] its projected Hessian
+  int pbuf_cap = 0;
+  unsigned long long* ckey = nullptr;  // coupling table: key (i << 32 | j), open addressing
+  double* cval = nullptr;              // [ccap][9] barrier blocks (kappa, no h^2)
+  int ccap = 0;
+  int4* xc = nullptr;                // cross-body couplings {i, j, slot of H, 0}
+  int xcap = 0;
+  int nxc = 0;
+  Vec4d* cgrad = nullptr;            // [n] barrier gradient of the pairs (no h^2)
+  double* ccd = nullptr;             // device: smallest CCD fraction
+  std::vector<int> h_body;
+};
+}  // namespace mls
+
 struct mls_ctx {
   mls_options opt{};
   cudaStream_t stream = nullptr;
@@ -616,6 +665,8 @@ struct mls_ctx {
   int64_t nnzb = 0;                // real (non-padding) blocks
   double mass_min = 0.0;           // smallest lumped vertex mass
   std::vector<int> h_slice_ptr, h_row_len, h_col;
+  std::vector<int> h_tets;         // [t][4] host copy (the pattern is rebuilt with contact slots)
+  mls::ContactState cs;            // mesh-mesh contact
 
   // per-timestep / per-iteration state
   double h = 1.0 / 60.0;           // step of the implicit-Euler potential the Newton loop minimises
@@ -762,6 +813,8 @@ mls_status launch_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double al
 mls_status launch_ccd(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double* alpha);
 mls_status launch_norms(mls_ctx* ctx, const Vec4d* d, double* dinf, double* xdisp_inf);
 mls_status launch_axpy_state(mls_ctx* ctx, Vec4d* x, const Vec4d* d, double alpha);
+mls_status launch_diff_state(mls_ctx* ctx, const Vec4d* a, const Vec4d* b, Vec4d* out);   // out = a - b
+mls_status launch_xpay_state(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double alpha, Vec4d* out);  // x + alpha d
 mls_status launch_predictor(mls_ctx* ctx, const double* x, const double* v, double dt);
 // BDF2 predictor from (x^t, v^t) and (x^{t-1}, v^{t-1}) with timestep dt
 mls_status launch_predictor_bdf2(mls_ctx* ctx, const double* x, const double* v, const double* x_prev,
@@ -824,6 +877,15 @@ mls_status sms_pcg(mls_ctx* ctx, const void* b, double rtol, int max_iter, int* 
 mls_status build_coarse_unfactored(mls_ctx* ctx);
 mls_status launch_assemble_lagged(mls_ctx* ctx, const Vec4d* x);
 mls_status affine_operator(mls_ctx* ctx, const double om[3]);
+// mesh-mesh contact (contact.cu)
+mls_status build_pattern(mls_ctx* ctx, const std::vector<int>* spare);
+mls_status contact_assemble(mls_ctx* ctx, const Vec4d* x);           // pairs, gradient, coupling blocks at x
+mls_status contact_merge(mls_ctx* ctx, void* val, void* dinv, bool record);  // coupling blocks into H
+mls_status contact_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double alpha, double* E, int* infeasible);
+mls_status contact_ccd(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double* t);
+mls_status contact_galerkin(mls_ctx* ctx, const void* val);          // cross-body U_i^T H_ij U_j into Ac
+void contact_invalidate(mls_ctx* ctx);                               // x or d changed: sweep again
+void contact_free(mls_ctx* ctx);
 mls_status warm_start_begin(mls_ctx* ctx, int* used);
 mls_status warm_start_first_iteration(mls_ctx* ctx);
 mls_status warm_start_end(mls_ctx* ctx);

@@ -1088,7 +1088,10 @@ template <typename VT, typename MT>
 static mls_status galerkin_t(mls_ctx* ctx) {
   Basis& B = ctx->basis;
   const int r = 12 * B.m;
-  GalerkinView G{ctx->n, ctx->slice_ptr, ctx->col, ctx->row_len, B.yrow, B.yh, B.yslot, B.maxk};
+  // Y = H U over H's element pattern; the cross-body contact blocks in the
+  // spare slots past it are added separately (contact_galerkin)
+  const int* rl0 = ctx->cs.row_len0 ? ctx->cs.row_len0 : ctx->row_len;
+  GalerkinView G{ctx->n, ctx->slice_ptr, ctx->col, rl0, B.yrow, B.yh, B.yslot, B.maxk};
   if (!B.ypair_row) {
     mls_status st = dalloc(ctx, (void**)&B.ypair_row, sizeof(int) * std::max<int64_t>(B.ny, 1));
     if (st != MLS_OK) return st;
@@ -1119,7 +1122,9 @@ static mls_status galerkin_t(mls_ctx* ctx) {
     { ++ctx->launches; k_galerkin_reduce<VT><<<B.nb, 144, 0, ctx->stream>>>(B.chunk_ptr, B.slot_row, B.hn,
                                                                             (const VT*)ctx->gpart, r, ctx->Ac); }
   }
-  return cuda_check(ctx, cudaGetLastError(), "galerkin");
+  st = cuda_check(ctx, cudaGetLastError(), "galerkin");
+  if (st != MLS_OK) return st;
+  return contact_galerkin(ctx, hv);
 }
 
 // Factor the dense SPD float64 matrix A (r x r, row-major, overwritten by
