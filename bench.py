@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--learned-steps", type=int, default=480,
                     help="training timesteps of the learned warm start (seeded drops of the same lattice, 40 steps "
                          "each; 0 skips the learned arm)")
+    ap.add_argument("--contact-steps", type=int, default=4,
+                    help="steps timed on the two-lattice stack with mesh-mesh contact (0 skips the arm)")
+    ap.add_argument("--contact-grid", type=int, default=24, help="lattice grid of each body of the stack")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end pass")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
@@ -723,6 +726,9 @@ def main():
         # the mixed step from the timed start state against the oracle
         dxm, _ = ours.newton_step(x_s.clone(), v_s.clone(), h)
         oracle_err = oracle_error_estimate(scene, xs_h, vs_h, xs_h + dxm.cpu().numpy(), threads)
+    contact_res = None
+    if not args.profile_run and args.contact_steps > 0 and rank == 0:
+        contact_res = contact_arm(args, dev, stream, flush)
     headline = "mixed two-level PCG (the learned start is reported in 'learned' and loses or does not gain)"
     ms_per_step = total_s * 1e3 / args.steps
     # the learned arm heads the line only if its start was taken and it is faster within the gate
@@ -761,6 +767,7 @@ def main():
         "headline_arm": headline,
         "learned": learned_res,
         "paper_direction": paper,
+        "mesh_contact": contact_res,
         "fp64_plain": {"value": 1e3 / float(np.mean(fp64_ms)) if fp64_ms else None, "unit": UNIT,
                        "ms_per_step": float(np.mean(fp64_ms)) if fp64_ms else None,
                        "steps": len(fp64_ms),
@@ -782,6 +789,92 @@ def main():
     print(json.dumps(line))
     if world > 1:
         dist.barrier()
+
+
+def contact_arm(args, dev, stream, flush):
+    """Mesh-mesh contact (the barrier between bodies and its CCD filter) on
+    the two-lattice stack (synth.lattice_stack_scene): the upper lattice
+    falls onto the lower one, which rests on the ground.  Same solver
+    settings as the headline arm, with an SMS basis per body (64 handles
+    each).  The first step is warm-up (the bodies meet during it); the
+    next ``--contact-steps`` are timed with CUDA events, L2 flushed before
+    each, then one more step is taken with the kernel-class timers on."""
+    import torch
+    import synth
+    import paper_2508_13386_gb300 as mls
+    from paper_2508_13386_gb300 import basis as sms
+    scene, body = synth.lattice_stack_scene(args.contact_grid)
+    origins, vrow, handle, phi = [], [0], [], []
+    m0 = 0
+    parts = []
+    for b in (0, 1):
+        vid = np.nonzero(body == b)[0]
+        remap = -np.ones(scene.n_verts, np.int64)
+        remap[vid] = np.arange(len(vid))
+        keep = np.all(body[scene.tets] == b, axis=1)
+        Bb = sms.build_sms_basis(scene.X[vid], remap[scene.tets[keep]], scene.E[keep], 64, seed=1)
+        parts.append((vid, Bb, m0))
+        m0 += len(Bb["origins"])
+    # merge: vertex rows in global order, handle indices offset per body
+    rows = [None] * scene.n_verts
+    for vid, Bb, off in parts:
+        for k, v in enumerate(vid):
+            lo, hi = Bb["vrow"][k], Bb["vrow"][k + 1]
+            rows[v] = (Bb["handle"][lo:hi] + off, Bb["phi"][lo:hi])
+        origins.append(Bb["origins"])
+    for v in range(scene.n_verts):
+        handle.extend(rows[v][0].tolist())
+        phi.extend(rows[v][1].tolist())
+        vrow.append(len(handle))
+    origins = np.vstack(origins)
+    sol = mls.Solver(precision=args.precision, preconditioner="two_level", cycle=args.cycle, omega=args.omega,
+                     newton_tol=args.newton_tol, pcg_rtol=args.pcg_rtol, pcg_check_every=args.pcg_check_every,
+                     coarse_refresh=args.coarse_refresh, stream=stream, coarse_lag_steps=args.coarse_lag)
+    sol.setup_scene(scene)
+    sol.set_bodies(body, scene.dhat, scene.kappa)
+    sol.upload_basis(origins, np.asarray(vrow, np.int32), np.asarray(handle, np.int32), np.asarray(phi))
+    h = scene.dt
+    x = torch.as_tensor(scene.x0, device=dev).contiguous()
+    v = torch.as_tensor(scene.v0, device=dev).contiguous()
+    dx = torch.empty_like(x)
+
+    def step():
+        _, st = sol.newton_step(x, v, h, dx=dx)
+        v.copy_(dx / h)
+        x.add_(dx)
+        return st
+
+    step()
+    torch.cuda.synchronize()
+    ms, stats = [], []
+    for k in range(args.contact_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    sol.profile_enable(["elements", "assemble", "spmv", "pcg_update", "precond", "galerkin", "cholesky",
+                        "linesearch"])
+    step()
+    torch.cuda.synchronize()
+    prof = sol.profile_read()
+    sol.profile_enable([])
+    gap = float((x[body == 1, 2].min() - x[body == 0, 2].max()).item())
+    out = {"value": 1e3 / float(np.mean(ms)), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
+           "step_ms": [round(t, 3) for t in ms], "steps": len(ms),
+           "workload": f"two {args.contact_grid}^3 lattices (seeds 3, 4): {scene.n_tets} tets, {scene.n_verts} "
+                       f"verts; upper falls at 1 m/s from 5 mm onto the lower one resting on the ground; "
+                       f"mesh-mesh and ground barrier dhat=1e-3 kappa=1e5; SMS basis 64 handles per body",
+           "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in stats])),
+           "pcg_iters_per_step": float(np.mean([s["pcg_iters"] for s in stats])),
+           "contact_pairs_last_assembly": [int(s["contact_pairs"]) for s in stats],
+           "gap_after_m": gap,
+           "breakdown_one_step": {k: {"ms": round(t, 3), "launches": n} for k, (t, n) in prof.items() if n}}
+    sol.close()
+    return out
 
 
 def learned_arm(args, scene, B, make, dev, stream, x_prev, v_prev, x_s, v_s, flush, fp64):

@@ -234,7 +234,7 @@ static void free_all(mls_ctx* ctx) {
   ctx->ws_hist = ctx->ws_qg = ctx->ws_qtilde = ctx->ws_qnext = nullptr;
   ctx->ws_feat = ctx->ws_target = ctx->ws_pred = nullptr;
   ctx->ws_hsave = nullptr;
-  ctx->oz_fwd = ctx->oz_rev = nullptr;
+  ctx->oz_fwd = nullptr;
   ctx->oz_e = ctx->umma_err = nullptr;
   ctx->sms_buf = nullptr;
   ctx->sms_cg = nullptr;
@@ -1075,7 +1075,7 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
                    B.vcoef, B.hcoef, B.rchunk_handle, B.rchunk_beg, B.rchunk_ptr, B.rpart, B.rcount,
                    ctx->gpart, ctx->yval, ctx->Ac, ctx->Acopy,
                    ctx->Linv, ctx->LinvT, ctx->Ainv, ctx->cvec, ctx->cvec2, ctx->chol_info, ctx->chol_tinv,
-                   ctx->oz_fwd, ctx->oz_rev, ctx->oz_e, ctx->sms_buf, ctx->sms_cg, ctx->sms_m,
+                   ctx->oz_fwd, ctx->oz_e, ctx->sms_buf, ctx->sms_cg, ctx->sms_m,
                    ctx->Am, ctx->Wm, ctx->WmT, ctx->ws_c, ctx->ws_c2, ctx->ws_tmp, ctx->ws_hist, ctx->ws_qg,
                    ctx->ws_qtilde, ctx->ws_qnext, ctx->ws_feat, ctx->ws_target, ctx->ws_pred, ctx->ws_hsave};
     for (void* p : old) dfree(ctx, p);
@@ -1083,7 +1083,7 @@ mls_status mls_upload_basis(mls_ctx* ctx, int32_t m, const double* origins, cons
     ctx->ws_hist = ctx->ws_qg = ctx->ws_qtilde = ctx->ws_qnext = nullptr;
     ctx->ws_feat = ctx->ws_target = ctx->ws_pred = nullptr;
     ctx->ws_hsave = nullptr;
-    ctx->oz_fwd = ctx->oz_rev = nullptr;
+    ctx->oz_fwd = nullptr;
     ctx->oz_e = nullptr;
     ctx->sms_buf = nullptr;
     ctx->sms_cg = nullptr;

@@ -84,12 +84,19 @@ __device__ __forceinline__ uint32_t cell_hash(int ix, int iy, int iz) {
   return ((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u);
 }
 
+// cells are addressed by 21-bit coordinates, |i| < 2^20
+constexpr double kCellRange = 1048000.0;
+__device__ __forceinline__ unsigned long long cell_key(int ix, int iy, int iz) {
+  return (unsigned long long)(ix + (1 << 20)) | ((unsigned long long)(iy + (1 << 20)) << 21) |
+         ((unsigned long long)(iz + (1 << 20)) << 42);
+}
+
 // integer cell range of a box; false (and a flag) when it is out of range or too large
 __device__ __forceinline__ bool cell_range(const Box& b, double inv_cell, int (&c0)[3], int (&c1)[3], int* flags) {
   int64_t count = 1;
   for (int c = 0; c < 3; ++c) {
     const double l = floor(b.lo[c] * inv_cell), h = floor(b.hi[c] * inv_cell);
-    if (!(l > -1e9 && h < 1e9)) {
+    if (!(l > -kCellRange && h < kCellRange)) {
       atomicOr(flags, kFlagRange);
       return false;
     }
@@ -104,18 +111,62 @@ __device__ __forceinline__ bool cell_range(const Box& b, double inv_cell, int (&
   return true;
 }
 
+// monotone map of doubles to unsigned 64-bit keys (for atomic min / max)
+__device__ __forceinline__ unsigned long long dkey(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+constexpr int kMaxBodyBoxes = 64;  // bodies up to this count get the box prefilter
+
+// per-body boxes of the surface vertices over x -> x + d: block-level
+// reduction in shared memory, one global atomic per block and coordinate
+__global__ void __launch_bounds__(kBlock) k_body_boxes(const int2* __restrict__ sverts, int nsv, int nbody,
+                                                       const Vec4d* __restrict__ x, const Vec4d* __restrict__ d,
+                                                       unsigned long long* __restrict__ lo,
+                                                       unsigned long long* __restrict__ hi) {
+  __shared__ unsigned long long slo[kMaxBodyBoxes * 3], shi[kMaxBodyBoxes * 3];
+  for (int k = threadIdx.x; k < 3 * nbody; k += blockDim.x) {
+    slo[k] = ~0ull;
+    shi[k] = 0ull;
+  }
+  __syncthreads();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nsv) {
+    const int2 sv = sverts[q];
+    for (int pass = 0; pass < (d ? 2 : 1); ++pass) {
+      const D3 p = pos(x, d, pass ? 1.0 : 0.0, sv.x);
+      for (int c = 0; c < 3; ++c) {
+        const unsigned long long k = dkey(cgeom::comp(p, c));
+        atomicMin(slo + 3 * sv.y + c, k);
+        atomicMax(shi + 3 * sv.y + c, k);
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 3 * nbody; k += blockDim.x) {
+    if (slo[k] != ~0ull) atomicMin(lo + k, slo[k]);
+    if (shi[k] != 0ull) atomicMax(hi + k, shi[k]);
+  }
+}
+
 struct GridView {
-  int nf, ne, nsv;
+  int nf, ne, nsv, nbody;
   const int4* __restrict__ faces;
   const int4* __restrict__ edges;
   const int2* __restrict__ sverts;
-  int* head;
+  int* head;                 // [2 << hbits]: faces' buckets, then edges'
   int hmask;
-  int4* ent;
+  int4* ent;                 // {primitive, body, cell key low, cell key high}
   int* next;
   int64_t ecap;
   double* boxes;
   int* cnt;
+  const unsigned long long* blo;  // per-body boxes (nullable: no prefilter)
+  const unsigned long long* bhi;
   double inv_cell, dhat;
 };
 
@@ -123,13 +174,13 @@ struct GridView {
 __global__ void k_grid_insert(GridView G, const Vec4d* __restrict__ x, const Vec4d* __restrict__ d) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= G.nf + G.ne) return;
-  int vs[3], k;
+  int vs[3], k, body;
   if (p < G.nf) {
     const int4 f = G.faces[p];
-    vs[0] = f.x; vs[1] = f.y; vs[2] = f.z; k = 3;
+    vs[0] = f.x; vs[1] = f.y; vs[2] = f.z; k = 3; body = f.w;
   } else {
     const int4 e = G.edges[p - G.nf];
-    vs[0] = e.x; vs[1] = e.y; vs[2] = e.y; k = 2;
+    vs[0] = e.x; vs[1] = e.y; vs[2] = e.y; k = 2; body = e.z;
   }
   const Box b = prim_box(x, d, vs, k, G.dhat);
   for (int c = 0; c < 3; ++c) {
@@ -138,13 +189,15 @@ __global__ void k_grid_insert(GridView G, const Vec4d* __restrict__ x, const Vec
   }
   int c0[3], c1[3];
   if (!cell_range(b, G.inv_cell, c0, c1, G.cnt + kCntFlags)) return;
+  int* head = G.head + (p < G.nf ? 0 : G.hmask + 1);
   for (int iz = c0[2]; iz <= c1[2]; ++iz)
     for (int iy = c0[1]; iy <= c1[1]; ++iy)
       for (int ix = c0[0]; ix <= c1[0]; ++ix) {
         const int e = atomicAdd(G.cnt + kCntEnt, 1);
         if (e >= G.ecap) continue;  // counted; the host grows the table and enters again
-        G.ent[e] = make_int4(p, ix, iy, iz);
-        G.next[e] = atomicExch(G.head + (cell_hash(ix, iy, iz) & G.hmask), e);
+        const unsigned long long key = cell_key(ix, iy, iz);
+        G.ent[e] = make_int4(p, body, (int)(unsigned)key, (int)(unsigned)(key >> 32));
+        G.next[e] = atomicExch(head + (cell_hash(ix, iy, iz) & G.hmask), e);
       }
 }
 
@@ -154,9 +207,11 @@ struct PairOut {
   int64_t cap;
 };
 
-// Each surface vertex (point-triangle) and edge (edge-edge, partner index
-// above its own) walks the cells of its own box.  Proximity mode (d null):
-// keep pairs at distance < dhat at x.  Sweep mode: keep every candidate.
+// Each surface vertex (point-triangle, against the faces' buckets) and edge
+// (edge-edge, the edges' buckets, partner index above its own) walks the
+// cells of its own box; primitives whose box meets no other body's box are
+// skipped.  Proximity mode (d null): keep pairs at distance < dhat at x.
+// Sweep mode: keep every candidate.
 __global__ void k_grid_query(GridView G, const Vec4d* __restrict__ x, const Vec4d* __restrict__ d, PairOut out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= G.nsv + G.ne) return;
@@ -170,30 +225,35 @@ __global__ void k_grid_query(GridView G, const Vec4d* __restrict__ x, const Vec4
     vs[0] = e.x; vs[1] = e.y; k = 2; body = e.z; self = q - G.nsv;
   }
   const Box b = prim_box(x, d, vs, k, 0.0);
+  if (G.blo) {  // near another body at all?
+    bool near = false;
+    for (int o = 0; o < G.nbody && !near; ++o) {
+      if (o == body) continue;
+      bool m = true;
+      for (int c = 0; c < 3; ++c)
+        m = m && b.hi[c] >= dkey_inv(G.blo[3 * o + c]) - 2.0 * G.dhat &&
+            b.lo[c] <= dkey_inv(G.bhi[3 * o + c]) + 2.0 * G.dhat;
+      near = m;
+    }
+    if (!near) return;
+  }
   int c0[3], c1[3];
   if (!cell_range(b, G.inv_cell, c0, c1, G.cnt + kCntFlags)) return;
   const double dh = G.dhat;
+  const int* head = G.head + (is_pt ? 0 : G.hmask + 1);
   for (int iz = c0[2]; iz <= c1[2]; ++iz)
     for (int iy = c0[1]; iy <= c1[1]; ++iy)
       for (int ix = c0[0]; ix <= c1[0]; ++ix) {
-        int e = __ldcg(G.head + (cell_hash(ix, iy, iz) & G.hmask));
+        const unsigned long long key = cell_key(ix, iy, iz);
+        const int klo = (int)(unsigned)key, khi = (int)(unsigned)(key >> 32);
+        int e = __ldcg(head + (cell_hash(ix, iy, iz) & G.hmask));
         while (e >= 0) {
           const int4 en = G.ent[e];
           e = G.next[e];
-          if (en.y != ix || en.z != iy || en.w != iz) continue;
+          if (en.z != klo || en.w != khi || en.y == body) continue;
           const int p = en.x;
-          int other;
-          if (is_pt) {
-            if (p >= G.nf) continue;
-            if (G.faces[p].w == body) continue;
-            other = p;
-          } else {
-            if (p < G.nf) continue;
-            const int j = p - G.nf;
-            if (j <= self) continue;
-            if (G.edges[j].z == body) continue;
-            other = j;
-          }
+          const int other = is_pt ? p : p - G.nf;
+          if (!is_pt && other <= self) continue;
           // boxes meet, and this cell holds the lower corner of their intersection
           const double* ib = G.boxes + 6 * (int64_t)p;
           bool meet = true, own = true;
@@ -254,15 +314,27 @@ __device__ __forceinline__ double bar_b2(double d, double dhat) {
 }
 
 // kappa (b'' grad d grad d^T + b' Hess d) from d, grad d (gd) and Hess d (in H),
-// projected to the PSD cone in place; g = kappa b' grad d.  V: workspace [144]
-__device__ __forceinline__ void barrier_terms(double d, const double* gd, double kappa, double dhat, double* g,
-                                              double* H, double* V) {
+// projected to the PSD cone in place; g = kappa b' grad d.  Only the rows and
+// columns of the feature's vertices are nonzero, so the projection runs on
+// that 3 nv x 3 nv block (gathered into W, V: workspaces of 144).
+__device__ __forceinline__ void barrier_terms(const cgeom::Feature& F, double d, const double* gd, double kappa,
+                                              double dhat, double* g, double* H, double* W, double* V) {
   const double b1 = kappa * bar_b1(d, dhat), b2 = kappa * bar_b2(d, dhat);
-  for (int i = 0; i < 12; ++i) {
-    g[i] = b1 * gd[i];
-    for (int j = 0; j < 12; ++j) H[i * 12 + j] = b2 * gd[i] * gd[j] + b1 * H[i * 12 + j];
+  for (int i = 0; i < 12; ++i) g[i] = b1 * gd[i];
+  const int k = 3 * F.nv;
+  for (int a = 0; a < k; ++a) {
+    const int ra = 3 * F.idx[a / 3] + a % 3;
+    for (int b = 0; b < k; ++b) {
+      const int cb = 3 * F.idx[b / 3] + b % 3;
+      W[a * 12 + b] = b2 * gd[ra] * gd[cb] + b1 * H[ra * 12 + cb];
+    }
   }
-  cgeom::psd_project(H, V, 12);
+  cgeom::psd_project(W, V, k);
+  for (int q = 0; q < 144; ++q) H[q] = 0.0;
+  for (int a = 0; a < k; ++a) {
+    const int ra = 3 * F.idx[a / 3] + a % 3;
+    for (int b = 0; b < k; ++b) H[ra * 12 + 3 * F.idx[b / 3] + b % 3] = W[a * 12 + b];
+  }
 }
 
 struct CouplingView {
@@ -308,9 +380,9 @@ __global__ void k_pair_eval(const int2* __restrict__ pt, int npt, const int2* __
   }
   const cgeom::Feature F = kind == 0 ? cgeom::pt_feature(P[0], P[1], P[2], P[3])
                                      : cgeom::ee_feature(P[0], P[1], P[2], P[3]);
-  double gd[12], g[12], H[144], V[144];
+  double gd[12], g[12], H[144], W[144], V[144];
   const double d = cgeom::feature_derivatives(F, P, gd, H);
-  barrier_terms(d, gd, kappa, dhat, g, H, V);
+  barrier_terms(F, d, gd, kappa, dhat, g, H, W, V);
   for (int q = 0; q < 12; ++q) og[q] = g[q];
   for (int q = 0; q < 144; ++q) oH[q] = H[q];
 }
@@ -561,12 +633,12 @@ __global__ void k_pair_derivatives(const int* __restrict__ kind, const double* _
   for (int a = 0; a < 4; ++a) P[a] = D3{X[12 * p + 3 * a], X[12 * p + 3 * a + 1], X[12 * p + 3 * a + 2]};
   const int k = kind[p];
   const cgeom::Feature F = k == 0 ? cgeom::pt_feature(P[0], P[1], P[2], P[3]) : cgeom::ee_feature(P[0], P[1], P[2], P[3]);
-  double g[12], gb[12], H[144], V[144];
+  double g[12], gb[12], H[144], W[144], V[144];
   const double d = cgeom::feature_derivatives(F, P, g, H);
   dist[p] = d;
   for (int q = 0; q < 12; ++q) gd[12 * p + q] = g[q];
   for (int q = 0; q < 144; ++q) Hd[144 * (int64_t)p + q] = H[q];
-  barrier_terms(d, g, kappa, dhat, gb, H, V);
+  barrier_terms(F, d, g, kappa, dhat, gb, H, W, V);
   for (int q = 0; q < 144; ++q) Hb[144 * (int64_t)p + q] = H[q];
 }
 
@@ -582,7 +654,7 @@ static int pow2_at_least(int64_t v) {
 void contact_free(mls_ctx* ctx) {
   ContactState& cs = ctx->cs;
   void* bufs[] = {cs.faces, cs.edges, cs.sverts, cs.row_len0, cs.head, cs.ent,  cs.next, cs.boxes, cs.cnt, cs.pt,
-                  cs.ee,    cs.spt,   cs.see,    cs.ckey,     cs.cval, cs.xc,   cs.cgrad, cs.ccd,  cs.pg,  cs.pH};
+                  cs.ee,    cs.spt,   cs.see,    cs.ckey,     cs.cval, cs.xc,   cs.cgrad, cs.ccd,  cs.pg,  cs.pH, cs.bbox};
   for (void* p : bufs) dfree(ctx, p);
   int* keep = cs.cnt_host;  // pinned, freed with the context
   cs = ContactState{};
@@ -616,10 +688,24 @@ static mls_status broad_phase(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, int2
   for (int attempt = 0; attempt < 24; ++attempt) {
     if ((st = cuda_check(ctx, cudaMemsetAsync(cs.cnt, 0, sizeof(int) * kCntWords, ctx->stream), "counters")) != MLS_OK)
       return st;
-    if ((st = cuda_check(ctx, cudaMemsetAsync(cs.head, 0xFF, sizeof(int) << cs.hbits, ctx->stream), "grid")) != MLS_OK)
+    if ((st = cuda_check(ctx, cudaMemsetAsync(cs.head, 0xFF, sizeof(int) << (cs.hbits + 1), ctx->stream), "grid")) !=
+        MLS_OK)
       return st;
-    GridView G{cs.nf, cs.ne, cs.nsv, cs.faces, cs.edges, cs.sverts, cs.head, (1 << cs.hbits) - 1, cs.ent, cs.next,
-               cs.ecap, cs.boxes, cs.cnt, 1.0 / cell, cs.dhat};
+    const bool pre = cs.nbody <= kMaxBodyBoxes;
+    if (pre) {
+      if ((st = cuda_check(ctx, cudaMemsetAsync(cs.bbox, 0xFF, sizeof(unsigned long long) * 3 * cs.nbody, ctx->stream),
+                           "body boxes")) != MLS_OK)
+        return st;
+      if ((st = cuda_check(ctx, cudaMemsetAsync(cs.bbox + 3 * cs.nbody, 0, sizeof(unsigned long long) * 3 * cs.nbody,
+                                                ctx->stream), "body boxes")) != MLS_OK)
+        return st;
+      ++ctx->launches;
+      k_body_boxes<<<nblocks(cs.nsv), kBlock, 0, ctx->stream>>>(cs.sverts, cs.nsv, cs.nbody, x, d, cs.bbox,
+                                                                 cs.bbox + 3 * cs.nbody);
+    }
+    GridView G{cs.nf, cs.ne, cs.nsv, cs.nbody, cs.faces, cs.edges, cs.sverts, cs.head, (1 << cs.hbits) - 1, cs.ent,
+               cs.next, cs.ecap, cs.boxes, cs.cnt, pre ? cs.bbox : nullptr, pre ? cs.bbox + 3 * cs.nbody : nullptr,
+               1.0 / cell, cs.dhat};
     ++ctx->launches;
     k_grid_insert<<<nblocks(cs.nf + cs.ne), kBlock, 0, ctx->stream>>>(G, x, d);
     ++ctx->launches;
@@ -637,7 +723,7 @@ static mls_status broad_phase(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, int2
       cs.hbits = pow2_at_least(2 * cs.ecap);
       if ((st = regrow(ctx, (void**)&cs.ent, sizeof(int4) * cs.ecap)) != MLS_OK) return st;
       if ((st = regrow(ctx, (void**)&cs.next, sizeof(int) * cs.ecap)) != MLS_OK) return st;
-      if ((st = regrow(ctx, (void**)&cs.head, sizeof(int) << cs.hbits)) != MLS_OK) return st;
+      if ((st = regrow(ctx, (void**)&cs.head, sizeof(int) << (cs.hbits + 1))) != MLS_OK) return st;
       continue;
     }
     if (c[kCntPT] > *cap || c[kCntEE] > *cap) {
@@ -699,7 +785,9 @@ mls_status contact_assemble(mls_ctx* ctx, const Vec4d* x) {
   const CouplingView C{cs.ckey, cs.cval, cs.ccap - 1, cs.cnt + kCntFlags};
   if (np > 0) {
     ++ctx->launches;
-    k_pair_eval<<<nblocks(np, 64), 64, 0, ctx->stream>>>(cs.pt, cs.npt, cs.ee, cs.nee, cs.faces, cs.edges, x,
+    // few threads per block: the float64 work of a pair is long and serial, so
+    // the pairs are spread over every SM rather than packed onto a few
+    k_pair_eval<<<nblocks(np, 8), 8, 0, ctx->stream>>>(cs.pt, cs.npt, cs.ee, cs.nee, cs.faces, cs.edges, x,
                                                          cs.kappa, cs.dhat, cs.pg, cs.pH);
     ++ctx->launches;
     k_pair_scatter<<<nblocks(16 * (int64_t)np), kBlock, 0, ctx->stream>>>(cs.pt, cs.npt, cs.ee, cs.nee, cs.faces,
@@ -946,7 +1034,11 @@ mls_status mls_set_bodies(mls_ctx* ctx, const int32_t* body, double dhat, double
   cs.hbits = pow2_at_least(2 * cs.ecap);
   if ((st = dalloc(ctx, (void**)&cs.ent, sizeof(int4) * cs.ecap)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&cs.next, sizeof(int) * cs.ecap)) != MLS_OK) return st;
-  if ((st = dalloc(ctx, (void**)&cs.head, sizeof(int) << cs.hbits)) != MLS_OK) return st;
+  if ((st = dalloc(ctx, (void**)&cs.head, sizeof(int) << (cs.hbits + 1))) != MLS_OK) return st;
+  cs.nbody = *std::max_element(body, body + n) + 1;
+  if (cs.nbody <= kMaxBodyBoxes &&
+      (st = dalloc(ctx, (void**)&cs.bbox, sizeof(unsigned long long) * 6 * cs.nbody)) != MLS_OK)
+    return st;
   if ((st = dalloc(ctx, (void**)&cs.boxes, sizeof(double) * 6 * std::max(cs.nf + cs.ne, 1))) != MLS_OK) return st;
   cs.pcap = cs.scap = 2 * (int64_t)(cs.nsv + cs.ne) + 1024;
   void** pb[] = {(void**)&cs.pt, (void**)&cs.ee, (void**)&cs.spt, (void**)&cs.see};

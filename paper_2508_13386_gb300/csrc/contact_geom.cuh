@@ -344,11 +344,14 @@ __device__ __noinline__ void psd_project(double* A, double* V, int k) {
       dia += A[i * 12 + i] * A[i * 12 + i];
       for (int j = i + 1; j < k; ++j) off += A[i * 12 + j] * A[i * 12 + j];
     }
-    if (off <= 1e-32 * dia || off == 0.0) break;
+    // off-diagonal mass below 1e-24 of the diagonal's (1e-12 in norm): the
+    // eigenvalues are then exact to far below the 1e-9 the pairs need, and
+    // rounding keeps a stricter test from ever passing
+    if (off <= 1e-24 * dia || off == 0.0) break;
     for (int p = 0; p < k - 1; ++p)
       for (int q = p + 1; q < k; ++q) {
         const double apq = A[p * 12 + q];
-        if (apq == 0.0) continue;
+        if (apq == 0.0 || apq * apq <= 1e-36 * fabs(A[p * 12 + p] * A[q * 12 + q])) continue;
         const double tau = (A[q * 12 + q] - A[p * 12 + p]) / (2.0 * apq);
         const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
         const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;

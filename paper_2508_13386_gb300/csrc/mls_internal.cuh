@@ -599,6 +599,8 @@ struct ContactState {
   double dhat = 1e-3, kappa = 1e5;   // barrier of the pairs
   double cell0 = 0.0;                // mean rest length of the surface edges
   int spare = 0;                     // spare block slots per surface-vertex row
+  int nbody = 0;                     // bodies (largest label + 1)
+  unsigned long long* bbox = nullptr;  // per-body boxes of the broad phase: [3 nbody] low, [3 nbody] high keys
   // hashed grid: bucket heads, entries {primitive, ix, iy, iz} and chain links
   int* head = nullptr;
   int hbits = 0;
@@ -735,7 +737,6 @@ struct mls_ctx {
   void* cvec = nullptr;            // [r] coarse vectors (solve precision)
   void* cvec2 = nullptr;
   __nv_bfloat16* oz_fwd = nullptr;  // [r][8 x 128] bf16 slices of a Cholesky panel (tensor-core update)
-  __nv_bfloat16* oz_rev = nullptr;  // the same slices in reversed order
   int* oz_e = nullptr;              // [r] row exponents of the panel
   int* umma_err = nullptr;          // set by a tensor-core product whose bounded wait gave up
   double* sms_buf = nullptr;        // Alg. 2 subspace PCG: [r] q, res, z, p and the [m][144] block inverses
@@ -871,6 +872,10 @@ struct GemmEpilogue {
 };
 mls_status gemm_bf16_tn(cudaStream_t stream, int M, int N, int K, const __nv_bfloat16* A, int lda,
                         const __nv_bfloat16* B, int ldb, float* C, int ldc, const GemmEpilogue& ep, int* err);
+// A[i][j] -= (L21 L21^T)[i][j], j <= i < n, on the tensor cores from the
+// bf16 slices of L21's rows (umma.cu; slicing in multilevel.cu)
+mls_status ozaki_syrk(cudaStream_t stream, int n, const __nv_bfloat16* fwd, int opitch, const int* e, double* A,
+                      int lda, int* err);
 mls_status build_galerkin(mls_ctx* ctx);   // U^T H U into the dense Ac only (no factorisation)
 mls_status coarse_apply(mls_ctx* ctx, const void* c_in, void* c_out);
 mls_status sms_pcg(mls_ctx* ctx, const void* b, double rtol, int max_iter, int* iters);

@@ -255,7 +255,6 @@ mls_status basis_upload(mls_ctx* ctx, int m, const double* origins, const int* v
   if ((st = dalloc(ctx, &ctx->cvec2, (size_t)r * vb)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->chol_info, sizeof(int) * 4)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->oz_fwd, sizeof(__nv_bfloat16) * (size_t)r * kOzSlices * kOzPanel)) != MLS_OK) return st;
-  if ((st = dalloc(ctx, (void**)&ctx->oz_rev, sizeof(__nv_bfloat16) * (size_t)r * kOzSlices * kOzPanel)) != MLS_OK) return st;
   if ((st = dalloc(ctx, (void**)&ctx->oz_e, sizeof(int) * (size_t)r)) != MLS_OK) return st;
   if (!ctx->umma_err) {
     if ((st = dalloc(ctx, (void**)&ctx->umma_err, sizeof(int))) != MLS_OK) return st;
@@ -800,17 +799,16 @@ __global__ void k_syrk_tiles(double* __restrict__ A, int r, int k, int ntiles) {
 // r_p = 2^beta r_{p-1} - a_p (exact in float64).  Every slice entry is an
 // integer of magnitude < 2^7, exact in bf16, and a product of two slices
 // summed over at most 1024 terms stays below 2^24, exact in the float32
-// accumulator.  So S_d = sum_{p+q=d} a_p a_q^T, one tensor-core product per
-// d with the slices concatenated along K, is exact, and
+// accumulator.  So S_d = sum_{p+q=d} a_p a_q^T, each a sum of tensor-core
+// products of slice pairs, is exact, and
 //   (L21 L21^T)_ij = 2^(e_i + e_j) sum_d 2^(-beta d) S_d,ij
 // up to the dropped terms p + q > kOzSlices + 1, below 2^-56 relative to the
-// row scales.  Each S_d is scaled exactly by a power of two and subtracted
-// from A22 in float64.
-// slices of the rows of an FP64 block [rows][K] (pitch lda): forward order
-// (slice p at columns p K of fwd) and reversed (slice p at (S - 1 - p) K of
-// rev), row pitch opitch; the row exponents to e
+// row scales.  The S_d are formed together (k_ozaki_syrk, umma.cu), scaled
+// exactly by powers of two, summed and subtracted from A22 in float64.
+// slices of the rows of an FP64 block [rows][K] (pitch lda), slice p at
+// columns p K of fwd (row pitch opitch); the row exponents to e
 __global__ void k_ozaki_split(int rows, int K, const double* __restrict__ A, int lda, int opitch,
-                              __nv_bfloat16* __restrict__ fwd, __nv_bfloat16* __restrict__ rev, int* __restrict__ e) {
+                              __nv_bfloat16* __restrict__ fwd, int* __restrict__ e) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * (blockDim.x >> 5) + warp;
   if (i >= rows) return;
@@ -823,7 +821,6 @@ __global__ void k_ozaki_split(int rows, int K, const double* __restrict__ A, int
   if (mx > 0.0) frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1): every |a_k| < 2^ex
   if (lane == 0) e[i] = ex;
   __nv_bfloat16* f = fwd + (int64_t)i * opitch;
-  __nv_bfloat16* b = rev + (int64_t)i * opitch;
   for (int k = lane; k < K; k += 32) {
     double r = ldexp(a[k], -ex);
 #pragma unroll
@@ -833,7 +830,6 @@ __global__ void k_ozaki_split(int rows, int K, const double* __restrict__ A, int
       r -= t;
       const __nv_bfloat16 v = __double2bfloat16(t);
       f[p * K + k] = v;
-      b[(kOzSlices - 1 - p) * K + k] = v;
     }
   }
 }
@@ -844,23 +840,13 @@ static mls_status ozaki_trailing_update(mls_ctx* ctx, double* A, int r, int c0, 
   if (n <= 0) return MLS_OK;
   const int opitch = kOzSlices * kOzPanel;
   { ++ctx->launches; k_ozaki_split<<<(n + 7) / 8, 256, 0, ctx->stream>>>(n, w, A + (int64_t)r1 * r + c0, r, opitch,
-                                                                        ctx->oz_fwd, ctx->oz_rev, ctx->oz_e); }
+                                                                        ctx->oz_fwd, ctx->oz_e); }
   mls_status st = cuda_check(ctx, cudaGetLastError(), "k_ozaki_split");
   if (st != MLS_OK) return st;
-  for (int d = kOzSlices + 1; d >= 2; --d) {  // least significant first
-    GemmEpilogue ep;
-    ep.acc64 = A + (int64_t)r1 * r + r1;
-    ep.ld64 = r;
-    ep.ea = ctx->oz_e;
-    ep.eb = ctx->oz_e;
-    ep.ebias = kOzBits * d;
-    ep.sign = -1.0;
-    ep.lower = 1;
-    ++ctx->launches;
-    st = gemm_bf16_tn(ctx->stream, n, n, (d - 1) * w, ctx->oz_fwd, opitch, ctx->oz_rev + (kOzSlices - d + 1) * w,
-                      opitch, nullptr, 0, ep, ctx->umma_err);
-    if (st != MLS_OK) return fail(ctx, st, "tensor-core trailing update");
-  }
+  if (w != kOzPanel) return fail(ctx, MLS_EINVAL, "tensor-core trailing update: panel width");
+  ++ctx->launches;
+  st = ozaki_syrk(ctx->stream, n, ctx->oz_fwd, opitch, ctx->oz_e, A + (int64_t)r1 * r + r1, r, ctx->umma_err);
+  if (st != MLS_OK) return fail(ctx, st, "tensor-core trailing update");
   return MLS_OK;
 }
 

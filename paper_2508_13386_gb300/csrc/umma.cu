@@ -184,6 +184,163 @@ __global__ void __launch_bounds__(128, 1) k_gemm_umma(const __grid_constant__ CU
   if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
 }
 
+// ---- split-product trailing update of the coarse Cholesky ------------------------------
+// A22 -= L21 L21^T on its lower triangle from the bf16 slices of L21's rows
+// (the splitting of multilevel.cu: slice p of row i at columns p 128 ..
+// p 128 + 127 of fwd, row exponents e).  One CTA per 128 x 64 tile of A22:
+// the 64-row slices of the tile's columns (all eight, both 64-wide K blocks)
+// stay in shared memory, the 128-row slices of its rows stream through a
+// four-stage ring, and slice p of the rows times slice q of the columns
+// accumulates into tensor-memory accumulator p + q (eight of 64 columns:
+// all 512).  The epilogue scales accumulator d by 2^(e_i + e_j - 7 (d + 2))
+// (exact: integer operations on the float's bits), sums the eight in float64
+// from the least significant up, and subtracts the sum from A22 once, with
+// the tile staged through shared memory so that rows are written whole.  (An
+// exact 128-bit integer sum rounded once measured slower here.)
+constexpr int kOzBM = 128, kOzBN = 64, kOzKB = kOzPanel / 64, kOzStagesA = 4;
+constexpr int kOzTileA = kOzBM * 64 * 2;
+constexpr int kOzTileB = kOzBN * 64 * 2;
+constexpr int kOzSmemB = kOzSlices * kOzKB * kOzTileB;
+constexpr int kOzSmem = kOzSmemB + kOzStagesA * kOzTileA + 1024;
+static_assert(kOzSmem <= 227 * 1024, "split-product update: shared memory");
+static_assert(kOzSlices * kOzBN <= 512, "split-product update: tensor memory");
+
+__global__ void __launch_bounds__(128, 1) k_ozaki_syrk(const __grid_constant__ CUtensorMap tmA,
+                                                       const __grid_constant__ CUtensorMap tmB, int n,
+                                                       const int* __restrict__ e, double* __restrict__ A, int lda,
+                                                       int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sB = base;
+  uint8_t* sA = base + kOzSmemB;
+  __shared__ uint64_t bfull, full_bar[kOzStagesA], empty_bar[kOzStagesA], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kOzBM, n0 = blockIdx.x * kOzBN;
+  if (n0 > m0 + kOzBM - 1) return;  // tile strictly above the diagonal (uniform per CTA)
+  constexpr int na = kOzSlices * kOzKB;
+  if (threadIdx.x == 0) {
+    umma::mbar_init(&bfull, 1);
+    for (int s = 0; s < kOzStagesA; ++s) {
+      umma::mbar_init(&full_bar[s], 1);
+      umma::mbar_init(&empty_bar[s], 1);
+    }
+    umma::mbar_init(&done_bar, 1);
+    umma::mbar_fence_init();
+    s_fail = 0;
+    umma::tma_prefetch_map(&tmA);
+    umma::tma_prefetch_map(&tmB);
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(&tmem_base, 512);
+    umma::tmem_relinquish();
+  }
+  umma::tc_fence_before();
+  __syncthreads();
+  umma::tc_fence_after();
+  const uint32_t tacc = tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    umma::mbar_arrive_expect_tx(&bfull, kOzSmemB);
+    for (int q = 0; q < kOzSlices; ++q)
+      for (int kk = 0; kk < kOzKB; ++kk)
+        umma::tma_load_2d(sB + (q * kOzKB + kk) * kOzTileB, &tmB, &bfull, q * kOzPanel + kk * 64, n0);
+    int issued = 0;
+    bool failed = false;
+    for (int a = 0; a < na; ++a) {
+      const int s = a % kOzStagesA;
+      if (a >= kOzStagesA && !umma::mbar_wait(&empty_bar[s], ((a / kOzStagesA) - 1) & 1, kGemmWaitLimit)) {
+        failed = true;
+        break;
+      }
+      umma::mbar_arrive_expect_tx(&full_bar[s], kOzTileA);
+      umma::tma_load_2d(sA + s * kOzTileA, &tmA, &full_bar[s], (a / kOzKB) * kOzPanel + (a % kOzKB) * 64, m0);
+      ++issued;
+    }
+    if (failed) {
+      s_fail = 1;
+      umma::mbar_wait(&bfull, 0, kGemmWaitLimit);
+      for (int a = issued > kOzStagesA ? issued - kOzStagesA : 0; a < issued; ++a)
+        umma::mbar_wait(&full_bar[a % kOzStagesA], (a / kOzStagesA) & 1, kGemmWaitLimit);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = umma::idesc_bf16_f32(kOzBM, kOzBN);
+    bool ok = umma::mbar_wait(&bfull, 0, kGemmWaitLimit);
+    for (int a = 0; ok && a < na; ++a) {
+      const int s = a % kOzStagesA;
+      if (!umma::mbar_wait(&full_bar[s], (a / kOzStagesA) & 1, kGemmWaitLimit)) {
+        ok = false;
+        break;
+      }
+      umma::tc_fence_after();
+      const int p = a / kOzKB, kk = a % kOzKB;
+      const uint32_t a0 = umma::smem_u32(sA + s * kOzTileA);
+      for (int q = 0; q < kOzSlices - p; ++q) {
+        const uint32_t b0 = umma::smem_u32(sB + (q * kOzKB + kk) * kOzTileB);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          umma::mma_bf16(tacc + (uint32_t)(kOzBN * (p + q)), umma::sdesc_k_sw128(a0 + 32 * k),
+                         umma::sdesc_k_sw128(b0 + 32 * k), idesc, (p | kk | k) ? 1u : 0u);
+      }
+      umma::mma_commit(&empty_bar[s]);
+    }
+    if (!ok) s_fail = 1;
+    umma::mma_commit(&done_bar);
+  }
+  __syncthreads();
+  const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(&done_bar, 0, kGemmWaitLimit) ? 1 : 0);
+  umma::tc_fence_after();
+  if (!ok && lane == 0) s_fail = 1;
+  __syncthreads();
+  if (!s_fail) {
+    const int m = m0 + warp * 32 + lane;
+    const int em = m < n ? e[m] : 0;
+    double* stage = (double*)sA + warp * 32 * 17;  // 32 rows x 16 columns (+1 pad) per warp
+    for (int c0 = 0; c0 < kOzBN && n0 + c0 < n; c0 += 16) {
+      int en[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) en[j] = n0 + c0 + j < n ? e[n0 + c0 + j] : 0;
+      double acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+      for (int d = kOzSlices - 1; d >= 0; --d) {  // least significant first
+        float v[16];
+        umma::tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kOzBN * d + c0), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          // -v 2^(e_i + e_j - 7 (d + 2)) as a double from v's bits (v: an integer below 2^24)
+          const unsigned fb = __float_as_uint(v[j]) ^ 0x80000000u;
+          if (fb & 0x7fffffffu) {
+            const int ex = (int)((fb >> 23) & 0xffu) - 127 + 1023 + em + en[j] - kOzBits * (d + 2);
+            const unsigned long long db = ((unsigned long long)(fb >> 31) << 63) |
+                                          ((unsigned long long)(ex < 1 ? 0 : (ex > 2046 ? 2047 : ex)) << 52) |
+                                          ((unsigned long long)(fb & 0x7fffffu) << 29);
+            acc[j] += __longlong_as_double((long long)db);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j) stage[lane * 17 + j] = acc[j];
+      __syncwarp();
+#pragma unroll 4
+      for (int it = 0; it < 16; ++it) {
+        const int row = 2 * it + (lane >> 4), col = lane & 15;
+        const int mm = m0 + warp * 32 + row, nn = n0 + c0 + col;
+        if (mm < n && nn < n && nn <= mm) A[(int64_t)mm * lda + nn] += stage[row * 17 + col];
+      }
+      __syncwarp();
+    }
+  }
+  umma::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    umma::tc_fence_after();
+    umma::tmem_dealloc(tacc, 512);
+  }
+  if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+}
+
 // ---- host side ------------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -235,6 +392,26 @@ mls_status gemm_bf16_tn(cudaStream_t stream, int M, int N, int K, const __nv_bfl
   if (attr_err != cudaSuccess) return MLS_ECUDA;
   const dim3 grid((N + kGemmBN - 1) / kGemmBN, (M + kGemmBM - 1) / kGemmBM);
   k_gemm_umma<<<grid, 128, kGemmSmem, stream>>>(ma, mb, M, N, K, C, ldc, ep, err);
+  return cudaGetLastError() == cudaSuccess ? MLS_OK : MLS_ECUDA;
+}
+
+// A[i][j] -= (L21 L21^T)[i][j] for j <= i < n from the slices fwd [n][opitch]
+// (slice p at columns p 128) and row exponents e; A row-major with pitch lda
+mls_status ozaki_syrk(cudaStream_t stream, int n, const __nv_bfloat16* fwd, int opitch, const int* e, double* A,
+                      int lda, int* err) {
+  if (n < 1 || !fwd || !e || !A || !err || opitch < kOzSlices * kOzPanel || (opitch % 8) || lda < n) return MLS_EINVAL;
+  CUtensorMap ma, mb;
+  if (!bf16_map(&ma, fwd, n, kOzSlices * kOzPanel, opitch, kOzBM) ||
+      !bf16_map(&mb, fwd, n, kOzSlices * kOzPanel, opitch, kOzBN))
+    return MLS_ECUDA;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [] {
+    attr_err = cudaFuncSetAttribute(k_ozaki_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+  });
+  if (attr_err != cudaSuccess) return MLS_ECUDA;
+  const dim3 grid((n + kOzBN - 1) / kOzBN, (n + kOzBM - 1) / kOzBM);
+  k_ozaki_syrk<<<grid, 128, kOzSmem, stream>>>(ma, mb, n, e, A, lda, err);
   return cudaGetLastError() == cudaSuccess ? MLS_OK : MLS_ECUDA;
 }
 

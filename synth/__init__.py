@@ -21,6 +21,7 @@ from .workloads import (  # noqa: F401
     batched_lattice_scenes,
     tiny_scene,
     two_block_scene,
+    lattice_stack_scene,
     random_sparse_basis,
     mlp_init,
 )

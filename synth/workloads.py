@@ -183,6 +183,37 @@ def two_block_scene(gap: float = 0.01, speed: float = 1.0, seed: int = 0):
     return scene, body
 
 
+def lattice_stack_scene(n: int = 24, gap: float = 0.005, speed: float = 1.0, seed: int = 3):
+    """Two random voxel lattices (grid ``n`` in the unit cube, p = 0.55,
+    materials as ``lattice_scene``, seeds ``seed`` and ``seed + 1``): the
+    lower one 0.5 mm above the ground plane z = 0 at rest, the upper one
+    ``gap`` above it, shifted by (0.3, 0.37) voxels horizontally so that no
+    two parallel surface edges of the two lie within 2 mm of each other,
+    falling at ``speed`` m/s.  Gravity, ground barrier dhat = 1e-3,
+    kappa = 1e5, h = 1/60.  Returns (scene, body) with ``body`` [n] the
+    lattice of each vertex (a mesh-mesh contact workload)."""
+    lo = lattice_scene(n=n, seed=seed, lift=0.0005)
+    hi = lattice_scene(n=n, seed=seed + 1, lift=0.0)
+    top = lo.X[:, 2].max()
+    Xh = hi.X.copy()
+    Xh[:, 2] += top + gap - Xh[:, 2].min()
+    Xh[:, 0] += 0.3 / n
+    Xh[:, 1] += 0.37 / n
+    n0 = lo.n_verts
+    X = np.vstack([lo.X, Xh])
+    tets = np.vstack([lo.tets, hi.tets + n0]).astype(np.int32)
+    mesh = Mesh(X=X, tets=tets, lattice_index=np.vstack([lo.mesh.lattice_index, hi.mesh.lattice_index]),
+                voxel_of_tet=np.concatenate([lo.mesh.voxel_of_tet, hi.mesh.voxel_of_tet]))
+    v0 = np.zeros_like(X)
+    v0[n0:, 2] = -speed
+    body = np.concatenate([np.zeros(n0, np.int64), np.ones(len(X) - n0, np.int64)])
+    scene = Scene(name=f"lattice_stack{n}_s{seed}", mesh=mesh, E=np.concatenate([lo.E, hi.E]),
+                  nu=np.concatenate([lo.nu, hi.nu]), rho=np.concatenate([lo.rho, hi.rho]),
+                  dirichlet=np.zeros(len(X), np.uint8), x0=X.copy(), v0=v0, dt=1.0 / 60.0, contact=True,
+                  meta={"grid": n, "seed": seed, "gap": gap, "speed": speed})
+    return scene, body
+
+
 def random_sparse_basis(X: np.ndarray, m: int, k: int, seed: int):
     """A synthetic sparse handle basis for kernel tests (not the paper's
     construction): ``m`` handle origins at random vertices, each vertex tied

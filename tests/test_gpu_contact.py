@@ -211,3 +211,52 @@ def test_set_bodies_rejects_bad_input():
     sol.upload_basis(origins, vrow, handle, phi)
     with pytest.raises(mls.MLSError):        # after a basis: rejected
         sol.set_bodies(body, s.dhat, s.kappa)
+
+
+def test_stack_pairs_sampled_against_brute_force():
+    """On the stacked-lattice workload (two 12^3 lattices, the upper one
+    lowered into the barrier zone of the lower one, positions jittered) the
+    pairs the grid finds for a sample of 300 surface vertices and 300
+    surface edges are exactly the oracle's brute-force pairs of those
+    primitives with every face or edge of the other body (a box prefilter
+    drops only primitives farther than dhat)."""
+    s, body = synth.lattice_stack_scene(12)
+    x = s.x0.copy()
+    up = body == 1
+    x[up, 2] -= 0.005 - 4e-4
+    x += 5e-5 * np.random.default_rng(4).normal(size=x.shape)
+    sol = _solver(s, body)
+    pt, ee = sol.contact_pairs(dev(x))
+    faces = contact.boundary_faces(s.tets)
+    edges = contact.face_edges(faces)
+    assert len(pt) > 50 and len(ee) > 100
+    r = np.random.default_rng(5)
+    sv = np.unique(faces)
+    in_pt = np.unique(pt[:, 0])
+    vs = np.unique(np.concatenate([r.choice(in_pt, min(200, len(in_pt)), replace=False),
+                                 r.choice(sv, 100, replace=False)]))
+    flo, fhi = x[faces].min(axis=1) - s.dhat, x[faces].max(axis=1) + s.dhat
+    brute = set()
+    for v in vs:
+        cand = np.nonzero(np.all((flo <= x[v]) & (x[v] <= fhi), axis=1) & (body[faces[:, 0]] != body[v]))[0]
+        for k in cand:
+            if contact.point_triangle_distance(x[v], *x[faces[k]]) < s.dhat:
+                brute.add(_key_pt([v, *faces[k]]))
+    found = {_key_pt(q) for q in pt if q[0] in set(vs.tolist())}
+    assert found == brute and len(brute) > 30
+    eidx = {tuple(e): i for i, e in enumerate(edges)}
+    in_ee = np.unique([eidx[tuple(sorted(q[:2]))] for q in ee])
+    es = np.unique(np.concatenate([r.choice(in_ee, min(200, len(in_ee)), replace=False),
+                                 r.choice(len(edges), 100, replace=False)]))
+    elo, ehi = x[edges].min(axis=1), x[edges].max(axis=1)
+    brute = set()
+    for i in es:
+        a, b = edges[i]
+        cand = np.nonzero(np.all((elo <= ehi[i] + s.dhat) & (elo[i] - s.dhat <= ehi), axis=1)
+                          & (body[edges[:, 0]] != body[a]))[0]
+        for j in cand:
+            if contact.edge_edge_distance(x[a], x[b], *x[edges[j]]) < s.dhat:
+                brute.add(_key_ee([a, b, *edges[j]]))
+    sample = {tuple(edges[i]) for i in es}
+    found = {_key_ee(q) for q in ee if tuple(sorted(q[:2])) in sample or tuple(sorted(q[2:])) in sample}
+    assert found == brute and len(brute) > 50
