@@ -313,30 +313,6 @@ __device__ __forceinline__ double bar_b2(double d, double dhat) {
   return -2.0 * log(d / dhat) - 4.0 * r / d + r * r / (d * d);
 }
 
-// kappa (b'' grad d grad d^T + b' Hess d) from d, grad d (gd) and Hess d (in H),
-// projected to the PSD cone in place; g = kappa b' grad d.  Only the rows and
-// columns of the feature's vertices are nonzero, so the projection runs on
-// that 3 nv x 3 nv block (gathered into W, V: workspaces of 144).
-__device__ __forceinline__ void barrier_terms(const cgeom::Feature& F, double d, const double* gd, double kappa,
-                                              double dhat, double* g, double* H, double* W, double* V) {
-  const double b1 = kappa * bar_b1(d, dhat), b2 = kappa * bar_b2(d, dhat);
-  for (int i = 0; i < 12; ++i) g[i] = b1 * gd[i];
-  const int k = 3 * F.nv;
-  for (int a = 0; a < k; ++a) {
-    const int ra = 3 * F.idx[a / 3] + a % 3;
-    for (int b = 0; b < k; ++b) {
-      const int cb = 3 * F.idx[b / 3] + b % 3;
-      W[a * 12 + b] = b2 * gd[ra] * gd[cb] + b1 * H[ra * 12 + cb];
-    }
-  }
-  cgeom::psd_project(W, V, k);
-  for (int q = 0; q < 144; ++q) H[q] = 0.0;
-  for (int a = 0; a < k; ++a) {
-    const int ra = 3 * F.idx[a / 3] + a % 3;
-    for (int b = 0; b < k; ++b) H[ra * 12 + 3 * F.idx[b / 3] + b % 3] = W[a * 12 + b];
-  }
-}
-
 struct CouplingView {
   unsigned long long* key;
   double* val;
@@ -357,14 +333,158 @@ __device__ __forceinline__ int coupling_slot(const CouplingView& C, int i, int j
   return -1;
 }
 
-// one thread per pair: the barrier gradient [12] and projected Hessian
-// [144] of the pair into pg / pH (zero at or beyond dhat)
-__global__ void k_pair_eval(const int2* __restrict__ pt, int npt, const int2* __restrict__ ee, int nee,
-                            const int4* __restrict__ faces, const int4* __restrict__ edges,
-                            const Vec4d* __restrict__ x, double kappa, double dhat, double* __restrict__ pg,
-                            double* __restrict__ pH) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= npt + nee) return;
+// ---- one warp per pair: derivatives by one lane, PSD projection by the warp ----------------
+// The float64 work of a pair is too long and serial for one thread (float64
+// instructions issue at a small fraction of the integer rate here), so a
+// warp evaluates each pair: lane 0 finds the closest feature and the
+// distance derivatives, then the warp forms the barrier Hessian on the
+// feature's 3 nv x 3 nv block and diagonalises it by parallel cyclic Jacobi
+// (Golub and Van Loan, Sec. 8.5): in each round the index pairs of a
+// round-robin tournament are rotated at once (the rotations are disjoint,
+// so J^T A J takes one column pass and one row pass), n - 1 rounds a sweep,
+// until the off-diagonal mass is below 1e-24 of the diagonal's.
+constexpr int kPairWarps = 4;
+
+struct PairWarp {
+  double A[144];   // the block being diagonalised (leading dimension 12)
+  double V[144];   // its eigenvectors
+  double H[144];   // Hess d over the pair's 12 coordinates, then the projected barrier Hessian
+  double gd[12];   // grad d
+  double c[6], s[6];
+  int p[6], q[6];
+  double b1, b2;
+  int ok, k;
+  cgeom::Feature F;
+};
+
+// lane 0: distance, feature and derivatives of the pair P; the warp: the
+// projected barrier Hessian into W.H (12 x 12, zero outside the feature).
+// Returns false (uniformly) when the pair is at or beyond dhat.
+__device__ bool pair_eval_warp(int kind, const D3 (&P)[4], double kappa, double dhat, PairWarp& W, int lane,
+                               double* hd_out) {
+  if (lane == 0) {
+    const double dist = cgeom::pair_distance(kind, P);
+    W.ok = (dist < dhat && dist > 0.0) || hd_out;
+    if (W.ok) {
+      W.F = kind == 0 ? cgeom::pt_feature(P[0], P[1], P[2], P[3]) : cgeom::ee_feature(P[0], P[1], P[2], P[3]);
+      const double d = cgeom::feature_derivatives(W.F, P, W.gd, W.H);
+      W.b1 = kappa * bar_b1(d, dhat);
+      W.b2 = kappa * bar_b2(d, dhat);
+      W.k = 3 * W.F.nv;
+    }
+  }
+  __syncwarp();
+  if (!W.ok) return false;
+  if (hd_out)
+    for (int t = lane; t < 144; t += 32) hd_out[t] = W.H[t];
+  const int k = W.k;
+  const cgeom::Feature F = W.F;
+  const double b1 = W.b1, b2 = W.b2;
+  for (int t = lane; t < k * k; t += 32) {
+    const int a = t / k, b = t % k;
+    const int ra = 3 * F.idx[a / 3] + a % 3, cb = 3 * F.idx[b / 3] + b % 3;
+    W.A[a * 12 + b] = b2 * W.gd[ra] * W.gd[cb] + b1 * W.H[ra * 12 + cb];
+    W.V[a * 12 + b] = a == b ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  const int n = k + (k & 1);  // even order of the tournament (index k stands out when k is odd)
+  const int half = n / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int t = lane; t < k * k; t += 32) {
+      const int a = t / k, b = t % k;
+      const double v = W.A[a * 12 + b];
+      if (a == b) dia += v * v;
+      else if (a < b) off += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if (off <= 1e-24 * dia || off == 0.0) break;
+    for (int r = 0; r < n - 1; ++r) {
+      if (lane < half) {
+        int p, q;
+        if (lane == 0) {
+          p = r;
+          q = n - 1;
+        } else {
+          p = (r + lane) % (n - 1);
+          q = (r - lane + n - 1) % (n - 1);
+        }
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        if (q < k) {
+          const double apq = W.A[p * 12 + q], app = W.A[p * 12 + p], aqq = W.A[q * 12 + q];
+          if (apq != 0.0 && apq * apq > 1e-36 * fabs(app * aqq)) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        W.p[lane] = p;
+        W.q[lane] = q < k ? q : p;  // a pair with the standing-out index does nothing
+        W.c[lane] = c;
+        W.s[lane] = sn;
+      }
+      __syncwarp();
+      for (int t = lane; t < half * k; t += 32) {  // A <- A J and V <- V J (columns p, q)
+        const int m = t / k, row = t % k;
+        const int p = W.p[m], q = W.q[m];
+        if (p == q) continue;
+        const double c = W.c[m], sn = W.s[m];
+        const double arp = W.A[row * 12 + p], arq = W.A[row * 12 + q];
+        W.A[row * 12 + p] = c * arp - sn * arq;
+        W.A[row * 12 + q] = sn * arp + c * arq;
+        const double vrp = W.V[row * 12 + p], vrq = W.V[row * 12 + q];
+        W.V[row * 12 + p] = c * vrp - sn * vrq;
+        W.V[row * 12 + q] = sn * vrp + c * vrq;
+      }
+      __syncwarp();
+      for (int t = lane; t < half * k; t += 32) {  // A <- J^T A (rows p, q)
+        const int m = t / k, col = t % k;
+        const int p = W.p[m], q = W.q[m];
+        if (p == q) continue;
+        const double c = W.c[m], sn = W.s[m];
+        const double apr = W.A[p * 12 + col], aqr = W.A[q * 12 + col];
+        W.A[p * 12 + col] = c * apr - sn * aqr;
+        W.A[q * 12 + col] = sn * apr + c * aqr;
+      }
+      __syncwarp();
+    }
+  }
+  // H = V max(Lambda, 0) V^T scattered to the feature's rows and columns
+  for (int t = lane; t < 144; t += 32) W.H[t] = 0.0;
+  __syncwarp();
+  for (int t = lane; t < k * k; t += 32) {
+    const int a = t / k, b = t % k;
+    if (b < a) continue;
+    double sum = 0.0;
+    for (int m = 0; m < k; ++m) sum += W.V[a * 12 + m] * fmax(W.A[m * 12 + m], 0.0) * W.V[b * 12 + m];
+    const int ra = 3 * F.idx[a / 3] + a % 3, cb = 3 * F.idx[b / 3] + b % 3;
+    W.H[ra * 12 + cb] = sum;
+    W.H[cb * 12 + ra] = sum;
+  }
+  __syncwarp();
+  return true;
+}
+
+// one warp per pair: the barrier gradient [12] and projected Hessian [144]
+// of the pair into pg / pH (zero at or beyond dhat)
+__global__ void __launch_bounds__(32 * kPairWarps) k_pair_eval(const int2* __restrict__ pt, int npt,
+                                                               const int2* __restrict__ ee, int nee,
+                                                               const int4* __restrict__ faces,
+                                                               const int4* __restrict__ edges,
+                                                               const Vec4d* __restrict__ x, double kappa,
+                                                               double dhat, double* __restrict__ pg,
+                                                               double* __restrict__ pH) {
+  __shared__ PairWarp sw[kPairWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int idx = blockIdx.x * kPairWarps + warp;
+  if (idx >= npt + nee) return;  // uniform per warp
+  PairWarp& W = sw[warp];
   const int kind = idx < npt ? 0 : 1;
   int v[4];
   pair_vertices(kind, kind == 0 ? pt[idx] : ee[idx - npt], faces, edges, v);
@@ -372,19 +492,13 @@ __global__ void k_pair_eval(const int2* __restrict__ pt, int npt, const int2* __
   for (int a = 0; a < 4; ++a) P[a] = pos(x, nullptr, 0.0, v[a]);
   double* og = pg + 12 * (int64_t)idx;
   double* oH = pH + 144 * (int64_t)idx;
-  const double dist = cgeom::pair_distance(kind, P);
-  if (!(dist < dhat) || !(dist > 0.0)) {
-    for (int q = 0; q < 12; ++q) og[q] = 0.0;
-    for (int q = 0; q < 144; ++q) oH[q] = 0.0;
+  if (!pair_eval_warp(kind, P, kappa, dhat, W, lane, nullptr)) {
+    if (lane < 12) og[lane] = 0.0;
+    for (int t = lane; t < 144; t += 32) oH[t] = 0.0;
     return;
   }
-  const cgeom::Feature F = kind == 0 ? cgeom::pt_feature(P[0], P[1], P[2], P[3])
-                                     : cgeom::ee_feature(P[0], P[1], P[2], P[3]);
-  double gd[12], g[12], H[144], W[144], V[144];
-  const double d = cgeom::feature_derivatives(F, P, gd, H);
-  barrier_terms(F, d, gd, kappa, dhat, g, H, W, V);
-  for (int q = 0; q < 12; ++q) og[q] = g[q];
-  for (int q = 0; q < 144; ++q) oH[q] = H[q];
+  if (lane < 12) og[lane] = W.b1 * W.gd[lane];
+  for (int t = lane; t < 144; t += 32) oH[t] = W.H[t];
 }
 
 // one thread per (pair, vertex a, vertex b): block (a, b) of the pair's
@@ -623,23 +737,26 @@ __global__ void __launch_bounds__(144) k_galerkin_contact(const int4* __restrict
 
 // ---- per-pair derivatives for testing -------------------------------------------------------
 // pairs given by their vertex positions X [P][4][3]: distance, grad d [12],
-// Hess d [144] and the projected barrier Hessian [144]
-__global__ void k_pair_derivatives(const int* __restrict__ kind, const double* __restrict__ X, int n, double kappa,
-                                   double dhat, double* __restrict__ dist, double* __restrict__ gd,
-                                   double* __restrict__ Hd, double* __restrict__ Hb) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// Hess d [144] and the projected barrier Hessian [144], by the same warp
+// code as the assembly
+__global__ void __launch_bounds__(32 * kPairWarps) k_pair_derivatives(const int* __restrict__ kind,
+                                                                      const double* __restrict__ X, int n,
+                                                                      double kappa, double dhat,
+                                                                      double* __restrict__ dist,
+                                                                      double* __restrict__ gd,
+                                                                      double* __restrict__ Hd,
+                                                                      double* __restrict__ Hb) {
+  __shared__ PairWarp sw[kPairWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x * kPairWarps + warp;
   if (p >= n) return;
+  PairWarp& W = sw[warp];
   D3 P[4];
   for (int a = 0; a < 4; ++a) P[a] = D3{X[12 * p + 3 * a], X[12 * p + 3 * a + 1], X[12 * p + 3 * a + 2]};
-  const int k = kind[p];
-  const cgeom::Feature F = k == 0 ? cgeom::pt_feature(P[0], P[1], P[2], P[3]) : cgeom::ee_feature(P[0], P[1], P[2], P[3]);
-  double g[12], gb[12], H[144], W[144], V[144];
-  const double d = cgeom::feature_derivatives(F, P, g, H);
-  dist[p] = d;
-  for (int q = 0; q < 12; ++q) gd[12 * p + q] = g[q];
-  for (int q = 0; q < 144; ++q) Hd[144 * (int64_t)p + q] = H[q];
-  barrier_terms(F, d, g, kappa, dhat, gb, H, W, V);
-  for (int q = 0; q < 144; ++q) Hb[144 * (int64_t)p + q] = H[q];
+  pair_eval_warp(kind[p], P, kappa, dhat, W, lane, Hd + 144 * (int64_t)p);
+  if (lane == 0) dist[p] = cgeom::pair_distance(kind[p], P);
+  if (lane < 12) gd[12 * p + lane] = W.gd[lane];
+  for (int t = lane; t < 144; t += 32) Hb[144 * (int64_t)p + t] = W.H[t];
 }
 
 // ---- host side -------------------------------------------------------------------------------
@@ -785,10 +902,9 @@ mls_status contact_assemble(mls_ctx* ctx, const Vec4d* x) {
   const CouplingView C{cs.ckey, cs.cval, cs.ccap - 1, cs.cnt + kCntFlags};
   if (np > 0) {
     ++ctx->launches;
-    // few threads per block: the float64 work of a pair is long and serial, so
-    // the pairs are spread over every SM rather than packed onto a few
-    k_pair_eval<<<nblocks(np, 8), 8, 0, ctx->stream>>>(cs.pt, cs.npt, cs.ee, cs.nee, cs.faces, cs.edges, x,
-                                                         cs.kappa, cs.dhat, cs.pg, cs.pH);
+    k_pair_eval<<<nblocks(np, kPairWarps), 32 * kPairWarps, 0, ctx->stream>>>(cs.pt, cs.npt, cs.ee, cs.nee, cs.faces,
+                                                                              cs.edges, x, cs.kappa, cs.dhat, cs.pg,
+                                                                              cs.pH);
     ++ctx->launches;
     k_pair_scatter<<<nblocks(16 * (int64_t)np), kBlock, 0, ctx->stream>>>(cs.pt, cs.npt, cs.ee, cs.nee, cs.faces,
                                                                           cs.edges, ctx->pinned, cs.pg, cs.pH,
@@ -1104,7 +1220,8 @@ mls_status mls_contact_pair_derivatives(const int32_t* kind, const double* X, in
   if (n < 0 || (n > 0 && (!kind || !X || !dist || !grad || !hess_d || !hess_b)) || !(dhat > 0) || !(kappa > 0))
     return MLS_EINVAL;
   if (n == 0) return MLS_OK;
-  k_pair_derivatives<<<nblocks(n, 64), 64>>>(kind, X, n, kappa, dhat, dist, grad, hess_d, hess_b);
+  k_pair_derivatives<<<nblocks(n, kPairWarps), 32 * kPairWarps>>>(kind, X, n, kappa, dhat, dist, grad, hess_d,
+                                                                   hess_b);
   if (cudaGetLastError() != cudaSuccess) return MLS_ECUDA;
   return cudaDeviceSynchronize() == cudaSuccess ? MLS_OK : MLS_ECUDA;
 }

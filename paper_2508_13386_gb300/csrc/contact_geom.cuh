@@ -266,9 +266,9 @@ __device__ __forceinline__ double form_line(D3 e, D3 d, double* g, double* H) {
 
 // Distance d of the pair's feature with grad d [12] and Hess d [144] over
 // the pair's 12 stacked coordinates (zero outside the feature's vertices).
-// Kept out of line, like psd_project: inlined into the pair kernel of the
-// assembly, the projected Hessians came out wrong while the same code in the
-// derivative test kernel was right; out of line both match the oracle.
+// Kept out of line: inlined into the pair kernel of the assembly, the
+// projected Hessians came out wrong while the same code in the derivative
+// test kernel was right; out of line both match the oracle.
 __device__ __noinline__ double feature_derivatives(const Feature& F, const D3 (&P)[4], double* gd, double* Hd) {
   double gy[9], Hy[81];
   int nb;
@@ -329,58 +329,6 @@ __device__ __noinline__ double feature_derivatives(const Feature& F, const D3 (&
           Hd[(3 * F.idx[v] + c) * 12 + 3 * F.idx[w] + e] = s * i2d - gx[3 * v + c] * gx[3 * w + e] * i4d3;
         }
   return d;
-}
-
-// ---- projection to the positive semi-definite cone --------------------------------------
-// In place on the symmetric k x k matrix A (row-major, leading dimension 12):
-// cyclic Jacobi rotations to diagonal form (Golub and Van Loan, Sec. 8.5),
-// then A <- V max(Lambda, 0) V^T.  V: workspace of 144 doubles.
-__device__ __noinline__ void psd_project(double* A, double* V, int k) {
-  for (int i = 0; i < k; ++i)
-    for (int j = 0; j < k; ++j) V[i * 12 + j] = i == j ? 1.0 : 0.0;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int i = 0; i < k; ++i) {
-      dia += A[i * 12 + i] * A[i * 12 + i];
-      for (int j = i + 1; j < k; ++j) off += A[i * 12 + j] * A[i * 12 + j];
-    }
-    // off-diagonal mass below 1e-24 of the diagonal's (1e-12 in norm): the
-    // eigenvalues are then exact to far below the 1e-9 the pairs need, and
-    // rounding keeps a stricter test from ever passing
-    if (off <= 1e-24 * dia || off == 0.0) break;
-    for (int p = 0; p < k - 1; ++p)
-      for (int q = p + 1; q < k; ++q) {
-        const double apq = A[p * 12 + q];
-        if (apq == 0.0 || apq * apq <= 1e-36 * fabs(A[p * 12 + p] * A[q * 12 + q])) continue;
-        const double tau = (A[q * 12 + q] - A[p * 12 + p]) / (2.0 * apq);
-        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-        const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-        for (int r = 0; r < k; ++r) {  // A <- A J (columns p, q)
-          const double arp = A[r * 12 + p], arq = A[r * 12 + q];
-          A[r * 12 + p] = c * arp - s * arq;
-          A[r * 12 + q] = s * arp + c * arq;
-        }
-        for (int r = 0; r < k; ++r) {  // A <- J^T A (rows p, q)
-          const double apr = A[p * 12 + r], aqr = A[q * 12 + r];
-          A[p * 12 + r] = c * apr - s * aqr;
-          A[q * 12 + r] = s * apr + c * aqr;
-        }
-        for (int r = 0; r < k; ++r) {  // V <- V J
-          const double vrp = V[r * 12 + p], vrq = V[r * 12 + q];
-          V[r * 12 + p] = c * vrp - s * vrq;
-          V[r * 12 + q] = s * vrp + c * vrq;
-        }
-      }
-  }
-  double lam[12];
-  for (int i = 0; i < k; ++i) lam[i] = fmax(A[i * 12 + i], 0.0);
-  for (int i = 0; i < k; ++i)
-    for (int j = i; j < k; ++j) {
-      double s = 0.0;
-      for (int m = 0; m < k; ++m) s += V[i * 12 + m] * lam[m] * V[j * 12 + m];
-      A[i * 12 + j] = s;
-      A[j * 12 + i] = s;
-    }
 }
 
 }  // namespace cgeom
