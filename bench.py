@@ -95,9 +95,10 @@ def parse():
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
                     help="1: PCG iterations in one persistent cooperative kernel per solve")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="persistent kernel blocks per SM (0: library default)")
-    ap.add_argument("--workload", default="lattice", choices=["lattice", "batch64"],
+    ap.add_argument("--workload", default="lattice", choices=["lattice", "batch64", "stack"],
                     help="lattice: the 220K-tet scene (the metric); batch64: 64 independent lattices "
-                         "of 2K-60K tets in one batched solve")
+                         "of 2K-60K tets in one batched solve; stack: the two-lattice stack with mesh-mesh "
+                         "contact alone (--steps timed steps)")
     ap.add_argument("--batch-precond", default="two_level", choices=["two_level", "jacobi"],
                     help="batch64: per-mesh SMS bases with the two-level cycle, or block Jacobi")
     ap.add_argument("--profile-run", action="store_true",
@@ -452,6 +453,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "stack":
+        return run_stack(args)
     import torch
     import torch.distributed as dist
 
@@ -789,6 +792,28 @@ def main():
     print(json.dumps(line))
     if world > 1:
         dist.barrier()
+
+
+def run_stack(args):
+    """The mesh-mesh contact workload alone (contact_arm with --steps timed
+    steps after one warm-up step): one JSON line.  Rank 0 runs it; other
+    ranks exit (the stack is one scene)."""
+    import torch
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    args.contact_steps = args.steps
+    r = contact_arm(args, dev, stream, flush)
+    line = {"metric": "timesteps/s, two-lattice stack with mesh-mesh contact", "value": r["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32+f64", "bf16": "bf16+f32+f64", "fp64": "f64"}[args.precision],
+            "data": "synthetic", "config": {"workload": r["workload"], "l2": "flushed before every timed step"},
+            "mesh_contact": r}
+    print(json.dumps(line))
 
 
 def contact_arm(args, dev, stream, flush):

@@ -192,11 +192,18 @@ __global__ void __launch_bounds__(128, 1) k_gemm_umma(const __grid_constant__ CU
 // stay in shared memory, the 128-row slices of its rows stream through a
 // four-stage ring, and slice p of the rows times slice q of the columns
 // accumulates into tensor-memory accumulator p + q (eight of 64 columns:
-// all 512).  The epilogue scales accumulator d by 2^(e_i + e_j - 7 (d + 2))
-// (exact: integer operations on the float's bits), sums the eight in float64
-// from the least significant up, and subtracts the sum from A22 once, with
-// the tile staged through shared memory so that rows are written whole.  (An
-// exact 128-bit integer sum rounded once measured slower here.)
+// all 512).  The epilogue sums accumulators 0..3 and 4..7 exactly in two
+// 64-bit integers, scales each by a power of two, adds them in float64 (one
+// rounding) and subtracts the result from A22 once; the tile's old values
+// are loaded before the accumulators are read, and the tile is staged
+// through shared memory so that rows are written whole.
+// d 2^k for a double d that is zero or an integer below 2^53 in magnitude
+// and a scaled result in the normal range: the exponent field moved by k
+__device__ __forceinline__ double pow2_scale(double d, int k) {
+  if (d == 0.0) return 0.0;
+  return __longlong_as_double(__double_as_longlong(d) + ((long long)k << 52));
+}
+
 constexpr int kOzBM = 128, kOzBN = 64, kOzKB = kOzPanel / 64, kOzStagesA = 4;
 constexpr int kOzTileA = kOzBM * 64 * 2;
 constexpr int kOzTileB = kOzBN * 64 * 2;
@@ -301,33 +308,48 @@ __global__ void __launch_bounds__(128, 1) k_ozaki_syrk(const __grid_constant__ C
       int en[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) en[j] = n0 + c0 + j < n ? e[n0 + c0 + j] : 0;
-      double acc[16];
+      // this chunk's old values of A22, loaded now so that their latency
+      // hides behind the accumulator reads and the sums below
+      double old[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = 0.0;
-      for (int d = kOzSlices - 1; d >= 0; --d) {  // least significant first
+      for (int it = 0; it < 16; ++it) {
+        const int row = 2 * it + (lane >> 4), col = lane & 15;
+        const int mm = m0 + warp * 32 + row, nn = n0 + c0 + col;
+        old[it] = (mm < n && nn < n && nn <= mm) ? A[(int64_t)mm * lda + nn] : 0.0;
+      }
+      // S_0..S_3 and S_4..S_7 summed exactly in two 64-bit integers
+      // (sum_d S_d 2^(7 (3 - d)) stays below 2^46), then each scaled by a power
+      // of two and added in float64 once
+      long long hi[16], lo[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) hi[j] = lo[j] = 0;
+      for (int d = 0; d < kOzSlices; ++d) {
         float v[16];
         umma::tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kOzBN * d + c0), v);
+        const int sh = kOzBits * ((kOzSlices / 2 - 1) - (d % (kOzSlices / 2)));
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          // -v 2^(e_i + e_j - 7 (d + 2)) as a double from v's bits (v: an integer below 2^24)
-          const unsigned fb = __float_as_uint(v[j]) ^ 0x80000000u;
-          if (fb & 0x7fffffffu) {
-            const int ex = (int)((fb >> 23) & 0xffu) - 127 + 1023 + em + en[j] - kOzBits * (d + 2);
-            const unsigned long long db = ((unsigned long long)(fb >> 31) << 63) |
-                                          ((unsigned long long)(ex < 1 ? 0 : (ex > 2046 ? 2047 : ex)) << 52) |
-                                          ((unsigned long long)(fb & 0x7fffffu) << 29);
-            acc[j] += __longlong_as_double((long long)db);
-          }
+          const long long t = (long long)__float2int_rz(v[j]) << sh;
+          if (d < kOzSlices / 2) hi[j] += t;
+          else lo[j] += t;
         }
+      }
+      double acc[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        // -(hi 2^(e - 35) + lo 2^(e - 63)), e = e_i + e_j: exact scalings, one rounding
+        const int e = em + en[j];
+        acc[j] = -(pow2_scale((double)hi[j], e - kOzBits * (kOzSlices / 2 + 1)) +
+                   pow2_scale((double)lo[j], e - kOzBits * (kOzSlices + 1)));
       }
 #pragma unroll
       for (int j = 0; j < 16; ++j) stage[lane * 17 + j] = acc[j];
       __syncwarp();
-#pragma unroll 4
+#pragma unroll
       for (int it = 0; it < 16; ++it) {
         const int row = 2 * it + (lane >> 4), col = lane & 15;
         const int mm = m0 + warp * 32 + row, nn = n0 + c0 + col;
-        if (mm < n && nn < n && nn <= mm) A[(int64_t)mm * lda + nn] += stage[row * 17 + col];
+        if (mm < n && nn < n && nn <= mm) A[(int64_t)mm * lda + nn] = old[it] + stage[row * 17 + col];
       }
       __syncwarp();
     }
