@@ -50,7 +50,7 @@ REF_NEWTON = 11
 # cold-cache ncu capture inside the timed step) of the dominant kernel on the
 # 41^3 lattice, keyed by (kernel, precision); valid for the kernel version it
 # was taken on and reported as null for anything else
-MEASURED_TRAFFIC = {}  # the product kernel's opening step changed (scale-safe float ratios) after the last capture
+MEASURED_TRAFFIC = {("k_pcg_spmv", "fp32", 41): 46755584}
 METRIC = "timesteps/s at 220K tets: plain FP64 vs mixed+learned PCG at 1e-4 disp error"
 UNIT = "timesteps/s"
 
@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--contact-steps", type=int, default=4,
                     help="steps timed on the two-lattice stack with mesh-mesh contact (0 skips the arm)")
     ap.add_argument("--contact-grid", type=int, default=24, help="lattice grid of each body of the stack")
+    ap.add_argument("--cubature-steps", type=int, default=0,
+                    help="steps timed with the cubature coarse operator (Sec. 3.8; its host precompute takes "
+                         "minutes on the lattice, so the default run leaves it out)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end pass")
     ap.add_argument("--persistent", type=int, default=0, choices=[0, 1],
@@ -729,6 +732,9 @@ def main():
         # the mixed step from the timed start state against the oracle
         dxm, _ = ours.newton_step(x_s.clone(), v_s.clone(), h)
         oracle_err = oracle_error_estimate(scene, xs_h, vs_h, xs_h + dxm.cpu().numpy(), threads)
+    cub_res = None
+    if not args.profile_run and args.cubature_steps > 0 and rank == 0:
+        cub_res = cubature_arm(args, scene, B, make, x_s, v_s, flush, fp64, stream)
     contact_res = None
     if not args.profile_run and args.contact_steps > 0 and rank == 0:
         contact_res = contact_arm(args, dev, stream, flush)
@@ -771,6 +777,7 @@ def main():
         "learned": learned_res,
         "paper_direction": paper,
         "mesh_contact": contact_res,
+        "cubature": cub_res,
         "fp64_plain": {"value": 1e3 / float(np.mean(fp64_ms)) if fp64_ms else None, "unit": UNIT,
                        "ms_per_step": float(np.mean(fp64_ms)) if fp64_ms else None,
                        "steps": len(fp64_ms),
@@ -792,6 +799,56 @@ def main():
     print(json.dumps(line))
     if world > 1:
         dist.barrier()
+
+
+def cubature_arm(args, scene, B, make, x_s, v_s, flush, fp64, stream):
+    """The headline arm's settings with the coarse operator built from the
+    cubature H (Sec. 3.8; cubature.build_cubature: modal moment fitting,
+    Alg. 3) on the same steps: host precompute time, elements kept, ms per
+    step, kernel classes of one step with a coarse build, and the first
+    step's displacement error against the FP64 GPU path."""
+    import torch
+    from paper_2508_13386_gb300 import cubature
+    t0 = time.perf_counter()
+    C = cubature.build_cubature(scene.X, scene.tets, B, seed=0)
+    build_s = time.perf_counter() - t0
+    sol = make(args.precision, "two_level")
+    sol.upload_cubature(C["scale"])
+    h = scene.dt
+    x, v = x_s.clone(), v_s.clone()
+    dx = torch.empty_like(x)
+    dxc, _ = sol.newton_step(x_s.clone(), v_s.clone(), h)
+    err = None
+    if fp64 is not None:
+        dx64, _ = fp64.newton_step(x_s.clone(), v_s.clone(), h)
+        err = float(torch.linalg.norm(dxc - dx64) / torch.linalg.norm(dx64))
+    sol.set_options()
+    ms, stats = [], []
+    for k in range(args.cubature_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = sol.newton_step(x, v, h, dx=dx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+        v.copy_(dx / h)
+        x.add_(dx)
+    sol.set_options()
+    sol.profile_enable(["galerkin", "cholesky"])
+    sol.newton_step(x_s.clone(), v_s.clone(), h)
+    torch.cuda.synchronize()
+    prof = sol.profile_read()
+    sol.profile_enable([])
+    sol.close()
+    return {"value": 1e3 / float(np.mean(ms)), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
+            "step_ms": [round(t, 3) for t in ms], "steps": len(ms),
+            "elements": int(len(C["elem"])), "of_tets": int(scene.n_tets), "host_build_s": build_s,
+            "pcg_iters_per_step": float(np.mean([s["pcg_iters"] for s in stats])),
+            "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in stats])),
+            "disp_err_vs_fp64_first_step": err,
+            "coarse_build_ms": {k: round(t, 3) for k, (t, n) in prof.items() if n}}
 
 
 def run_stack(args):

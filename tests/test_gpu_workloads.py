@@ -69,18 +69,17 @@ def test_beam_timestep_with_cubature_coarse_operator(beam):
 def test_beam_bf16_reports_indefinite_operator(beam):
     """bfloat16 keeps 8 mantissa bits: with E = 1e9 next to E = 1e5 the
     rounded H is indefinite (its rounding error exceeds the mass term in the
-    stiff blocks' rigid modes), and the library must say so with a status
-    instead of returning a wrong step."""
+    stiff blocks' rigid modes).  The coarse operator, summed in float64 from
+    the stored H, still factors, and PCG meets the non-positive curvature:
+    the library reports MLS_ENONFINITE (-7, a PCG breakdown) instead of
+    returning a wrong step."""
     import paper_2508_13386_gb300 as mls
     s, p, x_o, B = beam
     solver = solver_for(s, precision="bf16", preconditioner="two_level", newton_tol=1e-6)
     solver.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
-    try:
-        dx, stats = solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
-    except mls.MLSError as e:
-        assert e.status in (-6, -7), e
-    else:
-        assert rel_disp_error(s.x0 + host(dx), x_o, s.x0) <= 1e-4
+    with pytest.raises(mls.MLSError) as e:
+        solver.newton_step(dev(s.x0), dev(s.v0), s.dt)
+    assert e.value.status == -7 and "PCG breakdown" in str(e.value)
 
 
 def test_beam_two_level_cuts_pcg_iterations(beam):
