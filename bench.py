@@ -818,7 +818,7 @@ def cubature_arm(args, scene, B, make, x_s, v_s, flush, fp64, stream):
     x, v = x_s.clone(), v_s.clone()
     dx = torch.empty_like(x)
     dxc, _ = sol.newton_step(x_s.clone(), v_s.clone(), h)
-    err = None
+    err, dx64 = None, None
     if fp64 is not None:
         dx64, _ = fp64.newton_step(x_s.clone(), v_s.clone(), h)
         err = float(torch.linalg.norm(dxc - dx64) / torch.linalg.norm(dx64))
@@ -842,8 +842,41 @@ def cubature_arm(args, scene, B, make, x_s, v_s, flush, fp64, stream):
     prof = sol.profile_read()
     sol.profile_enable([])
     sol.close()
+    # the paper's own direction (Alg. 1, Alg. 2) solves with the coarse
+    # operator: the same steps with and without the cubature
+    import paper_2508_13386_gb300 as mls
+    paper = {}
+    for tag, use in (("without", False), ("with", True)):
+        pap = mls.Solver(precision=args.precision, preconditioner="two_level", cycle=args.cycle, omega=args.omega,
+                         coarse_refresh=args.coarse_refresh, direction="paper", refine_iters=20, paper_tol=1e-3,
+                         stream=stream)
+        pap.setup_scene(scene)
+        pap.upload_basis(B["origins"], B["vrow"], B["handle"], B["phi"])
+        if use:
+            pap.upload_cubature(C["scale"])
+        dxp, _ = pap.newton_step(x_s.clone(), v_s.clone(), h)
+        perr = float(torch.linalg.norm(dxp - dx64) / torch.linalg.norm(dx64)) if fp64 is not None else None
+        xp, vp = x_s.clone(), v_s.clone()
+        pms, pst = [], []
+        for k in range(args.cubature_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = pap.newton_step(xp, vp, h, dx=dx)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pms.append(e0.elapsed_time(e1))
+            pst.append(st)
+            vp.copy_(dx / h)
+            xp.add_(dx)
+        pap.close()
+        paper[tag] = {"value": 1e3 / float(np.mean(pms)), "ms_per_step": float(np.mean(pms)),
+                      "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in pst])),
+                      "cg_iters_per_step": float(np.mean([s["pcg_iters"] for s in pst])),
+                      "disp_err_vs_fp64_first_step": perr}
     return {"value": 1e3 / float(np.mean(ms)), "unit": UNIT, "ms_per_step": float(np.mean(ms)),
             "step_ms": [round(t, 3) for t in ms], "steps": len(ms),
+            "paper_direction": paper,
             "elements": int(len(C["elem"])), "of_tets": int(scene.n_tets), "host_build_s": build_s,
             "pcg_iters_per_step": float(np.mean([s["pcg_iters"] for s in stats])),
             "newton_iters_per_step": float(np.mean([s["newton_iters"] for s in stats])),

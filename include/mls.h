@@ -366,6 +366,13 @@ mls_status mls_build_coarse(mls_ctx* ctx);
 /* Copy A_c (HOST, [12m][12m] float64, before factorisation) out. */
 mls_status mls_get_coarse(mls_ctx* ctx, double* A);
 
+/* Copy the Cholesky factor of the last coarse build out (stage entry point,
+ * for testing the factorisation): L (HOST, [12m][12m] float64, row-major)
+ * receives the lower triangle of L with L L^T = A_c (1 + sigma diag, see
+ * mls_coarse_shift); the strict upper triangle is set to zero.
+ * MLS_EINVAL without a factored coarse operator. */
+mls_status mls_get_coarse_factor(mls_ctx* ctx, double* L);
+
 /* *sigma (HOST) = the relative diagonal shift of the current coarse factor:
  * 0 when U^T H U factored as built, else the sigma of the retry that
  * succeeded (see mls_build_coarse).  MLS_EINVAL for a null argument. */

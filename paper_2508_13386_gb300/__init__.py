@@ -302,6 +302,13 @@ class Solver:
         self._check(self._l.mls_smoother_omega(self._ctx, C.byref(om), C.byref(lm)))
         return om.value, lm.value
 
+    def get_coarse_factor(self):
+        """Lower Cholesky factor L of the last coarse build (mls_get_coarse_factor)."""
+        r = 12 * self.m
+        L = np.zeros((r, r))
+        self._check(self._l.mls_get_coarse_factor(self._ctx, L.ctypes.data_as(C.c_void_p)))
+        return L
+
     def coarse_shift(self):
         """Relative diagonal shift of the current coarse factor (0: none); see mls_coarse_shift."""
         sig = C.c_double()

@@ -101,6 +101,7 @@ SIGNATURES = {
     "mls_build_coarse": [_P],
     "mls_get_coarse": [_P, _P],
     "mls_coarse_shift": [_P, _P],
+    "mls_get_coarse_factor": [_P, _P],
     "mls_energy": [_P, _P, _P, _D, C.POINTER(_D), C.POINTER(_I)],
     "mls_ccd_bound": [_P, _P, _P, C.POINTER(_D)],
     "mls_set_bodies": [_P, _P, _D, _D, _I32],

@@ -1323,6 +1323,19 @@ mls_status mls_get_coarse(mls_ctx* ctx, double* A) {
   return cuda_check(ctx, cudaMemcpy(A, ctx->Acopy, sizeof(double) * r * r, cudaMemcpyDeviceToHost), "Ac readback");
 }
 
+mls_status mls_get_coarse_factor(mls_ctx* ctx, double* L) {
+  mls_status st = check_mesh(ctx);
+  if (st != MLS_OK) return st;
+  if (!L) return fail(ctx, MLS_EINVAL, "null pointer");
+  if (!ctx->has_basis || !ctx->coarse_ready || !ctx->Ac) return fail(ctx, MLS_EINVAL, "no coarse factor");
+  const int r = 12 * ctx->basis.m;
+  st = cuda_check(ctx, cudaMemcpy(L, ctx->Ac, sizeof(double) * r * r, cudaMemcpyDeviceToHost), "factor readback");
+  if (st != MLS_OK) return st;
+  for (int i = 0; i < r; ++i)
+    for (int j = i + 1; j < r; ++j) L[(size_t)i * r + j] = 0.0;
+  return MLS_OK;
+}
+
 mls_status mls_energy(mls_ctx* ctx, const double* x, const double* d, double alpha, double* E, int* feasible) {
   mls_status st = check_mesh(ctx);
   if (st != MLS_OK) return st;

@@ -401,9 +401,10 @@ def test_two_level_apply_many_coarse_tiles(precision, tol):
 def test_tensor_core_coarse_factor_float64_accuracy():
     """A 1,320 x 1,320 coarse operator (110 handles; 42 tiles of 32, ten
     128-wide panels whose rank-128 trailing updates are exact sums of bf16
-    slice products on the tensor cores, E in [1e5, 1e9]): the FP64 two-level
-    apply, which solves with the factor and its inverse, matches the
-    oracle's dense solve to 1e-9, as a float64 factorisation must."""
+    slice products on the tensor cores, E in [1e5, 1e9]): the factor's
+    backward error is below 1e-14 r, and the FP64 two-level apply, which
+    solves with the factor and its inverse, matches the oracle's dense solve
+    to 1e-9, as a float64 factorisation must."""
     s = synth.tiny_scene(16, 12, 8, seed=23, E_range=(1e5, 1e9), pinned=False)
     p = ip.Problem(s)
     origins, vrow, handle, phi = synth.random_sparse_basis(s.X, m=110, k=4, seed=9)
@@ -413,6 +414,11 @@ def test_tensor_core_coarse_factor_float64_accuracy():
     solver.assemble(dev(p.x_tilde), dev(s.x0), dev(s.v0), s.dt)
     solver.build_coarse()
     assert solver.coarse_shift() == 0.0
+    # the factor itself: backward error ||L L^T - A|| / ||A|| <= 1e-14 r
+    A = solver.get_coarse()
+    L = solver.get_coarse_factor()
+    r = A.shape[0]
+    assert np.linalg.norm(L @ L.T - A) <= 1e-14 * r * np.linalg.norm(A)
     H = p.hessian(p.x_tilde)
     Ac = subspace.galerkin(H, U)
     for seed in range(2):
