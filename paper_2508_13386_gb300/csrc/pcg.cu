@@ -94,9 +94,14 @@ __device__ __forceinline__ void spmv_quad(const SellView& A, const MT* __restric
 // during a solve, so this may run before chain_wait(), while the previous
 // kernel finishes); after the wait quad_gather() and quad_combine() below
 // finish the rows.
+// resident blocks of 128 threads per SM the row-quad kernels are compiled
+// for: 12 in float32 (40 registers; measured 8% faster per product than 8
+// blocks with four slots loaded ahead), 8 in float64 (wider values)
+template <typename VT> constexpr int kQuadBlocks = sizeof(VT) == 4 ? 12 : 8;
+
 template <typename VT>
 struct QuadH {
-  static constexpr int PF = sizeof(VT) == 4 ? 4 : 2;   // slots per lane loaded ahead (register budget)
+  static constexpr int PF = 2;   // slots per lane loaded ahead (register budget, see kQuadBlocks)
   int len, rl, part;
   int64_t g0;
   int c[PF];
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 16) k_spmv(SellView A, const 
 
 // out = b - H x
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_residual(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, kQuadBlocks<VT>) k_residual(SellView A, const MT* __restrict__ val,
                                                               const Vec4<VT>* __restrict__ b,
                                                               const Vec4<VT>* __restrict__ x,
                                                               Vec4<VT>* __restrict__ out,
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(int n, const Vec4<VT>* __re
 // it) r.zout goes to the order-independent sum that opens iteration it + 1;
 // on the application before the loop (first = 1) a grid sum sets rz_0.
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_post_smooth_rz(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, kQuadBlocks<VT>) k_post_smooth_rz(SellView A, const MT* __restrict__ val,
                                                                     const Vec4<VT>* __restrict__ r,
                                                                     const Vec4<VT>* __restrict__ z2,
                                                                     const VT* __restrict__ dinv, VT omega,
@@ -329,7 +334,7 @@ __global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_post_smooth_rz(SellView 
 // stops on convergence, the iteration cap or breakdown; block 0 publishes
 // them.
 template <typename VT, typename MT>
-__global__ void __launch_bounds__(32 * kSpmvWarps, 8) k_pcg_spmv(SellView A, const MT* __restrict__ val,
+__global__ void __launch_bounds__(32 * kSpmvWarps, kQuadBlocks<VT>) k_pcg_spmv(SellView A, const MT* __restrict__ val,
                                                               const Vec4<VT>* __restrict__ z, Vec4<VT>* __restrict__ p,
                                                               Vec4<VT>* __restrict__ q, int it,
                                                               unsigned long long* __restrict__ fix,
