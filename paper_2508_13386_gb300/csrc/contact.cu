@@ -336,54 +336,66 @@ __device__ __forceinline__ int coupling_slot(const CouplingView& C, int i, int j
 // ---- one warp per pair: derivatives by one lane, PSD projection by the warp ----------------
 // The float64 work of a pair is too long and serial for one thread (float64
 // instructions issue at a small fraction of the integer rate here), so a
-// warp evaluates each pair: lane 0 finds the closest feature and the
-// distance derivatives, then the warp forms the barrier Hessian on the
-// feature's 3 nv x 3 nv block and diagonalises it by parallel cyclic Jacobi
-// (Golub and Van Loan, Sec. 8.5): in each round the index pairs of a
-// round-robin tournament are rotated at once (the rotations are disjoint,
-// so J^T A J takes one column pass and one row pass), n - 1 rounds a sweep,
-// until the off-diagonal mass is below 1e-24 of the diagonal's.
+// warp evaluates each pair.  Lane 0 finds the closest feature and the
+// distance's derivatives in the feature's edge vectors with the thin QR
+// factors of their map (contact_geom.cuh, feature_reduced); the warp forms
+// the barrier Hessian's reduced matrix N = R M R^T (order 3 nb: 9, 6 or 3)
+// and diagonalises it by parallel cyclic Jacobi (Golub and Van Loan,
+// Sec. 8.5): in each round the index pairs of a round-robin tournament are
+// rotated at once (the rotations are disjoint, so J^T A J takes one column
+// pass and one row pass), n - 1 rounds a sweep, until the off-diagonal mass
+// is below 1e-24 of the diagonal's; then Q N_+ Q^T is the projected 12 x 12
+// pair Hessian.
 constexpr int kPairWarps = 4;
 
 struct PairWarp {
-  double A[144];   // the block being diagonalised (leading dimension 12)
-  double V[144];   // its eigenvectors
-  double H[144];   // Hess d over the pair's 12 coordinates, then the projected barrier Hessian
-  double gd[12];   // grad d
+  double A[144];   // N being diagonalised (leading dimension 12), then the projected pair Hessian
+  double V[144];   // N's eigenvectors
+  double H[144];   // N_+
+  double gx[12];   // barrier gradient over the pair's 12 coordinates
+  double lam[12];  // N's eigenvalues clamped at zero
   double c[6], s[6];
   int p[6], q[6];
   double b1, b2;
   int ok, k;
   cgeom::Feature F;
+  cgeom::Reduced Rd;
 };
 
-// lane 0: distance, feature and derivatives of the pair P; the warp: the
-// projected barrier Hessian into W.H (12 x 12, zero outside the feature).
-// Returns false (uniformly) when the pair is at or beyond dhat.
+// lane 0: distance, feature and reduced derivatives of the pair P; the warp:
+// the projected barrier Hessian into W.A (12 x 12, zero outside the
+// feature) and the barrier gradient into W.gx.  Returns false (uniformly)
+// when the pair is at or beyond dhat.  With hd_out / gd_out (testing), lane
+// 0 also writes grad d and Hess d over the 12 coordinates there.
 __device__ bool pair_eval_warp(int kind, const D3 (&P)[4], double kappa, double dhat, PairWarp& W, int lane,
-                               double* hd_out) {
+                               double* hd_out, double* gd_out) {
   if (lane == 0) {
     const double dist = cgeom::pair_distance(kind, P);
     W.ok = (dist < dhat && dist > 0.0) || hd_out;
     if (W.ok) {
       W.F = kind == 0 ? cgeom::pt_feature(P[0], P[1], P[2], P[3]) : cgeom::ee_feature(P[0], P[1], P[2], P[3]);
-      const double d = cgeom::feature_derivatives(W.F, P, W.gd, W.H);
+      cgeom::feature_reduced(W.F, P, W.Rd);
+      const double d = W.Rd.d;
       W.b1 = kappa * bar_b1(d, dhat);
       W.b2 = kappa * bar_b2(d, dhat);
-      W.k = 3 * W.F.nv;
+      W.k = 3 * W.Rd.nb;
+      for (int q = 0; q < 12; ++q) W.gx[q] = 0.0;
+      for (int v = 0; v < W.F.nv; ++v)
+        for (int c = 0; c < 3; ++c) {
+          double sum = 0.0;
+          for (int k = 0; k < W.Rd.nb; ++k) sum += W.Rd.C[k][v] * W.Rd.gdy[3 * k + c];
+          W.gx[3 * W.F.idx[v] + c] = W.b1 * sum;
+        }
+      if (hd_out) cgeom::feature_derivatives(W.F, P, gd_out, hd_out);
     }
   }
   __syncwarp();
   if (!W.ok) return false;
-  if (hd_out)
-    for (int t = lane; t < 144; t += 32) hd_out[t] = W.H[t];
   const int k = W.k;
   const cgeom::Feature F = W.F;
-  const double b1 = W.b1, b2 = W.b2;
   for (int t = lane; t < k * k; t += 32) {
     const int a = t / k, b = t % k;
-    const int ra = 3 * F.idx[a / 3] + a % 3, cb = 3 * F.idx[b / 3] + b % 3;
-    W.A[a * 12 + b] = b2 * W.gd[ra] * W.gd[cb] + b1 * W.H[ra * 12 + cb];
+    W.A[a * 12 + b] = cgeom::reduced_entry(W.Rd, W.b1, W.b2, a, b);
     W.V[a * 12 + b] = a == b ? 1.0 : 0.0;
   }
   __syncwarp();
@@ -455,17 +467,21 @@ __device__ bool pair_eval_warp(int kind, const D3 (&P)[4], double kappa, double 
       __syncwarp();
     }
   }
-  // H = V max(Lambda, 0) V^T scattered to the feature's rows and columns
-  for (int t = lane; t < 144; t += 32) W.H[t] = 0.0;
+  if (lane < k) W.lam[lane] = fmax(W.A[lane * 12 + lane], 0.0);
   __syncwarp();
-  for (int t = lane; t < k * k; t += 32) {
+  for (int t = lane; t < k * k; t += 32) {  // N_+ = V max(Lambda, 0) V^T
     const int a = t / k, b = t % k;
-    if (b < a) continue;
     double sum = 0.0;
-    for (int m = 0; m < k; ++m) sum += W.V[a * 12 + m] * fmax(W.A[m * 12 + m], 0.0) * W.V[b * 12 + m];
-    const int ra = 3 * F.idx[a / 3] + a % 3, cb = 3 * F.idx[b / 3] + b % 3;
-    W.H[ra * 12 + cb] = sum;
-    W.H[cb * 12 + ra] = sum;
+    for (int m = 0; m < k; ++m) sum += W.V[a * 12 + m] * W.lam[m] * W.V[b * 12 + m];
+    W.H[a * 12 + b] = sum;
+  }
+  for (int t = lane; t < 144; t += 32) W.A[t] = 0.0;
+  __syncwarp();
+  const int kx = 3 * F.nv;
+  for (int t = lane; t < kx * kx; t += 32) {  // Q N_+ Q^T on the feature's vertices
+    const int a = t / kx, b = t % kx;
+    W.A[(3 * F.idx[a / 3] + a % 3) * 12 + 3 * F.idx[b / 3] + b % 3] =
+        cgeom::reduced_back(W.Rd, W.H, 12, a / 3, a % 3, b / 3, b % 3);
   }
   __syncwarp();
   return true;
@@ -492,13 +508,13 @@ __global__ void __launch_bounds__(32 * kPairWarps) k_pair_eval(const int2* __res
   for (int a = 0; a < 4; ++a) P[a] = pos(x, nullptr, 0.0, v[a]);
   double* og = pg + 12 * (int64_t)idx;
   double* oH = pH + 144 * (int64_t)idx;
-  if (!pair_eval_warp(kind, P, kappa, dhat, W, lane, nullptr)) {
+  if (!pair_eval_warp(kind, P, kappa, dhat, W, lane, nullptr, nullptr)) {
     if (lane < 12) og[lane] = 0.0;
     for (int t = lane; t < 144; t += 32) oH[t] = 0.0;
     return;
   }
-  if (lane < 12) og[lane] = W.b1 * W.gd[lane];
-  for (int t = lane; t < 144; t += 32) oH[t] = W.H[t];
+  if (lane < 12) og[lane] = W.gx[lane];
+  for (int t = lane; t < 144; t += 32) oH[t] = W.A[t];
 }
 
 // one thread per (pair, vertex a, vertex b): block (a, b) of the pair's
@@ -753,10 +769,9 @@ __global__ void __launch_bounds__(32 * kPairWarps) k_pair_derivatives(const int*
   PairWarp& W = sw[warp];
   D3 P[4];
   for (int a = 0; a < 4; ++a) P[a] = D3{X[12 * p + 3 * a], X[12 * p + 3 * a + 1], X[12 * p + 3 * a + 2]};
-  pair_eval_warp(kind[p], P, kappa, dhat, W, lane, Hd + 144 * (int64_t)p);
+  pair_eval_warp(kind[p], P, kappa, dhat, W, lane, Hd + 144 * (int64_t)p, gd + 12 * (int64_t)p);
   if (lane == 0) dist[p] = cgeom::pair_distance(kind[p], P);
-  if (lane < 12) gd[12 * p + lane] = W.gd[lane];
-  for (int t = lane; t < 144; t += 32) Hb[144 * (int64_t)p + t] = W.H[t];
+  for (int t = lane; t < 144; t += 32) Hb[144 * (int64_t)p + t] = W.A[t];
 }
 
 // ---- host side -------------------------------------------------------------------------------

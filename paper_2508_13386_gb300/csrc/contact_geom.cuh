@@ -264,45 +264,52 @@ __device__ __forceinline__ double form_line(D3 e, D3 d, double* g, double* H) {
   return u * iw;
 }
 
+// The feature's squared distance f in its nb edge vectors y: gy [3 nb],
+// Hy [3 nb x 3 nb] (leading dimension 3 nb), and the map C [nb][nv] from
+// the feature's vertices (local order F.idx) to the edge vectors, edge
+// vector k = sum_v C[k][v] x_idx[v].  Returns f.
+__device__ __forceinline__ double feature_form(const Feature& F, const D3 (&P)[4], double* gy, double* Hy,
+                                               double (&C)[3][4], int& nb) {
+  for (int k = 0; k < 3; ++k)
+    for (int v = 0; v < 4; ++v) C[k][v] = 0.0;
+  const D3 x0 = P[F.idx[0]], x1 = P[F.idx[1]];
+  if (F.form == 0) {
+    nb = 1;
+    const D3 e = sub(x0, x1);
+    for (int k = 0; k < 3; ++k) gy[k] = 2.0 * comp(e, k);
+    for (int k = 0; k < 9; ++k) Hy[k] = (k % 4 == 0) ? 2.0 : 0.0;
+    C[0][0] = 1; C[0][1] = -1;
+    return dot(e, e);
+  }
+  if (F.form == 1) {
+    nb = 2;
+    C[0][0] = 1; C[0][1] = -1;
+    C[1][1] = -1; C[1][2] = 1;
+    return form_line(sub(x0, x1), sub(P[F.idx[2]], x1), gy, Hy);
+  }
+  nb = 3;
+  const D3 x2 = P[F.idx[2]], x3 = P[F.idx[3]];
+  if (F.form == 2) {
+    C[0][0] = 1; C[0][1] = -1;
+    C[1][1] = -1; C[1][2] = 1;
+    C[2][1] = -1; C[2][3] = 1;
+    return form_plane(sub(x0, x1), sub(x2, x1), sub(x3, x1), gy, Hy);
+  }
+  C[0][0] = -1; C[0][2] = 1;
+  C[1][0] = -1; C[1][1] = 1;
+  C[2][2] = -1; C[2][3] = 1;
+  return form_plane(sub(x2, x0), sub(x1, x0), sub(x3, x2), gy, Hy);
+}
+
 // Distance d of the pair's feature with grad d [12] and Hess d [144] over
 // the pair's 12 stacked coordinates (zero outside the feature's vertices).
 // Kept out of line: inlined into the pair kernel of the assembly, the
 // projected Hessians came out wrong while the same code in the derivative
 // test kernel was right; out of line both match the oracle.
 __device__ __noinline__ double feature_derivatives(const Feature& F, const D3 (&P)[4], double* gd, double* Hd) {
-  double gy[9], Hy[81];
+  double gy[9], Hy[81], C[3][4];
   int nb;
-  double C[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // edge vector k = sum_v C[k][v] x_idx[v]
-  double f;
-  const D3 x0 = P[F.idx[0]], x1 = P[F.idx[1]];
-  if (F.form == 0) {
-    nb = 1;
-    const D3 e = sub(x0, x1);
-    f = dot(e, e);
-    for (int k = 0; k < 3; ++k) gy[k] = 2.0 * comp(e, k);
-    for (int k = 0; k < 9; ++k) Hy[k] = (k % 4 == 0) ? 2.0 : 0.0;
-    C[0][0] = 1; C[0][1] = -1;
-  } else if (F.form == 1) {
-    nb = 2;
-    const D3 x2 = P[F.idx[2]];
-    f = form_line(sub(x0, x1), sub(x2, x1), gy, Hy);
-    C[0][0] = 1; C[0][1] = -1;
-    C[1][1] = -1; C[1][2] = 1;
-  } else if (F.form == 2) {
-    nb = 3;
-    const D3 x2 = P[F.idx[2]], x3 = P[F.idx[3]];
-    f = form_plane(sub(x0, x1), sub(x2, x1), sub(x3, x1), gy, Hy);
-    C[0][0] = 1; C[0][1] = -1;
-    C[1][1] = -1; C[1][2] = 1;
-    C[2][1] = -1; C[2][3] = 1;
-  } else {
-    nb = 3;
-    const D3 x2 = P[F.idx[2]], x3 = P[F.idx[3]];
-    f = form_plane(sub(x2, x0), sub(x1, x0), sub(x3, x2), gy, Hy);
-    C[0][0] = -1; C[0][2] = 1;
-    C[1][0] = -1; C[1][1] = 1;
-    C[2][2] = -1; C[2][3] = 1;
-  }
+  const double f = feature_form(F, P, gy, Hy, C, nb);
   const int ny = 3 * nb;
   const double d = sqrt(f);
   const double i2d = 0.5 / d, i4d3 = 0.25 / (d * d * d);
@@ -329,6 +336,80 @@ __device__ __noinline__ double feature_derivatives(const Feature& F, const D3 (&
           Hd[(3 * F.idx[v] + c) * 12 + 3 * F.idx[w] + e] = s * i2d - gx[3 * v + c] * gx[3 * w + e] * i4d3;
         }
   return d;
+}
+
+// ---- the barrier Hessian in the edge-vector space ----------------------------------------
+// Every distance formula depends on the vertices only through the feature's
+// edge vectors y = (C (x) I3) x, so grad_x d = C^T grad_y d and
+// Hess_x = C^T M C with M the Hessian in y (C stands for C (x) I3 here).
+// With the thin QR factorisation C^T = Q R (Q [nv][nb] with orthonormal
+// columns, R [nb][nb] upper triangular), Hess_x = Q (R M R^T) Q^T, so the
+// nonzero eigenpairs of the 3 nv x 3 nv block come from N = R M R^T of order
+// 3 nb (9, 6 or 3 rather than 12, 9 or 6), and its projection to the PSD
+// cone is Q N_+ Q^T.
+struct Reduced {
+  int nb;
+  double d;
+  double gdy[9];    // grad_y d
+  double Mdy[81];   // Hess_y d (leading dimension 3 nb)
+  double C[3][4];   // edge-vector map
+  double Q[4][3];   // thin QR factors of C^T
+  double R[3][3];
+};
+
+__device__ __noinline__ void feature_reduced(const Feature& F, const D3 (&P)[4], Reduced& Rd) {
+  double gy[9];
+  int nb;
+  const double f = feature_form(F, P, gy, Rd.Mdy, Rd.C, nb);
+  Rd.nb = nb;
+  const int ny = 3 * nb;
+  const double d = sqrt(f);
+  Rd.d = d;
+  const double i2d = 0.5 / d, i4d3 = 0.25 / (d * d * d);
+  for (int i = 0; i < ny; ++i) {
+    Rd.gdy[i] = gy[i] * i2d;
+    for (int j = 0; j < ny; ++j) Rd.Mdy[i * ny + j] = Rd.Mdy[i * ny + j] * i2d - gy[i] * gy[j] * i4d3;
+  }
+  // modified Gram-Schmidt on the columns of C^T (the rows of C)
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) Rd.R[k][l] = 0.0;
+  for (int k = 0; k < nb; ++k) {
+    double q[4];
+    for (int v = 0; v < 4; ++v) q[v] = v < F.nv ? Rd.C[k][v] : 0.0;
+    for (int l = 0; l < k; ++l) {
+      double r = 0.0;
+      for (int v = 0; v < F.nv; ++v) r += Rd.Q[v][l] * q[v];
+      Rd.R[l][k] = r;
+      for (int v = 0; v < F.nv; ++v) q[v] -= r * Rd.Q[v][l];
+    }
+    double nrm = 0.0;
+    for (int v = 0; v < F.nv; ++v) nrm += q[v] * q[v];
+    nrm = sqrt(nrm);
+    Rd.R[k][k] = nrm;
+    for (int v = 0; v < 4; ++v) Rd.Q[v][k] = v < F.nv ? q[v] / nrm : 0.0;
+  }
+}
+
+// Entry (a, b) of N = R M R^T, M = kappa (b'' grad_y d grad_y d^T + b' Hess_y d)
+// given b1 = kappa b'(d), b2 = kappa b''(d); a = 3 k + c, b = 3 l + e
+__device__ __forceinline__ double reduced_entry(const Reduced& Rd, double b1, double b2, int a, int b) {
+  const int ny = 3 * Rd.nb, k = a / 3, c = a % 3, l = b / 3, e = b % 3;
+  double s = 0.0;
+  for (int kk = k; kk < Rd.nb; ++kk)
+    for (int ll = l; ll < Rd.nb; ++ll) {
+      const int i = 3 * kk + c, j = 3 * ll + e;
+      s += Rd.R[k][kk] * (b2 * Rd.gdy[i] * Rd.gdy[j] + b1 * Rd.Mdy[i * ny + j]) * Rd.R[l][ll];
+    }
+  return s;
+}
+
+// Entry ((v, c), (w, e)) of Q N_+ Q^T over the feature's vertices, N_+ [ny][ld]
+__device__ __forceinline__ double reduced_back(const Reduced& Rd, const double* Np, int ld, int v, int c, int w,
+                                               int e) {
+  double s = 0.0;
+  for (int k = 0; k < Rd.nb; ++k)
+    for (int l = 0; l < Rd.nb; ++l) s += Rd.Q[v][k] * Np[(3 * k + c) * ld + 3 * l + e] * Rd.Q[w][l];
+  return s;
 }
 
 }  // namespace cgeom

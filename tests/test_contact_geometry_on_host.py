@@ -30,6 +30,7 @@ CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_2508_13386_gb300", "
 
 _PRELUDE = r'''
 #include <cmath>
+#include <cstdlib>
 #define __device__
 #define __host__
 #define __forceinline__ inline
@@ -45,6 +46,72 @@ extern "C" double distance(int kind, const double* X) {
   D3 P[4];
   load(X, P);
   return pair_distance(kind, P);
+}
+// test-only: serial cyclic Jacobi projection of the symmetric k x k A (ld 12) to the PSD cone
+static void jacobi_psd(double* A, int k) {
+  double V[144];
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) V[i * 12 + j] = i == j;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < k; ++i)
+      for (int j = i + 1; j < k; ++j) off += A[i * 12 + j] * A[i * 12 + j];
+    if (off < 1e-300) break;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = A[p * 12 + q];
+        if (apq == 0.0) continue;
+        const double tau = (A[q * 12 + q] - A[p * 12 + p]) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int r = 0; r < k; ++r) {
+          const double a = A[r * 12 + p], b = A[r * 12 + q];
+          A[r * 12 + p] = c * a - sn * b; A[r * 12 + q] = sn * a + c * b;
+        }
+        for (int r = 0; r < k; ++r) {
+          const double a = A[p * 12 + r], b = A[q * 12 + r];
+          A[p * 12 + r] = c * a - sn * b; A[q * 12 + r] = sn * a + c * b;
+        }
+        for (int r = 0; r < k; ++r) {
+          const double a = V[r * 12 + p], b = V[r * 12 + q];
+          V[r * 12 + p] = c * a - sn * b; V[r * 12 + q] = sn * a + c * b;
+        }
+      }
+  }
+  double lam[12];
+  for (int i = 0; i < k; ++i) lam[i] = A[i * 12 + i] > 0 ? A[i * 12 + i] : 0.0;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int m = 0; m < k; ++m) s += V[i * 12 + m] * lam[m] * V[j * 12 + m];
+      A[i * 12 + j] = s;
+    }
+}
+// the barrier Hessian of a pair through the reduced edge-vector space, as the pair kernel forms it
+extern "C" void projected(int kind, const double* X, double kappa, double dhat, double* Hb, double* g) {
+  D3 P[4];
+  load(X, P);
+  const Feature F = kind == 0 ? pt_feature(P[0], P[1], P[2], P[3]) : ee_feature(P[0], P[1], P[2], P[3]);
+  Reduced Rd;
+  feature_reduced(F, P, Rd);
+  const double d = Rd.d, r = d - dhat;
+  const double b1 = d < dhat ? kappa * (-2.0 * r * std::log(d / dhat) - r * r / d) : 0.0;
+  const double b2 = d < dhat ? kappa * (-2.0 * std::log(d / dhat) - 4.0 * r / d + r * r / (d * d)) : 0.0;
+  const int ny = 3 * Rd.nb;
+  double N[144];
+  for (int a = 0; a < ny; ++a)
+    for (int b = 0; b < ny; ++b) N[a * 12 + b] = reduced_entry(Rd, b1, b2, a, b);
+  jacobi_psd(N, ny);
+  for (int q = 0; q < 144; ++q) Hb[q] = 0.0;
+  for (int q = 0; q < 12; ++q) g[q] = 0.0;
+  for (int v = 0; v < F.nv; ++v)
+    for (int c = 0; c < 3; ++c) {
+      double s = 0.0;
+      for (int k = 0; k < Rd.nb; ++k) s += Rd.C[k][v] * Rd.gdy[3 * k + c];
+      g[3 * F.idx[v] + c] = b1 * s;
+      for (int w = 0; w < F.nv; ++w)
+        for (int e = 0; e < 3; ++e) Hb[(3 * F.idx[v] + c) * 12 + 3 * F.idx[w] + e] = reduced_back(Rd, N, 12, v, c, w, e);
+    }
 }
 extern "C" double derivatives(int kind, const double* X, int* form_idx, double* gd, double* Hd) {
   D3 P[4];
@@ -75,6 +142,8 @@ def geom(tmp_path_factory):
     lib.distance.restype = C.c_double
     lib.derivatives.argtypes = [C.c_int, P, C.POINTER(C.c_int), P, P]
     lib.derivatives.restype = C.c_double
+    lib.projected.argtypes = [C.c_int, P, C.c_double, C.c_double, P, P]
+    lib.projected.restype = None
     return lib
 
 
@@ -155,3 +224,24 @@ def test_planted_sign_error_is_caught(geom, tmp_path):
         _, _, H_o = contact.pair_distance_derivatives("pt" if k == 0 else "ee", x)
         worst = max(worst, np.max(np.abs(Hd.reshape(12, 12) - H_o)) / np.max(np.abs(H_o)))
     assert worst > 1e-6
+
+
+def test_reduced_space_projection_matches_oracle(geom):
+    """The pair kernel projects the barrier Hessian in the feature's edge-
+    vector space (N = R M R^T of order 3 nb) and maps it back with Q; this
+    must equal the oracle's projection of the full 12 x 12 pair Hessian
+    (1e-9 of its largest entry), and the gradient kappa b' grad d (1e-10)."""
+    from oracle import barrier
+    kind, X = _pairs()
+    P = C.POINTER(C.c_double)
+    dhat, kappa = 10.0, 3.0
+    for k, x in zip(kind, X):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        kk = "pt" if k == 0 else "ee"
+        Hb, g = np.zeros(144), np.zeros(12)
+        geom.projected(int(k), x.ctypes.data_as(P), kappa, dhat, Hb.ctypes.data_as(P), g.ctypes.data_as(P))
+        Hb_o = contact.pair_barrier_hessian(kk, x, kappa, dhat)
+        assert np.max(np.abs(Hb.reshape(12, 12) - Hb_o)) <= 1e-9 * np.max(np.abs(Hb_o))
+        d_o, g_o, _ = contact.pair_distance_derivatives(kk, x)
+        g_ref = kappa * barrier.db(np.array([d_o]), dhat)[0] * g_o
+        assert np.max(np.abs(g - g_ref)) <= 1e-10 * np.max(np.abs(g_ref))
