@@ -512,8 +512,11 @@ mls_status mls_mlp_column_stats(const float* X, int32_t n, int32_t d, float* mea
  * iterate; requires coarse_refresh >= the Newton count).  With a network
  * attached (3r inputs, r outputs, r = 12 handles) the step starts from
  * x_tilde + U dq_hat, dq_hat = net(f), when that point is feasible and has
- * lower energy than x_tilde; otherwise from x_tilde.  The converged step
- * does not depend on the start.  Not in the paper. */
+ * lower energy than x_tilde; otherwise from x_tilde.  With bodies set
+ * (mls_set_bodies) the candidate must also be reachable from x^t on a
+ * straight path the CCD filter does not cut, and it is compared with the
+ * start the step would otherwise take (x_tilde cut by the same filter).
+ * The converged step does not depend on the start.  Not in the paper. */
 /* enable: 0 off, 1 history/features (and prediction when a network is
  * attached), 2 as 1 plus recording targets (two-level preconditioner only).
  * The first enable factors U^T M U (float64 Cholesky). */

@@ -210,6 +210,27 @@ mls_status warm_start_begin(mls_ctx* ctx, int* used) {
   }
   if ((st = launch_prolong(ctx, ctx->ws_c, ctx->vw, false)) != MLS_OK) return st;
   if ((st = launch_from_solve(ctx, ctx->vw, ctx->dir)) != MLS_OK) return st;  // zero on Dirichlet vertices
+  if (ctx->cs.on) {
+    // Between bodies a feasible end point does not rule out a primitive that
+    // passed through another on the way (Sec. 3.9): the candidate c is taken
+    // only when the straight path x^t -> c, on which the start iterate is
+    // cut too, needs no CCD cut, and when it lowers the energy of the start
+    // the step has already chosen.
+    if ((st = launch_axpy_state(ctx, ctx->dir, ctx->xtil, 1.0)) != MLS_OK) return st;
+    if ((st = launch_axpy_state(ctx, ctx->dir, ctx->xt, -1.0)) != MLS_OK) return st;  // c - x^t
+    double a = 0.0;
+    if ((st = launch_ccd(ctx, ctx->xt, ctx->dir, &a)) != MLS_OK) return st;
+    if (!(a >= 1.0)) return cuda_check(ctx, cudaGetLastError(), "warm start");
+    double Ec = 0, Ecur = 0;
+    int infc = 0, infcur = 0;
+    if ((st = launch_energy(ctx, ctx->xk, ctx->tmp4, 0.0, &Ecur, &infcur)) != MLS_OK) return st;
+    if ((st = launch_energy(ctx, ctx->xt, ctx->dir, 1.0, &Ec, &infc)) != MLS_OK) return st;
+    if (!infc && std::isfinite(Ec) && (infcur || Ec < Ecur)) {
+      if ((st = launch_xpay_state(ctx, ctx->xt, ctx->dir, 1.0, ctx->xk)) != MLS_OK) return st;
+      *used = 1;
+    }
+    return cuda_check(ctx, cudaGetLastError(), "warm start");
+  }
   double E0 = 0, E1 = 0;
   int inf0 = 0, inf1 = 0;
   if ((st = launch_energy(ctx, ctx->xtil, ctx->dir, 0.0, &E0, &inf0)) != MLS_OK) return st;
