@@ -67,6 +67,15 @@ def ccd_step_bound(prob, x, d):
 ROUNDING_REGIME = 1e-13
 
 
+def _uncut_between_bodies(prob, x, d):
+    """True without bodies; with bodies, True when the mesh-mesh CCD filter
+    (Sec. 3.9) lets the whole step d through."""
+    if getattr(prob, "body", None) is None:
+        return True
+    from . import contact
+    return contact.ccd_step(x, d, prob.faces, prob.edges, prob.body, s=1.0 - CCD_FRACTION) >= 1.0
+
+
 def line_search(prob, x, d, g, E0):
     """Filtered backtracking.  Returns alpha or raises."""
     alpha = ccd_step_bound(prob, x, d)
@@ -100,7 +109,9 @@ def timestep(prob, xtol_rel=1e-12, max_iter=100, method="auto", x_init=None):
 
     Stops after the first iteration whose Newton direction satisfies
     |d|_inf <= xtol_rel * max(|x - x^t|_inf, h^2 |gravity|); that final
-    direction is applied in full when it keeps x feasible.
+    direction is applied in full when it keeps x feasible and, with bodies,
+    when the mesh-mesh CCD filter of Sec. 3.9 does not cut it (a feasible end
+    point does not rule out a vertex that passed through a triangle).
     """
     x = initial_guess(prob) if x_init is None else np.array(x_init, dtype=np.float64)
     scale0 = prob.h ** 2 * max(np.linalg.norm(prob.gravity), 1e-30)
@@ -115,7 +126,7 @@ def timestep(prob, xtol_rel=1e-12, max_iter=100, method="auto", x_init=None):
         scale = max(float(np.max(np.abs(x - prob.x_t))), scale0)
         if np.max(np.abs(d)) <= xtol_rel * scale:
             xn = x + d
-            if prob.feasible(xn):
+            if prob.feasible(xn) and _uncut_between_bodies(prob, x, d):
                 x = xn
             info["converged"] = True
             break

@@ -925,8 +925,16 @@ static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
     if ((st = dot4(ctx, ctx->grad, ctx->dir, &gd)) != MLS_OK) return st;
     if (step_rel <= ctx->opt.newton_tol) {
       // converged: apply the final (tiny) direction in full when feasible
+      // and, with bodies, when the mesh-mesh CCD filter does not cut it (a
+      // feasible end point does not rule out a vertex that passed through a
+      // triangle on the way)
       if ((st = launch_energy(ctx, ctx->xk, ctx->dir, 1.0, &E, &infeasible)) != MLS_OK) return st;
       S.line_search_trials++;
+      if (!infeasible && ctx->cs.on) {
+        double t = 1.0;
+        if ((st = contact_ccd(ctx, ctx->xk, ctx->dir, &t)) != MLS_OK) return st;
+        infeasible = t < 1.0;
+      }
       if (!infeasible) {
         if ((st = launch_axpy_state(ctx, ctx->xk, ctx->dir, 1.0)) != MLS_OK) return st;
       }

@@ -246,6 +246,29 @@ def test_problem_with_mesh_contact_gradient_and_collision_step():
     assert _vertices_inside_other_body(x_free, s.tets, body) > 0
 
 
+
+def test_final_newton_direction_is_ccd_filtered_between_bodies():
+    """Sec. 3.9: every update of the iterate passes the CCD filter, the
+    final small Newton direction too.  A move that carries a vertex of one
+    tet through the other's top face ends with no touching pair, so the
+    feasibility test alone would accept it; the mesh-mesh filter rejects
+    it and lets the opposite move through.  Without bodies nothing is cut."""
+    from types import SimpleNamespace
+    from oracle import newton
+    gap = 1e-4
+    X, tets, body = _two_tets(gap)
+    faces = contact.boundary_faces(tets)
+    edges = contact.face_edges(faces)
+    prob = SimpleNamespace(body=body, faces=faces, edges=edges)
+    d = np.zeros_like(X)
+    d[4:, 2] = -2 * gap
+    pt, ee = contact.contact_pairs(X + d, faces, edges, body, 1e-300)
+    assert not pt and not ee
+    assert _vertices_inside_other_body(X + d, tets, body) == 1
+    assert not newton._uncut_between_bodies(prob, X, d)
+    assert newton._uncut_between_bodies(prob, X, -d)
+    assert newton._uncut_between_bodies(SimpleNamespace(body=None), X, d)
+
 def _vertices_inside_other_body(x, tets, body):
     """How many vertices lie strictly inside a tet of another body."""
     count = 0
