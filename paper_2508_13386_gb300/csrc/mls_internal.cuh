@@ -218,10 +218,10 @@ struct PcgScalars {
 // there is no arrival counter, fence or final pass.  The consumer (a later
 // kernel) rebuilds the total from the limbs.  The exponent e comes from an
 // estimate of the sum's magnitude that producers and consumer read from the
-// same place (the value of the same quantity one iteration earlier): a block
-// partial up to 2^30 times the estimate fits (beyond that, or not finite, it
-// sets the slot's overflow word), and sums down to 2^-27 times the estimate
-// keep all 53 bits.  Each limb accumulates fewer than 2^16 terms below 2^33,
+// same place (the value of the same quantity one iteration earlier), with
+// 2^e <= estimate < 2^(e+1): a block partial below 2^(e+30) fits (from there
+// up, or not finite, it sets the slot's overflow word), and totals down to
+// 2^(e-27) keep all 53 bits.  Each limb accumulates fewer than 2^16 terms below 2^33,
 // so no accumulator overflows.  The conversions work on the bit patterns
 // with integer instructions: one thread per block runs them, and float64
 // instructions issue slowly on this GPU.
