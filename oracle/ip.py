@@ -14,7 +14,9 @@ Readings used where the paper is silent:
 * gravity g enters through the predictor, x_tilde += alpha h^2 g
   (equivalent to the potential -M g . x in the alpha h^2-scaled bracket);
 * friction D = 0 unless ``mu`` > 0 is given (no workload uses friction);
-  then D is the lagged, mollified point-plane friction of ``friction.py``;
+  then D is the lagged, mollified point-plane friction of ``friction.py``
+  and, with bodies, its mesh-mesh form between their surface primitives
+  (``friction.PairFriction``);
 * Dirichlet vertices are held at x^t: they are not unknowns, their inertia
   term is dropped, their gradient entries are zero and their Hessian rows
   and columns are the identity.
@@ -84,6 +86,10 @@ class Problem:
         if mu > 0 and self.contact:
             self.friction = friction.GroundFriction(mu, eps_v, self.h, self.kappa, self.dhat, self.plane_n,
                                                     self.plane_o, self.x_t)
+        self.pair_friction = None
+        if mu > 0 and self.body is not None:
+            self.pair_friction = friction.PairFriction(mu, eps_v, self.h, self.kappa, self.dhat, self.faces,
+                                                       self.edges, self.body, self.x_t)
 
     def velocity(self, x_new):
         """v^{t+1} of the integrator from the step's solution."""
@@ -118,6 +124,8 @@ class Problem:
         if self.contact:
             B = self.kappa * np.sum(barrier.b(self.distances(x), self.dhat))
         D = self.friction.energy(x) if self.friction is not None else 0.0
+        if self.pair_friction is not None:
+            D += self.pair_friction.energy(x)
         if self.body is not None:
             pt, ee = self.pairs(x)
             B = B + contact.pair_energy(x, self.faces, self.edges, pt, ee, self.kappa, self.dhat)
@@ -139,6 +147,8 @@ class Problem:
                 * self.plane_n[None, :]
         if self.friction is not None:
             gel += self.friction.gradient(x)
+        if self.pair_friction is not None:
+            gel += self.pair_friction.gradient(x)
         if self.body is not None:
             pt, ee = self.pairs(x)
             gel += contact.pair_gradient(x, self.faces, self.edges, pt, ee, self.kappa, self.dhat)
@@ -193,6 +203,12 @@ class Problem:
             rows = np.concatenate([rows, r.ravel()])
             cols = np.concatenate([cols, c.ravel()])
             vals = np.concatenate([vals, (self.ah2 * Hf[act]).ravel()])
+        if self.pair_friction is not None and len(self.pair_friction.vids):
+            Hp = self.pair_friction.hessian_pairs(x)
+            dof = (3 * self.pair_friction.vids[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
+            rows = np.concatenate([rows, np.repeat(dof, 12, axis=1).ravel()])
+            cols = np.concatenate([cols, np.tile(dof, (1, 12)).ravel()])
+            vals = np.concatenate([vals, (self.ah2 * Hp).ravel()])
         H = sp.coo_matrix((vals, (rows, cols)), shape=(3 * self.n, 3 * self.n)).tocsr()
         fixed = np.repeat(self.pinned, 3)
         if fixed.any():

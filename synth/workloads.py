@@ -159,14 +159,14 @@ def tiny_scene(nx: int = 3, ny: int = 2, nz: int = 2, seed: int = 0, contact: bo
                  dt=1.0 / 60.0, contact=contact)
 
 
-def two_block_scene(gap: float = 0.01, speed: float = 1.0, seed: int = 0):
-    """Two separate blocks of 2 x 2 x 1 voxels (edge 0.1 m), one above the
+def two_block_scene(gap: float = 0.01, speed: float = 1.0, seed: int = 0, voxels=(2, 2, 1)):
+    """Two separate blocks of ``voxels`` voxels (edge 0.1 m), one above the
     other with ``gap`` between them and a small horizontal offset; the upper
     block moves down at ``speed`` m/s, the lower one rests.  No gravity, no
     ground plane, no pins (a mesh-mesh contact input).  Returns (scene,
     body) with ``body`` [n] the block of each vertex."""
-    lower = kuhn_voxel_mesh(np.ones((2, 2, 1), dtype=bool), voxel=0.1)
-    upper_X = lower.X + np.array([0.013, -0.007, 0.1 + gap])
+    lower = kuhn_voxel_mesh(np.ones(tuple(voxels), dtype=bool), voxel=0.1)
+    upper_X = lower.X + np.array([0.013, -0.007, 0.1 * voxels[2] + gap])
     n0 = lower.n_verts
     X = np.vstack([lower.X, upper_X])
     tets = np.vstack([lower.tets, lower.tets + n0]).astype(np.int32)
