@@ -257,9 +257,18 @@ mls_status mls_set_forces(mls_ctx* ctx, const double* gravity, int contact,
  * added to E with the same h^2 (BDF2: (4/9) h^2) factor as the elastic energy;
  * its gradient, its (PSD) diagonal Hessian blocks and its energy enter the
  * assembly and the line search.  mu = 0 turns it off (the default).
- * MLS_EINVAL for mu < 0, eps_v <= 0 with mu > 0, or mu > 0 while contact is
- * off (call mls_set_forces with contact first; turning contact off later
- * suspends the term). */
+ * With bodies set (mls_set_bodies) the same mu and eps_v also give the
+ * friction between them, the ground form with the plane replaced by each
+ * pair's closest points: every point-triangle and edge-edge pair of
+ * different bodies within dhat at x^t keeps, for the step, the weights w of
+ * its closest-point difference (sum_j w_j x_j, the weights summing to zero),
+ * the unit normal n along it and lam = -kappa b'(d); its slip is
+ *   u = (I - n n^T) sum_j w_j (x_j - x_j^t)
+ * and it adds mu lam f0(|u|), with PSD 12 x 12 Hessian w w^T (x) mu lam K,
+ * K = (f1/y)(I - n n^T) + (f1' - f1/y) u^ u^T.
+ * MLS_EINVAL for mu < 0, eps_v <= 0 with mu > 0, or mu > 0 with neither the
+ * contact plane nor bodies (call mls_set_forces with contact, or
+ * mls_set_bodies, first; turning either off later suspends its term). */
 mls_status mls_set_friction(mls_ctx* ctx, double mu, double eps_v);
 
 /* Mesh-mesh contact (Eq. IP term B, Sec. 3.1, which takes IPC's barrier on

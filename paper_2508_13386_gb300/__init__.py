@@ -178,8 +178,9 @@ class Solver:
                                            float(dhat), float(kappa)))
 
     def set_friction(self, mu, eps_v=1e-3):
-        """Lagged point-plane friction (coefficient mu, mollifier velocity eps_v);
-        needs contact on (set_forces).  mu = 0 turns it off."""
+        """Lagged friction (coefficient mu, mollifier velocity eps_v) against the
+        contact plane and, with bodies set, between them (mls_set_friction);
+        needs contact on (set_forces) or bodies (set_bodies).  mu = 0 turns it off."""
         self._check(self._l.mls_set_friction(self._ctx, float(mu), float(eps_v)))
 
     def setup_scene(self, scene):

@@ -768,6 +768,8 @@ static mls_status newton_loop(mls_ctx* ctx, mls_stats* stats) {
   const double scale0 = h * h * std::max(gmag, 1e-30);
   double E = 0;
   int infeasible = 0;
+  // friction between bodies: its pairs and frames, lagged at x^t for the step
+  if ((st = contact_friction_lag(ctx)) != MLS_OK) return st;
   // x^t must be feasible; start from x_tilde when it is, else from x^t
   if ((st = launch_energy(ctx, ctx->xt, ctx->tmp4, 0.0, &E, &infeasible)) != MLS_OK) return st;
   if (infeasible) return fail(ctx, MLS_EINVERTED, "x^t has an inverted tet or a vertex on/below the plane");
@@ -1044,7 +1046,8 @@ mls_status mls_set_friction(mls_ctx* ctx, double mu, double eps_v) {
   if (!(mu >= 0.0) || !std::isfinite(mu)) return fail(ctx, MLS_EINVAL, "friction coefficient must be >= 0");
   if (mu > 0.0 && !(eps_v > 0.0 && std::isfinite(eps_v)))
     return fail(ctx, MLS_EINVAL, "friction needs a positive mollifier velocity eps_v");
-  if (mu > 0.0 && !ctx->contact) return fail(ctx, MLS_EINVAL, "friction needs the contact plane (mls_set_forces)");
+  if (mu > 0.0 && !ctx->contact && !ctx->cs.on)
+    return fail(ctx, MLS_EINVAL, "friction needs the contact plane (mls_set_forces) or bodies (mls_set_bodies)");
   ctx->fric_mu = mu;
   if (mu > 0.0) ctx->fric_eps_v = eps_v;
   return MLS_OK;

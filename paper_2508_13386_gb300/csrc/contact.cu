@@ -716,6 +716,103 @@ __global__ void k_pair_ccd(const int2* __restrict__ pt, int npt, const int2* __r
   if (t < 1.0) atomic_min_nonneg(tmin, t);
 }
 
+// ---- friction between bodies (Eq. IP term D), lagged at x^t ------------------------------
+// The ground friction with the plane replaced by each pair's closest points:
+// the pairs within dhat at x^t keep, for the whole step, the weights w of
+// their closest-point difference, its unit normal n and mu lambda with
+// lambda = -kappa b'(d); D = sum mu lambda f0(|u|), u = (I - n n^T)
+// sum_j w_j (x_j - x_j^t).
+
+// one thread per pair within dhat at x^t: its four vertices, w, n and mu lambda
+__global__ void k_friction_lag(const int2* __restrict__ pt, int npt, const int2* __restrict__ ee, int nee,
+                               const int4* __restrict__ faces, const int4* __restrict__ edges,
+                               const Vec4d* __restrict__ xt, double mu, double kappa, double dhat,
+                               int4* __restrict__ fv, double* __restrict__ fw) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npt + nee) return;
+  const int kind = idx < npt ? 0 : 1;
+  int v[4];
+  pair_vertices(kind, kind == 0 ? pt[idx] : ee[idx - npt], faces, edges, v);
+  D3 P[4];
+  for (int a = 0; a < 4; ++a) P[a] = pos(xt, nullptr, 0.0, v[a]);
+  double w[4];
+  D3 n;
+  const double d = cgeom::friction_frame(kind, P, w, n);
+  fv[idx] = make_int4(v[0], v[1], v[2], v[3]);
+  double* o = fw + 8 * (int64_t)idx;
+  for (int j = 0; j < 4; ++j) o[j] = w[j];
+  o[4] = n.x;
+  o[5] = n.y;
+  o[6] = n.z;
+  o[7] = mu * fric_lambda(d, dhat, kappa);
+}
+
+// a lagged pair's slip at x (+ alpha d, d nullable)
+__device__ __forceinline__ double friction_pair_slip(const int (&v)[4], const double* o, const Vec4d* __restrict__ x,
+                                                     const Vec4d* __restrict__ d, double alpha,
+                                                     const Vec4d* __restrict__ xt, D3& u) {
+  const double w[4] = {o[0], o[1], o[2], o[3]};
+  D3 dx[4];
+  for (int j = 0; j < 4; ++j) dx[j] = cgeom::sub(pos(x, d, alpha, v[j]), pos(xt, nullptr, 0.0, v[j]));
+  return cgeom::friction_slip(w, D3{o[4], o[5], o[6]}, dx, u);
+}
+
+// one thread per (lagged pair, vertex a, vertex b), as k_pair_scatter: the
+// block w_a w_b mu lambda K at x into the coupling table and, for b = 0, the
+// gradient mu lambda (f1(y)/y) w_a u of vertex a into cgrad (Dirichlet
+// vertices left out)
+__global__ void k_friction_scatter(const int4* __restrict__ fv, const double* __restrict__ fw, int nfr,
+                                   const Vec4d* __restrict__ x, const Vec4d* __restrict__ xt,
+                                   const uint8_t* __restrict__ pinned, double eps, Vec4d* __restrict__ cgrad,
+                                   CouplingView C) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 16 * (int64_t)nfr) return;
+  const int idx = (int)(t >> 4), a = (int)(t >> 2) & 3, b = (int)t & 3;
+  const int4 v4 = fv[idx];
+  const int v[4] = {v4.x, v4.y, v4.z, v4.w};
+  if (pinned[v[a]] || pinned[v[b]]) return;
+  const double* o = fw + 8 * (int64_t)idx;
+  const double mul = o[7];
+  if (!(mul > 0.0)) return;
+  D3 u;
+  const double y = friction_pair_slip(v, o, x, nullptr, 0.0, xt, u);
+  const double ratio = fric_ratio(y, eps), slope = fric_slope(y, eps);
+  if (b == 0 && o[a] != 0.0) {
+    const double s = mul * ratio * o[a];
+    atomicAdd(&cgrad[v[a]].x, s * u.x);
+    atomicAdd(&cgrad[v[a]].y, s * u.y);
+    atomicAdd(&cgrad[v[a]].z, s * u.z);
+  }
+  const double ww = mul * o[a] * o[b];
+  if (ww == 0.0) return;
+  double K[9];
+  cgeom::friction_block(D3{o[4], o[5], o[6]}, u, y, ratio, slope, K);
+  const int s = coupling_slot(C, v[a], v[b]);
+  if (s < 0) return;
+  for (int q = 0; q < 9; ++q) atomicAdd(C.val + 9 * (int64_t)s + q, ww * K[q]);
+}
+
+// sum over the lagged pairs of h^2 mu lambda f0(|u|) at x + alpha d
+__global__ void __launch_bounds__(kBlock) k_friction_energy(const int4* __restrict__ fv, const double* __restrict__ fw,
+                                                            int nfr, const Vec4d* __restrict__ x,
+                                                            const Vec4d* __restrict__ d, double alpha,
+                                                            const Vec4d* __restrict__ xt, double eps, double h2,
+                                                            GridReduce gr, double* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[1] = {0.0};
+  if (idx < nfr) {
+    const double* o = fw + 8 * (int64_t)idx;
+    if (o[7] > 0.0) {
+      const int4 v4 = fv[idx];
+      const int v[4] = {v4.x, v4.y, v4.z, v4.w};
+      D3 u;
+      const double y = friction_pair_slip(v, o, x, d, alpha, xt, u);
+      acc[0] = h2 * o[7] * fric_f0(y, eps);
+    }
+  }
+  if (grid_sum<1>(acc, gr, RS_CONTACT) && threadIdx.x == 0) out[0] = acc[0];
+}
+
 // ---- coarse operator: U_i^T H_ij U_j of the cross-body blocks ----------------------------
 // one 144-thread block per cross-body coupling (i, j) with H_ij in slot s:
 // for handles a of i and b of j, entry (12a + 4c + l, 12b + 4e + m) gains
@@ -785,8 +882,9 @@ static int pow2_at_least(int64_t v) {
 
 void contact_free(mls_ctx* ctx) {
   ContactState& cs = ctx->cs;
-  void* bufs[] = {cs.faces, cs.edges, cs.sverts, cs.row_len0, cs.head, cs.ent,  cs.next, cs.boxes, cs.cnt, cs.pt,
-                  cs.ee,    cs.spt,   cs.see,    cs.ckey,     cs.cval, cs.xc,   cs.cgrad, cs.ccd,  cs.pg,  cs.pH, cs.bbox};
+  void* bufs[] = {cs.faces, cs.edges, cs.sverts, cs.row_len0, cs.head, cs.ent, cs.next, cs.boxes, cs.cnt,
+                  cs.pt,    cs.ee,    cs.spt,    cs.see,      cs.ckey, cs.cval, cs.xc,  cs.cgrad, cs.ccd,
+                  cs.pg,    cs.pH,    cs.bbox,   cs.fpt,      cs.fee,  cs.fv,   cs.fw};
   for (void* p : bufs) dfree(ctx, p);
   int* keep = cs.cnt_host;  // pinned, freed with the context
   cs = ContactState{};
@@ -888,8 +986,9 @@ mls_status contact_assemble(mls_ctx* ctx, const Vec4d* x) {
   mls_status st = broad_phase(ctx, x, nullptr, &cs.pt, &cs.ee, &cs.pcap, &cs.npt, &cs.nee);
   if (st != MLS_OK) return st;
   const int np = cs.npt + cs.nee;
-  // every pair adds at most 16 vertex couplings; the table stays at most half full
-  const int64_t need = std::max<int64_t>(64, 32 * (int64_t)np);
+  // every pair (and every lagged friction pair) adds at most 16 vertex
+  // couplings; the table stays at most half full
+  const int64_t need = std::max<int64_t>(64, 32 * ((int64_t)np + cs.nfr));
   if (need > INT32_MAX / 2) return fail(ctx, MLS_ENOMEM, "too many contact pairs");
   if (cs.ccap < need) {
     cs.ccap = 1 << pow2_at_least(need);
@@ -925,11 +1024,42 @@ mls_status contact_assemble(mls_ctx* ctx, const Vec4d* x) {
                                                                           cs.edges, ctx->pinned, cs.pg, cs.pH,
                                                                           cs.cgrad, C);
   }
+  if (cs.nfr > 0) {
+    ++ctx->launches;
+    k_friction_scatter<<<nblocks(16 * (int64_t)cs.nfr), kBlock, 0, ctx->stream>>>(
+        cs.fv, cs.fw, cs.nfr, x, ctx->xt, ctx->pinned, ctx->fric_eps_v * ctx->h_step, cs.cgrad, C);
+  }
   ++ctx->launches;
   k_contact_reset_rows<<<nblocks(cs.nsv), kBlock, 0, ctx->stream>>>(cs.sverts, cs.nsv, ctx->slice_ptr, cs.row_len0,
                                                                      ctx->row_len, ctx->col);
   cs.nxc = 0;
   return cuda_check(ctx, cudaGetLastError(), "contact pairs");
+}
+
+// The friction pairs of a step: the pairs within dhat at x^t, with their
+// frames and normal forces (friction between bodies needs mu > 0 from
+// mls_set_friction); called once per timestep before the Newton loop
+mls_status contact_friction_lag(mls_ctx* ctx) {
+  ContactState& cs = ctx->cs;
+  cs.nfr = 0;
+  if (!cs.on || !(ctx->fric_mu > 0.0)) return MLS_OK;
+  int npt = 0, nee = 0;
+  mls_status st = broad_phase(ctx, ctx->xt, nullptr, &cs.fpt, &cs.fee, &cs.fbcap, &npt, &nee);
+  if (st != MLS_OK) return st;
+  const int np = npt + nee;
+  if (np > cs.fcap) {
+    cs.fcap = np + np / 2 + 256;
+    if ((st = regrow(ctx, (void**)&cs.fv, sizeof(int4) * cs.fcap)) != MLS_OK) return st;
+    if ((st = regrow(ctx, (void**)&cs.fw, sizeof(double) * 8 * cs.fcap)) != MLS_OK) return st;
+  }
+  if (np > 0) {
+    ++ctx->launches;
+    k_friction_lag<<<nblocks(np), kBlock, 0, ctx->stream>>>(cs.fpt, npt, cs.fee, nee, cs.faces, cs.edges, ctx->xt,
+                                                            ctx->fric_mu, cs.kappa, cs.dhat, cs.fv, cs.fw);
+    if ((st = cuda_check(ctx, cudaGetLastError(), "k_friction_lag")) != MLS_OK) return st;
+  }
+  cs.nfr = np;
+  return MLS_OK;
 }
 
 template <typename MT, typename VT>
@@ -944,7 +1074,7 @@ static void launch_merge(mls_ctx* ctx, void* val, void* dinv, bool record) {
 
 mls_status contact_merge(mls_ctx* ctx, void* val, void* dinv, bool record) {
   ContactState& cs = ctx->cs;
-  if (!cs.on || cs.npt + cs.nee == 0) return MLS_OK;
+  if (!cs.on || cs.npt + cs.nee + cs.nfr == 0) return MLS_OK;
   mls_status st;
   if (record &&
       (st = cuda_check(ctx, cudaMemsetAsync(cs.cnt + kCntXc, 0, sizeof(int), ctx->stream), "xc count")) != MLS_OK)
@@ -997,6 +1127,19 @@ mls_status contact_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double a
   if (!cs.on) return MLS_OK;
   mls_status st = contact_sweep(ctx, x, d);
   if (st != MLS_OK) return st;
+  if (cs.nfr > 0) {  // friction between bodies over the lagged pairs
+    if (nblocks(cs.nfr) > kMaxPartials) return fail(ctx, MLS_EINVAL, "too many friction pairs for one reduction grid");
+    ++ctx->launches;
+    k_friction_energy<<<nblocks(cs.nfr), kBlock, 0, ctx->stream>>>(cs.fv, cs.fw, cs.nfr, x, d, alpha, ctx->xt,
+                                                                   ctx->fric_eps_v * ctx->h_step, ctx->h * ctx->h,
+                                                                   ctx->red, ctx->dscal + 12);
+    if ((st = cuda_check(ctx, cudaGetLastError(), "k_friction_energy")) != MLS_OK) return st;
+    if ((st = cuda_check(ctx, cudaMemcpyAsync(ctx->dscal_host + 12, ctx->dscal + 12, sizeof(double),
+                                              cudaMemcpyDeviceToHost, ctx->stream), "friction energy")) != MLS_OK)
+      return st;
+    if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "friction energy sync")) != MLS_OK) return st;
+    *E = ctx->dscal_host[12];
+  }
   const int np = cs.nspt + cs.nsee;
   if (np == 0) return MLS_OK;
   if (nblocks(np) > kMaxPartials) return fail(ctx, MLS_EINVAL, "too many contact candidates for one reduction grid");
@@ -1009,7 +1152,7 @@ mls_status contact_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double a
                                             cudaMemcpyDeviceToHost, ctx->stream), "pair energy")) != MLS_OK)
     return st;
   if ((st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "pair energy sync")) != MLS_OK) return st;
-  *E = ctx->dscal_host[8];
+  *E += ctx->dscal_host[8];
   *infeasible = ctx->dscal_host[9] > 0.5 ? 1 : 0;
   return MLS_OK;
 }

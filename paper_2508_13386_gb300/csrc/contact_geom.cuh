@@ -1,7 +1,8 @@
 // Mesh-mesh contact geometry on the device: closest points of primitive
 // pairs, the closest feature, and the distance with its gradient and Hessian
 // (Eq. IP term B, Sec. 3.1, which takes IPC's barrier on point-triangle and
-// edge-edge pairs without writing it out).
+// edge-edge pairs without writing it out); and the lagged frame, slip and
+// Hessian block of the friction term D between bodies.
 //
 // A pair is four vertices: (p, a, b, c) for a point and a triangle, (p0, p1,
 // q0, q1) for two edges.  Its distance is the Euclidean distance of the
@@ -410,6 +411,52 @@ __device__ __forceinline__ double reduced_back(const Reduced& Rd, const double* 
   for (int k = 0; k < Rd.nb; ++k)
     for (int l = 0; l < Rd.nb; ++l) s += Rd.Q[v][k] * Np[(3 * k + c) * ld + 3 * l + e] * Rd.Q[w][l];
   return s;
+}
+
+// ---- friction between bodies (Eq. IP term D) ----------------------------------------------
+// The ground friction with the plane replaced by the pair's closest points,
+// lagged at x^t for the whole step.  The frame of a pair: the weights w with
+// which its closest-point difference is y - z = sum_j w_j P_j (point-triangle:
+// 1 and minus the closest point's barycentric weights; edge-edge: 1 - s, s,
+// -(1 - t), -t; they sum to zero), and the unit normal n along y - z.
+// Returns the distance |y - z|.
+__device__ __forceinline__ double friction_frame(int kind, const D3 (&P)[4], double (&w)[4], D3& n) {
+  if (kind == 0) {
+    double b[3];
+    pt_closest(P[0], P[1], P[2], P[3], b);
+    w[0] = 1.0; w[1] = -b[0]; w[2] = -b[1]; w[3] = -b[2];
+  } else {
+    D3 y, z;
+    ee_closest(P[0], P[1], P[2], P[3], y, z);
+    const double s = seg_weight(y, P[0], P[1]), t = seg_weight(z, P[2], P[3]);
+    w[0] = 1.0 - s; w[1] = s; w[2] = -(1.0 - t); w[3] = -t;
+  }
+  D3 e{0.0, 0.0, 0.0};
+  for (int j = 0; j < 4; ++j) e = add(e, scl(w[j], P[j]));
+  const double d = sqrt(dot(e, e));
+  n = d > 0.0 ? scl(1.0 / d, e) : D3{0.0, 0.0, 0.0};
+  return d;
+}
+
+// The slip of a lagged pair over the step, u = (I - n n^T) sum_j w_j dx_j
+// with dx_j = x_j - x_j^t; returns |u|.
+__device__ __forceinline__ double friction_slip(const double (&w)[4], D3 n, const D3 (&dx)[4], D3& u) {
+  D3 r{0.0, 0.0, 0.0};
+  for (int j = 0; j < 4; ++j) r = add(r, scl(w[j], dx[j]));
+  u = sub(r, scl(dot(r, n), n));
+  return sqrt(dot(u, u));
+}
+
+// The 3 x 3 K of the pair's Hessian, d2D/dx_i dx_j = w_i w_j mu lambda K:
+// K = ratio (I - n n^T) + (slope - ratio) u^ u^T with ratio = f1(y)/y,
+// slope = f1'(y), u^ = u / y (at y = 0 both factors are 2/eps and u^ drops
+// out).  Positive semi-definite since ratio > 0 and slope >= 0.
+__device__ __forceinline__ void friction_block(D3 n, D3 u, double y, double ratio, double slope, double (&K)[9]) {
+  const double nn[3] = {n.x, n.y, n.z};
+  const double uh[3] = {y > 0.0 ? u.x / y : 0.0, y > 0.0 ? u.y / y : 0.0, y > 0.0 ? u.z / y : 0.0};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      K[3 * r + c] = ratio * ((r == c ? 1.0 : 0.0) - nn[r] * nn[c]) + (slope - ratio) * uh[r] * uh[c];
 }
 
 }  // namespace cgeom

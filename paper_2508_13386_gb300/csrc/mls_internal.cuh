@@ -630,9 +630,17 @@ struct ContactState {
   int4* xc = nullptr;                // cross-body couplings {i, j, slot of H, 0}
   int xcap = 0;
   int nxc = 0;
-  Vec4d* cgrad = nullptr;            // [n] barrier gradient of the pairs (no h^2)
+  Vec4d* cgrad = nullptr;            // [n] barrier and friction gradient of the pairs (no h^2)
   double* ccd = nullptr;             // device: smallest CCD fraction
   std::vector<int> h_body;
+  // friction between bodies, lagged at x^t: the pairs within dhat there
+  int2* fpt = nullptr;               // broad-phase output at x^t
+  int2* fee = nullptr;
+  int64_t fbcap = 0;
+  int4* fv = nullptr;                // [fcap] each lagged pair's four vertices
+  double* fw = nullptr;              // [fcap][8] w[4], n[3], mu lambda
+  int fcap = 0;
+  int nfr = 0;                       // lagged pairs of the current step
 };
 }  // namespace mls
 
@@ -890,6 +898,7 @@ mls_status contact_energy(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double a
 mls_status contact_ccd(mls_ctx* ctx, const Vec4d* x, const Vec4d* d, double* t);
 mls_status contact_galerkin(mls_ctx* ctx, const void* val);          // cross-body U_i^T H_ij U_j into Ac
 void contact_invalidate(mls_ctx* ctx);                               // x or d changed: sweep again
+mls_status contact_friction_lag(mls_ctx* ctx);                       // friction pairs and frames at x^t
 void contact_free(mls_ctx* ctx);
 mls_status warm_start_begin(mls_ctx* ctx, int* used);
 mls_status warm_start_first_iteration(mls_ctx* ctx);
