@@ -1159,6 +1159,7 @@ mls_status mls_assemble(mls_ctx* ctx, const double* x, const double* x_t, const 
   if (st != MLS_OK) return st;
   if (!x || !x_t || !v_t) return fail(ctx, MLS_EINVAL, "null pointer");
   if ((st = set_timestep(ctx, x_t, v_t, dt)) != MLS_OK) return st;
+  if ((st = contact_friction_lag(ctx)) != MLS_OK) return st;  // friction between bodies lagged at this x^t
   if ((st = launch_pack(ctx, x, ctx->xk)) != MLS_OK) return st;
   if ((st = assemble_at(ctx, ctx->xk, nullptr)) != MLS_OK) return st;
   if (grad_out && (st = launch_unpack(ctx, ctx->grad, grad_out)) != MLS_OK) return st;
