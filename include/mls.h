@@ -287,7 +287,8 @@ mls_status mls_set_friction(mls_ctx* ctx, double mu, double eps_v);
  * Blocks of H between vertices of different bodies go to spare slots of the
  * surface-vertex rows: spare slots per row (0 = 32).  Call after
  * mls_upload_mesh and before mls_upload_basis / mls_upload_cubature; it
- * rebuilds H's sparsity.  body = NULL turns mesh-mesh contact off.
+ * rebuilds H's sparsity.  body = NULL turns mesh-mesh contact off.  With
+ * mls_set_friction mu > 0 the pairs also carry friction (see there).
  * MLS_EINVAL for a negative label, dhat <= 0 or kappa <= 0, spare < 0, no
  * mesh, or an uploaded basis or cubature.  A timestep fails with MLS_ENOMEM
  * when a vertex touches more vertices of other bodies than its spare slots
