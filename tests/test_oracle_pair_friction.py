@@ -203,3 +203,19 @@ def test_sliding_block_sticks_and_momentum_is_conserved():
     x0, _ = newton.timestep(p0)
     slip0 = np.linalg.norm(pf._u(x0), axis=1)       # without friction: slides on by 0.3 h = 5 mm
     assert np.allclose(slip0, 0.3 * s.dt, rtol=1e-2)
+
+
+def test_no_pair_within_dhat_gives_no_friction():
+    """Bodies farther apart than dhat at x^t: no lagged pair, D = 0, a zero
+    gradient, an empty Hessian list, and the problem's H is the frictionless one."""
+    s, body = synth.two_block_scene(gap=0.004, speed=0.0, voxels=(1, 1, 1))   # 4 mm > dhat = 1 mm
+    n0 = int((body == 0).sum())
+    s.v0[n0:, 0] = 0.3
+    p = ip.Problem(s, body=body, mu=MU, eps_v=EPS_V)
+    pf = p.pair_friction
+    assert pf is not None and len(pf.vids) == 0
+    x = p.x_tilde
+    assert pf.energy(x) == 0.0 and not np.any(pf.gradient(x)) and pf.hessian_pairs(x).shape == (0, 12, 12)
+    p0 = ip.Problem(s, body=body)
+    assert p.energy(x) == p0.energy(x)
+    assert (p.hessian(x) != p0.hessian(x)).nnz == 0
